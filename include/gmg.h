@@ -1,0 +1,201 @@
+/*
+ * gmg.h -- C ABI of the B300 (sm_103a) matrix-free Galerkin geometric-multigrid
+ * preconditioned-CG solver for the frozen-density 3D SIMP elasticity system
+ * K(rho) u = f on a structured grid of unit hex8 elements.
+ *
+ * The method is the one of "A Matrix-Free Galerkin Multigrid Solver and
+ * Failure-Mode Screen for Single-GPU 3D SIMP Linear Systems" (arXiv 2604.26441):
+ *   - Sec. "Problem Setup", Eq. simp_filter / Eq. state_eq: E_e = Emin +
+ *     (E0 - Emin) rho_e^p, K = sum_e E_e K_e, free-DOF system K_ff u_f = f_f;
+ *   - Sec. "Transfer Operators and Boundary Masking": 2:1 trilinear transfers
+ *     (Eq. trilinear_weights, Eq. vector_prolongation), Dirichlet inheritance by
+ *     injection, matrix-free fine operator (Eq. mf_matvec), element-wise level-1
+ *     Galerkin operator (Eq. galerkin_level1), Galerkin triple products below;
+ *   - Sec. "Chebyshev-Jacobi Smoother" (Algorithm cheb) and damped Jacobi;
+ *   - Sec. "Matrix-Free V-Cycle" (Eq. vcycle) with a dense Cholesky coarsest solve;
+ *   - Sec. "Outer Krylov Solver and Convergence Statement": left-preconditioned
+ *     CG, acceptance only by the true residual ||f - K u|| / ||f|| < tol.
+ *
+ * Conventions shared by every entry point:
+ *   - grid: nx, ny, nz unit elements; node n = i + (nx+1)*(j + (ny+1)*k);
+ *     DOF 3n + c (c = x, y, z); element e = ex + nx*(ey + ny*ez);
+ *   - all vectors are node-major with 3 values per node (length 3*n_nodes of
+ *     the level they live on); fixed DOFs are ignored on input and written as 0;
+ *   - pointers named *_dev are CUDA device pointers owned by the caller; the
+ *     library never frees them and keeps no reference past the call; the
+ *     handle owns the hierarchy and all workspaces;
+ *   - every call returns an int status: 0 = success, > 0 = a solve outcome that
+ *     is not success (GMG_NOT_CONVERGED, GMG_NONFINITE), < 0 = an error; no C++
+ *     exception crosses the ABI; gmg_last_error() gives a text for the last error
+ *     of the calling thread;
+ *   - all device work is issued on the stream given in gmg_options.stream
+ *     (NULL = the legacy default stream).  gmg_setup and gmg_solve return after
+ *     their work is complete; the other compute calls are asynchronous.
+ */
+#ifndef GMG_B300_H
+#define GMG_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define GMG_OK 0
+#define GMG_NOT_CONVERGED 1      /* iteration cap reached; u holds the last iterate */
+#define GMG_NONFINITE 2          /* a non-finite residual or step length appeared */
+#define GMG_ERR_ARG (-1)         /* bad argument (null pointer, size, level index...) */
+#define GMG_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define GMG_ERR_CHOLESKY (-3)    /* coarsest matrix not positive definite */
+#define GMG_ERR_SMOOTHER (-4)    /* damped Jacobi with omega * lambda_max >= 2 */
+#define GMG_ERR_NOMEM (-5)       /* device allocation failed */
+#define GMG_ERR_NO_DEVICE (-6)   /* no CUDA device usable by this build (sm_103a) */
+
+/* ---- boundary conditions ----------------------------------------------- */
+#define GMG_BC_CLAMP_XMIN 0      /* every DOF of the face i = 0 fixed */
+#define GMG_BC_MASK 1            /* per-DOF flags supplied by the caller */
+
+/* ---- smoothers ---------------------------------------------------------- */
+#define GMG_SMOOTHER_JACOBI 0
+#define GMG_SMOOTHER_CHEBYSHEV 1
+
+typedef struct gmg_handle gmg_handle;
+
+typedef struct {
+    int nx, ny, nz;              /* element counts, each >= 1 */
+} gmg_grid;
+
+typedef struct {
+    int kind;                    /* GMG_BC_CLAMP_XMIN or GMG_BC_MASK */
+    const uint8_t* fixed;        /* HOST pointer, 3*n_nodes bytes, 1 = fixed (kind == MASK) */
+} gmg_bc;
+
+typedef struct {
+    int levels;                  /* number of grids including the fine one; 0 = automatic
+                                    (coarsen while the coarsest free-DOF count exceeds
+                                    chol_cutoff and every element count is >= 2) */
+    int smoother, degree;        /* fine-level smoother kind and steps per pass */
+    int coarse_smoother;         /* levels 1..L-1; -1 = same as the fine level */
+    int coarse_degree;           /* -1 = same as the fine level */
+    double omega;                /* Jacobi damping, fine level */
+    double coarse_omega;         /* Jacobi damping, coarse levels; <= 0: same as omega */
+    double cheb_alpha;           /* Chebyshev band [alpha*lam, lam], paper default 1/30 */
+    double lambda_safety;        /* Chebyshev uses lam = safety * power-iteration estimate */
+    int power_iters_fine;        /* power iterations for lambda_max(D^-1 K), fine (20) */
+    int power_iters_coarse;      /* ... on assembled levels (10) */
+    int chol_cutoff;             /* dense-Cholesky size limit for the coarsest level (5000) */
+    void* stream;                /* cudaStream_t for all device work; NULL = default stream */
+} gmg_options;
+
+typedef struct {
+    int status;                  /* same value the solve call returned */
+    int iterations;              /* completed PCG updates */
+    int replacements;            /* residual replacements after a failed true-residual check */
+    double rel_residual;         /* FP64 true ||f - K u|| / ||f|| over free DOFs at return */
+    double rel_residual_recursive; /* last recursive (FP32-updated) residual ratio */
+    double solve_ms;             /* wall time of the call on the host clock */
+} gmg_info;
+
+/* Fills *opt with the paper's defaults: 4 levels, Chebyshev degree 2 on the
+ * fine level, 2 Jacobi steps with omega 0.5 on the coarse levels, alpha = 1/30,
+ * lambda_safety 1.1, 20/10 power iterations, Cholesky cutoff 5000, NULL stream. */
+void gmg_default_options(gmg_options* opt);
+
+/* Builds the hierarchy for one frozen density field (Eq. simp_filter, Eq.
+ * state_eq, Eq. galerkin_level1, "Coarser levels", "Spectral-radius estimation",
+ * coarsest dense Cholesky of K^L_ff + eps I with eps = max(mean_diag 1e-8, 1e-14)).
+ *   rho_dev : device float[nx*ny*nz] densities, element order as above;
+ *   p, E0, Emin : SIMP law; nu : Poisson ratio of the unit element stiffness;
+ *   bc : Dirichlet set (the mask, if any, is copied; the pointer is not kept);
+ *   opt : options, or NULL for gmg_default_options().
+ * On success *h receives a new handle (free it with gmg_destroy).  Errors:
+ * GMG_ERR_ARG, GMG_ERR_CUDA, GMG_ERR_NOMEM, GMG_ERR_CHOLESKY, GMG_ERR_SMOOTHER,
+ * GMG_ERR_NO_DEVICE; *h is left NULL. */
+int gmg_setup(gmg_handle** h, const gmg_grid* g, const float* rho_dev, double p, double E0,
+              double Emin, double nu, const gmg_bc* bc, const gmg_options* opt);
+
+/* Solves K_ff u_f = f_f by GMG-preconditioned CG (Sec. "Outer Krylov Solver and
+ * Convergence Statement").  f_dev: device double[3*n_nodes]; u_dev: device
+ * double[3*n_nodes], on entry the initial guess (zeros = cold start), on exit the
+ * solution with fixed DOFs set to 0.  The inner iteration runs in FP32 with FP64
+ * dot products; u is accumulated in FP64 and a solve is accepted only when the
+ * FP64 true residual is below tol.  Returns GMG_OK, GMG_NOT_CONVERGED (maxit
+ * reached), GMG_NONFINITE, or an error.  info may be NULL. */
+int gmg_solve(gmg_handle* h, const double* f_dev, double* u_dev, double tol, int maxit,
+              gmg_info* info);
+
+/* y = K_ff u on the fine level in FP32 (Eq. mf_matvec): u_dev, y_dev device
+ * float[3*n_nodes]; fixed DOFs of u are ignored and written as 0 in y.
+ * Asynchronous on the handle's stream.  u_dev and y_dev must not overlap. */
+int gmg_apply(gmg_handle* h, const float* u_dev, float* y_dev);
+
+/* Frees every device resource of the handle.  NULL is accepted. */
+void gmg_destroy(gmg_handle* h);
+
+/* Static text for a status code. */
+const char* gmg_status_str(int status);
+
+/* Text of the last error recorded on the calling thread ("" if none). */
+const char* gmg_last_error(void);
+
+/* ---- introspection and per-step entry points ----------------------------
+ * These expose the individual steps of the hot path so that each can be checked
+ * on its own.  Vectors are device float[3*n_nodes(level)] unless stated; all
+ * are asynchronous on the handle's stream except the host-output getters, which
+ * synchronise that stream before returning. */
+
+int gmg_num_levels(const gmg_handle* h);
+
+/* dims[0..2] = element counts of the level. */
+int gmg_level_dims(const gmg_handle* h, int level, int dims[3]);
+
+/* HOST uint8[n_nodes(level)] of fixed-component bits (bit c set = DOF c fixed),
+ * inherited level to level by injection (Sec. "Transfer Operators and Boundary
+ * Masking"). */
+int gmg_get_mask(gmg_handle* h, int level, uint8_t* host_out);
+
+/* HOST double[243*n_nodes(level)] (level >= 1): the 3x3-block 27-point Galerkin
+ * operator K^level in FP64 (Eq. galerkin_level1 for level 1, R K P below),
+ * plane-major: entry (slot s, row r, col c) of node n at [(s*9 + r*3 + c)*n_nodes
+ * + n], slot s = (dx+1) + 3(dy+1) + 9(dz+1) for the neighbour n + (dx, dy, dz).
+ * Rows and columns of fixed DOFs and neighbours outside the grid are 0. */
+int gmg_get_bsr(gmg_handle* h, int level, double* host_out);
+
+/* lambda_max(D^-1 K) estimate of a level before lambda_safety (Sec.
+ * "Spectral-radius estimation"), and an override that also refreshes the
+ * level's smoother coefficients. */
+int gmg_get_lambda(gmg_handle* h, int level, double* out);
+int gmg_set_lambda(gmg_handle* h, int level, double lam);
+
+/* y = K^level x (masked), FP32 (level 0 matrix-free, levels >= 1 from the BSR). */
+int gmg_level_apply(gmg_handle* h, int level, const float* x_dev, float* y_dev);
+
+/* One smoothing pass (degree steps of the level's smoother, Algorithm cheb or
+ * damped Jacobi) on K^level x = b; x_is_zero != 0 means x enters as 0 (and is
+ * not read). */
+int gmg_level_smooth(gmg_handle* h, int level, const float* b_dev, float* x_dev, int x_is_zero);
+
+/* coarse = R^level fine (R = P^T, Eq. vector_prolongation; coarse fixed DOFs 0):
+ * fine on `level`, coarse on level+1. */
+int gmg_restrict(gmg_handle* h, int level, const float* fine_dev, float* coarse_dev);
+
+/* fine += P^level coarse (fine fixed DOFs untouched). */
+int gmg_prolong_add(gmg_handle* h, int level, const float* coarse_dev, float* fine_dev);
+
+/* x = (K^L_ff + eps I)^-1 b on the coarsest level (FP64 Cholesky factor). */
+int gmg_coarse_solve(gmg_handle* h, const float* b_dev, float* x_dev);
+
+/* z = V(r): one V-cycle of Eq. vcycle on the fine level. */
+int gmg_vcycle(gmg_handle* h, const float* r_dev, float* z_dev);
+
+/* FP64 true residual r = f - K u on the fine level (r_dev may be NULL) and
+ * *rel_out = ||r_free|| / ||f_free|| (HOST double; synchronises). */
+int gmg_residual64(gmg_handle* h, const double* f_dev, const double* u_dev, double* r_dev,
+                   double* rel_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMG_B300_H */

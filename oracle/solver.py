@@ -24,8 +24,9 @@ literal reading, under which the 20-step estimate sits ~8 % below lambda_max on
 a 40^3 cantilever and degree-2 Chebyshev-PCG fails the 200 cap there, whereas
 the paper reports it converging); an iteration is one
 completed x/r update; when the recursive residual passes the test but the
-recomputed true residual does not, the residual is replaced by the true one and
-the search direction restarts.
+recomputed true residual does not, the recursive residual is replaced by the
+true one and the search direction restarts from its preconditioned value (a
+replacement that keeps the old direction stalls near the attainable accuracy).
 """
 
 from __future__ import annotations
@@ -153,7 +154,7 @@ def pcg(apply_K, precond, f: np.ndarray, x0: np.ndarray | None = None, tol: floa
             rel_t = float(np.linalg.norm(rt)) / nf
             if rel_t < tol:
                 return PCGResult(x, OK, k, rel_t, hist)
-            r = rt
+            r = rt  # residual replacement, and the search direction restarts
             z = precond(r)
             p = z.copy()
             rz = float(r @ z)

@@ -1,0 +1,713 @@
+// C ABI of the GMG-preconditioned CG solver: set-up of the hierarchy, the
+// V-cycle of Eq. vcycle, and the outer PCG with true-residual acceptance
+// (Sec. "Outer Krylov Solver and Convergence Statement").  Host code here only
+// sequences kernels and moves scalars; every arithmetic step runs on the GPU.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+
+#include "internal.cuh"
+
+using namespace gmg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CU(expr)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess) return fail(GMG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(expr)                 \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != GMG_OK) return rc_; \
+    } while (0)
+
+template <class T>
+int dalloc(gmg_handle* h, T** p, size_t count) {
+    void* q = nullptr;
+    const size_t bytes = sizeof(T) * (count ? count : 1);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GMG_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return GMG_OK;
+}
+
+void dfree(gmg_handle* h, void* p) {
+    if (!p) return;
+    for (auto& a : h->allocs)
+        if (a == p) { a = nullptr; break; }
+    cudaFree(p);
+}
+
+long long nodes_of(int nx, int ny, int nz) { return (long long)(nx + 1) * (ny + 1) * (nz + 1); }
+
+// ---- level operations -----------------------------------------------------
+FineArgs fine_args(gmg_handle* h) {
+    const Level& l = h->lev[0];
+    FineArgs a{};
+    a.nx = l.nx; a.ny = l.ny; a.nz = l.nz;
+    a.E = h->E32; a.mask = l.mask; a.kd = h->kd; a.coef = l.coef;
+    return a;
+}
+
+BsrArgs bsr_args(gmg_handle* h, int li) {
+    const Level& l = h->lev[li];
+    BsrArgs a{};
+    a.nx = l.nx; a.ny = l.ny; a.nz = l.nz; a.nn = l.nn;
+    a.A = l.A32; a.invdiag = l.invdiag; a.mask = l.mask; a.coef = l.coef;
+    return a;
+}
+
+int partial_count(gmg_handle* h, int li, int kind) {
+    // kind 0: operator-kernel partials, 1: vector-kernel partials
+    if (kind == 1) return vec_grid_blocks();
+    if (li == 0) return fine_grid_blocks(h->lev[0].nx, h->lev[0].ny, h->lev[0].nz);
+    return bsr_grid_blocks(h->lev[li].nn);
+}
+
+// y = K^l x (masked); with dot: partial += x . y and finalised into `slot`.
+void level_apply(gmg_handle* h, int li, const float* x, float* y, int dot_slot = -1, int op = FIN_NONE) {
+    cudaStream_t s = h->stream;
+    const bool dot = dot_slot >= 0;
+    if (li == 0) {
+        FineArgs a = fine_args(h);
+        a.xin = x; a.out = y; a.partial = dot ? h->partials : nullptr;
+        launch_fine(FM_APPLY, dot, a, h->keF, s);
+    } else {
+        BsrArgs a = bsr_args(h, li);
+        a.xin = x; a.out = y; a.partial = dot ? h->partials : nullptr;
+        launch_bsr(FM_APPLY, dot, a, s);
+    }
+    if (dot) launch_finalize(h->partials, partial_count(h, li, 0), h->sc, dot_slot, op, s);
+}
+
+void level_resid(gmg_handle* h, int li, const float* b, const float* x, float* t) {
+    if (li == 0) {
+        FineArgs a = fine_args(h);
+        a.xin = x; a.b = b; a.out = t;
+        launch_fine(FM_RESID, 0, a, h->keF, h->stream);
+    } else {
+        BsrArgs a = bsr_args(h, li);
+        a.xin = x; a.b = b; a.out = t;
+        launch_bsr(FM_RESID, 0, a, h->stream);
+    }
+}
+
+// One smoother step k on level li: reads x_cur (ignored when zero_init), writes x_next.
+void smooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, const float* xcur, float* xnext,
+                 bool write_d, bool dot) {
+    Level& l = h->lev[li];
+    float* d = li == 0 ? h->d0 : l.d;
+    cudaStream_t s = h->stream;
+    if (li == 0) {
+        FineArgs a = fine_args(h);
+        a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
+        a.partial = dot ? h->partials : nullptr;
+        if (zero_init) launch_fine_smooth0(a, s);
+        else { a.xin = xcur; launch_fine(FM_SMOOTH, dot, a, h->keF, s); }
+    } else {
+        BsrArgs a = bsr_args(h, li);
+        a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
+        a.partial = dot ? h->partials : nullptr;
+        if (zero_init) launch_bsr_smooth0(a, s);
+        else { a.xin = xcur; launch_bsr(FM_SMOOTH, dot, a, s); }
+    }
+}
+
+// A smoothing pass of `degree` steps.  Writes alternate S, X, S, ...; returns the
+// buffer holding the result.  With dot_slot >= 0 the last step also forms b . x.
+float* smooth_pass(gmg_handle* h, int li, const float* b, float* cur, float* X, float* S, bool zero_init,
+                   int& writes, int dot_slot = -1, int op = FIN_NONE) {
+    Level& l = h->lev[li];
+    const bool cheb = l.kind == GMG_SMOOTHER_CHEBYSHEV;
+    for (int k = 0; k < l.degree; ++k) {
+        float* next = (writes % 2 == 0) ? S : X;
+        const bool last = k == l.degree - 1;
+        const bool dot = last && dot_slot >= 0;
+        smooth_step(h, li, k, zero_init && k == 0, b, cur, next, cheb && !last, dot);
+        if (dot) launch_finalize(h->partials, partial_count(h, li, 0), h->sc, dot_slot, op, h->stream);
+        cur = next;
+        ++writes;
+    }
+    return cur;
+}
+
+// Eq. vcycle on level li: X = V(b), using S as the ping-pong partner.
+void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int dot_slot, int op) {
+    Level& l = h->lev[li];
+    cudaStream_t s = h->stream;
+    if (li == h->L - 1) {
+        launch_coarse_solve(h->nL, h->free_idx, h->Ainv, b, X, 3 * l.nn, s);
+        return;
+    }
+    int writes = 0;
+    float* cur = smooth_pass(h, li, b, nullptr, X, S, true, writes);
+    float* t = li == 0 ? h->t0 : l.t;
+    level_resid(h, li, b, cur, t);
+    Level& c = h->lev[li + 1];
+    launch_restrict(l, c, t, c.b, s);
+    vcycle_level(h, li + 1, c.b, c.x, c.x2, -1, FIN_NONE);
+    launch_prolong_add(l, c, c.x, cur, s);
+    smooth_pass(h, li, b, cur, X, S, false, writes, dot_slot, op);
+}
+
+// lambda_max(D^{-1} K) of level li by power iteration (Sec. "Spectral-radius estimation").
+void power_iteration(gmg_handle* h, int li, int iters) {
+    Level& l = h->lev[li];
+    cudaStream_t s = h->stream;
+    const long long n = 3 * l.nn;
+    float* v = li == 0 ? h->t0 : l.t;
+    float* w = li == 0 ? h->x2_0 : l.x2;
+    float* y = li == 0 ? h->d0 : l.d;
+    cudaMemsetAsync(h->sc + SC_TMP, 0, sizeof(double), s);
+    launch_power_start(v, l.mask, l.nn, s);
+    launch_dot_f32(v, v, n, h->partials, s);
+    launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_NRM, FIN_NRMCHK, s);
+    launch_scale_by_inv_sqrt(v, n, h->sc, SC_NRM, s);
+    for (int it = 0; it < iters; ++it) {
+        level_apply(h, li, v, y);
+        if (li == 0) launch_scale_invdiag_fine(y, w, h->E32, l.mask, l.nx, l.ny, l.nz, h->kd, s);
+        else launch_scale_invdiag_bsr(y, w, l.invdiag, n, s);
+        launch_dot_f32(w, w, n, h->partials, s);
+        launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_NRM, FIN_NRMCHK, s);
+        launch_scale_by_inv_sqrt(w, n, h->sc, SC_NRM, s);
+        std::swap(v, w);
+    }
+    level_apply(h, li, v, y);
+    launch_dot_f32(v, y, n, h->partials, s);
+    launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_VKV, FIN_NONE, s);
+    if (li == 0) launch_diag_dot_fine(v, h->E32, l.mask, l.nx, l.ny, l.nz, h->kd, h->partials, s);
+    else launch_diag_dot_bsr(v, l.invdiag, n, h->partials, s);
+    launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_VDV, FIN_NONE, s);
+    launch_lambda_finish(h->sc, h->lam + li, s);
+}
+
+void refresh_coef(gmg_handle* h, int li) {
+    Level& l = h->lev[li];
+    launch_smoother_coef(l.coef, h->lam + li, l.kind, l.degree, l.omega, h->opt.cheb_alpha, h->opt.lambda_safety,
+                         h->stream);
+}
+
+int check_level(const gmg_handle* h, int li) {
+    if (!h) return fail(GMG_ERR_ARG, "null handle");
+    if (li < 0 || li >= h->L) return fail(GMG_ERR_ARG, "level index out of range");
+    return GMG_OK;
+}
+
+int sync_scalars(gmg_handle* h) {
+    CU(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return GMG_OK;
+}
+
+int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E0, double Emin, double nu,
+          const gmg_bc* bc) {
+    cudaStream_t s = h->stream;
+    const gmg_options& o = h->opt;
+    // ---- fine level and masks
+    Level& l0 = h->lev[0];
+    l0.nx = g->nx; l0.ny = g->ny; l0.nz = g->nz;
+    l0.nn = nodes_of(g->nx, g->ny, g->nz);
+    TRY(dalloc(h, &l0.mask, l0.nn));
+    if (bc->kind == GMG_BC_CLAMP_XMIN) {
+        launch_mask_clamp(l0.mask, l0.nx, l0.ny, l0.nz, s);
+    } else {
+        uint8_t* tmp = nullptr;
+        TRY(dalloc(h, &tmp, 3 * l0.nn));
+        CU(cudaMemcpyAsync(tmp, bc->fixed, 3 * l0.nn, cudaMemcpyHostToDevice, s));
+        launch_mask_from_dofs(tmp, l0.mask, l0.nn, s);
+        CU(cudaStreamSynchronize(s));
+        dfree(h, tmp);
+    }
+    int* cnt = nullptr;
+    TRY(dalloc(h, &cnt, 1));
+    auto count_free = [&](const Level& l, int* out) -> int {
+        launch_count_free(l.mask, l.nn, cnt, s);
+        CU(cudaMemcpyAsync(out, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        return GMG_OK;
+    };
+    TRY(count_free(l0, &l0.n_free));
+    int L = 1;
+    const int want = o.levels;
+    while (true) {
+        const Level& f = h->lev[L - 1];
+        const bool can = f.nx >= 2 && f.ny >= 2 && f.nz >= 2 && L < kMaxLevels;
+        const bool more = want > 0 ? (L < want) : (f.n_free > o.chol_cutoff);
+        if (!more) break;
+        if (!can) {
+            if (want > 0) return fail(GMG_ERR_ARG, "grid too small for the requested number of levels");
+            break;
+        }
+        Level& c = h->lev[L];
+        c.nx = f.nx / 2; c.ny = f.ny / 2; c.nz = f.nz / 2;
+        c.nn = nodes_of(c.nx, c.ny, c.nz);
+        TRY(dalloc(h, &c.mask, c.nn));
+        launch_mask_inject(f, c, s);
+        TRY(count_free(c, &c.n_free));
+        ++L;
+    }
+    h->L = L;
+    // ---- smoother settings and buffers
+    for (int li = 0; li < L; ++li) {
+        Level& l = h->lev[li];
+        if (li == 0) { l.kind = o.smoother; l.degree = o.degree; l.omega = o.omega; }
+        else {
+            l.kind = o.coarse_smoother >= 0 ? o.coarse_smoother : o.smoother;
+            l.degree = o.coarse_degree > 0 ? o.coarse_degree : o.degree;
+            l.omega = o.coarse_omega > 0 ? o.coarse_omega : o.omega;
+        }
+        TRY(dalloc(h, &l.coef, 2 * kMaxDegree));
+        if (li > 0) {
+            TRY(dalloc(h, &l.A64, (size_t)kPlanes * l.nn));
+            TRY(dalloc(h, &l.A32, (size_t)kPlanes * l.nn));
+            TRY(dalloc(h, &l.invdiag, 3 * l.nn));
+            TRY(dalloc(h, &l.x, 3 * l.nn));
+            TRY(dalloc(h, &l.x2, 3 * l.nn));
+            TRY(dalloc(h, &l.b, 3 * l.nn));
+            TRY(dalloc(h, &l.t, 3 * l.nn));
+            TRY(dalloc(h, &l.d, 3 * l.nn));
+        }
+    }
+    const long long n0 = 3 * l0.nn;
+    TRY(dalloc(h, &h->r, n0));
+    TRY(dalloc(h, &h->z, n0));
+    TRY(dalloc(h, &h->p, n0));
+    TRY(dalloc(h, &h->q, n0));
+    TRY(dalloc(h, &h->x2_0, n0));
+    TRY(dalloc(h, &h->t0, n0));
+    TRY(dalloc(h, &h->d0, n0));
+    const long long ne = (long long)l0.nx * l0.ny * l0.nz;
+    TRY(dalloc(h, &h->E32, ne));
+    TRY(dalloc(h, &h->E64, ne));
+    TRY(dalloc(h, &h->lam, kMaxLevels));
+    TRY(dalloc(h, &h->sc, SC_COUNT));
+    CU(cudaMemsetAsync(h->sc, 0, sizeof(double) * SC_COUNT, s));
+    int maxp = vec_grid_blocks();
+    maxp = std::max(maxp, fine_grid_blocks(l0.nx, l0.ny, l0.nz));
+    for (int li = 1; li < L; ++li) maxp = std::max(maxp, bsr_grid_blocks(h->lev[li].nn));
+    h->max_partials = maxp;
+    TRY(dalloc(h, &h->partials, maxp));
+    CU(cudaMallocHost(&h->pinned, sizeof(double) * SC_COUNT));
+    h->sc_host = static_cast<double*>(h->pinned);
+
+    // ---- moduli (Eq. simp_filter) and K_e
+    launch_moduli(rho, ne, p, E0, Emin, h->E64, h->E32, s);
+    double* Ke = nullptr;
+    TRY(dalloc(h, &Ke, 576));
+    launch_element_stiffness(nu, Ke, s);
+    CU(cudaMemcpyAsync(h->keD.v, Ke, sizeof(double) * 576, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (int i = 0; i < 576; ++i) h->keF.v[i] = (float)h->keD.v[i];
+    h->kd = h->keF.v[0];
+
+    // ---- Galerkin hierarchy
+    if (L >= 2) {
+        Level& c = h->lev[1];
+        double *Mpat = nullptr, *Kc = nullptr;
+        const long long nce = (long long)c.nx * c.ny * c.nz;
+        TRY(dalloc(h, &Mpat, 27 * 576));
+        TRY(dalloc(h, &Kc, (size_t)nce * 576));
+        launch_child_patterns(Ke, Mpat, s);
+        launch_coarse_element_matrices(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, Ke, Mpat, Kc, s);
+        launch_gather_level1(c, Kc, c.A64, s);
+        launch_finish_bsr(c, s);
+        CU(cudaStreamSynchronize(s));
+        dfree(h, Kc);
+        dfree(h, Mpat);
+        for (int li = 2; li < L; ++li) {
+            launch_galerkin_rap(h->lev[li - 1], h->lev[li], s);
+            launch_finish_bsr(h->lev[li], s);
+        }
+    }
+    CU(cudaGetLastError());
+
+    // ---- spectral estimates and smoother coefficients
+    for (int li = 0; li < L; ++li) {
+        power_iteration(h, li, li == 0 ? o.power_iters_fine : o.power_iters_coarse);
+        refresh_coef(h, li);
+    }
+    double lam_host[kMaxLevels];
+    CU(cudaMemcpyAsync(lam_host, h->lam, sizeof(double) * L, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (int li = 0; li + 1 < L; ++li) {
+        const Level& l = h->lev[li];
+        if (l.kind == GMG_SMOOTHER_JACOBI && l.omega * lam_host[li] >= 2.0) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "damped Jacobi unstable on level %d: omega %.3g * lambda_max %.4g >= 2", li,
+                     l.omega, lam_host[li]);
+            return fail(GMG_ERR_SMOOTHER, buf);
+        }
+    }
+
+    // ---- coarsest level: dense K^L_ff + eps I, Cholesky, inverse
+    Level& cl = h->lev[L - 1];
+    TRY(dalloc(h, &h->free_idx, 3 * cl.nn));
+    launch_free_index(cl.mask, cl.nn, h->free_idx, cnt, s);
+    CU(cudaMemcpyAsync(&h->nL, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (h->nL > 0) {
+        if (h->nL > o.chol_cutoff)
+            return fail(GMG_ERR_ARG, "coarsest level has " + std::to_string(h->nL) +
+                                         " free DOFs, more than the dense-Cholesky cutoff");
+        const int n = h->nL;
+        double *dense = nullptr, *work = nullptr, *eps_dev = nullptr;
+        int* info = nullptr;
+        TRY(dalloc(h, &dense, (size_t)n * n));
+        TRY(dalloc(h, &work, (size_t)n * n));
+        TRY(dalloc(h, &h->Ainv, (size_t)n * n));
+        TRY(dalloc(h, &eps_dev, 1));
+        TRY(dalloc(h, &info, 1));
+        if (L == 1) {
+            // one-level hierarchy: assemble the fine operator into the 27-slot
+            // planes (element matrices E_e K_e scattered by owner nodes) so that the
+            // dense coarsest gather below can read it
+            double* Kc = nullptr;
+            const long long ne0 = (long long)l0.nx * l0.ny * l0.nz;
+            TRY(dalloc(h, &l0.A64, (size_t)kPlanes * l0.nn));
+            TRY(dalloc(h, &l0.A32, (size_t)kPlanes * l0.nn));
+            TRY(dalloc(h, &l0.invdiag, 3 * l0.nn));
+            TRY(dalloc(h, &Kc, (size_t)ne0 * 576));
+            launch_fine_element_matrices(h->E64, ne0, Ke, Kc, s);
+            launch_gather_level1(l0, Kc, l0.A64, s);
+            launch_finish_bsr(l0, s);
+            CU(cudaStreamSynchronize(s));
+            dfree(h, Kc);
+        }
+        launch_dense_gather(cl, h->free_idx, n, dense, s);
+        launch_regularise(dense, n, eps_dev, s);
+        CU(cudaMemcpyAsync(&h->eps, eps_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+        const int rc = cholesky_and_inverse(dense, n, work, info, h->Ainv, s);
+        if (rc == GMG_ERR_CHOLESKY) return fail(rc, "coarsest matrix is not positive definite");
+        if (rc != GMG_OK) return fail(rc, "coarsest factorisation failed");
+        CU(cudaStreamSynchronize(s));
+        dfree(h, dense);
+        dfree(h, work);
+    }
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(s));
+    return GMG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void gmg_default_options(gmg_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->levels = 4;
+    o->smoother = GMG_SMOOTHER_CHEBYSHEV;
+    o->degree = 2;
+    o->coarse_smoother = GMG_SMOOTHER_JACOBI;
+    o->coarse_degree = 2;
+    o->omega = 0.5;
+    o->coarse_omega = 0.5;
+    o->cheb_alpha = 1.0 / 30.0;
+    o->lambda_safety = 1.1;
+    o->power_iters_fine = 20;
+    o->power_iters_coarse = 10;
+    o->chol_cutoff = 5000;
+    o->stream = nullptr;
+}
+
+const char* gmg_status_str(int st) {
+    switch (st) {
+        case GMG_OK: return "ok";
+        case GMG_NOT_CONVERGED: return "not converged (iteration cap)";
+        case GMG_NONFINITE: return "non-finite residual or step";
+        case GMG_ERR_ARG: return "invalid argument";
+        case GMG_ERR_CUDA: return "CUDA error";
+        case GMG_ERR_CHOLESKY: return "coarsest Cholesky failed";
+        case GMG_ERR_SMOOTHER: return "unstable Jacobi damping";
+        case GMG_ERR_NOMEM: return "device out of memory";
+        case GMG_ERR_NO_DEVICE: return "no usable CUDA device";
+        default: return "unknown status";
+    }
+}
+
+const char* gmg_last_error(void) { return g_err.c_str(); }
+
+void gmg_destroy(gmg_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    for (void* p : h->allocs)
+        if (p) cudaFree(p);
+    if (h->pinned) cudaFreeHost(h->pinned);
+    delete h;
+}
+
+int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double p, double E0, double Emin,
+              double nu, const gmg_bc* bc, const gmg_options* opt) {
+    if (!out) return fail(GMG_ERR_ARG, "null output handle pointer");
+    *out = nullptr;
+    if (!g || !rho_dev || !bc) return fail(GMG_ERR_ARG, "null grid, density or boundary-condition pointer");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail(GMG_ERR_ARG, "element counts must be >= 1");
+    if (nodes_of(g->nx, g->ny, g->nz) > (1LL << 31) / 3) return fail(GMG_ERR_ARG, "grid too large");
+    if (bc->kind != GMG_BC_CLAMP_XMIN && bc->kind != GMG_BC_MASK) return fail(GMG_ERR_ARG, "unknown bc kind");
+    if (bc->kind == GMG_BC_MASK && !bc->fixed) return fail(GMG_ERR_ARG, "bc kind MASK needs a fixed-flag array");
+    if (!(nu > -1.0 && nu < 0.5)) return fail(GMG_ERR_ARG, "Poisson ratio outside (-1, 0.5)");
+    if (!(E0 > 0.0) || !(Emin >= 0.0) || !std::isfinite(p)) return fail(GMG_ERR_ARG, "bad SIMP parameters");
+    gmg_options o;
+    if (opt) o = *opt; else gmg_default_options(&o);
+    auto bad_kind = [](int k) { return k != GMG_SMOOTHER_JACOBI && k != GMG_SMOOTHER_CHEBYSHEV; };
+    if (bad_kind(o.smoother) || (o.coarse_smoother >= 0 && bad_kind(o.coarse_smoother)))
+        return fail(GMG_ERR_ARG, "unknown smoother kind");
+    if (o.degree < 1 || o.degree > kMaxDegree || o.coarse_degree > kMaxDegree)
+        return fail(GMG_ERR_ARG, "smoother degree outside [1, 16]");
+    if (o.levels < 0 || o.levels > kMaxLevels) return fail(GMG_ERR_ARG, "levels outside [0, 16]");
+    if (!(o.omega > 0.0) || !(o.cheb_alpha > 0.0 && o.cheb_alpha < 1.0) || !(o.lambda_safety > 0.0))
+        return fail(GMG_ERR_ARG, "bad smoother parameters");
+    if (o.power_iters_fine < 1 || o.power_iters_coarse < 1 || o.chol_cutoff < 1)
+        return fail(GMG_ERR_ARG, "bad iteration counts or cutoff");
+
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GMG_ERR_NO_DEVICE, "no CUDA device");
+    }
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(GMG_ERR_NO_DEVICE, "this library is built for sm_103a (compute capability 10.3) only");
+
+    gmg_handle* h = new gmg_handle();
+    h->opt = o;
+    h->device = dev;
+    h->stream = static_cast<cudaStream_t>(o.stream);
+    const int rc = build(h, g, rho_dev, p, E0, Emin, nu, bc);
+    if (rc != GMG_OK) {
+        std::string keep = g_err;
+        gmg_destroy(h);
+        g_err = keep;
+        return rc;
+    }
+    *out = h;
+    return GMG_OK;
+}
+
+int gmg_apply(gmg_handle* h, const float* u, float* y) {
+    if (!h || !u || !y) return fail(GMG_ERR_ARG, "null argument");
+    level_apply(h, 0, u, y);
+    CU(cudaGetLastError());
+    return GMG_OK;
+}
+
+int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, gmg_info* info) {
+    if (!h || !f || !u) return fail(GMG_ERR_ARG, "null argument");
+    if (!(tol > 0.0) || maxit < 0) return fail(GMG_ERR_ARG, "tol must be > 0 and maxit >= 0");
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = h->stream;
+    Level& l0 = h->lev[0];
+    const long long n = 3 * l0.nn;
+    double* sch = h->sc_host;
+    gmg_info inf{};
+    auto finish = [&](int st) -> int {
+        inf.status = st;
+        inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (info) *info = inf;
+        return st;
+    };
+    auto true_residual = [&](double& rel) -> int {
+        launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, h->sc, h->partials, h->keD, s);
+        launch_finalize(h->partials, partial_count(h, 0, 0), h->sc, SC_TRR, FIN_NONE, s);
+        TRY(sync_scalars(h));
+        rel = std::sqrt(sch[SC_TRR]) / std::sqrt(sch[SC_FF]);
+        return GMG_OK;
+    };
+
+    // fixed DOFs of u -> 0, nonzero count of u, ||f_free||^2
+    launch_mask_u64(u, l0.mask, l0.nn, h->partials, s);
+    launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_UNZ, FIN_NONE, s);
+    launch_dot_f64_masked(f, f, l0.mask, l0.nn, h->partials, s);
+    launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_FF, FIN_NONE, s);
+    TRY(sync_scalars(h));
+    if (!(sch[SC_FF] > 0.0)) {
+        if (!std::isfinite(sch[SC_FF])) { inf.rel_residual = NAN; return finish(GMG_NONFINITE); }
+        CU(cudaMemsetAsync(u, 0, sizeof(double) * n, s));
+        CU(cudaStreamSynchronize(s));
+        return finish(GMG_OK);
+    }
+    double rel = 0.0;
+    TRY(true_residual(rel));  // r (FP32) = f - K u, FP64 norm
+    // every later operator application sees u != 0 through the PCG updates
+    inf.rel_residual = rel;
+    inf.rel_residual_recursive = rel;
+    if (!std::isfinite(rel)) return finish(GMG_NONFINITE);
+    if (rel < tol) return finish(GMG_OK);
+    sch[SC_UNZ] = 1.0;
+    CU(cudaMemcpyAsync(h->sc + SC_UNZ, sch + SC_UNZ, sizeof(double), cudaMemcpyHostToDevice, s));
+
+    // z = V(r), rz = r . z, p = z
+    auto restart = [&]() {
+        vcycle_level(h, 0, h->r, h->z, h->x2_0, SC_RZ, FIN_NONE);
+        cudaMemcpyAsync(h->p, h->z, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
+    };
+    restart();
+    const double nf = std::sqrt(sch[SC_FF]);
+    int k = 0;
+    while (k < maxit) {
+        level_apply(h, 0, h->p, h->q, SC_PQ, FIN_ALPHA);                   // q = K p, alpha = rz / pq
+        launch_pcg_update(u, h->r, h->p, h->q, n, h->sc, h->partials, s);  // u += a p, r -= a q
+        launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_RR, FIN_NONE, s);
+        ++k;
+        TRY(sync_scalars(h));
+        const double relr = std::sqrt(sch[SC_RR]) / nf;
+        inf.iterations = k;
+        inf.rel_residual_recursive = relr;
+        if (!std::isfinite(relr) || !std::isfinite(sch[SC_ALPHA])) {
+            inf.rel_residual = relr;
+            return finish(GMG_NONFINITE);
+        }
+        if (relr < tol) {
+            TRY(true_residual(rel));
+            inf.rel_residual = rel;
+            if (rel < tol) return finish(GMG_OK);
+            if (!std::isfinite(rel)) return finish(GMG_NONFINITE);
+            ++inf.replacements;  // residual replacement (r now holds f - K u); restart the direction
+            restart();
+            continue;
+        }
+        vcycle_level(h, 0, h->r, h->z, h->x2_0, SC_RZNEW, FIN_BETA);   // z = V(r), beta
+        launch_p_update(h->p, h->z, n, h->sc, s);                         // p = z + beta p
+    }
+    TRY(true_residual(rel));
+    inf.rel_residual = rel;
+    CU(cudaGetLastError());
+    return finish(GMG_NOT_CONVERGED);
+}
+
+int gmg_num_levels(const gmg_handle* h) { return h ? h->L : 0; }
+
+int gmg_level_dims(const gmg_handle* h, int level, int dims[3]) {
+    TRY(check_level(h, level));
+    if (!dims) return fail(GMG_ERR_ARG, "null dims");
+    dims[0] = h->lev[level].nx; dims[1] = h->lev[level].ny; dims[2] = h->lev[level].nz;
+    return GMG_OK;
+}
+
+int gmg_get_mask(gmg_handle* h, int level, uint8_t* out) {
+    TRY(check_level(h, level));
+    if (!out) return fail(GMG_ERR_ARG, "null output");
+    CU(cudaMemcpyAsync(out, h->lev[level].mask, h->lev[level].nn, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return GMG_OK;
+}
+
+int gmg_get_bsr(gmg_handle* h, int level, double* out) {
+    TRY(check_level(h, level));
+    if (level == 0) return fail(GMG_ERR_ARG, "the fine level is matrix-free");
+    if (!out) return fail(GMG_ERR_ARG, "null output");
+    const Level& l = h->lev[level];
+    CU(cudaMemcpyAsync(out, l.A64, sizeof(double) * kPlanes * l.nn, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return GMG_OK;
+}
+
+int gmg_get_lambda(gmg_handle* h, int level, double* out) {
+    TRY(check_level(h, level));
+    if (!out) return fail(GMG_ERR_ARG, "null output");
+    CU(cudaMemcpyAsync(out, h->lam + level, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return GMG_OK;
+}
+
+int gmg_set_lambda(gmg_handle* h, int level, double lam) {
+    TRY(check_level(h, level));
+    if (!(lam > 0.0) || !std::isfinite(lam)) return fail(GMG_ERR_ARG, "lambda must be positive");
+    h->sc_host[SC_TMP + 1] = lam;
+    CU(cudaMemcpyAsync(h->lam + level, h->sc_host + SC_TMP + 1, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    refresh_coef(h, level);
+    CU(cudaStreamSynchronize(h->stream));
+    return GMG_OK;
+}
+
+int gmg_level_apply(gmg_handle* h, int level, const float* x, float* y) {
+    TRY(check_level(h, level));
+    if (!x || !y) return fail(GMG_ERR_ARG, "null vector");
+    level_apply(h, level, x, y);
+    CU(cudaGetLastError());
+    return GMG_OK;
+}
+
+int gmg_level_smooth(gmg_handle* h, int level, const float* b, float* x, int x_is_zero) {
+    TRY(check_level(h, level));
+    if (level == h->L - 1) return fail(GMG_ERR_ARG, "the coarsest level has no smoother");
+    if (!b || !x) return fail(GMG_ERR_ARG, "null vector");
+    Level& l = h->lev[level];
+    float* S = level == 0 ? h->x2_0 : l.x2;
+    int writes = 0;
+    float* res = smooth_pass(h, level, b, x, x, S, x_is_zero != 0, writes);
+    if (res != x) CU(cudaMemcpyAsync(x, res, sizeof(float) * 3 * l.nn, cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaGetLastError());
+    return GMG_OK;
+}
+
+int gmg_restrict(gmg_handle* h, int level, const float* fine, float* coarse) {
+    TRY(check_level(h, level));
+    if (level + 1 >= h->L) return fail(GMG_ERR_ARG, "no coarser level");
+    if (!fine || !coarse) return fail(GMG_ERR_ARG, "null vector");
+    launch_restrict(h->lev[level], h->lev[level + 1], fine, coarse, h->stream);
+    CU(cudaGetLastError());
+    return GMG_OK;
+}
+
+int gmg_prolong_add(gmg_handle* h, int level, const float* coarse, float* fine) {
+    TRY(check_level(h, level));
+    if (level + 1 >= h->L) return fail(GMG_ERR_ARG, "no coarser level");
+    if (!fine || !coarse) return fail(GMG_ERR_ARG, "null vector");
+    launch_prolong_add(h->lev[level], h->lev[level + 1], coarse, fine, h->stream);
+    CU(cudaGetLastError());
+    return GMG_OK;
+}
+
+int gmg_coarse_solve(gmg_handle* h, const float* b, float* x) {
+    if (!h || !b || !x) return fail(GMG_ERR_ARG, "null argument");
+    const Level& l = h->lev[h->L - 1];
+    launch_coarse_solve(h->nL, h->free_idx, h->Ainv, b, x, 3 * l.nn, h->stream);
+    CU(cudaGetLastError());
+    return GMG_OK;
+}
+
+int gmg_vcycle(gmg_handle* h, const float* r, float* z) {
+    if (!h || !r || !z) return fail(GMG_ERR_ARG, "null argument");
+    if (h->L == 1) return fail(GMG_ERR_ARG, "single-level hierarchy");
+    vcycle_level(h, 0, r, z, h->x2_0, -1, FIN_NONE);
+    CU(cudaGetLastError());
+    return GMG_OK;
+}
+
+int gmg_residual64(gmg_handle* h, const double* f, const double* u, double* r, double* rel_out) {
+    if (!h || !f || !u) return fail(GMG_ERR_ARG, "null argument");
+    Level& l0 = h->lev[0];
+    cudaStream_t s = h->stream;
+    h->sc_host[SC_UNZ] = 1.0;
+    CU(cudaMemcpyAsync(h->sc + SC_UNZ, h->sc_host + SC_UNZ, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, r, nullptr, h->sc, h->partials, h->keD, s);
+    launch_finalize(h->partials, partial_count(h, 0, 0), h->sc, SC_TRR, FIN_NONE, s);
+    launch_dot_f64_masked(f, f, l0.mask, l0.nn, h->partials, s);
+    launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_FF, FIN_NONE, s);
+    TRY(sync_scalars(h));
+    if (rel_out) *rel_out = std::sqrt(h->sc_host[SC_TRR]) / std::sqrt(h->sc_host[SC_FF]);
+    return GMG_OK;
+}
+
+}  // extern "C"

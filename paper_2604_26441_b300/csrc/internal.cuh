@@ -1,0 +1,196 @@
+// Internal declarations shared by the CUDA translation units of the GMG library.
+// Layout conventions are those of include/gmg.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "gmg.h"
+
+namespace gmg {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxDegree = 16;
+constexpr int kSlots = 27;     // 27-point neighbourhood of a node
+constexpr int kPlanes = 243;   // 27 slots x 3 x 3 block entries
+constexpr int kSelfSlot = 13;  // slot of offset (0, 0, 0)
+
+// Local node a of a hex8 element sits at offset (ldx(a), ldy(a), ldz(a)) from the
+// element's lowest corner; local DOF 3a + c.
+__host__ __device__ constexpr int ldx(int a) { return (a == 1 || a == 2 || a == 5 || a == 6) ? 1 : 0; }
+__host__ __device__ constexpr int ldy(int a) { return (a == 2 || a == 3 || a == 6 || a == 7) ? 1 : 0; }
+__host__ __device__ constexpr int ldz(int a) { return a >= 4 ? 1 : 0; }
+__host__ __device__ constexpr int slot_of(int dx, int dy, int dz) { return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1); }
+
+// Unit-element stiffness passed by value (lands in the kernel-parameter constant
+// bank, which broadcasts a warp-uniform read like __constant__ memory but is
+// private to each launch, so handles with different nu never collide).
+struct KeF { float v[576]; };
+struct KeD { double v[576]; };
+
+// Scalar slots of the per-handle FP64 scalar array.
+enum Scalar {
+    SC_FF = 0,      // ||f_free||^2
+    SC_RR = 1,      // ||r||^2 (recursive residual)
+    SC_RZ = 2,      // r . z
+    SC_PQ = 3,      // p . q
+    SC_ALPHA = 4,
+    SC_BETA = 5,
+    SC_RZNEW = 6,
+    SC_TRR = 7,     // ||f - K u||^2 in FP64 (true residual)
+    SC_NRM = 8,     // power iteration: ||w||^2
+    SC_VKV = 9,
+    SC_VDV = 10,
+    SC_UNZ = 11,    // nonzero count of u (> 0: u is not the zero vector)
+    SC_TMP = 12,
+    SC_COUNT = 16
+};
+
+// Operations the reduction finaliser applies after storing its sum.
+enum FinOp { FIN_NONE = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_NRMCHK = 3 };
+
+struct Level {
+    int nx = 0, ny = 0, nz = 0;     // element counts
+    long long nn = 0;               // node count (nx+1)(ny+1)(nz+1)
+    uint8_t* mask = nullptr;        // [nn] fixed-component bits
+    float* invdiag = nullptr;       // [3nn] D^{-1} (levels >= 1), 0 on fixed DOFs
+    double* A64 = nullptr;          // [243 nn] Galerkin operator planes, FP64 (levels >= 1)
+    float* A32 = nullptr;           // [243 nn] same in FP32 (levels >= 1)
+    float* x = nullptr;             // [3nn] smoother iterate / V-cycle output (levels >= 1)
+    float* x2 = nullptr;            // [3nn] ping-pong partner of x
+    float* b = nullptr;             // [3nn] right-hand side (levels >= 1)
+    float* t = nullptr;             // [3nn] residual before restriction
+    float* d = nullptr;             // [3nn] Chebyshev increment
+    double* coef = nullptr;         // [2 kMaxDegree] (c_d, c_a) per smoother step
+    int kind = GMG_SMOOTHER_JACOBI;
+    int degree = 2;
+    double omega = 0.5;
+    int n_free = 0;
+};
+
+}  // namespace gmg
+
+struct gmg_handle {
+    int L = 0;                                  // number of levels
+    gmg::Level lev[gmg::kMaxLevels];
+    cudaStream_t stream = nullptr;
+    gmg_options opt{};
+    int device = 0;
+    float* E32 = nullptr;                       // fine moduli, FP32
+    double* E64 = nullptr;                      // fine moduli, FP64
+    gmg::KeF keF{};
+    gmg::KeD keD{};
+    float kd = 0.f;                             // diagonal entry of K_e (all equal)
+    double* lam = nullptr;                      // [kMaxLevels] lambda estimates (device)
+    // fine-level PCG vectors
+    float *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x2_0 = nullptr, *t0 = nullptr, *d0 = nullptr;
+    // reductions
+    double* partials = nullptr;
+    int max_partials = 0;
+    double* sc = nullptr;                       // [SC_COUNT] device scalars
+    double* sc_host = nullptr;                  // pinned mirror
+    // coarsest dense solve
+    int nL = 0;
+    int* free_idx = nullptr;                    // [nL] DOF indices of the coarsest free DOFs
+    double* Ainv = nullptr;                     // [nL nL]
+    double eps = 0.0;
+    std::vector<void*> allocs;                  // every device allocation, freed by gmg_destroy
+    void* pinned = nullptr;                     // pinned host block (sc_host)
+};
+
+namespace gmg {
+
+// ---- launchers implemented in hot.cu ------------------------------------------
+enum FineMode { FM_APPLY = 0, FM_SMOOTH = 1, FM_RESID = 2 };
+
+struct FineArgs {
+    int nx, ny, nz;
+    const float* E;
+    const uint8_t* mask;
+    const float* xin;      // operand of K
+    const float* b;        // right-hand side (smooth / resid)
+    const float* dold;     // previous increment (smooth, c_d != 0)
+    float* dnew;           // new increment (smooth, may alias dold; nullptr = not written)
+    float* out;            // y, x_new or t
+    const double* coef;    // smoother coefficient table
+    int step;
+    double* partial;       // per-block partial dots (nullptr = none)
+    float kd;
+};
+
+int fine_grid_blocks(int nx, int ny, int nz);
+void launch_fine(int mode, int dot, const FineArgs& a, const KeF& ke, cudaStream_t s);
+void launch_fine_smooth0(const FineArgs& a, cudaStream_t s);
+void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,
+                         const double* f, const double* u, double* r64, float* r32,
+                         const double* sc, double* partial, const KeD& ke, cudaStream_t s);
+
+struct BsrArgs {
+    int nx, ny, nz;
+    long long nn;
+    const float* A;
+    const float* invdiag;
+    const uint8_t* mask;
+    const float* xin;
+    const float* b;
+    const float* dold;
+    float* dnew;
+    float* out;
+    const double* coef;
+    int step;
+    double* partial;
+};
+int bsr_grid_blocks(long long nn);
+void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s);
+void launch_bsr_smooth0(const BsrArgs& a, cudaStream_t s);
+
+void launch_restrict(const Level& f, const Level& c, const float* fine, float* coarse, cudaStream_t s);
+void launch_prolong_add(const Level& f, const Level& c, const float* coarse, float* fine, cudaStream_t s);
+void launch_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b, float* x,
+                         long long n_dof, cudaStream_t s);
+
+int vec_grid_blocks();
+void launch_dot_f32(const float* a, const float* b, long long n, double* partial, cudaStream_t s);
+void launch_dot_f64_masked(const double* a, const double* b, const uint8_t* mask, long long nn,
+                           double* partial, cudaStream_t s);
+void launch_finalize(const double* partial, int n, double* sc, int slot, int op, cudaStream_t s);
+void launch_pcg_update(double* u, float* r, const float* p, const float* q, long long n,
+                       const double* sc, double* partial, cudaStream_t s);
+void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s);
+void launch_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial, cudaStream_t s);
+void launch_scale_by_inv_sqrt(float* v, long long n, const double* sc, int slot, cudaStream_t s);
+void launch_scale_invdiag_fine(const float* y, float* w, const float* E, const uint8_t* mask,
+                               int nx, int ny, int nz, float kd, cudaStream_t s);
+void launch_scale_invdiag_bsr(const float* y, float* w, const float* invdiag, long long n, cudaStream_t s);
+void launch_diag_dot_fine(const float* v, const float* E, const uint8_t* mask, int nx, int ny, int nz,
+                          float kd, double* partial, cudaStream_t s);
+void launch_diag_dot_bsr(const float* v, const float* invdiag, long long n, double* partial, cudaStream_t s);
+void launch_power_start(float* v, const uint8_t* mask, long long nn, cudaStream_t s);
+
+// ---- launchers implemented in setup.cu ----------------------------------------
+void launch_moduli(const float* rho, long long ne, double p, double E0, double Emin, double* E64,
+                   float* E32, cudaStream_t s);
+void launch_element_stiffness(double nu, double* Ke, cudaStream_t s);
+void launch_mask_clamp(uint8_t* mask, int nx, int ny, int nz, cudaStream_t s);
+void launch_mask_from_dofs(const uint8_t* fixed_dofs, uint8_t* mask, long long nn, cudaStream_t s);
+void launch_mask_inject(const Level& f, Level& c, cudaStream_t s);
+void launch_count_free(const uint8_t* mask, long long nn, int* out, cudaStream_t s);
+void launch_child_patterns(const double* Ke, double* Mpat, cudaStream_t s);
+void launch_coarse_element_matrices(int nx, int ny, int nz, const double* E, const uint8_t* fine_mask,
+                                    const double* Ke, const double* Mpat, double* Kc, cudaStream_t s);
+void launch_fine_element_matrices(const double* E, long long ne, const double* Ke, double* Kc, cudaStream_t s);
+void launch_gather_level1(const Level& c, const double* Kc, double* A64, cudaStream_t s);
+void launch_galerkin_rap(const Level& f, const Level& c, cudaStream_t s);
+void launch_finish_bsr(Level& l, cudaStream_t s);
+void launch_smoother_coef(double* coef, const double* lam, int kind, int degree, double omega,
+                          double alpha, double safety, cudaStream_t s);
+void launch_free_index(const uint8_t* mask, long long nn, int* free_idx, int* count, cudaStream_t s);
+void launch_dense_gather(const Level& l, const int* free_idx, int n, double* dense, cudaStream_t s);
+void launch_regularise(double* dense, int n, double* eps_out, cudaStream_t s);
+int cholesky_and_inverse(double* A, int n, double* work, int* info_dev, double* Ainv, cudaStream_t s);
+void launch_lambda_finish(double* sc, double* lam_slot, cudaStream_t s);
+
+}  // namespace gmg

@@ -1,0 +1,316 @@
+"""Python binding of the C ABI in include/gmg.h (ctypes; argument marshalling only).
+
+Every numerical step runs in the CUDA library ``libgmg_b300.so`` built in-tree by
+``paper_2604_26441_b300.build``.  PyTorch supplies device memory and the stream;
+if the library is missing this module raises instead of computing anything
+another way.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgmg_b300.so")
+
+GMG_OK, GMG_NOT_CONVERGED, GMG_NONFINITE = 0, 1, 2
+BC_CLAMP_XMIN, BC_MASK = 0, 1
+JACOBI, CHEBYSHEV = 0, 1
+_KINDS = {"jacobi": JACOBI, "chebyshev": CHEBYSHEV}
+
+
+class GMGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gmg error {code}: {msg}")
+        self.code = code
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+
+
+class _BC(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("fixed", ctypes.c_void_p)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("smoother", ctypes.c_int), ("degree", ctypes.c_int),
+                ("coarse_smoother", ctypes.c_int), ("coarse_degree", ctypes.c_int),
+                ("omega", ctypes.c_double), ("coarse_omega", ctypes.c_double),
+                ("cheb_alpha", ctypes.c_double), ("lambda_safety", ctypes.c_double),
+                ("power_iters_fine", ctypes.c_int), ("power_iters_coarse", ctypes.c_int),
+                ("chol_cutoff", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("replacements", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("rel_residual_recursive", ctypes.c_double),
+                ("solve_ms", ctypes.c_double)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "gmg_default_options": (None, [ctypes.POINTER(_Options)]),
+    "gmg_setup": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_Grid), _P, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_BC),
+                                 ctypes.POINTER(_Options)]),
+    "gmg_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Info)]),
+    "gmg_apply": (ctypes.c_int, [_P, _P, _P]),
+    "gmg_destroy": (None, [_P]),
+    "gmg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "gmg_last_error": (ctypes.c_char_p, []),
+    "gmg_num_levels": (ctypes.c_int, [_P]),
+    "gmg_level_dims": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "gmg_get_mask": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "gmg_get_bsr": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "gmg_get_lambda": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "gmg_set_lambda": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
+    "gmg_level_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "gmg_level_smooth": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
+    "gmg_restrict": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "gmg_prolong_add": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "gmg_coarse_solve": (ctypes.c_int, [_P, _P, _P]),
+    "gmg_vcycle": (ctypes.c_int, [_P, _P, _P]),
+    "gmg_residual64": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; build it with "
+                           "`python -m paper_2604_26441_b300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, allow=(GMG_OK,)) -> int:
+    if rc in allow:
+        return rc
+    lib = load_library()
+    raise GMGError(rc, f"{lib.gmg_status_str(rc).decode()}: {lib.gmg_last_error().decode()}")
+
+
+def _ptr(t, dtype, numel: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coarse_smoother: str | None = "jacobi",
+            coarse_degree: int | None = 2, omega: float = 0.5, coarse_omega: float | None = 0.5,
+            alpha: float = 1.0 / 30.0, lambda_safety: float = 1.1, power_iters_fine: int = 20,
+            power_iters_coarse: int = 10, chol_cutoff: int = 5000, stream: int | None = None) -> _Options:
+    o = _Options()
+    load_library().gmg_default_options(ctypes.byref(o))
+    o.levels = levels
+    o.smoother = _KINDS[smoother]
+    o.degree = degree
+    o.coarse_smoother = -1 if coarse_smoother is None else _KINDS[coarse_smoother]
+    o.coarse_degree = -1 if coarse_degree is None else coarse_degree
+    o.omega = omega
+    o.coarse_omega = -1.0 if coarse_omega is None else coarse_omega
+    o.cheb_alpha = alpha
+    o.lambda_safety = lambda_safety
+    o.power_iters_fine = power_iters_fine
+    o.power_iters_coarse = power_iters_coarse
+    o.chol_cutoff = chol_cutoff
+    o.stream = stream
+    return o
+
+
+def config_options(cfg, stream: int | None = None) -> _Options:
+    """Options for one of the synthetic configurations in ``inputs.CONFIGS``."""
+    return options(levels=cfg.levels, smoother=cfg.smoother, degree=cfg.degree, coarse_smoother=None,
+                   coarse_degree=None, omega=cfg.omega, coarse_omega=None, stream=stream)
+
+
+class Solver:
+    """A GMG-PCG hierarchy for one frozen density field on one structured grid."""
+
+    def __init__(self, rho, p: float = 3.0, E0: float = 1.0, Emin: float = 1e-9, nu: float = 0.3,
+                 fixed: np.ndarray | None = None, opts: _Options | None = None):
+        import torch
+        lib = load_library()
+        if rho.dim() != 3:
+            raise ValueError("rho must have shape (nz, ny, nx)")
+        nz, ny, nx = (int(s) for s in rho.shape)
+        self.dims = (nx, ny, nz)
+        self.nn = (nx + 1) * (ny + 1) * (nz + 1)
+        g = _Grid(nx, ny, nz)
+        if fixed is None:
+            bc = _BC(BC_CLAMP_XMIN, None)
+            self._fixed_host = None
+        else:
+            self._fixed_host = np.ascontiguousarray(fixed, dtype=np.uint8)
+            if self._fixed_host.size != 3 * self.nn:
+                raise ValueError("fixed must have 3*n_nodes entries")
+            bc = _BC(BC_MASK, self._fixed_host.ctypes.data)
+        if opts is None:
+            opts = options()
+        if opts.stream is None:
+            opts.stream = torch.cuda.current_stream().cuda_stream
+        self.stream = opts.stream
+        h = ctypes.c_void_p()
+        rp = _ptr(rho, torch.float32, nx * ny * nz, "rho")
+        _check(lib.gmg_setup(ctypes.byref(h), ctypes.byref(g), rp, p, E0, Emin, nu, ctypes.byref(bc),
+                             ctypes.byref(opts)))
+        self._h = h
+        self._lib = lib
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- geometry
+    @property
+    def num_levels(self) -> int:
+        return self._lib.gmg_num_levels(self._h)
+
+    def level_dims(self, level: int) -> tuple[int, int, int]:
+        d = (ctypes.c_int * 3)()
+        _check(self._lib.gmg_level_dims(self._h, level, d))
+        return int(d[0]), int(d[1]), int(d[2])
+
+    def level_nodes(self, level: int) -> int:
+        nx, ny, nz = self.level_dims(level)
+        return (nx + 1) * (ny + 1) * (nz + 1)
+
+    # -- main entry points
+    def apply(self, u, y=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(u)
+        _check(self._lib.gmg_apply(self._h, _ptr(u, torch.float32, 3 * self.nn, "u"),
+                                   _ptr(y, torch.float32, 3 * self.nn, "y")))
+        return y
+
+    def solve(self, f, u=None, tol: float = 1e-6, maxit: int = 200):
+        import torch
+        if u is None:
+            u = torch.zeros_like(f)
+        info = _Info()
+        rc = self._lib.gmg_solve(self._h, _ptr(f, torch.float64, 3 * self.nn, "f"),
+                                 _ptr(u, torch.float64, 3 * self.nn, "u"), tol, maxit, ctypes.byref(info))
+        _check(rc, allow=(GMG_OK, GMG_NOT_CONVERGED, GMG_NONFINITE))
+        return u, {"status": info.status, "iterations": info.iterations, "replacements": info.replacements,
+                   "rel_residual": info.rel_residual, "rel_residual_recursive": info.rel_residual_recursive,
+                   "solve_ms": info.solve_ms}
+
+    # -- per-step entry points
+    def get_mask(self, level: int) -> np.ndarray:
+        out = np.empty(self.level_nodes(level), dtype=np.uint8)
+        _check(self._lib.gmg_get_mask(self._h, level, out.ctypes.data))
+        return out
+
+    def get_bsr(self, level: int) -> np.ndarray:
+        out = np.empty(243 * self.level_nodes(level), dtype=np.float64)
+        _check(self._lib.gmg_get_bsr(self._h, level, out.ctypes.data))
+        return out.reshape(243, -1)
+
+    def get_lambda(self, level: int) -> float:
+        v = ctypes.c_double()
+        _check(self._lib.gmg_get_lambda(self._h, level, ctypes.byref(v)))
+        return v.value
+
+    def set_lambda(self, level: int, lam: float):
+        _check(self._lib.gmg_set_lambda(self._h, level, lam))
+
+    def level_apply(self, level: int, x, y=None):
+        import torch
+        n = 3 * self.level_nodes(level)
+        if y is None:
+            y = torch.empty_like(x)
+        _check(self._lib.gmg_level_apply(self._h, level, _ptr(x, torch.float32, n, "x"),
+                                         _ptr(y, torch.float32, n, "y")))
+        return y
+
+    def level_smooth(self, level: int, b, x=None):
+        import torch
+        n = 3 * self.level_nodes(level)
+        zero = x is None
+        if zero:
+            x = torch.zeros_like(b)
+        _check(self._lib.gmg_level_smooth(self._h, level, _ptr(b, torch.float32, n, "b"),
+                                          _ptr(x, torch.float32, n, "x"), int(zero)))
+        return x
+
+    def restrict(self, level: int, fine, coarse=None):
+        import torch
+        nc = 3 * self.level_nodes(level + 1)
+        if coarse is None:
+            coarse = torch.empty(nc, dtype=torch.float32, device=fine.device)
+        _check(self._lib.gmg_restrict(self._h, level, _ptr(fine, torch.float32, 3 * self.level_nodes(level), "fine"),
+                                      _ptr(coarse, torch.float32, nc, "coarse")))
+        return coarse
+
+    def prolong_add(self, level: int, coarse, fine):
+        import torch
+        _check(self._lib.gmg_prolong_add(self._h, level,
+                                         _ptr(coarse, torch.float32, 3 * self.level_nodes(level + 1), "coarse"),
+                                         _ptr(fine, torch.float32, 3 * self.level_nodes(level), "fine")))
+        return fine
+
+    def coarse_solve(self, b, x=None):
+        import torch
+        L = self.num_levels - 1
+        n = 3 * self.level_nodes(L)
+        if x is None:
+            x = torch.empty_like(b)
+        _check(self._lib.gmg_coarse_solve(self._h, _ptr(b, torch.float32, n, "b"), _ptr(x, torch.float32, n, "x")))
+        return x
+
+    def vcycle(self, r, z=None):
+        import torch
+        if z is None:
+            z = torch.empty_like(r)
+        _check(self._lib.gmg_vcycle(self._h, _ptr(r, torch.float32, 3 * self.nn, "r"),
+                                    _ptr(z, torch.float32, 3 * self.nn, "z")))
+        return z
+
+    def residual64(self, f, u, r=None) -> float:
+        import torch
+        rel = ctypes.c_double()
+        rp = None if r is None else _ptr(r, torch.float64, 3 * self.nn, "r")
+        _check(self._lib.gmg_residual64(self._h, _ptr(f, torch.float64, 3 * self.nn, "f"),
+                                        _ptr(u, torch.float64, 3 * self.nn, "u"), rp, ctypes.byref(rel)))
+        return rel.value

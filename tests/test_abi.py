@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads without a GPU, and exports every entry point
+that include/gmg.h declares; argument errors come back as status codes."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gmg_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch  # noqa: F401  (provides the CUDA runtime the library links against)
+    from paper_2604_26441_b300 import build, gmg
+    build.build_library()
+    return gmg.load_library()
+
+
+def test_every_declared_symbol_is_exported_and_bound(lib):
+    from paper_2604_26441_b300 import gmg
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in gmg.exported_symbols(), n
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_2604_26441_b300 import gmg
+    assert lib.gmg_status_str(0) == b"ok"
+    assert b"invalid" in lib.gmg_status_str(-1)
+    o = gmg._Options()
+    lib.gmg_default_options(ctypes.byref(o))
+    assert o.levels == 4 and o.degree == 2 and o.power_iters_fine == 20 and o.power_iters_coarse == 10
+    assert abs(o.cheb_alpha - 1 / 30) < 1e-15 and o.chol_cutoff == 5000
+
+
+def test_argument_errors_without_device(lib):
+    from paper_2604_26441_b300 import gmg
+    h = ctypes.c_void_p()
+    g = gmg._Grid(4, 2, 2)
+    bc = gmg._BC(gmg.BC_CLAMP_XMIN, None)
+    assert lib.gmg_setup(None, ctypes.byref(g), None, 3.0, 1.0, 1e-9, 0.3, ctypes.byref(bc), None) == -1
+    assert lib.gmg_setup(ctypes.byref(h), ctypes.byref(g), None, 3.0, 1.0, 1e-9, 0.3, ctypes.byref(bc), None) == -1
+    bad = gmg._Grid(0, 2, 2)
+    assert lib.gmg_setup(ctypes.byref(h), ctypes.byref(bad), ctypes.c_void_p(16), 3.0, 1.0, 1e-9, 0.3,
+                         ctypes.byref(bc), None) == -1
+    assert b"element counts" in lib.gmg_last_error()
+    mask_bc = gmg._BC(gmg.BC_MASK, None)
+    assert lib.gmg_setup(ctypes.byref(h), ctypes.byref(g), ctypes.c_void_p(16), 3.0, 1.0, 1e-9, 0.3,
+                         ctypes.byref(mask_bc), None) == -1
+    assert lib.gmg_solve(None, None, None, 1e-6, 10, None) == -1
+    assert lib.gmg_num_levels(None) == 0
+    lib.gmg_destroy(None)
+
+
+def test_no_device_is_reported(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    from paper_2604_26441_b300 import gmg
+    h = ctypes.c_void_p()
+    g = gmg._Grid(4, 2, 2)
+    bc = gmg._BC(gmg.BC_CLAMP_XMIN, None)
+    rc = lib.gmg_setup(ctypes.byref(h), ctypes.byref(g), ctypes.c_void_p(256), 3.0, 1.0, 1e-9, 0.3, ctypes.byref(bc),
+                       None)
+    assert rc == -6 and not h.value

@@ -1,0 +1,342 @@
+"""GPU parity of every step of the hot path against the FP64 CPU oracle.
+
+Tolerances: the FP32 operator apply (fine and assembled levels), transfers and
+smoother passes within 1e-6 relative L2 (FP32 arithmetic on O(1) data, ~600
+terms per output); Galerkin operators bit-exact in pattern and within 1e-12
+relative in value (both FP64); masks bit-exact; converged displacements within
+1e-5 relative L2 of the oracle's exact solution with an FP64 true residual
+below 1e-6; pass/fail under the cap identical and iteration counts within
+max(2, 10 %) of the oracle's.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import fem, hierarchy as hy, solver as so
+from paper_2604_26441_b300 import inputs
+
+from gpu_helpers import (config_opts, gpu_solver, oracle_hierarchy, oracle_spec_from_opts, pattern_planes,
+                         planes_from_csr, rel_l2, slot_pattern_from_mask, structural_patterns)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2604_26441_b300 import build
+    build.build_library()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _t(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+# ---------------------------------------------------------------------------
+# fine operator
+# ---------------------------------------------------------------------------
+APPLY_CASES = [
+    ("c0", 16, 8, 8, "uniform", 3.0),
+    ("ragged", 37, 13, 9, "filtered", 3.0),
+    ("thin", 33, 2, 5, "filtered", 1.0),
+    ("c1", 40, 40, 40, "filtered", 2.0),
+]
+
+
+@pytest.mark.parametrize("name,nx,ny,nz,dens,p", APPLY_CASES)
+def test_fine_apply_matches_oracle(name, nx, ny, nz, dens, p):
+    rho = inputs.uniform_density(nx, ny, nz) if dens == "uniform" else inputs.filtered_random_density(nx, ny, nz, 7)
+    fixed = inputs.clamp_xmin_mask(nx, ny, nz)
+    S = gpu_solver(rho, p, levels=0, smoother="jacobi", coarse_smoother=None, omega=0.5)
+    u = inputs.random_free_vector(fixed, seed=11)
+    u_in = u.copy()
+    u_in[fixed == 1] = 1e3  # values on fixed DOFs must be ignored
+    y = S.apply(_t(u_in)).cpu().numpy()
+    g = fem.Grid(nx, ny, nz)
+    yref = fem.matfree_apply(g, fem.moduli(rho, p), fem.element_stiffness(0.3), u.astype(np.float64))
+    yref[fixed == 1] = 0.0
+    assert np.all(y[fixed == 1] == 0.0)
+    assert rel_l2(y, yref) < 1e-6
+    # bitwise reproducible (no atomics)
+    y2 = S.apply(_t(u_in)).cpu().numpy()
+    assert np.array_equal(y, y2)
+
+
+def test_fine_apply_random_mask():
+    nx, ny, nz = 12, 7, 5
+    rng = np.random.default_rng(3)
+    fixed = inputs.clamp_xmin_mask(nx, ny, nz) | (rng.random(3 * (nx + 1) * (ny + 1) * (nz + 1)) < 0.1).astype(np.uint8)
+    rho = inputs.filtered_random_density(nx, ny, nz, 5)
+    S = gpu_solver(rho, 3.0, fixed=fixed, levels=2, smoother="jacobi", coarse_smoother=None, omega=0.4)
+    u = inputs.random_free_vector(fixed, seed=2)
+    y = S.apply(_t(u)).cpu().numpy()
+    yref = fem.matfree_apply(fem.Grid(nx, ny, nz), fem.moduli(rho, 3.0), fem.element_stiffness(0.3),
+                             u.astype(np.float64))
+    yref[fixed == 1] = 0
+    assert rel_l2(y, yref) < 1e-6
+
+
+def test_fine_apply_full_size_sampled():
+    """100^3 (the throughput configuration): sampled rows against the oracle."""
+    c = inputs.CONFIGS["c2"]
+    rho = inputs.filtered_random_density(c.nx, c.ny, c.nz, 3)
+    S = gpu_solver(rho, 3.0, levels=0, smoother="jacobi", coarse_smoother=None, omega=0.5)
+    fixed = c.fixed()
+    u = inputs.random_free_vector(fixed, seed=4)
+    y = S.apply(_t(u)).cpu().numpy().reshape(-1, 3)
+    g = fem.Grid(c.nx, c.ny, c.nz)
+    rng = np.random.default_rng(0)
+    nodes = np.concatenate([rng.integers(0, g.n_nodes, 3000), [0, g.n_nodes - 1, c.nx, g.n_nodes // 2]])
+    ref = fem.matfree_apply_at_nodes(g, fem.moduli(rho, 3.0), fem.element_stiffness(0.3), u, nodes)
+    ref[fixed.reshape(-1, 3)[nodes] == 1] = 0
+    assert rel_l2(y[nodes], ref) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# hierarchy: masks, Galerkin operators, spectral estimates
+# ---------------------------------------------------------------------------
+HIER_CASES = [
+    ("c0", 16, 8, 8, 3, "clamp"),
+    ("odd", 13, 7, 11, 3, "clamp"),
+    ("random_mask", 10, 6, 6, 3, "random"),
+    ("c1", 40, 40, 40, 4, "clamp"),
+]
+
+
+def _case_inputs(nx, ny, nz, mask):
+    rho = inputs.filtered_random_density(nx, ny, nz, 9)
+    if mask == "clamp":
+        return rho, inputs.clamp_xmin_mask(nx, ny, nz), None
+    rng = np.random.default_rng(1)
+    fixed = inputs.clamp_xmin_mask(nx, ny, nz) | (rng.random(3 * (nx + 1) * (ny + 1) * (nz + 1)) < 0.08).astype(np.uint8)
+    return rho, fixed, fixed
+
+
+@pytest.mark.parametrize("name,nx,ny,nz,levels,mask", HIER_CASES)
+def test_masks_and_galerkin_operators(name, nx, ny, nz, levels, mask):
+    rho, fixed, fixed_arg = _case_inputs(nx, ny, nz, mask)
+    S = gpu_solver(rho, 3.0, fixed=fixed_arg, levels=levels, smoother="jacobi", coarse_smoother=None, omega=0.4)
+    H, _ = oracle_hierarchy(rho, 3.0, fixed, levels)
+    patterns = structural_patterns((nx, ny, nz), fixed, levels)
+    assert S.num_levels == levels
+    for li, lev in enumerate(H):
+        assert S.level_dims(li) == lev.dims
+        m = S.get_mask(li)
+        bits = lev.fixed.reshape(-1, 3)
+        assert np.array_equal(m, (bits[:, 0] | bits[:, 1] << 1 | bits[:, 2] << 2).astype(np.uint8))
+        if li == 0:
+            continue
+        A = S.get_bsr(li)
+        R = planes_from_csr(lev)
+        # pattern: the GPU's implicit index map (27 slots, free DOF pairs) equals
+        # the oracle's structural pattern of P^T K P, bit for bit
+        gpu_pat = slot_pattern_from_mask(m, lev.dims)
+        ora_pat = pattern_planes(patterns[li], lev.dims, lev.free)
+        if mask == "clamp":
+            assert np.array_equal(gpu_pat, ora_pat)
+        else:  # point constraints may remove structural couplings inside a slot
+            assert not np.any(ora_pat & ~gpu_pat)
+        assert not np.any(A[~gpu_pat])
+        assert np.max(np.abs(A - R)) <= 1e-12 * np.max(np.abs(R))
+
+
+@pytest.mark.parametrize("name,nx,ny,nz,levels,mask", HIER_CASES[:3])
+def test_lambda_estimates(name, nx, ny, nz, levels, mask):
+    rho, fixed, fixed_arg = _case_inputs(nx, ny, nz, mask)
+    S = gpu_solver(rho, 3.0, fixed=fixed_arg, levels=levels, smoother="jacobi", coarse_smoother=None, omega=0.4)
+    H, _ = oracle_hierarchy(rho, 3.0, fixed, levels)
+    for li, lev in enumerate(H):
+        assert abs(S.get_lambda(li) - lev.lam) < 1e-4 * lev.lam
+
+
+@pytest.mark.parametrize("name,nx,ny,nz,levels,mask", HIER_CASES)
+def test_level_ops_restrict_prolong_coarse(name, nx, ny, nz, levels, mask):
+    rho, fixed, fixed_arg = _case_inputs(nx, ny, nz, mask)
+    S = gpu_solver(rho, 3.0, fixed=fixed_arg, levels=levels, smoother="jacobi", coarse_smoother=None, omega=0.4)
+    H, _ = oracle_hierarchy(rho, 3.0, fixed, levels)
+    rng = np.random.default_rng(5)
+    for li, lev in enumerate(H):
+        n = 3 * fem.Grid(*lev.dims).n_nodes
+        x = np.zeros(n, dtype=np.float32)
+        x[lev.free] = rng.uniform(-1, 1, lev.n_free)
+        if li > 0:
+            y = S.level_apply(li, _t(x)).cpu().numpy()
+            yref = np.zeros(n)
+            yref[lev.free] = lev.K @ x[lev.free].astype(np.float64)
+            assert rel_l2(y, yref) < 1e-6
+        if li + 1 < len(H):
+            c = H[li + 1]
+            P = hy.prolongation(lev.dims)[lev.free][:, c.free]
+            xc = S.restrict(li, _t(x)).cpu().numpy()
+            ref = np.zeros(3 * fem.Grid(*c.dims).n_nodes)
+            ref[c.free] = P.T @ x[lev.free].astype(np.float64)
+            assert rel_l2(xc, ref) < 1e-6
+            e = np.zeros_like(ref, dtype=np.float32)
+            e[c.free] = rng.uniform(-1, 1, c.n_free)
+            base = np.zeros(n, dtype=np.float32)
+            base[lev.free] = rng.uniform(-1, 1, lev.n_free)
+            out = S.prolong_add(li, _t(e), _t(base)).cpu().numpy()
+            ref_f = base.astype(np.float64)
+            ref_f[lev.free] += P @ e[c.free].astype(np.float64)
+            assert rel_l2(out, ref_f) < 1e-6
+    last = H[-1]
+    nL = 3 * fem.Grid(*last.dims).n_nodes
+    b = np.zeros(nL, dtype=np.float32)
+    b[last.free] = rng.uniform(-1, 1, last.n_free)
+    x = S.coarse_solve(_t(b)).cpu().numpy()
+    ref = np.zeros(nL)
+    ref[last.free] = hy.coarse_solve(last.L, b[last.free].astype(np.float64))
+    assert rel_l2(x, ref) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# smoothers and the V-cycle (oracle lambda injected so both use one band)
+# ---------------------------------------------------------------------------
+SMOOTH_OPTS = [
+    dict(levels=3, smoother="jacobi", degree=2, coarse_smoother=None, coarse_degree=None, omega=0.5, coarse_omega=None),
+    dict(levels=3, smoother="chebyshev", degree=3, coarse_smoother=None, coarse_degree=None, omega=0.5,
+         coarse_omega=None),
+    dict(levels=3, smoother="chebyshev", degree=2, coarse_smoother="jacobi", coarse_degree=2, omega=0.5,
+         coarse_omega=0.5),
+]
+
+
+@pytest.mark.parametrize("opts", SMOOTH_OPTS, ids=["jacobi", "cheb3", "cheb2+jacobi"])
+def test_smoothers_and_vcycle(opts):
+    c = inputs.CONFIGS["c0"]
+    rho = inputs.filtered_random_density(c.nx, c.ny, c.nz, 2)
+    fixed = c.fixed()
+    S = gpu_solver(rho, 3.0, **opts)
+    H, _ = oracle_hierarchy(rho, 3.0, fixed, opts["levels"])
+    for li, lev in enumerate(H):
+        S.set_lambda(li, lev.lam)
+    spec = oracle_spec_from_opts(opts)
+    rng = np.random.default_rng(8)
+    for li, lev in enumerate(H[:-1]):
+        n = 3 * fem.Grid(*lev.dims).n_nodes
+        b = np.zeros(n, dtype=np.float32)
+        b[lev.free] = rng.uniform(-1, 1, lev.n_free)
+        x0 = np.zeros(n, dtype=np.float32)
+        x0[lev.free] = rng.uniform(-1, 1, lev.n_free)
+        xs = S.level_smooth(li, _t(b)).cpu().numpy()
+        ref = np.zeros(n)
+        ref[lev.free] = so.smooth(lev, b[lev.free].astype(np.float64), np.zeros(lev.n_free), spec, li)
+        assert rel_l2(xs, ref) < 1e-6
+        xs = S.level_smooth(li, _t(b), _t(x0)).cpu().numpy()
+        ref[lev.free] = so.smooth(lev, b[lev.free].astype(np.float64), x0[lev.free].astype(np.float64), spec, li)
+        assert rel_l2(xs, ref) < 1e-6
+    r = np.zeros(3 * c.n_nodes, dtype=np.float32)
+    r[H[0].free] = rng.uniform(-1, 1, H[0].n_free)
+    z = S.vcycle(_t(r)).cpu().numpy()
+    zref = np.zeros(3 * c.n_nodes)
+    zref[H[0].free] = so.vcycle(H, r[H[0].free].astype(np.float64), spec)
+    assert rel_l2(z, zref) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# end-to-end solves
+# ---------------------------------------------------------------------------
+def _solve_and_compare(rho, p, fixed, f, opts, cap=200, exact=True):
+    S = gpu_solver(rho, p, **opts)
+    H, E = oracle_hierarchy(rho, p, fixed, opts["levels"])
+    spec = oracle_spec_from_opts(opts)
+    u_or, res = so.gmg_pcg(H, f, spec, tol=1e-6, maxit=cap)
+    u_gpu, info = S.solve(_t(f, torch.float64), tol=1e-6, maxit=cap)
+    u_gpu = u_gpu.cpu().numpy()
+    assert (info["status"] == 0) == (res.status == so.OK)
+    if res.status == so.OK:
+        assert abs(info["iterations"] - res.iterations) <= max(2, 0.1 * res.iterations)
+        # the oracle recomputes the residual of the GPU solution independently
+        nz, ny, nx = rho.shape
+        g = fem.Grid(nx, ny, nz)
+        r = f - fem.matfree_apply(g, E, fem.element_stiffness(0.3), u_gpu)
+        free = fem.free_dofs(fixed)
+        assert np.linalg.norm(r[free]) / np.linalg.norm(f[free]) <= 1e-6
+        assert abs(info["rel_residual"] - np.linalg.norm(r[free]) / np.linalg.norm(f[free])) < 1e-9
+        assert np.all(u_gpu[fixed == 1] == 0)
+        if exact:
+            ue = so.exact_solve(H, f, spec)
+            assert rel_l2(u_gpu, ue) < 1e-5
+    return info, res
+
+
+def test_solve_config0():
+    c = inputs.CONFIGS["c0"]
+    info, res = _solve_and_compare(c.rho(), c.p, c.fixed(), c.load(), config_opts(c))
+    assert info["status"] == 0
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0, 3.0])
+def test_solve_config1(p):
+    c = inputs.CONFIGS["c1"]
+    info, res = _solve_and_compare(c.rho(), p, c.fixed(), c.load(), config_opts(c))
+    assert info["status"] == 0
+
+
+def test_solve_ragged_chebyshev():
+    nx, ny, nz = 23, 11, 9
+    rho = inputs.filtered_random_density(nx, ny, nz, 4)
+    opts = dict(levels=3, smoother="chebyshev", degree=3, coarse_smoother=None, coarse_degree=None, omega=0.5,
+                coarse_omega=None)
+    info, res = _solve_and_compare(rho, 3.0, inputs.clamp_xmin_mask(nx, ny, nz), inputs.tip_edge_load(nx, ny, nz), opts)
+    assert info["status"] == 0
+
+
+def test_solve_full_size_config2():
+    """100^3, 5 levels, Chebyshev degree 3: the oracle judges the GPU solution by
+    its own FP64 residual and the energy identity."""
+    c = inputs.CONFIGS["c2"]
+    S = gpu_solver(c.rho(), c.p, **config_opts(c))
+    f = c.load()
+    u, info = S.solve(_t(f, torch.float64), tol=1e-6, maxit=200)
+    assert info["status"] == 0
+    u = u.cpu().numpy()
+    g = fem.Grid(c.nx, c.ny, c.nz)
+    E = fem.moduli(c.rho(), c.p)
+    Ku = fem.matfree_apply(g, E, fem.element_stiffness(0.3), u)
+    free = fem.free_dofs(c.fixed())
+    rel = np.linalg.norm((f - Ku)[free]) / np.linalg.norm(f[free])
+    assert rel <= 1e-6
+    assert abs(u @ Ku - f @ u) <= 1e-5 * abs(f @ u)
+
+
+# ---------------------------------------------------------------------------
+# edge cases and failure reporting
+# ---------------------------------------------------------------------------
+def test_edge_cases():
+    from paper_2604_26441_b300 import gmg
+    c = inputs.CONFIGS["c0"]
+    S = gpu_solver(c.rho(), c.p, **config_opts(c))
+    f = _t(c.load(), torch.float64)
+    # zero load: zero solution, no iterations
+    u, info = S.solve(torch.zeros_like(f))
+    assert info["status"] == 0 and info["iterations"] == 0 and float(u.abs().max()) == 0.0
+    # cap reached
+    u, info = S.solve(f, tol=1e-6, maxit=1)
+    assert info["status"] == gmg.GMG_NOT_CONVERGED and info["iterations"] == 1
+    # warm start from the converged solution: accepted at once
+    u, info = S.solve(f)
+    u2, info2 = S.solve(f, u=u.clone())
+    assert info2["status"] == 0 and info2["iterations"] == 0
+    # non-finite load
+    fb = f.clone()
+    fb[3 * 40 + 1] = float("nan")
+    _, info = S.solve(fb)
+    assert info["status"] == gmg.GMG_NONFINITE
+    # unstable damping is refused at set-up
+    with pytest.raises(gmg.GMGError) as ei:
+        gpu_solver(c.rho(), c.p, levels=3, smoother="jacobi", coarse_smoother=None, omega=1.0, coarse_omega=None)
+    assert ei.value.code == -4
+    # too many levels for the grid
+    with pytest.raises(gmg.GMGError):
+        gpu_solver(c.rho(), c.p, levels=6, smoother="jacobi", coarse_smoother=None, omega=0.5)
+
+
+def test_smallest_grid():
+    rho = inputs.uniform_density(2, 2, 2)
+    opts = dict(levels=2, smoother="jacobi", degree=2, coarse_smoother=None, coarse_degree=None, omega=0.5,
+                coarse_omega=None)
+    info, res = _solve_and_compare(rho, 3.0, inputs.clamp_xmin_mask(2, 2, 2), inputs.tip_edge_load(2, 2, 2), opts)
+    assert info["status"] == 0
