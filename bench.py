@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GMG-preconditioned CG solver.
+
+Workload: the 100x100x100 unit-hex8 cantilever (1,000,000 elements, 3,060,300
+free DOFs), uniform rho = 0.5, p = 3, E0 = 1, Emin = 1e-9, nu = 0.3, clamped
+x = 0 face, unit tip-edge load, 5-level Galerkin hierarchy, degree-3 Chebyshev
+smoothing, tolerance 1e-6 on the FP64 true residual, cap 200.
+
+One step = one complete solve (FP64 load in, FP64 displacement out) with the
+hierarchy already built for the frozen density field; the metric is solves/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs independent replicas (one per GPU, launched by torch.distributed.run);
+the only collectives are the host-side barrier and the max-over-ranks timing.
+The reference arm times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s at rel. residual 1e-6 (1M hex8) vs plain FP32-GMG; fine-op % HBM peak"
+UNIT = "solves/s"
+WORKLOAD = ("cantilever 100x100x100 hex8 (1,000,000 elements, 3,060,300 free DOF), uniform rho=0.5, p=3, "
+            "5-level Galerkin GMG, Chebyshev degree 3, PCG tol 1e-6 (FP64 true residual), cap 200")
+SAMPLE_N = 50          # edge of the cube solved by the CPU oracle as the bounded sample
+FLUSH_BYTES = 256 << 20  # > 2x the 126 MB L2
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (a separate, freshly spawned interpreter with one thread)
+# ---------------------------------------------------------------------------
+_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import fem, hierarchy as hy, solver as so
+from paper_2604_26441_b300 import inputs
+n, reps = {n}, {reps}
+rho = inputs.uniform_density(n, n, n, 0.5)
+t0 = time.perf_counter()
+H = hy.build_hierarchy((n, n, n), fem.moduli(rho, 3.0), inputs.clamp_xmin_mask(n, n, n), levels=4)
+t1 = time.perf_counter()
+spec = so.SmootherSpec("chebyshev", 3)
+times, its, rel = [], [], []
+for _ in range(reps):
+    s = time.perf_counter()
+    u, res = so.gmg_pcg(H, inputs.tip_edge_load(n, n, n), spec, tol=1e-6, maxit=200)
+    times.append(time.perf_counter() - s)
+    its.append(res.iterations); rel.append(res.rel_residual)
+print(json.dumps({{"setup_s": t1 - t0, "solve_s": times, "iterations": its, "rel": rel}}))
+"""
+
+
+def run_oracle_sample(reps: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _ORACLE_SNIPPET.format(root=ROOT, n=SAMPLE_N, reps=reps)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_rate(rec: dict) -> float:
+    """Sample solves/s scaled to the 1M-element workload by the element count."""
+    scale = (SAMPLE_N ** 3) / 1_000_000
+    return scale / statistics.mean(rec["solve_s"])
+
+
+def cpu_baseline_obj(rec: dict) -> dict:
+    return {"value": oracle_rate(rec), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 CPU oracle (numpy/scipy, 1 thread): GMG-PCG solve of the {SAMPLE_N}^3 cantilever of "
+                       f"the same recipe (4 levels, Chebyshev 3), {len(rec['solve_s'])} solves, mean "
+                       f"{statistics.mean(rec['solve_s']):.2f} s, {rec['iterations'][0]} iterations, setup "
+                       f"{rec['setup_s']:.1f} s excluded; rate scaled by element count x{SAMPLE_N ** 3 / 1e6:.3f}")}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def _peaks() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def _profile_traffic(kernel_src: str) -> float | None:
+    """DRAM bytes per launch of the fine operator from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "fine_apply_c2_ncu.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    if not m_b or not m_h:
+        return None
+    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return float(m_b.group(1)) if m_h.group(1) == cur else None
+
+
+def main():
+    args = _args()
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        reps = args.warmup + args.steps
+        rec = run_oracle_sample(reps)
+        times = rec["solve_s"][args.warmup:]
+        value = (SAMPLE_N ** 3 / 1e6) / statistics.mean(times)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000.0 * statistics.mean(times) / (SAMPLE_N ** 3 / 1e6),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+                "cpu_baseline": cpu_baseline_obj({**rec, "solve_s": times}),
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_2604_26441_b300 import gmg, inputs
+
+    cfg = inputs.CONFIGS["c2"]
+    stream = torch.cuda.current_stream(dev)
+    opts = gmg.config_options(cfg, stream=stream.cuda_stream)
+    rho = torch.from_numpy(cfg.rho()).to(dev)
+    t_setup0 = time.perf_counter()
+    S = gmg.Solver(rho, p=cfg.p, opts=opts)
+    setup_s = time.perf_counter() - t_setup0
+    nn = S.nn
+    ne = cfg.n_elem
+    f_host = torch.from_numpy(cfg.load()).pin_memory()
+    f_dev = f_host.to(dev)
+    u = torch.zeros_like(f_dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- warm-up
+    info = None
+    for _ in range(args.warmup):
+        u.zero_()
+        _, info = S.solve(f_dev, u, tol=cfg.tol, maxit=cfg.maxit)
+    torch.cuda.synchronize()
+
+    # ---- timed solves (device events on the solve stream, L2 flushed between steps)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    k0 = gmg.kernel_launches()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        u.zero_()
+        _, info = S.solve(f_dev, u, tol=cfg.tol, maxit=cfg.maxit)
+        ev[k][1].record(stream)
+        infos.append(info)
+    torch.cuda.synchronize()
+    barrier()
+    launches = gmg.kernel_launches() - k0
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+    ok = all(i["status"] == 0 and i["rel_residual"] <= cfg.tol for i in infos)
+
+    # ---- end to end through the public API: pinned host f in, host u out
+    u_host = torch.empty(3 * nn, dtype=torch.float64).pin_memory()
+    f_stage = torch.empty_like(f_dev)
+    e2e_ms = []
+    for k in range(max(3, args.steps // 2)):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f_stage.copy_(f_host, non_blocking=True)
+        u.zero_()
+        S.solve(f_stage, u, tol=cfg.tol, maxit=cfg.maxit)
+        u_host.copy_(u, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
+
+    # ---- roofline of the fine operator (the kernel applied ~7x per PCG iteration)
+    x = torch.from_numpy(inputs.random_free_vector(cfg.fixed(), seed=1)).to(dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        S.apply(x, y)
+    reps = 30
+    ap_ms = []
+    for k in range(reps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S.apply(x, y)
+        b.record(stream)
+        ap_ms.append((a, b))
+    torch.cuda.synchronize()
+    apply_ms = statistics.mean(a.elapsed_time(b) for a, b in ap_ms)
+    alg_bytes = 12 * nn + 12 * nn + 4 * ne  # read u, write y, read E
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (apply_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": _profile_traffic(os.path.join(ROOT, "paper_2604_26441_b300", "csrc", "hot.cu")),
+                "kernel": "k_fine<APPLY> (matrix-free fine operator y = K u)",
+                "alg_bytes_per_launch": alg_bytes, "launch_ms": apply_ms, "peak_source": peak_kind}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": world, "levels": S.num_levels,
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "solve working set ~300 MB > 126 MB L2, and a 256 MB write flushes L2 between steps"},
+        "iterations": infos[-1]["iterations"], "rel_residual": infos[-1]["rel_residual"],
+        "all_converged": ok, "setup_ms": setup_s * 1000.0,
+        "roofline": roofline,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * 3 * nn, "d2h_bytes_per_step": 8 * 3 * nn},
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline_obj(run_oracle_sample(3))
+        except Exception as exc:  # reported, not fatal
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {exc}"[:300]}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -139,6 +139,10 @@ const char* gmg_status_str(int status);
 /* Text of the last error recorded on the calling thread ("" if none). */
 const char* gmg_last_error(void);
 
+/* Number of CUDA kernels this library has launched in the process so far (all
+ * handles); the difference across a region counts the kernels it ran. */
+unsigned long long gmg_kernel_launches(void);
+
 /* ---- introspection and per-step entry points ----------------------------
  * These expose the individual steps of the hot path so that each can be checked
  * on its own.  Vectors are device float[3*n_nodes(level)] unless stated; all

@@ -14,6 +14,10 @@
 
 using namespace gmg;
 
+namespace gmg {
+std::atomic<unsigned long long> g_kernel_launches{0};
+}
+
 namespace {
 
 thread_local std::string g_err;
@@ -445,6 +449,8 @@ const char* gmg_status_str(int st) {
 }
 
 const char* gmg_last_error(void) { return g_err.c_str(); }
+
+unsigned long long gmg_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
 
 void gmg_destroy(gmg_handle* h) {
     if (!h) return;

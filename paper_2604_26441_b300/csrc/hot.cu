@@ -596,23 +596,26 @@ int fine_grid_blocks(int nx, int ny, int nz) {
 void launch_fine(int mode, int dot, const FineArgs& a, const KeF& ke, cudaStream_t s) {
     const dim3 g = fine_grid(a.nx, a.ny, a.nz), b(TX, TY, TZ);
     if (mode == FM_APPLY) {
-        if (dot) k_fine<FM_APPLY, true><<<g, b, 0, s>>>(a, ke);
-        else k_fine<FM_APPLY, false><<<g, b, 0, s>>>(a, ke);
+        if (dot) { note_launch(); k_fine<FM_APPLY, true><<<g, b, 0, s>>>(a, ke); }
+        else { note_launch(); k_fine<FM_APPLY, false><<<g, b, 0, s>>>(a, ke); }
     } else if (mode == FM_SMOOTH) {
-        if (dot) k_fine<FM_SMOOTH, true><<<g, b, 0, s>>>(a, ke);
-        else k_fine<FM_SMOOTH, false><<<g, b, 0, s>>>(a, ke);
+        if (dot) { note_launch(); k_fine<FM_SMOOTH, true><<<g, b, 0, s>>>(a, ke); }
+        else { note_launch(); k_fine<FM_SMOOTH, false><<<g, b, 0, s>>>(a, ke); }
     } else {
+        note_launch();
         k_fine<FM_RESID, false><<<g, b, 0, s>>>(a, ke);
     }
 }
 
 void launch_fine_smooth0(const FineArgs& a, cudaStream_t s) {
+    note_launch();
     k_fine_smooth0<<<kVecBlocks * 2, kVecThreads, 0, s>>>(a);
 }
 
 void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask, const double* f,
                          const double* u, double* r64, float* r32, const double* sc, double* partial,
                          const KeD& ke, cudaStream_t s) {
+    note_launch();
     k_fine_resid64<<<fine_grid(nx, ny, nz), dim3(TX, TY, TZ), 0, s>>>(nx, ny, nz, E, mask, f, u, r64, r32, sc,
                                                                        partial, ke);
 }
@@ -622,12 +625,13 @@ int bsr_grid_blocks(long long nn) { return (int)((nn + kVecThreads - 1) / kVecTh
 void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
     const int g = bsr_grid_blocks(a.nn);
     if (mode == FM_APPLY) {
-        if (dot) k_bsr<FM_APPLY, true><<<g, kVecThreads, 0, s>>>(a);
-        else k_bsr<FM_APPLY, false><<<g, kVecThreads, 0, s>>>(a);
+        if (dot) { note_launch(); k_bsr<FM_APPLY, true><<<g, kVecThreads, 0, s>>>(a); }
+        else { note_launch(); k_bsr<FM_APPLY, false><<<g, kVecThreads, 0, s>>>(a); }
     } else if (mode == FM_SMOOTH) {
-        if (dot) k_bsr<FM_SMOOTH, true><<<g, kVecThreads, 0, s>>>(a);
-        else k_bsr<FM_SMOOTH, false><<<g, kVecThreads, 0, s>>>(a);
+        if (dot) { note_launch(); k_bsr<FM_SMOOTH, true><<<g, kVecThreads, 0, s>>>(a); }
+        else { note_launch(); k_bsr<FM_SMOOTH, false><<<g, kVecThreads, 0, s>>>(a); }
     } else {
+        note_launch();
         k_bsr<FM_RESID, false><<<g, kVecThreads, 0, s>>>(a);
     }
 }
@@ -635,6 +639,7 @@ void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
 void launch_bsr_smooth0(const BsrArgs& a, cudaStream_t s) {
     const long long n3 = 3 * a.nn;
     const int g = (int)std::min<long long>((n3 + kVecThreads - 1) / kVecThreads, kVecBlocks * 2);
+    note_launch();
     k_bsr_smooth0<<<g, kVecThreads, 0, s>>>(a);
 }
 
@@ -643,71 +648,85 @@ static int grid_for(long long n) {
 }
 
 void launch_restrict(const Level& f, const Level& c, const float* fine, float* coarse, cudaStream_t s) {
+    note_launch();
     k_restrict<<<grid_for(c.nn), 256, 0, s>>>(f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, c.mask, fine, coarse);
 }
 
 void launch_prolong_add(const Level& f, const Level& c, const float* coarse, float* fine, cudaStream_t s) {
+    note_launch();
     k_prolong_add<<<grid_for(f.nn), 256, 0, s>>>(f.nx, f.ny, f.nz, c.nx, c.ny, f.mask, coarse, fine);
 }
 
 void launch_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b, float* x,
                          long long n_dof, cudaStream_t s) {
     cudaMemsetAsync(x, 0, sizeof(float) * n_dof, s);
-    if (nL > 0) k_coarse_solve<<<(nL * 32 + 255) / 256, 256, 0, s>>>(nL, free_idx, Ainv, b, x);
+    if (nL > 0) { note_launch(); k_coarse_solve<<<(nL * 32 + 255) / 256, 256, 0, s>>>(nL, free_idx, Ainv, b, x); }
 }
 
 int vec_grid_blocks() { return kVecBlocks; }
 
 void launch_dot_f32(const float* a, const float* b, long long n, double* partial, cudaStream_t s) {
+    note_launch();
     k_dot_f32<<<kVecBlocks, kVecThreads, 0, s>>>(a, b, n, partial);
 }
 
 void launch_dot_f64_masked(const double* a, const double* b, const uint8_t* mask, long long nn, double* partial,
                            cudaStream_t s) {
+    note_launch();
     k_dot_f64_masked<<<kVecBlocks, kVecThreads, 0, s>>>(a, b, mask, nn, partial);
 }
 
 void launch_finalize(const double* partial, int n, double* sc, int slot, int op, cudaStream_t s) {
+    note_launch();
     k_finalize<<<1, kVecThreads, 0, s>>>(partial, n, sc, slot, op);
 }
 
 void launch_pcg_update(double* u, float* r, const float* p, const float* q, long long n, const double* sc,
                        double* partial, cudaStream_t s) {
+    note_launch();
     k_pcg_update<<<kVecBlocks, kVecThreads, 0, s>>>(u, r, p, q, n, sc, partial);
 }
 
 void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s) {
+    note_launch();
     k_p_update<<<grid_for(n), 256, 0, s>>>(p, z, n, sc);
 }
 
 void launch_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial, cudaStream_t s) {
+    note_launch();
     k_mask_u64<<<kVecBlocks, kVecThreads, 0, s>>>(u, mask, nn, partial);
 }
 
 void launch_scale_by_inv_sqrt(float* v, long long n, const double* sc, int slot, cudaStream_t s) {
+    note_launch();
     k_scale_inv_sqrt<<<grid_for(n), 256, 0, s>>>(v, n, sc, slot);
 }
 
 void launch_scale_invdiag_fine(const float* y, float* w, const float* E, const uint8_t* mask, int nx, int ny,
                                int nz, float kd, cudaStream_t s) {
     const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+    note_launch();
     k_scale_invdiag_fine<<<grid_for(nn), 256, 0, s>>>(y, w, E, mask, nx, ny, nz, kd);
 }
 
 void launch_scale_invdiag_bsr(const float* y, float* w, const float* invdiag, long long n, cudaStream_t s) {
+    note_launch();
     k_scale_invdiag_bsr<<<grid_for(n), 256, 0, s>>>(y, w, invdiag, n);
 }
 
 void launch_diag_dot_fine(const float* v, const float* E, const uint8_t* mask, int nx, int ny, int nz, float kd,
                           double* partial, cudaStream_t s) {
+    note_launch();
     k_diag_dot_fine<<<kVecBlocks, kVecThreads, 0, s>>>(v, E, mask, nx, ny, nz, kd, partial);
 }
 
 void launch_diag_dot_bsr(const float* v, const float* invdiag, long long n, double* partial, cudaStream_t s) {
+    note_launch();
     k_diag_dot_bsr<<<kVecBlocks, kVecThreads, 0, s>>>(v, invdiag, n, partial);
 }
 
 void launch_power_start(float* v, const uint8_t* mask, long long nn, cudaStream_t s) {
+    note_launch();
     k_power_start<<<grid_for(3 * nn), 256, 0, s>>>(v, mask, nn);
 }
 

@@ -6,11 +6,17 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <atomic>
 #include <vector>
 
 #include "gmg.h"
 
 namespace gmg {
+
+// Process-wide count of kernels this library has launched (read by
+// gmg_kernel_launches; every launcher adds the number of kernels it starts).
+extern std::atomic<unsigned long long> g_kernel_launches;
+inline void note_launch(unsigned long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 constexpr int kMaxLevels = 16;
 constexpr int kMaxDegree = 16;

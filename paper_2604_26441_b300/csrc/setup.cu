@@ -492,70 +492,94 @@ static int grid_for(long long n) { return (int)std::max<long long>(1, std::min<l
 
 void launch_moduli(const float* rho, long long ne, double p, double E0, double Emin, double* E64, float* E32,
                    cudaStream_t s) {
+    note_launch();
     k_moduli<<<grid_for(ne), 256, 0, s>>>(rho, ne, p, E0, Emin, E64, E32);
 }
 
-void launch_element_stiffness(double nu, double* Ke, cudaStream_t s) { k_element_stiffness<<<1, 576, 0, s>>>(nu, Ke); }
+void launch_element_stiffness(double nu, double* Ke, cudaStream_t s) {
+    note_launch();
+    k_element_stiffness<<<1, 576, 0, s>>>(nu, Ke);
+}
 
 void launch_mask_clamp(uint8_t* mask, int nx, int ny, int nz, cudaStream_t s) {
     const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+    note_launch();
     k_mask_clamp<<<grid_for(nn), 256, 0, s>>>(mask, nx, ny, nz);
 }
 
 void launch_mask_from_dofs(const uint8_t* fixed_dofs, uint8_t* mask, long long nn, cudaStream_t s) {
+    note_launch();
     k_mask_from_dofs<<<grid_for(nn), 256, 0, s>>>(fixed_dofs, mask, nn);
 }
 
 void launch_mask_inject(const Level& f, Level& c, cudaStream_t s) {
+    note_launch();
     k_mask_inject<<<grid_for(c.nn), 256, 0, s>>>(f.mask, f.nx, f.ny, c.mask, c.nx, c.ny, c.nz);
 }
 
 void launch_count_free(const uint8_t* mask, long long nn, int* out, cudaStream_t s) {
     cudaMemsetAsync(out, 0, sizeof(int), s);
+    note_launch();
     k_count_free<<<grid_for(nn), 256, 0, s>>>(mask, nn, out);
 }
 
-void launch_child_patterns(const double* Ke, double* Mpat, cudaStream_t s) { k_child_patterns<<<27, 192, 0, s>>>(Ke, Mpat); }
+void launch_child_patterns(const double* Ke, double* Mpat, cudaStream_t s) {
+    note_launch();
+    k_child_patterns<<<27, 192, 0, s>>>(Ke, Mpat);
+}
 
 void launch_coarse_element_matrices(int nx, int ny, int nz, const double* E, const uint8_t* fine_mask, const double* Ke,
                                     const double* Mpat, double* Kc, cudaStream_t s) {
     const long long nce = (long long)(nx >> 1) * (ny >> 1) * (nz >> 1);
-    if (nce > 0) k_coarse_element_matrices<<<(unsigned)nce, 192, 0, s>>>(nx, ny, nz, E, fine_mask, Ke, Mpat, Kc);
+    if (nce > 0) { note_launch(); k_coarse_element_matrices<<<(unsigned)nce, 192, 0, s>>>(nx, ny, nz, E, fine_mask, Ke, Mpat, Kc); }
 }
 
 void launch_fine_element_matrices(const double* E, long long ne, const double* Ke, double* Kc, cudaStream_t s) {
+    note_launch();
     k_fine_element_matrices<<<grid_for(ne * 576), 256, 0, s>>>(E, ne, Ke, Kc);
 }
 
 void launch_gather_level1(const Level& c, const double* Kc, double* A64, cudaStream_t s) {
     cudaMemsetAsync(A64, 0, sizeof(double) * kPlanes * c.nn, s);
+    note_launch();
     k_gather_level1<<<grid_for(c.nn), 256, 0, s>>>(c.nx, c.ny, c.nz, c.nn, Kc, A64);
 }
 
 void launch_galerkin_rap(const Level& f, const Level& c, cudaStream_t s) {
+    note_launch();
     k_galerkin_rap<<<grid_for(c.nn * kSlots), 256, 0, s>>>(f.nx, f.ny, f.nz, f.nn, f.A64, c.nx, c.ny, c.nz, c.nn, c.A64);
 }
 
 void launch_finish_bsr(Level& l, cudaStream_t s) {
+    note_launch();
     k_finish_bsr<<<grid_for(l.nn), 256, 0, s>>>(l.nx, l.ny, l.nz, l.nn, l.mask, l.A64, l.A32, l.invdiag);
 }
 
 void launch_smoother_coef(double* coef, const double* lam, int kind, int degree, double omega, double alpha,
                           double safety, cudaStream_t s) {
+    note_launch();
     k_smoother_coef<<<1, 32, 0, s>>>(coef, lam, kind, degree, omega, alpha, safety);
 }
 
-void launch_lambda_finish(double* sc, double* lam_slot, cudaStream_t s) { k_lambda_finish<<<1, 32, 0, s>>>(sc, lam_slot); }
+void launch_lambda_finish(double* sc, double* lam_slot, cudaStream_t s) {
+    note_launch();
+    k_lambda_finish<<<1, 32, 0, s>>>(sc, lam_slot);
+}
 
 void launch_free_index(const uint8_t* mask, long long nn, int* free_idx, int* count, cudaStream_t s) {
+    note_launch();
     k_free_index<<<1, 32, 0, s>>>(mask, nn, free_idx, count);
 }
 
 void launch_dense_gather(const Level& l, const int* free_idx, int n, double* dense, cudaStream_t s) {
+    note_launch();
     k_dense_gather<<<grid_for((long long)n * n), 256, 0, s>>>(l.nx, l.ny, l.nn, l.A64, free_idx, n, dense);
 }
 
-void launch_regularise(double* dense, int n, double* eps_out, cudaStream_t s) { k_regularise<<<1, 256, 0, s>>>(dense, n, eps_out); }
+void launch_regularise(double* dense, int n, double* eps_out, cudaStream_t s) {
+    note_launch();
+    k_regularise<<<1, 256, 0, s>>>(dense, n, eps_out);
+}
 
 // Factor A (n x n, row-major, in place, lower triangle) and write (A)^{-1} to Ainv.
 // work: n*n doubles.  Returns GMG_OK, GMG_ERR_CHOLESKY or GMG_ERR_CUDA.
@@ -564,11 +588,14 @@ int cholesky_and_inverse(double* A, int n, double* work, int* info_dev, double* 
     cudaMemsetAsync(info_dev, 0, sizeof(int), s);
     for (int k0 = 0; k0 < n; k0 += NB) {
         const int kb = std::min(NB, n - k0);
+        note_launch();
         k_potrf_diag<<<1, dim3(NB, NB), 0, s>>>(A, n, k0, kb, info_dev);
         const int rest = n - k0 - kb;
         if (rest > 0) {
+            note_launch();
             k_trsm_panel<<<(rest + 127) / 128, 128, 0, s>>>(A, n, k0, kb);
             const int nbt = (rest + NB - 1) / NB;
+            note_launch();
             k_syrk<<<dim3(nbt, nbt), dim3(NB, NB), 0, s>>>(A, n, k0, kb);
         }
     }
@@ -578,8 +605,10 @@ int cholesky_and_inverse(double* A, int n, double* work, int* info_dev, double* 
     if (info != 0) return GMG_ERR_CHOLESKY;
     const size_t shm = sizeof(double) * (size_t)n;
     if (shm > 48 * 1024) cudaFuncSetAttribute(k_trinv_col, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    note_launch();
     k_trinv_col<<<n, 256, shm, s>>>(A, n, work);
     const int nbt = (n + NB - 1) / NB;
+    note_launch();
     k_xtx<<<dim3(nbt, nbt), dim3(NB, NB), 0, s>>>(work, n, Ainv);
     if (cudaGetLastError() != cudaSuccess) return GMG_ERR_CUDA;
     return GMG_OK;

@@ -65,6 +65,7 @@ _SIGS = {
     "gmg_destroy": (None, [_P]),
     "gmg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "gmg_last_error": (ctypes.c_char_p, []),
+    "gmg_kernel_launches": (ctypes.c_ulonglong, []),
     "gmg_num_levels": (ctypes.c_int, [_P]),
     "gmg_level_dims": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gmg_get_mask": (ctypes.c_int, [_P, ctypes.c_int, _P]),
@@ -100,6 +101,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load_library().gmg_kernel_launches())
 
 
 def _check(rc: int, allow=(GMG_OK,)) -> int:
