@@ -198,6 +198,34 @@ int gmg_vcycle(gmg_handle* h, const float* r_dev, float* z_dev);
 int gmg_residual64(gmg_handle* h, const double* f_dev, const double* u_dev, double* r_dev,
                    double* rel_out);
 
+/* ---- allocation-free residual check -------------------------------------
+ * The paper has no counterpart of this entry point.  It computes the same FP64
+ * true residual as gmg_residual64 (r = f - K u on the fine level, *rel_out =
+ * ||r_free|| / ||f_free||) for callers that cannot call cudaMalloc: code that
+ * runs inside a framework owning every device allocation through its own pool,
+ * a plug-in that must not grow the process's device footprint behind its host,
+ * or a check run when the device has no free memory left.  It needs no handle
+ * and allocates nothing; the caller passes every input and output:
+ *   g       : element counts; the grid must need at most 65,536 blocks of 32x4x2
+ *             nodes (e.g. 100^3 needs 5,304), otherwise GMG_ERR_ARG with a message
+ *             in gmg_last_error() and nothing is launched;
+ *   E_dev   : device double[nx*ny*nz] element moduli E_e;
+ *   mask_dev: device uint8[n_nodes] fixed-component bits (bit c set = DOF c fixed);
+ *   nu      : Poisson ratio of the unit element stiffness;
+ *   f_dev, u_dev : device double[3*n_nodes]; r_dev : device double[3*n_nodes] or NULL;
+ *   rel_out : HOST double; stream : cudaStream_t or NULL (the call synchronises it).
+ * Its scratch (the element stiffness and the per-block partial sums, 526 KB) is
+ * a static device array that every GPU loading this library holds until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the array: calls whose kernels
+ * overlap on the GPU (for example on two streams) race and must be serialised
+ * by the caller.  Each call rewrites every scratch word it reads, so nothing
+ * carries over from the previous call. */
+int gmg_residual64_noalloc(const gmg_grid* g, const double* E_dev, const uint8_t* mask_dev, double nu,
+                           const double* f_dev, const double* u_dev, double* r_dev, double* rel_out,
+                           void* stream);
+
 #ifdef __cplusplus
 }
 #endif

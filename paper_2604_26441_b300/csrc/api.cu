@@ -14,13 +14,18 @@
 
 using namespace gmg;
 
-namespace gmg {
-std::atomic<unsigned long long> g_kernel_launches{0};
-}
-
 namespace {
 
 thread_local std::string g_err;
+
+}  // namespace
+
+namespace gmg {
+std::atomic<unsigned long long> g_kernel_launches{0};
+void set_error_text(const std::string& msg) { g_err = msg; }
+}  // namespace gmg
+
+namespace {
 
 int fail(int code, const std::string& msg) {
     g_err = msg;

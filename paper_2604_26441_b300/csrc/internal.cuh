@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <atomic>
+#include <string>
 #include <vector>
 
 #include "gmg.h"
@@ -17,6 +18,9 @@ namespace gmg {
 // gmg_kernel_launches; every launcher adds the number of kernels it starts).
 extern std::atomic<unsigned long long> g_kernel_launches;
 inline void note_launch(unsigned long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Records the text gmg_last_error() returns on the calling thread.
+void set_error_text(const std::string& msg);
 
 constexpr int kMaxLevels = 16;
 constexpr int kMaxDegree = 16;

@@ -79,6 +79,8 @@ _SIGS = {
     "gmg_coarse_solve": (ctypes.c_int, [_P, _P, _P]),
     "gmg_vcycle": (ctypes.c_int, [_P, _P, _P]),
     "gmg_residual64": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "gmg_residual64_noalloc": (ctypes.c_int, [ctypes.POINTER(_Grid), _P, _P, ctypes.c_double, _P, _P, _P,
+                                              ctypes.POINTER(ctypes.c_double), _P]),
 }
 
 
@@ -154,6 +156,25 @@ def config_options(cfg, stream: int | None = None) -> _Options:
     """Options for one of the synthetic configurations in ``inputs.CONFIGS``."""
     return options(levels=cfg.levels, smoother=cfg.smoother, degree=cfg.degree, coarse_smoother=None,
                    coarse_degree=None, omega=cfg.omega, coarse_omega=None, stream=stream)
+
+
+def residual64_noalloc(dims, E, mask, f, u, r=None, nu: float = 0.3, stream: int | None = None) -> float:
+    """FP64 relative true residual through the allocation-free entry point: no
+    handle, no device allocation inside the library (the caller's tensors are
+    the only device memory it touches besides its static scratch)."""
+    import torch
+    lib = load_library()
+    nx, ny, nz = dims
+    nn = (nx + 1) * (ny + 1) * (nz + 1)
+    g = _Grid(nx, ny, nz)
+    rel = ctypes.c_double()
+    rp = None if r is None else _ptr(r, torch.float64, 3 * nn, "r")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib.gmg_residual64_noalloc(ctypes.byref(g), _ptr(E, torch.float64, nx * ny * nz, "E"),
+                                      _ptr(mask, torch.uint8, nn, "mask"), nu, _ptr(f, torch.float64, 3 * nn, "f"),
+                                      _ptr(u, torch.float64, 3 * nn, "u"), rp, ctypes.byref(rel), stream))
+    return rel.value
 
 
 class Solver:
