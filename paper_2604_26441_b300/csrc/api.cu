@@ -92,13 +92,16 @@ int partial_count(gmg_handle* h, int li, int kind) {
 }
 
 // y = K^l x (masked); with dot: partial += x . y and finalised into `slot`.
-void level_apply(gmg_handle* h, int li, const float* x, float* y, int dot_slot = -1, int op = FIN_NONE) {
+// mask_in: x may hold values on fixed DOFs (caller input) that must be ignored.
+void level_apply(gmg_handle* h, int li, const float* x, float* y, int dot_slot = -1, int op = FIN_NONE,
+                 bool mask_in = false) {
     cudaStream_t s = h->stream;
     const bool dot = dot_slot >= 0;
     if (li == 0) {
         FineArgs a = fine_args(h);
         a.xin = x; a.out = y; a.partial = dot ? h->partials : nullptr;
-        launch_fine(FM_APPLY, dot, a, h->keF, s);
+        a.scratch = h->t0;
+        launch_fine(FM_APPLY, dot, mask_in && !dot, a, h->gh, s);
     } else {
         BsrArgs a = bsr_args(h, li);
         a.xin = x; a.out = y; a.partial = dot ? h->partials : nullptr;
@@ -111,7 +114,7 @@ void level_resid(gmg_handle* h, int li, const float* b, const float* x, float* t
     if (li == 0) {
         FineArgs a = fine_args(h);
         a.xin = x; a.b = b; a.out = t;
-        launch_fine(FM_RESID, 0, a, h->keF, h->stream);
+        launch_fine(FM_RESID, 0, 0, a, h->gh, h->stream);
     } else {
         BsrArgs a = bsr_args(h, li);
         a.xin = x; a.b = b; a.out = t;
@@ -130,7 +133,7 @@ void smooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, c
         a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
         a.partial = dot ? h->partials : nullptr;
         if (zero_init) launch_fine_smooth0(a, s);
-        else { a.xin = xcur; launch_fine(FM_SMOOTH, dot, a, h->keF, s); }
+        else { a.xin = xcur; launch_fine(FM_SMOOTH, dot, 0, a, h->gh, s); }
     } else {
         BsrArgs a = bsr_args(h, li);
         a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
@@ -286,7 +289,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         TRY(dalloc(h, &l.coef, 2 * kMaxDegree));
         if (li > 0) {
             TRY(dalloc(h, &l.A64, (size_t)kPlanes * l.nn));
-            TRY(dalloc(h, &l.A32, (size_t)kPlanes * l.nn));
+            TRY(dalloc(h, &l.A32, (size_t)kSymPlanes * l.nn));
             TRY(dalloc(h, &l.invdiag, 3 * l.nn));
             TRY(dalloc(h, &l.x, 3 * l.nn));
             TRY(dalloc(h, &l.x2, 3 * l.nn));
@@ -311,6 +314,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     CU(cudaMemsetAsync(h->sc, 0, sizeof(double) * SC_COUNT, s));
     int maxp = vec_grid_blocks();
     maxp = std::max(maxp, fine_grid_blocks(l0.nx, l0.ny, l0.nz));
+    maxp = std::max(maxp, resid64_grid_blocks(l0.nx, l0.ny, l0.nz));
     for (int li = 1; li < L; ++li) maxp = std::max(maxp, bsr_grid_blocks(h->lev[li].nn));
     h->max_partials = maxp;
     TRY(dalloc(h, &h->partials, maxp));
@@ -326,6 +330,16 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     CU(cudaStreamSynchronize(s));
     for (int i = 0; i < 576; ++i) h->keF.v[i] = (float)h->keD.v[i];
     h->kd = h->keF.v[0];
+    {
+        double* g72 = nullptr;
+        double gh[72];
+        TRY(dalloc(h, &g72, 72));
+        launch_hadamard_blocks(Ke, g72, s);
+        CU(cudaMemcpyAsync(gh, g72, sizeof gh, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        for (int i = 0; i < 72; ++i) { h->gh.g[i] = (float)gh[i]; h->gh64.g[i] = gh[i]; }
+        dfree(h, g72);
+    }
 
     // ---- Galerkin hierarchy
     if (L >= 2) {
@@ -391,7 +405,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
             double* Kc = nullptr;
             const long long ne0 = (long long)l0.nx * l0.ny * l0.nz;
             TRY(dalloc(h, &l0.A64, (size_t)kPlanes * l0.nn));
-            TRY(dalloc(h, &l0.A32, (size_t)kPlanes * l0.nn));
+            TRY(dalloc(h, &l0.A32, (size_t)kSymPlanes * l0.nn));
             TRY(dalloc(h, &l0.invdiag, 3 * l0.nn));
             TRY(dalloc(h, &Kc, (size_t)ne0 * 576));
             launch_fine_element_matrices(h->E64, ne0, Ke, Kc, s);
@@ -517,7 +531,7 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
 
 int gmg_apply(gmg_handle* h, const float* u, float* y) {
     if (!h || !u || !y) return fail(GMG_ERR_ARG, "null argument");
-    level_apply(h, 0, u, y);
+    level_apply(h, 0, u, y, -1, FIN_NONE, true);
     CU(cudaGetLastError());
     return GMG_OK;
 }
@@ -538,8 +552,8 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
         return st;
     };
     auto true_residual = [&](double& rel) -> int {
-        launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, h->sc, h->partials, h->keD, s);
-        launch_finalize(h->partials, partial_count(h, 0, 0), h->sc, SC_TRR, FIN_NONE, s);
+        launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, h->sc, h->partials, h->gh64, s);
+        launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
         TRY(sync_scalars(h));
         rel = std::sqrt(sch[SC_TRR]) / std::sqrt(sch[SC_FF]);
         return GMG_OK;
@@ -654,7 +668,7 @@ int gmg_set_lambda(gmg_handle* h, int level, double lam) {
 int gmg_level_apply(gmg_handle* h, int level, const float* x, float* y) {
     TRY(check_level(h, level));
     if (!x || !y) return fail(GMG_ERR_ARG, "null vector");
-    level_apply(h, level, x, y);
+    level_apply(h, level, x, y, -1, FIN_NONE, true);
     CU(cudaGetLastError());
     return GMG_OK;
 }
@@ -712,8 +726,8 @@ int gmg_residual64(gmg_handle* h, const double* f, const double* u, double* r, d
     cudaStream_t s = h->stream;
     h->sc_host[SC_UNZ] = 1.0;
     CU(cudaMemcpyAsync(h->sc + SC_UNZ, h->sc_host + SC_UNZ, sizeof(double), cudaMemcpyHostToDevice, s));
-    launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, r, nullptr, h->sc, h->partials, h->keD, s);
-    launch_finalize(h->partials, partial_count(h, 0, 0), h->sc, SC_TRR, FIN_NONE, s);
+    launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, r, nullptr, h->sc, h->partials, h->gh64, s);
+    launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
     launch_dot_f64_masked(f, f, l0.mask, l0.nn, h->partials, s);
     launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_FF, FIN_NONE, s);
     TRY(sync_scalars(h));

@@ -1,9 +1,8 @@
 // Hot-path kernels of the GMG-preconditioned CG solver (sm_103a).
 //
-//  * k_fine          -- matrix-free fine operator (Eq. mf_matvec) fused with its
-//                       consumers: plain apply (+ p.q), one smoother step
-//                       (damped Jacobi / Chebyshev, Algorithm cheb), or the
-//                       residual b - K x that feeds the restriction (Eq. vcycle);
+//  * k_fine_smooth0  -- first fine-level smoother step from zero (the fused
+//                       fine operator lives in fine.cu, its FP64 residual form
+//                       in resid64.cu);
 //  * k_bsr           -- the same three modes on an assembled Galerkin level
 //                       (27-point 3x3-block operator, implicit structured columns);
 //  * k_restrict / k_prolong_add -- R = P^T and P of Eq. trilinear_weights /
@@ -22,10 +21,6 @@ namespace gmg {
 
 namespace {
 
-constexpr int TX = 32, TY = 4, TZ = 2;               // owned nodes per fine block
-constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2; // node tile incl. halo
-constexpr int EX = TX + 1, EY = TY + 1, EZ = TZ + 1; // element tile
-constexpr int kFineThreads = TX * TY * TZ;
 constexpr int kVecThreads = 256;
 constexpr int kVecBlocks = 148 * 4;
 
@@ -47,130 +42,6 @@ __device__ __forceinline__ double block_sum(double v, int tid) {
 }
 
 __device__ __forceinline__ bool fixed_bit(uint8_t m, int c) { return (m >> c) & 1; }
-
-// ---------------------------------------------------------------------------
-// Fine level: owner-computes, one thread per node of a 32x4x2 tile.  The node
-// tile (with a one-node halo) and the element tile are staged in shared memory
-// with coalesced row loads; each thread forms
-//   y_n = sum_{elements e containing n} E_e * K_e[rows of n] * u_e
-// from the 27 neighbouring displacements held in registers.  K_e comes from
-// the kernel-parameter bank, so every FFMA takes its matrix entry directly as a
-// constant operand.  No atomics: results are bitwise reproducible.
-// ---------------------------------------------------------------------------
-template <int MODE, bool DOT>
-__global__ void __launch_bounds__(kFineThreads) k_fine(FineArgs a, KeF ke) {
-    __shared__ float su[HZ][HY][HX * 3];
-    __shared__ float sE[EZ][EY][EX];
-    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-    const int tid = tx + TX * (ty + TY * tz);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-    const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
-
-    for (int idx = tid; idx < HZ * HY * HX * 3; idx += kFineThreads) {
-        const int c3 = idx % (HX * 3);
-        const int row = idx / (HX * 3);
-        const int yy = row % HY, zz = row / HY;
-        const int gx = x0 - 1 + c3 / 3, comp = c3 % 3, gy = y0 - 1 + yy, gz = z0 - 1 + zz;
-        float v = 0.f;
-        if (gx >= 0 && gx < NX && gy >= 0 && gy < NY && gz >= 0 && gz < NZ) {
-            const long long node = gx + (long long)NX * (gy + (long long)NY * gz);
-            if (!fixed_bit(a.mask[node], comp)) v = a.xin[3 * node + comp];
-        }
-        su[zz][yy][c3] = v;
-    }
-    for (int idx = tid; idx < EZ * EY * EX; idx += kFineThreads) {
-        const int ex = idx % EX, ey = (idx / EX) % EY, ez = idx / (EX * EY);
-        const int gx = x0 - 1 + ex, gy = y0 - 1 + ey, gz = z0 - 1 + ez;
-        float v = 0.f;
-        if (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz)
-            v = a.E[gx + (long long)a.nx * (gy + (long long)a.ny * gz)];
-        sE[ez][ey][ex] = v;
-    }
-    __syncthreads();
-
-    const int i = x0 + tx, j = y0 + ty, k = z0 + tz;
-    double dotv = 0.0;
-    if (i < NX && j < NY && k < NZ) {
-        float u[3][3][3][3];
-#pragma unroll
-        for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) u[dz][dy][dx][c] = su[tz + dz][ty + dy][(tx + dx) * 3 + c];
-        // K_e annihilates rigid translations, so sum_b K_e[a][b] u_b = sum_b K_e[a][b] (u_b - u_n)
-        // exactly; contracting the differences keeps FP32 rounding proportional to the
-        // local variation of u instead of its magnitude (fixed neighbours enter as 0 - u_n).
-        const float un[3] = {u[1][1][1][0], u[1][1][1][1], u[1][1][1][2]};
-#pragma unroll
-        for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) u[dz][dy][dx][c] -= un[c];
-        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, esum = 0.f;
-#pragma unroll
-        for (int ea = 0; ea < 8; ++ea) {
-            const float Ee = sE[tz + 1 - ldz(ea)][ty + 1 - ldy(ea)][tx + 1 - ldx(ea)];
-            esum += Ee;
-            float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-#pragma unroll
-            for (int eb = 0; eb < 8; ++eb) {
-                if (eb == ea) continue;  // u_n - u_n = 0
-                const int ox = ldx(eb) - ldx(ea) + 1, oy = ldy(eb) - ldy(ea) + 1, oz = ldz(eb) - ldz(ea) + 1;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const float ud = u[oz][oy][ox][d];
-                    f0 = fmaf(ke.v[(3 * ea + 0) * 24 + 3 * eb + d], ud, f0);
-                    f1 = fmaf(ke.v[(3 * ea + 1) * 24 + 3 * eb + d], ud, f1);
-                    f2 = fmaf(ke.v[(3 * ea + 2) * 24 + 3 * eb + d], ud, f2);
-                }
-            }
-            acc0 = fmaf(Ee, f0, acc0);
-            acc1 = fmaf(Ee, f1, acc1);
-            acc2 = fmaf(Ee, f2, acc2);
-        }
-        const long long node = i + (long long)NX * (j + (long long)NY * k);
-        const uint8_t m = a.mask[node];
-        const float y[3] = {acc0, acc1, acc2};
-        if (MODE == FM_APPLY) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float v = fixed_bit(m, c) ? 0.f : y[c];
-                a.out[3 * node + c] = v;
-                if (DOT) dotv += (double)un[c] * (double)v;
-            }
-        } else if (MODE == FM_RESID) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                a.out[3 * node + c] = fixed_bit(m, c) ? 0.f : a.b[3 * node + c] - y[c];
-        } else {  // FM_SMOOTH
-            const float inv = 1.f / (a.kd * esum);
-            const float cd = (float)a.coef[2 * a.step], ca = (float)a.coef[2 * a.step + 1];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float xn = 0.f, dn = 0.f;
-                if (!fixed_bit(m, c)) {
-                    const float bc = a.b[3 * node + c];
-                    dn = ca * inv * (bc - y[c]);
-                    if (cd != 0.f) dn = fmaf(cd, a.dold[3 * node + c], dn);
-                    xn = un[c] + dn;
-                    if (DOT) dotv += (double)bc * (double)xn;
-                }
-                a.out[3 * node + c] = xn;
-                if (a.dnew) a.dnew[3 * node + c] = dn;
-            }
-        }
-    }
-    if (DOT) {
-        const double s = block_sum<kFineThreads>(dotv, tid);
-        if (tid == 0) a.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
-    }
-}
 
 // First smoother step from x = 0: x_1 = c_a D^{-1} b (no operator application).
 __global__ void k_fine_smooth0(FineArgs a) {
@@ -198,110 +69,49 @@ __global__ void k_fine_smooth0(FineArgs a) {
     }
 }
 
-// FP64 true residual r = f - K u on the fine level, ||r_free||^2 per block.
-// When the scalar SC_UNZ is 0 (u is identically zero) the operator is skipped.
-__global__ void __launch_bounds__(kFineThreads) k_fine_resid64(int nx, int ny, int nz, const double* E,
-                                                               const uint8_t* mask, const double* f,
-                                                               const double* uvec, double* r64, float* r32,
-                                                               const double* sc, double* partial, KeD ke) {
-    __shared__ double su[HZ][HY][HX * 3];
-    __shared__ double sE[EZ][EY][EX];
-    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-    const int tid = tx + TX * (ty + TY * tz);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-    const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
-    const bool uzero = sc[SC_UNZ] == 0.0;
-    if (!uzero) {
-        for (int idx = tid; idx < HZ * HY * HX * 3; idx += kFineThreads) {
-            const int c3 = idx % (HX * 3);
-            const int row = idx / (HX * 3);
-            const int yy = row % HY, zz = row / HY;
-            const int gx = x0 - 1 + c3 / 3, comp = c3 % 3, gy = y0 - 1 + yy, gz = z0 - 1 + zz;
-            double v = 0.0;
-            if (gx >= 0 && gx < NX && gy >= 0 && gy < NY && gz >= 0 && gz < NZ) {
-                const long long node = gx + (long long)NX * (gy + (long long)NY * gz);
-                if (!fixed_bit(mask[node], comp)) v = uvec[3 * node + comp];
-            }
-            su[zz][yy][c3] = v;
-        }
-        for (int idx = tid; idx < EZ * EY * EX; idx += kFineThreads) {
-            const int ex = idx % EX, ey = (idx / EX) % EY, ez = idx / (EX * EY);
-            const int gx = x0 - 1 + ex, gy = y0 - 1 + ey, gz = z0 - 1 + ez;
-            double v = 0.0;
-            if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
-                v = E[gx + (long long)nx * (gy + (long long)ny * gz)];
-            sE[ez][ey][ex] = v;
-        }
-    }
-    __syncthreads();
-    const int i = x0 + tx, j = y0 + ty, k = z0 + tz;
-    double rr = 0.0;
-    if (i < NX && j < NY && k < NZ) {
-        double acc[3] = {0.0, 0.0, 0.0};
-        if (!uzero) {
-#pragma unroll
-            for (int ea = 0; ea < 8; ++ea) {
-                const double Ee = sE[tz + 1 - ldz(ea)][ty + 1 - ldy(ea)][tx + 1 - ldx(ea)];
-                double f0 = 0.0, f1 = 0.0, f2 = 0.0;
-#pragma unroll
-                for (int eb = 0; eb < 8; ++eb) {
-                    const int ox = ldx(eb) - ldx(ea) + 1, oy = ldy(eb) - ldy(ea) + 1, oz = ldz(eb) - ldz(ea) + 1;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const double ud = su[tz + oz][ty + oy][(tx + ox) * 3 + d];
-                        f0 = fma(ke.v[(3 * ea + 0) * 24 + 3 * eb + d], ud, f0);
-                        f1 = fma(ke.v[(3 * ea + 1) * 24 + 3 * eb + d], ud, f1);
-                        f2 = fma(ke.v[(3 * ea + 2) * 24 + 3 * eb + d], ud, f2);
-                    }
-                }
-                acc[0] = fma(Ee, f0, acc[0]);
-                acc[1] = fma(Ee, f1, acc[1]);
-                acc[2] = fma(Ee, f2, acc[2]);
-            }
-        }
-        const long long node = i + (long long)NX * (j + (long long)NY * k);
-        const uint8_t m = mask[node];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            double v = 0.0;
-            if (!fixed_bit(m, c)) v = f[3 * node + c] - acc[c];
-            if (r64) r64[3 * node + c] = v;
-            if (r32) r32[3 * node + c] = (float)v;
-            rr += v * v;
-        }
-    }
-    const double s = block_sum<kFineThreads>(rr, tid);
-    if (tid == 0) partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
-}
-
 // ---------------------------------------------------------------------------
-// Assembled levels: one thread per node, 27 blocks of 3x3 read from
-// plane-major storage (coalesced across consecutive nodes); neighbour columns
-// are implicit in the structured grid.
+// Assembled levels: K^l is symmetric, so only the diagonal block and the 13
+// "forward" neighbour blocks (slots 13..26, offsets after the node in memory
+// order) are stored, plane-major: A[(u*9 + r*3 + c)*nn + n] is entry (r, c) of
+// block (n, n + o_u), u = slot - 13.  Row n of K^l is then
+//   sum_u A_u(n) x(n + o_u)  +  sum_{u>0} A_u(n - o_u)^T x(n - o_u),
+// one thread per node; every plane read is coalesced across consecutive nodes,
+// and the transposed reads at n - o_u re-touch planes read a few blocks earlier
+// (mostly L2 hits), so each stored value crosses HBM about once.
 // ---------------------------------------------------------------------------
 template <int MODE, bool DOT>
 __global__ void __launch_bounds__(kVecThreads) k_bsr(BsrArgs a) {
-    const long long n = blockIdx.x * (long long)kVecThreads + threadIdx.x;
+    const int n = blockIdx.x * kVecThreads + threadIdx.x;
+    const int nn = (int)a.nn;
     double dotv = 0.0;
-    if (n < a.nn) {
+    if (n < nn) {
         const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
-        const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / ((long long)NX * NY));
+        const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
         float y0 = 0.f, y1 = 0.f, y2 = 0.f;
 #pragma unroll
-        for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int ii = i + dx, jj = j + dy, kk = k + dz;
-                    if (ii < 0 || ii >= NX || jj < 0 || jj >= NY || kk < 0 || kk >= NZ) continue;
-                    const long long m = n + dx + (long long)NX * (dy + (long long)NY * dz);
-                    const float v0 = a.xin[3 * m], v1 = a.xin[3 * m + 1], v2 = a.xin[3 * m + 2];
-                    const float* A = a.A + (long long)(slot_of(dx, dy, dz) * 9) * a.nn + n;
-                    y0 = fmaf(A[0 * a.nn], v0, fmaf(A[1 * a.nn], v1, fmaf(A[2 * a.nn], v2, y0)));
-                    y1 = fmaf(A[3 * a.nn], v0, fmaf(A[4 * a.nn], v1, fmaf(A[5 * a.nn], v2, y1)));
-                    y2 = fmaf(A[6 * a.nn], v0, fmaf(A[7 * a.nn], v1, fmaf(A[8 * a.nn], v2, y2)));
-                }
+        for (int u = 0; u < 14; ++u) {
+            const int s = 13 + u;
+            const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+            const int off = dx + NX * (dy + NY * dz);
+            // forward block (n, n + o)
+            if (i + dx >= 0 && i + dx < NX && j + dy >= 0 && j + dy < NY && k + dz < NZ) {
+                const int m = n + off;
+                const float v0 = a.xin[3 * m], v1 = a.xin[3 * m + 1], v2 = a.xin[3 * m + 2];
+                const float* A = a.A + (long long)(u * 9) * nn + n;
+                y0 = fmaf(A[0 * (long long)nn], v0, fmaf(A[1 * (long long)nn], v1, fmaf(A[2 * (long long)nn], v2, y0)));
+                y1 = fmaf(A[3 * (long long)nn], v0, fmaf(A[4 * (long long)nn], v1, fmaf(A[5 * (long long)nn], v2, y1)));
+                y2 = fmaf(A[6 * (long long)nn], v0, fmaf(A[7 * (long long)nn], v1, fmaf(A[8 * (long long)nn], v2, y2)));
+            }
+            // backward block (n, n - o) = block (n - o, n)^T
+            if (u > 0 && i - dx >= 0 && i - dx < NX && j - dy >= 0 && j - dy < NY && k - dz >= 0) {
+                const int m = n - off;
+                const float v0 = a.xin[3 * m], v1 = a.xin[3 * m + 1], v2 = a.xin[3 * m + 2];
+                const float* A = a.A + (long long)(u * 9) * nn + m;
+                y0 = fmaf(A[0 * (long long)nn], v0, fmaf(A[3 * (long long)nn], v1, fmaf(A[6 * (long long)nn], v2, y0)));
+                y1 = fmaf(A[1 * (long long)nn], v0, fmaf(A[4 * (long long)nn], v1, fmaf(A[7 * (long long)nn], v2, y1)));
+                y2 = fmaf(A[2 * (long long)nn], v0, fmaf(A[5 * (long long)nn], v1, fmaf(A[8 * (long long)nn], v2, y2)));
+            }
+        }
         const uint8_t msk = a.mask[n];
         const float y[3] = {y0, y1, y2};
         if (MODE == FM_APPLY) {
@@ -584,40 +394,9 @@ __global__ void k_power_start(float* v, const uint8_t* mask, long long nn) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static dim3 fine_grid(int nx, int ny, int nz) {
-    return dim3((nx + 1 + TX - 1) / TX, (ny + 1 + TY - 1) / TY, (nz + 1 + TZ - 1) / TZ);
-}
-
-int fine_grid_blocks(int nx, int ny, int nz) {
-    const dim3 g = fine_grid(nx, ny, nz);
-    return (int)(g.x * g.y * g.z);
-}
-
-void launch_fine(int mode, int dot, const FineArgs& a, const KeF& ke, cudaStream_t s) {
-    const dim3 g = fine_grid(a.nx, a.ny, a.nz), b(TX, TY, TZ);
-    if (mode == FM_APPLY) {
-        if (dot) { note_launch(); k_fine<FM_APPLY, true><<<g, b, 0, s>>>(a, ke); }
-        else { note_launch(); k_fine<FM_APPLY, false><<<g, b, 0, s>>>(a, ke); }
-    } else if (mode == FM_SMOOTH) {
-        if (dot) { note_launch(); k_fine<FM_SMOOTH, true><<<g, b, 0, s>>>(a, ke); }
-        else { note_launch(); k_fine<FM_SMOOTH, false><<<g, b, 0, s>>>(a, ke); }
-    } else {
-        note_launch();
-        k_fine<FM_RESID, false><<<g, b, 0, s>>>(a, ke);
-    }
-}
-
 void launch_fine_smooth0(const FineArgs& a, cudaStream_t s) {
     note_launch();
     k_fine_smooth0<<<kVecBlocks * 2, kVecThreads, 0, s>>>(a);
-}
-
-void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask, const double* f,
-                         const double* u, double* r64, float* r32, const double* sc, double* partial,
-                         const KeD& ke, cudaStream_t s) {
-    note_launch();
-    k_fine_resid64<<<fine_grid(nx, ny, nz), dim3(TX, TY, TZ), 0, s>>>(nx, ny, nz, E, mask, f, u, r64, r32, sc,
-                                                                       partial, ke);
 }
 
 int bsr_grid_blocks(long long nn) { return (int)((nn + kVecThreads - 1) / kVecThreads); }

@@ -27,6 +27,7 @@ constexpr int kMaxDegree = 16;
 constexpr int kSlots = 27;     // 27-point neighbourhood of a node
 constexpr int kPlanes = 243;   // 27 slots x 3 x 3 block entries
 constexpr int kSelfSlot = 13;  // slot of offset (0, 0, 0)
+constexpr int kSymPlanes = 126;  // stored FP32 planes: diagonal + 13 forward blocks
 
 // Local node a of a hex8 element sits at offset (ldx(a), ldy(a), ldz(a)) from the
 // element's lowest corner; local DOF 3a + c.
@@ -40,6 +41,9 @@ __host__ __device__ constexpr int slot_of(int dx, int dy, int dz) { return (dx +
 // private to each launch, so handles with different nu never collide).
 struct KeF { float v[576]; };
 struct KeD { double v[576]; };
+// K_e in the Walsh-Hadamard mode basis: eight 3x3 parity-class blocks (fine.cu).
+struct GHat { float g[72]; };
+struct GHat64 { double g[72]; };
 
 // Scalar slots of the per-handle FP64 scalar array.
 enum Scalar {
@@ -68,7 +72,7 @@ struct Level {
     uint8_t* mask = nullptr;        // [nn] fixed-component bits
     float* invdiag = nullptr;       // [3nn] D^{-1} (levels >= 1), 0 on fixed DOFs
     double* A64 = nullptr;          // [243 nn] Galerkin operator planes, FP64 (levels >= 1)
-    float* A32 = nullptr;           // [243 nn] same in FP32 (levels >= 1)
+    float* A32 = nullptr;           // [126 nn] FP32 diagonal + forward blocks (levels >= 1)
     float* x = nullptr;             // [3nn] smoother iterate / V-cycle output (levels >= 1)
     float* x2 = nullptr;            // [3nn] ping-pong partner of x
     float* b = nullptr;             // [3nn] right-hand side (levels >= 1)
@@ -93,6 +97,8 @@ struct gmg_handle {
     double* E64 = nullptr;                      // fine moduli, FP64
     gmg::KeF keF{};
     gmg::KeD keD{};
+    gmg::GHat gh{};
+    gmg::GHat64 gh64{};
     float kd = 0.f;                             // diagonal entry of K_e (all equal)
     double* lam = nullptr;                      // [kMaxLevels] lambda estimates (device)
     // fine-level PCG vectors
@@ -129,14 +135,19 @@ struct FineArgs {
     int step;
     double* partial;       // per-block partial dots (nullptr = none)
     float kd;
+    float* scratch;        // fine-level vector used to mask a caller's operand (apply only)
 };
 
 int fine_grid_blocks(int nx, int ny, int nz);
-void launch_fine(int mode, int dot, const FineArgs& a, const KeF& ke, cudaStream_t s);
+// mask_in: treat fixed DOFs of the operand as 0 (for operands that may hold
+// values there, e.g. user input); internal vectors are already 0 on them.
+void launch_fine(int mode, int dot, int mask_in, const FineArgs& a, const GHat& G, cudaStream_t s);
+void launch_hadamard_blocks(const double* Ke, double* g72, cudaStream_t s);
+int resid64_grid_blocks(int nx, int ny, int nz);
 void launch_fine_smooth0(const FineArgs& a, cudaStream_t s);
 void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,
                          const double* f, const double* u, double* r64, float* r32,
-                         const double* sc, double* partial, const KeD& ke, cudaStream_t s);
+                         const double* sc, double* partial, const GHat64& G, cudaStream_t s);
 
 struct BsrArgs {
     int nx, ny, nz;

@@ -1,0 +1,245 @@
+// FP64 true residual of the fine level, r = f - K u, with ||r_free||^2 per block
+// (Sec. "Outer Krylov Solver and Convergence Statement": solves are accepted
+// only by the true residual, computed here in FP64 from the FP64 moduli and the
+// FP64 iterate).
+//
+// Same factorisation and schedule as the FP32 fine operator (fine.cu): K_e =
+// H^T G H with G in eight 3x3 parity-class blocks, one thread per element column
+// marching along z, face difference sums shared between layers, and the node
+// sums formed by warp shuffles and a shared-memory exchange.  FP64 arithmetic
+// runs at a small fraction of FP32 throughput on this part, so the ~200 FP64
+// operations per element of this form (instead of ~600 for the dense element
+// matrix) set the cost; a one-plane register prefetch is enough to cover memory
+// latency behind that arithmetic.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace gmg {
+
+namespace {
+
+constexpr int BX = 16, BY = 16, NT = BX * BY;
+
+__host__ __device__ constexpr int mono(int sigma, int c) {
+    return ((sigma & 1) ^ (c == 0 ? 1 : 0)) | ((((sigma >> 1) & 1) ^ (c == 1 ? 1 : 0)) << 1) |
+           ((((sigma >> 2) & 1) ^ (c == 2 ? 1 : 0)) << 2);
+}
+
+__device__ __forceinline__ bool fixed_bit(uint8_t m, int c) { return (m >> c) & 1; }
+
+__device__ __forceinline__ void face_diffs(double u00, double u10, double u01, double u11, double q[4]) {
+    const double dx0 = u10 - u00, dx1 = u11 - u01;
+    q[1] = dx0 + dx1;
+    q[2] = (u01 - u00) + (u11 - u10);
+    q[3] = dx1 - dx0;
+}
+
+__global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,
+                                                   const double* f, const double* uvec, double* r64, float* r32,
+                                                   const double* sc, double* partial, GHat64 G, int zchunk) {
+    __shared__ double sp[2][BY + 1][(BX + 1) * 3];
+    __shared__ double sx[2][BY][BX * 3];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    const int NX = nx + 1, NY = ny + 1, NZ = nz + 1, NXY = NX * NY, NEXY = nx * ny;
+    const int x0 = blockIdx.x * (BX - 1), y0 = blockIdx.y * (BY - 1);
+    const int k0 = blockIdx.z * zchunk, k1 = min(k0 + zchunk, NZ);
+    const int cx = x0 - 1 + tx, cy = y0 - 1 + ty, ox = cx + 1, oy = cy + 1;
+    const bool owner = tx < BX - 1 && ty < BY - 1 && ox < NX && oy < NY;
+    const bool cell_in = cx >= 0 && cx < nx && cy >= 0 && cy < ny;
+    const bool own_xy = cx >= 0 && cx < NX && cy >= 0 && cy < NY;
+    const int own_base = cy * NX + cx, onode_base = oy * NX + ox, e_base = cy * nx + cx;
+    const bool uzero = sc[SC_UNZ] == 0.0;  // u is identically zero: r = f
+
+    int hx = 0, hy = 0;
+    const bool halo = tid <= BX + BY;
+    if (tid <= BX) { hx = tid; hy = BY; }
+    else if (halo) { hx = BX; hy = tid - BX - 1; }
+    const int hpx = x0 - 1 + hx, hpy = y0 - 1 + hy;
+    const bool halo_xy = halo && hpx >= 0 && hpx < NX && hpy >= 0 && hpy < NY;
+    const int halo_base = hpy * NX + hpx;
+
+    double pv[3], ph[3];
+    uint8_t pm = 7, phm = 7;
+    auto prefetch = [&](int pz) {
+        const bool zok = !uzero && pz >= 0 && pz < NZ;
+        pv[0] = pv[1] = pv[2] = ph[0] = ph[1] = ph[2] = 0.0;
+        pm = phm = 7;
+        if (zok && own_xy) {
+            const int n = own_base + pz * NXY;
+            pv[0] = uvec[3 * n]; pv[1] = uvec[3 * n + 1]; pv[2] = uvec[3 * n + 2];
+            pm = mask[n];
+        }
+        if (zok && halo_xy) {
+            const int n = halo_base + pz * NXY;
+            ph[0] = uvec[3 * n]; ph[1] = uvec[3 * n + 1]; ph[2] = uvec[3 * n + 2];
+            phm = mask[n];
+        }
+    };
+    auto store_plane = [&](int buf) {
+        double* d = &sp[buf][ty][3 * tx];
+        d[0] = (pm & 1) ? 0.0 : pv[0];
+        d[1] = (pm & 2) ? 0.0 : pv[1];
+        d[2] = (pm & 4) ? 0.0 : pv[2];
+        if (halo) {
+            double* e = &sp[buf][hy][3 * hx];
+            e[0] = (phm & 1) ? 0.0 : ph[0];
+            e[1] = (phm & 2) ? 0.0 : ph[1];
+            e[2] = (phm & 4) ? 0.0 : ph[2];
+        }
+    };
+
+    prefetch(k0 - 1);
+    store_plane((k0 - 1) & 1);
+    prefetch(k0);
+    __syncthreads();
+    double Qb[4][3] = {}, Cb[4][3] = {}, Tprev[4][3] = {};
+    {
+        const int b = (k0 - 1) & 1;
+        for (int c = 0; c < 3; ++c) {
+            Cb[0][c] = sp[b][ty][3 * tx + c];
+            Cb[1][c] = sp[b][ty][3 * (tx + 1) + c];
+            Cb[2][c] = sp[b][ty + 1][3 * tx + c];
+            Cb[3][c] = sp[b][ty + 1][3 * (tx + 1) + c];
+            double q[4];
+            face_diffs(Cb[0][c], Cb[1][c], Cb[2][c], Cb[3][c], q);
+            for (int i = 1; i < 4; ++i) Qb[i][c] = q[i];
+        }
+    }
+    double Enext = (!uzero && cell_in && k0 - 1 >= 0 && k0 - 1 < nz) ? E[e_base + (k0 - 1) * NEXY] : 0.0;
+    bool pending = false;
+    int pend_k = 0;
+    double R1[3] = {0.0, 0.0, 0.0};
+    double rr = 0.0;
+
+    auto finish = [&]() {
+        const double* r0 = &sx[pend_k & 1][ty + 1][3 * tx];
+        const int n = onode_base + pend_k * NXY;
+        const uint8_t m = mask[n];
+        for (int c = 0; c < 3; ++c) {
+            const double v = fixed_bit(m, c) ? 0.0 : f[3 * n + c] - (R1[c] + r0[c]);
+            if (r64) r64[3 * n + c] = v;
+            if (r32) r32[3 * n + c] = (float)v;
+            rr += v * v;
+        }
+    };
+
+    for (int kl = k0 - 1; kl < k1; ++kl) {
+        const int pt = kl + 1;
+        store_plane(pt & 1);
+        __syncthreads();
+        if (pending && owner) finish();
+        pending = false;
+        const double Ee = Enext;
+        if (pt + 1 <= k1) prefetch(pt + 1);
+        Enext = (!uzero && cell_in && kl + 1 < nz && kl + 1 < k1) ? E[e_base + (kl + 1) * NEXY] : 0.0;
+        const int b = pt & 1;
+        double Qt[4][3], Ct[4][3];
+        for (int c = 0; c < 3; ++c) {
+            Ct[0][c] = sp[b][ty][3 * tx + c];
+            Ct[1][c] = sp[b][ty][3 * (tx + 1) + c];
+            Ct[2][c] = sp[b][ty + 1][3 * tx + c];
+            Ct[3][c] = sp[b][ty + 1][3 * (tx + 1) + c];
+            double q[4];
+            face_diffs(Ct[0][c], Ct[1][c], Ct[2][c], Ct[3][c], q);
+            Qt[0][c] = 0.0;
+            for (int i = 1; i < 4; ++i) Qt[i][c] = q[i];
+        }
+        double v[8][3];
+        for (int c = 0; c < 3; ++c) {
+            v[0][c] = 0.0;
+            v[4][c] = ((Ct[0][c] - Cb[0][c]) + (Ct[1][c] - Cb[1][c])) + ((Ct[2][c] - Cb[2][c]) + (Ct[3][c] - Cb[3][c]));
+            for (int q = 1; q < 4; ++q) {
+                v[q][c] = Qt[q][c] + Qb[q][c];
+                v[q + 4][c] = Qt[q][c] - Qb[q][c];
+            }
+        }
+        double w[8][3];
+        for (int c = 0; c < 3; ++c) w[0][c] = 0.0;
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const int mi = mono(s, i);
+                if (mi == 0) continue;
+                double acc = 0.0;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int mj = mono(s, j);
+                    if (mj == 0) continue;
+                    acc = fma(G.g[s * 9 + i * 3 + j], v[mj][j], acc);
+                }
+                w[mi][i] = Ee * acc;
+            }
+        double T[4][3], B[4][3];
+        for (int q = 0; q < 4; ++q)
+            for (int c = 0; c < 3; ++c) {
+                T[q][c] = w[q][c] + w[q + 4][c];
+                B[q][c] = w[q][c] - w[q + 4][c];
+            }
+        if (kl >= k0) {
+            double r0[3];
+            for (int c = 0; c < 3; ++c) {
+                const double S0 = Tprev[0][c] + B[0][c], S1 = Tprev[1][c] + B[1][c];
+                const double S2 = Tprev[2][c] + B[2][c], S3 = Tprev[3][c] + B[3][c];
+                const double p = S0 - S2, qd = S1 - S3, r = S0 + S2, sd = S1 + S3;
+                const double c00 = p - qd, c10 = p + qd, c01 = r - sd, c11 = r + sd;
+                R1[c] = c11 + __shfl_down_sync(0xffffffffu, c01, 1, BX);
+                r0[c] = c10 + __shfl_down_sync(0xffffffffu, c00, 1, BX);
+            }
+            double* dst = &sx[kl & 1][ty][3 * tx];
+            dst[0] = r0[0]; dst[1] = r0[1]; dst[2] = r0[2];
+            pending = true;
+            pend_k = kl;
+        }
+        for (int q = 0; q < 4; ++q)
+            for (int c = 0; c < 3; ++c) {
+                Tprev[q][c] = T[q][c];
+                Qb[q][c] = Qt[q][c];
+                Cb[q][c] = Ct[q][c];
+            }
+    }
+    __syncthreads();
+    if (pending && owner) finish();
+    // block sum of ||r||^2 in a fixed order
+    __shared__ double wsum[NT / 32];
+    for (int o = 16; o > 0; o >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, o);
+    if ((tid & 31) == 0) wsum[tid >> 5] = rr;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int w2 = 0; w2 < NT / 32; ++w2) s += wsum[w2];
+        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+    }
+}
+
+dim3 resid_grid(int nx, int ny, int nz, int* zc_out) {
+    const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
+    const int gx = (NX + BX - 2) / (BX - 1), gy = (NY + BY - 2) / (BY - 1);
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 148;
+    const int want = std::max(1, (2 * sms + gx * gy - 1) / (gx * gy));
+    int zc = std::max(4, (NZ + want - 1) / want);
+    zc = std::min(zc, NZ);
+    *zc_out = zc;
+    return dim3(gx, gy, (NZ + zc - 1) / zc);
+}
+
+}  // namespace
+
+int resid64_grid_blocks(int nx, int ny, int nz) {
+    int zc = 0;
+    const dim3 g = resid_grid(nx, ny, nz, &zc);
+    return (int)(g.x * g.y * g.z);
+}
+
+void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask, const double* f, const double* u,
+                         double* r64, float* r32, const double* sc, double* partial, const GHat64& G, cudaStream_t s) {
+    int zc = 0;
+    const dim3 g = resid_grid(nx, ny, nz, &zc);
+    note_launch();
+    k_resid64<<<g, dim3(BX, BY), 0, s>>>(nx, ny, nz, E, mask, f, u, r64, r32, sc, partial, G, zc);
+}
+
+}  // namespace gmg

@@ -281,8 +281,9 @@ __global__ void k_galerkin_rap(int fnx, int fny, int fnz, long long fnn, const d
     }
 }
 
-// Zero rows/columns of fixed DOFs and out-of-grid neighbours, convert to FP32,
-// and form D^{-1} from the self block.
+// Zero rows/columns of fixed DOFs and out-of-grid neighbours, form D^{-1} from
+// the self block, and write the FP32 copy used by the solve: the diagonal block
+// and the 13 forward neighbour blocks (slots 13..26) of the symmetric operator.
 __global__ void k_finish_bsr(int nx, int ny, int nz, long long nn, const uint8_t* mask, double* A64, float* A32,
                              float* invdiag) {
     const long long NX = nx + 1, NY = ny + 1, NZ = nz + 1;
@@ -299,7 +300,7 @@ __global__ void k_finish_bsr(int nx, int ny, int nz, long long nn, const uint8_t
                     double v = A64[q];
                     if (!in || fixed_bit(mr, r) || fixed_bit(mc, c)) v = 0.0;
                     A64[q] = v;
-                    A32[q] = (float)v;
+                    if (s >= kSelfSlot) A32[(long long)((s - kSelfSlot) * 9 + r * 3 + c) * nn + n] = (float)v;
                 }
         }
         for (int r = 0; r < 3; ++r) {
