@@ -157,7 +157,7 @@ def _peaks() -> tuple[float, str]:
 def _profile_traffic(kernel_src: str) -> float | None:
     """DRAM bytes per launch of the fine operator from the committed ncu summary,
     if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "fine_apply_c2_ncu.md")
+    path = os.path.join(ROOT, "profiles", "fine_smooth_c2_ncu.md")
     try:
         text = open(path).read()
     except OSError:
@@ -282,29 +282,48 @@ def main():
         e2e_ms.append(a.elapsed_time(b))
     e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
 
-    # ---- roofline of the fine operator (the kernel applied ~7x per PCG iteration)
+    # ---- roofline of the dominant kernel: the fused fine-level smoother step
+    # (k_fine in SMOOTH mode, ~6 of the ~7 fine-operator launches per PCG
+    # iteration), timed as whole smoothing passes of `degree` launches from a
+    # nonzero iterate, L2 flushed before each pass
     x = torch.from_numpy(inputs.random_free_vector(cfg.fixed(), seed=1)).to(dev)
-    y = torch.empty_like(x)
+    y = torch.from_numpy(inputs.random_free_vector(cfg.fixed(), seed=2)).to(dev)
     for _ in range(3):
-        S.apply(x, y)
-    reps = 30
-    ap_ms = []
+        S.level_smooth(0, x, y)
+    reps = 20
+    ev_s = []
     for k in range(reps):
+        flush_l2(k)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S.level_smooth(0, x, y)
+        b.record(stream)
+        ev_s.append((a, b))
+    torch.cuda.synchronize()
+    deg = cfg.degree
+    pass_ms = statistics.median(a.elapsed_time(b) for a, b in ev_s)
+    launch_ms = pass_ms / deg
+    # algorithmic bytes of one pass: every step reads x, b and E and writes x;
+    # all but the first read the previous increment, all but the last write one
+    alg_pass = deg * (12 * nn + 12 * nn + 4 * ne + 12 * nn) + 2 * (deg - 1) * 12 * nn
+    alg_bytes = alg_pass / deg
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": _profile_traffic(os.path.join(ROOT, "paper_2604_26441_b300", "csrc", "fine.cu")),
+                "kernel": "k_fine<SMOOTH> (fused fine operator + Chebyshev step)",
+                "alg_bytes_per_launch": alg_bytes, "launch_ms": launch_ms, "peak_source": peak_kind}
+    # the plain operator y = K u as well (includes the caller-input masking pass)
+    ap = []
+    for k in range(10):
         flush_l2(k)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         S.apply(x, y)
         b.record(stream)
-        ap_ms.append((a, b))
+        ap.append((a, b))
     torch.cuda.synchronize()
-    apply_ms = statistics.mean(a.elapsed_time(b) for a, b in ap_ms)
-    alg_bytes = 12 * nn + 12 * nn + 4 * ne  # read u, write y, read E
-    peak, peak_kind = _peaks()
-    achieved = alg_bytes / (apply_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": _profile_traffic(os.path.join(ROOT, "paper_2604_26441_b300", "csrc", "hot.cu")),
-                "kernel": "k_fine<APPLY> (matrix-free fine operator y = K u)",
-                "alg_bytes_per_launch": alg_bytes, "launch_ms": apply_ms, "peak_source": peak_kind}
+    apply_ms = statistics.median(a.elapsed_time(b) for a, b in ap)
 
     if rank != 0:
         return
@@ -318,6 +337,8 @@ def main():
         "iterations": infos[-1]["iterations"], "rel_residual": infos[-1]["rel_residual"],
         "all_converged": ok, "setup_ms": setup_s * 1000.0,
         "roofline": roofline,
+        "fine_apply": {"ms": apply_ms, "gdof_per_s": 3 * nn / (apply_ms * 1e-3) / 1e9,
+                       "alg_gbs": (24 * nn + 4 * ne) / (apply_ms * 1e-3) / 1e9},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * 3 * nn, "d2h_bytes_per_step": 8 * 3 * nn},
         "clocks": clk,
         "gpu_launches": launches,

@@ -22,7 +22,7 @@ namespace gmg {
 namespace {
 
 constexpr int kVecThreads = 256;
-constexpr int kVecBlocks = 148 * 4;
+constexpr int kVecBlocks = 148 * 8;
 
 // Sum of v over the block (blockDim.x*y*z == nthreads, multiple of 32); the
 // result is valid in thread 0.  Fixed combination order.
@@ -79,37 +79,41 @@ __global__ void k_fine_smooth0(FineArgs a) {
 // and the transposed reads at n - o_u re-touch planes read a few blocks earlier
 // (mostly L2 hits), so each stored value crosses HBM about once.
 // ---------------------------------------------------------------------------
-template <int MODE, bool DOT>
-__global__ void __launch_bounds__(kVecThreads) k_bsr(BsrArgs a) {
-    const int n = blockIdx.x * kVecThreads + threadIdx.x;
+template <int MODE, bool DOT, int NTB>
+__global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
     const int nn = (int)a.nn;
+    const int n = blockIdx.x * NTB + threadIdx.x;
     double dotv = 0.0;
     if (n < nn) {
         const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
         const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
+        const long long N = nn;
         float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+        // branch-free: every load is unconditional (indices clamped to this node
+        // when the neighbour is outside the grid), so all of them can be in
+        // flight together; out-of-grid forward blocks are stored as zero, and
+        // out-of-grid backward terms are scaled by 0
 #pragma unroll
         for (int u = 0; u < 14; ++u) {
-            const int s = 13 + u;
-            const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+            const int sl = 13 + u;
+            const int dx = sl % 3 - 1, dy = (sl / 3) % 3 - 1, dz = sl / 9 - 1;
             const int off = dx + NX * (dy + NY * dz);
-            // forward block (n, n + o)
-            if (i + dx >= 0 && i + dx < NX && j + dy >= 0 && j + dy < NY && k + dz < NZ) {
-                const int m = n + off;
-                const float v0 = a.xin[3 * m], v1 = a.xin[3 * m + 1], v2 = a.xin[3 * m + 2];
-                const float* A = a.A + (long long)(u * 9) * nn + n;
-                y0 = fmaf(A[0 * (long long)nn], v0, fmaf(A[1 * (long long)nn], v1, fmaf(A[2 * (long long)nn], v2, y0)));
-                y1 = fmaf(A[3 * (long long)nn], v0, fmaf(A[4 * (long long)nn], v1, fmaf(A[5 * (long long)nn], v2, y1)));
-                y2 = fmaf(A[6 * (long long)nn], v0, fmaf(A[7 * (long long)nn], v1, fmaf(A[8 * (long long)nn], v2, y2)));
-            }
-            // backward block (n, n - o) = block (n - o, n)^T
-            if (u > 0 && i - dx >= 0 && i - dx < NX && j - dy >= 0 && j - dy < NY && k - dz >= 0) {
-                const int m = n - off;
-                const float v0 = a.xin[3 * m], v1 = a.xin[3 * m + 1], v2 = a.xin[3 * m + 2];
-                const float* A = a.A + (long long)(u * 9) * nn + m;
-                y0 = fmaf(A[0 * (long long)nn], v0, fmaf(A[3 * (long long)nn], v1, fmaf(A[6 * (long long)nn], v2, y0)));
-                y1 = fmaf(A[1 * (long long)nn], v0, fmaf(A[4 * (long long)nn], v1, fmaf(A[7 * (long long)nn], v2, y1)));
-                y2 = fmaf(A[2 * (long long)nn], v0, fmaf(A[5 * (long long)nn], v1, fmaf(A[8 * (long long)nn], v2, y2)));
+            const bool okf = i + dx >= 0 && i + dx < NX && j + dy >= 0 && j + dy < NY && k + dz < NZ;
+            const int mf = okf ? n + off : n;
+            const float* A = a.A + (long long)(u * 9) * N + n;
+            const float v0 = a.xin[3 * mf], v1 = a.xin[3 * mf + 1], v2 = a.xin[3 * mf + 2];
+            y0 = fmaf(A[0 * N], v0, fmaf(A[1 * N], v1, fmaf(A[2 * N], v2, y0)));
+            y1 = fmaf(A[3 * N], v0, fmaf(A[4 * N], v1, fmaf(A[5 * N], v2, y1)));
+            y2 = fmaf(A[6 * N], v0, fmaf(A[7 * N], v1, fmaf(A[8 * N], v2, y2)));
+            if (u > 0) {
+                const bool okb = i - dx >= 0 && i - dx < NX && j - dy >= 0 && j - dy < NY && k - dz >= 0;
+                const int mb = okb ? n - off : n;
+                const float wgt = okb ? 1.f : 0.f;
+                const float* B = a.A + (long long)(u * 9) * N + mb;
+                const float w0 = wgt * a.xin[3 * mb], w1 = wgt * a.xin[3 * mb + 1], w2 = wgt * a.xin[3 * mb + 2];
+                y0 = fmaf(B[0 * N], w0, fmaf(B[3 * N], w1, fmaf(B[6 * N], w2, y0)));
+                y1 = fmaf(B[1 * N], w0, fmaf(B[4 * N], w1, fmaf(B[7 * N], w2, y1)));
+                y2 = fmaf(B[2 * N], w0, fmaf(B[5 * N], w1, fmaf(B[8 * N], w2, y2)));
             }
         }
         const uint8_t msk = a.mask[n];
@@ -143,7 +147,87 @@ __global__ void __launch_bounds__(kVecThreads) k_bsr(BsrArgs a) {
         }
     }
     if (DOT) {
-        const double s = block_sum<kVecThreads>(dotv, threadIdx.x);
+        const double s = block_sum<NTB>(dotv, threadIdx.x);
+        if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+    }
+}
+
+// Small levels (latency-bound): one warp per node.  Lanes 0..13 take the
+// diagonal and forward blocks, lanes 14..26 the transposed backward blocks, so
+// each lane issues 12 independent loads; a shuffle reduction forms the row.
+template <int MODE, bool DOT>
+__global__ void __launch_bounds__(256) k_bsr_warp(BsrArgs a) {
+    const int nn = (int)a.nn;
+    const int lane = threadIdx.x & 31;
+    const int n = blockIdx.x * 8 + (threadIdx.x >> 5);
+    double dotv = 0.0;
+    if (n < nn) {
+        const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
+        const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
+        const long long N = nn;
+        float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+        if (lane < 27) {
+            const bool fwd = lane < 14;
+            const int u = fwd ? lane : lane - 13;
+            const int sl = 13 + u;
+            const int dx = sl % 3 - 1, dy = (sl / 3) % 3 - 1, dz = sl / 9 - 1;
+            const int off = dx + NX * (dy + NY * dz);
+            const int sx = fwd ? dx : -dx, sy = fwd ? dy : -dy, sz = fwd ? dz : -dz;
+            const bool ok = i + sx >= 0 && i + sx < NX && j + sy >= 0 && j + sy < NY && k + sz >= 0 && k + sz < NZ;
+            const int m = ok ? (fwd ? n + off : n - off) : n;
+            const float wgt = ok ? 1.f : 0.f;
+            const float v0 = wgt * a.xin[3 * m], v1 = wgt * a.xin[3 * m + 1], v2 = wgt * a.xin[3 * m + 2];
+            const float* A = a.A + (long long)(u * 9) * N + (fwd ? n : m);
+            if (fwd) {
+                y0 = fmaf(A[0 * N], v0, fmaf(A[1 * N], v1, A[2 * N] * v2));
+                y1 = fmaf(A[3 * N], v0, fmaf(A[4 * N], v1, A[5 * N] * v2));
+                y2 = fmaf(A[6 * N], v0, fmaf(A[7 * N], v1, A[8 * N] * v2));
+            } else {
+                y0 = fmaf(A[0 * N], v0, fmaf(A[3 * N], v1, A[6 * N] * v2));
+                y1 = fmaf(A[1 * N], v0, fmaf(A[4 * N], v1, A[7 * N] * v2));
+                y2 = fmaf(A[2 * N], v0, fmaf(A[5 * N], v1, A[8 * N] * v2));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+            y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+        }
+        if (lane == 0) {
+            const uint8_t msk = a.mask[n];
+            const float y[3] = {y0, y1, y2};
+            if (MODE == FM_APPLY) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float v = fixed_bit(msk, c) ? 0.f : y[c];
+                    a.out[3 * n + c] = v;
+                    if (DOT) dotv += (double)a.xin[3 * n + c] * (double)v;
+                }
+            } else if (MODE == FM_RESID) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    a.out[3 * n + c] = fixed_bit(msk, c) ? 0.f : a.b[3 * n + c] - y[c];
+            } else {
+                const float cd = (float)a.coef[2 * a.step], ca = (float)a.coef[2 * a.step + 1];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float xn = 0.f, dn = 0.f;
+                    if (!fixed_bit(msk, c)) {
+                        const float bc = a.b[3 * n + c];
+                        dn = ca * a.invdiag[3 * n + c] * (bc - y[c]);
+                        if (cd != 0.f) dn = fmaf(cd, a.dold[3 * n + c], dn);
+                        xn = a.xin[3 * n + c] + dn;
+                        if (DOT) dotv += (double)bc * (double)xn;
+                    }
+                    a.out[3 * n + c] = xn;
+                    if (a.dnew) a.dnew[3 * n + c] = dn;
+                }
+            }
+        }
+    }
+    if (DOT) {
+        const double s = block_sum<256>(dotv, threadIdx.x);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
     }
 }
@@ -164,90 +248,109 @@ __global__ void k_bsr_smooth0(BsrArgs a) {
 // node 2I with weight 1 and 2I-1, 2I+1 with weight 1/2; when the fine count is
 // odd, the last fine node 2*nc+1 hangs on coarse node nc with weight 1.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int fine_support(int I, int nf, int* idx, float* w) {
-    const int nc = nf >> 1;
-    int n = 0;
-    idx[n] = 2 * I; w[n++] = 1.f;
-    if (I >= 1) { idx[n] = 2 * I - 1; w[n++] = 0.5f; }
-    const int f = 2 * I + 1;
-    if (f <= nf) { idx[n] = f; w[n++] = (f < 2 * nc) ? 0.5f : 1.f; }
-    return n;
+// Branch-free 1D stencils: every candidate entry is present, with weight 0 and
+// a clamped index when it does not exist, so all loads of a node are
+// independent and issue together.
+__device__ __forceinline__ void fine_support3(int I, int nf, int idx[3], float w[3]) {
+    const int nc = nf >> 1, f = 2 * I + 1;
+    idx[0] = I >= 1 ? 2 * I - 1 : 2 * I; w[0] = I >= 1 ? 0.5f : 0.f;
+    idx[1] = 2 * I; w[1] = 1.f;
+    idx[2] = f <= nf ? f : 2 * I; w[2] = f <= nf ? (f < 2 * nc ? 0.5f : 1.f) : 0.f;
 }
 
-__device__ __forceinline__ int coarse_parents(int f, int nf, int* idx, float* w) {
+__device__ __forceinline__ void coarse_parents2(int f, int nf, int idx[2], float w[2]) {
     const int nc = nf >> 1;
-    if ((f & 1) == 0) { idx[0] = f >> 1; w[0] = 1.f; return 1; }
-    if (f < 2 * nc) { idx[0] = (f - 1) >> 1; w[0] = 0.5f; idx[1] = (f + 1) >> 1; w[1] = 0.5f; return 2; }
-    idx[0] = nc; w[0] = 1.f; return 1;
+    if ((f & 1) == 0) { idx[0] = idx[1] = f >> 1; w[0] = 1.f; w[1] = 0.f; }
+    else if (f < 2 * nc) { idx[0] = (f - 1) >> 1; idx[1] = (f + 1) >> 1; w[0] = w[1] = 0.5f; }
+    else { idx[0] = idx[1] = nc; w[0] = 1.f; w[1] = 0.f; }
 }
 
 __global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz, const uint8_t* cmask,
                            const float* fine, float* coarse) {
-    const long long CX = cnx + 1, CY = cny + 1, CZ = cnz + 1, nn = CX * CY * CZ;
-    const long long FX = fnx + 1, FY = fny + 1;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int I = (int)(n % CX), J = (int)((n / CX) % CY), K = (int)(n / (CX * CY));
-        int ix[3], iy[3], iz[3];
-        float wx[3], wy[3], wz[3];
-        const int sx = fine_support(I, fnx, ix, wx), sy = fine_support(J, fny, iy, wy),
-                  sz = fine_support(K, fnz, iz, wz);
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int c = 0; c < sz; ++c)
-            for (int b = 0; b < sy; ++b)
-                for (int a = 0; a < sx; ++a) {
-                    const float w = wx[a] * wy[b] * wz[c];
-                    const long long f = ix[a] + FX * (iy[b] + FY * iz[c]);
-                    s0 = fmaf(w, fine[3 * f], s0);
-                    s1 = fmaf(w, fine[3 * f + 1], s1);
-                    s2 = fmaf(w, fine[3 * f + 2], s2);
-                }
-        const uint8_t m = cmask[n];
-        coarse[3 * n] = fixed_bit(m, 0) ? 0.f : s0;
-        coarse[3 * n + 1] = fixed_bit(m, 1) ? 0.f : s1;
-        coarse[3 * n + 2] = fixed_bit(m, 2) ? 0.f : s2;
-    }
+    const int CX = cnx + 1, CY = cny + 1, nn = CX * CY * (cnz + 1);
+    const int FX = fnx + 1, FY = fny + 1;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    const int I = n % CX, J = (n / CX) % CY, K = n / (CX * CY);
+    int ix[3], iy[3], iz[3];
+    float wx[3], wy[3], wz[3];
+    fine_support3(I, fnx, ix, wx);
+    fine_support3(J, fny, iy, wy);
+    fine_support3(K, fnz, iz, wz);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float w = wx[a] * wy[b] * wz[c];
+                const int f = ix[a] + FX * (iy[b] + FY * iz[c]);
+                s0 = fmaf(w, fine[3 * f], s0);
+                s1 = fmaf(w, fine[3 * f + 1], s1);
+                s2 = fmaf(w, fine[3 * f + 2], s2);
+            }
+    const uint8_t m = cmask[n];
+    coarse[3 * n] = fixed_bit(m, 0) ? 0.f : s0;
+    coarse[3 * n + 1] = fixed_bit(m, 1) ? 0.f : s1;
+    coarse[3 * n + 2] = fixed_bit(m, 2) ? 0.f : s2;
 }
 
 __global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, const uint8_t* fmask,
                               const float* coarse, float* fine) {
-    const long long FX = fnx + 1, FY = fny + 1, FZ = fnz + 1, nn = FX * FY * FZ;
-    const long long CX = cnx + 1, CY = cny + 1;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(n % FX), j = (int)((n / FX) % FY), k = (int)(n / (FX * FY));
-        int ix[2], iy[2], iz[2];
-        float wx[2], wy[2], wz[2];
-        const int sx = coarse_parents(i, fnx, ix, wx), sy = coarse_parents(j, fny, iy, wy),
-                  sz = coarse_parents(k, fnz, iz, wz);
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int c = 0; c < sz; ++c)
-            for (int b = 0; b < sy; ++b)
-                for (int a = 0; a < sx; ++a) {
-                    const float w = wx[a] * wy[b] * wz[c];
-                    const long long m = ix[a] + CX * (iy[b] + CY * iz[c]);
-                    s0 = fmaf(w, coarse[3 * m], s0);
-                    s1 = fmaf(w, coarse[3 * m + 1], s1);
-                    s2 = fmaf(w, coarse[3 * m + 2], s2);
-                }
-        const uint8_t msk = fmask[n];
-        if (!fixed_bit(msk, 0)) fine[3 * n] += s0;
-        if (!fixed_bit(msk, 1)) fine[3 * n + 1] += s1;
-        if (!fixed_bit(msk, 2)) fine[3 * n + 2] += s2;
-    }
+    const int FX = fnx + 1, FY = fny + 1, nn = FX * FY * (fnz + 1);
+    const int CX = cnx + 1, CY = cny + 1;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    const int i = n % FX, j = (n / FX) % FY, k = n / (FX * FY);
+    int ix[2], iy[2], iz[2];
+    float wx[2], wy[2], wz[2];
+    coarse_parents2(i, fnx, ix, wx);
+    coarse_parents2(j, fny, iy, wy);
+    coarse_parents2(k, fnz, iz, wz);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const float w = wx[a] * wy[b] * wz[c];
+                const int m = ix[a] + CX * (iy[b] + CY * iz[c]);
+                s0 = fmaf(w, coarse[3 * m], s0);
+                s1 = fmaf(w, coarse[3 * m + 1], s1);
+                s2 = fmaf(w, coarse[3 * m + 2], s2);
+            }
+    const uint8_t msk = fmask[n];
+    if (!fixed_bit(msk, 0)) fine[3 * n] += s0;
+    if (!fixed_bit(msk, 1)) fine[3 * n + 1] += s1;
+    if (!fixed_bit(msk, 2)) fine[3 * n + 2] += s2;
 }
 
-// x[free_idx[i]] = sum_j Ainv[i][j] b[free_idx[j]]  (FP64 accumulation, one warp per row)
-__global__ void k_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b, float* x) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= nL) return;
-    const double* row = Ainv + (long long)warp * nL;
-    double s = 0.0;
-    for (int jx = lane; jx < nL; jx += 32) s = fma(row[jx], (double)b[free_idx[jx]], s);
+// x[free_idx[i]] = sum_j Ainv[i][j] b[free_idx[j]]  (FP64 accumulation): the
+// gathered right-hand side is staged in shared memory once per block, then each
+// warp reduces a few rows of the inverse.
+constexpr int kCoarseRowsPerBlock = 8;
+__global__ void __launch_bounds__(256) k_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b,
+                                                      float* x) {
+    extern __shared__ double bs[];
+    for (int j = threadIdx.x; j < nL; j += blockDim.x) bs[j] = (double)b[free_idx[j]];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * kCoarseRowsPerBlock + warp;
+    if (row >= nL) return;
+    const double* rp = Ainv + (long long)row * nL;
+    double s0 = 0.0, s1 = 0.0;
+    int jx = lane;
+    for (; jx + 32 < nL; jx += 64) {
+        s0 = fma(rp[jx], bs[jx], s0);
+        s1 = fma(rp[jx + 32], bs[jx + 32], s1);
+    }
+    if (jx < nL) s0 = fma(rp[jx], bs[jx], s0);
+    double s = s0 + s1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) x[free_idx[warp]] = (float)s;
+    if (lane == 0) x[free_idx[row]] = (float)s;
 }
 
 // ---------------------------------------------------------------------------
@@ -399,19 +502,38 @@ void launch_fine_smooth0(const FineArgs& a, cudaStream_t s) {
     k_fine_smooth0<<<kVecBlocks * 2, kVecThreads, 0, s>>>(a);
 }
 
-int bsr_grid_blocks(long long nn) { return (int)((nn + kVecThreads - 1) / kVecThreads); }
+// Levels below ~32k nodes are latency-bound: one warp per node there; larger
+// levels stream the operator with one thread per node.
+constexpr long long kBsrWarpLevel = 32768;
+
+int bsr_grid_blocks(long long nn) {
+    if (nn < kBsrWarpLevel) return (int)((nn + 7) / 8);
+    return (int)((nn + 255) / 256);
+}
 
 void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
     const int g = bsr_grid_blocks(a.nn);
+    note_launch();
+    if (a.nn < kBsrWarpLevel) {
+        if (mode == FM_APPLY) {
+            if (dot) k_bsr_warp<FM_APPLY, true><<<g, 256, 0, s>>>(a);
+            else k_bsr_warp<FM_APPLY, false><<<g, 256, 0, s>>>(a);
+        } else if (mode == FM_SMOOTH) {
+            if (dot) k_bsr_warp<FM_SMOOTH, true><<<g, 256, 0, s>>>(a);
+            else k_bsr_warp<FM_SMOOTH, false><<<g, 256, 0, s>>>(a);
+        } else {
+            k_bsr_warp<FM_RESID, false><<<g, 256, 0, s>>>(a);
+        }
+        return;
+    }
     if (mode == FM_APPLY) {
-        if (dot) { note_launch(); k_bsr<FM_APPLY, true><<<g, kVecThreads, 0, s>>>(a); }
-        else { note_launch(); k_bsr<FM_APPLY, false><<<g, kVecThreads, 0, s>>>(a); }
+        if (dot) k_bsr<FM_APPLY, true, 256><<<g, 256, 0, s>>>(a);
+        else k_bsr<FM_APPLY, false, 256><<<g, 256, 0, s>>>(a);
     } else if (mode == FM_SMOOTH) {
-        if (dot) { note_launch(); k_bsr<FM_SMOOTH, true><<<g, kVecThreads, 0, s>>>(a); }
-        else { note_launch(); k_bsr<FM_SMOOTH, false><<<g, kVecThreads, 0, s>>>(a); }
+        if (dot) k_bsr<FM_SMOOTH, true, 256><<<g, 256, 0, s>>>(a);
+        else k_bsr<FM_SMOOTH, false, 256><<<g, 256, 0, s>>>(a);
     } else {
-        note_launch();
-        k_bsr<FM_RESID, false><<<g, kVecThreads, 0, s>>>(a);
+        k_bsr<FM_RESID, false, 256><<<g, 256, 0, s>>>(a);
     }
 }
 
@@ -428,18 +550,22 @@ static int grid_for(long long n) {
 
 void launch_restrict(const Level& f, const Level& c, const float* fine, float* coarse, cudaStream_t s) {
     note_launch();
-    k_restrict<<<grid_for(c.nn), 256, 0, s>>>(f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, c.mask, fine, coarse);
+    k_restrict<<<(int)((c.nn + 127) / 128), 128, 0, s>>>(f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, c.mask, fine, coarse);
 }
 
 void launch_prolong_add(const Level& f, const Level& c, const float* coarse, float* fine, cudaStream_t s) {
     note_launch();
-    k_prolong_add<<<grid_for(f.nn), 256, 0, s>>>(f.nx, f.ny, f.nz, c.nx, c.ny, f.mask, coarse, fine);
+    k_prolong_add<<<(int)((f.nn + 255) / 256), 256, 0, s>>>(f.nx, f.ny, f.nz, c.nx, c.ny, f.mask, coarse, fine);
 }
 
 void launch_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b, float* x,
                          long long n_dof, cudaStream_t s) {
     cudaMemsetAsync(x, 0, sizeof(float) * n_dof, s);
-    if (nL > 0) { note_launch(); k_coarse_solve<<<(nL * 32 + 255) / 256, 256, 0, s>>>(nL, free_idx, Ainv, b, x); }
+    if (nL > 0) {
+        note_launch();
+        k_coarse_solve<<<(nL + kCoarseRowsPerBlock - 1) / kCoarseRowsPerBlock, 32 * kCoarseRowsPerBlock,
+                         sizeof(double) * nL, s>>>(nL, free_idx, Ainv, b, x);
+    }
 }
 
 int vec_grid_blocks() { return kVecBlocks; }
