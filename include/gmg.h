@@ -85,6 +85,8 @@ typedef struct {
     int power_iters_fine;        /* power iterations for lambda_max(D^-1 K), fine (20) */
     int power_iters_coarse;      /* ... on assembled levels (10) */
     int chol_cutoff;             /* dense-Cholesky size limit for the coarsest level (5000) */
+    int fused_coarse_nodes;      /* assembled levels with fewer nodes than this run, together with
+                                    the coarsest solve, as one persistent kernel (4096); 0 = off */
     void* stream;                /* cudaStream_t for all device work; NULL = default stream */
 } gmg_options;
 

@@ -165,6 +165,12 @@ float* smooth_pass(gmg_handle* h, int li, const float* b, float* cur, float* X, 
 void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int dot_slot, int op) {
     Level& l = h->lev[li];
     cudaStream_t s = h->stream;
+    if (h->use_fused && li == h->cf.start) {
+        // levels li..L-1 and the coarsest solve in one persistent kernel; b and X
+        // are this level's own b and x buffers on this path
+        launch_coarse_fused(h->cf, h->fused_blocks, s);
+        return;
+    }
     if (li == h->L - 1) {
         launch_coarse_solve(h->nL, h->free_idx, h->Ainv, b, X, 3 * l.nn, s);
         return;
@@ -424,8 +430,49 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         dfree(h, dense);
         dfree(h, work);
     }
+    // ---- fused lower V-cycle: every assembled level below the node threshold
+    if (o.fused_coarse_nodes > 0 && L >= 2) {
+        int start = L - 1;
+        while (start - 1 >= 1 && h->lev[start - 1].nn < o.fused_coarse_nodes) --start;
+        if (h->lev[start].nn < o.fused_coarse_nodes || start == L - 1) {
+            CoarseFused& cf = h->cf;
+            cf.start = start;
+            cf.L = L;
+            cf.nL = h->nL;
+            cf.free_idx = h->free_idx;
+            cf.Ainv = h->Ainv;
+            for (int li = 1; li < L; ++li) {
+                const Level& l = h->lev[li];
+                CoarseLevel& c = cf.lev[li];
+                c.nx = l.nx; c.ny = l.ny; c.nz = l.nz; c.nn = (int)l.nn;
+                c.mask = l.mask; c.A = l.A32; c.invdiag = l.invdiag;
+                c.x = l.x; c.x2 = l.x2; c.b = l.b; c.t = l.t; c.d = l.d;
+                c.coef = l.coef; c.kind = l.kind; c.degree = l.degree;
+            }
+            unsigned* words = nullptr;
+            TRY(dalloc(h, &words, 4));
+            CU(cudaMemsetAsync(words, 0, 4 * sizeof(unsigned), s));
+            cf.bar_count = words;
+            cf.bar_gen = words + 1;
+            cf.err = reinterpret_cast<int*>(words + 2);
+            cf.spin_limit = 1LL << 24;
+            if (coarse_fused_blocks(&h->fused_blocks, sizeof(double) * (size_t)std::max(h->nL, 1)) == GMG_OK &&
+                h->fused_blocks > 0)
+                h->use_fused = true;
+        }
+    }
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(s));
+    return GMG_OK;
+}
+
+// Reports a timed-out wait of the fused lower V-cycle (its error word is sticky).
+int check_fused(gmg_handle* h) {
+    if (!h->use_fused) return GMG_OK;
+    int err = 0;
+    CU(cudaMemcpyAsync(&err, h->cf.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (err) return fail(GMG_ERR_CUDA, "the fused coarse-level V-cycle gave up waiting at a grid barrier");
     return GMG_OK;
 }
 
@@ -449,6 +496,7 @@ void gmg_default_options(gmg_options* o) {
     o->power_iters_fine = 20;
     o->power_iters_coarse = 10;
     o->chol_cutoff = 5000;
+    o->fused_coarse_nodes = 4096;
     o->stream = nullptr;
 }
 
@@ -546,6 +594,8 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     double* sch = h->sc_host;
     gmg_info inf{};
     auto finish = [&](int st) -> int {
+        const int fe = check_fused(h);
+        if (fe != GMG_OK) return fe;
         inf.status = st;
         inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (info) *info = inf;

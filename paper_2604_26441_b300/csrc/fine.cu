@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
     float R1[3] = {0.f, 0.f, 0.f}, eR1 = 0.f;
     float un_pend[3] = {0.f, 0.f, 0.f}, un_next[3] = {0.f, 0.f, 0.f};
     uint8_t m_pend = 7;
-    double dotv = 0.0;
+    DSAcc dotv;
 
     auto finish = [&]() {
         // complete the 4-cell sum with the row published by the thread above
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
             for (int c = 0; c < 3; ++c) {
                 const float v = fixed_bit(m_pend, c) ? 0.f : y[c];
                 out[c] = v;
-                if (DOT) dotv += (double)un_pend[c] * (double)v;
+                if (DOT) dotv.add_prod(un_pend[c], v);
             }
         } else if (MODE == FM_RESID) {
             const float* bb = &sB[pend_k & 3][3 * own_slot];
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
                     dn = ca * inv * (bb[c] - y[c]);
                     if (need_d) dn = fmaf(cd, dd[c], dn);
                     xn = un_pend[c] + dn;
-                    if (DOT) dotv += (double)bb[c] * (double)xn;
+                    if (DOT) dotv.add_prod(bb[c], xn);
                 }
                 out[c] = xn;
                 if (a.dnew) a.dnew[3 * n + c] = dn;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
     __syncthreads();
     if (pending && owner) finish();
     if (DOT) {
-        const double s = block_sum<NT>(dotv, tid);
+        const double s = block_sum<NT>(dotv.value(), tid);
         if (tid == 0) a.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
     }
 }

@@ -74,16 +74,17 @@ __global__ void k_fine_smooth0(FineArgs a) {
 // "forward" neighbour blocks (slots 13..26, offsets after the node in memory
 // order) are stored, plane-major: A[(u*9 + r*3 + c)*nn + n] is entry (r, c) of
 // block (n, n + o_u), u = slot - 13.  Row n of K^l is then
-//   sum_u A_u(n) x(n + o_u)  +  sum_{u>0} A_u(n - o_u)^T x(n - o_u),
-// one thread per node; every plane read is coalesced across consecutive nodes,
-// and the transposed reads at n - o_u re-touch planes read a few blocks earlier
-// (mostly L2 hits), so each stored value crosses HBM about once.
+//   sum_u A_u(n) x(n + o_u)  +  sum_{u>0} A_u(n - o_u)^T x(n - o_u).
 // ---------------------------------------------------------------------------
+// Large levels (bandwidth-bound): one thread per node streaming the planes,
+// branch-free so that all of a node's loads can be in flight together
+// (out-of-grid forward blocks are stored as zero; out-of-grid backward terms are
+// scaled by 0).
 template <int MODE, bool DOT, int NTB>
 __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
     const int nn = (int)a.nn;
     const int n = blockIdx.x * NTB + threadIdx.x;
-    double dotv = 0.0;
+    DSAcc dotv;
     if (n < nn) {
         const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
         const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
             for (int c = 0; c < 3; ++c) {
                 const float v = fixed_bit(msk, c) ? 0.f : y[c];
                 a.out[3 * n + c] = v;
-                if (DOT) dotv += (double)a.xin[3 * n + c] * (double)v;
+                if (DOT) dotv.add_prod(a.xin[3 * n + c], v);
             }
         } else if (MODE == FM_RESID) {
 #pragma unroll
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
                     dn = ca * a.invdiag[3 * n + c] * (bc - y[c]);
                     if (cd != 0.f) dn = fmaf(cd, a.dold[3 * n + c], dn);
                     xn = a.xin[3 * n + c] + dn;
-                    if (DOT) dotv += (double)bc * (double)xn;
+                    if (DOT) dotv.add_prod(bc, xn);
                 }
                 a.out[3 * n + c] = xn;
                 if (a.dnew) a.dnew[3 * n + c] = dn;
@@ -147,88 +148,95 @@ __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
         }
     }
     if (DOT) {
-        const double s = block_sum<NTB>(dotv, threadIdx.x);
+        const double s = block_sum<NTB>(dotv.value(), threadIdx.x);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
     }
 }
 
-// Small levels (latency-bound): one warp per node.  Lanes 0..13 take the
-// diagonal and forward blocks, lanes 14..26 the transposed backward blocks, so
-// each lane issues 12 independent loads; a shuffle reduction forms the row.
+// Assembled levels, "K-split" form: a block of 256 threads takes 64 consecutive
+// nodes; its four slices of 64 threads each apply a quarter of every node's 27
+// blocks (diagonal, 13 forward, 13 transposed backward), so each thread issues
+// ~84 loads instead of ~324 and every plane read is coalesced across the 64
+// nodes.  The four partial rows are added in shared memory in a fixed order.
 template <int MODE, bool DOT>
-__global__ void __launch_bounds__(256) k_bsr_warp(BsrArgs a) {
+__global__ void __launch_bounds__(256) k_bsr_ks(BsrArgs a) {
+    constexpr int NPB = 64;
+    __shared__ float part[4][NPB][3];
     const int nn = (int)a.nn;
-    const int lane = threadIdx.x & 31;
-    const int n = blockIdx.x * 8 + (threadIdx.x >> 5);
-    double dotv = 0.0;
-    if (n < nn) {
-        const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
-        const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
-        const long long N = nn;
-        float y0 = 0.f, y1 = 0.f, y2 = 0.f;
-        if (lane < 27) {
-            const bool fwd = lane < 14;
-            const int u = fwd ? lane : lane - 13;
+    const int t = threadIdx.x & (NPB - 1), slice = threadIdx.x >> 6;
+    const int n = blockIdx.x * NPB + t;
+    const bool live = n < nn;
+    const int nsafe = live ? n : 0;
+    const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
+    const int i = nsafe % NX, j = (nsafe / NX) % NY, k = nsafe / (NX * NY);
+    const long long N = nn;
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const int blk = slice + 4 * q;  // 0..13 forward (u = blk), 14..26 backward (u = blk - 13)
+        if (blk < 27) {
+            const bool fwd = blk < 14;
+            const int u = fwd ? blk : blk - 13;
             const int sl = 13 + u;
             const int dx = sl % 3 - 1, dy = (sl / 3) % 3 - 1, dz = sl / 9 - 1;
             const int off = dx + NX * (dy + NY * dz);
             const int sx = fwd ? dx : -dx, sy = fwd ? dy : -dy, sz = fwd ? dz : -dz;
-            const bool ok = i + sx >= 0 && i + sx < NX && j + sy >= 0 && j + sy < NY && k + sz >= 0 && k + sz < NZ;
-            const int m = ok ? (fwd ? n + off : n - off) : n;
+            const bool ok = live && i + sx >= 0 && i + sx < NX && j + sy >= 0 && j + sy < NY && k + sz >= 0 && k + sz < NZ;
+            const int m = ok ? (fwd ? nsafe + off : nsafe - off) : nsafe;
             const float wgt = ok ? 1.f : 0.f;
             const float v0 = wgt * a.xin[3 * m], v1 = wgt * a.xin[3 * m + 1], v2 = wgt * a.xin[3 * m + 2];
-            const float* A = a.A + (long long)(u * 9) * N + (fwd ? n : m);
+            const float* A = a.A + (long long)(u * 9) * N + (fwd ? nsafe : m);
             if (fwd) {
-                y0 = fmaf(A[0 * N], v0, fmaf(A[1 * N], v1, A[2 * N] * v2));
-                y1 = fmaf(A[3 * N], v0, fmaf(A[4 * N], v1, A[5 * N] * v2));
-                y2 = fmaf(A[6 * N], v0, fmaf(A[7 * N], v1, A[8 * N] * v2));
+                y0 = fmaf(A[0 * N], v0, fmaf(A[1 * N], v1, fmaf(A[2 * N], v2, y0)));
+                y1 = fmaf(A[3 * N], v0, fmaf(A[4 * N], v1, fmaf(A[5 * N], v2, y1)));
+                y2 = fmaf(A[6 * N], v0, fmaf(A[7 * N], v1, fmaf(A[8 * N], v2, y2)));
             } else {
-                y0 = fmaf(A[0 * N], v0, fmaf(A[3 * N], v1, A[6 * N] * v2));
-                y1 = fmaf(A[1 * N], v0, fmaf(A[4 * N], v1, A[7 * N] * v2));
-                y2 = fmaf(A[2 * N], v0, fmaf(A[5 * N], v1, A[8 * N] * v2));
+                y0 = fmaf(A[0 * N], v0, fmaf(A[3 * N], v1, fmaf(A[6 * N], v2, y0)));
+                y1 = fmaf(A[1 * N], v0, fmaf(A[4 * N], v1, fmaf(A[7 * N], v2, y1)));
+                y2 = fmaf(A[2 * N], v0, fmaf(A[5 * N], v1, fmaf(A[8 * N], v2, y2)));
             }
         }
+    }
+    part[slice][t][0] = y0;
+    part[slice][t][1] = y1;
+    part[slice][t][2] = y2;
+    __syncthreads();
+    DSAcc dotv;
+    if (slice == 0 && live) {
+        float y[3];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            y0 += __shfl_xor_sync(0xffffffffu, y0, o);
-            y1 += __shfl_xor_sync(0xffffffffu, y1, o);
-            y2 += __shfl_xor_sync(0xffffffffu, y2, o);
-        }
-        if (lane == 0) {
-            const uint8_t msk = a.mask[n];
-            const float y[3] = {y0, y1, y2};
-            if (MODE == FM_APPLY) {
+        for (int c = 0; c < 3; ++c) y[c] = ((part[0][t][c] + part[1][t][c]) + part[2][t][c]) + part[3][t][c];
+        const uint8_t msk = a.mask[n];
+        if (MODE == FM_APPLY) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float v = fixed_bit(msk, c) ? 0.f : y[c];
-                    a.out[3 * n + c] = v;
-                    if (DOT) dotv += (double)a.xin[3 * n + c] * (double)v;
+            for (int c = 0; c < 3; ++c) {
+                const float v = fixed_bit(msk, c) ? 0.f : y[c];
+                a.out[3 * n + c] = v;
+                if (DOT) dotv.add_prod(a.xin[3 * n + c], v);
+            }
+        } else if (MODE == FM_RESID) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a.out[3 * n + c] = fixed_bit(msk, c) ? 0.f : a.b[3 * n + c] - y[c];
+        } else {
+            const float cd = (float)a.coef[2 * a.step], ca = (float)a.coef[2 * a.step + 1];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float xn = 0.f, dn = 0.f;
+                if (!fixed_bit(msk, c)) {
+                    const float bc = a.b[3 * n + c];
+                    dn = ca * a.invdiag[3 * n + c] * (bc - y[c]);
+                    if (cd != 0.f) dn = fmaf(cd, a.dold[3 * n + c], dn);
+                    xn = a.xin[3 * n + c] + dn;
+                    if (DOT) dotv.add_prod(bc, xn);
                 }
-            } else if (MODE == FM_RESID) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    a.out[3 * n + c] = fixed_bit(msk, c) ? 0.f : a.b[3 * n + c] - y[c];
-            } else {
-                const float cd = (float)a.coef[2 * a.step], ca = (float)a.coef[2 * a.step + 1];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float xn = 0.f, dn = 0.f;
-                    if (!fixed_bit(msk, c)) {
-                        const float bc = a.b[3 * n + c];
-                        dn = ca * a.invdiag[3 * n + c] * (bc - y[c]);
-                        if (cd != 0.f) dn = fmaf(cd, a.dold[3 * n + c], dn);
-                        xn = a.xin[3 * n + c] + dn;
-                        if (DOT) dotv += (double)bc * (double)xn;
-                    }
-                    a.out[3 * n + c] = xn;
-                    if (a.dnew) a.dnew[3 * n + c] = dn;
-                }
+                a.out[3 * n + c] = xn;
+                if (a.dnew) a.dnew[3 * n + c] = dn;
             }
         }
     }
     if (DOT) {
-        const double s = block_sum<256>(dotv, threadIdx.x);
-        if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+        const double s2 = block_sum<256>(dotv.value(), threadIdx.x);
+        if (threadIdx.x == 0) a.partial[blockIdx.x] = s2;
     }
 }
 
@@ -358,10 +366,10 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int nL, const int* free_id
 // summation order are independent of timing).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVecThreads) k_dot_f32(const float* a, const float* b, long long n, double* partial) {
-    double s = 0.0;
+    DSAcc acc;
     for (long long q = blockIdx.x * (long long)kVecThreads + threadIdx.x; q < n; q += (long long)gridDim.x * kVecThreads)
-        s += (double)a[q] * (double)b[q];
-    s = block_sum<kVecThreads>(s, threadIdx.x);
+        acc.add_prod(a[q], b[q]);
+    const double s = block_sum<kVecThreads>(acc.value(), threadIdx.x);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
@@ -391,18 +399,47 @@ __global__ void __launch_bounds__(kVecThreads) k_finalize(const double* partial,
     }
 }
 
+// u += alpha p (FP64), r -= alpha q (FP32), partial ||r||^2.  Four consecutive
+// entries per thread and iteration with 16-byte loads when every pointer allows.
 __global__ void __launch_bounds__(kVecThreads) k_pcg_update(double* u, float* r, const float* p, const float* q, long long n,
-                                                            const double* sc, double* partial) {
+                                                            const double* sc, double* partial, int vec4) {
     const double alpha = sc[SC_ALPHA];
     const float af = (float)alpha;
-    double s = 0.0;
-    for (long long i = blockIdx.x * (long long)kVecThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kVecThreads) {
+    DSAcc acc;
+    const long long stride = (long long)gridDim.x * kVecThreads;
+    long long done = 0;
+    if (vec4) {
+        const long long n4 = n / 4;
+        for (long long i = blockIdx.x * (long long)kVecThreads + threadIdx.x; i < n4; i += stride) {
+            const float4 pv = reinterpret_cast<const float4*>(p)[i];
+            const float4 qv = reinterpret_cast<const float4*>(q)[i];
+            float4 rv = reinterpret_cast<float4*>(r)[i];
+            double2 u0 = reinterpret_cast<double2*>(u)[2 * i], u1 = reinterpret_cast<double2*>(u)[2 * i + 1];
+            u0.x = fma(alpha, (double)pv.x, u0.x);
+            u0.y = fma(alpha, (double)pv.y, u0.y);
+            u1.x = fma(alpha, (double)pv.z, u1.x);
+            u1.y = fma(alpha, (double)pv.w, u1.y);
+            rv.x = fmaf(-af, qv.x, rv.x);
+            rv.y = fmaf(-af, qv.y, rv.y);
+            rv.z = fmaf(-af, qv.z, rv.z);
+            rv.w = fmaf(-af, qv.w, rv.w);
+            reinterpret_cast<double2*>(u)[2 * i] = u0;
+            reinterpret_cast<double2*>(u)[2 * i + 1] = u1;
+            reinterpret_cast<float4*>(r)[i] = rv;
+            acc.add_prod(rv.x, rv.x);
+            acc.add_prod(rv.y, rv.y);
+            acc.add_prod(rv.z, rv.z);
+            acc.add_prod(rv.w, rv.w);
+        }
+        done = 4 * n4;
+    }
+    for (long long i = done + blockIdx.x * (long long)kVecThreads + threadIdx.x; i < n; i += stride) {
         u[i] = fma(alpha, (double)p[i], u[i]);
         const float rn = fmaf(-af, q[i], r[i]);
         r[i] = rn;
-        s += (double)rn * (double)rn;
+        acc.add_prod(rn, rn);
     }
-    s = block_sum<kVecThreads>(s, threadIdx.x);
+    const double s = block_sum<kVecThreads>(acc.value(), threadIdx.x);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
@@ -502,38 +539,38 @@ void launch_fine_smooth0(const FineArgs& a, cudaStream_t s) {
     k_fine_smooth0<<<kVecBlocks * 2, kVecThreads, 0, s>>>(a);
 }
 
-// Levels below ~32k nodes are latency-bound: one warp per node there; larger
-// levels stream the operator with one thread per node.
-constexpr long long kBsrWarpLevel = 32768;
+// Standalone launches of the assembled-level operator: levels of at least
+// kBsrStreamLevel nodes stream with one thread per node; smaller ones are
+// latency-bound and use the K-split form (64 nodes per 256-thread block).
+constexpr long long kBsrStreamLevel = 65536;
 
 int bsr_grid_blocks(long long nn) {
-    if (nn < kBsrWarpLevel) return (int)((nn + 7) / 8);
-    return (int)((nn + 255) / 256);
+    return nn >= kBsrStreamLevel ? (int)((nn + 255) / 256) : (int)((nn + 63) / 64);
 }
 
 void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
     const int g = bsr_grid_blocks(a.nn);
     note_launch();
-    if (a.nn < kBsrWarpLevel) {
+    if (a.nn >= kBsrStreamLevel) {
         if (mode == FM_APPLY) {
-            if (dot) k_bsr_warp<FM_APPLY, true><<<g, 256, 0, s>>>(a);
-            else k_bsr_warp<FM_APPLY, false><<<g, 256, 0, s>>>(a);
+            if (dot) k_bsr<FM_APPLY, true, 256><<<g, 256, 0, s>>>(a);
+            else k_bsr<FM_APPLY, false, 256><<<g, 256, 0, s>>>(a);
         } else if (mode == FM_SMOOTH) {
-            if (dot) k_bsr_warp<FM_SMOOTH, true><<<g, 256, 0, s>>>(a);
-            else k_bsr_warp<FM_SMOOTH, false><<<g, 256, 0, s>>>(a);
+            if (dot) k_bsr<FM_SMOOTH, true, 256><<<g, 256, 0, s>>>(a);
+            else k_bsr<FM_SMOOTH, false, 256><<<g, 256, 0, s>>>(a);
         } else {
-            k_bsr_warp<FM_RESID, false><<<g, 256, 0, s>>>(a);
+            k_bsr<FM_RESID, false, 256><<<g, 256, 0, s>>>(a);
         }
         return;
     }
     if (mode == FM_APPLY) {
-        if (dot) k_bsr<FM_APPLY, true, 256><<<g, 256, 0, s>>>(a);
-        else k_bsr<FM_APPLY, false, 256><<<g, 256, 0, s>>>(a);
+        if (dot) k_bsr_ks<FM_APPLY, true><<<g, 256, 0, s>>>(a);
+        else k_bsr_ks<FM_APPLY, false><<<g, 256, 0, s>>>(a);
     } else if (mode == FM_SMOOTH) {
-        if (dot) k_bsr<FM_SMOOTH, true, 256><<<g, 256, 0, s>>>(a);
-        else k_bsr<FM_SMOOTH, false, 256><<<g, 256, 0, s>>>(a);
+        if (dot) k_bsr_ks<FM_SMOOTH, true><<<g, 256, 0, s>>>(a);
+        else k_bsr_ks<FM_SMOOTH, false><<<g, 256, 0, s>>>(a);
     } else {
-        k_bsr<FM_RESID, false, 256><<<g, 256, 0, s>>>(a);
+        k_bsr_ks<FM_RESID, false><<<g, 256, 0, s>>>(a);
     }
 }
 
@@ -589,7 +626,9 @@ void launch_finalize(const double* partial, int n, double* sc, int slot, int op,
 void launch_pcg_update(double* u, float* r, const float* p, const float* q, long long n, const double* sc,
                        double* partial, cudaStream_t s) {
     note_launch();
-    k_pcg_update<<<kVecBlocks, kVecThreads, 0, s>>>(u, r, p, q, n, sc, partial);
+    const bool vec4 = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(p) |
+                        reinterpret_cast<uintptr_t>(q)) & 15) == 0;
+    k_pcg_update<<<kVecBlocks, kVecThreads, 0, s>>>(u, r, p, q, n, sc, partial, vec4 ? 1 : 0);
 }
 
 void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s) {

@@ -85,6 +85,49 @@ struct Level {
     int n_free = 0;
 };
 
+// Device view of one assembled level for the fused lower V-cycle (coarse_fused.cu).
+struct CoarseLevel {
+    int nx, ny, nz, nn;
+    const uint8_t* mask;
+    const float* A;          // symmetric half storage, [126][nn]
+    const float* invdiag;
+    float *x, *x2, *b, *t, *d;
+    const double* coef;
+    int kind, degree;
+};
+
+// Arguments of the fused lower V-cycle: levels start..L-1, coarsest solve data,
+// and the grid-barrier words (arrival count, generation, error flag).
+struct CoarseFused {
+    CoarseLevel lev[kMaxLevels];
+    int start, L, nL;
+    const int* free_idx;
+    const double* Ainv;
+    unsigned* bar_count;
+    unsigned* bar_gen;
+    int* err;
+    long long spin_limit;
+};
+
+// Per-thread dot-product accumulator in double-single arithmetic: products are
+// split exactly with an FMA and summed with TwoSum, so a thread's partial is
+// accurate to ~2^-48 of the sum of |terms| while staying on the FP32 pipes (FP64
+// issue is a small fraction of FP32 on this part).  Partials are combined across
+// threads and blocks in FP64.
+struct DSAcc {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = a * b;
+        const float e = fmaf(a, b, -p);
+        const float s = hi + p;
+        const float bb = s - hi;
+        const float t = (hi - (s - bb)) + (p - bb);
+        hi = s;
+        lo += t + e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 }  // namespace gmg
 
 struct gmg_handle {
@@ -113,6 +156,9 @@ struct gmg_handle {
     int* free_idx = nullptr;                    // [nL] DOF indices of the coarsest free DOFs
     double* Ainv = nullptr;                     // [nL nL]
     double eps = 0.0;
+    gmg::CoarseFused cf{};                      // fused lower V-cycle (levels cf.start..L-1)
+    bool use_fused = false;
+    int fused_blocks = 0;
     std::vector<void*> allocs;                  // every device allocation, freed by gmg_destroy
     void* pinned = nullptr;                     // pinned host block (sc_host)
 };
@@ -212,6 +258,10 @@ void launch_free_index(const uint8_t* mask, long long nn, int* free_idx, int* co
 void launch_dense_gather(const Level& l, const int* free_idx, int n, double* dense, cudaStream_t s);
 void launch_regularise(double* dense, int n, double* eps_out, cudaStream_t s);
 int cholesky_and_inverse(double* A, int n, double* work, int* info_dev, double* Ainv, cudaStream_t s);
+
+// ---- coarse_fused.cu ------------------------------------------------------------
+int coarse_fused_blocks(int* blocks_out, size_t shm);
+int launch_coarse_fused(const CoarseFused& a, int blocks, cudaStream_t s);
 void launch_lambda_finish(double* sc, double* lam_slot, cudaStream_t s);
 
 }  // namespace gmg

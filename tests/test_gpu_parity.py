@@ -340,3 +340,25 @@ def test_smallest_grid():
                 coarse_omega=None)
     info, res = _solve_and_compare(rho, 3.0, inputs.clamp_xmin_mask(2, 2, 2), inputs.tip_edge_load(2, 2, 2), opts)
     assert info["status"] == 0
+
+
+@pytest.mark.parametrize("cfg_name", ["c0", "c1"])
+def test_fused_lower_vcycle_matches_per_level_kernels(cfg_name):
+    """The persistent kernel that runs the assembled levels below the node
+    threshold (and the coarsest solve) gives the same V-cycle and the same
+    solve as one kernel launch per step."""
+    c = inputs.CONFIGS[cfg_name]
+    rho = c.rho()
+    opts = config_opts(c)
+    S_f = gpu_solver(rho, c.p, **opts, fused_coarse_nodes=65536)
+    S_u = gpu_solver(rho, c.p, **opts, fused_coarse_nodes=0)
+    rng = np.random.default_rng(12)
+    r = inputs.random_free_vector(c.fixed(), seed=13)
+    zf = S_f.vcycle(_t(r)).cpu().numpy()
+    zu = S_u.vcycle(_t(r)).cpu().numpy()
+    assert rel_l2(zf, zu) < 1e-5
+    f = _t(c.load(), torch.float64)
+    _, inf_f = S_f.solve(f)
+    _, inf_u = S_u.solve(f)
+    assert inf_f["status"] == 0 and inf_u["status"] == 0
+    assert abs(inf_f["iterations"] - inf_u["iterations"]) <= 1
