@@ -6,11 +6,46 @@
 
 Each case prints the library's kernel-launch counter after set-up, so that
 ``ncu -s`` can skip the set-up kernels.
+
+    python -m paper_2604_26441_b300.profile_cases summarize LAUNCHES.csv [FIRST_ID]
+
+reads the CSV that ``ncu --metrics gpu__time_duration.sum --csv --log-file``
+writes and prints, per kernel, its launches, total time and share of the time of
+the launches with ID >= FIRST_ID (e.g. the set-up launch count, to keep only the
+solves).
 """
 
 from __future__ import annotations
 
 import sys
+
+
+def summarize(path: str, first_id: int = 0) -> str:
+    import collections
+    import csv
+    import re
+
+    with open(path) as fh:
+        lines = [ln for ln in fh if ln.startswith('"')]
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    n = 0
+    for row in csv.DictReader(lines):
+        if row.get("Metric Name") != "gpu__time_duration.sum" or int(row["ID"]) < first_id:
+            continue
+        us = float(row["Metric Value"].replace(",", ""))
+        us *= {"nsecond": 1e-3, "ns": 1e-3, "usecond": 1.0, "us": 1.0, "msecond": 1e3, "ms": 1e3, "second": 1e6, "s": 1e6}[row["Metric Unit"]]
+        name = re.sub(r"^void ", "", row["Kernel Name"])
+        name = re.sub(r"<unnamed>::|\(anonymous namespace\)::|gmg::", "", name)
+        name = re.sub(r"\((FineArgs|BsrArgs|GHat|CoarseFused|const|int|float|double|unsigned|long|std::).*$", "", name)
+        agg[name][0] += 1
+        agg[name][1] += us
+        n += 1
+    tot = sum(v[1] for v in agg.values())
+    out = [f"launches {n}, total {tot:.1f} us", "", "| kernel | launches | total us | share | us/launch |",
+           "|---|---:|---:|---:|---:|"]
+    for k, (c, t) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        out.append(f"| `{k}` | {c} | {t:.1f} | {100 * t / tot:.2f} % | {t / c:.2f} |")
+    return "\n".join(out)
 
 
 def main(case: str) -> None:
@@ -42,4 +77,7 @@ def main(case: str) -> None:
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "solve-c2")
+    if len(sys.argv) > 2 and sys.argv[1] == "summarize":
+        print(summarize(sys.argv[2], int(sys.argv[3]) if len(sys.argv) > 3 else 0))
+    else:
+        main(sys.argv[1] if len(sys.argv) > 1 else "solve-c2")
