@@ -622,7 +622,13 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
         return finish(GMG_OK);
     }
     double rel = 0.0;
-    TRY(true_residual(rel));  // r (FP32) = f - K u, FP64 norm
+    if (sch[SC_UNZ] == 0.0) {
+        // zero iterate (a cold start): K u = 0 exactly, so r = f and ||r|| / ||f|| = 1
+        launch_cast_masked(f, l0.mask, l0.nn, h->r, s);
+        rel = 1.0;
+    } else {
+        TRY(true_residual(rel));  // r (FP32) = f - K u, FP64 norm
+    }
     // every later operator application sees u != 0 through the PCG updates
     inf.rel_residual = rel;
     inf.rel_residual_recursive = rel;

@@ -459,6 +459,12 @@ __global__ void __launch_bounds__(kVecThreads) k_mask_u64(double* u, const uint8
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// r = f on free DOFs (as FP32), 0 on fixed ones: the residual of the zero iterate.
+__global__ void __launch_bounds__(kVecThreads) k_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r) {
+    for (long long q = blockIdx.x * (long long)kVecThreads + threadIdx.x; q < 3 * nn; q += (long long)gridDim.x * kVecThreads)
+        r[q] = fixed_bit(mask[q / 3], (int)(q % 3)) ? 0.f : (float)f[q];
+}
+
 __global__ void k_scale_inv_sqrt(float* v, long long n, const double* sc, int slot) {
     const double s = sc[slot];
     if (!(s > 0.0) || !isfinite(s)) return;
@@ -639,6 +645,11 @@ void launch_p_update(float* p, const float* z, long long n, const double* sc, cu
 void launch_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial, cudaStream_t s) {
     note_launch();
     k_mask_u64<<<kVecBlocks, kVecThreads, 0, s>>>(u, mask, nn, partial);
+}
+
+void launch_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r, cudaStream_t s) {
+    note_launch();
+    k_cast_masked<<<kVecBlocks, kVecThreads, 0, s>>>(f, mask, nn, r);
 }
 
 void launch_scale_by_inv_sqrt(float* v, long long n, const double* sc, int slot, cudaStream_t s) {

@@ -228,6 +228,7 @@ void launch_pcg_update(double* u, float* r, const float* p, const float* q, long
                        const double* sc, double* partial, cudaStream_t s);
 void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s);
 void launch_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial, cudaStream_t s);
+void launch_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r, cudaStream_t s);
 void launch_scale_by_inv_sqrt(float* v, long long n, const double* sc, int slot, cudaStream_t s);
 void launch_scale_invdiag_fine(const float* y, float* w, const float* E, const uint8_t* mask,
                                int nx, int ny, int nz, float kd, cudaStream_t s);

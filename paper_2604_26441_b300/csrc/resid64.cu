@@ -213,17 +213,37 @@ __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const
     }
 }
 
+// Picks the z-chunk that minimises (waves x steps per block).  At ~230
+// registers per thread one 256-thread block fits per SM, so a partial last wave
+// costs a whole chunk of steps: at 100^3 (7 x 7 columns of blocks) chunks of 34
+// planes give one wave of 147 blocks, where chunks of 15 gave 3 waves of 343.
 dim3 resid_grid(int nx, int ny, int nz, int* zc_out) {
     const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
     const int gx = (NX + BX - 2) / (BX - 1), gy = (NY + BY - 2) / (BY - 1);
-    int dev = 0, sms = 148;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        sms = 148;
-    const int want = std::max(1, (2 * sms + gx * gy - 1) / (gx * gy));
-    int zc = std::max(4, (NZ + want - 1) / want);
-    zc = std::min(zc, NZ);
-    *zc_out = zc;
-    return dim3(gx, gy, (NZ + zc - 1) / zc);
+    static int slots = 0;
+    if (slots == 0) {
+        int dev = 0, sms = 148, per_sm = 1;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 148;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid64, NT, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        slots = sms * per_sm;
+    }
+    int best_zc = NZ;
+    long long best_cost = -1;
+    for (int gz = 1; gz <= NZ; ++gz) {
+        const int zc = (NZ + gz - 1) / gz;
+        if (zc < 4 && gz > 1) break;
+        const long long blocks = (long long)gx * gy * ((NZ + zc - 1) / zc);
+        const long long cost = ((blocks + slots - 1) / slots) * (zc + 1);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best_zc = zc;
+        }
+    }
+    *zc_out = best_zc;
+    return dim3(gx, gy, (NZ + best_zc - 1) / best_zc);
 }
 
 }  // namespace
