@@ -87,6 +87,10 @@ typedef struct {
     int chol_cutoff;             /* dense-Cholesky size limit for the coarsest level (5000) */
     int fused_coarse_nodes;      /* assembled levels with fewer nodes than this run, together with
                                     the coarsest solve, as one persistent kernel (4096); 0 = off */
+    int bsr_tma_nodes;           /* assembled levels with at least this many nodes load their
+                                    operator planes as TMA-staged shared-memory tiles;
+                                    <= 0 (default) = never: levels of >= 65536 nodes stream one
+                                    thread per node, smaller ones use the K-split kernel */
     void* stream;                /* cudaStream_t for all device work; NULL = default stream */
 } gmg_options;
 

@@ -80,7 +80,9 @@ BsrArgs bsr_args(gmg_handle* h, int li) {
     const Level& l = h->lev[li];
     BsrArgs a{};
     a.nx = l.nx; a.ny = l.ny; a.nz = l.nz; a.nn = l.nn;
-    a.A = l.A32; a.invdiag = l.invdiag; a.mask = l.mask; a.coef = l.coef;
+    a.A = l.A32; a.ps = l.ps; a.invdiag = l.invdiag; a.mask = l.mask; a.coef = l.coef;
+    a.err = h->kerr;
+    if (l.tma) { a.tm_own = &l.tm_own; a.tm_back = &l.tm_back; }
     return a;
 }
 
@@ -88,7 +90,7 @@ int partial_count(gmg_handle* h, int li, int kind) {
     // kind 0: operator-kernel partials, 1: vector-kernel partials
     if (kind == 1) return vec_grid_blocks();
     if (li == 0) return fine_grid_blocks(h->lev[0].nx, h->lev[0].ny, h->lev[0].nz);
-    return bsr_grid_blocks(h->lev[li].nn);
+    return bsr_grid_blocks(h->lev[li].nn, h->lev[li].tma);
 }
 
 // y = K^l x (masked); with dot: partial += x . y and finalised into `slot`.
@@ -295,7 +297,9 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         TRY(dalloc(h, &l.coef, 2 * kMaxDegree));
         if (li > 0) {
             TRY(dalloc(h, &l.A64, (size_t)kPlanes * l.nn));
-            TRY(dalloc(h, &l.A32, (size_t)kSymPlanes * l.nn));
+            l.ps = (l.nn + 3) / 4 * 4;
+            TRY(dalloc(h, &l.A32, (size_t)kSymPlanes * l.ps));
+            CU(cudaMemsetAsync(l.A32, 0, sizeof(float) * kSymPlanes * l.ps, s));
             TRY(dalloc(h, &l.invdiag, 3 * l.nn));
             TRY(dalloc(h, &l.x, 3 * l.nn));
             TRY(dalloc(h, &l.x2, 3 * l.nn));
@@ -318,10 +322,13 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     TRY(dalloc(h, &h->lam, kMaxLevels));
     TRY(dalloc(h, &h->sc, SC_COUNT));
     CU(cudaMemsetAsync(h->sc, 0, sizeof(double) * SC_COUNT, s));
+    TRY(dalloc(h, &h->kerr, 1));
+    CU(cudaMemsetAsync(h->kerr, 0, sizeof(int), s));
     int maxp = vec_grid_blocks();
     maxp = std::max(maxp, fine_grid_blocks(l0.nx, l0.ny, l0.nz));
     maxp = std::max(maxp, resid64_grid_blocks(l0.nx, l0.ny, l0.nz));
-    for (int li = 1; li < L; ++li) maxp = std::max(maxp, bsr_grid_blocks(h->lev[li].nn));
+    // (the kernel of a level is chosen later; size for the one with more blocks)
+    for (int li = 1; li < L; ++li) maxp = std::max(maxp, bsr_grid_blocks(h->lev[li].nn, true));
     h->max_partials = maxp;
     TRY(dalloc(h, &h->partials, maxp));
     CU(cudaMallocHost(&h->pinned, sizeof(double) * SC_COUNT));
@@ -411,7 +418,9 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
             double* Kc = nullptr;
             const long long ne0 = (long long)l0.nx * l0.ny * l0.nz;
             TRY(dalloc(h, &l0.A64, (size_t)kPlanes * l0.nn));
-            TRY(dalloc(h, &l0.A32, (size_t)kSymPlanes * l0.nn));
+            l0.ps = (l0.nn + 3) / 4 * 4;
+            TRY(dalloc(h, &l0.A32, (size_t)kSymPlanes * l0.ps));
+            CU(cudaMemsetAsync(l0.A32, 0, sizeof(float) * kSymPlanes * l0.ps, s));
             TRY(dalloc(h, &l0.invdiag, 3 * l0.nn));
             TRY(dalloc(h, &Kc, (size_t)ne0 * 576));
             launch_fine_element_matrices(h->E64, ne0, Ke, Kc, s);
@@ -430,6 +439,14 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         dfree(h, dense);
         dfree(h, work);
     }
+    // ---- TMA-staged operator for the large assembled levels
+    for (int li = 1; li < L; ++li) {
+        Level& l = h->lev[li];
+        if (o.bsr_tma_nodes > 0 && l.nn >= o.bsr_tma_nodes) {
+            const int rc = encode_bsr_maps(l);
+            if (rc != GMG_OK) return fail(rc, "could not encode the tensor maps of an assembled level");
+        }
+    }
     // ---- fused lower V-cycle: every assembled level below the node threshold
     if (o.fused_coarse_nodes > 0 && L >= 2) {
         int start = L - 1;
@@ -445,7 +462,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
                 const Level& l = h->lev[li];
                 CoarseLevel& c = cf.lev[li];
                 c.nx = l.nx; c.ny = l.ny; c.nz = l.nz; c.nn = (int)l.nn;
-                c.mask = l.mask; c.A = l.A32; c.invdiag = l.invdiag;
+                c.mask = l.mask; c.A = l.A32; c.ps = (int)l.ps; c.invdiag = l.invdiag;
                 c.x = l.x; c.x2 = l.x2; c.b = l.b; c.t = l.t; c.d = l.d;
                 c.coef = l.coef; c.kind = l.kind; c.degree = l.degree;
             }
@@ -466,13 +483,15 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     return GMG_OK;
 }
 
-// Reports a timed-out wait of the fused lower V-cycle (its error word is sticky).
+// Reports a timed-out wait of the TMA-staged operator or of the fused lower
+// V-cycle (both error words are sticky).
 int check_fused(gmg_handle* h) {
-    if (!h->use_fused) return GMG_OK;
-    int err = 0;
-    CU(cudaMemcpyAsync(&err, h->cf.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    int err[2] = {0, 0};
+    CU(cudaMemcpyAsync(&err[0], h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (h->use_fused) CU(cudaMemcpyAsync(&err[1], h->cf.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
-    if (err) return fail(GMG_ERR_CUDA, "the fused coarse-level V-cycle gave up waiting at a grid barrier");
+    if (err[0]) return fail(GMG_ERR_CUDA, "an assembled-level operator gave up waiting for its TMA tiles");
+    if (err[1]) return fail(GMG_ERR_CUDA, "the fused coarse-level V-cycle gave up waiting at a grid barrier");
     return GMG_OK;
 }
 
@@ -497,6 +516,7 @@ void gmg_default_options(gmg_options* o) {
     o->power_iters_coarse = 10;
     o->chol_cutoff = 5000;
     o->fused_coarse_nodes = 4096;
+    o->bsr_tma_nodes = 0;
     o->stream = nullptr;
 }
 

@@ -69,7 +69,7 @@ __device__ __forceinline__ bool grid_barrier(const CoarseFused& a, unsigned& gen
 __device__ __forceinline__ void warp_row(const CoarseLevel& L, int n, const float* x, int lane, float y[3]) {
     const int NX = L.nx + 1, NY = L.ny + 1, NZ = L.nz + 1;
     const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
-    const long long N = L.nn;
+    const long long N = L.ps;
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
     if (lane < 27) {
         const bool fwd = lane < 14;

@@ -3,8 +3,11 @@
 //  * k_fine_smooth0  -- first fine-level smoother step from zero (the fused
 //                       fine operator lives in fine.cu, its FP64 residual form
 //                       in resid64.cu);
-//  * k_bsr           -- the same three modes on an assembled Galerkin level
-//                       (27-point 3x3-block operator, implicit structured columns);
+//  * k_bsr / k_bsr_ks / k_bsr_tma -- the same three modes on an assembled
+//                       Galerkin level (27-point 3x3-block operator, implicit
+//                       structured columns): one streaming thread per node for
+//                       large levels, a K-split form for small ones, and an
+//                       optional TMA-staged form;
 //  * k_restrict / k_prolong_add -- R = P^T and P of Eq. trilinear_weights /
 //                       Eq. vector_prolongation with the odd-size clamp;
 //  * k_coarse_solve  -- dense FP64 solve with the Cholesky-derived inverse;
@@ -72,14 +75,58 @@ __global__ void k_fine_smooth0(FineArgs a) {
 // ---------------------------------------------------------------------------
 // Assembled levels: K^l is symmetric, so only the diagonal block and the 13
 // "forward" neighbour blocks (slots 13..26, offsets after the node in memory
-// order) are stored, plane-major: A[(u*9 + r*3 + c)*nn + n] is entry (r, c) of
+// order) are stored, plane-major: A[(u*9 + r*3 + c)*ps + n] is entry (r, c) of
 // block (n, n + o_u), u = slot - 13.  Row n of K^l is then
 //   sum_u A_u(n) x(n + o_u)  +  sum_{u>0} A_u(n - o_u)^T x(n - o_u).
+// The plane stride ps is nn rounded up to a multiple of 4 (16-byte aligned
+// planes, zero padding), which the TMA-staged kernel needs.
 // ---------------------------------------------------------------------------
+
+// Node offset of forward block u (slot 13 + u) on a grid of NX x NY nodes per plane.
+__device__ __forceinline__ int fwd_offset(int u, int NX, int NY, int& dx, int& dy, int& dz) {
+    const int sl = 13 + u;
+    dx = sl % 3 - 1; dy = (sl / 3) % 3 - 1; dz = sl / 9 - 1;
+    return dx + NX * (dy + NY * dz);
+}
+
+// Epilogue of one node's row y = (K x)_n: apply (masked, optional x.y), residual
+// b - y, or one smoother step (Jacobi / Chebyshev, optional b.x_new).
+template <int MODE, bool DOT>
+__device__ __forceinline__ void bsr_epilogue(const BsrArgs& a, int n, const float y[3], DSAcc& dotv) {
+    const uint8_t msk = a.mask[n];
+    if (MODE == FM_APPLY) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float v = fixed_bit(msk, c) ? 0.f : y[c];
+            a.out[3 * n + c] = v;
+            if (DOT) dotv.add_prod(a.xin[3 * n + c], v);
+        }
+    } else if (MODE == FM_RESID) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a.out[3 * n + c] = fixed_bit(msk, c) ? 0.f : a.b[3 * n + c] - y[c];
+    } else {
+        const float cd = (float)a.coef[2 * a.step], ca = (float)a.coef[2 * a.step + 1];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float xn = 0.f, dn = 0.f;
+            if (!fixed_bit(msk, c)) {
+                const float bc = a.b[3 * n + c];
+                dn = ca * a.invdiag[3 * n + c] * (bc - y[c]);
+                if (cd != 0.f) dn = fmaf(cd, a.dold[3 * n + c], dn);
+                xn = a.xin[3 * n + c] + dn;
+                if (DOT) dotv.add_prod(bc, xn);
+            }
+            a.out[3 * n + c] = xn;
+            if (a.dnew) a.dnew[3 * n + c] = dn;
+        }
+    }
+}
+
 // Large levels (bandwidth-bound): one thread per node streaming the planes,
-// branch-free so that all of a node's loads can be in flight together
-// (out-of-grid forward blocks are stored as zero; out-of-grid backward terms are
-// scaled by 0).
+// branch-free so that all of a node's loads can be in flight together: every
+// load is unconditional (indices clamped to the node itself for neighbours
+// outside the grid); out-of-grid forward blocks are stored as zero and
+// out-of-grid backward terms are scaled by 0.
 template <int MODE, bool DOT, int NTB>
 __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
     const int nn = (int)a.nn;
@@ -88,7 +135,7 @@ __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
     if (n < nn) {
         const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
         const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
-        const long long N = nn;
+        const long long N = a.ps;
         float y0 = 0.f, y1 = 0.f, y2 = 0.f;
         // branch-free: every load is unconditional (indices clamped to this node
         // when the neighbour is outside the grid), so all of them can be in
@@ -117,39 +164,151 @@ __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
                 y2 = fmaf(B[2 * N], w0, fmaf(B[5 * N], w1, fmaf(B[8 * N], w2, y2)));
             }
         }
-        const uint8_t msk = a.mask[n];
         const float y[3] = {y0, y1, y2};
-        if (MODE == FM_APPLY) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float v = fixed_bit(msk, c) ? 0.f : y[c];
-                a.out[3 * n + c] = v;
-                if (DOT) dotv.add_prod(a.xin[3 * n + c], v);
-            }
-        } else if (MODE == FM_RESID) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                a.out[3 * n + c] = fixed_bit(msk, c) ? 0.f : a.b[3 * n + c] - y[c];
-        } else {
-            const float cd = (float)a.coef[2 * a.step], ca = (float)a.coef[2 * a.step + 1];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float xn = 0.f, dn = 0.f;
-                if (!fixed_bit(msk, c)) {
-                    const float bc = a.b[3 * n + c];
-                    dn = ca * a.invdiag[3 * n + c] * (bc - y[c]);
-                    if (cd != 0.f) dn = fmaf(cd, a.dold[3 * n + c], dn);
-                    xn = a.xin[3 * n + c] + dn;
-                    if (DOT) dotv.add_prod(bc, xn);
-                }
-                a.out[3 * n + c] = xn;
-                if (a.dnew) a.dnew[3 * n + c] = dn;
-            }
-        }
+        bsr_epilogue<MODE, DOT>(a, n, y, dotv);
     }
     if (DOT) {
         const double s = block_sum<NTB>(dotv.value(), threadIdx.x);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
+    }
+}
+
+// ---- TMA and mbarrier primitives (inline PTX) ------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 2D tiled TMA load of the box at (x = node, y = plane) into shared memory,
+// completing on `bar` (x must be a multiple of 4: 16-byte aligned start).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Large levels: TMA-staged tiles.  A block of 128 threads owns 64 consecutive
+// nodes.  One elected thread issues 14 tensor loads on one mbarrier:
+//   - the block's own 126 planes (box 126 x 64: diagonal + forward blocks);
+//   - for each backward block u = 1..13, the 9 planes of block u at the nodes
+//     n - o_u, i.e. a box 9 x 68 starting at (n0 - o_u) rounded down to a
+//     multiple of 4 nodes (TMA wants 16-byte aligned starts; the remainder is
+//     applied when reading; coordinates outside the tensor read as zero).
+// That is 64,080 bytes in flight per block with no registers held, while the
+// threads fetch their neighbours' x values.  Slice 0 (threads 0-63) applies
+// the diagonal and forward blocks, slice 1 the transposed backward blocks;
+// slice 0 adds the two rows in a fixed order and runs the epilogue.
+// ---------------------------------------------------------------------------
+constexpr int kTmaNodes = 64;
+constexpr int kTmaBackW = kTmaNodes + 4;
+constexpr int kTmaOwnFloats = kSymPlanes * kTmaNodes;            // 8064 floats = 252 x 128 B
+constexpr int kTmaBackStride = 640;                              // 9 x 68 = 612 floats, padded to 128 B
+constexpr unsigned kTmaTxBytes = 4u * (kTmaOwnFloats + 13 * 9 * kTmaBackW);
+constexpr int kTmaSmemBytes = 128 + 4 * (kTmaOwnFloats + 13 * kTmaBackStride + 3 * kTmaNodes) + 16;
+constexpr long long kTmaSpin = 1LL << 22;
+
+template <int MODE, bool DOT>
+__global__ void __launch_bounds__(128) k_bsr_tma(const __grid_constant__ CUtensorMap tm_own,
+                                                 const __grid_constant__ CUtensorMap tm_back, BsrArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    float* sOwn = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float* sBack = sOwn + kTmaOwnFloats;
+    float* part = sBack + 13 * kTmaBackStride;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(part + 3 * kTmaNodes);
+    const int tid = threadIdx.x, t = tid & (kTmaNodes - 1), slice = tid >> 6;
+    const int nn = (int)a.nn;
+    const int n0 = blockIdx.x * kTmaNodes, n = n0 + t;
+    const bool live = n < nn;
+    const int nsafe = live ? n : nn - 1;
+    const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
+    const int i = nsafe % NX, j = (nsafe / NX) % NY, k = nsafe / (NX * NY);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(bar, kTmaTxBytes);
+        tma_load_2d(sOwn, &tm_own, n0, 0, bar);
+#pragma unroll 1
+        for (int u = 1; u < 14; ++u) {
+            int dx, dy, dz;
+            const int off = fwd_offset(u, NX, NY, dx, dy, dz);
+            tma_load_2d(sBack + (u - 1) * kTmaBackStride, &tm_back, (n0 - off) & ~3, 9 * u, bar);
+        }
+    }
+    // neighbour values (branch-free: out-of-grid neighbours read this node with weight 0)
+    float v[14][3];
+#pragma unroll
+    for (int u = 0; u < 14; ++u) {
+        if (slice == 1 && u == 0) { v[0][0] = v[0][1] = v[0][2] = 0.f; continue; }
+        int dx, dy, dz;
+        const int off = fwd_offset(u, NX, NY, dx, dy, dz);
+        const int sx = slice ? -dx : dx, sy = slice ? -dy : dy, sz = slice ? -dz : dz;
+        const bool ok = i + sx >= 0 && i + sx < NX && j + sy >= 0 && j + sy < NY && k + sz >= 0 && k + sz < NZ;
+        const int m = ok ? (slice ? nsafe - off : nsafe + off) : nsafe;
+        const float w = ok ? 1.f : 0.f;
+        v[u][0] = w * a.xin[3 * m];
+        v[u][1] = w * a.xin[3 * m + 1];
+        v[u][2] = w * a.xin[3 * m + 2];
+    }
+    // bounded wait for the tiles; the decision to give up is taken by the whole block
+    bool ok = false;
+    for (long long it = 0; it < kTmaSpin; ++it)
+        if (mbar_try_wait(bar, 0)) { ok = true; break; }
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(a.err, 1);
+        return;
+    }
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+    if (slice == 0) {
+#pragma unroll
+        for (int u = 0; u < 14; ++u) {
+            const float* A = sOwn + (9 * u) * kTmaNodes + t;
+            y0 = fmaf(A[0 * kTmaNodes], v[u][0], fmaf(A[1 * kTmaNodes], v[u][1], fmaf(A[2 * kTmaNodes], v[u][2], y0)));
+            y1 = fmaf(A[3 * kTmaNodes], v[u][0], fmaf(A[4 * kTmaNodes], v[u][1], fmaf(A[5 * kTmaNodes], v[u][2], y1)));
+            y2 = fmaf(A[6 * kTmaNodes], v[u][0], fmaf(A[7 * kTmaNodes], v[u][1], fmaf(A[8 * kTmaNodes], v[u][2], y2)));
+        }
+    } else {
+#pragma unroll
+        for (int u = 1; u < 14; ++u) {
+            int dx, dy, dz;
+            const int off = fwd_offset(u, NX, NY, dx, dy, dz);
+            const float* B = sBack + (u - 1) * kTmaBackStride + ((n0 - off) - ((n0 - off) & ~3)) + t;
+            y0 = fmaf(B[0 * kTmaBackW], v[u][0], fmaf(B[3 * kTmaBackW], v[u][1], fmaf(B[6 * kTmaBackW], v[u][2], y0)));
+            y1 = fmaf(B[1 * kTmaBackW], v[u][0], fmaf(B[4 * kTmaBackW], v[u][1], fmaf(B[7 * kTmaBackW], v[u][2], y1)));
+            y2 = fmaf(B[2 * kTmaBackW], v[u][0], fmaf(B[5 * kTmaBackW], v[u][1], fmaf(B[8 * kTmaBackW], v[u][2], y2)));
+        }
+        part[3 * t] = y0;
+        part[3 * t + 1] = y1;
+        part[3 * t + 2] = y2;
+    }
+    __syncthreads();
+    DSAcc dotv;
+    if (slice == 0 && live) {
+        const float y[3] = {y0 + part[3 * t], y1 + part[3 * t + 1], y2 + part[3 * t + 2]};
+        bsr_epilogue<MODE, DOT>(a, n, y, dotv);
+    }
+    if (DOT) {
+        const double s2 = block_sum<128>(dotv.value(), tid);
+        if (tid == 0) a.partial[blockIdx.x] = s2;
     }
 }
 
@@ -169,7 +328,7 @@ __global__ void __launch_bounds__(256) k_bsr_ks(BsrArgs a) {
     const int nsafe = live ? n : 0;
     const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
     const int i = nsafe % NX, j = (nsafe / NX) % NY, k = nsafe / (NX * NY);
-    const long long N = nn;
+    const long long N = a.ps;
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
@@ -206,33 +365,7 @@ __global__ void __launch_bounds__(256) k_bsr_ks(BsrArgs a) {
         float y[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) y[c] = ((part[0][t][c] + part[1][t][c]) + part[2][t][c]) + part[3][t][c];
-        const uint8_t msk = a.mask[n];
-        if (MODE == FM_APPLY) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float v = fixed_bit(msk, c) ? 0.f : y[c];
-                a.out[3 * n + c] = v;
-                if (DOT) dotv.add_prod(a.xin[3 * n + c], v);
-            }
-        } else if (MODE == FM_RESID) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) a.out[3 * n + c] = fixed_bit(msk, c) ? 0.f : a.b[3 * n + c] - y[c];
-        } else {
-            const float cd = (float)a.coef[2 * a.step], ca = (float)a.coef[2 * a.step + 1];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float xn = 0.f, dn = 0.f;
-                if (!fixed_bit(msk, c)) {
-                    const float bc = a.b[3 * n + c];
-                    dn = ca * a.invdiag[3 * n + c] * (bc - y[c]);
-                    if (cd != 0.f) dn = fmaf(cd, a.dold[3 * n + c], dn);
-                    xn = a.xin[3 * n + c] + dn;
-                    if (DOT) dotv.add_prod(bc, xn);
-                }
-                a.out[3 * n + c] = xn;
-                if (a.dnew) a.dnew[3 * n + c] = dn;
-            }
-        }
+        bsr_epilogue<MODE, DOT>(a, n, y, dotv);
     }
     if (DOT) {
         const double s2 = block_sum<256>(dotv.value(), threadIdx.x);
@@ -545,18 +678,43 @@ void launch_fine_smooth0(const FineArgs& a, cudaStream_t s) {
     k_fine_smooth0<<<kVecBlocks * 2, kVecThreads, 0, s>>>(a);
 }
 
-// Standalone launches of the assembled-level operator: levels of at least
-// kBsrStreamLevel nodes stream with one thread per node; smaller ones are
-// latency-bound and use the K-split form (64 nodes per 256-thread block).
+// Standalone launches of the assembled-level operator.  Levels with tensor maps
+// (bsr_tma_nodes option) use the TMA-staged kernel; otherwise levels of at
+// least kBsrStreamLevel nodes stream with one thread per node and smaller ones,
+// which are latency-bound, use the K-split form.
 constexpr long long kBsrStreamLevel = 65536;
 
-int bsr_grid_blocks(long long nn) {
+int bsr_grid_blocks(long long nn, bool tma) {
+    if (tma) return (int)((nn + kTmaNodes - 1) / kTmaNodes);
     return nn >= kBsrStreamLevel ? (int)((nn + 255) / 256) : (int)((nn + 63) / 64);
 }
 
+template <int MODE, bool DOT>
+void launch_bsr_tma(int g, const BsrArgs& a, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_bsr_tma<MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmemBytes);
+        attr = true;
+    }
+    k_bsr_tma<MODE, DOT><<<g, 128, kTmaSmemBytes, s>>>(*a.tm_own, *a.tm_back, a);
+}
+
 void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
-    const int g = bsr_grid_blocks(a.nn);
     note_launch();
+    if (a.tm_own) {
+        const int g = bsr_grid_blocks(a.nn, true);
+        if (mode == FM_APPLY) {
+            if (dot) launch_bsr_tma<FM_APPLY, true>(g, a, s);
+            else launch_bsr_tma<FM_APPLY, false>(g, a, s);
+        } else if (mode == FM_SMOOTH) {
+            if (dot) launch_bsr_tma<FM_SMOOTH, true>(g, a, s);
+            else launch_bsr_tma<FM_SMOOTH, false>(g, a, s);
+        } else {
+            launch_bsr_tma<FM_RESID, false>(g, a, s);
+        }
+        return;
+    }
+    const int g = bsr_grid_blocks(a.nn, false);
     if (a.nn >= kBsrStreamLevel) {
         if (mode == FM_APPLY) {
             if (dot) k_bsr<FM_APPLY, true, 256><<<g, 256, 0, s>>>(a);
@@ -578,6 +736,40 @@ void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
     } else {
         k_bsr_ks<FM_RESID, false><<<g, 256, 0, s>>>(a);
     }
+}
+
+// Tensor maps of a level's FP32 planes, [126][ps] row-major (x = node, y = plane):
+// the own-block box (64 nodes x 126 planes) and the backward box (68 x 9).
+int encode_bsr_maps(Level& l) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode enc = nullptr;
+    if (!enc) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return GMG_ERR_CUDA;
+        enc = reinterpret_cast<Encode>(fn);
+    }
+    if (l.ps % 4 != 0 || (reinterpret_cast<uintptr_t>(l.A32) & 15) != 0) return GMG_ERR_ARG;
+    const cuuint64_t dims[2] = {(cuuint64_t)l.ps, (cuuint64_t)kSymPlanes};
+    const cuuint64_t strides[1] = {(cuuint64_t)l.ps * sizeof(float)};
+    const cuuint32_t box_own[2] = {(cuuint32_t)kTmaNodes, (cuuint32_t)kSymPlanes};
+    const cuuint32_t box_back[2] = {(cuuint32_t)kTmaBackW, 9u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    if (enc(&l.tm_own, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, l.A32, dims, strides, box_own, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return GMG_ERR_CUDA;
+    if (enc(&l.tm_back, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, l.A32, dims, strides, box_back, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return GMG_ERR_CUDA;
+    l.tma = true;
+    return GMG_OK;
 }
 
 void launch_bsr_smooth0(const BsrArgs& a, cudaStream_t s) {

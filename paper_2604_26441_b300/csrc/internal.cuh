@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap (type only; the encoder is fetched through the runtime)
+
 #include "gmg.h"
 
 namespace gmg {
@@ -72,7 +74,11 @@ struct Level {
     uint8_t* mask = nullptr;        // [nn] fixed-component bits
     float* invdiag = nullptr;       // [3nn] D^{-1} (levels >= 1), 0 on fixed DOFs
     double* A64 = nullptr;          // [243 nn] Galerkin operator planes, FP64 (levels >= 1)
-    float* A32 = nullptr;           // [126 nn] FP32 diagonal + forward blocks (levels >= 1)
+    float* A32 = nullptr;           // [126 ps] FP32 diagonal + forward blocks (levels >= 1)
+    long long ps = 0;               // plane stride of A32: nn rounded up to 4 (16-byte aligned planes)
+    bool tma = false;               // operator streamed by the TMA-staged kernel (tm_own / tm_back valid)
+    CUtensorMap tm_own{};           // A32 as a [126][ps] FP32 tensor, box 126 planes x 64 nodes
+    CUtensorMap tm_back{};          // same tensor, box 9 planes x 68 nodes
     float* x = nullptr;             // [3nn] smoother iterate / V-cycle output (levels >= 1)
     float* x2 = nullptr;            // [3nn] ping-pong partner of x
     float* b = nullptr;             // [3nn] right-hand side (levels >= 1)
@@ -89,7 +95,8 @@ struct Level {
 struct CoarseLevel {
     int nx, ny, nz, nn;
     const uint8_t* mask;
-    const float* A;          // symmetric half storage, [126][nn]
+    const float* A;          // symmetric half storage, [126][ps]
+    int ps;
     const float* invdiag;
     float *x, *x2, *b, *t, *d;
     const double* coef;
@@ -158,6 +165,7 @@ struct gmg_handle {
     double eps = 0.0;
     gmg::CoarseFused cf{};                      // fused lower V-cycle (levels cf.start..L-1)
     bool use_fused = false;
+    int* kerr = nullptr;                        // sticky error word of the TMA-staged operator
     int fused_blocks = 0;
     std::vector<void*> allocs;                  // every device allocation, freed by gmg_destroy
     void* pinned = nullptr;                     // pinned host block (sc_host)
@@ -198,6 +206,7 @@ void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t*
 struct BsrArgs {
     int nx, ny, nz;
     long long nn;
+    long long ps;                // plane stride of A
     const float* A;
     const float* invdiag;
     const uint8_t* mask;
@@ -209,8 +218,15 @@ struct BsrArgs {
     const double* coef;
     int step;
     double* partial;
+    int* err;                    // sticky error word (a TMA wait that gave up)
+    const CUtensorMap* tm_own;   // non-null: stream through the TMA-staged kernel
+    const CUtensorMap* tm_back;
 };
-int bsr_grid_blocks(long long nn);
+// Blocks (= dot partials) of the operator launch for a level of nn nodes: 64
+// nodes per block for the TMA-staged and K-split kernels, 256 for streaming.
+int bsr_grid_blocks(long long nn, bool tma);
+// Encodes the two tensor maps of a level's FP32 planes; GMG_OK or an error code.
+int encode_bsr_maps(Level& l);
 void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s);
 void launch_bsr_smooth0(const BsrArgs& a, cudaStream_t s);
 

@@ -284,8 +284,8 @@ __global__ void k_galerkin_rap(int fnx, int fny, int fnz, long long fnn, const d
 // Zero rows/columns of fixed DOFs and out-of-grid neighbours, form D^{-1} from
 // the self block, and write the FP32 copy used by the solve: the diagonal block
 // and the 13 forward neighbour blocks (slots 13..26) of the symmetric operator.
-__global__ void k_finish_bsr(int nx, int ny, int nz, long long nn, const uint8_t* mask, double* A64, float* A32,
-                             float* invdiag) {
+__global__ void k_finish_bsr(int nx, int ny, int nz, long long nn, long long ps, const uint8_t* mask, double* A64,
+                             float* A32, float* invdiag) {
     const long long NX = nx + 1, NY = ny + 1, NZ = nz + 1;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
@@ -300,7 +300,7 @@ __global__ void k_finish_bsr(int nx, int ny, int nz, long long nn, const uint8_t
                     double v = A64[q];
                     if (!in || fixed_bit(mr, r) || fixed_bit(mc, c)) v = 0.0;
                     A64[q] = v;
-                    if (s >= kSelfSlot) A32[(long long)((s - kSelfSlot) * 9 + r * 3 + c) * nn + n] = (float)v;
+                    if (s >= kSelfSlot) A32[(long long)((s - kSelfSlot) * 9 + r * 3 + c) * ps + n] = (float)v;
                 }
         }
         for (int r = 0; r < 3; ++r) {
@@ -553,7 +553,7 @@ void launch_galerkin_rap(const Level& f, const Level& c, cudaStream_t s) {
 
 void launch_finish_bsr(Level& l, cudaStream_t s) {
     note_launch();
-    k_finish_bsr<<<grid_for(l.nn), 256, 0, s>>>(l.nx, l.ny, l.nz, l.nn, l.mask, l.A64, l.A32, l.invdiag);
+    k_finish_bsr<<<grid_for(l.nn), 256, 0, s>>>(l.nx, l.ny, l.nz, l.nn, l.ps, l.mask, l.A64, l.A32, l.invdiag);
 }
 
 void launch_smoother_coef(double* coef, const double* lam, int kind, int degree, double omega, double alpha,

@@ -41,6 +41,36 @@ def test_status_strings_and_defaults(lib):
     lib.gmg_default_options(ctypes.byref(o))
     assert o.levels == 4 and o.degree == 2 and o.power_iters_fine == 20 and o.power_iters_coarse == 10
     assert abs(o.cheb_alpha - 1 / 30) < 1e-15 and o.chol_cutoff == 5000
+    assert o.fused_coarse_nodes == 4096 and o.bsr_tma_nodes == 0
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of gmg_options / gmg_info / gmg_grid / gmg_bc have the
+    sizes and field offsets a C compiler gives the declarations in gmg.h."""
+    import shutil
+    import subprocess
+    from paper_2604_26441_b300 import gmg
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"gmg_options": gmg._Options, "gmg_info": gmg._Info, "gmg_grid": gmg._Grid, "gmg_bc": gmg._BC}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gmg.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                              check=True).stdout.splitlines())
+    for cname, cls in structs.items():
+        assert int(out[cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(out[f"{cname}.{fname}"]) == getattr(cls, fname).offset, f"{cname}.{fname}"
 
 
 def test_argument_errors_without_device(lib):
