@@ -19,7 +19,10 @@
 // (x0-1+tx, y0-1+ty).  Operands stream through shared-memory rings filled by
 // cp.async (LDGSTS) several steps ahead: node planes and element moduli three
 // layers ahead, smoother operands two planes ahead, so HBM latency is covered
-// without register staging.  Per element layer a thread
+// without register staging.  (TMA boxes do not fit here: a node row is 3(nx+1)
+// floats, not a multiple of 16 bytes, so every row would be its own small box,
+// and a TMA instruction takes warp-uniform operands, so the boxes of a step
+// would issue one at a time.)  Per element layer a thread
 //   - reads the four corner nodes of the layer's top plane from the ring,
 //   - forms the x/y difference sums of the top plane once and reuses them for
 //     the next layer (the Z mode is summed from per-corner z-differences),
@@ -28,7 +31,9 @@
 //     expands to the four corners, sums the four cells around each node with a
 //     warp shuffle (x) and a shared-memory exchange (y), and runs the epilogue
 //     (apply / smoother step / residual) for its node one step later.
-// No atomics: every output is formed by its owner in a fixed order.
+// The x and y components travel as packed f32x2 pairs, and the loop takes two
+// layers per trip so that the layer state alternates between two register
+// sets.  No atomics: every output is formed by its owner in a fixed order.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -60,28 +65,58 @@ __device__ __forceinline__ double block_sum(double v, int tid) {
     return s;
 }
 
-// 4-byte asynchronous global -> shared copy; when `valid` is false nothing is
-// read and the destination is filled with zero.
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    const int sz = valid ? 4 : 0;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(sz) : "memory");
+// ---------------------------------------------------------------------------
+// Packed arithmetic.  A node value is held as V3 = {(u_x, u_y) as an f32x2
+// pair, u_z}: every componentwise add or subtract is one packed instruction for
+// x and y plus one scalar for z (sm_100+ FADD2 / FFMA2).  a - b is formed as
+// fma(b, -1, a), which rounds exactly like the subtraction.
+// ---------------------------------------------------------------------------
+struct V3 {
+    float2 xy;
+    float z;
+};
+__device__ __forceinline__ V3 vadd(const V3& a, const V3& b) { return {__fadd2_rn(a.xy, b.xy), a.z + b.z}; }
+__device__ __forceinline__ V3 vsub(const V3& a, const V3& b) {
+    return {__ffma2_rn(b.xy, make_float2(-1.f, -1.f), a.xy), a.z - b.z};
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
+__device__ __forceinline__ V3 vld(const float* p) { return {make_float2(p[0], p[1]), p[2]}; }
+__device__ __forceinline__ float comp(const V3& v, int c) { return c == 0 ? v.xy.x : (c == 1 ? v.xy.y : v.z); }
+__device__ __forceinline__ void set_comp(V3& v, int c, float x) {
+    if (c == 0) v.xy.x = x;
+    else if (c == 1) v.xy.y = x;
+    else v.z = x;
+}
 
 // Difference sums of four corner values (x fastest), formed from node
-// differences first: q1 = x-difference, q2 = y-difference, q3 = xy-difference
-// (signs of the corner coordinates).
-__device__ __forceinline__ void face_diffs(const float u00, const float u10, const float u01, const float u11, float q[4]) {
-    const float dx0 = u10 - u00, dx1 = u11 - u01;
-    q[1] = dx0 + dx1;
-    q[2] = (u01 - u00) + (u11 - u10);
-    q[3] = dx1 - dx0;
+// differences first: q[1] = x-difference, q[2] = y-difference, q[3] =
+// xy-difference (signs of the corner coordinates).
+__device__ __forceinline__ void face_diffs(const V3 c[4], V3 q[4]) {
+    const V3 dx0 = vsub(c[1], c[0]), dx1 = vsub(c[3], c[2]);
+    q[1] = vadd(dx0, dx1);
+    q[2] = vadd(vsub(c[2], c[0]), vsub(c[3], c[1]));
+    q[3] = vsub(dx1, dx0);
 }
 
+// State carried from one element layer to the next: the corners and the x/y
+// difference sums of the shared face, and the top-face quantities of the layer.
+struct Layer {
+    V3 C[4];
+    V3 Q[4];  // Q[0] unused
+    V3 T[4];
+    float E;
+};
+
+// 4-byte asynchronous global -> shared copy; when `valid` is false nothing is
+// read and the destination is filled with zero.
+__device__ __forceinline__ void cp_async4(unsigned dst, const float* gmem, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(gmem), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
 // Ring slots of the shared-memory pipelines (lookahead 3 for planes and
-// moduli, 2 for the epilogue operands, which are read one step late).
+// moduli, 2 for the epilogue operands, which are read one step late).  Slots are
+// indexed by the step relative to the block's first layer.
 constexpr int kRing = 4;
 
 template <int BX, int BY, int MODE, bool DOT>
@@ -93,22 +128,24 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
     constexpr int OWN = (BX - 1) * (BY - 1);    // owned nodes per block
     constexpr bool EPI_B = MODE != FM_APPLY;
     constexpr bool EPI_D = MODE == FM_SMOOTH;
-    __shared__ float sp[kRing][PLANE];                         // node planes
-    __shared__ float sE[kRing][NT];                            // element moduli per layer
+    __shared__ float sp[kRing][PLANE];                            // node planes
+    __shared__ float sE[kRing][NT];                               // element moduli per layer
     __shared__ float sB[EPI_B ? kRing : 1][EPI_B ? OWN * 3 : 1];  // right-hand side at owned nodes
     __shared__ float sD[EPI_D ? kRing : 1][EPI_D ? OWN * 3 : 1];  // previous increment at owned nodes
-    __shared__ float sx[2][BY][BX * 4];                        // y-exchange: 3 row sums + modulus sum
+    __shared__ float4 sx[2][BY][BX];                              // y-exchange: 3 row sums + modulus sum
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
-    const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1, NXY = NX * NY, NEXY = a.nx * a.ny;
+    const int nx = a.nx;
+    const int NX = nx + 1, NY = a.ny + 1, NZ = a.nz + 1, NXY = NX * NY, NEXY = nx * a.ny;
     const int x0 = blockIdx.x * (BX - 1), y0 = blockIdx.y * (BY - 1);
     const int k0 = blockIdx.z * zchunk, k1 = min(k0 + zchunk, NZ);
+    const int kb = k0 - 1;                         // slot of plane / layer p is (p - kb) mod kRing
     const int cx = x0 - 1 + tx, cy = y0 - 1 + ty;  // this column's cell; owned node (cx+1, cy+1)
     const int ox = cx + 1, oy = cy + 1;
     const bool owner = tx < BX - 1 && ty < BY - 1 && ox < NX && oy < NY;
-    const bool cell_in = cx >= 0 && cx < a.nx && cy >= 0 && cy < a.ny;
-    const int onode_base = oy * NX + ox, e_base = cy * a.nx + cx;
-    const int own_slot = ty * (BX - 1) + tx;  // owned-node index inside the block (owners only)
+    const bool cell_in = cx >= 0 && cx < nx && cy >= 0 && cy < a.ny;
+    const int onode_base = oy * NX + ox, e_base = cy * nx + cx;
+    const int own3 = 3 * (ty * (BX - 1) + tx);  // owned-node slot inside the block (owners only)
 
     // per-thread plane copy slots: offset inside a global plane and validity
     int cp_goff[NCP];
@@ -121,6 +158,8 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
         cp_ok[q] = idx < PLANE && px >= 0 && px < NX && py >= 0 && py < NY;
         cp_goff[q] = cp_ok[q] ? 3 * (py * NX + px) + c3 % 3 : 0;
     }
+    const unsigned sp_dst = smem_u32(&sp[0][tid]), sE_dst = smem_u32(&sE[0][tid]);
+    const unsigned sB_dst = smem_u32(&sB[0][EPI_B ? own3 : 0]), sD_dst = smem_u32(&sD[0][EPI_D ? own3 : 0]);
     const float cd = EPI_D ? (float)a.coef[2 * a.step] : 0.f;
     const float ca = EPI_D ? (float)a.coef[2 * a.step + 1] : 0.f;
     const bool need_d = EPI_D && cd != 0.f;
@@ -128,10 +167,10 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
     auto copy_plane = [&](int pz) {
         const bool zok = pz >= 0 && pz < NZ;
         const float* base = a.xin + 3 * (zok ? pz : 0) * NXY;
-        float* dst = sp[pz & 3];
+        const unsigned dst = sp_dst + 4u * (unsigned)(((pz - kb) & (kRing - 1)) * PLANE);
 #pragma unroll
         for (int q = 0; q < NCP; ++q)
-            if (tid + q * NT < PLANE) cp_async4(dst + tid + q * NT, base + cp_goff[q], zok && cp_ok[q]);
+            if (tid + q * NT < PLANE) cp_async4(dst + 4u * q * NT, base + cp_goff[q], zok && cp_ok[q]);
     };
     // one commit group per step j: node plane j+4, modulus layer j+3, epilogue plane j+2
     auto issue = [&](int j) {
@@ -139,20 +178,23 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
         const int le = j + 3;
         if (le < k1) {
             const bool ok = cell_in && le >= 0 && le < a.nz;
-            cp_async4(&sE[le & 3][tid], a.E + (ok ? e_base + le * NEXY : 0), ok);
+            cp_async4(sE_dst + 4u * (unsigned)(((le - kb) & (kRing - 1)) * NT), a.E + (ok ? e_base + le * NEXY : 0),
+                      ok);
         }
         const int pe = j + 2;
         if (EPI_B && owner && pe >= k0 && pe < k1) {
-            const int n3 = 3 * (onode_base + pe * NXY);
-            float* db = &sB[pe & 3][3 * own_slot];
-            cp_async4(db + 0, a.b + n3 + 0, true);
-            cp_async4(db + 1, a.b + n3 + 1, true);
-            cp_async4(db + 2, a.b + n3 + 2, true);
+            const int slot = (pe - kb) & (kRing - 1);
+            const float* src = a.b + 3 * (onode_base + pe * NXY);
+            const unsigned db = sB_dst + 4u * (unsigned)(slot * OWN * 3);
+            cp_async4(db, src, true);
+            cp_async4(db + 4u, src + 1, true);
+            cp_async4(db + 8u, src + 2, true);
             if (EPI_D && need_d) {
-                float* dd = &sD[pe & 3][3 * own_slot];
-                cp_async4(dd + 0, a.dold + n3 + 0, true);
-                cp_async4(dd + 1, a.dold + n3 + 1, true);
-                cp_async4(dd + 2, a.dold + n3 + 2, true);
+                const float* srd = a.dold + 3 * (onode_base + pe * NXY);
+                const unsigned dd = sD_dst + 4u * (unsigned)(slot * OWN * 3);
+                cp_async4(dd, srd, true);
+                cp_async4(dd + 4u, srd + 1, true);
+                cp_async4(dd + 8u, srd + 2, true);
             }
         }
         cp_commit();
@@ -163,120 +205,106 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
     };
 
     // ---- prologue: bottom plane k0-1 (own group), then the groups of steps k0-4 .. k0-2
-    copy_plane(k0 - 1);
+    copy_plane(kb);
     cp_commit();
     issue(k0 - 4);
     issue(k0 - 3);
     issue(k0 - 2);
     uint8_t mk0 = 7, mk1 = load_mask(k0);  // masks of planes kl and kl+1 at step kl
 
-    float Qb[4][3] = {}, Cb[4][3] = {}, Tprev[4][3] = {};
+    Layer s0, s1;
     asm volatile("cp.async.wait_group 3;\n" ::: "memory");
     __syncthreads();
     {
-        // bottom plane of the first layer
-        const float* pl = sp[(k0 - 1) & 3];
+        const float* pl = sp[0];
+        s0.C[0] = vld(pl + ty * ROW + 3 * tx);
+        s0.C[1] = vld(pl + ty * ROW + 3 * tx + 3);
+        s0.C[2] = vld(pl + (ty + 1) * ROW + 3 * tx);
+        s0.C[3] = vld(pl + (ty + 1) * ROW + 3 * tx + 3);
+        face_diffs(s0.C, s0.Q);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            Cb[0][c] = pl[ty * ROW + 3 * tx + c];
-            Cb[1][c] = pl[ty * ROW + 3 * (tx + 1) + c];
-            Cb[2][c] = pl[(ty + 1) * ROW + 3 * tx + c];
-            Cb[3][c] = pl[(ty + 1) * ROW + 3 * (tx + 1) + c];
-            float q[4];
-            face_diffs(Cb[0][c], Cb[1][c], Cb[2][c], Cb[3][c], q);
-#pragma unroll
-            for (int i = 1; i < 4; ++i) Qb[i][c] = q[i];
-        }
+        for (int q = 0; q < 4; ++q) s0.T[q] = V3{make_float2(0.f, 0.f), 0.f};
+        s0.E = 0.f;
     }
-    float Eprev = 0.f;
     bool pending = false;
-    int pend_k = 0;
-    float R1[3] = {0.f, 0.f, 0.f}, eR1 = 0.f;
-    float un_pend[3] = {0.f, 0.f, 0.f}, un_next[3] = {0.f, 0.f, 0.f};
+    V3 R1{make_float2(0.f, 0.f), 0.f}, un_pend{make_float2(0.f, 0.f), 0.f};
+    float eR1 = 0.f;
     uint8_t m_pend = 7;
     DSAcc dotv;
 
-    auto finish = [&]() {
-        // complete the 4-cell sum with the row published by the thread above
-        const float* r0 = &sx[pend_k & 1][ty + 1][4 * tx];
-        const float y[3] = {R1[0] + r0[0], R1[1] + r0[1], R1[2] + r0[2]};
-        const int n = onode_base + pend_k * NXY;
+    // epilogue of the owned node of plane kp: its 4-cell sums R1 + the row above
+    auto finish = [&](int kp) {
+        const float4 up = sx[kp & 1][ty + 1][tx];
+        const float y[3] = {R1.xy.x + up.x, R1.xy.y + up.y, R1.z + up.z};
+        const int n = onode_base + kp * NXY;
         float* out = a.out + 3 * n;
         if (MODE == FM_APPLY) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const float v = fixed_bit(m_pend, c) ? 0.f : y[c];
                 out[c] = v;
-                if (DOT) dotv.add_prod(un_pend[c], v);
+                if (DOT) dotv.add_prod(comp(un_pend, c), v);
             }
-        } else if (MODE == FM_RESID) {
-            const float* bb = &sB[pend_k & 3][3 * own_slot];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) out[c] = fixed_bit(m_pend, c) ? 0.f : bb[c] - y[c];
         } else {
-            const float* bb = &sB[pend_k & 3][3 * own_slot];
-            const float* dd = &sD[pend_k & 3][3 * own_slot];
-            const float inv = __frcp_rn(a.kd * (eR1 + r0[3]));
+            const int slot = (kp - kb) & (kRing - 1);
+            const float* bb = &sB[EPI_B ? slot : 0][EPI_B ? own3 : 0];
+            if (MODE == FM_RESID) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float xn = 0.f, dn = 0.f;
-                if (!fixed_bit(m_pend, c)) {
-                    dn = ca * inv * (bb[c] - y[c]);
-                    if (need_d) dn = fmaf(cd, dd[c], dn);
-                    xn = un_pend[c] + dn;
-                    if (DOT) dotv.add_prod(bb[c], xn);
+                for (int c = 0; c < 3; ++c) out[c] = fixed_bit(m_pend, c) ? 0.f : bb[c] - y[c];
+            } else {
+                const float* dd = &sD[EPI_D ? slot : 0][EPI_D ? own3 : 0];
+                const float inv = __frcp_rn(a.kd * (eR1 + up.w));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float xn = 0.f, dn = 0.f;
+                    if (!fixed_bit(m_pend, c)) {
+                        dn = ca * inv * (bb[c] - y[c]);
+                        if (need_d) dn = fmaf(cd, dd[c], dn);
+                        xn = comp(un_pend, c) + dn;
+                        if (DOT) dotv.add_prod(bb[c], xn);
+                    }
+                    out[c] = xn;
+                    if (a.dnew) a.dnew[3 * n + c] = dn;
                 }
-                out[c] = xn;
-                if (a.dnew) a.dnew[3 * n + c] = dn;
             }
         }
     };
 
-    for (int kl = k0 - 1; kl < k1; ++kl) {
-        cp_wait2();  // the group of step kl-3 (plane kl+1, modulus kl, epilogue kl-1) has landed
+    // one element layer kl: bottom face in `in`, top face into `out`
+    auto layer = [&](const int kl, const Layer& in, Layer& out) {
+        asm volatile("cp.async.wait_group 2;\n" ::: "memory");  // group of step kl-3 has landed
         __syncthreads();
-        if (pending && owner) finish();
+        if (pending && owner) finish(kl - 1);
         pending = false;
-        issue(kl);  // writes the slot of plane kl, last read (as a top plane) in step kl-1
+        issue(kl);  // overwrites the slots of plane kl and layer kl-1, last read in step kl-1
         const uint8_t mcur = mk0;
         mk0 = mk1;
         mk1 = load_mask(kl + 2);
-        const float E = sE[kl & 3][tid];
-        const bool fin = kl >= k0;
-        // top plane: raw corners and difference sums
-        const float* pl = sp[(kl + 1) & 3];
-        float Qt[4][3], Ct[4][3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            Ct[0][c] = pl[ty * ROW + 3 * tx + c];
-            Ct[1][c] = pl[ty * ROW + 3 * (tx + 1) + c];
-            Ct[2][c] = pl[(ty + 1) * ROW + 3 * tx + c];
-            Ct[3][c] = pl[(ty + 1) * ROW + 3 * (tx + 1) + c];
-            float q[4];
-            face_diffs(Ct[0][c], Ct[1][c], Ct[2][c], Ct[3][c], q);
-            Qt[0][c] = 0.f;
-#pragma unroll
-            for (int i = 1; i < 4; ++i) Qt[i][c] = q[i];
+        {
+            const float* pl = sp[(kl + 1 - kb) & (kRing - 1)];
+            out.C[0] = vld(pl + ty * ROW + 3 * tx);
+            out.C[1] = vld(pl + ty * ROW + 3 * tx + 3);
+            out.C[2] = vld(pl + (ty + 1) * ROW + 3 * tx);
+            out.C[3] = vld(pl + (ty + 1) * ROW + 3 * tx + 3);
+            face_diffs(out.C, out.Q);
         }
-        // modes v[monomial][c]: Z from per-corner z-differences, the others from
-        // the x/y difference sums of the two faces
-        float v[8][3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float z00 = Ct[0][c] - Cb[0][c], z10 = Ct[1][c] - Cb[1][c];
-            const float z01 = Ct[2][c] - Cb[2][c], z11 = Ct[3][c] - Cb[3][c];
-            v[0][c] = 0.f;
-            v[4][c] = (z00 + z10) + (z01 + z11);
+        out.E = sE[(kl - kb) & (kRing - 1)][tid];
+        // modes: Z from per-corner z-differences, the others from the x/y
+        // difference sums of the two faces
+        V3 v[8];
+        {
+            const V3 z00 = vsub(out.C[0], in.C[0]), z10 = vsub(out.C[1], in.C[1]);
+            const V3 z01 = vsub(out.C[2], in.C[2]), z11 = vsub(out.C[3], in.C[3]);
+            v[4] = vadd(vadd(z00, z10), vadd(z01, z11));
 #pragma unroll
             for (int q = 1; q < 4; ++q) {
-                v[q][c] = Qt[q][c] + Qb[q][c];
-                v[q + 4][c] = Qt[q][c] - Qb[q][c];
+                v[q] = vadd(out.Q[q], in.Q[q]);
+                v[q + 4] = vsub(out.Q[q], in.Q[q]);
             }
         }
         // w = E G v, class by class (the constant monomial carries no energy)
-        float w[8][3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) w[0][c] = 0.f;
+        V3 w[8];
+        w[0] = V3{make_float2(0.f, 0.f), 0.f};
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
 #pragma unroll
@@ -288,58 +316,60 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
                 for (int j = 0; j < 3; ++j) {
                     const int mj = mono(s, j);
                     if (mj == 0) continue;
-                    acc = fmaf(G.g[s * 9 + i * 3 + j], v[mj][j], acc);
+                    acc = fmaf(G.g[s * 9 + i * 3 + j], comp(v[mj], j), acc);
                 }
-                w[mi][i] = E * acc;
+                set_comp(w[mi], i, acc);
             }
         }
+        const float2 E2 = make_float2(out.E, out.E);
+#pragma unroll
+        for (int m = 1; m < 8; ++m) w[m] = V3{__fmul2_rn(E2, w[m].xy), out.E * w[m].z};
         // back to face quantities: top = w + w_z, bottom = w - w_z
-        float T[4][3], B[4][3];
+        V3 Bf[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                T[q][c] = w[q][c] + w[q + 4][c];
-                B[q][c] = w[q][c] - w[q + 4][c];
-            }
-        if (fin) {
-            // plane kl is complete for this cell: S = top of layer kl-1 + bottom of layer kl,
-            // expanded to the four corners and summed over the four cells of each node
-            float r1[3], r0[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float S0 = Tprev[0][c] + B[0][c], S1 = Tprev[1][c] + B[1][c];
-                const float S2 = Tprev[2][c] + B[2][c], S3 = Tprev[3][c] + B[3][c];
-                const float p = S0 - S2, qd = S1 - S3, r = S0 + S2, sd = S1 + S3;
-                const float c00 = p - qd, c10 = p + qd, c01 = r - sd, c11 = r + sd;
-                r1[c] = c11 + __shfl_down_sync(0xffffffffu, c01, 1, BX);
-                r0[c] = c10 + __shfl_down_sync(0xffffffffu, c00, 1, BX);
-            }
-            const float es = Eprev + E;
+        for (int q = 0; q < 4; ++q) {
+            out.T[q] = vadd(w[q], w[q + 4]);
+            Bf[q] = vsub(w[q], w[q + 4]);
+        }
+        if (kl >= k0) {
+            // plane kl is complete for this cell: S = top of layer kl-1 + bottom of
+            // layer kl, expanded to the four corners and summed over the four cells
+            // of each node (x by warp shuffle, y through shared memory)
+            const V3 S0 = vadd(in.T[0], Bf[0]), S1 = vadd(in.T[1], Bf[1]);
+            const V3 S2 = vadd(in.T[2], Bf[2]), S3 = vadd(in.T[3], Bf[3]);
+            const V3 p = vsub(S0, S2), qd = vsub(S1, S3), r = vadd(S0, S2), sd = vadd(S1, S3);
+            const V3 c00 = vsub(p, qd), c10 = vadd(p, qd), c01 = vsub(r, sd), c11 = vadd(r, sd);
+            V3 n01, n00;
+            n01.xy.x = __shfl_down_sync(0xffffffffu, c01.xy.x, 1, BX);
+            n01.xy.y = __shfl_down_sync(0xffffffffu, c01.xy.y, 1, BX);
+            n01.z = __shfl_down_sync(0xffffffffu, c01.z, 1, BX);
+            n00.xy.x = __shfl_down_sync(0xffffffffu, c00.xy.x, 1, BX);
+            n00.xy.y = __shfl_down_sync(0xffffffffu, c00.xy.y, 1, BX);
+            n00.z = __shfl_down_sync(0xffffffffu, c00.z, 1, BX);
+            R1 = vadd(c11, n01);
+            const V3 r0 = vadd(c10, n00);
+            const float es = in.E + out.E;
             const float er = es + __shfl_down_sync(0xffffffffu, es, 1, BX);
-            float* dst = &sx[kl & 1][ty][4 * tx];
-            dst[0] = r0[0]; dst[1] = r0[1]; dst[2] = r0[2]; dst[3] = er;
+            sx[kl & 1][ty][tx] = make_float4(r0.xy.x, r0.xy.y, r0.z, er);
             pending = true;
-            pend_k = kl;
-            R1[0] = r1[0]; R1[1] = r1[1]; R1[2] = r1[2];
             eR1 = er;
-            un_pend[0] = un_next[0]; un_pend[1] = un_next[1]; un_pend[2] = un_next[2];
+            un_pend = in.C[3];
             m_pend = mcur;
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                Tprev[q][c] = T[q][c];
-                Qb[q][c] = Qt[q][c];
-                Cb[q][c] = Ct[q][c];
-            }
-        Eprev = E;
-        un_next[0] = Ct[3][0]; un_next[1] = Ct[3][1]; un_next[2] = Ct[3][2];
+    };
+
+    // layers k0-1 .. k1-1, two per trip so that the layer state alternates
+    // between s0 and s1 instead of being copied
+    int kl = kb;
+#pragma unroll 1
+    for (; kl + 1 < k1; kl += 2) {
+        layer(kl, s0, s1);
+        layer(kl + 1, s1, s0);
     }
+    if (kl < k1) layer(kl, s0, s1);
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
-    if (pending && owner) finish();
+    if (pending && owner) finish(k1 - 1);
     if (DOT) {
         const double s = block_sum<NT>(dotv.value(), tid);
         if (tid == 0) a.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;

@@ -17,6 +17,7 @@
 // Reductions are deterministic: every block writes one partial sum, and a
 // single-block finaliser adds the partials in a fixed order.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -171,36 +172,6 @@ __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
         const double s = block_sum<NTB>(dotv.value(), threadIdx.x);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = s;
     }
-}
-
-// ---- TMA and mbarrier primitives (inline PTX) ------------------------------
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// 2D tiled TMA load of the box at (x = node, y = plane) into shared memory,
-// completing on `bar` (x must be a multiple of 4: 16-byte aligned start).
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -738,36 +709,40 @@ void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
     }
 }
 
-// Tensor maps of a level's FP32 planes, [126][ps] row-major (x = node, y = plane):
-// the own-block box (64 nodes x 126 planes) and the backward box (68 x 9).
-int encode_bsr_maps(Level& l) {
+bool encode_f32_map(CUtensorMap* map, const float* base, int rank, const unsigned long long* dims,
+                    const unsigned* box) {
     using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
     static Encode enc = nullptr;
-    if (!enc) {
+    static std::once_flag once;
+    std::call_once(once, [] {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return GMG_ERR_CUDA;
-        enc = reinterpret_cast<Encode>(fn);
-    }
-    if (l.ps % 4 != 0 || (reinterpret_cast<uintptr_t>(l.A32) & 15) != 0) return GMG_ERR_ARG;
-    const cuuint64_t dims[2] = {(cuuint64_t)l.ps, (cuuint64_t)kSymPlanes};
-    const cuuint64_t strides[1] = {(cuuint64_t)l.ps * sizeof(float)};
-    const cuuint32_t box_own[2] = {(cuuint32_t)kTmaNodes, (cuuint32_t)kSymPlanes};
-    const cuuint32_t box_back[2] = {(cuuint32_t)kTmaBackW, 9u};
-    const cuuint32_t estr[2] = {1u, 1u};
-    if (enc(&l.tm_own, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, l.A32, dims, strides, box_own, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return GMG_ERR_CUDA;
-    if (enc(&l.tm_back, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, l.A32, dims, strides, box_back, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return GMG_ERR_CUDA;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            enc = reinterpret_cast<Encode>(fn);
+    });
+    if (!enc || rank < 1 || rank > 2 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+    const cuuint64_t gd[2] = {dims[0], rank > 1 ? dims[1] : 1};
+    const cuuint64_t gs[1] = {dims[0] * sizeof(float)};
+    const cuuint32_t bx[2] = {box[0], rank > 1 ? box[1] : 1};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<float*>(base), gd, gs, bx, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps of a level's FP32 planes, [126][ps] row-major (x = node, y = plane):
+// the own-block box (64 nodes x 126 planes) and the backward box (68 x 9).
+int encode_bsr_maps(Level& l) {
+    if (l.ps % 4 != 0) return GMG_ERR_ARG;
+    const unsigned long long dims[2] = {(unsigned long long)l.ps, (unsigned long long)kSymPlanes};
+    const unsigned box_own[2] = {(unsigned)kTmaNodes, (unsigned)kSymPlanes};
+    const unsigned box_back[2] = {(unsigned)kTmaBackW, 9u};
+    if (!encode_f32_map(&l.tm_own, l.A32, 2, dims, box_own)) return GMG_ERR_CUDA;
+    if (!encode_f32_map(&l.tm_back, l.A32, 2, dims, box_back)) return GMG_ERR_CUDA;
     l.tma = true;
     return GMG_OK;
 }

@@ -135,6 +135,53 @@ struct DSAcc {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// ---- TMA and mbarrier primitives (inline PTX, sm_90+ forms; this build targets sm_103a)
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Makes initialised mbarriers visible to the asynchronous (TMA) proxy.
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// Arrives once on `bar` and adds `bytes` to the transaction count of its phase.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// One bounded probe of phase `parity` of `bar` (true once that phase has completed).
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Tiled TMA loads into shared memory completing on `bar`.  The innermost
+// coordinate must be a multiple of 4 FP32 elements (16-byte aligned start);
+// coordinates outside the tensor read as zero.
+__device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* map, int x, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2}], [%3];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Host: tiled tensor map of an FP32 array, rank 1 (dims[0] elements, box[0]) or
+// rank 2 (dims[0] x dims[1], row pitch dims[0] elements, box[0] x box[1]).
+// Returns false when the driver entry point is unavailable or the encoder
+// rejects the geometry (e.g. an address that is not 16-byte aligned).
+bool encode_f32_map(CUtensorMap* map, const float* base, int rank, const unsigned long long* dims,
+                    const unsigned* box);
+
 }  // namespace gmg
 
 struct gmg_handle {
