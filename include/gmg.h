@@ -91,6 +91,10 @@ typedef struct {
                                     operator planes as TMA-staged shared-memory tiles;
                                     <= 0 (default) = never: levels of >= 65536 nodes stream one
                                     thread per node, smaller ones use the K-split kernel */
+    int device_loop;             /* 1 (default): PCG iterations run as one CUDA graph with a
+                                    conditional while node, returning to the host only for the
+                                    FP64 acceptance test; 0: one host round trip per iteration.
+                                    Both run the same kernels in the same order. */
     void* stream;                /* cudaStream_t for all device work; NULL = default stream */
 } gmg_options;
 

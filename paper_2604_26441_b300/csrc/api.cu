@@ -483,6 +483,107 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     return GMG_OK;
 }
 
+// ---- PCG steps (Sec. "Outer Krylov Solver and Convergence Statement"), shared
+// by the host-driven loop and the captured graph ---------------------------------
+// z = V(r), rz = r . z, p = z
+void pcg_restart(gmg_handle* h) {
+    const long long n = 3 * h->lev[0].nn;
+    vcycle_level(h, 0, h->r, h->z, h->x2_0, SC_RZ, FIN_NONE);
+    cudaMemcpyAsync(h->p, h->z, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->stream);
+}
+// q = K p, alpha = rz / p.q, u += alpha p, r -= alpha q, ||r||^2
+void pcg_step(gmg_handle* h, double* u) {
+    const long long n = 3 * h->lev[0].nn;
+    level_apply(h, 0, h->p, h->q, SC_PQ, FIN_ALPHA);
+    launch_pcg_update(u, h->r, h->p, h->q, n, h->sc, h->partials, h->stream);
+    launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_RR, FIN_NONE, h->stream);
+}
+// z = V(r), beta = r.z / rz, p = z + beta p
+void pcg_direction(gmg_handle* h) {
+    const long long n = 3 * h->lev[0].nn;
+    vcycle_level(h, 0, h->r, h->z, h->x2_0, SC_RZNEW, FIN_BETA);
+    launch_p_update(h->p, h->z, n, h->sc, h->stream);
+}
+
+void loop_free(gmg_handle* h) {
+    if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
+    if (h->loop_graph) cudaGraphDestroy(h->loop_graph);
+    h->loop_exec = nullptr;
+    h->loop_graph = nullptr;
+    h->loop_u = nullptr;
+}
+
+// Captures the device-resident PCG loop for iterate u:
+//   restart; step; check; while (condition) { direction; step; check }
+// so that one graph launch runs PCG until the recursive residual passes the
+// tolerance (or the cap, or a non-finite scalar) with no host round trip; the
+// host then takes the FP64 acceptance decision.  The kernel sequence is that of
+// the host-driven loop, so both give bitwise-identical iterates.
+int loop_build(gmg_handle* h, double* u) {
+    loop_free(h);
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return GMG_ERR_CUDA;
+    }
+    const unsigned long long l0 = g_kernel_launches.load();
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
+    cudaGraph_t g = nullptr, body = nullptr, out = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaGraphConditionalHandle cond{};
+    unsigned long long l1 = l0, l2 = l0;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess && cudaGraphConditionalHandleCreate(&cond, g, 0, 0) == cudaSuccess;
+    if (ok) ok = cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+    if (ok) {
+        pcg_restart(h);
+        pcg_step(h, u);
+        launch_loop_check(h->sc, cond, h->stream);
+        l1 = g_kernel_launches.load();
+        cudaStreamCaptureStatus st{};
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode = nullptr;
+        ok = cudaStreamGetCaptureInfo(h->stream, &st, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess &&
+             st == cudaStreamCaptureStatusActive;
+        if (ok) ok = cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp) == cudaSuccess;
+        if (ok) ok = cudaStreamUpdateCaptureDependencies(h->stream, &cnode, nullptr, 1,
+                                                         cudaStreamSetCaptureDependencies) == cudaSuccess;
+        if (ok) body = cp.conditional.phGraph_out[0];
+        ok = (cudaStreamEndCapture(h->stream, &out) == cudaSuccess) && ok;
+    }
+    if (ok) {
+        ok = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+             cudaSuccess;
+        if (ok) {
+            pcg_direction(h);
+            pcg_step(h, u);
+            launch_loop_check(h->sc, cond, h->stream);
+            l2 = g_kernel_launches.load();
+            ok = cudaStreamEndCapture(h->stream, &body) == cudaSuccess;
+        }
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    h->stream = user;
+    g_kernel_launches.fetch_sub(g_kernel_launches.load() - l0);  // capturing launches nothing
+    cudaGetLastError();
+    if (!ok) {
+        if (g) cudaGraphDestroy(g);
+        return GMG_ERR_CUDA;
+    }
+    h->loop_graph = g;
+    h->loop_exec = ex;
+    h->loop_u = u;
+    h->loop_prefix_kernels = l1 - l0;
+    h->loop_body_kernels = l2 - l1;
+    return GMG_OK;
+}
+
 // Reports a timed-out wait of the TMA-staged operator or of the fused lower
 // V-cycle (both error words are sticky).
 int check_fused(gmg_handle* h) {
@@ -517,6 +618,7 @@ void gmg_default_options(gmg_options* o) {
     o->chol_cutoff = 5000;
     o->fused_coarse_nodes = 4096;
     o->bsr_tma_nodes = 0;
+    o->device_loop = 1;
     o->stream = nullptr;
 }
 
@@ -543,6 +645,8 @@ void gmg_destroy(gmg_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    loop_free(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (void* p : h->allocs)
         if (p) cudaFree(p);
     if (h->pinned) cudaFreeHost(h->pinned);
@@ -657,18 +761,50 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     sch[SC_UNZ] = 1.0;
     CU(cudaMemcpyAsync(h->sc + SC_UNZ, sch + SC_UNZ, sizeof(double), cudaMemcpyHostToDevice, s));
 
-    // z = V(r), rz = r . z, p = z
-    auto restart = [&]() {
-        vcycle_level(h, 0, h->r, h->z, h->x2_0, SC_RZ, FIN_NONE);
-        cudaMemcpyAsync(h->p, h->z, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
-    };
-    restart();
     const double nf = std::sqrt(sch[SC_FF]);
+    if (maxit > 0 && h->opt.device_loop && !h->loop_unavailable && h->loop_u != u) {
+        if (loop_build(h, u) != GMG_OK) h->loop_unavailable = true;  // e.g. no graph support: host loop
+    }
+    if (maxit > 0 && h->opt.device_loop && h->loop_exec && h->loop_u == u) {
+        // device-resident loop: one graph launch per convergence candidate
+        sch[SC_IT] = 0.0;
+        sch[SC_TOL] = tol;
+        sch[SC_MAXIT] = (double)maxit;
+        sch[SC_NF] = nf;
+        CU(cudaMemcpyAsync(h->sc + SC_IT, sch + SC_IT, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+        int k = 0;
+        while (true) {
+            CU(cudaGraphLaunch(h->loop_exec, s));
+            TRY(sync_scalars(h));
+            const int k_new = (int)sch[SC_IT];
+            note_launch(h->loop_prefix_kernels + h->loop_body_kernels * (unsigned long long)(k_new - k - 1));
+            k = k_new;
+            const double relr = std::sqrt(sch[SC_RR]) / nf;
+            inf.iterations = k;
+            inf.rel_residual_recursive = relr;
+            if (!std::isfinite(relr) || !std::isfinite(sch[SC_ALPHA])) {
+                inf.rel_residual = relr;
+                return finish(GMG_NONFINITE);
+            }
+            if (!(relr < tol)) break;  // the cap
+            TRY(true_residual(rel));
+            inf.rel_residual = rel;
+            if (rel < tol) return finish(GMG_OK);
+            if (!std::isfinite(rel)) return finish(GMG_NONFINITE);
+            ++inf.replacements;  // residual replacement (r now holds f - K u); restart the direction
+            if (k >= maxit) break;
+        }
+        TRY(true_residual(rel));
+        inf.rel_residual = rel;
+        CU(cudaGetLastError());
+        return finish(GMG_NOT_CONVERGED);
+    }
+
+    // host-driven loop (same kernels, one scalar read-back per iteration)
+    pcg_restart(h);
     int k = 0;
     while (k < maxit) {
-        level_apply(h, 0, h->p, h->q, SC_PQ, FIN_ALPHA);                   // q = K p, alpha = rz / pq
-        launch_pcg_update(u, h->r, h->p, h->q, n, h->sc, h->partials, s);  // u += a p, r -= a q
-        launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_RR, FIN_NONE, s);
+        pcg_step(h, u);
         ++k;
         TRY(sync_scalars(h));
         const double relr = std::sqrt(sch[SC_RR]) / nf;
@@ -684,11 +820,10 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
             if (rel < tol) return finish(GMG_OK);
             if (!std::isfinite(rel)) return finish(GMG_NONFINITE);
             ++inf.replacements;  // residual replacement (r now holds f - K u); restart the direction
-            restart();
+            pcg_restart(h);
             continue;
         }
-        vcycle_level(h, 0, h->r, h->z, h->x2_0, SC_RZNEW, FIN_BETA);   // z = V(r), beta
-        launch_p_update(h->p, h->z, n, h->sc, s);                         // p = z + beta p
+        pcg_direction(h);
     }
     TRY(true_residual(rel));
     inf.rel_residual = rel;

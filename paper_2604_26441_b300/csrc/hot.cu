@@ -563,6 +563,15 @@ __global__ void __launch_bounds__(kVecThreads) k_mask_u64(double* u, const uint8
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+__global__ void k_loop_check(double* sc, cudaGraphConditionalHandle cond) {
+    if (threadIdx.x != 0) return;
+    const double k = sc[SC_IT] + 1.0;
+    sc[SC_IT] = k;
+    const double relr = sqrt(sc[SC_RR]) / sc[SC_NF];
+    const bool go = isfinite(relr) && isfinite(sc[SC_ALPHA]) && !(relr < sc[SC_TOL]) && k < sc[SC_MAXIT];
+    cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
+
 // r = f on free DOFs (as FP32), 0 on fixed ones: the residual of the zero iterate.
 __global__ void __launch_bounds__(kVecThreads) k_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r) {
     for (long long q = blockIdx.x * (long long)kVecThreads + threadIdx.x; q < 3 * nn; q += (long long)gridDim.x * kVecThreads)
@@ -812,6 +821,11 @@ void launch_p_update(float* p, const float* z, long long n, const double* sc, cu
 void launch_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial, cudaStream_t s) {
     note_launch();
     k_mask_u64<<<kVecBlocks, kVecThreads, 0, s>>>(u, mask, nn, partial);
+}
+
+void launch_loop_check(double* sc, cudaGraphConditionalHandle cond, cudaStream_t s) {
+    note_launch();
+    k_loop_check<<<1, 32, 0, s>>>(sc, cond);
 }
 
 void launch_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r, cudaStream_t s) {

@@ -61,8 +61,12 @@ enum Scalar {
     SC_VKV = 9,
     SC_VDV = 10,
     SC_UNZ = 11,    // nonzero count of u (> 0: u is not the zero vector)
-    SC_TMP = 12,
-    SC_COUNT = 16
+    SC_TMP = 12,    // 12, 13: scratch
+    SC_IT = 16,     // PCG iterations completed (device-resident loop)
+    SC_TOL = 17,    // relative tolerance
+    SC_MAXIT = 18,  // iteration cap
+    SC_NF = 19,     // ||f_free||
+    SC_COUNT = 24
 };
 
 // Operations the reduction finaliser applies after storing its sum.
@@ -213,6 +217,13 @@ struct gmg_handle {
     gmg::CoarseFused cf{};                      // fused lower V-cycle (levels cf.start..L-1)
     bool use_fused = false;
     int* kerr = nullptr;                        // sticky error word of the TMA-staged operator
+    // device-resident PCG loop: a CUDA graph [restart, step, check, while{direction, step, check}]
+    cudaStream_t cap_stream = nullptr;          // private stream used only to capture the graph
+    cudaGraph_t loop_graph = nullptr;
+    cudaGraphExec_t loop_exec = nullptr;
+    const double* loop_u = nullptr;             // iterate the captured graph updates
+    unsigned long long loop_prefix_kernels = 0, loop_body_kernels = 0;
+    bool loop_unavailable = false;              // capture failed once: use the host loop
     int fused_blocks = 0;
     std::vector<void*> allocs;                  // every device allocation, freed by gmg_destroy
     void* pinned = nullptr;                     // pinned host block (sc_host)
@@ -292,6 +303,10 @@ void launch_pcg_update(double* u, float* r, const float* p, const float* q, long
 void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s);
 void launch_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial, cudaStream_t s);
 void launch_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r, cudaStream_t s);
+// Convergence test of the device-resident loop: counts the iteration and sets
+// the while-node condition to 1 while ||r|| / ||f|| >= tol, the scalars are
+// finite and the cap is not reached.
+void launch_loop_check(double* sc, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_scale_by_inv_sqrt(float* v, long long n, const double* sc, int slot, cudaStream_t s);
 void launch_scale_invdiag_fine(const float* y, float* w, const float* E, const uint8_t* mask,
                                int nx, int ny, int nz, float kd, cudaStream_t s);

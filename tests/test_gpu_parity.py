@@ -376,3 +376,38 @@ def test_fused_lower_vcycle_matches_per_level_kernels(cfg_name):
     _, inf_u = S_u.solve(f)
     assert inf_f["status"] == 0 and inf_u["status"] == 0
     assert abs(inf_f["iterations"] - inf_u["iterations"]) <= 1
+
+
+# ---------------------------------------------------------------------------
+# device-resident PCG loop (CUDA graph with a conditional while node)
+# ---------------------------------------------------------------------------
+LOOP_CASES = [
+    ("c0", 1e-6, 200),
+    ("c1", 1e-6, 200),
+    ("c0", 1e-9, 60),   # tight: residual replacements relaunch the graph
+    ("c1", 1e-6, 5),    # the cap ends the loop
+]
+
+
+@pytest.mark.parametrize("cfg_name,tol,maxit", LOOP_CASES)
+def test_device_loop_matches_host_loop(cfg_name, tol, maxit):
+    """The graph runs the host loop's kernels in the same order: the iterates,
+    counts and residuals agree bit for bit, also across replacements and the cap."""
+    c = inputs.CONFIGS[cfg_name]
+    f = _t(c.load(), torch.float64)
+    res = {}
+    for dev in (True, False):
+        S = gpu_solver(c.rho(), c.p, **config_opts(c), device_loop=dev)
+        u = torch.zeros_like(f)
+        _, info = S.solve(f, u, tol=tol, maxit=maxit)
+        first = u.clone()
+        u.zero_()
+        _, info2 = S.solve(f, u, tol=tol, maxit=maxit)  # same iterate buffer: the captured graph is reused
+        assert torch.equal(u, first) and info["iterations"] == info2["iterations"]
+        res[dev] = (u.cpu().numpy(), info)
+    (ud, idv), (uh, ih) = res[True], res[False]
+    assert np.array_equal(ud, uh)
+    for key in ("status", "iterations", "replacements", "rel_residual", "rel_residual_recursive"):
+        assert idv[key] == ih[key], key
+    if maxit == 5:
+        assert idv["iterations"] == 5 and idv["status"] != 0
