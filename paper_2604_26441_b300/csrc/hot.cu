@@ -3,11 +3,11 @@
 //  * k_fine_smooth0  -- first fine-level smoother step from zero (the fused
 //                       fine operator lives in fine.cu, its FP64 residual form
 //                       in resid64.cu);
-//  * k_bsr / k_bsr_ks / k_bsr_tma -- the same three modes on an assembled
+//  * k_bsr / k_bsr_ks / k_bsr_pipe -- the same three modes on an assembled
 //                       Galerkin level (27-point 3x3-block operator, implicit
 //                       structured columns): one streaming thread per node for
-//                       large levels, a K-split form for small ones, and an
-//                       optional TMA-staged form;
+//                       large levels, a K-split form for small ones, and a
+//                       persistent TMA-pipelined form;
 //  * k_restrict / k_prolong_add -- R = P^T and P of Eq. trilinear_weights /
 //                       Eq. vector_prolongation with the odd-size clamp;
 //  * k_coarse_solve  -- dense FP64 solve with the Cholesky-derived inverse;
@@ -175,110 +175,224 @@ __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Large levels: TMA-staged tiles.  A block of 128 threads owns 64 consecutive
-// nodes.  One elected thread issues 14 tensor loads on one mbarrier:
-//   - the block's own 126 planes (box 126 x 64: diagonal + forward blocks);
+// Large levels, TMA-pipelined: a persistent kernel, one block of 256 threads
+// per SM, walking tiles of 64 consecutive nodes (tile i of block b is
+// b + i * gridDim.x) through a two-stage shared-memory ring.  For each tile,
+// thread 0 issues 14 tensor loads on the stage's mbarrier:
+//   - the tile's own 126 planes (box 126 x 64: diagonal + forward blocks);
 //   - for each backward block u = 1..13, the 9 planes of block u at the nodes
-//     n - o_u, i.e. a box 9 x 68 starting at (n0 - o_u) rounded down to a
-//     multiple of 4 nodes (TMA wants 16-byte aligned starts; the remainder is
-//     applied when reading; coordinates outside the tensor read as zero).
-// That is 64,080 bytes in flight per block with no registers held, while the
-// threads fetch their neighbours' x values.  Slice 0 (threads 0-63) applies
-// the diagonal and forward blocks, slice 1 the transposed backward blocks;
-// slice 0 adds the two rows in a fixed order and runs the epilogue.
+//     n - o_u (box 9 x 68 from (n0 - o_u) rounded down to 4 nodes; the
+//     remainder (-o_u) mod 4 is the same for every tile);
+// and all threads stage, with 4-byte cp.async, the 9 rows of x that the tile's
+// 27 neighbour offsets touch (66 nodes each), the epilogue operands and the
+// masks.  The loads of tile i+1 are in flight while tile i is computed.
+//
+// No neighbour test is needed: a block towards a node outside the grid (or a
+// row wrap-around) is stored as zero, and nodes outside [0, nn) read as zero.
+// Four 64-thread slices each take a quarter of the 27 blocks of every node;
+// the partial rows are added in shared memory in a fixed order.
 // ---------------------------------------------------------------------------
 constexpr int kTmaNodes = 64;
 constexpr int kTmaBackW = kTmaNodes + 4;
 constexpr int kTmaOwnFloats = kSymPlanes * kTmaNodes;            // 8064 floats = 252 x 128 B
 constexpr int kTmaBackStride = 640;                              // 9 x 68 = 612 floats, padded to 128 B
 constexpr unsigned kTmaTxBytes = 4u * (kTmaOwnFloats + 13 * 9 * kTmaBackW);
-constexpr int kTmaSmemBytes = 128 + 4 * (kTmaOwnFloats + 13 * kTmaBackStride + 3 * kTmaNodes) + 16;
+constexpr int kXRow = 3 * (kTmaNodes + 2);                       // 198 floats of x per neighbour row
+constexpr int kXRowS = 200;
+constexpr int kPipeThreads = 256;
+// stage layout (floats): own | 13 backward boxes | 9 x rows | b, d, D^-1 (3 x 192) | masks (16 words)
+constexpr int kStOwn = 0;
+constexpr int kStBack = kStOwn + kTmaOwnFloats;
+constexpr int kStX = kStBack + 13 * kTmaBackStride;
+constexpr int kStEpi = kStX + 9 * kXRowS;
+constexpr int kStMask = kStEpi + 3 * 3 * kTmaNodes;
+constexpr int kStage = (kStMask + 16 + 31) / 32 * 32;            // 128-byte multiple
+constexpr int kPipeSmemBytes = 4 * (2 * kStage + 3 * 3 * kTmaNodes) + 16;
+constexpr int kXCopies = (9 * kXRow + kPipeThreads - 1) / kPipeThreads;
 constexpr long long kTmaSpin = 1LL << 22;
 
 template <int MODE, bool DOT>
-__global__ void __launch_bounds__(128) k_bsr_tma(const __grid_constant__ CUtensorMap tm_own,
-                                                 const __grid_constant__ CUtensorMap tm_back, BsrArgs a) {
-    extern __shared__ unsigned char smem_raw[];
-    float* sOwn = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float* sBack = sOwn + kTmaOwnFloats;
-    float* part = sBack + 13 * kTmaBackStride;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(part + 3 * kTmaNodes);
+__global__ void __launch_bounds__(kPipeThreads, 1) k_bsr_pipe(const __grid_constant__ CUtensorMap tm_own,
+                                                              const __grid_constant__ CUtensorMap tm_back,
+                                                              BsrArgs a) {
+    extern __shared__ __align__(128) float sm[];
+    float* const part = sm + 2 * kStage;  // [3][64][3] partial rows of slices 1..3
+    uint64_t* const bars = reinterpret_cast<uint64_t*>(part + 3 * 3 * kTmaNodes);
     const int tid = threadIdx.x, t = tid & (kTmaNodes - 1), slice = tid >> 6;
     const int nn = (int)a.nn;
-    const int n0 = blockIdx.x * kTmaNodes, n = n0 + t;
-    const bool live = n < nn;
-    const int nsafe = live ? n : nn - 1;
-    const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
-    const int i = nsafe % NX, j = (nsafe / NX) % NY, k = nsafe / (NX * NY);
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        mbar_expect_tx(bar, kTmaTxBytes);
-        tma_load_2d(sOwn, &tm_own, n0, 0, bar);
-#pragma unroll 1
-        for (int u = 1; u < 14; ++u) {
-            int dx, dy, dz;
-            const int off = fwd_offset(u, NX, NY, dx, dy, dz);
-            tma_load_2d(sBack + (u - 1) * kTmaBackStride, &tm_back, (n0 - off) & ~3, 9 * u, bar);
-        }
-    }
-    // neighbour values (branch-free: out-of-grid neighbours read this node with weight 0)
-    float v[14][3];
+    const int NX = a.nx + 1, NXY = NX * (a.ny + 1);
+    const int ntiles = (nn + kTmaNodes - 1) / kTmaNodes;
+    constexpr bool EPI_B = MODE != FM_APPLY;
+    constexpr bool EPI_D = MODE == FM_SMOOTH;
+    const float cd = EPI_D ? (float)a.coef[2 * a.step] : 0.f;
+    const float ca = EPI_D ? (float)a.coef[2 * a.step + 1] : 0.f;
+    const bool need_d = EPI_D && cd != 0.f;
+
+    // x staging slots of this thread (the same for every tile): float w of
+    // neighbour row c, (dy, dz) = (c % 3 - 1, c / 3 - 1), which starts at node
+    // n0 + o_c - 1; its source is x[3 n0 + xs_off]
+    int xs_off[kXCopies], xs_dst[kXCopies];
 #pragma unroll
-    for (int u = 0; u < 14; ++u) {
-        if (slice == 1 && u == 0) { v[0][0] = v[0][1] = v[0][2] = 0.f; continue; }
-        int dx, dy, dz;
-        const int off = fwd_offset(u, NX, NY, dx, dy, dz);
-        const int sx = slice ? -dx : dx, sy = slice ? -dy : dy, sz = slice ? -dz : dz;
-        const bool ok = i + sx >= 0 && i + sx < NX && j + sy >= 0 && j + sy < NY && k + sz >= 0 && k + sz < NZ;
-        const int m = ok ? (slice ? nsafe - off : nsafe + off) : nsafe;
-        const float w = ok ? 1.f : 0.f;
-        v[u][0] = w * a.xin[3 * m];
-        v[u][1] = w * a.xin[3 * m + 1];
-        v[u][2] = w * a.xin[3 * m + 2];
+    for (int q = 0; q < kXCopies; ++q) {
+        const int idx = tid + q * kPipeThreads;
+        const int c = idx / kXRow, w = idx % kXRow;
+        const int dy = c % 3 - 1, dz = c / 3 - 1;
+        const bool used = idx < 9 * kXRow;
+        xs_off[q] = used ? 3 * (NX * dy + NXY * dz - 1) + w : 0;
+        xs_dst[q] = used ? kStX + c * kXRowS + w : -1;
     }
-    // bounded wait for the tiles; the decision to give up is taken by the whole block
-    bool ok = false;
-    for (long long it = 0; it < kTmaSpin; ++it)
-        if (mbar_try_wait(bar, 0)) { ok = true; break; }
-    if (__syncthreads_or(!ok)) {
+    if ((smem_u32(sm) & 127) != 0) {  // TMA destinations must be 128-byte aligned
         if (tid == 0) atomicExch(a.err, 1);
         return;
     }
-    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
-    if (slice == 0) {
-#pragma unroll
-        for (int u = 0; u < 14; ++u) {
-            const float* A = sOwn + (9 * u) * kTmaNodes + t;
-            y0 = fmaf(A[0 * kTmaNodes], v[u][0], fmaf(A[1 * kTmaNodes], v[u][1], fmaf(A[2 * kTmaNodes], v[u][2], y0)));
-            y1 = fmaf(A[3 * kTmaNodes], v[u][0], fmaf(A[4 * kTmaNodes], v[u][1], fmaf(A[5 * kTmaNodes], v[u][2], y1)));
-            y2 = fmaf(A[6 * kTmaNodes], v[u][0], fmaf(A[7 * kTmaNodes], v[u][1], fmaf(A[8 * kTmaNodes], v[u][2], y2)));
-        }
-    } else {
-#pragma unroll
-        for (int u = 1; u < 14; ++u) {
-            int dx, dy, dz;
-            const int off = fwd_offset(u, NX, NY, dx, dy, dz);
-            const float* B = sBack + (u - 1) * kTmaBackStride + ((n0 - off) - ((n0 - off) & ~3)) + t;
-            y0 = fmaf(B[0 * kTmaBackW], v[u][0], fmaf(B[3 * kTmaBackW], v[u][1], fmaf(B[6 * kTmaBackW], v[u][2], y0)));
-            y1 = fmaf(B[1 * kTmaBackW], v[u][0], fmaf(B[4 * kTmaBackW], v[u][1], fmaf(B[7 * kTmaBackW], v[u][2], y1)));
-            y2 = fmaf(B[2 * kTmaBackW], v[u][0], fmaf(B[5 * kTmaBackW], v[u][1], fmaf(B[8 * kTmaBackW], v[u][2], y2)));
-        }
-        part[3 * t] = y0;
-        part[3 * t + 1] = y1;
-        part[3 * t + 2] = y2;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
     }
     __syncthreads();
+
+    auto issue = [&](int tile, int st) {
+        float* S = sm + st * kStage;
+        const int n0 = tile * kTmaNodes;
+        if (tid == 0) {
+            mbar_expect_tx(&bars[st], kTmaTxBytes);
+            tma_load_2d(S + kStOwn, &tm_own, n0, 0, &bars[st]);
+#pragma unroll 1
+            for (int u = 1; u < 14; ++u) {
+                int dx, dy, dz;
+                const int off = fwd_offset(u, NX, a.ny + 1, dx, dy, dz);
+                tma_load_2d(S + kStBack + (u - 1) * kTmaBackStride, &tm_back, (n0 - off) & ~3, 9 * u, &bars[st]);
+            }
+        }
+        const unsigned sbase = smem_u32(S);
+#pragma unroll
+        for (int q = 0; q < kXCopies; ++q) {
+            if (xs_dst[q] < 0) continue;
+            const long long fo = 3LL * n0 + xs_off[q];  // float offset in x
+            const bool ok = fo >= 0 && fo < 3LL * nn;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sbase + 4u * xs_dst[q]),
+                         "l"(a.xin + (ok ? fo : 0)), "r"(ok ? 4 : 0)
+                         : "memory");
+        }
+        if (tid < 3 * kTmaNodes) {
+            const long long fo = 3LL * n0 + tid;
+            const bool ok = fo < 3LL * nn;
+            const float* srcs[3] = {a.b, a.dold, a.invdiag};
+            const bool want[3] = {EPI_B, EPI_D, EPI_D};
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                if (!want[e] || (e == 1 && !need_d)) continue;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sbase + 4u * (kStEpi + e * 3 * kTmaNodes + tid)),
+                             "l"(srcs[e] + (ok ? fo : 0)), "r"(ok ? 4 : 0)
+                             : "memory");
+            }
+        }
+        if (tid < kTmaNodes / 4) {
+            const int b0 = n0 + 4 * tid;
+            const int nb = min(4, max(0, nn - b0));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sbase + 4u * (kStMask + tid)),
+                         "l"(a.mask + (nb > 0 ? b0 : 0)), "r"(nb)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
     DSAcc dotv;
-    if (slice == 0 && live) {
-        const float y[3] = {y0 + part[3 * t], y1 + part[3 * t + 1], y2 + part[3 * t + 2]};
-        bsr_epilogue<MODE, DOT>(a, n, y, dotv);
+    bool failed = false;
+    int it = 0;
+    int tile = blockIdx.x;
+    if (tile < ntiles) issue(tile, 0);
+#pragma unroll 1
+    for (; tile < ntiles; tile += gridDim.x, ++it) {
+        const int st = it & 1;
+        const int next = tile + gridDim.x;
+        if (next < ntiles) issue(next, st ^ 1);
+        // the tile's TMA boxes (bounded wait) and this thread's cp.async copies
+        bool ok = false;
+        for (long long k = 0; k < kTmaSpin; ++k)
+            if (mbar_try_wait(&bars[st], (it >> 1) & 1)) { ok = true; break; }
+        if (next < ntiles) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        const float* S = sm + st * kStage;
+        const int n0 = tile * kTmaNodes, n = n0 + t;
+        float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const int blk = slice + 4 * q;  // 0..13 forward (u = blk), 14..26 backward (u = blk - 13)
+            if (blk < 27) {
+                const bool fwd = blk < 14;
+                const int u = fwd ? blk : blk - 13;
+                int dx, dy, dz;
+                const int off = fwd_offset(u, NX, a.ny + 1, dx, dy, dz);
+                const int sx = fwd ? dx : -dx, sy = fwd ? dy : -dy, sz = fwd ? dz : -dz;
+                const float* xr = S + kStX + ((sy + 1) + 3 * (sz + 1)) * kXRowS + 3 * (t + sx + 1);
+                const float v0 = xr[0], v1 = xr[1], v2 = xr[2];
+                if (fwd) {
+                    const float* A = S + kStOwn + 9 * u * kTmaNodes + t;
+                    y0 = fmaf(A[0 * kTmaNodes], v0, fmaf(A[1 * kTmaNodes], v1, fmaf(A[2 * kTmaNodes], v2, y0)));
+                    y1 = fmaf(A[3 * kTmaNodes], v0, fmaf(A[4 * kTmaNodes], v1, fmaf(A[5 * kTmaNodes], v2, y1)));
+                    y2 = fmaf(A[6 * kTmaNodes], v0, fmaf(A[7 * kTmaNodes], v1, fmaf(A[8 * kTmaNodes], v2, y2)));
+                } else {
+                    const float* B = S + kStBack + (u - 1) * kTmaBackStride + ((-off) & 3) + t;
+                    y0 = fmaf(B[0 * kTmaBackW], v0, fmaf(B[3 * kTmaBackW], v1, fmaf(B[6 * kTmaBackW], v2, y0)));
+                    y1 = fmaf(B[1 * kTmaBackW], v0, fmaf(B[4 * kTmaBackW], v1, fmaf(B[7 * kTmaBackW], v2, y1)));
+                    y2 = fmaf(B[2 * kTmaBackW], v0, fmaf(B[5 * kTmaBackW], v1, fmaf(B[8 * kTmaBackW], v2, y2)));
+                }
+            }
+        }
+        if (slice > 0) {
+            float* pp = part + ((slice - 1) * kTmaNodes + t) * 3;
+            pp[0] = y0; pp[1] = y1; pp[2] = y2;
+        }
+        __syncthreads();
+        if (slice == 0 && n < nn) {
+            float y[3] = {y0, y1, y2};
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                y[c] = ((y[c] + part[t * 3 + c]) + part[(kTmaNodes + t) * 3 + c]) + part[(2 * kTmaNodes + t) * 3 + c];
+            const uint8_t msk = reinterpret_cast<const uint8_t*>(S + kStMask)[t];
+            const float* bb = S + kStEpi + 3 * t;
+            const float* dd = S + kStEpi + 3 * kTmaNodes + 3 * t;
+            const float* iv = S + kStEpi + 6 * kTmaNodes + 3 * t;
+            const float* xo = S + kStX + 4 * kXRowS + 3 * (t + 1);  // this node's own x (row dy = dz = 0)
+            if (MODE == FM_APPLY) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float v = fixed_bit(msk, c) ? 0.f : y[c];
+                    a.out[3 * n + c] = v;
+                    if (DOT) dotv.add_prod(xo[c], v);
+                }
+            } else if (MODE == FM_RESID) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) a.out[3 * n + c] = fixed_bit(msk, c) ? 0.f : bb[c] - y[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float xn = 0.f, dn = 0.f;
+                    if (!fixed_bit(msk, c)) {
+                        dn = ca * iv[c] * (bb[c] - y[c]);
+                        if (need_d) dn = fmaf(cd, dd[c], dn);
+                        xn = xo[c] + dn;
+                        if (DOT) dotv.add_prod(bb[c], xn);
+                    }
+                    a.out[3 * n + c] = xn;
+                    if (a.dnew) a.dnew[3 * n + c] = dn;
+                }
+            }
+        }
+        __syncthreads();  // stage st is free for tile + 2 * gridDim.x
+    }
+    if (failed) {
+        if (tid == 0) atomicExch(a.err, 1);
+        return;
     }
     if (DOT) {
-        const double s2 = block_sum<128>(dotv.value(), tid);
+        const double s2 = block_sum<kPipeThreads>(dotv.value(), tid);
         if (tid == 0) a.partial[blockIdx.x] = s2;
     }
 }
@@ -664,8 +778,20 @@ void launch_fine_smooth0(const FineArgs& a, cudaStream_t s) {
 // which are latency-bound, use the K-split form.
 constexpr long long kBsrStreamLevel = 65536;
 
+int pipe_blocks(long long nn) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 148;
+    }
+    const long long tiles = (nn + kTmaNodes - 1) / kTmaNodes;
+    return (int)std::min<long long>(tiles, sms);
+}
+
 int bsr_grid_blocks(long long nn, bool tma) {
-    if (tma) return (int)((nn + kTmaNodes - 1) / kTmaNodes);
+    if (tma) return pipe_blocks(nn);
     return nn >= kBsrStreamLevel ? (int)((nn + 255) / 256) : (int)((nn + 63) / 64);
 }
 
@@ -673,10 +799,10 @@ template <int MODE, bool DOT>
 void launch_bsr_tma(int g, const BsrArgs& a, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_bsr_tma<MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmemBytes);
+        cudaFuncSetAttribute(k_bsr_pipe<MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmemBytes);
         attr = true;
     }
-    k_bsr_tma<MODE, DOT><<<g, 128, kTmaSmemBytes, s>>>(*a.tm_own, *a.tm_back, a);
+    k_bsr_pipe<MODE, DOT><<<g, kPipeThreads, kPipeSmemBytes, s>>>(*a.tm_own, *a.tm_back, a);
 }
 
 void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
