@@ -1,11 +1,15 @@
 """Fixed workloads for profiling the CUDA path under ncu.
 
     python -m paper_2604_26441_b300.profile_cases solve-c2    # set-up + 2 solves, 100^3
+    python -m paper_2604_26441_b300.profile_cases solve-c2-hostloop  # the same, PCG driven from the host
     python -m paper_2604_26441_b300.profile_cases smooth-c2   # set-up + 3 fine smoothing passes
     python -m paper_2604_26441_b300.profile_cases apply-c2    # set-up + 5 fine operator applies
 
 Each case prints the library's kernel-launch counter after set-up, so that
-``ncu -s`` can skip the set-up kernels.
+``ncu -s`` can skip the set-up kernels.  The solve normally runs its PCG
+iterations as one CUDA graph with a conditional while node, whose kernels a
+per-launch ncu list does not show; the host-loop case launches the same kernels
+in the same order one by one.
 
     python -m paper_2604_26441_b300.profile_cases summarize LAUNCHES.csv [FIRST_ID]
 
@@ -54,10 +58,11 @@ def main(case: str) -> None:
     from paper_2604_26441_b300 import gmg, inputs
 
     cfg = inputs.CONFIGS["c2"]
-    S = gmg.Solver(torch.from_numpy(cfg.rho()).cuda(), p=cfg.p, opts=gmg.config_options(cfg))
+    S = gmg.Solver(torch.from_numpy(cfg.rho()).cuda(), p=cfg.p,
+                   opts=gmg.config_options(cfg, device_loop=case != "solve-c2-hostloop"))
     torch.cuda.synchronize()
     print("setup launches", gmg.kernel_launches(), flush=True)
-    if case == "solve-c2":
+    if case in ("solve-c2", "solve-c2-hostloop"):
         f = torch.from_numpy(cfg.load()).cuda()
         for _ in range(2):
             u, info = S.solve(f, tol=cfg.tol, maxit=cfg.maxit)
