@@ -397,17 +397,19 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_bsr_pipe(const __grid_const
     }
 }
 
-// Assembled levels, "K-split" form: a block of 256 threads takes 64 consecutive
-// nodes; its four slices of 64 threads each apply a quarter of every node's 27
-// blocks (diagonal, 13 forward, 13 transposed backward), so each thread issues
-// ~84 loads instead of ~324 and every plane read is coalesced across the 64
-// nodes.  The four partial rows are added in shared memory in a fixed order.
-template <int MODE, bool DOT>
+// Assembled levels, "K-split" form: a block of 256 threads takes 256/NS
+// consecutive nodes; its NS slices each apply every NS-th of a node's 27 blocks
+// (diagonal, 13 forward, 13 transposed backward), so each thread issues ~324/NS
+// loads instead of ~324, all independent, and every plane read is coalesced
+// across the block's nodes.  The partial rows are added in shared memory in a
+// fixed order.
+template <int MODE, bool DOT, int NS>
 __global__ void __launch_bounds__(256) k_bsr_ks(BsrArgs a) {
-    constexpr int NPB = 64;
-    __shared__ float part[4][NPB][3];
+    constexpr int NPB = 256 / NS;
+    constexpr int NQ = (27 + NS - 1) / NS;
+    __shared__ float part[NS][NPB][3];
     const int nn = (int)a.nn;
-    const int t = threadIdx.x & (NPB - 1), slice = threadIdx.x >> 6;
+    const int t = threadIdx.x % NPB, slice = threadIdx.x / NPB;
     const int n = blockIdx.x * NPB + t;
     const bool live = n < nn;
     const int nsafe = live ? n : 0;
@@ -416,8 +418,8 @@ __global__ void __launch_bounds__(256) k_bsr_ks(BsrArgs a) {
     const long long N = a.ps;
     float y0 = 0.f, y1 = 0.f, y2 = 0.f;
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
-        const int blk = slice + 4 * q;  // 0..13 forward (u = blk), 14..26 backward (u = blk - 13)
+    for (int q = 0; q < NQ; ++q) {
+        const int blk = slice + NS * q;  // 0..13 forward (u = blk), 14..26 backward (u = blk - 13)
         if (blk < 27) {
             const bool fwd = blk < 14;
             const int u = fwd ? blk : blk - 13;
@@ -449,7 +451,12 @@ __global__ void __launch_bounds__(256) k_bsr_ks(BsrArgs a) {
     if (slice == 0 && live) {
         float y[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) y[c] = ((part[0][t][c] + part[1][t][c]) + part[2][t][c]) + part[3][t][c];
+        for (int c = 0; c < 3; ++c) {
+            float acc = part[0][t][c];
+#pragma unroll
+            for (int q = 1; q < NS; ++q) acc += part[q][t][c];
+            y[c] = acc;
+        }
         bsr_epilogue<MODE, DOT>(a, n, y, dotv);
     }
     if (DOT) {
@@ -776,7 +783,10 @@ void launch_fine_smooth0(const FineArgs& a, cudaStream_t s) {
 // (bsr_tma_nodes option) use the TMA-staged kernel; otherwise levels of at
 // least kBsrStreamLevel nodes stream with one thread per node and smaller ones,
 // which are latency-bound, use the K-split form.
+// (K-split slices measured at 100^3: 4 -> 7.78 ms per solve, 8 -> 7.63, 16 -> 7.68;
+// the K-split form at level 1 instead of streaming: 8.20 ms.)
 constexpr long long kBsrStreamLevel = 65536;
+constexpr int kKsSlices = 8;
 
 int pipe_blocks(long long nn) {
     static int sms = 0;
@@ -792,7 +802,8 @@ int pipe_blocks(long long nn) {
 
 int bsr_grid_blocks(long long nn, bool tma) {
     if (tma) return pipe_blocks(nn);
-    return nn >= kBsrStreamLevel ? (int)((nn + 255) / 256) : (int)((nn + 63) / 64);
+    constexpr int npb = 256 / kKsSlices;
+    return nn >= kBsrStreamLevel ? (int)((nn + 255) / 256) : (int)((nn + npb - 1) / npb);
 }
 
 template <int MODE, bool DOT>
@@ -833,14 +844,15 @@ void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
         }
         return;
     }
+    constexpr int NS = kKsSlices;
     if (mode == FM_APPLY) {
-        if (dot) k_bsr_ks<FM_APPLY, true><<<g, 256, 0, s>>>(a);
-        else k_bsr_ks<FM_APPLY, false><<<g, 256, 0, s>>>(a);
+        if (dot) k_bsr_ks<FM_APPLY, true, NS><<<g, 256, 0, s>>>(a);
+        else k_bsr_ks<FM_APPLY, false, NS><<<g, 256, 0, s>>>(a);
     } else if (mode == FM_SMOOTH) {
-        if (dot) k_bsr_ks<FM_SMOOTH, true><<<g, 256, 0, s>>>(a);
-        else k_bsr_ks<FM_SMOOTH, false><<<g, 256, 0, s>>>(a);
+        if (dot) k_bsr_ks<FM_SMOOTH, true, NS><<<g, 256, 0, s>>>(a);
+        else k_bsr_ks<FM_SMOOTH, false, NS><<<g, 256, 0, s>>>(a);
     } else {
-        k_bsr_ks<FM_RESID, false><<<g, 256, 0, s>>>(a);
+        k_bsr_ks<FM_RESID, false, NS><<<g, 256, 0, s>>>(a);
     }
 }
 
