@@ -95,6 +95,12 @@ typedef struct {
                                     conditional while node, returning to the host only for the
                                     FP64 acceptance test; 0: one host round trip per iteration.
                                     Both run the same kernels in the same order. */
+    double ir_factor;            /* 0 (default): plain PCG to tol.  In (0, 1): outer FP64 iterative
+                                    refinement -- each inner FP32 PCG phase starts from the FP64
+                                    residual of the current u and stops when its recursive residual
+                                    is ir_factor times smaller (not below tol); the FP64 residual
+                                    is then recomputed (gmg_info.replacements counts the outer
+                                    steps after the first).  Reaches tolerances below FP32 reach. */
     void* stream;                /* cudaStream_t for all device work; NULL = default stream */
 } gmg_options;
 

@@ -619,6 +619,7 @@ void gmg_default_options(gmg_options* o) {
     o->fused_coarse_nodes = 4096;
     o->bsr_tma_nodes = 0;
     o->device_loop = 1;
+    o->ir_factor = 0.0;
     o->stream = nullptr;
 }
 
@@ -674,6 +675,7 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
     if (o.levels < 0 || o.levels > kMaxLevels) return fail(GMG_ERR_ARG, "levels outside [0, 16]");
     if (!(o.omega > 0.0) || !(o.cheb_alpha > 0.0 && o.cheb_alpha < 1.0) || !(o.lambda_safety > 0.0))
         return fail(GMG_ERR_ARG, "bad smoother parameters");
+    if (!(o.ir_factor >= 0.0 && o.ir_factor < 1.0)) return fail(GMG_ERR_ARG, "ir_factor must be in [0, 1)");
     if (o.power_iters_fine < 1 || o.power_iters_coarse < 1 || o.chol_cutoff < 1)
         return fail(GMG_ERR_ARG, "bad iteration counts or cutoff");
 
@@ -762,18 +764,30 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     CU(cudaMemcpyAsync(h->sc + SC_UNZ, sch + SC_UNZ, sizeof(double), cudaMemcpyHostToDevice, s));
 
     const double nf = std::sqrt(sch[SC_FF]);
+    // Stopping target of an inner PCG phase.  Plain solve: tol.  Outer FP64
+    // iterative refinement (ir_factor in (0, 1)): each phase, started from the
+    // FP64 residual of the current u, stops once its recursive residual is
+    // ir_factor times smaller (but not below tol); the FP64 residual
+    // replacement and restart that follow are the outer refinement step.
+    const double irf = h->opt.ir_factor;
+    auto inner_target = [&](double rel_start) { return irf > 0.0 ? std::max(tol, irf * rel_start) : tol; };
+    double target = inner_target(rel);
     if (maxit > 0 && h->opt.device_loop && !h->loop_unavailable && h->loop_u != u) {
         if (loop_build(h, u) != GMG_OK) h->loop_unavailable = true;  // e.g. no graph support: host loop
     }
     if (maxit > 0 && h->opt.device_loop && h->loop_exec && h->loop_u == u) {
         // device-resident loop: one graph launch per convergence candidate
         sch[SC_IT] = 0.0;
-        sch[SC_TOL] = tol;
+        sch[SC_TOL] = target;
         sch[SC_MAXIT] = (double)maxit;
         sch[SC_NF] = nf;
         CU(cudaMemcpyAsync(h->sc + SC_IT, sch + SC_IT, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
         int k = 0;
         while (true) {
+            if (sch[SC_TOL] != target) {
+                sch[SC_TOL] = target;
+                CU(cudaMemcpyAsync(h->sc + SC_TOL, sch + SC_TOL, sizeof(double), cudaMemcpyHostToDevice, s));
+            }
             CU(cudaGraphLaunch(h->loop_exec, s));
             TRY(sync_scalars(h));
             const int k_new = (int)sch[SC_IT];
@@ -786,12 +800,13 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
                 inf.rel_residual = relr;
                 return finish(GMG_NONFINITE);
             }
-            if (!(relr < tol)) break;  // the cap
+            if (!(relr < target)) break;  // the cap
             TRY(true_residual(rel));
             inf.rel_residual = rel;
             if (rel < tol) return finish(GMG_OK);
             if (!std::isfinite(rel)) return finish(GMG_NONFINITE);
             ++inf.replacements;  // residual replacement (r now holds f - K u); restart the direction
+            target = inner_target(rel);
             if (k >= maxit) break;
         }
         TRY(true_residual(rel));
@@ -814,12 +829,13 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
             inf.rel_residual = relr;
             return finish(GMG_NONFINITE);
         }
-        if (relr < tol) {
+        if (relr < target) {
             TRY(true_residual(rel));
             inf.rel_residual = rel;
             if (rel < tol) return finish(GMG_OK);
             if (!std::isfinite(rel)) return finish(GMG_NONFINITE);
             ++inf.replacements;  // residual replacement (r now holds f - K u); restart the direction
+            target = inner_target(rel);
             pcg_restart(h);
             continue;
         }
