@@ -60,6 +60,11 @@ extern "C" {
 #define GMG_SMOOTHER_JACOBI 0
 #define GMG_SMOOTHER_CHEBYSHEV 1
 
+/* Fine-level smoother arithmetic (gmg_options.fine_smoother). */
+#define GMG_FINE_FP32 0
+#define GMG_FINE_BF16X3 1
+#define GMG_FINE_BF16 2
+
 typedef struct gmg_handle gmg_handle;
 
 typedef struct {
@@ -101,6 +106,12 @@ typedef struct {
                                     is ir_factor times smaller (not below tol); the FP64 residual
                                     is then recomputed (gmg_info.replacements counts the outer
                                     steps after the first).  Reaches tolerances below FP32 reach. */
+    int fine_smoother;           /* arithmetic of the fine-level smoother's element contraction:
+                                    GMG_FINE_FP32 (default, CUDA cores), GMG_FINE_BF16X3 (tensor
+                                    cores, split BF16: 3 MMA passes, ~16 significant bits) or
+                                    GMG_FINE_BF16 (tensor cores, one BF16 pass).  FP32
+                                    accumulation; the PCG operator, residuals and coarser levels
+                                    are unaffected. */
     void* stream;                /* cudaStream_t for all device work; NULL = default stream */
 } gmg_options;
 

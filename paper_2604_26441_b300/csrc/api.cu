@@ -73,6 +73,7 @@ FineArgs fine_args(gmg_handle* h) {
     FineArgs a{};
     a.nx = l.nx; a.ny = l.ny; a.nz = l.nz;
     a.E = h->E32; a.mask = l.mask; a.kd = h->kd; a.coef = l.coef;
+    a.tcB = h->tcB; a.err = h->kerr;
     return a;
 }
 
@@ -135,7 +136,10 @@ void smooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, c
         a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
         a.partial = dot ? h->partials : nullptr;
         if (zero_init) launch_fine_smooth0(a, s);
-        else { a.xin = xcur; launch_fine(FM_SMOOTH, dot, 0, a, h->gh, s); }
+        else if (h->opt.fine_smoother != GMG_FINE_FP32) {
+            a.xin = xcur;
+            launch_fine_tc(h->opt.fine_smoother == GMG_FINE_BF16X3 ? 3 : 1, dot, a, s);
+        } else { a.xin = xcur; launch_fine(FM_SMOOTH, dot, 0, a, h->gh, s); }
     } else {
         BsrArgs a = bsr_args(h, li);
         a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
@@ -351,6 +355,15 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         CU(cudaMemcpyAsync(gh, g72, sizeof gh, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
         for (int i = 0; i < 72; ++i) { h->gh.g[i] = (float)gh[i]; h->gh64.g[i] = gh[i]; }
+        if (o.fine_smoother != GMG_FINE_FP32) {
+            uint16_t op[2048];
+            build_tc_operand(gh, op);
+            uint16_t* dev = nullptr;
+            TRY(dalloc(h, &dev, 2048));
+            CU(cudaMemcpyAsync(dev, op, sizeof op, cudaMemcpyHostToDevice, s));
+            CU(cudaStreamSynchronize(s));
+            h->tcB = dev;
+        }
         dfree(h, g72);
     }
 
@@ -620,6 +633,7 @@ void gmg_default_options(gmg_options* o) {
     o->bsr_tma_nodes = 0;
     o->device_loop = 1;
     o->ir_factor = 0.0;
+    o->fine_smoother = GMG_FINE_FP32;
     o->stream = nullptr;
 }
 
@@ -676,6 +690,8 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
     if (!(o.omega > 0.0) || !(o.cheb_alpha > 0.0 && o.cheb_alpha < 1.0) || !(o.lambda_safety > 0.0))
         return fail(GMG_ERR_ARG, "bad smoother parameters");
     if (!(o.ir_factor >= 0.0 && o.ir_factor < 1.0)) return fail(GMG_ERR_ARG, "ir_factor must be in [0, 1)");
+    if (o.fine_smoother != GMG_FINE_FP32 && o.fine_smoother != GMG_FINE_BF16 && o.fine_smoother != GMG_FINE_BF16X3)
+        return fail(GMG_ERR_ARG, "unknown fine_smoother");
     if (o.power_iters_fine < 1 || o.power_iters_coarse < 1 || o.chol_cutoff < 1)
         return fail(GMG_ERR_ARG, "bad iteration counts or cutoff");
 

@@ -34,7 +34,10 @@
 // The x and y components travel as packed f32x2 pairs, and the loop takes two
 // layers per trip so that the layer state alternates between two register
 // sets.  No atomics: every output is formed by its owner in a fixed order.
+#include <cuda_bf16.h>
+
 #include <algorithm>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -376,6 +379,397 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core smoother (the precision line of Sec. "Mixed precision"): the
+// same z-marching smoother step, with the element contraction on the 5th-gen
+// tensor cores.  Per element layer every thread forms its element's 21 Hadamard
+// modes in FP32 (as above; differences, so the low-precision rounding acts on
+// the variation of u), splits them into BF16 hi (+ lo) parts and writes one row
+// of a 128 x 32 BF16 A tile in shared memory.  One thread issues
+// tcgen05.mma (kind::f16, FP32 accumulation in TMEM) against the fixed 32 x 32
+// operand B that maps the 21 modes to the 24 corner forces of the element (G
+// composed with the face split and the corner expansion, built on the host in
+// FP64 and split into BF16 hi + lo).  PASSES = 1: A_hi B_hi (plain BF16);
+// PASSES = 3: + A_lo B_hi + A_hi B_lo (split BF16, ~16 significant bits).  The
+// result of layer k is read back from TMEM one step later (tcgen05.ld), scaled
+// by E_e in FP32 and summed into the nodes as above; node plane p is finished
+// three steps after its layer, so the epilogue operands are loaded one plane
+// earlier than in k_fine.
+// ---------------------------------------------------------------------------
+constexpr int kTcTileBytes = 128 * 32 * 2;  // one 128 x 32 BF16 operand tile
+constexpr unsigned kTcSpin = 1u << 22;
+
+__device__ __forceinline__ uint64_t tc_sdesc(unsigned addr) {
+    // K-major, no swizzle: core matrices of 8 rows x 16 bytes; K-adjacent cores
+    // 128 bytes apart (leading offset), row-group-adjacent cores 512 bytes apart
+    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// byte offset of (row r, k-chunk j of 8 BF16 values) in a tile
+__device__ __forceinline__ int tc_chunk(int r, int j) { return ((r >> 3) * 4 + j) * 128 + (r & 7) * 16; }
+
+__device__ __forceinline__ unsigned bf2(float lo, float hi) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned*>(&b);
+}
+__device__ __forceinline__ float2 unbf2(unsigned u) {
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+}
+
+template <int BX, int BY, int PASSES, bool DOT>
+__global__ void __launch_bounds__(BX * BY, 2) k_fine_tc(FineArgs a, int zchunk) {
+    static_assert(BX * BY == 256, "two 128-element MMA tiles per block");
+    constexpr int NT = BX * BY;
+    constexpr int ROW = (BX + 1) * 3;
+    constexpr int PLANE = (BY + 1) * ROW;
+    constexpr int NCP = (PLANE + NT - 1) / NT;
+    constexpr int OWN = (BX - 1) * (BY - 1);
+    constexpr int APARTS = PASSES > 1 ? 2 : 1;
+    __shared__ float sp[kRing][PLANE];
+    __shared__ float sE[kRing][NT];
+    __shared__ float sB[kRing][OWN * 3];
+    __shared__ float sD[kRing][OWN * 3];
+    __shared__ float4 sx[2][BY][BX];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ unsigned tslot;
+    extern __shared__ __align__(1024) unsigned char dyn[];  // A tiles [APARTS][2], then B [2]
+    unsigned char* const sA = dyn;
+    unsigned char* const sBop = dyn + APARTS * 2 * kTcTileBytes;
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty, warp = tid >> 5;
+    const int nx = a.nx;
+    const int NX = nx + 1, NY = a.ny + 1, NZ = a.nz + 1, NXY = NX * NY, NEXY = nx * a.ny;
+    const int x0 = blockIdx.x * (BX - 1), y0 = blockIdx.y * (BY - 1);
+    const int k0 = blockIdx.z * zchunk, k1 = min(k0 + zchunk, NZ);
+    const int kb = k0 - 1;
+    const int cx = x0 - 1 + tx, cy = y0 - 1 + ty, ox = cx + 1, oy = cy + 1;
+    const bool owner = tx < BX - 1 && ty < BY - 1 && ox < NX && oy < NY;
+    const bool cell_in = cx >= 0 && cx < nx && cy >= 0 && cy < a.ny;
+    const int onode_base = oy * NX + ox, e_base = cy * nx + cx;
+    const int own3 = 3 * (ty * (BX - 1) + tx);
+    const int trow = tid & 127, ttile = tid >> 7;  // this element's row and tile in the MMA
+
+    if ((smem_u32(dyn) & 1023) != 0) {  // operand tiles must be 16-byte (here 1 KB) aligned
+        if (tid == 0) atomicExch(a.err, 1);
+        return;
+    }
+    // ---- operand B into shared memory, A pad columns (k 24..31) to zero, TMEM, barriers
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.tcB);
+        uint4* dst = reinterpret_cast<uint4*>(sBop);
+        for (int q = tid; q < 2 * 2048 / 16; q += NT) dst[q] = src[q];
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int pa = 0; pa < APARTS; ++pa)
+            *reinterpret_cast<uint4*>(sA + (pa * 2 + ttile) * kTcTileBytes + tc_chunk(trow, 3)) = z;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_fence_init();
+    }
+
+    int cp_goff[NCP];
+    bool cp_ok[NCP];
+#pragma unroll
+    for (int q = 0; q < NCP; ++q) {
+        const int idx = tid + q * NT;
+        const int row = idx / ROW, c3 = idx % ROW;
+        const int px = x0 - 1 + c3 / 3, py = y0 - 1 + row;
+        cp_ok[q] = idx < PLANE && px >= 0 && px < NX && py >= 0 && py < NY;
+        cp_goff[q] = cp_ok[q] ? 3 * (py * NX + px) + c3 % 3 : 0;
+    }
+    const unsigned sp_dst = smem_u32(&sp[0][tid]), sE_dst = smem_u32(&sE[0][tid]);
+    const unsigned sB_dst = smem_u32(&sB[0][own3]), sD_dst = smem_u32(&sD[0][own3]);
+    const float cd = (float)a.coef[2 * a.step], ca = (float)a.coef[2 * a.step + 1];
+    const bool need_d = cd != 0.f;
+
+    auto copy_plane = [&](int pz) {
+        const bool zok = pz >= 0 && pz < NZ;
+        const float* base = a.xin + 3 * (zok ? pz : 0) * NXY;
+        const unsigned dst = sp_dst + 4u * (unsigned)(((pz - kb) & (kRing - 1)) * PLANE);
+#pragma unroll
+        for (int q = 0; q < NCP; ++q)
+            if (tid + q * NT < PLANE) cp_async4(dst + 4u * q * NT, base + cp_goff[q], zok && cp_ok[q]);
+    };
+    // group j: node plane j+4, modulus layer j+3, epilogue operands of plane j+1
+    auto issue = [&](int j) {
+        if (j + 4 <= k1) copy_plane(j + 4);
+        const int le = j + 3;
+        if (le < k1) {
+            const bool ok = cell_in && le >= 0 && le < a.nz;
+            cp_async4(sE_dst + 4u * (unsigned)(((le - kb) & (kRing - 1)) * NT), a.E + (ok ? e_base + le * NEXY : 0),
+                      ok);
+        }
+        const int pe = j + 1;
+        if (owner && pe >= k0 && pe < k1) {
+            const int slot = (pe - kb) & (kRing - 1);
+            const float* src = a.b + 3 * (onode_base + pe * NXY);
+            const unsigned db = sB_dst + 4u * (unsigned)(slot * OWN * 3);
+            cp_async4(db, src, true);
+            cp_async4(db + 4u, src + 1, true);
+            cp_async4(db + 8u, src + 2, true);
+            if (need_d) {
+                const float* srd = a.dold + 3 * (onode_base + pe * NXY);
+                const unsigned dd = sD_dst + 4u * (unsigned)(slot * OWN * 3);
+                cp_async4(dd, srd, true);
+                cp_async4(dd + 4u, srd + 1, true);
+                cp_async4(dd + 8u, srd + 2, true);
+            }
+        }
+        cp_commit();
+    };
+    auto load_mask = [&](int kp) -> uint8_t {
+        return (owner && kp >= k0 && kp < k1) ? a.mask[onode_base + kp * NXY] : (uint8_t)7;
+    };
+
+    // ---- prologue (as k_fine; one more epilogue group ahead)
+    copy_plane(kb);
+    cp_commit();
+    issue(k0 - 4);
+    issue(k0 - 3);
+    issue(k0 - 2);
+    asm volatile("cp.async.wait_group 3;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tslot;
+    const unsigned a_base = smem_u32(sA), b_base = smem_u32(sBop);
+    // TMEM address of this thread's row in buffer `buf`, tile `ttile`: lanes 32*(warp%4).., columns (buf*2+tile)*32
+    const unsigned my_d = tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(ttile * 32);
+
+    Layer L0, L1;
+    {
+        const float* pl = sp[0];
+        L0.C[0] = vld(pl + ty * ROW + 3 * tx);
+        L0.C[1] = vld(pl + ty * ROW + 3 * tx + 3);
+        L0.C[2] = vld(pl + (ty + 1) * ROW + 3 * tx);
+        L0.C[3] = vld(pl + (ty + 1) * ROW + 3 * tx + 3);
+        face_diffs(L0.C, L0.Q);
+    }
+    // pipelines: E of the last three layers, x of the owned node at the last three
+    // planes, masks of the next planes
+    float e_h0 = 0.f, e_h1 = 0.f, e_h2 = 0.f, e_prevc = 0.f;
+    V3 u_h0{make_float2(0.f, 0.f), 0.f}, u_h1 = u_h0, u_h2 = u_h0, un_pend = u_h0;
+    uint8_t m_h0 = 7, m_h1 = 7, m_pend = 7;
+    V3 topPrev[4], R1 = u_h0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) topPrev[q] = u_h0;
+    float eR1 = 0.f;
+    bool pending = false;
+    int pend_k = 0;
+    bool failed = false;
+    DSAcc dotv;
+
+    auto wait_mma = [&](int p) -> bool {
+        const int g = p - kb;
+        for (unsigned it = 0; it < kTcSpin; ++it)
+            if (mbar_try_wait(&mbar[g & 1], (g >> 1) & 1)) return true;
+        return false;
+    };
+    auto finish = [&](int kp) {
+        const float4 up = sx[kp & 1][ty + 1][tx];
+        const float y[3] = {R1.xy.x + up.x, R1.xy.y + up.y, R1.z + up.z};
+        const int n = onode_base + kp * NXY;
+        float* out = a.out + 3 * n;
+        const int slot = (kp - kb) & (kRing - 1);
+        const float* bb = &sB[slot][own3];
+        const float* dd = &sD[slot][own3];
+        const float inv = __frcp_rn(a.kd * (eR1 + up.w));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float xn = 0.f, dn = 0.f;
+            if (!fixed_bit(m_pend, c)) {
+                dn = ca * inv * (bb[c] - y[c]);
+                if (need_d) dn = fmaf(cd, dd[c], dn);
+                xn = comp(un_pend, c) + dn;
+                if (DOT) dotv.add_prod(bb[c], xn);
+            }
+            out[c] = xn;
+            if (a.dnew) a.dnew[3 * n + c] = dn;
+        }
+    };
+
+    // step s: MMA of layer s-1, epilogue of plane s-3, modes of layer s, node
+    // sums of plane s-2 (from the MMA of layer s-2)
+    auto step = [&](const int s, const Layer& in, Layer& out) {
+        asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int p1 = s - 1;
+        if (tid == 0 && p1 >= kb && p1 < k1) {
+            constexpr unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+            const unsigned dbuf = tmem + (unsigned)(((p1 - kb) & 1) * 64);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+#pragma unroll
+                for (int pass = 0; pass < PASSES; ++pass) {
+                    const int apart = pass == 1 ? 1 : 0, bpart = pass == 2 ? 1 : 0;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t da = tc_sdesc(a_base + (apart * 2 + t) * kTcTileBytes + ks * 256);
+                        const uint64_t db = tc_sdesc(b_base + bpart * 2048 + ks * 256);
+                        const unsigned acc = (pass > 0 || ks > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dbuf + t * 32),
+                            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar[(p1 - kb) & 1]))
+                         : "memory");
+        }
+        if (pending && owner) finish(pend_k);
+        pending = false;
+        issue(s);
+        // pipelines
+        m_h1 = m_h0;
+        m_h0 = load_mask(s - 1);
+        e_h2 = e_h1;
+        e_h1 = e_h0;
+        u_h2 = u_h1;
+        u_h1 = u_h0;
+        u_h0 = in.C[3];
+        if (s < k1) {
+            // modes of layer s (bottom face in `in`, top plane s+1 from the ring)
+            const float* pl = sp[(s + 1 - kb) & (kRing - 1)];
+            out.C[0] = vld(pl + ty * ROW + 3 * tx);
+            out.C[1] = vld(pl + ty * ROW + 3 * tx + 3);
+            out.C[2] = vld(pl + (ty + 1) * ROW + 3 * tx);
+            out.C[3] = vld(pl + (ty + 1) * ROW + 3 * tx + 3);
+            face_diffs(out.C, out.Q);
+            e_h0 = cell_in ? sE[(s - kb) & (kRing - 1)][tid] : 0.f;
+            V3 v[8];
+            {
+                const V3 z00 = vsub(out.C[0], in.C[0]), z10 = vsub(out.C[1], in.C[1]);
+                const V3 z01 = vsub(out.C[2], in.C[2]), z11 = vsub(out.C[3], in.C[3]);
+                v[4] = vadd(vadd(z00, z10), vadd(z01, z11));
+#pragma unroll
+                for (int q = 1; q < 4; ++q) {
+                    v[q] = vadd(out.Q[q], in.Q[q]);
+                    v[q + 4] = vsub(out.Q[q], in.Q[q]);
+                }
+            }
+            // the A tile is free once the MMA of layer s-1 has completed
+            if (p1 >= kb && !wait_mma(p1)) failed = true;
+            float m21[22];
+#pragma unroll
+            for (int m = 1; m < 8; ++m) {
+                m21[3 * (m - 1)] = v[m].xy.x;
+                m21[3 * (m - 1) + 1] = v[m].xy.y;
+                m21[3 * (m - 1) + 2] = v[m].z;
+            }
+            m21[21] = 0.f;
+            unsigned hi[11], lo[11];
+#pragma unroll
+            for (int q = 0; q < 11; ++q) {
+                hi[q] = bf2(m21[2 * q], m21[2 * q + 1]);
+                if (PASSES > 1) {
+                    const float2 h = unbf2(hi[q]);
+                    lo[q] = bf2(m21[2 * q] - h.x, m21[2 * q + 1] - h.y);
+                }
+            }
+            unsigned char* at = sA + ttile * kTcTileBytes;
+            *reinterpret_cast<uint4*>(at + tc_chunk(trow, 0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(at + tc_chunk(trow, 1)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+            *reinterpret_cast<uint4*>(at + tc_chunk(trow, 2)) = make_uint4(hi[8], hi[9], hi[10], 0u);
+            if (PASSES > 1) {
+                unsigned char* al = sA + (2 + ttile) * kTcTileBytes;
+                *reinterpret_cast<uint4*>(al + tc_chunk(trow, 0)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                *reinterpret_cast<uint4*>(al + tc_chunk(trow, 1)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+                *reinterpret_cast<uint4*>(al + tc_chunk(trow, 2)) = make_uint4(lo[8], lo[9], lo[10], 0u);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        // node sums of plane p = s-2 from the corner forces of layer p
+        const int p = s - 2;
+        if (p >= kb && p < k1) {
+            if (!wait_mma(p)) failed = true;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            unsigned d[24];
+            const unsigned taddr = my_d + (unsigned)(((p - kb) & 1) * 64);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+                  "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]), "=r"(d[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(d[16]), "=r"(d[17]), "=r"(d[18]), "=r"(d[19]), "=r"(d[20]), "=r"(d[21]), "=r"(d[22]),
+                           "=r"(d[23])
+                         : "r"(taddr + 16u));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const float E = e_h2;
+            const float2 E2 = make_float2(E, E);
+            V3 bot[4], top[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                bot[q] = V3{__fmul2_rn(E2, make_float2(__uint_as_float(d[3 * q]), __uint_as_float(d[3 * q + 1]))),
+                            E * __uint_as_float(d[3 * q + 2])};
+                top[q] = V3{__fmul2_rn(E2, make_float2(__uint_as_float(d[12 + 3 * q]), __uint_as_float(d[13 + 3 * q]))),
+                            E * __uint_as_float(d[14 + 3 * q])};
+            }
+            if (p >= k0) {
+                const V3 c00 = vadd(topPrev[0], bot[0]), c10 = vadd(topPrev[1], bot[1]);
+                const V3 c01 = vadd(topPrev[2], bot[2]), c11 = vadd(topPrev[3], bot[3]);
+                V3 n01, n00;
+                n01.xy.x = __shfl_down_sync(0xffffffffu, c01.xy.x, 1, BX);
+                n01.xy.y = __shfl_down_sync(0xffffffffu, c01.xy.y, 1, BX);
+                n01.z = __shfl_down_sync(0xffffffffu, c01.z, 1, BX);
+                n00.xy.x = __shfl_down_sync(0xffffffffu, c00.xy.x, 1, BX);
+                n00.xy.y = __shfl_down_sync(0xffffffffu, c00.xy.y, 1, BX);
+                n00.z = __shfl_down_sync(0xffffffffu, c00.z, 1, BX);
+                R1 = vadd(c11, n01);
+                const V3 r0 = vadd(c10, n00);
+                const float es = e_prevc + E;
+                const float er = es + __shfl_down_sync(0xffffffffu, es, 1, BX);
+                sx[p & 1][ty][tx] = make_float4(r0.xy.x, r0.xy.y, r0.z, er);
+                pending = true;
+                pend_k = p;
+                eR1 = er;
+                un_pend = u_h2;
+                m_pend = m_h1;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) topPrev[q] = top[q];
+            e_prevc = E;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    };
+
+    int s = kb;
+#pragma unroll 1
+    for (; s + 1 <= k1 + 2; s += 2) {
+        step(s, L0, L1);
+        step(s + 1, L1, L0);
+        if (__syncthreads_or(failed)) break;
+    }
+    if (!failed && s <= k1 + 2) step(s, L0, L1);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    const bool bad = __syncthreads_or(failed);
+    if (!bad && pending && owner) finish(pend_k);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    if (bad) {
+        if (tid == 0) atomicExch(a.err, 1);
+        return;
+    }
+    if (DOT) {
+        const double sum = block_sum<NT>(dotv.value(), tid);
+        if (tid == 0) a.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = sum;
+    }
+}
+
 // Copies x with the fixed DOFs of the fine level set to 0 (operands supplied by
 // a caller may hold values there; the operator ignores them).
 __global__ void k_mask_copy(const float* x, const uint8_t* mask, long long nn, float* out) {
@@ -478,6 +872,91 @@ void launch_fine(int mode, int dot, int mask_in, const FineArgs& a_in, const GHa
         else launch_shape<FM_SMOOTH, false>(pl, a, G, s);
     } else {
         launch_shape<FM_RESID, false>(pl, a, G, s);
+    }
+}
+
+// Operand B of the tensor-core smoother: row o = the 24 corner forces of an
+// element (bottom face corners 00, 10, 01, 11 then the top face, 3 components
+// each), column j = the 21 Hadamard modes (monomial m = 1..7, component c:
+// j = 3 (m - 1) + c), i.e. G composed with the face split and the corner
+// expansion of k_fine, evaluated in FP64 on unit modes.  Stored as BF16 hi and
+// lo = bf16(M - hi) in the MMA's K-major core-matrix layout, 32 x 32 each.
+static uint16_t host_bf16(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even
+    return (uint16_t)(u >> 16);
+}
+static float host_bf16_value(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+void build_tc_operand(const double g[72], uint16_t out[2048]) {
+    double M[24][21] = {};
+    for (int j = 0; j < 21; ++j) {
+        double v[8][3] = {}, w[8][3] = {};
+        v[1 + j / 3][j % 3] = 1.0;
+        for (int sg = 0; sg < 8; ++sg)
+            for (int i = 0; i < 3; ++i) {
+                const int mi = mono(sg, i);
+                if (mi == 0) continue;
+                double acc = 0.0;
+                for (int jj = 0; jj < 3; ++jj) {
+                    const int mj = mono(sg, jj);
+                    if (mj == 0) continue;
+                    acc += g[sg * 9 + i * 3 + jj] * v[mj][jj];
+                }
+                w[mi][i] = acc;
+            }
+        for (int f = 0; f < 2; ++f)
+            for (int c = 0; c < 3; ++c) {
+                double S[4];
+                for (int q = 0; q < 4; ++q) S[q] = f == 0 ? w[q][c] - w[q + 4][c] : w[q][c] + w[q + 4][c];
+                const double pp = S[0] - S[2], qd = S[1] - S[3], r = S[0] + S[2], sd = S[1] + S[3];
+                const double corner[4] = {pp - qd, pp + qd, r - sd, r + sd};
+                for (int q = 0; q < 4; ++q) M[f * 12 + q * 3 + c][j] = corner[q];
+            }
+    }
+    std::memset(out, 0, 2048 * sizeof(uint16_t));
+    for (int o = 0; o < 24; ++o)
+        for (int j = 0; j < 21; ++j) {
+            const int idx = ((o >> 3) * 4 + (j >> 3)) * 64 + (o & 7) * 8 + (j & 7);
+            const uint16_t hi = host_bf16((float)M[o][j]);
+            out[idx] = hi;
+            out[1024 + idx] = host_bf16((float)(M[o][j] - (double)host_bf16_value(hi)));
+        }
+}
+
+namespace {
+template <int BX, int BY, int PASSES, bool DOT>
+void launch_tc_tile(const FinePlan& pl, const FineArgs& a, cudaStream_t s) {
+    constexpr int dyn = (PASSES > 1 ? 2 : 1) * 2 * kTcTileBytes + 4096;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_fine_tc<BX, BY, PASSES, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        attr = true;
+    }
+    k_fine_tc<BX, BY, PASSES, DOT><<<pl.grid, dim3(BX, BY), dyn, s>>>(a, pl.zc);
+}
+template <int PASSES, bool DOT>
+void launch_tc_shape(const FinePlan& pl, const FineArgs& a, cudaStream_t s) {
+    if (pl.tile == 0) launch_tc_tile<32, 8, PASSES, DOT>(pl, a, s);
+    else launch_tc_tile<16, 16, PASSES, DOT>(pl, a, s);
+}
+}  // namespace
+
+void launch_fine_tc(int passes, int dot, const FineArgs& a, cudaStream_t s) {
+    const FinePlan pl = plan_fine(a.nx, a.ny, a.nz);
+    note_launch();
+    if (passes > 1) {
+        if (dot) launch_tc_shape<3, true>(pl, a, s);
+        else launch_tc_shape<3, false>(pl, a, s);
+    } else {
+        if (dot) launch_tc_shape<1, true>(pl, a, s);
+        else launch_tc_shape<1, false>(pl, a, s);
     }
 }
 

@@ -216,7 +216,8 @@ struct gmg_handle {
     double eps = 0.0;
     gmg::CoarseFused cf{};                      // fused lower V-cycle (levels cf.start..L-1)
     bool use_fused = false;
-    int* kerr = nullptr;                        // sticky error word of the TMA-staged operator
+    int* kerr = nullptr;                        // sticky error word of the TMA / tensor-core kernels
+    void* tcB = nullptr;                        // tensor-core smoother operand (device, 4 KB)
     // device-resident PCG loop: a CUDA graph [restart, step, check, while{direction, step, check}]
     cudaStream_t cap_stream = nullptr;          // private stream used only to capture the graph
     cudaGraph_t loop_graph = nullptr;
@@ -248,6 +249,8 @@ struct FineArgs {
     double* partial;       // per-block partial dots (nullptr = none)
     float kd;
     float* scratch;        // fine-level vector used to mask a caller's operand (apply only)
+    const void* tcB;       // tensor-core smoother: BF16 mode-to-corner operand (hi, lo), 4 KB
+    int* err;              // sticky error word (a tensor-core wait that gave up)
 };
 
 int fine_grid_blocks(int nx, int ny, int nz);
@@ -255,6 +258,10 @@ int fine_grid_blocks(int nx, int ny, int nz);
 // values there, e.g. user input); internal vectors are already 0 on them.
 void launch_fine(int mode, int dot, int mask_in, const FineArgs& a, const GHat& G, cudaStream_t s);
 void launch_hadamard_blocks(const double* Ke, double* g72, cudaStream_t s);
+// Tensor-core fine smoother step (SMOOTH mode): passes = 1 (BF16) or 3 (split BF16).
+void launch_fine_tc(int passes, int dot, const FineArgs& a, cudaStream_t s);
+// Host: the BF16 hi/lo mode-to-corner operand of the tensor-core smoother from G.
+void build_tc_operand(const double g[72], uint16_t out[2048]);
 int resid64_grid_blocks(int nx, int ny, int nz);
 void launch_fine_smooth0(const FineArgs& a, cudaStream_t s);
 void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,

@@ -28,6 +28,10 @@ class GMGError(RuntimeError):
         self.code = code
 
 
+# arithmetic of the fine-level smoother's element contraction (gmg_options.fine_smoother)
+FINE_SMOOTHERS = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+
+
 class _Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
 
@@ -44,7 +48,8 @@ class _Options(ctypes.Structure):
                 ("power_iters_fine", ctypes.c_int), ("power_iters_coarse", ctypes.c_int),
                 ("chol_cutoff", ctypes.c_int), ("fused_coarse_nodes", ctypes.c_int),
                 ("bsr_tma_nodes", ctypes.c_int), ("device_loop", ctypes.c_int),
-                ("ir_factor", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("ir_factor", ctypes.c_double),
+                ("fine_smoother", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class _Info(ctypes.Structure):
@@ -137,7 +142,7 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
             alpha: float = 1.0 / 30.0, lambda_safety: float = 1.1, power_iters_fine: int = 20,
             power_iters_coarse: int = 10, chol_cutoff: int = 5000, fused_coarse_nodes: int = 4096,
             bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
-            stream: int | None = None) -> _Options:
+            fine_smoother: str = "fp32", stream: int | None = None) -> _Options:
     o = _Options()
     load_library().gmg_default_options(ctypes.byref(o))
     o.levels = levels
@@ -156,16 +161,19 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
     o.bsr_tma_nodes = bsr_tma_nodes
     o.device_loop = 1 if device_loop else 0
     o.ir_factor = ir_factor
+    o.fine_smoother = FINE_SMOOTHERS[fine_smoother]
     o.stream = stream
     return o
 
 
 def config_options(cfg, stream: int | None = None, fused_coarse_nodes: int = 4096,
-                   bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0) -> _Options:
+                   bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
+                   fine_smoother: str = "fp32") -> _Options:
     """Options for one of the synthetic configurations in ``inputs.CONFIGS``."""
     return options(levels=cfg.levels, smoother=cfg.smoother, degree=cfg.degree, coarse_smoother=None,
                    coarse_degree=None, omega=cfg.omega, coarse_omega=None, fused_coarse_nodes=fused_coarse_nodes,
-                   bsr_tma_nodes=bsr_tma_nodes, device_loop=device_loop, ir_factor=ir_factor, stream=stream)
+                   bsr_tma_nodes=bsr_tma_nodes, device_loop=device_loop, ir_factor=ir_factor,
+                   fine_smoother=fine_smoother, stream=stream)
 
 
 def residual64_noalloc(dims, E, mask, f, u, r=None, nu: float = 0.3, stream: int | None = None) -> float:

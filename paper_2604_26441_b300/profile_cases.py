@@ -4,6 +4,7 @@
     python -m paper_2604_26441_b300.profile_cases solve-c2-hostloop  # the same, PCG driven from the host
     python -m paper_2604_26441_b300.profile_cases smooth-c2   # set-up + 3 fine smoothing passes
     python -m paper_2604_26441_b300.profile_cases apply-c2    # set-up + 5 fine operator applies
+    python -m paper_2604_26441_b300.profile_cases smooth-c2-bf16x3  # fine smoothing, tensor-core contraction
 
 Each case prints the library's kernel-launch counter after set-up, so that
 ``ncu -s`` can skip the set-up kernels.  The solve normally runs its PCG
@@ -58,8 +59,9 @@ def main(case: str) -> None:
     from paper_2604_26441_b300 import gmg, inputs
 
     cfg = inputs.CONFIGS["c2"]
+    fine = "bf16x3" if case.endswith("-bf16x3") else "fp32"
     S = gmg.Solver(torch.from_numpy(cfg.rho()).cuda(), p=cfg.p,
-                   opts=gmg.config_options(cfg, device_loop=case != "solve-c2-hostloop"))
+                   opts=gmg.config_options(cfg, device_loop=case != "solve-c2-hostloop", fine_smoother=fine))
     torch.cuda.synchronize()
     print("setup launches", gmg.kernel_launches(), flush=True)
     if case in ("solve-c2", "solve-c2-hostloop"):
@@ -67,11 +69,11 @@ def main(case: str) -> None:
         for _ in range(2):
             u, info = S.solve(f, tol=cfg.tol, maxit=cfg.maxit)
             print(info, flush=True)
-    elif case in ("smooth-c2", "apply-c2"):
+    elif case in ("smooth-c2", "smooth-c2-bf16x3", "apply-c2"):
         x = torch.from_numpy(inputs.random_free_vector(cfg.fixed(), 1)).cuda()
         y = torch.from_numpy(inputs.random_free_vector(cfg.fixed(), 2)).cuda()
-        for _ in range(3 if case == "smooth-c2" else 5):
-            if case == "smooth-c2":
+        for _ in range(3 if case.startswith("smooth-c2") else 5):
+            if case.startswith("smooth-c2"):
                 S.level_smooth(0, x, y)
             else:
                 S.apply(x, y)

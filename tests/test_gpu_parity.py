@@ -442,3 +442,58 @@ def test_iterative_refinement_reaches_fp64_tolerance(cfg_name):
     S2 = gpu_solver(c.rho(), c.p, **config_opts(c), ir_factor=1e-3, device_loop=False)
     u2, info2 = S2.solve(_t(f, torch.float64), tol=1e-10, maxit=400)
     assert np.array_equal(u, u2.cpu().numpy()) and info2["iterations"] == info["iterations"]
+
+
+# ---------------------------------------------------------------------------
+# tensor-core fine smoother (BF16 / split-BF16 element contraction on tcgen05)
+# ---------------------------------------------------------------------------
+TC_MODES = [pytest.param("bf16x3", 3e-5, id="bf16x3"), pytest.param("bf16", 2e-2, id="bf16")]
+
+
+@pytest.mark.parametrize("mode,tol", TC_MODES)
+@pytest.mark.parametrize("name,nx,ny,nz,levels", [("c0", 16, 8, 8, 3), ("ragged", 23, 11, 9, 3), ("c1", 40, 40, 40, 4)])
+def test_tensor_core_smoother_matches_oracle(mode, tol, name, nx, ny, nz, levels):
+    """One fine smoothing pass through the tensor-core kernel against the oracle's
+    FP64 smoother on the same FP32 inputs (Chebyshev degree 3 exercises the
+    increment recurrence and the zero / nonzero initial iterate)."""
+    rho = inputs.filtered_random_density(nx, ny, nz, 3)
+    fixed = inputs.clamp_xmin_mask(nx, ny, nz)
+    opts = dict(levels=levels, smoother="chebyshev", degree=3, coarse_smoother=None, coarse_degree=None, omega=0.5,
+                coarse_omega=None)
+    S = gpu_solver(rho, 3.0, **opts, fine_smoother=mode)
+    H, _ = oracle_hierarchy(rho, 3.0, fixed, levels)
+    S.set_lambda(0, H[0].lam)
+    spec = oracle_spec_from_opts(opts)
+    lev = H[0]
+    rng = np.random.default_rng(21)
+    n = 3 * fem.Grid(nx, ny, nz).n_nodes
+    b = np.zeros(n, dtype=np.float32)
+    b[lev.free] = rng.uniform(-1, 1, lev.n_free)
+    x0 = np.zeros(n, dtype=np.float32)
+    x0[lev.free] = rng.uniform(-1, 1, lev.n_free)
+    xs = S.level_smooth(0, _t(b), _t(x0)).cpu().numpy()
+    ref = np.zeros(n)
+    ref[lev.free] = so.smooth(lev, b[lev.free].astype(np.float64), x0[lev.free].astype(np.float64), spec, 0)
+    assert rel_l2(xs, ref) < tol
+    assert np.all(xs[fixed == 1] == 0)
+
+
+@pytest.mark.parametrize("mode,extra", [("bf16x3", 1), ("bf16", 6)])
+@pytest.mark.parametrize("cfg_name", ["c0", "c1", "c2"])
+def test_tensor_core_smoother_solves(mode, extra, cfg_name):
+    """PCG with the tensor-core fine smoother converges to the FP64-checked
+    tolerance; split BF16 needs at most one more iteration than the FP32 smoother."""
+    c = inputs.CONFIGS[cfg_name]
+    f = c.load()
+    iters = {}
+    for sm in ("fp32", mode):
+        S = gpu_solver(c.rho(), c.p, **config_opts(c), fine_smoother=sm)
+        u, info = S.solve(_t(f, torch.float64), tol=1e-6, maxit=200)
+        assert info["status"] == 0 and info["rel_residual"] < 1e-6
+        iters[sm] = info["iterations"]
+    assert iters[mode] <= iters["fp32"] + extra
+    u = u.cpu().numpy()
+    g = fem.Grid(c.nx, c.ny, c.nz)
+    r = f - fem.matfree_apply(g, fem.moduli(c.rho(), c.p), fem.element_stiffness(0.3), u)
+    free = fem.free_dofs(c.fixed())
+    assert np.linalg.norm(r[free]) / np.linalg.norm(f[free]) < 1e-6
