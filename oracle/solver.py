@@ -15,7 +15,17 @@ Paper passages followed:
   restrict, recurse, prolong-add, post-smooth; coarsest level solved exactly;
 * Sec. "Outer Krylov Solver and Convergence Statement" -- left-preconditioned
   CG with the frozen V-cycle, ||r_k|| / ||b|| < tol accepted only by the true
-  residual; iteration caps and non-finite iterates are failures.
+  residual; iteration caps and non-finite iterates are failures; restarted
+  right-preconditioned flexible GMRES with modified Gram-Schmidt Arnoldi,
+  Givens rotations for the incremental QR update and a happy-breakdown test on
+  the new Hessenberg entry (1e-14), default restart 32;
+* Sec. "Ablations", item (c) -- the W-cycle (cycle index 2);
+* Sec. "Outer Krylov Solver and Convergence Statement" (Remark on the frozen
+  hierarchy) and the appendix on the effective condition number --
+  kappa_eff = lambda_max(M K) / lambda_min(M K), estimated by a Lanczos probe;
+  here the Lanczos tridiagonal is the one CG builds from its coefficients
+  (alpha_k, beta_k), the standard CG-Lanczos correspondence;
+* the same section's symmetry-defect diagnostic of the applied preconditioner.
 
 Readings: the smoother may differ between the fine level and the coarse levels
 (same count before and after the coarse correction); the Chebyshev band uses
@@ -112,6 +122,73 @@ def vcycle(H: list[Level], r: np.ndarray, spec: SmootherSpec, l: int = 0) -> np.
     return smooth(lev, r, x, spec, l)
 
 
+def mgcycle(H: list[Level], b: np.ndarray, spec: SmootherSpec, l: int = 0, gamma: int = 1,
+            x0: np.ndarray | None = None) -> np.ndarray:
+    """Multigrid cycle with cycle index gamma (1: V, 2: W) on level l, from the
+    initial guess x0 (zero if None): pre-smooth, residual, gamma coarse visits
+    (the second one starting from the first one's result), prolong-add,
+    post-smooth; the coarsest level is solved exactly."""
+    lev = H[l]
+    if l == len(H) - 1:
+        return coarse_solve(lev.L, b)
+    x = smooth(lev, b, np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64), spec, l)
+    t = b - lev.apply(x)
+    bc = lev.P.T @ t
+    e = None
+    for _ in range(gamma):
+        e = mgcycle(H, bc, spec, l + 1, gamma, e)
+    x = x + lev.P @ e
+    return smooth(lev, b, x, spec, l)
+
+
+def cg_lanczos_tridiagonal(alphas, betas) -> tuple[np.ndarray, np.ndarray]:
+    """Diagonal and off-diagonal of the Lanczos matrix of the preconditioned
+    operator from k CG steps: T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+    T_{j,j+1} = sqrt(beta_j)/alpha_j (beta_j = r_{j+1}.z_{j+1} / r_j.z_j)."""
+    a = np.asarray(alphas, dtype=np.float64)
+    bt = np.asarray(betas, dtype=np.float64)
+    k = len(a)
+    diag = 1.0 / a
+    diag[1:] += bt[:k - 1] / a[:k - 1]
+    off = np.sqrt(bt[:k - 1]) / a[:k - 1]
+    return diag, off
+
+
+def kappa_eff(H: list[Level], b_free: np.ndarray, spec: SmootherSpec, steps: int,
+              precond=None) -> tuple[float, float, float]:
+    """Lanczos estimate of lambda_min, lambda_max and kappa_eff of M K from
+    `steps` CG steps on K x = b (start vector b), M one V-cycle by default."""
+    lev = H[0]
+    M = precond or (lambda r: vcycle(H, r, spec))
+    r = np.array(b_free, dtype=np.float64)
+    z = M(r)
+    p = z.copy()
+    rz = float(r @ z)
+    alphas, betas = [], []
+    for _ in range(steps):
+        q = lev.apply(p)
+        alpha = rz / float(p @ q)
+        r = r - alpha * q
+        z = M(r)
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        alphas.append(alpha)
+        betas.append(beta)
+        p = z + beta * p
+        rz = rz_new
+    d, o = cg_lanczos_tridiagonal(alphas, betas)
+    T = np.diag(d) + np.diag(o, 1) + np.diag(o, -1)
+    ev = np.linalg.eigvalsh(T)
+    return float(ev[0]), float(ev[-1]), float(ev[-1] / ev[0])
+
+
+def symmetry_defect(precond, x: np.ndarray, y: np.ndarray) -> float:
+    """|x.M(y) - y.M(x)| / max(|x.M(y)|, |y.M(x)|) for the operator M."""
+    a = float(x @ precond(y))
+    b = float(y @ precond(x))
+    return abs(a - b) / max(abs(a), abs(b))
+
+
 @dataclasses.dataclass
 class PCGResult:
     x: np.ndarray
@@ -165,6 +242,75 @@ def pcg(apply_K, precond, f: np.ndarray, x0: np.ndarray | None = None, tol: floa
         rz = rz_new
     rt = f - apply_K(x)
     return PCGResult(x, NOT_CONVERGED, k, float(np.linalg.norm(rt)) / nf, hist)
+
+
+def fgmres(apply_K, precond, f: np.ndarray, x0: np.ndarray | None = None, tol: float = 1e-6,
+           maxit: int = 200, restart: int = 32, breakdown: float = 1e-14) -> PCGResult:
+    """Restarted right-preconditioned flexible GMRES (free-DOF vectors).
+
+    Each cycle starts from the true residual r = f - K x, beta = ||r||,
+    v_1 = r / beta; step j stores z_j = M v_j, forms w = K z_j, orthogonalises
+    it against v_1..v_j by modified Gram-Schmidt (h_ij), h_{j+1,j} = ||w||,
+    applies the previous Givens rotations to column j of H and a new one that
+    annihilates h_{j+1,j}; |g_{j+1}| is the residual norm of the minimiser.
+    The cycle ends at restart, at |g_{j+1}| / ||f|| < tol, or when h_{j+1,j} <
+    breakdown; then x += Z y with H y = g (upper triangular).  A solve is
+    accepted only by the true residual.  `iterations` counts Arnoldi steps."""
+    nf = float(np.linalg.norm(f))
+    x = np.zeros_like(f) if x0 is None else np.array(x0, dtype=np.float64)
+    if nf == 0.0:
+        return PCGResult(np.zeros_like(f), OK, 0, 0.0, [0.0])
+    k = 0
+    hist = []
+    while True:
+        r = f - apply_K(x)
+        beta = float(np.linalg.norm(r))
+        rel = beta / nf
+        hist.append(rel)
+        if not np.isfinite(rel):
+            return PCGResult(x, NONFINITE, k, rel, hist)
+        if rel < tol:
+            return PCGResult(x, OK, k, rel, hist)
+        if k >= maxit:
+            return PCGResult(x, NOT_CONVERGED, k, rel, hist)
+        V = [r / beta]
+        Z = []
+        Hm = np.zeros((restart + 1, restart))
+        cs = np.zeros(restart)
+        sn = np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        j = 0
+        while j < restart and k < maxit:
+            z = precond(V[j])
+            Z.append(z)
+            w = apply_K(z)
+            for i in range(j + 1):
+                Hm[i, j] = float(w @ V[i])
+                w = w - Hm[i, j] * V[i]
+            Hm[j + 1, j] = float(np.linalg.norm(w))
+            for i in range(j):  # previous rotations on column j
+                t = cs[i] * Hm[i, j] + sn[i] * Hm[i + 1, j]
+                Hm[i + 1, j] = -sn[i] * Hm[i, j] + cs[i] * Hm[i + 1, j]
+                Hm[i, j] = t
+            den = np.hypot(Hm[j, j], Hm[j + 1, j])
+            cs[j], sn[j] = Hm[j, j] / den, Hm[j + 1, j] / den
+            happy = Hm[j + 1, j] < breakdown
+            if not happy:
+                V.append(w / Hm[j + 1, j])
+            Hm[j, j] = den
+            Hm[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            j += 1
+            k += 1
+            if happy or abs(g[j]) / nf < tol:
+                break
+        y = np.zeros(j)
+        for i in range(j - 1, -1, -1):
+            y[i] = (g[i] - Hm[i, i + 1:j] @ y[i + 1:j]) / Hm[i, i]
+        for i in range(j):
+            x = x + y[i] * Z[i]
 
 
 def gmg_pcg(H: list[Level], f_full: np.ndarray, spec: SmootherSpec, tol: float = 1e-6,

@@ -179,3 +179,119 @@ def test_pcg_cap_and_nonfinite():
     f[H[0].free[3]] = np.nan
     u, res = so.gmg_pcg(H, f, so.SmootherSpec("jacobi", 2, 0.6))
     assert res.status == so.NONFINITE
+
+
+# ---------------------------------------------------------------------------
+# cycle index (V / W), Lanczos kappa_eff, symmetry defect, FGMRES
+# ---------------------------------------------------------------------------
+def test_mgcycle_gamma1_is_the_vcycle():
+    _, H = _c0_hierarchy(3)
+    spec = so.SmootherSpec("chebyshev", 3)
+    r = np.random.default_rng(3).normal(size=H[0].n_free)
+    assert np.array_equal(so.mgcycle(H, r, spec, gamma=1), so.vcycle(H, r, spec))
+
+
+def test_mgcycle_large_gamma_tends_to_two_grid_with_exact_coarse_solve():
+    """Each revisit of level 1 starts from the previous iterate, so many visits
+    converge to K1^-1 R t: the cycle tends to the two-grid method."""
+    _, H = _c0_hierarchy(3)
+    spec = so.SmootherSpec("jacobi", 2, 0.5)
+    lev, lev1 = H[0], H[1]
+    r = np.random.default_rng(4).normal(size=lev.n_free)
+    x = so.smooth(lev, r, np.zeros_like(r), spec, 0)
+    t = r - lev.apply(x)
+    import scipy.sparse.linalg as spla_
+    e = spla_.spsolve(lev1.K.tocsc(), lev.P.T @ t)
+    two_grid = so.smooth(lev, r, x + lev.P @ e, spec, 0)
+    w = so.mgcycle(H, r, spec, gamma=60)
+    assert np.linalg.norm(w - two_grid) < 1e-8 * np.linalg.norm(two_grid)
+    w2 = so.mgcycle(H, r, spec, gamma=2)
+    assert np.linalg.norm(w2 - two_grid) < np.linalg.norm(so.vcycle(H, r, spec) - two_grid)
+
+
+def test_cg_lanczos_tridiagonal_reproduces_the_spectrum():
+    """n CG steps on diag(d) (no preconditioner): the Lanczos matrix built from
+    the CG coefficients has exactly the eigenvalues d."""
+    d = np.array([0.5, 1.0, 2.0, 3.5, 7.0, 11.0])
+    r = np.ones_like(d)
+    p = r.copy()
+    rz = r @ r
+    al, be = [], []
+    for _ in range(d.size):
+        q = d * p
+        a = rz / (p @ q)
+        r = r - a * q
+        rz_new = r @ r
+        al.append(a)
+        be.append(rz_new / rz)
+        p = r + be[-1] * p
+        rz = rz_new
+    dg, off = so.cg_lanczos_tridiagonal(al, be)
+    T = np.diag(dg) + np.diag(off, 1) + np.diag(off, -1)
+    assert np.allclose(np.sort(np.linalg.eigvalsh(T)), d, rtol=1e-10)
+
+
+def test_kappa_eff_exact_preconditioner_is_one():
+    _, H = _c0_hierarchy(2)
+    lev = H[0]
+    import scipy.linalg as sla
+    c = sla.cho_factor(lev.K.toarray())
+    b = np.random.default_rng(6).normal(size=lev.n_free)
+    lmin, lmax, kap = so.kappa_eff(H, b, so.SmootherSpec(), 1, precond=lambda r: sla.cho_solve(c, r))
+    assert abs(kap - 1.0) < 1e-10 and abs(lmin - 1.0) < 1e-10
+
+
+def test_kappa_eff_of_the_vcycle_is_moderate():
+    _, H = _c0_hierarchy(3)
+    b = np.random.default_rng(7).normal(size=H[0].n_free)
+    lmin, lmax, kap = so.kappa_eff(H, b, so.SmootherSpec("jacobi", 2, 0.6), 12)
+    assert 1.0 < kap < 50.0 and 0 < lmin <= 1.0 + 1e-9
+
+
+def test_symmetry_defect_detects_unmatched_smoothers():
+    _, H = _c0_hierarchy(3)
+    rng = np.random.default_rng(8)
+    x, y = rng.normal(size=(2, H[0].n_free))
+    spec = so.SmootherSpec("chebyshev", 3)
+    assert so.symmetry_defect(lambda r: so.vcycle(H, r, spec), x, y) < 1e-12
+
+    def lopsided(r):  # pre-smoothing Jacobi 0.5, post-smoothing Jacobi 0.3
+        lev = H[0]
+        xx = so.jacobi(lev, r, np.zeros_like(r), 0.5, 2)
+        e = so.vcycle(H, lev.P.T @ (r - lev.apply(xx)), spec, 1)
+        return so.jacobi(lev, r, xx + lev.P @ e, 0.3, 2)
+    assert so.symmetry_defect(lopsided, x, y) > 1e-4
+
+
+@pytest.mark.parametrize("restart", [40, 5])
+def test_fgmres_matches_dense_solve(restart):
+    rng = np.random.default_rng(9)
+    n = 30
+    A = rng.normal(size=(n, n)) + 8.0 * np.eye(n)  # non-symmetric, well conditioned
+    b = rng.normal(size=n)
+    res = so.fgmres(lambda v: A @ v, lambda v: v, b, tol=1e-12, maxit=400, restart=restart)
+    assert res.status == so.OK
+    assert np.linalg.norm(res.x - np.linalg.solve(A, b)) < 1e-10 * np.linalg.norm(np.linalg.solve(A, b))
+    if restart >= n:
+        assert res.iterations <= n
+
+
+def test_fgmres_exact_preconditioner_one_step():
+    rng = np.random.default_rng(10)
+    A = rng.normal(size=(12, 12)) + 5.0 * np.eye(12)
+    Ainv = np.linalg.inv(A)
+    b = rng.normal(size=12)
+    res = so.fgmres(lambda v: A @ v, lambda v: Ainv @ v, b, tol=1e-10)
+    assert res.status == so.OK and res.iterations == 1
+
+
+def test_gmg_fgmres_vs_direct():
+    c = inputs.CONFIGS["c0"]
+    H = hy.build_hierarchy((c.nx, c.ny, c.nz), fem.moduli(c.rho(), c.p), c.fixed(), levels=c.levels)
+    spec = so.SmootherSpec(c.smoother, c.degree, c.omega)
+    lev = H[0]
+    f = c.load()[lev.free]
+    res = so.fgmres(lev.apply, lambda r: so.vcycle(H, r, spec), f, tol=1e-10, restart=32)
+    assert res.status == so.OK
+    x = np.linalg.solve(lev.K.toarray(), f)
+    assert np.linalg.norm(res.x - x) < 1e-8 * np.linalg.norm(x)
