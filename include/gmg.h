@@ -65,6 +65,10 @@ extern "C" {
 #define GMG_FINE_BF16X3 1
 #define GMG_FINE_BF16 2
 
+/* Outer Krylov solver (gmg_options.outer). */
+#define GMG_OUTER_PCG 0
+#define GMG_OUTER_FGMRES 1
+
 typedef struct gmg_handle gmg_handle;
 
 typedef struct {
@@ -112,6 +116,14 @@ typedef struct {
                                     GMG_FINE_BF16 (tensor cores, one BF16 pass).  FP32
                                     accumulation; the PCG operator, residuals and coarser levels
                                     are unaffected. */
+    int cycle_index;             /* multigrid cycle: 1 = V-cycle (default), 2 = W-cycle (each coarse
+                                    level visited twice, the second visit from the first's result;
+                                    Sec. Ablations (c)) */
+    int outer;                   /* GMG_OUTER_PCG (default): left-preconditioned CG;
+                                    GMG_OUTER_FGMRES: restarted right-preconditioned flexible GMRES
+                                    (MGS Arnoldi, Givens rotations, happy breakdown at 1e-14);
+                                    gmg_info.iterations counts Arnoldi steps, .replacements restarts */
+    int restart;                 /* FGMRES restart length (32) */
     void* stream;                /* cudaStream_t for all device work; NULL = default stream */
 } gmg_options;
 
@@ -216,6 +228,20 @@ int gmg_prolong_add(gmg_handle* h, int level, const float* coarse_dev, float* fi
 
 /* x = (K^L_ff + eps I)^-1 b on the coarsest level (FP64 Cholesky factor). */
 int gmg_coarse_solve(gmg_handle* h, const float* b_dev, float* x_dev);
+
+/* Lanczos probe of the effective condition number of the preconditioned
+ * operator M K (M = one multigrid cycle): `steps` CG iterations on K x = b from
+ * x = 0 (b: device FP64, fixed DOFs ignored), the Lanczos tridiagonal built
+ * from the CG coefficients (T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+ * T_{j,j+1} = sqrt(beta_j)/alpha_j), its extreme eigenvalues by Sturm-sequence
+ * bisection.  out = {lambda_min, lambda_max, kappa_eff}.  Stops early at a
+ * breakdown (beta = 0).  Synchronous. */
+int gmg_kappa_eff(gmg_handle* h, const double* b_dev, int steps, double out[3]);
+
+/* Symmetry defect of the applied preconditioner: |x.M(y) - y.M(x)| /
+ * max(|x.M(y)|, |y.M(x)|) for one multigrid cycle M (x, y device FP32, zero on
+ * fixed DOFs).  0 in exact arithmetic for matched pre/post smoothers. */
+int gmg_vcycle_symmetry(gmg_handle* h, const float* x_dev, const float* y_dev, double* defect);
 
 /* z = V(r): one V-cycle of Eq. vcycle on the fine level. */
 int gmg_vcycle(gmg_handle* h, const float* r_dev, float* z_dev);

@@ -3,6 +3,7 @@
 // (Sec. "Outer Krylov Solver and Convergence Statement").  Host code here only
 // sequences kernels and moves scalars; every arithmetic step runs on the GPU.
 #include <algorithm>
+#include <vector>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -167,11 +168,14 @@ float* smooth_pass(gmg_handle* h, int li, const float* b, float* cur, float* X, 
     return cur;
 }
 
-// Eq. vcycle on level li: X = V(b), using S as the ping-pong partner.
-void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int dot_slot, int op) {
+// Eq. vcycle on level li: X = V(b), using S as the ping-pong partner.  With
+// cycle index 2 (W-cycle) the coarse level is visited twice, the second visit
+// starting from the first one's result (warm: pre-smoothing from the current X).
+void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int dot_slot, int op,
+                  bool warm = false) {
     Level& l = h->lev[li];
     cudaStream_t s = h->stream;
-    if (h->use_fused && li == h->cf.start) {
+    if (h->use_fused && li == h->cf.start && !warm) {
         // levels li..L-1 and the coarsest solve in one persistent kernel; b and X
         // are this level's own b and x buffers on this path
         launch_coarse_fused(h->cf, h->fused_blocks, s);
@@ -182,12 +186,13 @@ void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int
         return;
     }
     int writes = 0;
-    float* cur = smooth_pass(h, li, b, nullptr, X, S, true, writes);
+    float* cur = smooth_pass(h, li, b, warm ? X : nullptr, X, S, !warm, writes);
     float* t = li == 0 ? h->t0 : l.t;
     level_resid(h, li, b, cur, t);
     Level& c = h->lev[li + 1];
     launch_restrict(l, c, t, c.b, s);
-    vcycle_level(h, li + 1, c.b, c.x, c.x2, -1, FIN_NONE);
+    const int gamma = li + 1 == h->L - 1 ? 1 : std::max(1, h->opt.cycle_index);  // exact coarsest: one visit
+    for (int g = 0; g < gamma; ++g) vcycle_level(h, li + 1, c.b, c.x, c.x2, -1, FIN_NONE, g > 0);
     launch_prolong_add(l, c, c.x, cur, s);
     smooth_pass(h, li, b, cur, X, S, false, writes, dot_slot, op);
 }
@@ -461,7 +466,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         }
     }
     // ---- fused lower V-cycle: every assembled level below the node threshold
-    if (o.fused_coarse_nodes > 0 && L >= 2) {
+    if (o.fused_coarse_nodes > 0 && L >= 2 && o.cycle_index <= 1) {
         int start = L - 1;
         while (start - 1 >= 1 && h->lev[start - 1].nn < o.fused_coarse_nodes) --start;
         if (h->lev[start].nn < o.fused_coarse_nodes || start == L - 1) {
@@ -597,6 +602,128 @@ int loop_build(gmg_handle* h, double* u) {
     return GMG_OK;
 }
 
+// ---- diagnostics: extreme eigenvalues of a symmetric tridiagonal matrix by
+// Sturm-sequence bisection (number of eigenvalues below x from the LDL^T pivots)
+int sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
+    int c = 0;
+    double q = 1.0;
+    for (size_t i = 0; i < d.size(); ++i) {
+        const double e2 = i > 0 ? e[i - 1] * e[i - 1] : 0.0;
+        q = d[i] - x - (i > 0 ? e2 / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0.0) ++c;
+    }
+    return c;
+}
+
+double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e, int k) {
+    // k-th smallest eigenvalue (k = 1..n) within the Gershgorin interval
+    double lo = d[0], hi = d[0];
+    for (size_t i = 0; i < d.size(); ++i) {
+        const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < d.size() ? std::fabs(e[i]) : 0.0);
+        lo = std::min(lo, d[i] - r);
+        hi = std::max(hi, d[i] + r);
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(d, e, mid) >= k) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Restarted right-preconditioned flexible GMRES (Sec. "Outer Krylov Solver and
+// Convergence Statement"): modified Gram-Schmidt Arnoldi on FP32 vectors with
+// FP64-accumulated inner products, Givens rotations on the host, a happy
+// breakdown when the new Hessenberg entry drops below 1e-14, the update
+// u += Z y accumulated in FP64, and every cycle started from (and every
+// solve accepted by) the FP64 true residual.
+int fgmres_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, double nf, gmg_info& inf) {
+    cudaStream_t s = h->stream;
+    Level& l0 = h->lev[0];
+    const long long n = 3 * l0.nn;
+    const int m = h->opt.restart;
+    if (h->fg_m != m) {
+        dfree(h, h->fg_V);
+        dfree(h, h->fg_Z);
+        dfree(h, h->fg_h);
+        h->fg_V = h->fg_Z = nullptr;
+        h->fg_h = nullptr;
+        TRY(dalloc(h, &h->fg_V, (size_t)(m + 1) * n));
+        TRY(dalloc(h, &h->fg_Z, (size_t)m * n));
+        TRY(dalloc(h, &h->fg_h, (size_t)m + 2));
+        h->fg_m = m;
+    }
+    double* sch = h->sc_host;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 2), y(m);
+    int k = 0;
+    while (true) {
+        double rel = 0.0;
+        launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, h->sc, h->partials, h->gh64, s);
+        launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
+        TRY(sync_scalars(h));
+        const double beta = std::sqrt(sch[SC_TRR]);
+        rel = beta / nf;
+        inf.rel_residual = rel;
+        inf.iterations = k;
+        if (!std::isfinite(rel)) return GMG_NONFINITE;
+        if (rel < tol) return GMG_OK;
+        if (k >= maxit) return GMG_NOT_CONVERGED;
+        if (k > 0) ++inf.replacements;  // restarts
+        float* V0 = h->fg_V;
+        CU(cudaMemcpyAsync(V0, h->r, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+        launch_scale_by_inv_sqrt(V0, n, h->sc, SC_TRR, s);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int j = 0;
+        bool stop = false;
+        while (j < m && k < maxit && !stop) {
+            float* Vj = h->fg_V + (size_t)j * n;
+            float* Zj = h->fg_Z + (size_t)j * n;
+            float* W = h->fg_V + (size_t)(j + 1) * n;
+            vcycle_level(h, 0, Vj, Zj, h->x2_0, -1, FIN_NONE);   // z_j = M v_j
+            level_apply(h, 0, Zj, W);                             // w = K z_j
+            for (int i = 0; i <= j; ++i) {                        // modified Gram-Schmidt
+                const float* Vi = h->fg_V + (size_t)i * n;
+                launch_dot_f32(W, Vi, n, h->partials, s);
+                launch_finalize(h->partials, vec_grid_blocks(), h->fg_h, i, FIN_NONE, s);
+                launch_axpy_dev(W, Vi, n, h->fg_h + i, -1.f, s);
+            }
+            launch_dot_f32(W, W, n, h->partials, s);
+            launch_finalize(h->partials, vec_grid_blocks(), h->fg_h, j + 1, FIN_NONE, s);
+            launch_scale_by_inv_sqrt(W, n, h->fg_h, j + 1, s);    // v_{j+1} = w / ||w||
+            CU(cudaMemcpyAsync(hcol.data(), h->fg_h, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+            double hn = std::sqrt(std::max(hcol[j + 1], 0.0));
+            if (!std::isfinite(hn)) return GMG_NONFINITE;
+            for (int i = 0; i < j; ++i) {  // previous rotations on column j
+                const double a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+            }
+            const double hjj = H[(size_t)j * m + j];
+            const double den = std::hypot(hjj, hn);
+            const bool happy = hn < 1e-14;
+            cs[j] = hjj / den;
+            sn[j] = hn / den;
+            H[(size_t)j * m + j] = den;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++j;
+            ++k;
+            inf.rel_residual_recursive = std::fabs(g[j]) / nf;
+            stop = happy || std::fabs(g[j]) / nf < tol;
+        }
+        for (int i = j - 1; i >= 0; --i) {  // H y = g
+            double acc = g[i];
+            for (int q = i + 1; q < j; ++q) acc -= H[(size_t)i * m + q] * y[q];
+            y[i] = acc / H[(size_t)i * m + i];
+        }
+        for (int i = 0; i < j; ++i) launch_axpy_u64(u, h->fg_Z + (size_t)i * n, n, y[i], s);
+    }
+}
+
 // Reports a timed-out wait of the TMA-staged operator or of the fused lower
 // V-cycle (both error words are sticky).
 int check_fused(gmg_handle* h) {
@@ -634,6 +761,9 @@ void gmg_default_options(gmg_options* o) {
     o->device_loop = 1;
     o->ir_factor = 0.0;
     o->fine_smoother = GMG_FINE_FP32;
+    o->cycle_index = 1;
+    o->outer = GMG_OUTER_PCG;
+    o->restart = 32;
     o->stream = nullptr;
 }
 
@@ -692,6 +822,9 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
     if (!(o.ir_factor >= 0.0 && o.ir_factor < 1.0)) return fail(GMG_ERR_ARG, "ir_factor must be in [0, 1)");
     if (o.fine_smoother != GMG_FINE_FP32 && o.fine_smoother != GMG_FINE_BF16 && o.fine_smoother != GMG_FINE_BF16X3)
         return fail(GMG_ERR_ARG, "unknown fine_smoother");
+    if (o.cycle_index < 1 || o.cycle_index > 2) return fail(GMG_ERR_ARG, "cycle_index must be 1 (V) or 2 (W)");
+    if (o.outer != GMG_OUTER_PCG && o.outer != GMG_OUTER_FGMRES) return fail(GMG_ERR_ARG, "unknown outer solver");
+    if (o.restart < 1 || o.restart > 256) return fail(GMG_ERR_ARG, "restart must be in [1, 256]");
     if (o.power_iters_fine < 1 || o.power_iters_coarse < 1 || o.chol_cutoff < 1)
         return fail(GMG_ERR_ARG, "bad iteration counts or cutoff");
 
@@ -785,6 +918,12 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     // FP64 residual of the current u, stops once its recursive residual is
     // ir_factor times smaller (but not below tol); the FP64 residual
     // replacement and restart that follow are the outer refinement step.
+    if (h->opt.outer == GMG_OUTER_FGMRES) {
+        const int st = fgmres_solve(h, f, u, tol, maxit, nf, inf);
+        if (st < 0) return st;
+        CU(cudaGetLastError());
+        return finish(st);
+    }
     const double irf = h->opt.ir_factor;
     auto inner_target = [&](double rel_start) { return irf > 0.0 ? std::max(tol, irf * rel_start) : tol; };
     double target = inner_target(rel);
@@ -861,6 +1000,57 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     inf.rel_residual = rel;
     CU(cudaGetLastError());
     return finish(GMG_NOT_CONVERGED);
+}
+
+int gmg_kappa_eff(gmg_handle* h, const double* b, int steps, double out[3]) {
+    if (!h || !b || !out) return fail(GMG_ERR_ARG, "null argument");
+    if (steps < 1 || steps > 1000) return fail(GMG_ERR_ARG, "steps must be in [1, 1000]");
+    if (h->L == 1) return fail(GMG_ERR_ARG, "single-level hierarchy");
+    cudaStream_t s = h->stream;
+    Level& l0 = h->lev[0];
+    const long long n = 3 * l0.nn;
+    if (!h->kap_u) TRY(dalloc(h, &h->kap_u, (size_t)n));
+    CU(cudaMemsetAsync(h->kap_u, 0, sizeof(double) * n, s));
+    launch_cast_masked(b, l0.mask, l0.nn, h->r, s);
+    pcg_restart(h);
+    std::vector<double> al, be;
+    for (int k = 0; k < steps; ++k) {
+        pcg_step(h, h->kap_u);
+        pcg_direction(h);
+        TRY(sync_scalars(h));
+        const double a = h->sc_host[SC_ALPHA], bt = h->sc_host[SC_BETA];
+        if (!(std::isfinite(a) && a > 0.0 && std::isfinite(bt) && bt >= 0.0)) break;
+        al.push_back(a);
+        be.push_back(bt);
+        if (bt == 0.0) break;
+    }
+    if (al.empty()) return fail(GMG_NONFINITE, "the Lanczos probe broke down at its first step");
+    // Lanczos matrix from the CG coefficients
+    const size_t kk = al.size();
+    std::vector<double> d(kk), e(kk > 1 ? kk - 1 : 1, 0.0);
+    for (size_t j = 0; j < kk; ++j) d[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    for (size_t j = 0; j + 1 < kk; ++j) e[j] = std::sqrt(be[j]) / al[j];
+    out[0] = tridiag_eig(d, e, 1);
+    out[1] = tridiag_eig(d, e, (int)kk);
+    out[2] = out[1] / out[0];
+    return GMG_OK;
+}
+
+int gmg_vcycle_symmetry(gmg_handle* h, const float* x, const float* y, double* defect) {
+    if (!h || !x || !y || !defect) return fail(GMG_ERR_ARG, "null argument");
+    if (h->L == 1) return fail(GMG_ERR_ARG, "single-level hierarchy");
+    cudaStream_t s = h->stream;
+    const long long n = 3 * h->lev[0].nn;
+    vcycle_level(h, 0, y, h->z, h->x2_0, -1, FIN_NONE);   // M y
+    vcycle_level(h, 0, x, h->p, h->x2_0, -1, FIN_NONE);   // M x
+    launch_dot_f32(x, h->z, n, h->partials, s);
+    launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_TMP, FIN_NONE, s);
+    launch_dot_f32(y, h->p, n, h->partials, s);
+    launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_TMP + 1, FIN_NONE, s);
+    TRY(sync_scalars(h));
+    const double a = h->sc_host[SC_TMP], b = h->sc_host[SC_TMP + 1];
+    *defect = std::fabs(a - b) / std::max(std::fabs(a), std::fabs(b));
+    return GMG_OK;
 }
 
 int gmg_num_levels(const gmg_handle* h) { return h ? h->L : 0; }

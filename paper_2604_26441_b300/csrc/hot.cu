@@ -684,6 +684,19 @@ __global__ void __launch_bounds__(kVecThreads) k_mask_u64(double* u, const uint8
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// y += sign * (*coef) * x (FP32 vectors, coefficient from device memory).
+__global__ void k_axpy_dev(float* y, const float* x, long long n, const double* coef, float sign) {
+    const float c = sign * (float)coef[0];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = fmaf(c, x[i], y[i]);
+}
+
+// u += a * z, accumulated in FP64.
+__global__ void k_axpy_u64(double* u, const float* z, long long n, double a) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        u[i] = fma(a, (double)z[i], u[i]);
+}
+
 __global__ void k_loop_check(double* sc, cudaGraphConditionalHandle cond) {
     if (threadIdx.x != 0) return;
     const double k = sc[SC_IT] + 1.0;
@@ -959,6 +972,16 @@ void launch_p_update(float* p, const float* z, long long n, const double* sc, cu
 void launch_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial, cudaStream_t s) {
     note_launch();
     k_mask_u64<<<kVecBlocks, kVecThreads, 0, s>>>(u, mask, nn, partial);
+}
+
+void launch_axpy_dev(float* y, const float* x, long long n, const double* coef, float sign, cudaStream_t s) {
+    note_launch();
+    k_axpy_dev<<<grid_for(n), 256, 0, s>>>(y, x, n, coef, sign);
+}
+
+void launch_axpy_u64(double* u, const float* z, long long n, double a, cudaStream_t s) {
+    note_launch();
+    k_axpy_u64<<<grid_for(n), 256, 0, s>>>(u, z, n, a);
 }
 
 void launch_loop_check(double* sc, cudaGraphConditionalHandle cond, cudaStream_t s) {

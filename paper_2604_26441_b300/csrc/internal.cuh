@@ -225,6 +225,13 @@ struct gmg_handle {
     const double* loop_u = nullptr;             // iterate the captured graph updates
     unsigned long long loop_prefix_kernels = 0, loop_body_kernels = 0;
     bool loop_unavailable = false;              // capture failed once: use the host loop
+    // restarted FGMRES (outer = 1): Arnoldi basis V (restart + 1 vectors),
+    // preconditioned directions Z (restart vectors), Hessenberg column (device)
+    float* fg_V = nullptr;
+    float* fg_Z = nullptr;
+    double* fg_h = nullptr;
+    int fg_m = 0;
+    double* kap_u = nullptr;                    // FP64 scratch iterate of the kappa_eff probe
     int fused_blocks = 0;
     std::vector<void*> allocs;                  // every device allocation, freed by gmg_destroy
     void* pinned = nullptr;                     // pinned host block (sc_host)
@@ -314,6 +321,8 @@ void launch_cast_masked(const double* f, const uint8_t* mask, long long nn, floa
 // the while-node condition to 1 while ||r|| / ||f|| >= tol, the scalars are
 // finite and the cap is not reached.
 void launch_loop_check(double* sc, cudaGraphConditionalHandle cond, cudaStream_t s);
+void launch_axpy_dev(float* y, const float* x, long long n, const double* coef, float sign, cudaStream_t s);
+void launch_axpy_u64(double* u, const float* z, long long n, double a, cudaStream_t s);
 void launch_scale_by_inv_sqrt(float* v, long long n, const double* sc, int slot, cudaStream_t s);
 void launch_scale_invdiag_fine(const float* y, float* w, const float* E, const uint8_t* mask,
                                int nx, int ny, int nz, float kd, cudaStream_t s);

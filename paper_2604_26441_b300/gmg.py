@@ -49,7 +49,9 @@ class _Options(ctypes.Structure):
                 ("chol_cutoff", ctypes.c_int), ("fused_coarse_nodes", ctypes.c_int),
                 ("bsr_tma_nodes", ctypes.c_int), ("device_loop", ctypes.c_int),
                 ("ir_factor", ctypes.c_double),
-                ("fine_smoother", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("fine_smoother", ctypes.c_int),
+                ("cycle_index", ctypes.c_int), ("outer", ctypes.c_int), ("restart", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class _Info(ctypes.Structure):
@@ -85,6 +87,8 @@ _SIGS = {
     "gmg_prolong_add": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "gmg_coarse_solve": (ctypes.c_int, [_P, _P, _P]),
     "gmg_vcycle": (ctypes.c_int, [_P, _P, _P]),
+    "gmg_kappa_eff": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "gmg_vcycle_symmetry": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gmg_residual64": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gmg_residual64_noalloc": (ctypes.c_int, [ctypes.POINTER(_Grid), _P, _P, ctypes.c_double, _P, _P, _P,
                                               ctypes.POINTER(ctypes.c_double), _P]),
@@ -142,7 +146,8 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
             alpha: float = 1.0 / 30.0, lambda_safety: float = 1.1, power_iters_fine: int = 20,
             power_iters_coarse: int = 10, chol_cutoff: int = 5000, fused_coarse_nodes: int = 4096,
             bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
-            fine_smoother: str = "fp32", stream: int | None = None) -> _Options:
+            fine_smoother: str = "fp32", cycle: str = "V", outer: str = "pcg", restart: int = 32,
+            stream: int | None = None) -> _Options:
     o = _Options()
     load_library().gmg_default_options(ctypes.byref(o))
     o.levels = levels
@@ -162,18 +167,22 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
     o.device_loop = 1 if device_loop else 0
     o.ir_factor = ir_factor
     o.fine_smoother = FINE_SMOOTHERS[fine_smoother]
+    o.cycle_index = {"V": 1, "W": 2}[cycle]
+    o.outer = {"pcg": 0, "fgmres": 1}[outer]
+    o.restart = restart
     o.stream = stream
     return o
 
 
 def config_options(cfg, stream: int | None = None, fused_coarse_nodes: int = 4096,
                    bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
-                   fine_smoother: str = "fp32") -> _Options:
+                   fine_smoother: str = "fp32", cycle: str = "V", outer: str = "pcg",
+                   restart: int = 32) -> _Options:
     """Options for one of the synthetic configurations in ``inputs.CONFIGS``."""
     return options(levels=cfg.levels, smoother=cfg.smoother, degree=cfg.degree, coarse_smoother=None,
                    coarse_degree=None, omega=cfg.omega, coarse_omega=None, fused_coarse_nodes=fused_coarse_nodes,
                    bsr_tma_nodes=bsr_tma_nodes, device_loop=device_loop, ir_factor=ir_factor,
-                   fine_smoother=fine_smoother, stream=stream)
+                   fine_smoother=fine_smoother, cycle=cycle, outer=outer, restart=restart, stream=stream)
 
 
 def residual64_noalloc(dims, E, mask, f, u, r=None, nu: float = 0.3, stream: int | None = None) -> float:
@@ -352,6 +361,22 @@ class Solver:
                                     _ptr(z, torch.float32, 3 * self.nn, "z")))
         return z
 
+
+    def kappa_eff(self, b, steps: int = 20) -> tuple[float, float, float]:
+        """(lambda_min, lambda_max, kappa_eff) of M K from a CG-Lanczos probe
+        started at the FP64 device vector b."""
+        import torch
+        out = (ctypes.c_double * 3)()
+        _check(self._lib.gmg_kappa_eff(self._h, _ptr(b, torch.float64, 3 * self.nn, "b"), steps, out))
+        return out[0], out[1], out[2]
+
+    def vcycle_symmetry(self, x, y) -> float:
+        """|x.M(y) - y.M(x)| / max(|x.M(y)|, |y.M(x)|) for one multigrid cycle M."""
+        import torch
+        v = ctypes.c_double()
+        _check(self._lib.gmg_vcycle_symmetry(self._h, _ptr(x, torch.float32, 3 * self.nn, "x"),
+                                             _ptr(y, torch.float32, 3 * self.nn, "y"), ctypes.byref(v)))
+        return v.value
     def residual64(self, f, u, r=None) -> float:
         import torch
         rel = ctypes.c_double()

@@ -138,6 +138,21 @@ def filtered_random_density(nx: int, ny: int, nz: int, seed: int,
     return np.clip(sm, lo, 1.0).astype(np.float32)
 
 
+def checkerboard_density(nx: int, ny: int, nz: int, solid: float = 1.0, void: float = 1e-3) -> np.ndarray:
+    """Deterministic stress state: elements alternate between solid and void in
+    all three directions ((i + j + k) even -> solid), FP32 [nz][ny][nx]."""
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return np.where((i + j + k) % 2 == 0, solid, void).astype(np.float32)
+
+
+def layered_band_density(nx: int, ny: int, nz: int, solid: float = 1.0, void: float = 1e-3) -> np.ndarray:
+    """Deterministic stress state: the lower half of the beam in z is solid and
+    the upper half void (a half-solid / half-void band), FP32 [nz][ny][nx]."""
+    rho = np.full((nz, ny, nx), void, dtype=np.float32)
+    rho[: nz // 2] = solid
+    return rho
+
+
 def random_free_vector(fixed: np.ndarray, seed: int, dtype=np.float32) -> np.ndarray:
     """Seeded U[-1,1] on free DOFs, exactly 0 on fixed DOFs."""
     rng = np.random.default_rng(seed)

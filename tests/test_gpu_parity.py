@@ -497,3 +497,94 @@ def test_tensor_core_smoother_solves(mode, extra, cfg_name):
     r = f - fem.matfree_apply(g, fem.moduli(c.rho(), c.p), fem.element_stiffness(0.3), u)
     free = fem.free_dofs(c.fixed())
     assert np.linalg.norm(r[free]) / np.linalg.norm(f[free]) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# solver variants and diagnostics: W-cycle, FGMRES, kappa_eff, symmetry defect,
+# deterministic stress states
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["jacobi", "chebyshev"])
+def test_wcycle_matches_oracle(kind):
+    c = inputs.CONFIGS["c1"]
+    rho = c.rho()
+    opts = dict(levels=4, smoother=kind, degree=2 if kind == "jacobi" else 3, coarse_smoother=None,
+                coarse_degree=None, omega=0.5, coarse_omega=None)
+    S = gpu_solver(rho, c.p, **opts, cycle="W")
+    H, _ = oracle_hierarchy(rho, c.p, c.fixed(), 4)
+    for li, lev in enumerate(H):
+        S.set_lambda(li, lev.lam)
+    spec = oracle_spec_from_opts(opts)
+    r = np.zeros(3 * c.n_nodes, dtype=np.float32)
+    r[H[0].free] = np.random.default_rng(31).uniform(-1, 1, H[0].n_free)
+    z = S.vcycle(_t(r)).cpu().numpy()
+    zref = np.zeros(3 * c.n_nodes)
+    zref[H[0].free] = so.mgcycle(H, r[H[0].free].astype(np.float64), spec, gamma=2)
+    assert rel_l2(z, zref) < 1e-5
+
+
+@pytest.mark.parametrize("cfg_name", ["c0", "c1"])
+def test_wcycle_and_fgmres_solves(cfg_name):
+    c = inputs.CONFIGS[cfg_name]
+    f = c.load()
+    H, E = oracle_hierarchy(c.rho(), c.p, c.fixed(), c.levels)
+    spec = oracle_spec_from_opts(config_opts(c))
+    lev = H[0]
+    res = {}
+    for name, extra in (("V", {}), ("W", dict(cycle="W")), ("fgmres", dict(outer="fgmres", restart=32))):
+        S = gpu_solver(c.rho(), c.p, **config_opts(c), **extra)
+        u, info = S.solve(_t(f, torch.float64), tol=1e-6, maxit=200)
+        assert info["status"] == 0, name
+        u = u.cpu().numpy()
+        r = f - fem.matfree_apply(fem.Grid(c.nx, c.ny, c.nz), E, fem.element_stiffness(0.3), u)
+        free = fem.free_dofs(c.fixed())
+        assert np.linalg.norm(r[free]) / np.linalg.norm(f[free]) < 1e-6
+        res[name] = info["iterations"]
+    assert res["W"] <= res["V"]
+    ores = so.fgmres(lev.apply, lambda v: so.vcycle(H, v, spec), f[lev.free], tol=1e-6, restart=32)
+    assert ores.status == so.OK and abs(res["fgmres"] - ores.iterations) <= 2
+
+
+def test_kappa_eff_matches_oracle():
+    c = inputs.CONFIGS["c1"]
+    S = gpu_solver(c.rho(), c.p, **config_opts(c))
+    H, _ = oracle_hierarchy(c.rho(), c.p, c.fixed(), c.levels)
+    for li, lev in enumerate(H):
+        S.set_lambda(li, lev.lam)
+    b = np.zeros(3 * c.n_nodes)
+    b[H[0].free] = np.random.default_rng(41).normal(size=H[0].n_free)
+    lmin, lmax, kap = S.kappa_eff(_t(b, torch.float64), steps=15)
+    olmin, olmax, okap = so.kappa_eff(H, b[H[0].free], oracle_spec_from_opts(config_opts(c)), 15)
+    assert abs(lmax - olmax) < 1e-3 * olmax and abs(lmin - olmin) < 1e-3 * olmin
+    assert abs(kap - okap) < 2e-3 * okap and kap > 1.0
+
+
+@pytest.mark.parametrize("cfg_name", ["c0", "c1"])
+def test_vcycle_symmetry_defect_is_rounding_level(cfg_name):
+    c = inputs.CONFIGS[cfg_name]
+    S = gpu_solver(c.rho(), c.p, **config_opts(c))
+    fixed = c.fixed()
+    x = inputs.random_free_vector(fixed, 51)
+    y = inputs.random_free_vector(fixed, 52)
+    assert S.vcycle_symmetry(_t(x), _t(y)) < 1e-5
+
+
+@pytest.mark.parametrize("state", ["checkerboard", "layered"])
+def test_stress_states_agree_with_oracle(state):
+    nx, ny, nz = 24, 12, 12
+    rho = (inputs.checkerboard_density if state == "checkerboard" else inputs.layered_band_density)(nx, ny, nz)
+    fixed = inputs.clamp_xmin_mask(nx, ny, nz)
+    f = inputs.tip_edge_load(nx, ny, nz)
+    opts = dict(levels=3, smoother="chebyshev", degree=3, coarse_smoother=None, coarse_degree=None, omega=0.5,
+                coarse_omega=None)
+    S = gpu_solver(rho, 3.0, **opts, outer="fgmres", restart=50)
+    u, info = S.solve(_t(f, torch.float64), tol=1e-6, maxit=300)
+    H, E = oracle_hierarchy(rho, 3.0, fixed, 3)
+    lev = H[0]
+    ores = so.fgmres(lev.apply, lambda v: so.vcycle(H, v, oracle_spec_from_opts(opts)), f[lev.free], tol=1e-6,
+                     maxit=300, restart=50)
+    assert (info["status"] == 0) == (ores.status == so.OK)
+    if info["status"] == 0:
+        u = u.cpu().numpy()
+        r = f - fem.matfree_apply(fem.Grid(nx, ny, nz), E, fem.element_stiffness(0.3), u)
+        free = fem.free_dofs(fixed)
+        assert np.linalg.norm(r[free]) / np.linalg.norm(f[free]) < 1e-6
