@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -168,6 +169,75 @@ def _profile_traffic(kernel_src: str) -> float | None:
         return None
     cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
     return float(m_b.group(1)) if m_h.group(1) == cur else None
+
+
+BATCH_GRIDS = (32, 40, 48, 56, 60, 64, 72, 80)
+BATCH_RHS = 16
+
+
+def batched_leg(dev, stream) -> dict:
+    """Eight heterogeneous cantilevers of uneven sizes (32^3 .. 80^3, densities
+    as the 40^3 configuration with distinct seeds, p = 3) x 16 right-hand sides
+    (the tip-edge load rotated through 16 directions in the y-z plane): 128
+    solves in one CUDA-graph launch (gmg_solve_batch), against the same 128
+    solves one after another (gmg_solve, each with its own captured loop)."""
+    import torch
+
+    from paper_2604_26441_b300 import gmg, inputs
+
+    solvers, fs = [], []
+    elements = 0
+    for gi, n in enumerate(BATCH_GRIDS):
+        rho = torch.from_numpy(inputs.filtered_random_density(n, n, n, 300 + gi)).to(dev)
+        opts = gmg.options(levels=0, smoother="jacobi", degree=2, coarse_smoother=None, coarse_degree=None,
+                           omega=0.5, coarse_omega=None, stream=stream.cuda_stream)
+        base = gmg.Solver(rho, p=3.0, opts=opts)
+        for k in range(BATCH_RHS):
+            solvers.append(base if k == 0 else base.clone())
+            fs.append(torch.from_numpy(inputs.rotated_tip_edge_load(n, n, n, k, BATCH_RHS)).to(dev))
+        elements += n ** 3
+    us = [torch.zeros_like(f) for f in fs]
+    nsol = len(solvers)
+
+    def zero_all():
+        for u in us:
+            u.zero_()
+
+    zero_all()
+    _, infos = gmg.solve_batch(solvers, fs, us)  # warm-up: captures the batch graph
+    reps = 3
+    times = []
+    for _ in range(reps):
+        zero_all()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, infos = gmg.solve_batch(solvers, fs, us)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    batch_ms = statistics.median(times)
+    ok = all(i["status"] == 0 and i["rel_residual"] <= 1e-6 for i in infos)
+    its = [i["iterations"] for i in infos]
+    # the same solves one after another (each handle's own loop graph, captured in the warm-up)
+    for s_, f, u in zip(solvers, fs, us):
+        u.zero_()
+        s_.solve(f, u)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for s_, f, u in zip(solvers, fs, us):
+        u.zero_()
+        s_.solve(f, u)
+    b.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(b)
+    for s_ in reversed(solvers):
+        s_.close()
+    return {"workload": f"8 cantilevers {'/'.join(str(n) for n in BATCH_GRIDS)}^3 ({elements:,} elements) x "
+                        f"{BATCH_RHS} rotated tip loads = {nsol} solves, Jacobi 2/2, auto levels, tol 1e-6",
+            "value": nsol / (batch_ms / 1000.0), "unit": "solves/s", "ms_per_batch": batch_ms,
+            "sequential_solves_per_s": nsol / (seq_ms / 1000.0), "speedup_vs_sequential": seq_ms / batch_ms,
+            "all_converged": ok, "iterations_min_max": [min(its), max(its)]}
 
 
 def main():
@@ -325,6 +395,8 @@ def main():
     torch.cuda.synchronize()
     apply_ms = statistics.median(a.elapsed_time(b) for a, b in ap)
 
+    batched = None if args.no_batch else batched_leg(dev, stream)
+
     if rank != 0:
         return
     line = {
@@ -343,6 +415,8 @@ def main():
         "clocks": clk,
         "gpu_launches": launches,
     }
+    if batched is not None:
+        line["batched"] = batched
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_obj(run_oracle_sample(3))

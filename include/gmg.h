@@ -243,6 +243,28 @@ int gmg_kappa_eff(gmg_handle* h, const double* b_dev, int steps, double out[3]);
  * fixed DOFs).  0 in exact arithmetic for matched pre/post smoothers. */
 int gmg_vcycle_symmetry(gmg_handle* h, const float* x_dev, const float* y_dev, double* defect);
 
+/* A handle that shares src's hierarchy (operators, masks, smoother
+ * coefficients, coarsest factor, moduli) and owns a workspace of its own, for
+ * solving further right-hand sides on the same density field (e.g. in one
+ * gmg_solve_batch).  src must outlive the clone; gmg_set_lambda on either
+ * changes the shared smoother coefficients.  Release with gmg_destroy. */
+int gmg_clone(const gmg_handle* src, gmg_handle** out);
+
+/* Solves count independent problems -- handles of different grids, clones for
+ * further loads -- f[i] -> u[i] (device FP64, u[i] the initial guess), sharing
+ * tol and maxit.  The device-resident PCG loops of all items run as independent
+ * branches of one CUDA graph (captured on the first call for a given list of
+ * handles and iterates, then replayed), so small instances run concurrently;
+ * the FP64 acceptance test is taken for all items after one synchronisation.
+ * Each item's iterates equal those of gmg_solve on a handle with
+ * fused_coarse_nodes = 0 (the batch uses the per-level lower V-cycle).  Items
+ * whose options need the host loop (outer FGMRES, ir_factor, device_loop = 0)
+ * make the batch run one gmg_solve after the other.  Each handle appears at
+ * most once.  Runs on the first handle's stream.  Returns GMG_OK when every
+ * item converged, else the last failing status; infos[i] per item. */
+int gmg_solve_batch(gmg_handle* const* handles, int count, const double* const* f_dev, double* const* u_dev,
+                    double tol, int maxit, gmg_info* infos);
+
 /* z = V(r): one V-cycle of Eq. vcycle on the fine level. */
 int gmg_vcycle(gmg_handle* h, const float* r_dev, float* z_dev);
 

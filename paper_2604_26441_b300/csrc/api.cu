@@ -537,25 +537,24 @@ void loop_free(gmg_handle* h) {
 // tolerance (or the cap, or a non-finite scalar) with no host round trip; the
 // host then takes the FP64 acceptance decision.  The kernel sequence is that of
 // the host-driven loop, so both give bitwise-identical iterates.
-int loop_build(gmg_handle* h, double* u) {
-    loop_free(h);
-    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        return GMG_ERR_CUDA;
-    }
+// Captures [restart, step, check, while (condition) {direction, step, check}]
+// for handle h and iterate u into graph g as an independent branch (no
+// dependencies on nodes already in g), using stream cap for the capture.
+// Returns false on any capture error; prefix / body receive the kernel counts.
+bool capture_loop(gmg_handle* h, double* u, cudaGraph_t g, cudaStream_t cap, unsigned long long& prefix,
+                  unsigned long long& body_k) {
     const unsigned long long l0 = g_kernel_launches.load();
     cudaStream_t user = h->stream;
-    h->stream = h->cap_stream;
-    cudaGraph_t g = nullptr, body = nullptr, out = nullptr;
-    cudaGraphExec_t ex = nullptr;
+    h->stream = cap;
+    cudaGraph_t body = nullptr, out = nullptr;
     cudaGraphConditionalHandle cond{};
     unsigned long long l1 = l0, l2 = l0;
-    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess && cudaGraphConditionalHandleCreate(&cond, g, 0, 0) == cudaSuccess;
-    if (ok) ok = cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+    bool ok = cudaGraphConditionalHandleCreate(&cond, g, 0, 0) == cudaSuccess;
+    if (ok) ok = cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
     if (ok) {
         pcg_restart(h);
         pcg_step(h, u);
-        launch_loop_check(h->sc, cond, h->stream);
+        launch_loop_check(h->sc, cond, cap);
         l1 = g_kernel_launches.load();
         cudaStreamCaptureStatus st{};
         cudaGraph_t cg = nullptr;
@@ -567,28 +566,48 @@ int loop_build(gmg_handle* h, double* u) {
         cp.conditional.type = cudaGraphCondTypeWhile;
         cp.conditional.size = 1;
         cudaGraphNode_t cnode = nullptr;
-        ok = cudaStreamGetCaptureInfo(h->stream, &st, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess &&
+        ok = cudaStreamGetCaptureInfo(cap, &st, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess &&
              st == cudaStreamCaptureStatusActive;
         if (ok) ok = cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp) == cudaSuccess;
-        if (ok) ok = cudaStreamUpdateCaptureDependencies(h->stream, &cnode, nullptr, 1,
-                                                         cudaStreamSetCaptureDependencies) == cudaSuccess;
+        if (ok) ok = cudaStreamUpdateCaptureDependencies(cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                     cudaSuccess;
         if (ok) body = cp.conditional.phGraph_out[0];
-        ok = (cudaStreamEndCapture(h->stream, &out) == cudaSuccess) && ok;
+        ok = (cudaStreamEndCapture(cap, &out) == cudaSuccess) && ok;
     }
     if (ok) {
-        ok = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
-             cudaSuccess;
+        ok = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
         if (ok) {
             pcg_direction(h);
             pcg_step(h, u);
-            launch_loop_check(h->sc, cond, h->stream);
+            launch_loop_check(h->sc, cond, cap);
             l2 = g_kernel_launches.load();
-            ok = cudaStreamEndCapture(h->stream, &body) == cudaSuccess;
+            ok = cudaStreamEndCapture(cap, &body) == cudaSuccess;
         }
     }
-    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
     h->stream = user;
     g_kernel_launches.fetch_sub(g_kernel_launches.load() - l0);  // capturing launches nothing
+    cudaGetLastError();
+    prefix = l1 - l0;
+    body_k = l2 - l1;
+    return ok;
+}
+
+int ensure_cap_stream(gmg_handle* h) {
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return GMG_ERR_CUDA;
+    }
+    return GMG_OK;
+}
+
+int loop_build(gmg_handle* h, double* u) {
+    loop_free(h);
+    TRY(ensure_cap_stream(h));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    unsigned long long pre = 0, bod = 0;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess && capture_loop(h, u, g, h->cap_stream, pre, bod);
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
     cudaGetLastError();
     if (!ok) {
         if (g) cudaGraphDestroy(g);
@@ -597,8 +616,8 @@ int loop_build(gmg_handle* h, double* u) {
     h->loop_graph = g;
     h->loop_exec = ex;
     h->loop_u = u;
-    h->loop_prefix_kernels = l1 - l0;
-    h->loop_body_kernels = l2 - l1;
+    h->loop_prefix_kernels = pre;
+    h->loop_body_kernels = bod;
     return GMG_OK;
 }
 
@@ -791,6 +810,8 @@ void gmg_destroy(gmg_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     loop_free(h);
+    if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
+    if (h->batch_graph) cudaGraphDestroy(h->batch_graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (void* p : h->allocs)
         if (p) cudaFree(p);
@@ -1051,6 +1072,282 @@ int gmg_vcycle_symmetry(gmg_handle* h, const float* x, const float* y, double* d
     const double a = h->sc_host[SC_TMP], b = h->sc_host[SC_TMP + 1];
     *defect = std::fabs(a - b) / std::max(std::fabs(a), std::fabs(b));
     return GMG_OK;
+}
+
+int gmg_clone(const gmg_handle* src, gmg_handle** out) {
+    if (!src || !out) return fail(GMG_ERR_ARG, "null argument");
+    *out = nullptr;
+    gmg_handle* h = new gmg_handle(*src);
+    // nothing of src is owned by the clone
+    h->allocs.clear();
+    h->pinned = nullptr;
+    h->sc_host = nullptr;
+    h->cap_stream = nullptr;
+    h->loop_graph = nullptr;
+    h->loop_exec = nullptr;
+    h->loop_u = nullptr;
+    h->loop_unavailable = false;
+    h->fg_V = h->fg_Z = nullptr;
+    h->fg_h = nullptr;
+    h->fg_m = 0;
+    h->kap_u = nullptr;
+    h->batch_graph = nullptr;
+    h->batch_exec = nullptr;
+    h->batch_key.clear();
+    h->batch_counts.clear();
+    h->is_clone = true;
+    auto bad = [&](int rc) {
+        std::string keep = g_err;
+        gmg_destroy(h);
+        g_err = keep;
+        return rc;
+    };
+    cudaStream_t s = h->stream;
+    const long long n0 = 3 * h->lev[0].nn;
+    int rc = GMG_OK;
+    for (int li = 1; li < h->L && rc == GMG_OK; ++li) {
+        Level& l = h->lev[li];
+        rc = dalloc(h, &l.x, 3 * l.nn);
+        if (rc == GMG_OK) rc = dalloc(h, &l.x2, 3 * l.nn);
+        if (rc == GMG_OK) rc = dalloc(h, &l.b, 3 * l.nn);
+        if (rc == GMG_OK) rc = dalloc(h, &l.t, 3 * l.nn);
+        if (rc == GMG_OK) rc = dalloc(h, &l.d, 3 * l.nn);
+    }
+    float** fv[] = {&h->r, &h->z, &h->p, &h->q, &h->x2_0, &h->t0, &h->d0};
+    for (float** v : fv)
+        if (rc == GMG_OK) rc = dalloc(h, v, n0);
+    if (rc == GMG_OK) rc = dalloc(h, &h->sc, SC_COUNT);
+    if (rc == GMG_OK) rc = dalloc(h, &h->kerr, 1);
+    if (rc == GMG_OK) rc = dalloc(h, &h->partials, h->max_partials);
+    if (rc != GMG_OK) return bad(rc);
+    if (cudaMemsetAsync(h->sc, 0, sizeof(double) * SC_COUNT, s) != cudaSuccess ||
+        cudaMemsetAsync(h->kerr, 0, sizeof(int), s) != cudaSuccess ||
+        cudaMallocHost(&h->pinned, sizeof(double) * SC_COUNT) != cudaSuccess) {
+        cudaGetLastError();
+        return bad(fail(GMG_ERR_CUDA, "clone workspace"));
+    }
+    h->sc_host = static_cast<double*>(h->pinned);
+    if (h->use_fused) {
+        CoarseFused& cf = h->cf;
+        for (int li = 1; li < h->L; ++li) {
+            const Level& l = h->lev[li];
+            CoarseLevel& c = cf.lev[li];
+            c.x = l.x; c.x2 = l.x2; c.b = l.b; c.t = l.t; c.d = l.d;
+        }
+        unsigned* words = nullptr;
+        if (dalloc(h, &words, 4) != GMG_OK || cudaMemsetAsync(words, 0, 4 * sizeof(unsigned), s) != cudaSuccess)
+            return bad(fail(GMG_ERR_CUDA, "clone barrier words"));
+        cf.bar_count = words;
+        cf.bar_gen = words + 1;
+        cf.err = reinterpret_cast<int*>(words + 2);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return bad(fail(GMG_ERR_CUDA, "clone synchronisation"));
+    }
+    *out = h;
+    return GMG_OK;
+}
+
+int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, double* const* u, double tol,
+                    int maxit, gmg_info* infos) {
+    if (!hs || !f || !u || !infos || count < 1) return fail(GMG_ERR_ARG, "null argument or empty batch");
+    if (!(tol > 0.0) || maxit < 0) return fail(GMG_ERR_ARG, "tol must be > 0 and maxit >= 0");
+    for (int i = 0; i < count; ++i)
+        if (!hs[i] || !f[i] || !u[i]) return fail(GMG_ERR_ARG, "null handle or vector in the batch");
+    bool plain = true;  // the batch graph covers the plain device-resident PCG
+    for (int i = 0; i < count; ++i) {
+        const gmg_options& o = hs[i]->opt;
+        plain = plain && o.outer == GMG_OUTER_PCG && o.device_loop && o.ir_factor == 0.0 && maxit > 0;
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return fail(GMG_ERR_ARG, "a handle appears twice in the batch");
+    }
+    if (!plain) {  // one solve after the other
+        int worst = GMG_OK;
+        for (int i = 0; i < count; ++i) {
+            const int rc = gmg_solve(hs[i], f[i], u[i], tol, maxit, &infos[i]);
+            if (rc < 0) return rc;
+            if (rc != GMG_OK) worst = rc;
+        }
+        return worst;
+    }
+    gmg_handle* h0 = hs[0];
+    cudaStream_t s = h0->stream;
+    std::vector<cudaStream_t> saved(count);
+    for (int i = 0; i < count; ++i) {
+        saved[i] = hs[i]->stream;
+        hs[i]->stream = s;
+    }
+    auto restore = [&]() {
+        for (int i = 0; i < count; ++i) hs[i]->stream = saved[i];
+    };
+    const auto t0 = std::chrono::steady_clock::now();
+    auto elapsed = [&]() { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); };
+    auto sync_all = [&]() -> int {
+        for (int i = 0; i < count; ++i)
+            CU(cudaMemcpyAsync(hs[i]->sc_host, hs[i]->sc, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        return GMG_OK;
+    };
+    std::vector<int> state(count, 0);  // 0: active, 1: done
+    std::vector<double> nf(count, 0.0);
+    for (int i = 0; i < count; ++i) infos[i] = gmg_info{};
+    // ---- norms, nonzero count of u, fixed DOFs of u to 0
+    for (int i = 0; i < count; ++i) {
+        gmg_handle* h = hs[i];
+        const Level& l0 = h->lev[0];
+        launch_mask_u64(u[i], l0.mask, l0.nn, h->partials, s);
+        launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_UNZ, FIN_NONE, s);
+        launch_dot_f64_masked(f[i], f[i], l0.mask, l0.nn, h->partials, s);
+        launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_FF, FIN_NONE, s);
+    }
+    if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
+    bool need_rel = false;
+    for (int i = 0; i < count; ++i) {
+        gmg_handle* h = hs[i];
+        const Level& l0 = h->lev[0];
+        const double ff = h->sc_host[SC_FF];
+        if (!(ff > 0.0)) {
+            state[i] = 1;
+            if (!std::isfinite(ff)) { infos[i].status = GMG_NONFINITE; infos[i].rel_residual = NAN; }
+            else cudaMemsetAsync(u[i], 0, sizeof(double) * 3 * l0.nn, s);
+            continue;
+        }
+        nf[i] = std::sqrt(ff);
+        if (h->sc_host[SC_UNZ] == 0.0) {
+            launch_cast_masked(f[i], l0.mask, l0.nn, h->r, s);
+            infos[i].rel_residual = 1.0;
+        } else {
+            launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, h->sc, h->partials,
+                                h->gh64, s);
+            launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
+            need_rel = true;
+        }
+    }
+    if (need_rel) {
+        if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
+        for (int i = 0; i < count; ++i)
+            if (state[i] == 0 && hs[i]->sc_host[SC_UNZ] != 0.0)
+                infos[i].rel_residual = std::sqrt(hs[i]->sc_host[SC_TRR]) / nf[i];
+    }
+    for (int i = 0; i < count; ++i)
+        if (state[i] == 0) {
+            const double rel = infos[i].rel_residual;
+            infos[i].rel_residual_recursive = rel;
+            if (!std::isfinite(rel)) { infos[i].status = GMG_NONFINITE; state[i] = 1; }
+            else if (rel < tol) { infos[i].status = GMG_OK; state[i] = 1; }
+        }
+    // ---- one graph for every active item: independent branches, each the
+    // device-resident PCG loop of its handle and iterate (the per-level lower
+    // V-cycle: concurrent cooperative kernels could not all be co-resident)
+    std::vector<std::pair<const gmg_handle*, const double*>> key;
+    for (int i = 0; i < count; ++i)
+        if (state[i] == 0) key.emplace_back(hs[i], u[i]);
+    if (!key.empty()) {
+        if (key != h0->batch_key || !h0->batch_exec) {
+            if (h0->batch_exec) cudaGraphExecDestroy(h0->batch_exec);
+            if (h0->batch_graph) cudaGraphDestroy(h0->batch_graph);
+            h0->batch_exec = nullptr;
+            h0->batch_graph = nullptr;
+            h0->batch_key.clear();
+            h0->batch_counts.clear();
+            if (int rc = ensure_cap_stream(h0); rc != GMG_OK) { restore(); return rc; }
+            cudaGraph_t g = nullptr;
+            bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+            for (int i = 0; i < count && ok; ++i) {
+                if (state[i] != 0) continue;
+                unsigned long long pre = 0, bod = 0;
+                const bool fused = hs[i]->use_fused;
+                hs[i]->use_fused = false;
+                ok = capture_loop(hs[i], u[i], g, h0->cap_stream, pre, bod);
+                hs[i]->use_fused = fused;
+                h0->batch_counts.emplace_back(pre, bod);
+            }
+            cudaGraphExec_t ex = nullptr;
+            if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+            cudaGetLastError();
+            if (!ok) {
+                if (g) cudaGraphDestroy(g);
+                h0->batch_counts.clear();
+                restore();
+                return fail(GMG_ERR_CUDA, "could not capture the batch graph");
+            }
+            h0->batch_graph = g;
+            h0->batch_exec = ex;
+            h0->batch_key = key;
+        }
+        for (int i = 0; i < count; ++i) {
+            if (state[i] != 0) continue;
+            double* sch = hs[i]->sc_host;
+            sch[SC_IT] = 0.0;
+            sch[SC_TOL] = tol;
+            sch[SC_MAXIT] = (double)maxit;
+            sch[SC_NF] = nf[i];
+            CU(cudaMemcpyAsync(hs[i]->sc + SC_IT, sch + SC_IT, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+        }
+        CU(cudaGraphLaunch(h0->batch_exec, s));
+        if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
+        // FP64 true residual of every item that left its loop
+        size_t q = 0;
+        for (int i = 0; i < count; ++i) {
+            if (state[i] != 0) continue;
+            gmg_handle* h = hs[i];
+            const Level& l0 = h->lev[0];
+            const int k = (int)h->sc_host[SC_IT];
+            note_launch(h0->batch_counts[q].first + h0->batch_counts[q].second * (unsigned long long)std::max(0, k - 1));
+            ++q;
+            infos[i].iterations = k;
+            infos[i].rel_residual_recursive = std::sqrt(h->sc_host[SC_RR]) / nf[i];
+            if (!std::isfinite(infos[i].rel_residual_recursive) || !std::isfinite(h->sc_host[SC_ALPHA])) {
+                infos[i].status = GMG_NONFINITE;
+                infos[i].rel_residual = infos[i].rel_residual_recursive;
+                state[i] = 1;
+                continue;
+            }
+            launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, h->sc, h->partials,
+                                h->gh64, s);
+            launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
+        }
+        if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
+        for (int i = 0; i < count; ++i) {
+            if (state[i] != 0) continue;
+            gmg_handle* h = hs[i];
+            const double rel = std::sqrt(h->sc_host[SC_TRR]) / nf[i];
+            infos[i].rel_residual = rel;
+            state[i] = 1;
+            if (!std::isfinite(rel)) infos[i].status = GMG_NONFINITE;
+            else if (rel < tol) infos[i].status = GMG_OK;
+            else if (!(infos[i].rel_residual_recursive < tol) || infos[i].iterations >= maxit)
+                infos[i].status = GMG_NOT_CONVERGED;
+            else {
+                // residual replacement: continue this item alone from its current
+                // iterate, with the same (per-level) lower V-cycle as the batch; the
+                // loop graph captured for it is dropped again afterwards
+                gmg_info more{};
+                const bool fused = h->use_fused;
+                h->use_fused = false;
+                loop_free(h);
+                const int rc = gmg_solve(h, f[i], u[i], tol, maxit - infos[i].iterations, &more);
+                loop_free(h);
+                h->use_fused = fused;
+                if (rc < 0) { restore(); return rc; }
+                infos[i].status = more.status;
+                infos[i].iterations += more.iterations;
+                infos[i].replacements += 1 + more.replacements;
+                infos[i].rel_residual = more.rel_residual;
+                infos[i].rel_residual_recursive = more.rel_residual_recursive;
+            }
+        }
+    }
+    int worst = GMG_OK;
+    for (int i = 0; i < count; ++i) {
+        if (int fe = check_fused(hs[i]); fe != GMG_OK) { restore(); return fe; }
+        infos[i].solve_ms = elapsed();
+        if (infos[i].status != GMG_OK) worst = infos[i].status;
+    }
+    restore();
+    CU(cudaGetLastError());
+    return worst;
 }
 
 int gmg_num_levels(const gmg_handle* h) { return h ? h->L : 0; }

@@ -232,6 +232,12 @@ struct gmg_handle {
     double* fg_h = nullptr;
     int fg_m = 0;
     double* kap_u = nullptr;                    // FP64 scratch iterate of the kappa_eff probe
+    bool is_clone = false;                      // shares the hierarchy of another handle
+    // gmg_solve_batch: the last batch graph captured with this handle first
+    cudaGraph_t batch_graph = nullptr;
+    cudaGraphExec_t batch_exec = nullptr;
+    std::vector<std::pair<const gmg_handle*, const double*>> batch_key;
+    std::vector<std::pair<unsigned long long, unsigned long long>> batch_counts;
     int fused_blocks = 0;
     std::vector<void*> allocs;                  // every device allocation, freed by gmg_destroy
     void* pinned = nullptr;                     // pinned host block (sc_host)

@@ -88,6 +88,9 @@ _SIGS = {
     "gmg_coarse_solve": (ctypes.c_int, [_P, _P, _P]),
     "gmg_vcycle": (ctypes.c_int, [_P, _P, _P]),
     "gmg_kappa_eff": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "gmg_clone": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "gmg_solve_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                       ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Info)]),
     "gmg_vcycle_symmetry": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gmg_residual64": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gmg_residual64_noalloc": (ctypes.c_int, [ctypes.POINTER(_Grid), _P, _P, ctypes.c_double, _P, _P, _P,
@@ -238,6 +241,18 @@ class Solver:
         self._lib = lib
 
     # -- lifetime
+    def clone(self) -> "Solver":
+        """A solver sharing this hierarchy with a workspace of its own (for
+        further right-hand sides, e.g. in solve_batch).  Keeps this solver
+        alive while the clone exists."""
+        c = object.__new__(Solver)
+        c.dims, c.nn, c.stream, c._fixed_host, c._lib = self.dims, self.nn, self.stream, self._fixed_host, self._lib
+        c._source = self
+        h = ctypes.c_void_p()
+        _check(self._lib.gmg_clone(self._h, ctypes.byref(h)))
+        c._h = h
+        return c
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.gmg_destroy(self._h)
@@ -384,3 +399,23 @@ class Solver:
         _check(self._lib.gmg_residual64(self._h, _ptr(f, torch.float64, 3 * self.nn, "f"),
                                         _ptr(u, torch.float64, 3 * self.nn, "u"), rp, ctypes.byref(rel)))
         return rel.value
+
+
+def solve_batch(solvers, fs, us=None, tol: float = 1e-6, maxit: int = 200):
+    """Solves solvers[i] with load fs[i] (device FP64) into us[i] (initial guess;
+    zeros when None) through one CUDA graph; returns (us, infos)."""
+    import torch
+    n = len(solvers)
+    if len(fs) != n or (us is not None and len(us) != n):
+        raise ValueError("one load and one iterate per solver")
+    if us is None:
+        us = [torch.zeros_like(f) for f in fs]
+    hs = (_P * n)(*[s._h for s in solvers])
+    fp = (_P * n)(*[_ptr(f, torch.float64, 3 * s.nn, "f") for s, f in zip(solvers, fs)])
+    up = (_P * n)(*[_ptr(u, torch.float64, 3 * s.nn, "u") for s, u in zip(solvers, us)])
+    infos = (_Info * n)()
+    rc = load_library().gmg_solve_batch(hs, n, fp, up, tol, maxit, infos)
+    _check(rc, allow=(GMG_OK, GMG_NOT_CONVERGED, GMG_NONFINITE))
+    return us, [{"status": i.status, "iterations": i.iterations, "replacements": i.replacements,
+                 "rel_residual": i.rel_residual, "rel_residual_recursive": i.rel_residual_recursive,
+                 "solve_ms": i.solve_ms} for i in infos]

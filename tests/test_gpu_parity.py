@@ -588,3 +588,50 @@ def test_stress_states_agree_with_oracle(state):
         r = f - fem.matfree_apply(fem.Grid(nx, ny, nz), E, fem.element_stiffness(0.3), u)
         free = fem.free_dofs(fixed)
         assert np.linalg.norm(r[free]) / np.linalg.norm(f[free]) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# batched solves: uneven instances x several loads in one CUDA graph
+# ---------------------------------------------------------------------------
+def _batch_problems():
+    grids = [(16, 8, 8, 3), (23, 11, 9, 3), (24, 24, 24, 3)]
+    out = []
+    for gi, (nx, ny, nz, levels) in enumerate(grids):
+        rho = inputs.filtered_random_density(nx, ny, nz, 100 + gi)
+        loads = [inputs.rotated_tip_edge_load(nx, ny, nz, k, nrhs=16) for k in (0, 5, 11)]
+        out.append((rho, levels, loads))
+    return out
+
+
+def test_batch_matches_single_solves():
+    from paper_2604_26441_b300 import gmg
+    opts = dict(smoother="chebyshev", degree=3, coarse_smoother=None, coarse_degree=None, omega=0.5,
+                coarse_omega=None)
+    solvers, fs, ref = [], [], []
+    for rho, levels, loads in _batch_problems():
+        base = gpu_solver(rho, 3.0, levels=levels, **opts)
+        for k, load in enumerate(loads):
+            solvers.append(base if k == 0 else base.clone())
+            fs.append(_t(load, torch.float64))
+        single = gpu_solver(rho, 3.0, levels=levels, **opts, fused_coarse_nodes=0)
+        for load in loads:
+            u, info = single.solve(_t(load, torch.float64))
+            ref.append((u.cpu().numpy(), info))
+    us, infos = gmg.solve_batch(solvers, fs)
+    for (u_ref, info_ref), u, info in zip(ref, us, infos):
+        assert info["status"] == 0 and info["rel_residual"] < 1e-6
+        assert info["iterations"] == info_ref["iterations"]
+        assert np.array_equal(u.cpu().numpy(), u_ref)
+    # the captured graph is replayed for the same handles and iterates
+    first = [u.clone() for u in us]
+    for u in us:
+        u.zero_()
+    us2, infos2 = gmg.solve_batch(solvers, fs, us)
+    assert all(torch.equal(a, b) for a, b in zip(first, us2))
+    # the oracle's own FP64 residual of one batched answer
+    rho, levels, loads = _batch_problems()[2]
+    nz, ny, nx = rho.shape
+    u = us[-1].cpu().numpy()
+    r = loads[-1] - fem.matfree_apply(fem.Grid(nx, ny, nz), fem.moduli(rho, 3.0), fem.element_stiffness(0.3), u)
+    free = fem.free_dofs(inputs.clamp_xmin_mask(nx, ny, nz))
+    assert np.linalg.norm(r[free]) / np.linalg.norm(loads[-1][free]) < 1e-6
