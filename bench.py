@@ -171,6 +171,23 @@ def _profile_traffic(kernel_src: str) -> float | None:
     return float(m_b.group(1)) if m_h.group(1) == cur else None
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (all ranks take part; with one rank, ms itself)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job solves/s: every rank's solves over the slowest rank's time."""
+    return world * steps_per_rank / (max_ms / 1000.0)
+
+
 BATCH_GRIDS = (32, 40, 48, 56, 60, 64, 72, 80)
 BATCH_RHS = 16
 
@@ -328,11 +345,8 @@ def main():
     launches = gmg.kernel_launches() - k0
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = job_rate(args.steps, world, total_ms)
     ok = all(i["status"] == 0 and i["rel_residual"] <= cfg.tol for i in infos)
 
     # ---- end to end through the public API: pinned host f in, host u out
