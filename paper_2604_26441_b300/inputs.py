@@ -35,6 +35,7 @@ __all__ = [
     "uniform_density",
     "filtered_random_density",
     "random_free_vector",
+    "he_normal_params",
 ]
 
 
@@ -159,3 +160,17 @@ def random_free_vector(fixed: np.ndarray, seed: int, dtype=np.float32) -> np.nda
     v = rng.uniform(-1.0, 1.0, size=fixed.shape[0]).astype(dtype)
     v[fixed.astype(bool)] = 0
     return v
+
+
+def he_normal_params(shapes, seed: int) -> np.ndarray:
+    """Seeded initial parameters of a stack of 3-D convolution layers, flat
+    float32: for each (cout, taps, cin) in ``shapes`` the weights
+    [cout][taps][cin] drawn N(0, 2 / (taps * cin)), followed by cout zero
+    biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for cout, taps, cin in shapes:
+        std = math.sqrt(2.0 / (taps * cin))
+        parts.append(rng.normal(0.0, std, size=cout * taps * cin))
+        parts.append(np.zeros(cout))
+    return np.concatenate(parts).astype(np.float32)
