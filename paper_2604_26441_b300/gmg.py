@@ -95,6 +95,20 @@ _SIGS = {
     "gmg_residual64": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gmg_residual64_noalloc": (ctypes.c_int, [ctypes.POINTER(_Grid), _P, _P, ctypes.c_double, _P, _P, _P,
                                               ctypes.POINTER(ctypes.c_double), _P]),
+    # learned warm start (include/gmg_warmnet.h)
+    "gmg_net_num_params": (ctypes.c_longlong, []),
+    "gmg_net_layer_shape": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "gmg_net_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P]),
+    "gmg_net_set_params": (ctypes.c_int, [_P, _P]),
+    "gmg_net_get_params": (ctypes.c_int, [_P, _P]),
+    "gmg_net_get_grads": (ctypes.c_int, [_P, _P]),
+    "gmg_net_forward": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "gmg_net_train_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_float, _P]),
+    "gmg_net_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "gmg_net_target": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "gmg_warm_start": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "gmg_net_destroy": (None, [_P]),
 }
 
 
@@ -419,3 +433,142 @@ def solve_batch(solvers, fs, us=None, tol: float = 1e-6, maxit: int = 200):
     return us, [{"status": i.status, "iterations": i.iterations, "replacements": i.replacements,
                  "rel_residual": i.rel_residual, "rel_residual_recursive": i.rel_residual_recursive,
                  "solve_ms": i.solve_ms} for i in infos]
+
+
+# ---------------------------------------------------------------- learned warm start
+
+NET_IN, NET_OUT, NET_LAYERS = 8, 3, 12
+
+
+def net_num_params() -> int:
+    return int(load_library().gmg_net_num_params())
+
+
+def net_layer_shapes() -> list[tuple[int, int, int, int]]:
+    """(cin, cout, stride, has_activation) per layer, in parameter order."""
+    lib = load_library()
+    out = []
+    for l in range(NET_LAYERS):
+        sh = (ctypes.c_int * 4)()
+        _check(lib.gmg_net_layer_shape(l, sh))
+        out.append(tuple(int(v) for v in sh))
+    return out
+
+
+def net_features(dims, rho, f, fixed, x=None, stream: int | None = None):
+    """Input features [n_nodes, 8] (device float) of one problem."""
+    import torch
+    nx, ny, nz = dims
+    nn = (nx + 1) * (ny + 1) * (nz + 1)
+    if x is None:
+        x = torch.empty(nn, NET_IN, dtype=torch.float32, device=f.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load_library().gmg_net_features(nx, ny, nz, _ptr(rho, torch.float32, nx * ny * nz, "rho"),
+                                           _ptr(f, torch.float64, 3 * nn, "f"),
+                                           _ptr(fixed, torch.uint8, 3 * nn, "fixed"),
+                                           _ptr(x, torch.float32, NET_IN * nn, "x"), stream))
+    return x
+
+
+def net_target(dims, u, t=None, stream: int | None = None):
+    """Training target u / RMS(u) (device float [n_nodes, 3])."""
+    import torch
+    nx, ny, nz = dims
+    nn = (nx + 1) * (ny + 1) * (nz + 1)
+    if t is None:
+        t = torch.empty(nn, 3, dtype=torch.float32, device=u.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load_library().gmg_net_target(nx, ny, nz, _ptr(u, torch.float64, 3 * nn, "u"),
+                                         _ptr(t, torch.float32, 3 * nn, "t"), stream))
+    return t
+
+
+class WarmNet:
+    """The warm-start encoder-decoder: parameters, Adam state and per-shape
+    workspaces live in the CUDA library."""
+
+    def __init__(self, params, stream: int | None = None):
+        import torch
+        lib = load_library()
+        self._lib = lib
+        self.n_params = int(lib.gmg_net_num_params())
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.gmg_net_create(ctypes.byref(h), _ptr(params, torch.float32, self.n_params, "params"), stream))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gmg_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        import torch
+        _check(self._lib.gmg_net_set_params(self._h, _ptr(params, torch.float32, self.n_params, "params")))
+
+    def params(self):
+        import torch
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(self._lib.gmg_net_get_params(self._h, _ptr(out, torch.float32, self.n_params, "params")))
+        return out
+
+    def grads(self):
+        import torch
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(self._lib.gmg_net_get_grads(self._h, _ptr(out, torch.float32, self.n_params, "grads")))
+        return out
+
+    def forward(self, dims, x, g=None):
+        """x: [B, n_nodes, 8] (or [n_nodes, 8]) device float -> g of shape [..., n_nodes, 3]."""
+        import torch
+        nx, ny, nz = dims
+        nn = (nx + 1) * (ny + 1) * (nz + 1)
+        B = x.numel() // (NET_IN * nn)
+        if g is None:
+            g = torch.empty(*x.shape[:-1], 3, dtype=torch.float32, device=x.device)
+        _check(self._lib.gmg_net_forward(self._h, nx, ny, nz, B, _ptr(x, torch.float32, B * NET_IN * nn, "x"),
+                                         _ptr(g, torch.float32, B * 3 * nn, "g")))
+        return g
+
+    def train_step(self, dims, xs, ts, lr: float, loss_out=None):
+        """One Adam step on the batch (lists of [n_nodes, 8] / [n_nodes, 3]
+        device tensors of one grid); loss_out: optional one-element device
+        float tensor (a view) receiving the batch loss."""
+        import torch
+        nx, ny, nz = dims
+        nn = (nx + 1) * (ny + 1) * (nz + 1)
+        B = len(xs)
+        if len(ts) != B or B == 0:
+            raise ValueError("xs and ts must be non-empty lists of equal length")
+        xp = (ctypes.c_void_p * B)(*[_ptr(x, torch.float32, NET_IN * nn, "x").value for x in xs])
+        tp = (ctypes.c_void_p * B)(*[_ptr(t, torch.float32, 3 * nn, "t").value for t in ts])
+        lp = None
+        if loss_out is not None:
+            if not (loss_out.is_cuda and loss_out.dtype == torch.float32 and loss_out.numel() >= 1):
+                raise TypeError("loss_out must be a CUDA float32 tensor")
+            lp = ctypes.c_void_p(loss_out.data_ptr())
+        _check(self._lib.gmg_net_train_step(self._h, nx, ny, nz, B, xp, tp, float(lr), lp))
+
+    def warm_start(self, solver: "Solver", rho, f, u0=None, sync: bool = True):
+        """u0 = alpha g for solver (energy-optimal alpha; 0 keeps the cold start).
+        Returns (u0, alpha or None when sync is False)."""
+        import torch
+        if u0 is None:
+            u0 = torch.empty_like(f)
+        nx, ny, nz = solver.dims
+        a = ctypes.c_double()
+        _check(self._lib.gmg_warm_start(solver._h, self._h, _ptr(rho, torch.float32, nx * ny * nz, "rho"),
+                                        _ptr(f, torch.float64, 3 * solver.nn, "f"),
+                                        _ptr(u0, torch.float64, 3 * solver.nn, "u0"),
+                                        ctypes.byref(a) if sync else None))
+        return u0, (a.value if sync else None)

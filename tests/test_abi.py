@@ -1,5 +1,5 @@
 """The C-ABI library builds, loads without a GPU, and exports every entry point
-that include/gmg.h declares; argument errors come back as status codes."""
+that include/*.h declares; argument errors come back as status codes."""
 
 import ctypes
 import os
@@ -11,9 +11,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "gmg.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(gmg_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(gmg_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -104,3 +108,25 @@ def test_no_device_is_reported(lib):
     rc = lib.gmg_setup(ctypes.byref(h), ctypes.byref(g), ctypes.c_void_p(256), 3.0, 1.0, 1e-9, 0.3, ctypes.byref(bc),
                        None)
     assert rc == -6 and not h.value
+
+
+def test_warm_start_network_shape_and_argument_errors(lib):
+    """The library's network table agrees with the oracle's (both are written
+    from the same architecture statement), and bad arguments are refused
+    before any device work."""
+    from oracle import warmnet
+    from paper_2604_26441_b300 import gmg
+    assert "gmg_warm_start" in _declared() and "gmg_net_train_step" in _declared()
+    assert lib.gmg_net_num_params() == warmnet.n_params()
+    shapes = gmg.net_layer_shapes()
+    assert [(ci, co, s, int(a)) for _, ci, co, s, a in warmnet.LAYERS] == shapes
+    sh = (ctypes.c_int * 4)()
+    assert lib.gmg_net_layer_shape(12, sh) == -1
+    h = ctypes.c_void_p()
+    assert lib.gmg_net_create(None, ctypes.c_void_p(16), None) == -1
+    assert lib.gmg_net_create(ctypes.byref(h), None, None) == -1
+    assert lib.gmg_net_forward(None, 8, 8, 8, 1, ctypes.c_void_p(16), ctypes.c_void_p(16)) == -1
+    assert lib.gmg_net_features(8, 8, 8, None, None, None, None, None) == -1
+    assert lib.gmg_net_target(0, 8, 8, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == -1
+    assert lib.gmg_warm_start(None, None, None, None, None, None) == -1
+    lib.gmg_net_destroy(None)

@@ -1,0 +1,194 @@
+"""GPU parity of the learned warm start's kernels against the FP64 oracle
+(oracle.warmnet): input features and targets, the forward pass, the loss and
+its gradient through every layer, the Adam update, and the energy-optimal
+warm start u0 = alpha g.
+
+Tolerances.  The network runs in FP32 with the same bfloat16-rounded weights
+the oracle uses, so the only difference is FP32 rounding: sums of up to
+27 x 128 products per layer over 12 layers give relative errors ~1e-6; the
+forward output is held to 1e-5 relative L2, the loss to 1e-5 relative, the
+gradient (sums over every output node) to 1e-4 relative L2 per layer.  One
+Adam step moves a weight by lr * m_hat / (sqrt(v_hat) + eps), which on the
+first step is lr * sign(g) when |g| >> eps, so an FP32 gradient whose sign
+differs from the FP64 one (|g| at rounding level) flips that weight's step:
+the update is compared on the weights whose FP64 gradient is not at that level.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import fem, warmnet as W
+from paper_2604_26441_b300 import inputs
+
+from gpu_helpers import gpu_solver, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2604_26441_b300 import build
+    build.build_library()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _t(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def _theta(seed=3):
+    th = inputs.he_normal_params(W.layer_shapes(), seed).astype(np.float64)
+    r = np.random.default_rng(seed + 100)
+    bias = np.zeros(th.size, dtype=bool)
+    k = 0
+    for _, ci, co, _, _ in W.LAYERS:
+        k += co * 27 * ci
+        bias[k:k + co] = True
+        k += co
+    th[bias] = 0.05 * r.normal(size=bias.sum())
+    return th.astype(np.float32)
+
+
+def _problem(nx, ny, nz, seed, k_load=3):
+    rho = inputs.filtered_random_density(nx, ny, nz, seed)
+    fixed = inputs.clamp_xmin_mask(nx, ny, nz)
+    f = inputs.rotated_tip_edge_load(nx, ny, nz, k_load)
+    return rho, fixed, f
+
+
+# grids: one tile in x at level 3 (8^3), ragged tiles everywhere (16 x 24 x 8),
+# several tiles per level (32 x 16 x 24)
+GRIDS = [(8, 8, 8), (16, 24, 8), (32, 16, 24)]
+
+
+@pytest.mark.parametrize("dims", GRIDS)
+def test_features_and_target_match_oracle(dims):
+    from paper_2604_26441_b300 import gmg
+    nx, ny, nz = dims
+    rho, fixed, f = _problem(nx, ny, nz, 5)
+    x = gmg.net_features(dims, _t(rho), _t(f, torch.float64), _t(fixed, torch.uint8)).cpu().numpy()
+    xr = W.node_features(nx, ny, nz, rho, f, fixed).reshape(-1, 8)
+    np.testing.assert_allclose(x, xr, rtol=0, atol=2e-7)
+    u = np.random.default_rng(1).normal(size=f.size)
+    t = gmg.net_target(dims, _t(u, torch.float64)).cpu().numpy().reshape(-1)
+    np.testing.assert_allclose(t, W.normalised_target(u), rtol=2e-7, atol=2e-7)
+    z = gmg.net_target(dims, _t(np.zeros_like(u), torch.float64)).cpu().numpy()
+    assert np.all(z == 0)
+
+
+@pytest.mark.parametrize("dims", GRIDS)
+def test_forward_matches_oracle(dims):
+    from paper_2604_26441_b300 import gmg
+    nx, ny, nz = dims
+    theta = _theta()
+    net = gmg.WarmNet(_t(theta))
+    xs = []
+    for s in (11, 12):
+        rho, fixed, f = _problem(nx, ny, nz, s, k_load=s)
+        xs.append(W.node_features(nx, ny, nz, rho, f, fixed))
+    xb = _t(np.stack([x.reshape(-1, 8) for x in xs]))
+    g = net.forward(dims, xb).cpu().numpy()
+    for b, x in enumerate(xs):
+        ref, _ = W.forward(theta.astype(np.float64), x)
+        assert rel_l2(g[b], ref.reshape(-1, 3)) < 1e-5, b
+    # batch of one equals the batched result bitwise (same kernels, same order)
+    g1 = net.forward(dims, xb[1:2].contiguous()).cpu().numpy()
+    assert np.array_equal(g1[0], g[1])
+    # parameters round-trip through the library's internal layout
+    np.testing.assert_array_equal(net.params().cpu().numpy(), theta)
+
+
+def _oracle_batch(dims, seeds):
+    nx, ny, nz = dims
+    batch = []
+    for s in seeds:
+        rho, fixed, f = _problem(nx, ny, nz, s, k_load=s % 16)
+        x = W.node_features(nx, ny, nz, rho, f, fixed)
+        tgt = np.random.default_rng(s).normal(size=(nz + 1, ny + 1, nx + 1, 3))
+        batch.append((x, tgt))
+    return batch
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8), (16, 24, 8)])
+def test_loss_gradient_and_adam_match_oracle(dims):
+    from paper_2604_26441_b300 import gmg
+    theta = _theta(4)
+    batch = _oracle_batch(dims, (21, 22))
+    xs = [_t(x.reshape(-1, 8)) for x, _ in batch]
+    ts = [_t(t.reshape(-1, 3)) for _, t in batch]
+    net = gmg.WarmNet(_t(theta))
+    loss = torch.zeros(1, device="cuda")
+    lr = 1e-3
+    net.train_step(dims, xs, ts, lr, loss)
+    g_gpu = net.grads().cpu().numpy().astype(np.float64)
+    p_gpu = net.params().cpu().numpy().astype(np.float64)
+    th = theta.astype(np.float64)
+    loss_ref, g_ref, p_ref, _, _ = W.train_step(th, np.zeros_like(th), np.zeros_like(th), 1, lr, batch)
+    assert abs(float(loss.item()) - loss_ref) <= 1e-5 * loss_ref
+    k = 0
+    for name, ci, co, _, _ in W.LAYERS:
+        n = co * 27 * ci + co
+        assert rel_l2(g_gpu[k:k + n], g_ref[k:k + n]) < 1e-4, name
+        k += n
+    stable = np.abs(g_ref) > 1e-4 * np.abs(g_ref).max()
+    assert stable.mean() > 0.5
+    np.testing.assert_allclose(p_gpu[stable], p_ref[stable], rtol=0, atol=1e-6)
+    assert np.all(np.abs(p_gpu - p_ref) <= 2 * lr + 1e-6)
+
+
+def test_train_steps_are_bitwise_reproducible():
+    from paper_2604_26441_b300 import gmg
+    dims = (16, 8, 8)
+    theta = _t(_theta(5))
+    batch = _oracle_batch(dims, (31, 32, 33))
+    xs = [_t(x.reshape(-1, 8)) for x, _ in batch]
+    ts = [_t(t.reshape(-1, 3)) for _, t in batch]
+    runs = []
+    for _ in range(2):
+        net = gmg.WarmNet(theta)
+        losses = torch.zeros(4, device="cuda")
+        for i in range(4):
+            net.train_step(dims, xs, ts, 1e-3, losses[i:i + 1])
+        runs.append((net.params().cpu().numpy(), losses.cpu().numpy()))
+        net.close()
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][1][-1] < runs[0][1][0]
+
+
+@pytest.mark.parametrize("dims", [(16, 8, 8), (24, 16, 16)])
+def test_warm_start_matches_oracle(dims):
+    from paper_2604_26441_b300 import gmg
+    nx, ny, nz = dims
+    rho, fixed, f = _problem(nx, ny, nz, 41, k_load=5)
+    theta = _theta(6)
+    net = gmg.WarmNet(_t(theta))
+    S = gpu_solver(rho, 3.0, levels=2, smoother="jacobi", coarse_smoother=None, omega=0.5)
+    u0, alpha = net.warm_start(S, _t(rho), _t(f, torch.float64))
+    x = W.node_features(nx, ny, nz, rho, f, fixed)
+    g, _ = W.forward(theta.astype(np.float64), x)
+    Kapply = lambda v: fem.matfree_apply(fem.Grid(nx, ny, nz), fem.moduli(rho, 3.0), fem.element_stiffness(0.3),
+                                         np.where(fixed == 1, 0.0, v))
+    u0_ref, alpha_ref = W.warm_start(Kapply, f, g.reshape(-1), fixed)
+    if alpha_ref == 0.0:
+        assert alpha == 0.0 and np.all(u0.cpu().numpy() == 0)
+    else:
+        assert alpha == pytest.approx(alpha_ref, rel=1e-4)
+        assert rel_l2(u0.cpu().numpy(), u0_ref) < 1e-4
+    # the negated output is rejected (f.g changes sign), leaving the cold start
+    neg = theta.copy()
+    k = W.n_params() - (3 * 27 * 16 + 3)
+    neg[k:] = -neg[k:]
+    net.set_params(_t(neg))
+    u0n, alphan = net.warm_start(S, _t(rho), _t(f, torch.float64))
+    if alpha_ref > 0:
+        assert alphan == 0.0 and torch.count_nonzero(u0n).item() == 0
+    # a warm-started solve converges to the same solution as the cold one
+    net.set_params(_t(theta))
+    u0, _ = net.warm_start(S, _t(rho), _t(f, torch.float64))
+    uw, iw = S.solve(_t(f, torch.float64), u0.clone(), tol=1e-8, maxit=200)
+    uc, ic = S.solve(_t(f, torch.float64), None, tol=1e-8, maxit=200)
+    assert iw["status"] == 0 and ic["status"] == 0
+    assert rel_l2(uw.cpu().numpy(), uc.cpu().numpy()) < 1e-6
