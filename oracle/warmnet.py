@@ -20,7 +20,7 @@ vector 3*n + c.
 
 Architecture (4 resolution levels, 16/32/64/64 channels, 3x3x3 kernels):
 
-    e0a  conv s1   8 -> 16  lrelu   level 0          x0   -> a0
+    e0a  conv s1  12 -> 16  lrelu   level 0          x0   -> a0
     e0b  conv s1  16 -> 16  lrelu   level 0          a0   -> s0
     d1   conv s2  16 -> 32  lrelu   level 0 -> 1     s0   -> b1
     e1   conv s1  32 -> 32  lrelu   level 1          b1   -> s1
@@ -43,12 +43,22 @@ Architecture (4 resolution levels, 16/32/64/64 channels, 3x3x3 kernels):
   stored output (1 where y > 0, else 0.1);
 * [a, b] = channel concatenation, upsampled part first.
 
-Inputs (8 channels per node): nodal density (mean of the adjacent elements'
-rho), the load f / max|f| (3), an indicator of nodes with a fixed DOF, and the
-normalised coordinates i/nx, j/ny, k/nz.  Target: the PCG solution divided by
-its RMS over all 3N entries.  Loss: mean squared error over the DOFs of nodes
-without a fixed DOF.  Optimiser: Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias
-corrected) on FP32 master weights; the network computes with the weights
+Inputs (12 channels per node): nodal density (mean of the adjacent elements'
+rho), the load f / max|f| (3), an indicator of nodes with a fixed DOF, the
+normalised coordinates i/nx, j/ny, k/nz, the direction of the resultant load
+sum(f) / |sum(f)| as a constant field (3; zero when the resultant vanishes) and
+a constant 1.  The constant fields carry the load direction to nodes beyond the
+network's receptive field (about 40 nodes), which the local load channels
+cannot reach on the larger grids.  Target: the PCG solution divided by
+its RMS over all 3N entries.  Two losses: (mse) the mean squared error over the
+DOFs of nodes without a fixed DOF; (energy) the error in the energy norm of
+the sample's own stiffness, sum_b e_b.K_b e_b / sum_b t_b.K_b t_b with
+e_b = g_b - t_b on the free DOFs (0 on fixed ones), whose gradient is
+2 K_b e_b / sum_b t_b.K_b t_b -- the norm in which PCG measures the error of
+its initial guess, which the mean squared error weights very differently
+(roughness of the output costs little in L2 and much in energy).  Optimiser: the gradient is rescaled to global L2 norm at most
+``clip`` (when clip > 0), then Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias
+corrected) updates FP32 master weights; the network computes with the weights
 rounded to bfloat16 (round to nearest even) and FP32 biases.  Warm start: the
 masked output g is rescaled by the energy-optimal factor
 alpha = f.g / g.K g (minimiser of ||u - alpha g||_K), kept only if both dot
@@ -61,11 +71,11 @@ import numpy as np
 
 SLOPE = 0.1
 BETA1, BETA2, ADAM_EPS = 0.9, 0.999, 1e-8
-N_IN, N_OUT = 8, 3
+N_IN, N_OUT = 12, 3
 
 # (name, cin, cout, stride, activation) in parameter order.
 LAYERS = [
-    ("e0a", 8, 16, 1, True),
+    ("e0a", 12, 16, 1, True),
     ("e0b", 16, 16, 1, True),
     ("d1", 16, 32, 2, True),
     ("e1", 32, 32, 1, True),
@@ -293,26 +303,63 @@ def adam_step(w, m, v, grad, t: int, lr: float):
     return w - lr * mh / (np.sqrt(vh) + ADAM_EPS), m, v
 
 
-def train_step(theta, m, v, t: int, lr: float, batch):
+def energy_loss(g: np.ndarray, t: np.ndarray, fixed: np.ndarray, apply_K):
+    """Energy-norm loss of one sample as (numerator, denominator, dNum/dg):
+    e = g - t and t restricted to the free DOFs (DOF vectors), numerator
+    e.K e, denominator t.K t, dNum/dg = 2 K e on the free DOFs."""
+    free = ~np.asarray(fixed).astype(bool)
+    e = np.where(free, np.asarray(g, dtype=np.float64).reshape(-1) - np.asarray(t).reshape(-1), 0.0)
+    tm = np.where(free, np.asarray(t, dtype=np.float64).reshape(-1), 0.0)
+    Ke = np.where(free, apply_K(e), 0.0)
+    Kt = np.where(free, apply_K(tm), 0.0)
+    return float(e @ Ke), float(tm @ Kt), 2.0 * Ke
+
+
+def clip_gradient(grad, clip: float):
+    """grad scaled to L2 norm at most clip (clip <= 0: unchanged); a
+    non-finite norm gives a zero gradient."""
+    if clip <= 0:
+        return grad
+    nrm = float(np.sqrt(np.sum(grad * grad)))
+    if not np.isfinite(nrm):
+        return np.zeros_like(grad)
+    return grad * min(1.0, clip / nrm) if nrm > 0 else grad
+
+
+def train_step(theta, m, v, t: int, lr: float, batch, clip: float = 0.0, ops=None):
     """Loss, gradient and Adam update on a batch [(x0, target), ...] of one
-    grid size: the loss averages over all unmasked DOFs of the batch."""
-    cnt = sum(3.0 * loss_mask(x).sum() for x, _ in batch)
-    total, grad = 0.0, np.zeros_like(theta)
-    for x, tgt in batch:
-        g, cache = forward(theta, x)
-        mask = loss_mask(x)
-        d = (g - tgt) * mask
-        total += float((d * d).sum())
-        gt, _ = backward(cache, 2.0 * d / cnt)
-        grad += gt
-    theta, m, v = adam_step(theta, m, v, grad, t, lr)
-    return total / cnt, grad, theta, m, v
+    grid size.  ops = None: the mean squared error over all unmasked DOFs of
+    the batch; else ops[b] = (fixed, apply_K) of sample b and the energy loss
+    sum_b e.K_b e / sum_b t.K_b t.  The returned gradient is the unclipped one."""
+    grad = np.zeros_like(theta)
+    if ops is None:
+        cnt = sum(3.0 * loss_mask(x).sum() for x, _ in batch)
+        total = 0.0
+        for x, tgt in batch:
+            g, cache = forward(theta, x)
+            d = (g - tgt) * loss_mask(x)
+            total += float((d * d).sum())
+            gt, _ = backward(cache, 2.0 * d / cnt)
+            grad += gt
+        loss = total / cnt
+    else:
+        parts = []
+        for (x, tgt), (fixed, apply_K) in zip(batch, ops):
+            g, cache = forward(theta, x)
+            parts.append((cache, g.shape) + energy_loss(g, tgt, fixed, apply_K))
+        den = sum(p[3] for p in parts)
+        loss = sum(p[2] for p in parts) / den
+        for cache, shape, _, _, dnum in parts:
+            gt, _ = backward(cache, (dnum / den).reshape(shape))
+            grad += gt
+    theta, m, v = adam_step(theta, m, v, clip_gradient(grad, clip), t, lr)
+    return loss, grad, theta, m, v
 
 
 # ---------------------------------------------------------------- features
 
 def node_features(nx: int, ny: int, nz: int, rho: np.ndarray, f: np.ndarray, fixed: np.ndarray) -> np.ndarray:
-    """[nz+1][ny+1][nx+1][8] network input for one cantilever problem."""
+    """[nz+1][ny+1][nx+1][12] network input for one cantilever problem."""
     rho = np.asarray(rho, dtype=np.float64).reshape(nz, ny, nx)
     acc = np.zeros((nz + 1, ny + 1, nx + 1))
     cnt = np.zeros_like(acc)
@@ -332,6 +379,11 @@ def node_features(nx: int, ny: int, nz: int, rho: np.ndarray, f: np.ndarray, fix
     x[..., 5] = i / nx
     x[..., 6] = j / ny
     x[..., 7] = k / nz
+    res = F.reshape(-1, 3).sum(axis=0)
+    rn = np.linalg.norm(res)
+    if rn > 0:
+        x[..., 8:11] = res / rn
+    x[..., 11] = 1.0
     return x
 
 

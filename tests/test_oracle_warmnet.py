@@ -87,10 +87,10 @@ def test_zero_weights_give_the_output_bias():
     P = W.unpack(theta)
     for name in P:
         P[name][1][:] = 0.3  # views into theta
-    x = _rng(6).normal(size=(9, 9, 9, 8))
+    x = _rng(6).normal(size=(9, 9, 9, W.N_IN))
     g, _ = W.forward(theta, x)
     np.testing.assert_allclose(g, 0.3)
-    assert W.n_params() == 27 * 28336 + 467
+    assert W.n_params() == 27 * 28400 + 467
 
 
 def _tiny_problem(seed=7, n=8):
@@ -177,7 +177,12 @@ def test_node_features():
     assert np.abs(x[..., 1:4]).max() == pytest.approx(1.0)
     np.testing.assert_array_equal(x[:, :, 0, 4], 1.0)
     assert x[:, :, 1:, 4].sum() == 0
-    np.testing.assert_allclose(x[2, 3, 5, 5:], [5 / nx, 3 / ny, 2 / nz])
+    np.testing.assert_allclose(x[2, 3, 5, 5:8], [5 / nx, 3 / ny, 2 / nz])
+    th = 2 * np.pi * 5 / 16  # rotated_tip_edge_load direction 5 of 16: (0, sin, -cos)
+    np.testing.assert_allclose(x[..., 8:11], np.broadcast_to([0.0, np.sin(th), -np.cos(th)], x[..., 8:11].shape),
+                               atol=1e-15)
+    np.testing.assert_array_equal(x[..., 11], 1.0)
+    assert np.all(W.node_features(nx, ny, nz, rho, 0 * f, fixed)[..., 8:11] == 0)
     np.testing.assert_allclose(W.node_features(nx, ny, nz, np.full((nz, ny, nx), 0.7), f, fixed)[..., 0], 0.7)
 
 
@@ -197,6 +202,60 @@ def test_warm_start_scaling():
     e0, e = u, u - u0
     assert e @ K @ e <= e0 @ K @ e0  # never worse than the cold start in the energy norm
     assert W.warm_start(lambda v: K @ v, f, -g, fixed)[1] == 0.0
+
+
+def _tiny_operator(n=8, seed=7):
+    from oracle import fem
+    rho = inputs.filtered_random_density(n, n, n, seed)
+    fixed = inputs.clamp_xmin_mask(n, n, n)
+    grid = fem.Grid(n, n, n)
+    E, Ke = fem.moduli(rho, 3.0), fem.element_stiffness(0.3)
+    return fixed, (lambda v: fem.matfree_apply(grid, E, Ke, v))
+
+
+def test_energy_loss_closed_forms():
+    fixed, K = _tiny_operator()
+    t = _rng(13).normal(size=fixed.size)
+    num, den, _ = W.energy_loss(t, t, fixed, K)
+    assert num == 0.0 and den > 0
+    num0, den0, _ = W.energy_loss(np.zeros_like(t), t, fixed, K)
+    assert num0 == pytest.approx(den0, rel=1e-14)
+    num2, den2, _ = W.energy_loss(2 * t, t, fixed, K)
+    assert num2 == pytest.approx(den2, rel=1e-14)
+    # values on fixed DOFs do not count
+    g = t + 5.0 * fixed
+    assert W.energy_loss(g, t, fixed, K)[0] == pytest.approx(0.0, abs=1e-12)
+
+
+def test_energy_loss_gradient_matches_central_differences():
+    """The loss is quadratic in the output g, so central differences in g are
+    exact up to rounding; the network's own backward pass is pinned per layer
+    above, and train_step is checked to chain the two."""
+    fixed, K = _tiny_operator(seed=14)
+    r = _rng(15)
+    t = r.normal(size=fixed.size)
+    g = r.normal(size=fixed.size)
+    num, den, dnum = W.energy_loss(g, t, fixed, K)
+    for _ in range(3):
+        v = r.normal(size=g.size)
+        fd = (W.energy_loss(g + 1e-3 * v, t, fixed, K)[0] - W.energy_loss(g - 1e-3 * v, t, fixed, K)[0]) / 2e-3
+        assert fd == pytest.approx(float(dnum @ v), rel=1e-9)
+    x, _, theta = _tiny_problem(14)
+    tgt = t.reshape(9, 9, 9, 3)
+    loss, grad, _, _, _ = W.train_step(theta, np.zeros_like(theta), np.zeros_like(theta), 1, 0.0,
+                                       [(x, tgt)], ops=[(fixed, K)])
+    gr, cr = W.forward(theta, x)
+    nr, dr, dnr = W.energy_loss(gr, tgt, fixed, K)
+    assert loss == pytest.approx(nr / dr, rel=1e-14)
+    np.testing.assert_allclose(grad, W.backward(cr, (dnr / dr).reshape(gr.shape))[0], rtol=1e-12, atol=1e-15)
+
+
+def test_gradient_clipping():
+    g = np.array([3.0, 4.0])
+    np.testing.assert_allclose(W.clip_gradient(g, 1.0), [0.6, 0.8])
+    np.testing.assert_array_equal(W.clip_gradient(g, 10.0), g)
+    np.testing.assert_array_equal(W.clip_gradient(g, 0.0), g)
+    assert np.all(W.clip_gradient(np.array([np.inf, 1.0]), 1.0) == 0)
 
 
 def test_training_lowers_the_loss():
