@@ -13,7 +13,7 @@
  * 16/32/64/64 channels, 3x3x3 kernels, zero padding, leaky ReLU slope 0.1):
  *
  *   layer  cin cout stride                     layer  cin cout stride
- *   0 e0a    8   16   1                        6 d3    64   64   2
+ *   0 e0a   12   16   1                        6 d3    64   64   2
  *   1 e0b   16   16   1  -> s0                 7 e3    64   64   1
  *   2 d1    16   32   2                        8 u2   128   64   1  in [up(e3), s2]
  *   3 e1    32   32   1  -> s1                 9 u1    96   32   1  in [up(u2), s1]
@@ -29,16 +29,20 @@
  *     n = i + (nx+1)*(j + (ny+1)*k); a batch of B fields of one grid is stored
  *     back to back.  The 3-channel output of one problem is therefore the
  *     solver's DOF vector (3n + c);
- *   - input features (8 channels, gmg_net_features): nodal density (mean over
+ *   - input features (12 channels, gmg_net_features): nodal density (mean over
  *     the adjacent elements), load f / max|f| (3), 1 on nodes with a fixed DOF,
- *     normalised coordinates i/nx, j/ny, k/nz;
+ *     normalised coordinates i/nx, j/ny, k/nz, the resultant load direction
+ *     sum(f) / |sum(f)| as a constant field (3; 0 when the resultant vanishes)
+ *     and a constant 1 -- the constant fields carry the load direction to nodes
+ *     beyond the network's receptive field;
  *   - parameters: one flat FP32 vector, per layer the weights W[cout][27][cin]
  *     (tap t = dx + 3 dy + 9 dz, offset d - 1 per axis) then the cout biases,
  *     layers in the order of the table (gmg_net_num_params() values);
  *   - arithmetic: the convolutions use the weights rounded to bfloat16 (round
- *     to nearest even) with FP32 activations, biases and accumulation; Adam
- *     (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) updates FP32 master
- *     weights and re-rounds them;
+ *     to nearest even) with FP32 activations, biases and accumulation; the
+ *     gradient is rescaled to global L2 norm <= clip (clip > 0; a non-finite
+ *     norm skips the update), then Adam (beta1 0.9, beta2 0.999, eps 1e-8,
+ *     bias-corrected) updates FP32 master weights and re-rounds them;
  *   - *_dev pointers are CUDA device memory owned by the caller; the network
  *     owns its parameters, optimiser state and per-shape workspaces;
  *   - status codes are those of gmg.h; gmg_last_error() describes errors;
@@ -58,11 +62,11 @@ extern "C" {
 
 typedef struct gmg_net gmg_net;
 
-#define GMG_NET_IN 8
+#define GMG_NET_IN 12
 #define GMG_NET_OUT 3
 #define GMG_NET_LAYERS 12
 
-/* Number of FP32 values in the flat parameter vector (765,539). */
+/* Number of FP32 values in the flat parameter vector (767,267). */
 long long gmg_net_num_params(void);
 
 /* shape = {cin, cout, stride, has_activation} of layer 0..GMG_NET_LAYERS-1. */
@@ -75,29 +79,40 @@ int gmg_net_create(gmg_net** net, const float* params_dev, void* stream);
 /* Replaces the parameters (device FP32) and resets the Adam state and step count. */
 int gmg_net_set_params(gmg_net* net, const float* params_dev);
 
-/* Copies the FP32 master parameters / the gradient of the last
- * gmg_net_train_step (before its update) into params_dev / grads_dev. */
+/* Copies the FP32 master parameters / the (unclipped) gradient of the last
+ * gmg_net_train_step into params_dev / grads_dev. */
 int gmg_net_get_params(gmg_net* net, float* params_dev);
 int gmg_net_get_grads(gmg_net* net, float* grads_dev);
 
-/* g_dev[B][n_nodes][3] = network(x_dev[B][n_nodes][8]) on the grid nx x ny x nz
+/* g_dev[B][n_nodes][3] = network(x_dev[B][n_nodes][12]) on the grid nx x ny x nz
  * (multiples of 8, each >= 8).  Errors: GMG_ERR_ARG, GMG_ERR_NOMEM, GMG_ERR_CUDA. */
 int gmg_net_forward(gmg_net* net, int nx, int ny, int nz, int batch, const float* x_dev, float* g_dev);
 
 /* One training step on a batch of `batch` problems of one grid: the inputs
- * x_dev[b] ([n_nodes][8]) and targets t_dev[b] ([n_nodes][3]) are host arrays
- * of device pointers.  Loss = mean over the DOFs of nodes without a fixed DOF
- * (feature channel 4 < 0.5) of (g - t)^2, summed over the batch before the
- * division; its gradient goes through every layer (straight through the
- * bf16 rounding of the weights), then one Adam update with step size lr.
- * loss_dev (device float, may be NULL) receives the batch loss.  The kernels
- * of a step are captured once per (grid, batch) in a CUDA graph and replayed. */
+ * x_dev[b] ([n_nodes][12]) and targets t_dev[b] ([n_nodes][3]) are host arrays
+ * of device pointers.  Loss:
+ *   ops == NULL: mean over the DOFs of nodes without a fixed DOF (feature
+ *     channel 4 < 0.5) of (g - t)^2, summed over the batch before the division;
+ *   ops != NULL: ops[b] is a solver handle of problem b (same grid and
+ *     Poisson's ratio for the whole batch); the batch mean of the relative
+ *     energy-norm error left after the best rescaling of the output,
+ *     L_b = min_a ||t_b - a g_b||^2_K / ||t_b||^2_K
+ *         = 1 - (t.K g)^2 / ((g.K g)(t.K t))  (g, t on the free DOFs),
+ *     K = K_b applied by the handle's matrix-free fine operator (FP32) -- the
+ *     quantity gmg_warm_start's rescaling leaves.
+ * The gradient goes through every layer (straight through the bf16 rounding
+ * of the weights), is clipped to L2 norm clip (clip <= 0: no clipping), then
+ * one Adam update with step size lr.  loss_dev (device float, may be NULL)
+ * receives the batch loss.  The kernels of a step are captured once per
+ * (grid, batch, loss) in a CUDA graph and replayed; the operators' moduli and
+ * masks are copied into the step's workspace, so the handles may differ from
+ * call to call. */
 int gmg_net_train_step(gmg_net* net, int nx, int ny, int nz, int batch, const float* const* x_dev,
-                       const float* const* t_dev, float lr, float* loss_dev);
+                       const float* const* t_dev, gmg_handle* const* ops, float lr, float clip, float* loss_dev);
 
 /* Input features of one problem: rho_dev element densities (device float
  * [nz][ny][nx]), f_dev load (device double[3*n_nodes]), fixed_dev per-DOF flags
- * (device uint8[3*n_nodes], 1 = fixed) -> x_dev (device float[n_nodes][8]).
+ * (device uint8[3*n_nodes], 1 = fixed) -> x_dev (device float[n_nodes][12]).
  * stream: cudaStream_t or NULL. */
 int gmg_net_features(int nx, int ny, int nz, const float* rho_dev, const double* f_dev,
                      const uint8_t* fixed_dev, float* x_dev, void* stream);
@@ -110,10 +125,11 @@ int gmg_net_target(int nx, int ny, int nz, const double* u_dev, float* t_dev, vo
  * features from rho_dev, f_dev and the handle's Dirichlet mask, one forward
  * pass, fixed DOFs zeroed, then the energy-optimal rescaling
  * u0 = alpha g, alpha = f.g / g.K g (the minimiser of ||u - alpha g||_K over
- * alpha, with K applied by gmg_apply), kept only when both dot products are
- * positive and finite; otherwise u0 = 0 (the cold start).  u0_dev: device
- * double[3*n_nodes].  alpha_out (host, may be NULL) receives alpha (0 = cold
- * start kept) and makes the call synchronous. */
+ * all real alpha, with K applied by gmg_apply, so never farther from u in
+ * the energy norm than u0 = 0); g.K g <= 0 or a non-finite product keeps
+ * u0 = 0 (the cold start).  u0_dev: device double[3*n_nodes].  alpha_out
+ * (host, may be NULL) receives alpha (0 = cold start kept) and makes the call
+ * synchronous. */
 int gmg_warm_start(gmg_handle* h, gmg_net* net, const float* rho_dev, const double* f_dev, double* u0_dev,
                    double* alpha_out);
 

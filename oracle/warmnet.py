@@ -51,18 +51,19 @@ a constant 1.  The constant fields carry the load direction to nodes beyond the
 network's receptive field (about 40 nodes), which the local load channels
 cannot reach on the larger grids.  Target: the PCG solution divided by
 its RMS over all 3N entries.  Two losses: (mse) the mean squared error over the
-DOFs of nodes without a fixed DOF; (energy) the error in the energy norm of
-the sample's own stiffness, sum_b e_b.K_b e_b / sum_b t_b.K_b t_b with
-e_b = g_b - t_b on the free DOFs (0 on fixed ones), whose gradient is
-2 K_b e_b / sum_b t_b.K_b t_b -- the norm in which PCG measures the error of
-its initial guess, which the mean squared error weights very differently
-(roughness of the output costs little in L2 and much in energy).  Optimiser: the gradient is rescaled to global L2 norm at most
+DOFs of nodes without a fixed DOF; (energy) the relative error in the energy
+norm of the sample's own stiffness after the best rescaling of the output,
+L_b = min_a ||t_b - a g_b||_K^2 / ||t_b||_K^2 = 1 - (t.K g)^2 / ((g.K g)(t.K t))
+(g, t restricted to the free DOFs), averaged over the batch -- exactly the
+quantity the warm start's rescaling leaves, measured in the norm in which PCG
+measures the error of its initial guess (roughness of the output costs little
+in L2 and much in energy).  Optimiser: the gradient is rescaled to global L2 norm at most
 ``clip`` (when clip > 0), then Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias
 corrected) updates FP32 master weights; the network computes with the weights
 rounded to bfloat16 (round to nearest even) and FP32 biases.  Warm start: the
 masked output g is rescaled by the energy-optimal factor
-alpha = f.g / g.K g (minimiser of ||u - alpha g||_K), kept only if both dot
-products are positive, else u0 = 0 (cold start).
+alpha = f.g / g.K g (minimiser of ||u - alpha g||_K over all real alpha, so
+never worse than u0 = 0); g.K g <= 0 or a non-finite value keeps u0 = 0.
 """
 
 from __future__ import annotations
@@ -304,15 +305,19 @@ def adam_step(w, m, v, grad, t: int, lr: float):
 
 
 def energy_loss(g: np.ndarray, t: np.ndarray, fixed: np.ndarray, apply_K):
-    """Energy-norm loss of one sample as (numerator, denominator, dNum/dg):
-    e = g - t and t restricted to the free DOFs (DOF vectors), numerator
-    e.K e, denominator t.K t, dNum/dg = 2 K e on the free DOFs."""
+    """Scale-free energy loss of one sample, (L, dL/dg): with g and t
+    restricted to the free DOFs (DOF vectors), a = t.K g, b = g.K g,
+    c = t.K t, L = 1 - a^2 / (b c) and dL/dg = (2a / (b c)) ((a/b) K g - K t);
+    L = 1 with a zero gradient when b or c is not positive."""
     free = ~np.asarray(fixed).astype(bool)
-    e = np.where(free, np.asarray(g, dtype=np.float64).reshape(-1) - np.asarray(t).reshape(-1), 0.0)
+    gm = np.where(free, np.asarray(g, dtype=np.float64).reshape(-1), 0.0)
     tm = np.where(free, np.asarray(t, dtype=np.float64).reshape(-1), 0.0)
-    Ke = np.where(free, apply_K(e), 0.0)
+    Kg = np.where(free, apply_K(gm), 0.0)
     Kt = np.where(free, apply_K(tm), 0.0)
-    return float(e @ Ke), float(tm @ Kt), 2.0 * Ke
+    a, b, c = float(tm @ Kg), float(gm @ Kg), float(tm @ Kt)
+    if not (b > 0 and c > 0):
+        return 1.0, np.zeros_like(gm)
+    return 1.0 - a * a / (b * c), (2.0 * a / (b * c)) * ((a / b) * Kg - Kt)
 
 
 def clip_gradient(grad, clip: float):
@@ -329,8 +334,8 @@ def clip_gradient(grad, clip: float):
 def train_step(theta, m, v, t: int, lr: float, batch, clip: float = 0.0, ops=None):
     """Loss, gradient and Adam update on a batch [(x0, target), ...] of one
     grid size.  ops = None: the mean squared error over all unmasked DOFs of
-    the batch; else ops[b] = (fixed, apply_K) of sample b and the energy loss
-    sum_b e.K_b e / sum_b t.K_b t.  The returned gradient is the unclipped one."""
+    the batch; else ops[b] = (fixed, apply_K) of sample b and the batch mean
+    of the scale-free energy loss.  The returned gradient is the unclipped one."""
     grad = np.zeros_like(theta)
     if ops is None:
         cnt = sum(3.0 * loss_mask(x).sum() for x, _ in batch)
@@ -343,14 +348,12 @@ def train_step(theta, m, v, t: int, lr: float, batch, clip: float = 0.0, ops=Non
             grad += gt
         loss = total / cnt
     else:
-        parts = []
+        loss = 0.0
         for (x, tgt), (fixed, apply_K) in zip(batch, ops):
             g, cache = forward(theta, x)
-            parts.append((cache, g.shape) + energy_loss(g, tgt, fixed, apply_K))
-        den = sum(p[3] for p in parts)
-        loss = sum(p[2] for p in parts) / den
-        for cache, shape, _, _, dnum in parts:
-            gt, _ = backward(cache, (dnum / den).reshape(shape))
+            L, dg = energy_loss(g, tgt, fixed, apply_K)
+            loss += L / len(batch)
+            gt, _ = backward(cache, (dg / len(batch)).reshape(g.shape))
             grad += gt
     theta, m, v = adam_step(theta, m, v, clip_gradient(grad, clip), t, lr)
     return loss, grad, theta, m, v
@@ -400,7 +403,7 @@ def warm_start(apply_K, f: np.ndarray, g: np.ndarray, fixed: np.ndarray):
     g = np.where(np.asarray(fixed).astype(bool), 0.0, np.asarray(g, dtype=np.float64))
     fg = float(f @ g)
     gKg = float(g @ apply_K(g))
-    if not (fg > 0 and gKg > 0):
+    if not (gKg > 0 and np.isfinite(fg) and np.isfinite(gKg)):
         return np.zeros_like(g), 0.0
     alpha = fg / gKg
     return alpha * g, alpha

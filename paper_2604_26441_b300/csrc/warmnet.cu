@@ -49,7 +49,7 @@ constexpr int kLayers = GMG_NET_LAYERS;
 struct LayerDef {
     int cin, cout, stride, act;
 };
-constexpr LayerDef kDefs[kLayers] = {{8, 16, 1, 1},  {16, 16, 1, 1}, {16, 32, 2, 1},  {32, 32, 1, 1},
+constexpr LayerDef kDefs[kLayers] = {{12, 16, 1, 1},  {16, 16, 1, 1}, {16, 32, 2, 1},  {32, 32, 1, 1},
                                      {32, 64, 2, 1}, {64, 64, 1, 1}, {64, 64, 2, 1},  {64, 64, 1, 1},
                                      {128, 64, 1, 1}, {96, 32, 1, 1}, {48, 16, 1, 1}, {16, 3, 1, 0}};
 enum { L_E0A, L_E0B, L_D1, L_E1, L_D2, L_E2, L_D3, L_E3, L_U2, L_U1, L_U0, L_OUT };
@@ -563,18 +563,127 @@ __global__ void k_loss_finish(const double* partial, int n, const double* sc, fl
     *loss = sc[0] > 0.0 ? (float)(s / sc[0]) : 0.f;
 }
 
+// Energy loss, step 1: gm = g and tm = t on the free DOFs (0 on fixed ones)
+// for B samples; g has pitch 4, t pitch 3, mask = per-node fixed-component bits.
+__global__ void k_energy_prep(const float* __restrict__ g, const float* __restrict__ t, const uint8_t* __restrict__ mask,
+                              long long nn, int B, float* __restrict__ gm, float* __restrict__ tm) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= 3 * nn * B) return;
+    const long long bn = i / 3;  // b * nn + n
+    const int c = (int)(i % 3);
+    const bool fx = (mask[bn] >> c) & 1;
+    gm[i] = fx ? 0.f : g[4 * bn + c];
+    tm[i] = fx ? 0.f : t[i];
+}
+
+constexpr int kEnergyBlocks = 64;  // reduction blocks per sample
+
+// Per sample b (blockIdx.y): partial[(b * kEnergyBlocks + block) * 3 + {0,1,2}] =
+// sums of tm.Kg, gm.Kg, tm.Kt over that sample's n = 3 nn entries.
+__global__ void __launch_bounds__(kRedThreads) k_energy_dots(const float* __restrict__ gm, const float* __restrict__ kg,
+                                                             const float* __restrict__ tm, const float* __restrict__ kt,
+                                                             long long n, double* partial) {
+    __shared__ double sh[3][kRedThreads];
+    const long long off = blockIdx.y * n;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kRedThreads) {
+        const double t = tm[off + i], g = gm[off + i], Kg = kg[off + i];
+        a += t * Kg;
+        b += g * Kg;
+        c += t * (double)kt[off + i];
+    }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    sh[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) partial[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 3 + k] = sh[k][0];
+}
+
+// Per sample: L_b = 1 - a^2 / (b c); dL/dg_b = coef[2b] K g + coef[2b+1] K t with
+// coef = (2a/(bc)) (a/b, -1) / B (zero, and L_b = 1, when b or c is not positive).
+// loss = mean of L_b.
+__global__ void k_energy_finish(const double* partial, int nb, int B, double* coef, float* loss) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double L = 0.0;
+    for (int s = 0; s < B; ++s) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int i = 0; i < nb; ++i) {
+            a += partial[((long long)s * nb + i) * 3];
+            b += partial[((long long)s * nb + i) * 3 + 1];
+            c += partial[((long long)s * nb + i) * 3 + 2];
+        }
+        if (b > 0.0 && c > 0.0 && isfinite(a) && isfinite(b) && isfinite(c)) {
+            L += 1.0 - a * a / (b * c);
+            const double k = 2.0 * a / (b * c) / (double)B;
+            coef[2 * s] = k * a / b;
+            coef[2 * s + 1] = -k;
+        } else {
+            L += 1.0;
+            coef[2 * s] = 0.0;
+            coef[2 * s + 1] = 0.0;
+        }
+    }
+    *loss = (float)(L / (double)B);
+}
+
+// gg[b][n][c] = coef[2b] Kg + coef[2b+1] Kt (pitch 4, channel 3 = 0)
+__global__ void k_energy_grad(const float* __restrict__ kg, const float* __restrict__ kt, long long nn, int B,
+                              const double* __restrict__ coef, float* __restrict__ gg) {
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= nn * B) return;
+    const int b = (int)(n / nn);
+    const float s1 = (float)coef[2 * b], s2 = (float)coef[2 * b + 1];
+    float4 o;
+    o.x = s1 * kg[3 * n] + s2 * kt[3 * n];
+    o.y = s1 * kg[3 * n + 1] + s2 * kt[3 * n + 1];
+    o.z = s1 * kg[3 * n + 2] + s2 * kt[3 * n + 2];
+    o.w = 0.f;
+    *reinterpret_cast<float4*>(gg + 4 * n) = o;
+}
+
 struct LayerTable {
     long long woff[kLayers], boff[kLayers];
     int cin[kLayers], coutp[kLayers];
 };
 
-// Adam step counter and bias corrections: adam[0] = t, adam[1] = 1/(1-b1^t), adam[2] = 1/(1-b2^t)
-__global__ void k_adam_tick(double* adam) {
+// partial[block] = sum of squares of a float vector
+__global__ void __launch_bounds__(kRedThreads) k_sumsq_f(const float* __restrict__ v, long long n, double* partial) {
+    __shared__ double sh[kRedThreads];
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kRedThreads)
+        s += (double)v[i] * (double)v[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// Adam step counter, bias corrections and gradient scale: adam[0] = t,
+// adam[1] = 1/(1-b1^t), adam[2] = 1/(1-b2^t), adam[3] = min(1, clip/|g|)
+// (1 without clipping, 0 for a non-finite norm).
+__global__ void k_adam_tick(double* adam, const double* gnorm_partial, int nb, const float* clip) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double t = adam[0] + 1.0;
     adam[0] = t;
     adam[1] = 1.0 / (1.0 - pow(kBeta1, t));
     adam[2] = 1.0 / (1.0 - pow(kBeta2, t));
+    double ss = 0.0;
+    for (int i = 0; i < nb; ++i) ss += gnorm_partial[i];
+    const double nrm = sqrt(ss);
+    const double c = (double)clip[0];
+    double scale = 1.0;
+    if (!isfinite(nrm)) scale = 0.0;
+    else if (c > 0.0 && nrm > c) scale = c / nrm;
+    adam[3] = scale;
 }
 
 // Writes the bfloat16-rounded copies of weight i of layer l: Wr (own layout),
@@ -605,7 +714,7 @@ __global__ void k_adam(const LayerTable T, long long n, float* __restrict__ P, f
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float c1 = (float)adam[1], c2 = (float)adam[2];
-    const float g = G[i];
+    const float g = G[i] * (float)adam[3];
     const float m = (float)kBeta1 * M[i] + (1.f - (float)kBeta1) * g;
     const float v = (float)kBeta2 * V[i] + (1.f - (float)kBeta2) * g * g;
     M[i] = m;
@@ -627,11 +736,54 @@ __global__ void k_round_all(const LayerTable T, long long n, const float* __rest
     else Wr[i] = P[i];
 }
 
+// Load statistics of one problem: partial[4 block + 0] = max |f|,
+// partial[4 block + 1..3] = sum of the x / y / z load components.
+__global__ void __launch_bounds__(kRedThreads) k_load_stats(const double* __restrict__ f, long long nn, double* partial) {
+    __shared__ double sh[4][kRedThreads];
+    double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (long long n = blockIdx.x * (long long)kRedThreads + threadIdx.x; n < nn; n += (long long)gridDim.x * kRedThreads) {
+        const double a = f[3 * n], b = f[3 * n + 1], c = f[3 * n + 2];
+        m = fmax(m, fmax(fabs(a), fmax(fabs(b), fabs(c))));
+        sx += a;
+        sy += b;
+        sz += c;
+    }
+    sh[0][threadIdx.x] = m;
+    sh[1][threadIdx.x] = sx;
+    sh[2][threadIdx.x] = sy;
+    sh[3][threadIdx.x] = sz;
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] = fmax(sh[0][threadIdx.x], sh[0][threadIdx.x + w]);
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+            sh[2][threadIdx.x] += sh[2][threadIdx.x + w];
+            sh[3][threadIdx.x] += sh[3][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) partial[4 * blockIdx.x + k] = sh[k][0];
+}
+
+// stats[0] = 1 / max|f| (0 for f = 0), stats[1..3] = sum(f) / |sum(f)| (0 when it vanishes)
+__global__ void k_load_stats_finish(const double* partial, int nb, double* stats) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double m = 0.0, s[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < nb; ++i) {
+        m = fmax(m, partial[4 * i]);
+        for (int k = 0; k < 3; ++k) s[k] += partial[4 * i + 1 + k];
+    }
+    stats[0] = m > 0.0 ? 1.0 / m : 0.0;
+    const double r = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    for (int k = 0; k < 3; ++k) stats[1 + k] = r > 0.0 ? s[k] / r : 0.0;
+}
+
 // Input features of one problem (see gmg_warmnet.h).  Exactly one of fixed
 // (per-DOF flags) and mask (per-node component bits) is non-null.
 __global__ void k_features(int nx, int ny, int nz, const float* __restrict__ rho, const double* __restrict__ f,
                            const uint8_t* __restrict__ fixed, const uint8_t* __restrict__ mask,
-                           const double* __restrict__ fmax, float* __restrict__ x) {
+                           const double* __restrict__ stats, float* __restrict__ x) {
     const int X = nx + 1, Y = ny + 1, Z = nz + 1;
     const long long nn = (long long)X * Y * Z;
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -645,12 +797,11 @@ __global__ void k_features(int nx, int ny, int nz, const float* __restrict__ rho
                     s += rho[((long long)ez * ny + ey) * nx + ex];
                     c += 1.f;
                 }
-    const double fm = fmax[0];
-    const double inv = fm > 0.0 ? 1.0 / fm : 0.0;
+    const double inv = stats[0];
     bool fx;
     if (fixed) fx = fixed[3 * n] | fixed[3 * n + 1] | fixed[3 * n + 2];
     else fx = mask[n] != 0;
-    float4 a, bq;
+    float4 a, bq, cq;
     a.x = s / c;
     a.y = (float)(f[3 * n] * inv);
     a.z = (float)(f[3 * n + 1] * inv);
@@ -659,8 +810,14 @@ __global__ void k_features(int nx, int ny, int nz, const float* __restrict__ rho
     bq.y = (float)i / (float)nx;
     bq.z = (float)j / (float)ny;
     bq.w = (float)k / (float)nz;
-    reinterpret_cast<float4*>(x + GMG_NET_IN * n)[0] = a;
-    reinterpret_cast<float4*>(x + GMG_NET_IN * n)[1] = bq;
+    cq.x = (float)stats[1];
+    cq.y = (float)stats[2];
+    cq.z = (float)stats[3];
+    cq.w = 1.f;
+    float4* o = reinterpret_cast<float4*>(x + GMG_NET_IN * n);
+    o[0] = a;
+    o[1] = bq;
+    o[2] = cq;
 }
 
 // partial[block] = max |v| (kind 0) or sum v^2 (kind 1) over a double vector.
@@ -737,7 +894,7 @@ __global__ void k_ws_alpha(const double* partial, int nb, double* alpha) {
         a += partial[2 * i];
         b += partial[2 * i + 1];
     }
-    *alpha = (a > 0.0 && b > 0.0 && isfinite(a) && isfinite(b)) ? a / b : 0.0;
+    *alpha = (b > 0.0 && isfinite(a) && isfinite(b)) ? a / b : 0.0;
 }
 
 __global__ void k_ws_scale(const float* __restrict__ g, long long n, const double* __restrict__ alpha, double* __restrict__ u0) {
@@ -769,9 +926,20 @@ struct Work {
     float* part = nullptr;
     long long part_cap = 0;
     double* red = nullptr;   // reduction partials (2 * kRedBlocks)
-    double* sc = nullptr;    // [0] = loss DOF count
-    cudaGraphExec_t exec = nullptr;
+    double* sc = nullptr;    // [0] = loss DOF count, [1] = energy-loss gradient scale
+    cudaGraphExec_t exec = nullptr;         // train step, mean squared error
     unsigned long long graph_kernels = 0;  // kernels one replay of exec runs
+    // energy loss: per-sample moduli and masks staged from the operators,
+    // masked output / target, their images under K, per-sample dot partials
+    // and gradient coefficients
+    bool energy = false;
+    float *Es = nullptr, *gm = nullptr, *tm = nullptr, *Kg = nullptr, *Kt = nullptr;
+    double *epart = nullptr, *coef = nullptr;
+    uint8_t* ms = nullptr;
+    int* kerr = nullptr;
+    gmg::GHat gh{};
+    cudaGraphExec_t exec_energy = nullptr;
+    unsigned long long graph_kernels_energy = 0;
     std::vector<void*> allocs;
 };
 
@@ -1125,6 +1293,24 @@ int get_work(gmg_net* net, int nx, int ny, int nz, int B, bool train, Work** out
     return GMG_OK;
 }
 
+int ensure_energy(Work* w) {
+    if (w->energy) return GMG_OK;
+    const long long n3 = 3 * w->N[0] * w->B;
+    const long long ne = (long long)w->nx * w->ny * w->nz * w->B;
+    TRY(dalloc(w->allocs, &w->Es, ne));
+    TRY(dalloc(w->allocs, &w->gm, n3));
+    TRY(dalloc(w->allocs, &w->tm, n3));
+    TRY(dalloc(w->allocs, &w->Kg, n3));
+    TRY(dalloc(w->allocs, &w->Kt, n3));
+    TRY(dalloc(w->allocs, &w->epart, 3LL * kEnergyBlocks * w->B));
+    TRY(dalloc(w->allocs, &w->coef, 2LL * w->B));
+    TRY(dalloc(w->allocs, &w->ms, w->N[0] * w->B));
+    TRY(dalloc(w->allocs, &w->kerr, 4));
+    CU(cudaMemset(w->kerr, 0, sizeof(int) * 4));
+    w->energy = true;
+    return GMG_OK;
+}
+
 // Forward pass: x (pitch 8) -> g (pitch gp, gc channels written), activations kept in w.
 int forward(gmg_net* net, Work* w, const float* x, float* g, int gp, int gc, cudaStream_t s) {
     const int B = w->B;
@@ -1150,21 +1336,50 @@ int forward(gmg_net* net, Work* w, const float* x, float* g, int gp, int gc, cud
     return GMG_OK;
 }
 
-// Loss, backward pass and Adam update (training workspace, inputs staged in x0 / t).
-int train_kernels(gmg_net* net, Work* w, cudaStream_t s) {
+// Loss, backward pass and Adam update (training workspace, inputs staged in
+// x0 / t, and for the energy loss the moduli / masks in Es / ms).
+int train_kernels(gmg_net* net, Work* w, bool energy, cudaStream_t s) {
     const int B = w->B;
     const int* X = w->X;
     const int* Y = w->Y;
     const int* Z = w->Z;
     const long long* N = w->N;
     const long long nodes = N[0] * B;
-    k_count_free<<<kRedBlocks, kRedThreads, 0, s>>>(w->x0, nodes, w->red);
-    k_finish_sum<<<1, 32, 0, s>>>(w->red, kRedBlocks, 3.0, w->sc, 0);
-    note_launch(2);
+    if (!energy) {
+        k_count_free<<<kRedBlocks, kRedThreads, 0, s>>>(w->x0, nodes, w->red);
+        k_finish_sum<<<1, 32, 0, s>>>(w->red, kRedBlocks, 3.0, w->sc, 0);
+        note_launch(2);
+    }
     TRY(forward(net, w, w->x0, w->g, 4, 4, s));
-    k_loss<<<kRedBlocks, kRedThreads, 0, s>>>(w->g, w->t, w->x0, nodes, w->sc, w->gg, w->red);
-    k_loss_finish<<<1, 32, 0, s>>>(w->red, kRedBlocks, w->sc, net->loss);
-    note_launch(2);
+    if (!energy) {
+        k_loss<<<kRedBlocks, kRedThreads, 0, s>>>(w->g, w->t, w->x0, nodes, w->sc, w->gg, w->red);
+        k_loss_finish<<<1, 32, 0, s>>>(w->red, kRedBlocks, w->sc, net->loss);
+        note_launch(2);
+    } else {
+        const long long n3 = 3 * N[0];
+        const long long ne = (long long)w->nx * w->ny * w->nz;
+        k_energy_prep<<<blocks_for(n3 * B, 256), 256, 0, s>>>(w->g, w->t, w->ms, N[0], B, w->gm, w->tm);
+        note_launch();
+        for (int b = 0; b < B; ++b) {
+            gmg::FineArgs a{};
+            a.nx = w->nx;
+            a.ny = w->ny;
+            a.nz = w->nz;
+            a.E = w->Es + b * ne;
+            a.mask = w->ms + b * N[0];
+            a.err = w->kerr;
+            a.xin = w->gm + b * n3;
+            a.out = w->Kg + b * n3;
+            gmg::launch_fine(gmg::FM_APPLY, 0, 0, a, w->gh, s);
+            a.xin = w->tm + b * n3;
+            a.out = w->Kt + b * n3;
+            gmg::launch_fine(gmg::FM_APPLY, 0, 0, a, w->gh, s);
+        }
+        k_energy_dots<<<dim3(kEnergyBlocks, B), kRedThreads, 0, s>>>(w->gm, w->Kg, w->tm, w->Kt, n3, w->epart);
+        k_energy_finish<<<1, 32, 0, s>>>(w->epart, kEnergyBlocks, B, w->coef, net->loss);
+        k_energy_grad<<<blocks_for(nodes, 256), 256, 0, s>>>(w->Kg, w->Kt, N[0], B, w->coef, w->gg);
+        note_launch(3);
+    }
     // out
     TRY(wgrad(net, w, L_OUT, w->y0, 16, 16 * N[0], X[0], Y[0], Z[0], w->gg, 4, 4 * N[0], s));
     TRY(conv_bwd_s1(net, L_OUT, w->gg, 4, 4 * N[0], w->g_y0, 16, 16 * N[0], w->y0, 16, 16 * N[0], 0, X[0], Y[0], Z[0], B, s));
@@ -1210,10 +1425,11 @@ int train_kernels(gmg_net* net, Work* w, cudaStream_t s) {
     // e0a
     TRY(wgrad(net, w, L_E0A, w->x0, GMG_NET_IN, GMG_NET_IN * N[0], X[0], Y[0], Z[0], w->g_a0, 16, 16 * N[0], s));
     // Adam
-    k_adam_tick<<<1, 32, 0, s>>>(net->adam);
+    k_sumsq_f<<<kRedBlocks, kRedThreads, 0, s>>>(net->G, net->n_int, w->red);
+    k_adam_tick<<<1, 32, 0, s>>>(net->adam, w->red, kRedBlocks, net->lr + 1);
     k_adam<<<blocks_for(net->n_int, 256), 256, 0, s>>>(net->T, net->n_int, net->P, net->M, net->V, net->G, net->Wr,
                                                        net->Wf, net->Wb, net->adam, net->lr);
-    note_launch(2);
+    note_launch(3);
     return GMG_OK;
 }
 
@@ -1287,10 +1503,10 @@ int gmg_net_create(gmg_net** out, const float* params, void* stream) {
     chain(dalloc(net->allocs, &net->Wf, net->n_int));
     chain(dalloc(net->allocs, &net->Wb, net->n_int));
     chain(dalloc(net->allocs, &net->adam, 4));
-    chain(dalloc(net->allocs, &net->lr, 4));
+    chain(dalloc(net->allocs, &net->lr, 4));  // lr, clip
     chain(dalloc(net->allocs, &net->loss, 4));
-    chain(dalloc(net->allocs, &net->ws_red, 2 * kRedBlocks));
-    chain(dalloc(net->allocs, &net->ws_alpha, 2));
+    chain(dalloc(net->allocs, &net->ws_red, 4 * kRedBlocks));
+    chain(dalloc(net->allocs, &net->ws_alpha, 8));
     if (rc == GMG_OK) rc = conv_attrs();
     if (rc == GMG_OK) rc = api_to_internal(net, params);
     if (rc == GMG_OK) rc = reset_state(net);
@@ -1332,22 +1548,48 @@ int gmg_net_forward(gmg_net* net, int nx, int ny, int nz, int batch, const float
 }
 
 int gmg_net_train_step(gmg_net* net, int nx, int ny, int nz, int batch, const float* const* x, const float* const* t,
-                       float lr, float* loss) {
+                       gmg_handle* const* ops, float lr, float clip, float* loss) {
     if (!net || !x || !t) return fail(GMG_ERR_ARG, "null argument");
     TRY(check_dims(nx, ny, nz, batch));
     for (int b = 0; b < batch; ++b)
-        if (!x[b] || !t[b]) return fail(GMG_ERR_ARG, "null sample pointer");
+        if (!x[b] || !t[b] || (ops && !ops[b])) return fail(GMG_ERR_ARG, "null sample pointer");
     if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(GMG_ERR_ARG, "lr must be finite and >= 0");
+    if (!std::isfinite(clip)) return fail(GMG_ERR_ARG, "clip must be finite");
+    const bool energy = ops != nullptr;
+    if (energy)
+        for (int b = 0; b < batch; ++b) {
+            const gmg::Level& l0 = ops[b]->lev[0];
+            if (l0.nx != nx || l0.ny != ny || l0.nz != nz)
+                return fail(GMG_ERR_ARG, "operator grid differs from the batch grid");
+            if (std::memcmp(&ops[b]->gh, &ops[0]->gh, sizeof(gmg::GHat)) != 0)
+                return fail(GMG_ERR_ARG, "the operators of one batch must share Poisson's ratio");
+        }
     Work* w = nullptr;
     TRY(get_work(net, nx, ny, nz, batch, true, &w));
+    if (energy) {
+        TRY(ensure_energy(w));
+        if (w->exec_energy && std::memcmp(&w->gh, &ops[0]->gh, sizeof(gmg::GHat)) != 0) {
+            cudaGraphExecDestroy(w->exec_energy);
+            w->exec_energy = nullptr;
+        }
+        w->gh = ops[0]->gh;
+    }
     cudaStream_t s = net->stream;
     const long long N0 = w->N[0];
+    const long long ne = (long long)nx * ny * nz;
     for (int b = 0; b < batch; ++b) {
         CU(cudaMemcpyAsync(w->x0 + b * GMG_NET_IN * N0, x[b], sizeof(float) * GMG_NET_IN * N0, cudaMemcpyDeviceToDevice, s));
         CU(cudaMemcpyAsync(w->t + b * 3 * N0, t[b], sizeof(float) * 3 * N0, cudaMemcpyDeviceToDevice, s));
+        if (energy) {
+            CU(cudaMemcpyAsync(w->Es + b * ne, ops[b]->E32, sizeof(float) * ne, cudaMemcpyDeviceToDevice, s));
+            CU(cudaMemcpyAsync(w->ms + b * N0, ops[b]->lev[0].mask, N0, cudaMemcpyDeviceToDevice, s));
+        }
     }
-    CU(cudaMemcpyAsync(net->lr, &lr, sizeof(float), cudaMemcpyHostToDevice, s));
-    if (!w->exec) {
+    const float hyper[2] = {lr, clip};
+    CU(cudaMemcpyAsync(net->lr, hyper, sizeof(hyper), cudaMemcpyHostToDevice, s));
+    cudaGraphExec_t& exec = energy ? w->exec_energy : w->exec;
+    unsigned long long& kernels = energy ? w->graph_kernels_energy : w->graph_kernels;
+    if (!exec) {
         if (!net->cap && cudaStreamCreateWithFlags(&net->cap, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
             return fail(GMG_ERR_CUDA, "cannot create the capture stream");
@@ -1355,25 +1597,25 @@ int gmg_net_train_step(gmg_net* net, int nx, int ny, int nz, int batch, const fl
         // captured kernels are counted when the graph runs, not here
         const unsigned long long before = gmg::g_kernel_launches.load();
         CU(cudaStreamBeginCapture(net->cap, cudaStreamCaptureModeThreadLocal));
-        const int rc = train_kernels(net, w, net->cap);
+        const int rc = train_kernels(net, w, energy, net->cap);
         cudaGraph_t graph = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(net->cap, &graph);
-        w->graph_kernels = gmg::g_kernel_launches.load() - before;
-        gmg::g_kernel_launches.fetch_sub(w->graph_kernels);
+        kernels = gmg::g_kernel_launches.load() - before;
+        gmg::g_kernel_launches.fetch_sub(kernels);
         if (rc != GMG_OK) {
             if (graph) cudaGraphDestroy(graph);
             return rc;
         }
         if (ec != cudaSuccess) return fail(GMG_ERR_CUDA, std::string("train-step capture failed: ") + cudaGetErrorString(ec));
-        const cudaError_t ei = cudaGraphInstantiate(&w->exec, graph, 0);
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ei != cudaSuccess) {
-            w->exec = nullptr;
+            exec = nullptr;
             return fail(GMG_ERR_CUDA, std::string("train-step graph instantiation failed: ") + cudaGetErrorString(ei));
         }
     }
-    CU(cudaGraphLaunch(w->exec, s));
-    note_launch(w->graph_kernels);
+    CU(cudaGraphLaunch(exec, s));
+    note_launch(kernels);
     if (loss) CU(cudaMemcpyAsync(loss, net->loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
     CU(cudaGetLastError());
     return GMG_OK;
@@ -1386,10 +1628,10 @@ int gmg_net_features(int nx, int ny, int nz, const float* rho, const double* f, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
     double* red = nullptr;
-    CU(cudaMallocAsync(&red, sizeof(double) * (kRedBlocks + 1), s));
-    k_reduce_vec<<<kRedBlocks, kRedThreads, 0, s>>>(f, 3 * nn, 0, red);
-    k_finish_vec<<<1, 32, 0, s>>>(red, kRedBlocks, 0, red + kRedBlocks);
-    k_features<<<blocks_for(nn, 256), 256, 0, s>>>(nx, ny, nz, rho, f, fixed, nullptr, red + kRedBlocks, x);
+    CU(cudaMallocAsync(&red, sizeof(double) * (4 * kRedBlocks + 4), s));
+    k_load_stats<<<kRedBlocks, kRedThreads, 0, s>>>(f, nn, red);
+    k_load_stats_finish<<<1, 32, 0, s>>>(red, kRedBlocks, red + 4 * kRedBlocks);
+    k_features<<<blocks_for(nn, 256), 256, 0, s>>>(nx, ny, nz, rho, f, fixed, nullptr, red + 4 * kRedBlocks, x);
     note_launch(3);
     CU(cudaFreeAsync(red, s));
     CU(cudaGetLastError());
@@ -1435,8 +1677,8 @@ int gmg_warm_start(gmg_handle* h, gmg_net* net, const float* rho, const double* 
     Work* w = nullptr;
     TRY(get_work(net, l0.nx, l0.ny, l0.nz, 1, false, &w));
     // features (mask bits of the handle)
-    k_reduce_vec<<<kRedBlocks, kRedThreads, 0, s>>>(f, 3 * nn, 0, net->ws_red);
-    k_finish_vec<<<1, 32, 0, s>>>(net->ws_red, kRedBlocks, 0, net->ws_alpha + 1);
+    k_load_stats<<<kRedBlocks, kRedThreads, 0, s>>>(f, nn, net->ws_red);
+    k_load_stats_finish<<<1, 32, 0, s>>>(net->ws_red, kRedBlocks, net->ws_alpha + 1);
     k_features<<<blocks_for(nn, 256), 256, 0, s>>>(l0.nx, l0.ny, l0.nz, rho, f, nullptr, l0.mask, net->ws_alpha + 1,
                                                    net->ws_x);
     note_launch(3);
@@ -1462,6 +1704,7 @@ void gmg_net_destroy(gmg_net* net) {
     else cudaDeviceSynchronize();
     for (Work* w : net->works) {
         if (w->exec) cudaGraphExecDestroy(w->exec);
+        if (w->exec_energy) cudaGraphExecDestroy(w->exec_energy);
         free_all(w->allocs);
         delete w;
     }

@@ -104,7 +104,8 @@ _SIGS = {
     "gmg_net_get_grads": (ctypes.c_int, [_P, _P]),
     "gmg_net_forward": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
     "gmg_net_train_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                          ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_float, _P]),
+                                          ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_float,
+                                          ctypes.c_float, _P]),
     "gmg_net_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
     "gmg_net_target": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "gmg_warm_start": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
@@ -437,7 +438,7 @@ def solve_batch(solvers, fs, us=None, tol: float = 1e-6, maxit: int = 200):
 
 # ---------------------------------------------------------------- learned warm start
 
-NET_IN, NET_OUT, NET_LAYERS = 8, 3, 12
+NET_IN, NET_OUT, NET_LAYERS = 12, 3, 12
 
 
 def net_num_params() -> int:
@@ -456,7 +457,7 @@ def net_layer_shapes() -> list[tuple[int, int, int, int]]:
 
 
 def net_features(dims, rho, f, fixed, x=None, stream: int | None = None):
-    """Input features [n_nodes, 8] (device float) of one problem."""
+    """Input features [n_nodes, 12] (device float) of one problem."""
     import torch
     nx, ny, nz = dims
     nn = (nx + 1) * (ny + 1) * (nz + 1)
@@ -529,7 +530,7 @@ class WarmNet:
         return out
 
     def forward(self, dims, x, g=None):
-        """x: [B, n_nodes, 8] (or [n_nodes, 8]) device float -> g of shape [..., n_nodes, 3]."""
+        """x: [B, n_nodes, 12] (or [n_nodes, 12]) device float -> g of shape [..., n_nodes, 3]."""
         import torch
         nx, ny, nz = dims
         nn = (nx + 1) * (ny + 1) * (nz + 1)
@@ -540,10 +541,13 @@ class WarmNet:
                                          _ptr(g, torch.float32, B * 3 * nn, "g")))
         return g
 
-    def train_step(self, dims, xs, ts, lr: float, loss_out=None):
-        """One Adam step on the batch (lists of [n_nodes, 8] / [n_nodes, 3]
-        device tensors of one grid); loss_out: optional one-element device
-        float tensor (a view) receiving the batch loss."""
+    def train_step(self, dims, xs, ts, lr: float, loss_out=None, clip: float = 0.0, ops=None):
+        """One Adam step on the batch (lists of [n_nodes, 12] / [n_nodes, 3]
+        device tensors of one grid), the gradient clipped to L2 norm clip
+        (0 = no clipping); ops: None (mean squared error) or one Solver per
+        sample (energy-norm loss with that problem's stiffness); loss_out:
+        optional one-element device float tensor (a view) receiving the batch
+        loss."""
         import torch
         nx, ny, nz = dims
         nn = (nx + 1) * (ny + 1) * (nz + 1)
@@ -557,7 +561,12 @@ class WarmNet:
             if not (loss_out.is_cuda and loss_out.dtype == torch.float32 and loss_out.numel() >= 1):
                 raise TypeError("loss_out must be a CUDA float32 tensor")
             lp = ctypes.c_void_p(loss_out.data_ptr())
-        _check(self._lib.gmg_net_train_step(self._h, nx, ny, nz, B, xp, tp, float(lr), lp))
+        op = None
+        if ops is not None:
+            if len(ops) != B:
+                raise ValueError("ops must hold one solver per sample")
+            op = (ctypes.c_void_p * B)(*[o._h.value for o in ops])
+        _check(self._lib.gmg_net_train_step(self._h, nx, ny, nz, B, xp, tp, op, float(lr), float(clip), lp))
 
     def warm_start(self, solver: "Solver", rho, f, u0=None, sync: bool = True):
         """u0 = alpha g for solver (energy-optimal alpha; 0 keeps the cold start).

@@ -9,9 +9,10 @@ the oracle uses, so the only difference is FP32 rounding: sums of up to
 forward output is held to 1e-5 relative L2, the loss to 1e-5 relative, the
 gradient (sums over every output node) to 1e-4 relative L2 per layer.  One
 Adam step moves a weight by lr * m_hat / (sqrt(v_hat) + eps), which on the
-first step is lr * sign(g) when |g| >> eps, so an FP32 gradient whose sign
-differs from the FP64 one (|g| at rounding level) flips that weight's step:
-the update is compared on the weights whose FP64 gradient is not at that level.
+first step is lr * g / (|g| + eps): a gradient entry that FP32 does not resolve
+(|g| at the rounding level of its sum) changes that weight's step by up to
+2 lr, so the update is compared on the weights whose FP32 gradient is within
+1 % of the FP64 one, and bounded by 2 lr elsewhere.
 """
 
 import numpy as np
@@ -69,7 +70,7 @@ def test_features_and_target_match_oracle(dims):
     nx, ny, nz = dims
     rho, fixed, f = _problem(nx, ny, nz, 5)
     x = gmg.net_features(dims, _t(rho), _t(f, torch.float64), _t(fixed, torch.uint8)).cpu().numpy()
-    xr = W.node_features(nx, ny, nz, rho, f, fixed).reshape(-1, 8)
+    xr = W.node_features(nx, ny, nz, rho, f, fixed).reshape(-1, W.N_IN)
     np.testing.assert_allclose(x, xr, rtol=0, atol=2e-7)
     u = np.random.default_rng(1).normal(size=f.size)
     t = gmg.net_target(dims, _t(u, torch.float64)).cpu().numpy().reshape(-1)
@@ -88,7 +89,7 @@ def test_forward_matches_oracle(dims):
     for s in (11, 12):
         rho, fixed, f = _problem(nx, ny, nz, s, k_load=s)
         xs.append(W.node_features(nx, ny, nz, rho, f, fixed))
-    xb = _t(np.stack([x.reshape(-1, 8) for x in xs]))
+    xb = _t(np.stack([x.reshape(-1, W.N_IN) for x in xs]))
     g = net.forward(dims, xb).cpu().numpy()
     for b, x in enumerate(xs):
         ref, _ = W.forward(theta.astype(np.float64), x)
@@ -98,6 +99,14 @@ def test_forward_matches_oracle(dims):
     assert np.array_equal(g1[0], g[1])
     # parameters round-trip through the library's internal layout
     np.testing.assert_array_equal(net.params().cpu().numpy(), theta)
+
+
+def _resolved(g_gpu, g_ref):
+    """Weights whose FP32 gradient is resolved: |g| well above Adam's eps and
+    within 1 % of the FP64 value.  For these the first Adam step,
+    lr g / (|g| + eps), differs by far less than the 1e-6 compared; the other
+    weights' steps are bounded by 2 lr."""
+    return (np.abs(g_ref) > 1e-6) & (np.abs(g_gpu - g_ref) <= 1e-2 * np.abs(g_ref))
 
 
 def _oracle_batch(dims, seeds):
@@ -111,31 +120,76 @@ def _oracle_batch(dims, seeds):
     return batch
 
 
-@pytest.mark.parametrize("dims", [(8, 8, 8), (16, 24, 8)])
-def test_loss_gradient_and_adam_match_oracle(dims):
+@pytest.mark.parametrize("dims,seeds,clip", [((8, 8, 8), (21, 22), 0.0), ((16, 24, 8), (23, 24), 0.0),
+                                             ((32, 32, 32), (25,), 0.0), ((16, 8, 8), (26, 27), "small")])
+def test_loss_gradient_and_adam_match_oracle(dims, seeds, clip):
     from paper_2604_26441_b300 import gmg
     theta = _theta(4)
-    batch = _oracle_batch(dims, (21, 22))
-    xs = [_t(x.reshape(-1, 8)) for x, _ in batch]
+    batch = _oracle_batch(dims, seeds)
+    xs = [_t(x.reshape(-1, W.N_IN)) for x, _ in batch]
     ts = [_t(t.reshape(-1, 3)) for _, t in batch]
+    th = theta.astype(np.float64)
+    if clip == "small":
+        # a limit well below the gradient norm, so that every step is rescaled
+        _, g0, _, _, _ = W.train_step(th, np.zeros_like(th), np.zeros_like(th), 1, 0.0, batch)
+        clip = 0.25 * float(np.linalg.norm(g0))
     net = gmg.WarmNet(_t(theta))
     loss = torch.zeros(1, device="cuda")
     lr = 1e-3
-    net.train_step(dims, xs, ts, lr, loss)
+    net.train_step(dims, xs, ts, lr, loss, clip=clip)
     g_gpu = net.grads().cpu().numpy().astype(np.float64)
     p_gpu = net.params().cpu().numpy().astype(np.float64)
-    th = theta.astype(np.float64)
-    loss_ref, g_ref, p_ref, _, _ = W.train_step(th, np.zeros_like(th), np.zeros_like(th), 1, lr, batch)
+    loss_ref, g_ref, p_ref, _, _ = W.train_step(th, np.zeros_like(th), np.zeros_like(th), 1, lr, batch, clip=clip)
     assert abs(float(loss.item()) - loss_ref) <= 1e-5 * loss_ref
     k = 0
     for name, ci, co, _, _ in W.LAYERS:
         n = co * 27 * ci + co
         assert rel_l2(g_gpu[k:k + n], g_ref[k:k + n]) < 1e-4, name
         k += n
-    stable = np.abs(g_ref) > 1e-4 * np.abs(g_ref).max()
+    stable = _resolved(g_gpu, g_ref)
     assert stable.mean() > 0.5
     np.testing.assert_allclose(p_gpu[stable], p_ref[stable], rtol=0, atol=1e-6)
     assert np.all(np.abs(p_gpu - p_ref) <= 2 * lr + 1e-6)
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8), (16, 24, 8)])
+def test_energy_loss_step_matches_oracle(dims):
+    from paper_2604_26441_b300 import gmg
+    nx, ny, nz = dims
+    theta = _theta(7)
+    seeds = (51, 52)
+    batch, solvers, ops = [], [], []
+    for s_ in seeds:
+        rho, fixed, f = _problem(nx, ny, nz, s_, k_load=s_ % 16)
+        x = W.node_features(nx, ny, nz, rho, f, fixed)
+        tgt = np.random.default_rng(s_).normal(size=(nz + 1, ny + 1, nx + 1, 3))
+        batch.append((x, tgt))
+        solvers.append(gpu_solver(rho, 3.0, levels=2, smoother="jacobi", coarse_smoother=None, omega=0.5))
+        E = fem.moduli(rho, 3.0)
+        Ke = fem.element_stiffness(0.3)
+        ops.append((fixed, (lambda v, E=E, Ke=Ke: fem.matfree_apply(fem.Grid(nx, ny, nz), E, Ke, v))))
+    net = gmg.WarmNet(_t(theta))
+    loss = torch.zeros(1, device="cuda")
+    lr = 1e-3
+    net.train_step(dims, [_t(x.reshape(-1, W.N_IN)) for x, _ in batch], [_t(t.reshape(-1, 3)) for _, t in batch],
+                   lr, loss, clip=0.0, ops=solvers)
+    g_gpu = net.grads().cpu().numpy().astype(np.float64)
+    th = theta.astype(np.float64)
+    loss_ref, g_ref, p_ref, _, _ = W.train_step(th, np.zeros_like(th), np.zeros_like(th), 1, lr, batch, ops=ops)
+    assert abs(float(loss.item()) - loss_ref) <= 1e-5 * loss_ref
+    k = 0
+    for name, ci, co, _, _ in W.LAYERS:
+        n = co * 27 * ci + co
+        assert rel_l2(g_gpu[k:k + n], g_ref[k:k + n]) < 1e-4, name
+        k += n
+    p_gpu = net.params().cpu().numpy().astype(np.float64)
+    stable = _resolved(g_gpu, g_ref)
+    assert stable.mean() > 0.5
+    np.testing.assert_allclose(p_gpu[stable], p_ref[stable], rtol=0, atol=1e-6)
+    # the mean-squared-error graph of the same shape is independent of this one
+    net.train_step(dims, [_t(x.reshape(-1, W.N_IN)) for x, _ in batch], [_t(t.reshape(-1, 3)) for _, t in batch],
+                   0.0, loss)
+    assert float(loss.item()) > 0
 
 
 def test_train_steps_are_bitwise_reproducible():
@@ -143,7 +197,7 @@ def test_train_steps_are_bitwise_reproducible():
     dims = (16, 8, 8)
     theta = _t(_theta(5))
     batch = _oracle_batch(dims, (31, 32, 33))
-    xs = [_t(x.reshape(-1, 8)) for x, _ in batch]
+    xs = [_t(x.reshape(-1, W.N_IN)) for x, _ in batch]
     ts = [_t(t.reshape(-1, 3)) for _, t in batch]
     runs = []
     for _ in range(2):
@@ -177,14 +231,14 @@ def test_warm_start_matches_oracle(dims):
     else:
         assert alpha == pytest.approx(alpha_ref, rel=1e-4)
         assert rel_l2(u0.cpu().numpy(), u0_ref) < 1e-4
-    # the negated output is rejected (f.g changes sign), leaving the cold start
+    # the negated output gives the same warm start with alpha negated
     neg = theta.copy()
     k = W.n_params() - (3 * 27 * 16 + 3)
     neg[k:] = -neg[k:]
     net.set_params(_t(neg))
     u0n, alphan = net.warm_start(S, _t(rho), _t(f, torch.float64))
-    if alpha_ref > 0:
-        assert alphan == 0.0 and torch.count_nonzero(u0n).item() == 0
+    assert alphan == pytest.approx(-alpha, rel=1e-6)
+    assert rel_l2(u0n.cpu().numpy(), u0.cpu().numpy()) < 1e-6
     # a warm-started solve converges to the same solution as the cold one
     net.set_params(_t(theta))
     u0, _ = net.warm_start(S, _t(rho), _t(f, torch.float64))
@@ -192,3 +246,51 @@ def test_warm_start_matches_oracle(dims):
     uc, ic = S.solve(_t(f, torch.float64), None, tol=1e-8, maxit=200)
     assert iw["status"] == 0 and ic["status"] == 0
     assert rel_l2(uw.cpu().numpy(), uc.cpu().numpy()) < 1e-6
+
+
+def test_trained_network_gains_over_cold_start():
+    """What training buys: on held-out problems the rescaled network guess is
+    much closer to the oracle's exact solution in the energy norm than the
+    cold start (whose relative energy error is exactly 1) and than the
+    untrained network, and warm-started PCG still converges to the FP64
+    tolerance.  Iteration counts are recorded; with a multigrid preconditioner
+    of kappa_eff ~ 1.5 each PCG iteration already cuts the energy error about
+    tenfold, so a guess at ~40 % energy error is worth about one iteration."""
+    from oracle import solver as so
+    from paper_2604_26441_b300 import gmg, warmstart as ws
+
+    from gpu_helpers import oracle_hierarchy
+
+    data = ws.generate(n_solves=120, grids=(16, 24, 32), loads_per_field=4, seed=5000)
+    n = 24
+    probs = ws.held_out_problems(n, 3, seed=777000)
+    net = gmg.WarmNet(ws.initial_params(0))
+
+    def oracle_errors():
+        out = []
+        for rho, f in probs:
+            S = gmg.Solver(rho, p=3.0, opts=ws.solver_options())
+            u0, _ = net.warm_start(S, rho, f)
+            S.close()
+            r = rho.cpu().numpy().astype(np.float64)
+            fixed = inputs.clamp_xmin_mask(n, n, n)
+            H, E = oracle_hierarchy(r, 3.0, fixed, 0)
+            fh = f.cpu().numpy()
+            ustar = so.exact_solve(H, fh, so.SmootherSpec("chebyshev", 2))
+            K = lambda v: fem.matfree_apply(fem.Grid(n, n, n), E, fem.element_stiffness(0.3),
+                                            np.where(fixed == 1, 0.0, v))
+            e = u0.cpu().numpy() - ustar
+            out.append(float(np.sqrt((e @ K(e)) / (ustar @ K(ustar)))))
+        return np.array(out)
+
+    before = oracle_errors()
+    losses, _ = ws.train(net, data, steps=1500, batch=4)
+    after = oracle_errors()
+    res = ws.evaluate(net, probs, reps=1)
+    data.close()
+    assert losses[-100:].mean() < 0.75 * losses[:100].mean()
+    assert np.all(before <= 1.0 + 1e-9)  # the rescaling never loses to the cold start
+    assert after.mean() < 0.75 and after.mean() < before.mean() - 0.1, (before, after)
+    assert all(r["cold_status"] == 0 and r["warm_status"] == 0 and r["warm_rel_residual"] <= 1e-6 for r in res)
+    for r in res:
+        assert r["warm_iterations"] <= r["cold_iterations"] + 1, r
