@@ -66,6 +66,10 @@ typedef struct gmg_net gmg_net;
 #define GMG_NET_OUT 3
 #define GMG_NET_LAYERS 12
 
+/* Arithmetic of the stride-1 convolutions (gmg_net_set_arith). */
+#define GMG_NET_FP32 0   /* FP32 CUDA-core direct convolution (default) */
+#define GMG_NET_TF32 1   /* tcgen05 tensor cores, kind::tf32: activations read as TF32, weights exact */
+
 /* Number of FP32 values in the flat parameter vector (767,267). */
 long long gmg_net_num_params(void);
 
@@ -83,6 +87,20 @@ int gmg_net_set_params(gmg_net* net, const float* params_dev);
  * gmg_net_train_step into params_dev / grads_dev. */
 int gmg_net_get_params(gmg_net* net, float* params_dev);
 int gmg_net_get_grads(gmg_net* net, float* grads_dev);
+
+/* Selects the arithmetic of the forward stride-1 convolutions (inference and
+ * the forward pass of training; the stride-2 layers and every backward pass
+ * stay on the FP32 path).  GMG_NET_TF32 runs them as implicit GEMMs on the
+ * tensor cores (tcgen05.mma kind::tf32, FP32 accumulation in TMEM, operands
+ * staged by TMA): the activations lose their 13 low mantissa bits inside the
+ * product, so outputs differ from GMG_NET_FP32 by ~1e-3 relative.
+ * Synchronises the network's stream; captured training graphs are rebuilt
+ * on the next step. */
+int gmg_net_set_arith(gmg_net* net, int arith);
+
+/* Synchronous check of the sticky error word of the tensor-core kernels
+ * (a bounded wait for operands that gave up): GMG_OK or GMG_ERR_CUDA. */
+int gmg_net_status(gmg_net* net);
 
 /* g_dev[B][n_nodes][3] = network(x_dev[B][n_nodes][12]) on the grid nx x ny x nz
  * (multiples of 8, each >= 8).  Errors: GMG_ERR_ARG, GMG_ERR_NOMEM, GMG_ERR_CUDA. */

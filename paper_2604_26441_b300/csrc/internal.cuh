@@ -185,6 +185,10 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 // rejects the geometry (e.g. an address that is not 16-byte aligned).
 bool encode_f32_map(CUtensorMap* map, const float* base, int rank, const unsigned long long* dims,
                     const unsigned* box);
+// Host: tiled tensor map of an FP32 array of rank 1..5 with explicit byte
+// strides of dimensions 1..rank-1 (multiples of 16); out-of-range boxes read 0.
+bool encode_f32_map_strided(CUtensorMap* map, const float* base, int rank, const unsigned long long* dims,
+                            const unsigned long long* strides, const unsigned* box);
 
 }  // namespace gmg
 

@@ -41,6 +41,11 @@
 namespace {
 
 using gmg::note_launch;
+using gmg::smem_u32;
+using gmg::mbar_init;
+using gmg::mbar_fence_init;
+using gmg::mbar_expect_tx;
+using gmg::mbar_try_wait;
 
 constexpr float kSlope = 0.1f;
 constexpr double kBeta1 = 0.9, kBeta2 = 0.999, kAdamEps = 1e-8;
@@ -903,6 +908,262 @@ __global__ void k_ws_scale(const float* __restrict__ g, long long n, const doubl
     u0[i] = alpha[0] * (double)g[i];
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core convolution, stride 1: implicit GEMM on tcgen05 (kind::tf32,
+// FP32 accumulation in TMEM).  A CTA owns an 8 (x) x 16 (y) x 1 (z) tile of
+// output nodes = M 128 and NB output channels.  Per chunk of 8 input channels
+// TMA brings the input halo (10 x 18 x 3 nodes) as two 4-channel slabs laid
+// out [z][y][x][4]: eight x-consecutive nodes are one 8-row x 16-byte core
+// matrix, the next y row the next 8-row group (160 bytes on), the second slab
+// (8,704 bytes on) the next 4 channels of K -- so the A operand of each of the 27 taps is the
+// same halo seen through a shifted descriptor, and the halo is loaded once per
+// chunk instead of once per tap.  The weights of the chunk (all taps, laid out
+// by k_tc_image in the same K-major core-matrix form) come with one bulk copy.
+// One thread streams the chunks through two stages and issues the 27 MMAs per
+// chunk; all four warps then read the accumulator rows (one output node per
+// thread) and apply bias, activation / derivative and the store.  The
+// activations stay FP32 in memory; the MMA reads them as TF32, and the
+// weights are bfloat16-valued, hence exact in TF32.
+// ---------------------------------------------------------------------------
+constexpr int kTcHX = 10, kTcHY = 18, kTcHZ = 3;  // halo of an 8 x 16 x 1 output tile
+constexpr unsigned kTcSlab = kTcHX * kTcHY * kTcHZ * 16;  // bytes of one 4-channel slab (one TMA box)
+constexpr unsigned kTcSlabPitch = (kTcSlab + 127u) & ~127u;  // its stride in shared memory (128-byte aligned)
+constexpr unsigned kTcSpinW = 1u << 20;
+
+template <int NB>
+struct TcGeom {
+    static constexpr unsigned W = 27u * 32u * NB;             // weight bytes of one 8-channel chunk
+    static constexpr unsigned STAGE = 2u * kTcSlabPitch + W;  // bytes of one pipeline stage
+    static constexpr unsigned TX = 2u * kTcSlab + W;          // bytes the stage's copies deliver
+    static constexpr unsigned SMEM = 2u * STAGE + 1024u;
+    static constexpr unsigned COLS = NB < 32 ? 32u : (unsigned)NB;
+};
+
+struct TcConvArgs {
+    float* out;
+    int out_pitch, cout;      // channels written: [0, cout)
+    const float* img;         // weight image [nblk][nch][27][2][NB/8][8][4]
+    const float* bias;
+    const float* ref;
+    int ref_pitch;
+    int mode, accumulate;     // as ConvArgs
+    int X, Y, Z;
+    int nch;                  // 8-channel chunks of the input
+    long long out_bs, ref_bs;
+    int* err;
+};
+
+__device__ __forceinline__ uint64_t tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    // K-major, no swizzle: lbo = byte distance of K-adjacent core matrices,
+    // sbo = byte distance of adjacent 8-row groups
+    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(unsigned addr, float* v) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUtensorMap tm, TcConvArgs a) {
+    using Gm = TcGeom<NB>;
+    extern __shared__ unsigned char dyn_raw[];
+    __shared__ __align__(8) uint64_t full[2], empty[2], done;
+    __shared__ unsigned tslot;
+    __shared__ int fail_flag;
+    unsigned char* dyn = dyn_raw + ((1024u - (smem_u32(dyn_raw) & 1023u)) & 1023u);  // 1 KB aligned
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = (a.X + 7) >> 3, nty = (a.Y + 15) >> 4;
+    int t = blockIdx.x;
+    const int bx = t % ntx;
+    t /= ntx;
+    const int by = t % nty, z = t / nty;
+    const int x0 = bx * 8, y0 = by * 16;
+    const int nblk = blockIdx.y, b = blockIdx.z;
+    if (tid == 0) {
+        fail_flag = 0;
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], 1);
+        mbar_init(&empty[1], 1);
+        mbar_init(&done, 1);
+        mbar_fence_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                     "r"(Gm::COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tslot;
+
+    if (tid == 0) {
+        const unsigned base = smem_u32(dyn);
+        const float* img = a.img + (size_t)nblk * a.nch * (Gm::W / 4);
+        auto wait = [&](uint64_t* bar, unsigned par) -> bool {
+            for (unsigned it = 0; it < kTcSpinW; ++it)
+                if (mbar_try_wait(bar, par)) return true;
+            return false;
+        };
+        auto load = [&](int c, int st) {
+            unsigned char* sp = dyn + st * Gm::STAGE;
+            mbar_expect_tx(&full[st], Gm::TX);
+            tma_load_5d(sp, &tm, 8 * c, x0 - 1, y0 - 1, z - 1, b, &full[st]);
+            tma_load_5d(sp + kTcSlabPitch, &tm, 8 * c + 4, x0 - 1, y0 - 1, z - 1, b, &full[st]);
+            bulk_load(sp + 2 * kTcSlabPitch, img + (size_t)c * (Gm::W / 4), Gm::W, &full[st]);
+        };
+        constexpr unsigned idesc =
+            (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(NB >> 3) << 17) | ((128u >> 4) << 24);
+        bool ok = true;
+        int loaded = 0, consumed = 0;
+        load(0, 0);
+        loaded = 1;
+        if (a.nch > 1) {
+            load(1, 1);
+            loaded = 2;
+        }
+        for (int c = 0; c < a.nch; ++c) {
+            const int st = c & 1;
+            if (!wait(&full[st], (c >> 1) & 1)) {
+                ok = false;
+                break;
+            }
+            consumed = c + 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned ab = base + st * Gm::STAGE, wb = ab + 2 * kTcSlabPitch;
+#pragma unroll 1
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+                const uint64_t da = tc_desc(ab + ((dz * kTcHY + dy) * kTcHX + dx) * 16, kTcSlabPitch, kTcHX * 16);
+                const uint64_t db = tc_desc(wb + tap * 32 * NB, 16 * NB, 128);
+                const unsigned acc = (c > 0 || tap > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[st]))
+                         : "memory");
+            if (c + 2 < a.nch) {
+                if (!wait(&empty[st], (c >> 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                load(c + 2, st);
+                loaded = c + 3;
+            }
+        }
+        // all MMAs issued so far, then every load still in flight, must finish
+        // before the shared memory and TMEM are given up
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&done))
+                     : "memory");
+        if (!wait(&done, 0)) ok = false;
+        for (int c = consumed; c < loaded; ++c)
+            if (!wait(&full[c & 1], (c >> 1) & 1)) ok = false;
+        if (!ok) {
+            fail_flag = 1;
+            atomicExch(a.err, 1);
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!fail_flag) {
+        float v[NB];
+        const unsigned row = tmem + ((unsigned)(32 * warp) << 16);
+#pragma unroll
+        for (int c = 0; c < NB; c += 16) tmem_ld16(row + c, v + c);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int m = 32 * warp + lane;
+        const int x = x0 + (m & 7), y = y0 + (m >> 3);
+        const int co0 = nblk * NB;
+        if (x < a.X && y < a.Y) {
+            const long long node = (long long)(z * a.Y + y) * a.X + x;
+            float* o = a.out + b * a.out_bs + node * a.out_pitch + co0;
+            const float* r = a.ref ? a.ref + b * a.ref_bs + node * a.ref_pitch + co0 : nullptr;
+            const int nc = min(NB, a.cout - co0);
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                if (j >= nc) break;
+                float val = v[j];
+                if (a.bias) val += a.bias[co0 + j];
+                if (a.accumulate) val += o[j];
+                if (a.mode == 1) val = val > 0.f ? val : kSlope * val;
+                else if (a.mode == 2) val *= r[j] > 0.f ? 1.f : kSlope;
+                o[j] = val;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Gm::COLS) : "memory");
+}
+
+// Weight image of one stride-1 layer for k_conv_tc.  Forward (flip = 0): the
+// GEMM's output channel is the layer's co and its K channel the layer's ci;
+// backward data (flip = 1): output channel = ci, K channel = co, tap mirrored.
+// img[nblk][nch][tap][kh][ng][r][q] = W[co][tap'][ci] with the GEMM output
+// channel nblk NB + 8 ng + r and K channel 8 c + 4 kh + q (0 outside).
+__global__ void k_tc_image(const float* __restrict__ W, int cin, int coutp, int flip, int NB, int nblk, int nch,
+                           float* __restrict__ img) {
+    const long long n = (long long)nblk * nch * 27 * NB * 8;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long r = i;
+    const int q = (int)(r % 4);
+    r /= 4;
+    const int rr = (int)(r % 8);
+    r /= 8;
+    const int ng = (int)(r % (NB / 8));
+    r /= NB / 8;
+    const int kh = (int)(r % 2);
+    r /= 2;
+    const int tap = (int)(r % 27);
+    r /= 27;
+    const int c = (int)(r % nch);
+    const int blk = (int)(r / nch);
+    const int gout = blk * NB + 8 * ng + rr;  // GEMM output channel
+    const int gk = 8 * c + 4 * kh + q;        // GEMM K channel
+    float v = 0.f;
+    if (!flip) {
+        if (gout < coutp && gk < cin) v = W[((long long)gout * 27 + tap) * cin + gk];
+    } else {
+        if (gout < cin && gk < coutp) v = W[((long long)gk * 27 + (26 - tap)) * cin + gout];
+    }
+    img[i] = v;
+}
+
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -956,6 +1217,12 @@ struct gmg_net {
     float* loss = nullptr;
     std::vector<Work*> works;
     std::vector<void*> allocs;
+    // tensor-core (TF32) stride-1 convolutions: per layer and direction
+    // (0 forward, 1 backward data) the weight image and its GEMM blocking
+    int arith = GMG_NET_FP32;
+    float* img[kLayers][2] = {};
+    int img_nb[kLayers][2] = {}, img_nblk[kLayers][2] = {}, img_nch[kLayers][2] = {};
+    int* kerr = nullptr;  // sticky error word of the tensor-core kernels
     // warm start scratch
     float *ws_g = nullptr, *ws_kg = nullptr, *ws_x = nullptr;
     long long ws_cap = 0;
@@ -1003,6 +1270,94 @@ LayerTable make_table(long long* total) {
     }
     *total = k;
     return T;
+}
+
+// ---- tensor-core convolution (stride 1)
+
+int tc_nb(int cout) { return cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16); }
+
+template <int NB>
+int tc_attr() {
+    CU(cudaFuncSetAttribute(k_conv_tc<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcGeom<NB>::SMEM));
+    return GMG_OK;
+}
+
+// Allocates the forward weight image of every stride-1 layer with its GEMM
+// blocking.  (k_tc_image also lays out the backward-data form, flip = 1; the
+// backward passes stay on the FP32 path: TF32 gradients lose ~8 % relative
+// accuracy on the first layer after eleven layers of cancellation.)
+int alloc_images(gmg_net* net) {
+    TRY(tc_attr<16>());
+    TRY(tc_attr<32>());
+    TRY(tc_attr<64>());
+    for (int l = 0; l < kLayers; ++l) {
+        if (kDefs[l].stride != 1) continue;
+        for (int dir = 0; dir < 1; ++dir) {
+            const int gout = dir == 0 ? net->T.coutp[l] : kDefs[l].cin;  // GEMM output channels
+            const int gk = dir == 0 ? kDefs[l].cin : net->T.coutp[l];    // GEMM K channels
+            const int nb = tc_nb(gout);
+            net->img_nb[l][dir] = nb;
+            net->img_nblk[l][dir] = (gout + nb - 1) / nb;
+            net->img_nch[l][dir] = (gk + 7) / 8;
+            const long long n = (long long)net->img_nblk[l][dir] * net->img_nch[l][dir] * 27 * nb * 8;
+            TRY(dalloc(net->allocs, &net->img[l][dir], n));
+        }
+    }
+    return GMG_OK;
+}
+
+// Rebuilds every weight image from the rounded weights Wr.
+int build_images(gmg_net* net, cudaStream_t s) {
+    for (int l = 0; l < kLayers; ++l)
+        for (int dir = 0; dir < 2; ++dir) {
+            if (!net->img[l][dir]) continue;
+            const int nb = net->img_nb[l][dir], nblk = net->img_nblk[l][dir], nch = net->img_nch[l][dir];
+            const long long n = (long long)nblk * nch * 27 * nb * 8;
+            k_tc_image<<<blocks_for(n, 256), 256, 0, s>>>(net->Wr + net->T.woff[l], kDefs[l].cin, net->T.coutp[l], dir,
+                                                          nb, nblk, nch, net->img[l][dir]);
+            note_launch();
+        }
+    return GMG_OK;
+}
+
+// Launches k_conv_tc for layer l in direction dir; returns 1 (nothing
+// launched) when the input cannot be described by a tensor map.
+int launch_conv_tc(gmg_net* net, int l, int dir, const float* in, int in_pitch, int cin, long long in_bs, int X, int Y,
+                   int Z, int B, float* out, int out_pitch, int cout, long long out_bs, const float* bias,
+                   const float* ref, int ref_pitch, long long ref_bs, int mode, int accumulate, cudaStream_t s) {
+    CUtensorMap tm;
+    const unsigned long long dims[5] = {(unsigned long long)cin, (unsigned long long)X, (unsigned long long)Y,
+                                        (unsigned long long)Z, (unsigned long long)B};
+    const unsigned long long st[4] = {4ULL * in_pitch, 4ULL * in_pitch * X, 4ULL * in_pitch * X * Y,
+                                      4ULL * (unsigned long long)in_bs};
+    const unsigned box[5] = {4, kTcHX, kTcHY, kTcHZ, 1};
+    if (!gmg::encode_f32_map_strided(&tm, in, 5, dims, st, box)) return 1;
+    TcConvArgs a{};
+    a.out = out;
+    a.out_pitch = out_pitch;
+    a.cout = cout;
+    a.img = net->img[l][dir];
+    a.bias = bias;
+    a.ref = ref;
+    a.ref_pitch = ref_pitch;
+    a.mode = mode;
+    a.accumulate = accumulate;
+    a.X = X;
+    a.Y = Y;
+    a.Z = Z;
+    a.nch = net->img_nch[l][dir];
+    a.out_bs = out_bs;
+    a.ref_bs = ref_bs;
+    a.err = net->kerr;
+    const int nb = net->img_nb[l][dir];
+    dim3 grid((unsigned)(((X + 7) / 8) * ((Y + 15) / 16) * Z), (unsigned)net->img_nblk[l][dir], (unsigned)B);
+    switch (nb) {
+        case 16: k_conv_tc<16><<<grid, 128, TcGeom<16>::SMEM, s>>>(tm, a); break;
+        case 32: k_conv_tc<32><<<grid, 128, TcGeom<32>::SMEM, s>>>(tm, a); break;
+        default: k_conv_tc<64><<<grid, 128, TcGeom<64>::SMEM, s>>>(tm, a); break;
+    }
+    note_launch();
+    return GMG_OK;
 }
 
 // ---- convolution launchers
@@ -1076,6 +1431,11 @@ int conv_fwd(gmg_net* net, int l, const float* in, int in_pitch, long long in_bs
     a.Zo = d.stride == 1 ? Z : (Z - 1) / 2 + 1;
     a.in_bs = in_bs;
     a.out_bs = out_bs;
+    if (net->arith == GMG_NET_TF32 && d.stride == 1) {
+        const int rc = launch_conv_tc(net, l, 0, in, in_pitch, d.cin, in_bs, X, Y, Z, B, out, out_pitch, cout, out_bs,
+                                      a.bias, nullptr, 0, 0, a.mode, 0, s);
+        if (rc != 1) return rc;
+    }
     return launch_conv(a, d.stride, B, s);
 }
 
@@ -1430,14 +1790,25 @@ int train_kernels(gmg_net* net, Work* w, bool energy, cudaStream_t s) {
     k_adam<<<blocks_for(net->n_int, 256), 256, 0, s>>>(net->T, net->n_int, net->P, net->M, net->V, net->G, net->Wr,
                                                        net->Wf, net->Wb, net->adam, net->lr);
     note_launch(3);
+    if (net->arith == GMG_NET_TF32) TRY(build_images(net, s));
     return GMG_OK;
 }
 
 int round_all(gmg_net* net) {
     k_round_all<<<blocks_for(net->n_int, 256), 256, 0, net->stream>>>(net->T, net->n_int, net->P, net->Wr, net->Wf, net->Wb);
     note_launch();
+    TRY(build_images(net, net->stream));
     CU(cudaGetLastError());
     return GMG_OK;
+}
+
+// Destroys the captured train-step graphs (they depend on the arithmetic).
+void drop_graphs(gmg_net* net) {
+    for (Work* w : net->works) {
+        if (w->exec) cudaGraphExecDestroy(w->exec);
+        if (w->exec_energy) cudaGraphExecDestroy(w->exec_energy);
+        w->exec = w->exec_energy = nullptr;
+    }
 }
 
 int api_to_internal(gmg_net* net, const float* params) {
@@ -1506,6 +1877,9 @@ int gmg_net_create(gmg_net** out, const float* params, void* stream) {
     chain(dalloc(net->allocs, &net->lr, 4));  // lr, clip
     chain(dalloc(net->allocs, &net->loss, 4));
     chain(dalloc(net->allocs, &net->ws_red, 4 * kRedBlocks));
+    chain(dalloc(net->allocs, &net->kerr, 4));
+    if (rc == GMG_OK) rc = alloc_images(net);
+    if (rc == GMG_OK && cudaMemsetAsync(net->kerr, 0, 16, net->stream) != cudaSuccess) rc = GMG_ERR_CUDA;
     chain(dalloc(net->allocs, &net->ws_alpha, 8));
     if (rc == GMG_OK) rc = conv_attrs();
     if (rc == GMG_OK) rc = api_to_internal(net, params);
@@ -1535,6 +1909,25 @@ int gmg_net_get_params(gmg_net* net, float* params) {
 int gmg_net_get_grads(gmg_net* net, float* grads) {
     if (!net || !grads) return fail(GMG_ERR_ARG, "null argument");
     return internal_to_api(net, net->G, grads);
+}
+
+int gmg_net_set_arith(gmg_net* net, int arith) {
+    if (!net || (arith != GMG_NET_FP32 && arith != GMG_NET_TF32)) return fail(GMG_ERR_ARG, "bad arithmetic mode");
+    if (arith != net->arith) {
+        CU(cudaStreamSynchronize(net->stream));
+        drop_graphs(net);
+        net->arith = arith;
+    }
+    return GMG_OK;
+}
+
+int gmg_net_status(gmg_net* net) {
+    if (!net) return fail(GMG_ERR_ARG, "null argument");
+    int e = 0;
+    CU(cudaMemcpyAsync(&e, net->kerr, sizeof(int), cudaMemcpyDeviceToHost, net->stream));
+    CU(cudaStreamSynchronize(net->stream));
+    if (e) return fail(GMG_ERR_CUDA, "a tensor-core convolution gave up waiting for its operands");
+    return GMG_OK;
 }
 
 int gmg_net_forward(gmg_net* net, int nx, int ny, int nz, int batch, const float* x, float* g) {

@@ -110,6 +110,8 @@ _SIGS = {
     "gmg_net_target": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "gmg_warm_start": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gmg_net_destroy": (None, [_P]),
+    "gmg_net_set_arith": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gmg_net_status": (ctypes.c_int, [_P]),
 }
 
 
@@ -439,6 +441,7 @@ def solve_batch(solvers, fs, us=None, tol: float = 1e-6, maxit: int = 200):
 # ---------------------------------------------------------------- learned warm start
 
 NET_IN, NET_OUT, NET_LAYERS = 12, 3, 12
+NET_ARITH = {"fp32": 0, "tf32": 1}
 
 
 def net_num_params() -> int:
@@ -512,6 +515,14 @@ class WarmNet:
             self.close()
         except Exception:
             pass
+
+    def set_arith(self, arith: str):
+        """'fp32' (CUDA-core convolutions) or 'tf32' (tensor-core stride-1 convolutions)."""
+        _check(self._lib.gmg_net_set_arith(self._h, NET_ARITH[arith]))
+
+    def status(self):
+        """Raises if a tensor-core kernel gave up waiting for its operands."""
+        _check(self._lib.gmg_net_status(self._h))
 
     def set_params(self, params):
         import torch

@@ -5,6 +5,9 @@
     python -m paper_2604_26441_b300.profile_cases smooth-c2   # set-up + 3 fine smoothing passes
     python -m paper_2604_26441_b300.profile_cases apply-c2    # set-up + 5 fine operator applies
     python -m paper_2604_26441_b300.profile_cases smooth-c2-bf16x3  # fine smoothing, tensor-core contraction
+    python -m paper_2604_26441_b300.profile_cases warmstart-80  # 80^3 set-up, one learned warm start + solve
+    python -m paper_2604_26441_b300.profile_cases warmstart-80-tf32  # the same with tensor-core convolutions
+    python -m paper_2604_26441_b300.profile_cases train-48      # 48^3 set-up, 3 energy-loss train steps (batch 4)
 
 Each case prints the library's kernel-launch counter after set-up, so that
 ``ncu -s`` can skip the set-up kernels.  The solve normally runs its PCG
@@ -58,6 +61,8 @@ def main(case: str) -> None:
 
     from paper_2604_26441_b300 import gmg, inputs
 
+    if case in ("warmstart-80", "warmstart-80-tf32", "train-48"):
+        return net_case(case)
     cfg = inputs.CONFIGS["c2"]
     fine = "bf16x3" if case.endswith("-bf16x3") else "fp32"
     S = gmg.Solver(torch.from_numpy(cfg.rho()).cuda(), p=cfg.p,
@@ -80,6 +85,38 @@ def main(case: str) -> None:
         torch.cuda.synchronize()
     else:
         raise SystemExit(f"unknown case {case}")
+    print("total launches", gmg.kernel_launches(), flush=True)
+
+
+def net_case(case: str) -> None:
+    """The learned warm start with seeded (untrained) parameters: the kernels
+    and their costs do not depend on the parameter values."""
+    import torch
+
+    from paper_2604_26441_b300 import gmg, inputs, warmstart as ws
+
+    n = 80 if case.startswith("warmstart-80") else 48
+    rho = torch.from_numpy(inputs.filtered_random_density(n, n, n, 4242)).cuda()
+    fixed = torch.from_numpy(inputs.clamp_xmin_mask(n, n, n)).cuda()
+    S = gmg.Solver(rho, p=3.0, opts=ws.solver_options())
+    net = gmg.WarmNet(ws.initial_params(0))
+    if case.endswith("-tf32"):
+        net.set_arith("tf32")
+    fs = [torch.from_numpy(inputs.rotated_tip_edge_load(n, n, n, k)).cuda() for k in range(4)]
+    if case == "train-48":
+        xs = [gmg.net_features((n, n, n), rho, f, fixed) for f in fs]
+        ts = [gmg.net_target((n, n, n), S.solve(f)[0]) for f in fs]
+    torch.cuda.synchronize()
+    print("setup launches", gmg.kernel_launches(), flush=True)
+    if case.startswith("warmstart-80"):
+        u0, alpha = net.warm_start(S, rho, fs[0])
+        net.status()
+        _, info = S.solve(fs[0], u0)
+        print("alpha", alpha, info, flush=True)
+    else:
+        for _ in range(3):
+            net.train_step((n, n, n), xs, ts, 1e-4, clip=1.0, ops=[S] * 4)
+    torch.cuda.synchronize()
     print("total launches", gmg.kernel_launches(), flush=True)
 
 

@@ -192,6 +192,64 @@ def test_energy_loss_step_matches_oracle(dims):
     assert float(loss.item()) > 0
 
 
+# TF32 keeps 10 of the activations' 23 mantissa bits inside the tensor-core
+# products (relative error < 2^-10 per product, biased toward zero); over the
+# network's 12 layers this is held to 1e-2 relative L2 for outputs, and to
+# 3e-2 for the per-layer gradients (FP32 backward passes through activations
+# that the TF32 forward pass computed).  The weights are bfloat16-valued, hence
+# exact in TF32.
+@pytest.mark.parametrize("dims", [(8, 8, 8), (16, 24, 8), (32, 16, 24)])
+def test_tensor_core_forward_matches_oracle(dims):
+    from paper_2604_26441_b300 import gmg
+    nx, ny, nz = dims
+    theta = _theta(8)
+    net = gmg.WarmNet(_t(theta))
+    xs = []
+    for s_ in (61, 62):
+        rho, fixed, f = _problem(nx, ny, nz, s_, k_load=s_ % 16)
+        xs.append(W.node_features(nx, ny, nz, rho, f, fixed))
+    xb = _t(np.stack([x.reshape(-1, W.N_IN) for x in xs]))
+    g32 = net.forward(dims, xb).cpu().numpy()
+    net.set_arith("tf32")
+    g = net.forward(dims, xb).cpu().numpy()
+    net.status()
+    for b, x in enumerate(xs):
+        ref, _ = W.forward(theta.astype(np.float64), x)
+        assert rel_l2(g[b], ref.reshape(-1, 3)) < 1e-2, b
+        assert rel_l2(g[b], g32[b]) < 1e-2, b
+    assert not np.array_equal(g, g32)  # the tensor-core path did run
+    g2 = net.forward(dims, xb).cpu().numpy()
+    assert np.array_equal(g, g2)
+
+
+@pytest.mark.parametrize("dims", [(16, 24, 8), (32, 32, 32)])
+def test_tensor_core_train_step_matches_oracle(dims):
+    """Mean-squared-error loss: its gradient is well conditioned, so it shows
+    the TF32 forward pass's effect on every layer's gradient.  (The energy
+    loss's gradient is proportional to t.K g, which nearly cancels for an
+    untrained network -- L ~ 0.9999 -- so there a 1e-3 change of the output
+    moves the gradient by a few per cent on every layer, with the FP32 path
+    still matching the oracle to 1e-5.)"""
+    from paper_2604_26441_b300 import gmg
+    theta = _theta(9)
+    batch = _oracle_batch(dims, (71, 72))
+    net = gmg.WarmNet(_t(theta))
+    net.set_arith("tf32")
+    loss = torch.zeros(1, device="cuda")
+    net.train_step(dims, [_t(x.reshape(-1, W.N_IN)) for x, _ in batch], [_t(t.reshape(-1, 3)) for _, t in batch],
+                   0.0, loss)
+    net.status()
+    g_gpu = net.grads().cpu().numpy().astype(np.float64)
+    th = theta.astype(np.float64)
+    loss_ref, g_ref, _, _, _ = W.train_step(th, np.zeros_like(th), np.zeros_like(th), 1, 0.0, batch)
+    assert abs(float(loss.item()) - loss_ref) <= 1e-2 * loss_ref
+    k = 0
+    for name, ci, co, _, _ in W.LAYERS:
+        n = co * 27 * ci + co
+        assert rel_l2(g_gpu[k:k + n], g_ref[k:k + n]) < 3e-2, name
+        k += n
+
+
 def test_train_steps_are_bitwise_reproducible():
     from paper_2604_26441_b300 import gmg
     dims = (16, 8, 8)
@@ -246,6 +304,13 @@ def test_warm_start_matches_oracle(dims):
     uc, ic = S.solve(_t(f, torch.float64), None, tol=1e-8, maxit=200)
     assert iw["status"] == 0 and ic["status"] == 0
     assert rel_l2(uw.cpu().numpy(), uc.cpu().numpy()) < 1e-6
+    # the tensor-core network gives the same warm start to TF32 accuracy
+    net.set_arith("tf32")
+    u0t, alphat = net.warm_start(S, _t(rho), _t(f, torch.float64))
+    net.status()
+    if alpha_ref != 0.0:
+        assert alphat == pytest.approx(alpha_ref, rel=2e-2)
+        assert rel_l2(u0t.cpu().numpy(), u0_ref) < 2e-2
 
 
 def test_trained_network_gains_over_cold_start():
