@@ -94,6 +94,8 @@ struct ConvArgs {
     int accumulate;           // add the previous content of out
     int X, Y, Z, Xo, Yo, Zo;  // input / output vertex grids
     long long in_bs, out_bs, ref_bs;  // per-sample strides (floats)
+    int ci_hi;                // input channels of this launch's split: [blockIdx.z / B * (ci_hi), ...) -- see k_conv
+    long long split_bs;       // output stride between input-channel splits (floats)
 };
 
 __device__ __forceinline__ float epilogue(float v, const ConvArgs& a, const float* o, long long ridx, int mode) {
@@ -131,7 +133,10 @@ __global__ void __launch_bounds__(ConvGeom<COB, TY, TZ, S>::NT) k_conv(ConvArgs 
     const int by = t % nty, bz = t / nty;
     const int ox0 = bx * G::TX, oy0 = by * TY, oz0 = bz * TZ;
     const int cob0 = blockIdx.y * COB;
-    const int b = blockIdx.z;
+    // blockIdx.z = split * B + b: split k sums input channels [k ci_hi, (k+1) ci_hi)
+    // into its own output slice (split_bs apart); ci_hi = cin without a split
+    const int nb = a.split_bs ? (int)(gridDim.z / (a.cin / a.ci_hi)) : (int)gridDim.z;
+    const int b = blockIdx.z % nb, split = blockIdx.z / nb;
     const float* in = a.in + b * a.in_bs;
     const int ix0 = S * ox0 - 1, iy0 = S * oy0 - 1, iz0 = S * oz0 - 1;
 
@@ -141,7 +146,8 @@ __global__ void __launch_bounds__(ConvGeom<COB, TY, TZ, S>::NT) k_conv(ConvArgs 
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
 
-    for (int ci0 = 0; ci0 < a.cin; ci0 += G::KC) {
+    const int ci_begin = split * a.ci_hi, ci_end = ci_begin + a.ci_hi;
+    for (int ci0 = ci_begin; ci0 < ci_end; ci0 += G::KC) {
         __syncthreads();
         for (int h = tid; h < G::HZ * G::HY * G::HX; h += G::NT) {
             const int hx = h % G::HX;
@@ -208,7 +214,7 @@ __global__ void __launch_bounds__(ConvGeom<COB, TY, TZ, S>::NT) k_conv(ConvArgs 
         const int ox = ox0 + i;
         if (ox >= a.Xo) break;
         const long long node = (long long)(oz * a.Yo + oy) * a.Xo + ox;
-        float* o = a.out + b * a.out_bs + node * a.out_pitch + co;
+        float* o = a.out + split * a.split_bs + b * a.out_bs + node * a.out_pitch + co;
         if (vec) {
             float4 r;
             r.x = epilogue(acc[i][0] + bv[0], a, o, 0, a.mode);
@@ -407,6 +413,23 @@ __global__ void __launch_bounds__(256) k_wgrad(WgArgs a) {
         for (int j = 0; j < 4; ++j) p[(long long)a.coutp * 27 * a.cin + 4 * co4 + j] = bacc[j];
 }
 
+// Input-channel splits of a convolution: out[node][co] = act(bias + sum over
+// splits of part[k][node][co]) in split order (part has pitch cout).
+__global__ void k_split_sum(const float* __restrict__ part, int splits, long long split_bs, long long nodes, int cout,
+                            const float* __restrict__ bias, int act, float* __restrict__ out, int out_pitch,
+                            long long out_bs, long long nodes_per_sample) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= nodes * cout) return;
+    const long long n = i / cout;
+    const int co = (int)(i % cout);
+    float v = 0.f;
+    for (int k = 0; k < splits; ++k) v += part[k * split_bs + i];
+    v += bias[co];
+    if (act) v = v > 0.f ? v : kSlope * v;
+    const long long b = n / nodes_per_sample, nl = n % nodes_per_sample;
+    out[b * out_bs + nl * out_pitch + co] = v;
+}
+
 // out[i] = sum_s part[s * stride + i] in split order.
 __global__ void k_sum_splits(const float* __restrict__ part, long long stride, int splits, long long n,
                              float* __restrict__ out) {
@@ -505,6 +528,30 @@ __global__ void k_upsample_adj(const float* __restrict__ g, int pg, float* __res
     *reinterpret_cast<float4*>(out + b * out_bs + node * po + 4 * c4) = s;
 }
 
+// Fixed-order reduction over the 256 threads of a block (sum, or max with
+// op = 1); every thread gets the result.  Deterministic: thread t first folds
+// partials t, t + 256, ... in order, then the tree has a fixed shape.
+template <int OP>
+__device__ double block_reduce256(double v) {
+    __shared__ double sh[256];
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) sh[t] = OP == 0 ? sh[t] + sh[t + w] : fmax(sh[t], sh[t + w]);
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double fold(const double* p, int n, int stride, int off, int op) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) v = op == 0 ? v + p[(long long)i * stride + off] : fmax(v, p[(long long)i * stride + off]);
+    return v;
+}
+
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 296;  // 2 x 148 SMs
 
@@ -524,11 +571,9 @@ __global__ void __launch_bounds__(kRedThreads) k_count_free(const float* __restr
 }
 
 // sc[slot] = scale * sum(partial[0..n))
-__global__ void k_finish_sum(const double* partial, int n, double scale, double* sc, int slot) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += partial[i];
-    sc[slot] = scale * s;
+__global__ void __launch_bounds__(256) k_finish_sum(const double* partial, int n, double scale, double* sc, int slot) {
+    const double s = block_reduce256<0>(fold(partial, n, 1, 0, 0));
+    if (threadIdx.x == 0) sc[slot] = scale * s;
 }
 
 // gg = 2 (g - t) mask / count on channels 0..2 (channel 3 = 0); partial sums of (g - t)^2 mask.
@@ -561,11 +606,9 @@ __global__ void __launch_bounds__(kRedThreads) k_loss(const float* __restrict__ 
 }
 
 // loss = sum(partial) / count, as float
-__global__ void k_loss_finish(const double* partial, int n, const double* sc, float* loss) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += partial[i];
-    *loss = sc[0] > 0.0 ? (float)(s / sc[0]) : 0.f;
+__global__ void __launch_bounds__(256) k_loss_finish(const double* partial, int n, const double* sc, float* loss) {
+    const double s = block_reduce256<0>(fold(partial, n, 1, 0, 0));
+    if (threadIdx.x == 0) *loss = sc[0] > 0.0 ? (float)(s / sc[0]) : 0.f;
 }
 
 // Energy loss, step 1: gm = g and tm = t on the free DOFs (0 on fixed ones)
@@ -613,16 +656,14 @@ __global__ void __launch_bounds__(kRedThreads) k_energy_dots(const float* __rest
 // Per sample: L_b = 1 - a^2 / (b c); dL/dg_b = coef[2b] K g + coef[2b+1] K t with
 // coef = (2a/(bc)) (a/b, -1) / B (zero, and L_b = 1, when b or c is not positive).
 // loss = mean of L_b.
-__global__ void k_energy_finish(const double* partial, int nb, int B, double* coef, float* loss) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(256) k_energy_finish(const double* partial, int nb, int B, double* coef, float* loss) {
     double L = 0.0;
     for (int s = 0; s < B; ++s) {
-        double a = 0.0, b = 0.0, c = 0.0;
-        for (int i = 0; i < nb; ++i) {
-            a += partial[((long long)s * nb + i) * 3];
-            b += partial[((long long)s * nb + i) * 3 + 1];
-            c += partial[((long long)s * nb + i) * 3 + 2];
-        }
+        const double* ps = partial + (long long)s * nb * 3;
+        const double a = block_reduce256<0>(fold(ps, nb, 3, 0, 0));
+        const double b = block_reduce256<0>(fold(ps, nb, 3, 1, 0));
+        const double c = block_reduce256<0>(fold(ps, nb, 3, 2, 0));
+        if (threadIdx.x != 0) continue;
         if (b > 0.0 && c > 0.0 && isfinite(a) && isfinite(b) && isfinite(c)) {
             L += 1.0 - a * a / (b * c);
             const double k = 2.0 * a / (b * c) / (double)B;
@@ -634,7 +675,7 @@ __global__ void k_energy_finish(const double* partial, int nb, int B, double* co
             coef[2 * s + 1] = 0.0;
         }
     }
-    *loss = (float)(L / (double)B);
+    if (threadIdx.x == 0) *loss = (float)(L / (double)B);
 }
 
 // gg[b][n][c] = coef[2b] Kg + coef[2b+1] Kt (pitch 4, channel 3 = 0)
@@ -675,14 +716,13 @@ __global__ void __launch_bounds__(kRedThreads) k_sumsq_f(const float* __restrict
 // Adam step counter, bias corrections and gradient scale: adam[0] = t,
 // adam[1] = 1/(1-b1^t), adam[2] = 1/(1-b2^t), adam[3] = min(1, clip/|g|)
 // (1 without clipping, 0 for a non-finite norm).
-__global__ void k_adam_tick(double* adam, const double* gnorm_partial, int nb, const float* clip) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(256) k_adam_tick(double* adam, const double* gnorm_partial, int nb, const float* clip) {
+    const double ss = block_reduce256<0>(fold(gnorm_partial, nb, 1, 0, 0));
+    if (threadIdx.x != 0) return;
     const double t = adam[0] + 1.0;
     adam[0] = t;
     adam[1] = 1.0 / (1.0 - pow(kBeta1, t));
     adam[2] = 1.0 / (1.0 - pow(kBeta2, t));
-    double ss = 0.0;
-    for (int i = 0; i < nb; ++i) ss += gnorm_partial[i];
     const double nrm = sqrt(ss);
     const double c = (double)clip[0];
     double scale = 1.0;
@@ -772,13 +812,11 @@ __global__ void __launch_bounds__(kRedThreads) k_load_stats(const double* __rest
 }
 
 // stats[0] = 1 / max|f| (0 for f = 0), stats[1..3] = sum(f) / |sum(f)| (0 when it vanishes)
-__global__ void k_load_stats_finish(const double* partial, int nb, double* stats) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double m = 0.0, s[3] = {0.0, 0.0, 0.0};
-    for (int i = 0; i < nb; ++i) {
-        m = fmax(m, partial[4 * i]);
-        for (int k = 0; k < 3; ++k) s[k] += partial[4 * i + 1 + k];
-    }
+__global__ void __launch_bounds__(256) k_load_stats_finish(const double* partial, int nb, double* stats) {
+    const double m = block_reduce256<1>(fold(partial, nb, 4, 0, 1));
+    double s[3];
+    for (int k = 0; k < 3; ++k) s[k] = block_reduce256<0>(fold(partial, nb, 4, 1 + k, 0));
+    if (threadIdx.x != 0) return;
     stats[0] = m > 0.0 ? 1.0 / m : 0.0;
     const double r = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
     for (int k = 0; k < 3; ++k) stats[1 + k] = r > 0.0 ? s[k] / r : 0.0;
@@ -841,11 +879,9 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_vec(const double* __rest
     if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
 }
 
-__global__ void k_finish_vec(const double* partial, int n, int kind, double* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s = kind == 0 ? fmax(s, partial[i]) : s + partial[i];
-    *out = s;
+__global__ void __launch_bounds__(256) k_finish_vec(const double* partial, int n, int kind, double* out) {
+    const double s = kind == 0 ? block_reduce256<1>(fold(partial, n, 1, 0, 1)) : block_reduce256<0>(fold(partial, n, 1, 0, 0));
+    if (threadIdx.x == 0) *out = s;
 }
 
 // t = u / sqrt(sumsq / n)   (0 when u = 0)
@@ -892,13 +928,10 @@ __global__ void __launch_bounds__(kRedThreads) k_ws_dots(const double* __restric
     }
 }
 
-__global__ void k_ws_alpha(const double* partial, int nb, double* alpha) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < nb; ++i) {
-        a += partial[2 * i];
-        b += partial[2 * i + 1];
-    }
+__global__ void __launch_bounds__(256) k_ws_alpha(const double* partial, int nb, double* alpha) {
+    const double a = block_reduce256<0>(fold(partial, nb, 2, 0, 0));
+    const double b = block_reduce256<0>(fold(partial, nb, 2, 1, 0));
+    if (threadIdx.x != 0) return;
     *alpha = (b > 0.0 && isfinite(a) && isfinite(b)) ? a / b : 0.0;
 }
 
@@ -1186,6 +1219,8 @@ struct Work {
           *g_cat2 = nullptr, *g_c3 = nullptr, *g_b3 = nullptr, *g_b2 = nullptr, *g_b1 = nullptr, *g_a0 = nullptr;
     float* part = nullptr;
     long long part_cap = 0;
+    float* split = nullptr;  // input-channel split partials of the stride-2 layers
+    long long split_cap = 0;
     double* red = nullptr;   // reduction partials (2 * kRedBlocks)
     double* sc = nullptr;    // [0] = loss DOF count, [1] = energy-loss gradient scale
     cudaGraphExec_t exec = nullptr;         // train step, mean squared error
@@ -1386,16 +1421,19 @@ template <int COB, int TY, int TZ, int S>
 int launch_conv_t(const ConvArgs& a, int B, cudaStream_t s) {
     using Gm = ConvGeom<COB, TY, TZ, S>;
     const unsigned tiles = (unsigned)(((a.Xo + 7) / 8) * ((a.Yo + TY - 1) / TY) * ((a.Zo + TZ - 1) / TZ));
-    dim3 grid(tiles, (unsigned)((a.cout + COB - 1) / COB), (unsigned)B);
+    const int splits = a.split_bs ? a.cin / a.ci_hi : 1;
+    dim3 grid(tiles, (unsigned)((a.cout + COB - 1) / COB), (unsigned)(B * splits));
     k_conv<COB, TY, TZ, S><<<grid, Gm::NT, Gm::SMEM, s>>>(a);
     note_launch();
     return GMG_OK;
 }
 
-int launch_conv(const ConvArgs& a, int S, int B, cudaStream_t s) {
+int launch_conv(ConvArgs a, int S, int B, cudaStream_t s) {
     if (a.cin % 4 || a.in_pitch % 4 || a.w_co % 4 || (reinterpret_cast<uintptr_t>(a.in) & 15) ||
         (reinterpret_cast<uintptr_t>(a.W) & 15))
         return fail(GMG_ERR_ARG, "conv: channel counts, pitches and pointers must be 16-byte aligned");
+    if (a.ci_hi <= 0) a.ci_hi = a.cin;
+    if (a.cin % a.ci_hi || a.ci_hi % 4) return fail(GMG_ERR_ARG, "conv: split must divide the input channels");
     const int c = a.cout;
     if (S == 1) {
         if (c % 64 == 0) return launch_conv_t<64, 4, 4, 1>(a, B, s);
@@ -1410,7 +1448,8 @@ int launch_conv(const ConvArgs& a, int S, int B, cudaStream_t s) {
 
 // out (cout channels) = act(conv(in) + bias) for layer l
 int conv_fwd(gmg_net* net, int l, const float* in, int in_pitch, long long in_bs, int X, int Y, int Z, float* out,
-             int out_pitch, int cout, long long out_bs, int B, cudaStream_t s) {
+             int out_pitch, int cout, long long out_bs, int B, cudaStream_t s, float* split = nullptr,
+             long long split_cap = 0) {
     const LayerDef& d = kDefs[l];
     ConvArgs a{};
     a.in = in;
@@ -1435,6 +1474,33 @@ int conv_fwd(gmg_net* net, int l, const float* in, int in_pitch, long long in_bs
         const int rc = launch_conv_tc(net, l, 0, in, in_pitch, d.cin, in_bs, X, Y, Z, B, out, out_pitch, cout, out_bs,
                                       a.bias, nullptr, 0, 0, a.mode, 0, s);
         if (rc != 1) return rc;
+    }
+    if (d.stride == 2 && split) {
+        // few output tiles (coarse levels): split the input channels over more
+        // blocks, then add the splits in order with bias and activation
+        const int cob = cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16);
+        const int ty = cob == 64 ? 4 : 8, tz = cob == 16 ? 8 : 4;
+        const long long blocks = (long long)((a.Xo + 7) / 8) * ((a.Yo + ty - 1) / ty) * ((a.Zo + tz - 1) / tz) *
+                                 ((cout + cob - 1) / cob) * B;
+        int splits = 1;
+        while (splits * 2 <= d.cin / 4 && blocks * splits < 2 * 148 && d.cin % (splits * 2 * 4) == 0) splits *= 2;
+        const long long no = (long long)a.Xo * a.Yo * a.Zo;
+        if (splits > 1 && (long long)splits * no * B * cout <= split_cap) {
+            ConvArgs p = a;
+            p.out = split;
+            p.out_pitch = cout;
+            p.out_bs = no * cout;
+            p.split_bs = no * B * cout;
+            p.ci_hi = d.cin / splits;
+            p.bias = nullptr;
+            p.mode = 0;
+            TRY(launch_conv(p, 2, B, s));
+            const long long n = no * B * cout;
+            k_split_sum<<<blocks_for(n, 256), 256, 0, s>>>(split, splits, p.split_bs, no * B, cout, a.bias, d.act, out,
+                                                           out_pitch, out_bs, no);
+            note_launch();
+            return GMG_OK;
+        }
     }
     return launch_conv(a, d.stride, B, s);
 }
@@ -1619,6 +1685,9 @@ int get_work(gmg_net* net, int nx, int ny, int nz, int B, bool train, Work** out
     chain(al(&w->y0, 16, 0));
     chain(al(&w->g, 4, 0));
     chain(dalloc(w->allocs, &w->red, 2 * kRedBlocks));
+    // split partials: at most 16 splits of the level-1..3 outputs of one stride-2 layer
+    w->split_cap = 16LL * w->N[1] * 32 * B;
+    chain(dalloc(w->allocs, &w->split, (size_t)w->split_cap));
     chain(dalloc(w->allocs, &w->sc, 4));
     if (train) {
         chain(al(&w->x0, GMG_NET_IN, 0));
@@ -1680,11 +1749,11 @@ int forward(gmg_net* net, Work* w, const float* x, float* g, int gp, int gc, cud
     const long long* N = w->N;
     TRY(conv_fwd(net, L_E0A, x, GMG_NET_IN, GMG_NET_IN * N[0], X[0], Y[0], Z[0], w->a0, 16, 16, 16 * N[0], B, s));
     TRY(conv_fwd(net, L_E0B, w->a0, 16, 16 * N[0], X[0], Y[0], Z[0], w->cat0 + 32, 48, 16, 48 * N[0], B, s));
-    TRY(conv_fwd(net, L_D1, w->cat0 + 32, 48, 48 * N[0], X[0], Y[0], Z[0], w->b1, 32, 32, 32 * N[1], B, s));
+    TRY(conv_fwd(net, L_D1, w->cat0 + 32, 48, 48 * N[0], X[0], Y[0], Z[0], w->b1, 32, 32, 32 * N[1], B, s, w->split, w->split_cap));
     TRY(conv_fwd(net, L_E1, w->b1, 32, 32 * N[1], X[1], Y[1], Z[1], w->cat1 + 64, 96, 32, 96 * N[1], B, s));
-    TRY(conv_fwd(net, L_D2, w->cat1 + 64, 96, 96 * N[1], X[1], Y[1], Z[1], w->b2, 64, 64, 64 * N[2], B, s));
+    TRY(conv_fwd(net, L_D2, w->cat1 + 64, 96, 96 * N[1], X[1], Y[1], Z[1], w->b2, 64, 64, 64 * N[2], B, s, w->split, w->split_cap));
     TRY(conv_fwd(net, L_E2, w->b2, 64, 64 * N[2], X[2], Y[2], Z[2], w->cat2 + 64, 128, 64, 128 * N[2], B, s));
-    TRY(conv_fwd(net, L_D3, w->cat2 + 64, 128, 128 * N[2], X[2], Y[2], Z[2], w->b3, 64, 64, 64 * N[3], B, s));
+    TRY(conv_fwd(net, L_D3, w->cat2 + 64, 128, 128 * N[2], X[2], Y[2], Z[2], w->b3, 64, 64, 64 * N[3], B, s, w->split, w->split_cap));
     TRY(conv_fwd(net, L_E3, w->b3, 64, 64 * N[3], X[3], Y[3], Z[3], w->c3, 64, 64, 64 * N[3], B, s));
     TRY(upsample(w->c3, 64, 64 * N[3], w->cat2, 128, 128 * N[2], 64, X[3], Y[3], Z[3], B, s));
     TRY(conv_fwd(net, L_U2, w->cat2, 128, 128 * N[2], X[2], Y[2], Z[2], w->y2, 64, 64, 64 * N[2], B, s));
@@ -1707,13 +1776,13 @@ int train_kernels(gmg_net* net, Work* w, bool energy, cudaStream_t s) {
     const long long nodes = N[0] * B;
     if (!energy) {
         k_count_free<<<kRedBlocks, kRedThreads, 0, s>>>(w->x0, nodes, w->red);
-        k_finish_sum<<<1, 32, 0, s>>>(w->red, kRedBlocks, 3.0, w->sc, 0);
+        k_finish_sum<<<1, 256, 0, s>>>(w->red, kRedBlocks, 3.0, w->sc, 0);
         note_launch(2);
     }
     TRY(forward(net, w, w->x0, w->g, 4, 4, s));
     if (!energy) {
         k_loss<<<kRedBlocks, kRedThreads, 0, s>>>(w->g, w->t, w->x0, nodes, w->sc, w->gg, w->red);
-        k_loss_finish<<<1, 32, 0, s>>>(w->red, kRedBlocks, w->sc, net->loss);
+        k_loss_finish<<<1, 256, 0, s>>>(w->red, kRedBlocks, w->sc, net->loss);
         note_launch(2);
     } else {
         const long long n3 = 3 * N[0];
@@ -1736,7 +1805,7 @@ int train_kernels(gmg_net* net, Work* w, bool energy, cudaStream_t s) {
             gmg::launch_fine(gmg::FM_APPLY, 0, 0, a, w->gh, s);
         }
         k_energy_dots<<<dim3(kEnergyBlocks, B), kRedThreads, 0, s>>>(w->gm, w->Kg, w->tm, w->Kt, n3, w->epart);
-        k_energy_finish<<<1, 32, 0, s>>>(w->epart, kEnergyBlocks, B, w->coef, net->loss);
+        k_energy_finish<<<1, 256, 0, s>>>(w->epart, kEnergyBlocks, B, w->coef, net->loss);
         k_energy_grad<<<blocks_for(nodes, 256), 256, 0, s>>>(w->Kg, w->Kt, N[0], B, w->coef, w->gg);
         note_launch(3);
     }
@@ -1786,7 +1855,7 @@ int train_kernels(gmg_net* net, Work* w, bool energy, cudaStream_t s) {
     TRY(wgrad(net, w, L_E0A, w->x0, GMG_NET_IN, GMG_NET_IN * N[0], X[0], Y[0], Z[0], w->g_a0, 16, 16 * N[0], s));
     // Adam
     k_sumsq_f<<<kRedBlocks, kRedThreads, 0, s>>>(net->G, net->n_int, w->red);
-    k_adam_tick<<<1, 32, 0, s>>>(net->adam, w->red, kRedBlocks, net->lr + 1);
+    k_adam_tick<<<1, 256, 0, s>>>(net->adam, w->red, kRedBlocks, net->lr + 1);
     k_adam<<<blocks_for(net->n_int, 256), 256, 0, s>>>(net->T, net->n_int, net->P, net->M, net->V, net->G, net->Wr,
                                                        net->Wf, net->Wb, net->adam, net->lr);
     note_launch(3);
@@ -2023,7 +2092,7 @@ int gmg_net_features(int nx, int ny, int nz, const float* rho, const double* f, 
     double* red = nullptr;
     CU(cudaMallocAsync(&red, sizeof(double) * (4 * kRedBlocks + 4), s));
     k_load_stats<<<kRedBlocks, kRedThreads, 0, s>>>(f, nn, red);
-    k_load_stats_finish<<<1, 32, 0, s>>>(red, kRedBlocks, red + 4 * kRedBlocks);
+    k_load_stats_finish<<<1, 256, 0, s>>>(red, kRedBlocks, red + 4 * kRedBlocks);
     k_features<<<blocks_for(nn, 256), 256, 0, s>>>(nx, ny, nz, rho, f, fixed, nullptr, red + 4 * kRedBlocks, x);
     note_launch(3);
     CU(cudaFreeAsync(red, s));
@@ -2039,7 +2108,7 @@ int gmg_net_target(int nx, int ny, int nz, const double* u, float* t, void* stre
     double* red = nullptr;
     CU(cudaMallocAsync(&red, sizeof(double) * (kRedBlocks + 1), s));
     k_reduce_vec<<<kRedBlocks, kRedThreads, 0, s>>>(u, n, 1, red);
-    k_finish_vec<<<1, 32, 0, s>>>(red, kRedBlocks, 1, red + kRedBlocks);
+    k_finish_vec<<<1, 256, 0, s>>>(red, kRedBlocks, 1, red + kRedBlocks);
     k_target<<<blocks_for(n, 256), 256, 0, s>>>(u, n, red + kRedBlocks, t);
     note_launch(3);
     CU(cudaFreeAsync(red, s));
@@ -2071,7 +2140,7 @@ int gmg_warm_start(gmg_handle* h, gmg_net* net, const float* rho, const double* 
     TRY(get_work(net, l0.nx, l0.ny, l0.nz, 1, false, &w));
     // features (mask bits of the handle)
     k_load_stats<<<kRedBlocks, kRedThreads, 0, s>>>(f, nn, net->ws_red);
-    k_load_stats_finish<<<1, 32, 0, s>>>(net->ws_red, kRedBlocks, net->ws_alpha + 1);
+    k_load_stats_finish<<<1, 256, 0, s>>>(net->ws_red, kRedBlocks, net->ws_alpha + 1);
     k_features<<<blocks_for(nn, 256), 256, 0, s>>>(l0.nx, l0.ny, l0.nz, rho, f, nullptr, l0.mask, net->ws_alpha + 1,
                                                    net->ws_x);
     note_launch(3);
@@ -2080,7 +2149,7 @@ int gmg_warm_start(gmg_handle* h, gmg_net* net, const float* rho, const double* 
     note_launch();
     TRY(gmg_apply(h, net->ws_g, net->ws_kg));
     k_ws_dots<<<kRedBlocks, kRedThreads, 0, s>>>(f, net->ws_g, net->ws_kg, 3 * nn, net->ws_red);
-    k_ws_alpha<<<1, 32, 0, s>>>(net->ws_red, kRedBlocks, net->ws_alpha);
+    k_ws_alpha<<<1, 256, 0, s>>>(net->ws_red, kRedBlocks, net->ws_alpha);
     k_ws_scale<<<blocks_for(3 * nn, 256), 256, 0, s>>>(net->ws_g, 3 * nn, net->ws_alpha, u0);
     note_launch(3);
     CU(cudaGetLastError());
