@@ -49,6 +49,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-warmstart", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     return ap.parse_args()
 
 
@@ -258,6 +259,64 @@ def batched_leg(dev, stream) -> dict:
             "all_converged": ok, "iterations_min_max": [min(its), max(its)]}
 
 
+def configs_leg(dev, stream, flush_l2) -> list:
+    """The two smaller configurations (16x8x8 uniform, Jacobi 0.6; 40^3
+    filtered field at p = 1, 2, 3, Jacobi 0.5): set-up and solve times,
+    iterations, FP64 true residual, and the fine operator's rate and HBM
+    fraction on that grid (y = K u, L2 flushed before each apply)."""
+    import torch
+
+    from paper_2604_26441_b300 import gmg, inputs
+
+    peak, _ = _peaks()
+    out = []
+    for name, p in (("c0", 3.0), ("c1", 1.0), ("c1", 2.0), ("c1", 3.0)):
+        cfg = inputs.CONFIGS[name]
+        rho = torch.from_numpy(cfg.rho()).to(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = gmg.Solver(rho, p=p, opts=gmg.config_options(cfg, stream=stream.cuda_stream))
+        torch.cuda.synchronize()
+        setup_ms = 1000.0 * (time.perf_counter() - t0)
+        f = torch.from_numpy(cfg.load()).to(dev)
+        u = torch.zeros_like(f)
+        for _ in range(2):
+            u.zero_()
+            S.solve(f, u, tol=cfg.tol, maxit=cfg.maxit)
+        ms = []
+        info = None
+        for k in range(5):
+            flush_l2(k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            u.zero_()
+            _, info = S.solve(f, u, tol=cfg.tol, maxit=cfg.maxit)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        x = torch.from_numpy(inputs.random_free_vector(cfg.fixed(), seed=1)).to(dev)
+        y = torch.empty_like(x)
+        S.apply(x, y)
+        ap = []
+        for k in range(10):
+            flush_l2(k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            S.apply(x, y)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ap.append(a.elapsed_time(b))
+        apply_ms = statistics.median(ap)
+        nn, ne = S.nn, cfg.n_elem
+        out.append({"config": name, "grid": [cfg.nx, cfg.ny, cfg.nz], "p": p, "levels": S.num_levels,
+                    "setup_ms": setup_ms, "solve_ms": statistics.median(ms), "iterations": info["iterations"],
+                    "status": info["status"], "rel_residual_fp64": info["rel_residual"],
+                    "fine_apply_us": 1000.0 * apply_ms, "fine_apply_gdof_per_s": 3 * nn / (apply_ms * 1e-3) / 1e9,
+                    "fine_apply_hbm_frac": (24 * nn + 4 * ne) / (apply_ms * 1e-3) / 1e9 / peak})
+        S.close()
+    return out
+
+
 WARM_SOLVES, WARM_STEPS, WARM_BATCH, WARM_EVAL = 2000, 4000, 4, 4
 
 
@@ -267,8 +326,10 @@ def warmstart_leg(dev) -> dict:
     heterogeneous cantilevers (filtered densities, p = 3, rotated tip loads),
     then evaluated on held-out 80^3 (512k-element) cantilevers against the
     cold-start solve with the same solver (Chebyshev 2/2, auto levels, tol
-    1e-6, cap 500).  Network error: energy-norm and L2 error of the rescaled
-    guess against the cold-start solution converged to 1e-10."""
+    1e-6, cap 500), with the network's convolutions in FP32 and again with its
+    forward stride-1 convolutions on the tensor cores (TF32).  Network error:
+    energy-norm and L2 error of the rescaled guess against the cold-start
+    solution converged to 1e-10."""
     import numpy as np
 
     from paper_2604_26441_b300 import gmg, warmstart as ws
@@ -277,7 +338,11 @@ def warmstart_leg(dev) -> dict:
     net = gmg.WarmNet(ws.initial_params(0))
     losses, train_s = ws.train(net, data, WARM_STEPS, batch=WARM_BATCH)
     data.close()
-    res = ws.evaluate(net, ws.held_out_problems(80, WARM_EVAL), tol=1e-6, maxit=500)
+    probs = ws.held_out_problems(80, WARM_EVAL)
+    res = ws.evaluate(net, probs, tol=1e-6, maxit=500)
+    net.set_arith("tf32")  # the same trained network with tensor-core forward convolutions
+    res_tc = ws.evaluate(net, probs, tol=1e-6, maxit=500)
+    net.status()
     net.close()
     cold_ms = float(np.mean([r["cold_ms"] for r in res]))
     warm_ms = float(np.mean([r["warm_ms"] for r in res]))
@@ -292,7 +357,11 @@ def warmstart_leg(dev) -> dict:
             "cold_solves_per_s": 1000.0 / cold_ms, "warm_solves_per_s": 1000.0 / warm_ms,
             "warm_start_ms": float(np.mean([r["warm_start_ms"] for r in res])),
             "energy_error": [r["energy_error"] for r in res], "l2_error": [r["l2_error"] for r in res],
-            "all_converged": all(r["cold_status"] == 0 and r["warm_status"] == 0 for r in res)}
+            "tf32": {"warm_iterations": [r["warm_iterations"] for r in res_tc],
+                     "warm_solves_per_s": 1000.0 / float(np.mean([r["warm_ms"] for r in res_tc])),
+                     "warm_start_ms": float(np.mean([r["warm_start_ms"] for r in res_tc])),
+                     "energy_error": [r["energy_error"] for r in res_tc]},
+            "all_converged": all(r["cold_status"] == 0 and r["warm_status"] == 0 for r in res + res_tc)}
 
 
 def main():
@@ -449,6 +518,7 @@ def main():
 
     batched = None if args.no_batch else batched_leg(dev, stream)
     warm = None if args.no_warmstart else warmstart_leg(dev)
+    small = None if args.no_configs else configs_leg(dev, stream, flush_l2)
 
     if rank != 0:
         return
@@ -472,6 +542,8 @@ def main():
         line["batched"] = batched
     if warm is not None:
         line["warmstart"] = warm
+    if small is not None:
+        line["configs"] = small
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_obj(run_oracle_sample(3))
