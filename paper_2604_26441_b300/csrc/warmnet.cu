@@ -1986,6 +1986,12 @@ int gmg_net_set_arith(gmg_net* net, int arith) {
         CU(cudaStreamSynchronize(net->stream));
         drop_graphs(net);
         net->arith = arith;
+        // the images follow the weights only while TF32 is selected: refresh
+        // them from the current (possibly trained) weights
+        if (arith == GMG_NET_TF32) {
+            TRY(build_images(net, net->stream));
+            CU(cudaGetLastError());
+        }
     }
     return GMG_OK;
 }

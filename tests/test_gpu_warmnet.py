@@ -222,6 +222,30 @@ def test_tensor_core_forward_matches_oracle(dims):
     assert np.array_equal(g, g2)
 
 
+def test_tensor_core_forward_follows_fp32_training():
+    """Weights trained with the FP32 path are the ones the tensor-core path
+    uses after switching (its weight images are refreshed on the switch)."""
+    from paper_2604_26441_b300 import gmg
+    dims = (16, 16, 16)
+    batch = _oracle_batch(dims, (81, 82))
+    xs = [_t(x.reshape(-1, W.N_IN)) for x, _ in batch]
+    ts = [_t(t.reshape(-1, 3)) for _, t in batch]
+    net = gmg.WarmNet(_t(_theta(10)))
+    xb = torch.stack(xs)
+    g0 = net.forward(dims, xb).cpu().numpy()
+    for _ in range(3):
+        net.train_step(dims, xs, ts, 1e-2)
+    g32 = net.forward(dims, xb).cpu().numpy()
+    assert rel_l2(g32, g0) > 0.1  # training moved the output
+    net.set_arith("tf32")
+    gtc = net.forward(dims, xb).cpu().numpy()
+    net.status()
+    assert rel_l2(gtc, g32) < 1e-2
+    # and back: the FP32 path is unaffected by the switch
+    net.set_arith("fp32")
+    assert np.array_equal(net.forward(dims, xb).cpu().numpy(), g32)
+
+
 @pytest.mark.parametrize("dims", [(16, 24, 8), (32, 32, 32)])
 def test_tensor_core_train_step_matches_oracle(dims):
     """Mean-squared-error loss: its gradient is well conditioned, so it shows
