@@ -199,18 +199,20 @@ def batched_leg(dev, stream) -> dict:
     as the 40^3 configuration with distinct seeds, p = 3) x 16 right-hand sides
     (the tip-edge load rotated through 16 directions in the y-z plane): 128
     solves in one CUDA-graph launch (gmg_solve_batch), against the same 128
-    solves one after another (gmg_solve, each with its own captured loop)."""
+    solves one after another (gmg_solve, each with its own captured loop).
+    Each grid's launch shapes are tuned first (gmg_autotune)."""
     import torch
 
     from paper_2604_26441_b300 import gmg, inputs
 
-    solvers, fs = [], []
+    solvers, fs, tuned = [], [], []
     elements = 0
     for gi, n in enumerate(BATCH_GRIDS):
         rho = torch.from_numpy(inputs.filtered_random_density(n, n, n, 300 + gi)).to(dev)
         opts = gmg.options(levels=0, smoother="jacobi", degree=2, coarse_smoother=None, coarse_degree=None,
                            omega=0.5, coarse_omega=None, stream=stream.cuda_stream)
         base = gmg.Solver(rho, p=3.0, opts=opts)
+        tuned.append(base.autotune(reps=3))
         for k in range(BATCH_RHS):
             solvers.append(base if k == 0 else base.clone())
             fs.append(torch.from_numpy(inputs.rotated_tip_edge_load(n, n, n, k, BATCH_RHS)).to(dev))
@@ -256,7 +258,11 @@ def batched_leg(dev, stream) -> dict:
                         f"{BATCH_RHS} rotated tip loads = {nsol} solves, Jacobi 2/2, auto levels, tol 1e-6",
             "value": nsol / (batch_ms / 1000.0), "unit": "solves/s", "ms_per_batch": batch_ms,
             "sequential_solves_per_s": nsol / (seq_ms / 1000.0), "speedup_vs_sequential": seq_ms / batch_ms,
-            "all_converged": ok, "iterations_min_max": [min(its), max(its)]}
+            "all_converged": ok, "iterations_min_max": [min(its), max(its)],
+            "autotune": [{"n": n, "fine": f"{t['fine_tile']}/z{t['fine_zchunk']}",
+                          "model": f"{t['model_tile']}/z{t['model_zchunk']}",
+                          "fine_us": round(t["fine_us"], 2), "model_us": round(t["model_us"], 2)}
+                         for n, t in zip(BATCH_GRIDS, tuned)]}
 
 
 def configs_leg(dev, stream, flush_l2) -> list:
@@ -407,6 +413,9 @@ def main():
     t_setup0 = time.perf_counter()
     S = gmg.Solver(rho, p=cfg.p, opts=opts)
     setup_s = time.perf_counter() - t_setup0
+    t_tune0 = time.perf_counter()
+    tuning = S.autotune(reps=5)  # launch shapes measured on this handle (gmg_autotune)
+    tune_s = time.perf_counter() - t_tune0
     nn = S.nn
     ne = cfg.n_elem
     f_host = torch.from_numpy(cfg.load()).pin_memory()
@@ -577,6 +586,7 @@ def main():
                    "l2": "solve working set ~300 MB > 126 MB L2; between steps a 256 MB buffer is written and another read"},
         "iterations": infos[-1]["iterations"], "rel_residual": infos[-1]["rel_residual"],
         "all_converged": ok, "setup_ms": setup_s * 1000.0,
+        "autotune": {**tuning, "ms": tune_s * 1000.0},
         "roofline": roofline,
         "fine_apply": {"ms": apply_ms, "gdof_per_s": 3 * nn / (apply_ms * 1e-3) / 1e9,
                        "alg_gbs": (24 * nn + 4 * ne) / (apply_ms * 1e-3) / 1e9},

@@ -265,6 +265,32 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out);
 int gmg_solve_batch(gmg_handle* const* handles, int count, const double* const* f_dev, double* const* u_dev,
                     double tol, int maxit, gmg_info* infos);
 
+/* Result of gmg_autotune. */
+typedef struct {
+    int fine_tile;               /* fine kernel tile: 0 = 32 x 8 threads (31 x 7 nodes), 1 = 16 x 16 (15 x 15) */
+    int fine_zchunk;             /* node planes per block of the z-marching fine kernel */
+    int model_tile, model_zchunk;  /* the cost model's choice (used without tuning) */
+    int fine_candidates;         /* plans timed */
+    double fine_us, model_us;    /* one fine smoothing step: tuned plan, model plan (median of reps) */
+    int bsr_kind[16];            /* per level: 0 streaming, 1 K-split, -1 not tuned (fine level,
+                                    TMA-staged levels, levels inside the fused lower V-cycle) */
+    double bsr_us[16];           /* chosen kernel, one smoothing step */
+    double bsr_alt_us[16];       /* the other kernel */
+} gmg_tuning;
+
+/* Measures the launch shapes of the handle's hot kernels on its own operands
+ * and keeps the fastest: the fine kernel's tile shape and z-chunk length
+ * (candidates of both tile shapes and z-chunks from the whole depth down to 4
+ * planes, timed as fused Chebyshev/Jacobi smoothing steps; the choice holds
+ * for every handle of that fine grid in this process), and per assembled
+ * level outside the TMA-staged and fused paths the streaming or the K-split
+ * SpMV kernel (kept in this handle).  The operator's results do not depend on
+ * these shapes (each node's arithmetic is the same); reduction partial sums
+ * are grouped differently.  reps: timed launches per candidate (>= 1); 0
+ * returns to the cost model's plan and the size rule.  Drops the handle's
+ * captured solve graphs.  Synchronous.  out may be NULL. */
+int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out);
+
 /* z = V(r): one V-cycle of Eq. vcycle on the fine level. */
 int gmg_vcycle(gmg_handle* h, const float* r_dev, float* z_dev);
 

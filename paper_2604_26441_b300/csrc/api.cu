@@ -84,6 +84,7 @@ BsrArgs bsr_args(gmg_handle* h, int li) {
     a.nx = l.nx; a.ny = l.ny; a.nz = l.nz; a.nn = l.nn;
     a.A = l.A32; a.ps = l.ps; a.invdiag = l.invdiag; a.mask = l.mask; a.coef = l.coef;
     a.err = h->kerr;
+    a.kind = l.bsr_kind;
     if (l.tma) { a.tm_own = &l.tm_own; a.tm_back = &l.tm_back; }
     return a;
 }
@@ -92,7 +93,7 @@ int partial_count(gmg_handle* h, int li, int kind) {
     // kind 0: operator-kernel partials, 1: vector-kernel partials
     if (kind == 1) return vec_grid_blocks();
     if (li == 0) return fine_grid_blocks(h->lev[0].nx, h->lev[0].ny, h->lev[0].nz);
-    return bsr_grid_blocks(h->lev[li].nn, h->lev[li].tma);
+    return bsr_grid_blocks(h->lev[li].nn, h->lev[li].tma, h->lev[li].bsr_kind);
 }
 
 // y = K^l x (masked); with dot: partial += x . y and finalised into `slot`.
@@ -336,8 +337,12 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     int maxp = vec_grid_blocks();
     maxp = std::max(maxp, fine_grid_blocks(l0.nx, l0.ny, l0.nz));
     maxp = std::max(maxp, resid64_grid_blocks(l0.nx, l0.ny, l0.nz));
-    // (the kernel of a level is chosen later; size for the one with more blocks)
-    for (int li = 1; li < L; ++li) maxp = std::max(maxp, bsr_grid_blocks(h->lev[li].nn, true));
+    // (the kernel of a level is chosen later or by gmg_autotune: size for
+    // every kernel, and leave room for the fine kernel's tuning candidates)
+    for (int li = 1; li < L; ++li)
+        for (int kind = 0; kind < 2; ++kind)
+            maxp = std::max({maxp, bsr_grid_blocks(h->lev[li].nn, true), bsr_grid_blocks(h->lev[li].nn, false, kind)});
+    maxp = std::max(maxp, 4096);
     h->max_partials = maxp;
     TRY(dalloc(h, &h->partials, maxp));
     CU(cudaMallocHost(&h->pinned, sizeof(double) * SC_COUNT));
@@ -1021,6 +1026,119 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     inf.rel_residual = rel;
     CU(cudaGetLastError());
     return finish(GMG_NOT_CONVERGED);
+}
+
+int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
+    if (!h || reps < 0) return fail(GMG_ERR_ARG, "null handle or reps < 0");
+    if (h->is_clone) return fail(GMG_ERR_ARG, "tune the source handle, not a clone");
+    cudaStream_t s = h->stream;
+    CU(cudaStreamSynchronize(s));
+    if (reps == 0) {  // back to the cost model and the size rule
+        fine_set_plan(h->lev[0].nx, h->lev[0].ny, h->lev[0].nz, -1, 0);
+        for (int li = 1; li < h->L; ++li) h->lev[li].bsr_kind = -1;
+        loop_free(h);
+        if (out) {
+            *out = gmg_tuning{};
+            fine_model_plan(h->lev[0].nx, h->lev[0].ny, h->lev[0].nz, &out->fine_tile, &out->fine_zchunk);
+            out->model_tile = out->fine_tile;
+            out->model_zchunk = out->fine_zchunk;
+            for (int li = 0; li < 16; ++li) out->bsr_kind[li] = -1;
+        }
+        return GMG_OK;
+    }
+    gmg_tuning t{};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(GMG_ERR_CUDA, "cudaEventCreate failed");
+    }
+    // median of three timed batches of `reps` launches, after one warm-up
+    auto timed = [&](auto&& launch, double& us) -> int {
+        launch();
+        double m[3];
+        for (int r = 0; r < 3; ++r) {
+            CU(cudaEventRecord(e0, s));
+            for (int i = 0; i < reps; ++i) launch();
+            CU(cudaEventRecord(e1, s));
+            CU(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, e0, e1));
+            m[r] = 1000.0 * ms / reps;
+        }
+        std::sort(m, m + 3);
+        us = m[1];
+        return GMG_OK;
+    };
+    int rc = GMG_OK;
+    {
+        // fine level: fused smoothing step (the dominant launch of a V-cycle)
+        const Level& l0 = h->lev[0];
+        FineArgs a = fine_args(h);
+        a.xin = h->z;
+        a.b = h->r;
+        a.out = h->q;
+        a.dold = nullptr;
+        a.dnew = nullptr;
+        a.step = 0;
+        auto fine = [&] { launch_fine(FM_SMOOTH, 0, 0, a, h->gh, s); };
+        int tiles[64], zcs[64];
+        const int nc = fine_candidates(l0.nx, l0.ny, l0.nz, h->max_partials, tiles, zcs, 64);
+        fine_model_plan(l0.nx, l0.ny, l0.nz, &t.model_tile, &t.model_zchunk);
+        fine_set_plan(l0.nx, l0.ny, l0.nz, t.model_tile, t.model_zchunk);
+        if (rc == GMG_OK) rc = timed(fine, t.model_us);
+        t.fine_tile = t.model_tile;
+        t.fine_zchunk = t.model_zchunk;
+        t.fine_us = t.model_us;
+        for (int c = 0; c < nc && rc == GMG_OK; ++c) {
+            fine_set_plan(l0.nx, l0.ny, l0.nz, tiles[c], zcs[c]);
+            double us = 0.0;
+            rc = timed(fine, us);
+            if (rc == GMG_OK && us < t.fine_us) {
+                t.fine_us = us;
+                t.fine_tile = tiles[c];
+                t.fine_zchunk = zcs[c];
+            }
+        }
+        t.fine_candidates = nc;
+        fine_set_plan(l0.nx, l0.ny, l0.nz, t.fine_tile, t.fine_zchunk);
+    }
+    for (int li = 0; li < 16; ++li) t.bsr_kind[li] = -1;
+    const int fused_start = h->use_fused ? h->cf.start : h->L;
+    for (int li = 1; li < h->L - 1 && li < 16 && rc == GMG_OK; ++li) {
+        Level& l = h->lev[li];
+        if (l.tma || li >= fused_start) continue;
+        double us[2] = {0.0, 0.0};
+        for (int kind = 0; kind < 2 && rc == GMG_OK; ++kind) {
+            l.bsr_kind = kind;
+            BsrArgs a = bsr_args(h, li);
+            a.xin = l.x;
+            a.b = l.b;
+            a.out = l.x2;
+            a.dold = nullptr;
+            a.dnew = nullptr;
+            a.step = 0;
+            rc = timed([&] { launch_bsr(FM_SMOOTH, 0, a, s); }, us[kind]);
+        }
+        l.bsr_kind = us[1] < us[0] ? 1 : 0;
+        t.bsr_kind[li] = l.bsr_kind;
+        t.bsr_us[li] = us[l.bsr_kind];
+        t.bsr_alt_us[li] = us[1 - l.bsr_kind];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != GMG_OK) return rc;
+    // graphs captured with the former shapes are dropped (they stay correct,
+    // but would keep the old shapes)
+    loop_free(h);
+    if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
+    if (h->batch_graph) cudaGraphDestroy(h->batch_graph);
+    h->batch_exec = nullptr;
+    h->batch_graph = nullptr;
+    h->batch_key.clear();
+    CU(cudaGetLastError());
+    if (out) *out = t;
+    return GMG_OK;
 }
 
 int gmg_kappa_eff(gmg_handle* h, const double* b, int steps, double out[3]) {

@@ -38,6 +38,9 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "internal.cuh"
 
@@ -812,10 +815,22 @@ int sm_count() {
     return n;
 }
 
-// Picks the tile shape and z-chunk length that minimise (waves x steps per
-// block) for two resident blocks per SM: the partial tiles at the grid edges
-// and the tail wave are the main losses on grids such as 101^3 nodes.
-FinePlan plan_fine(int nx, int ny, int nz) {
+FinePlan make_plan(int nx, int ny, int nz, int tile, int zc) {
+    const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
+    const int bx = tile == 0 ? 32 : 16, by = tile == 0 ? 8 : 16;
+    const int gx = (NX + bx - 2) / (bx - 1), gy = (NY + by - 2) / (by - 1);
+    zc = std::max(1, std::min(zc, NZ));
+    return FinePlan{tile, zc, dim3(gx, gy, (NZ + zc - 1) / zc)};
+}
+
+// Plans measured by gmg_autotune, per fine grid (process-wide).
+std::mutex g_plan_mu;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_plans;
+
+// The cost model: the tile shape and z-chunk length that minimise (waves x
+// steps per block) for two resident blocks per SM -- the partial tiles at the
+// grid edges and the tail wave are the main losses on grids such as 101^3.
+FinePlan model_plan(int nx, int ny, int nz) {
     const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
     const int slots = 2 * sm_count();
     FinePlan best{0, NZ, dim3(1, 1, 1)};
@@ -840,6 +855,16 @@ FinePlan plan_fine(int nx, int ny, int nz) {
     return best;
 }
 
+// A tuned plan when gmg_autotune measured one for this grid, else the model's.
+FinePlan plan_fine(int nx, int ny, int nz) {
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        const auto it = g_plans.find(std::make_tuple(nx, ny, nz));
+        if (it != g_plans.end()) return make_plan(nx, ny, nz, it->second.first, it->second.second);
+    }
+    return model_plan(nx, ny, nz);
+}
+
 template <int MODE, bool DOT>
 void launch_shape(const FinePlan& pl, const FineArgs& a, const GHat& G, cudaStream_t s) {
     if (pl.tile == 0) k_fine<32, 8, MODE, DOT><<<pl.grid, dim3(32, 8), 0, s>>>(a, G, pl.zc);
@@ -851,6 +876,39 @@ void launch_shape(const FinePlan& pl, const FineArgs& a, const GHat& G, cudaStre
 int fine_grid_blocks(int nx, int ny, int nz) {
     const FinePlan pl = plan_fine(nx, ny, nz);
     return (int)(pl.grid.x * pl.grid.y * pl.grid.z);
+}
+
+int fine_candidates(int nx, int ny, int nz, int max_blocks, int* tiles, int* zcs, int cap) {
+    const int NZ = nz + 1;
+    int n = 0;
+    for (int t = 0; t < 2; ++t) {
+        int last = -1;
+        for (int nch = 1; nch <= NZ && n < cap; ++nch) {
+            const int zc = (NZ + nch - 1) / nch;
+            if (zc < 4 && nch > 1) break;
+            if (zc == last) continue;
+            last = zc;
+            const FinePlan pl = make_plan(nx, ny, nz, t, zc);
+            if ((long long)pl.grid.x * pl.grid.y * pl.grid.z > max_blocks) continue;
+            tiles[n] = t;
+            zcs[n] = zc;
+            ++n;
+        }
+    }
+    return n;
+}
+
+void fine_model_plan(int nx, int ny, int nz, int* tile, int* zc) {
+    const FinePlan pl = model_plan(nx, ny, nz);
+    *tile = pl.tile;
+    *zc = pl.zc;
+}
+
+void fine_set_plan(int nx, int ny, int nz, int tile, int zc) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    const auto key = std::make_tuple(nx, ny, nz);
+    if (tile < 0) g_plans.erase(key);
+    else g_plans[key] = std::make_pair(tile, zc);
 }
 
 void launch_fine(int mode, int dot, int mask_in, const FineArgs& a_in, const GHat& G, cudaStream_t s) {

@@ -813,10 +813,12 @@ int pipe_blocks(long long nn) {
     return (int)std::min<long long>(tiles, sms);
 }
 
-int bsr_grid_blocks(long long nn, bool tma) {
+bool bsr_streams(long long nn, int kind) { return kind < 0 ? nn >= kBsrStreamLevel : kind == 0; }
+
+int bsr_grid_blocks(long long nn, bool tma, int kind) {
     if (tma) return pipe_blocks(nn);
     constexpr int npb = 256 / kKsSlices;
-    return nn >= kBsrStreamLevel ? (int)((nn + 255) / 256) : (int)((nn + npb - 1) / npb);
+    return bsr_streams(nn, kind) ? (int)((nn + 255) / 256) : (int)((nn + npb - 1) / npb);
 }
 
 template <int MODE, bool DOT>
@@ -844,8 +846,8 @@ void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
         }
         return;
     }
-    const int g = bsr_grid_blocks(a.nn, false);
-    if (a.nn >= kBsrStreamLevel) {
+    const int g = bsr_grid_blocks(a.nn, false, a.kind);
+    if (bsr_streams(a.nn, a.kind)) {
         if (mode == FM_APPLY) {
             if (dot) k_bsr<FM_APPLY, true, 256><<<g, 256, 0, s>>>(a);
             else k_bsr<FM_APPLY, false, 256><<<g, 256, 0, s>>>(a);

@@ -81,6 +81,7 @@ struct Level {
     float* A32 = nullptr;           // [126 ps] FP32 diagonal + forward blocks (levels >= 1)
     long long ps = 0;               // plane stride of A32: nn rounded up to 4 (16-byte aligned planes)
     bool tma = false;               // operator streamed by the TMA-staged kernel (tm_own / tm_back valid)
+    int bsr_kind = -1;              // kernel of the non-TMA operator (bsr_grid_blocks), set by gmg_autotune
     CUtensorMap tm_own{};           // A32 as a [126][ps] FP32 tensor, box 126 planes x 64 nodes
     CUtensorMap tm_back{};          // same tensor, box 9 planes x 68 nodes
     float* x = nullptr;             // [3nn] smoother iterate / V-cycle output (levels >= 1)
@@ -271,6 +272,12 @@ struct FineArgs {
 };
 
 int fine_grid_blocks(int nx, int ny, int nz);
+// Candidate (tile, z-chunk) plans of the fine kernel for a grid with at most
+// max_blocks blocks (tile 0: 32x8 threads, 1: 16x16); the cost model's plan;
+// and the process-wide override that gmg_autotune sets (tile < 0 clears it).
+int fine_candidates(int nx, int ny, int nz, int max_blocks, int* tiles, int* zcs, int cap);
+void fine_model_plan(int nx, int ny, int nz, int* tile, int* zc);
+void fine_set_plan(int nx, int ny, int nz, int tile, int zc);
 // mask_in: treat fixed DOFs of the operand as 0 (for operands that may hold
 // values there, e.g. user input); internal vectors are already 0 on them.
 void launch_fine(int mode, int dot, int mask_in, const FineArgs& a, const GHat& G, cudaStream_t s);
@@ -301,12 +308,15 @@ struct BsrArgs {
     int step;
     double* partial;
     int* err;                    // sticky error word (a TMA wait that gave up)
+    int kind;                    // kernel choice, as bsr_grid_blocks
     const CUtensorMap* tm_own;   // non-null: stream through the TMA-staged kernel
     const CUtensorMap* tm_back;
 };
 // Blocks (= dot partials) of the operator launch for a level of nn nodes: 64
 // nodes per block for the TMA-staged and K-split kernels, 256 for streaming.
-int bsr_grid_blocks(long long nn, bool tma);
+// kind: -1 = by size (streaming kernel from 65,536 nodes, K-split below),
+// 0 = streaming k_bsr, 1 = K-split k_bsr_ks (ignored when tma)
+int bsr_grid_blocks(long long nn, bool tma, int kind = -1);
 // Encodes the two tensor maps of a level's FP32 planes; GMG_OK or an error code.
 int encode_bsr_maps(Level& l);
 void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s);

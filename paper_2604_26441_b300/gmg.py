@@ -60,6 +60,14 @@ class _Info(ctypes.Structure):
                 ("solve_ms", ctypes.c_double)]
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("fine_tile", ctypes.c_int), ("fine_zchunk", ctypes.c_int), ("model_tile", ctypes.c_int),
+                ("model_zchunk", ctypes.c_int), ("fine_candidates", ctypes.c_int),
+                ("fine_us", ctypes.c_double), ("model_us", ctypes.c_double),
+                ("bsr_kind", ctypes.c_int * 16), ("bsr_us", ctypes.c_double * 16),
+                ("bsr_alt_us", ctypes.c_double * 16)]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -88,6 +96,7 @@ _SIGS = {
     "gmg_coarse_solve": (ctypes.c_int, [_P, _P, _P]),
     "gmg_vcycle": (ctypes.c_int, [_P, _P, _P]),
     "gmg_kappa_eff": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "gmg_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_Tuning)]),
     "gmg_clone": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "gmg_solve_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                        ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Info)]),
@@ -321,6 +330,19 @@ class Solver:
         return u, {"status": info.status, "iterations": info.iterations, "replacements": info.replacements,
                    "rel_residual": info.rel_residual, "rel_residual_recursive": info.rel_residual_recursive,
                    "solve_ms": info.solve_ms}
+
+    def autotune(self, reps: int = 5) -> dict:
+        """Times the fine kernel's launch shapes and each assembled level's
+        SpMV kernel on this handle and keeps the fastest (gmg_autotune);
+        reps = 0 returns to the untuned choices."""
+        t = _Tuning()
+        _check(self._lib.gmg_autotune(self._h, reps, ctypes.byref(t)))
+        L = self.num_levels
+        return {"fine_tile": ["32x8", "16x16"][t.fine_tile], "fine_zchunk": t.fine_zchunk,
+                "model_tile": ["32x8", "16x16"][t.model_tile], "model_zchunk": t.model_zchunk,
+                "fine_candidates": t.fine_candidates, "fine_us": t.fine_us, "model_us": t.model_us,
+                "bsr": [{"level": l, "kind": ["streaming", "k-split"][t.bsr_kind[l]], "us": t.bsr_us[l],
+                         "other_us": t.bsr_alt_us[l]} for l in range(1, min(L, 16)) if t.bsr_kind[l] >= 0]}
 
     # -- per-step entry points
     def get_mask(self, level: int) -> np.ndarray:

@@ -58,7 +58,8 @@ def test_struct_layouts_match_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = {"gmg_options": gmg._Options, "gmg_info": gmg._Info, "gmg_grid": gmg._Grid, "gmg_bc": gmg._BC}
+    structs = {"gmg_options": gmg._Options, "gmg_info": gmg._Info, "gmg_grid": gmg._Grid, "gmg_bc": gmg._BC,
+               "gmg_tuning": gmg._Tuning}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gmg.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
@@ -93,6 +94,7 @@ def test_argument_errors_without_device(lib):
     assert lib.gmg_setup(ctypes.byref(h), ctypes.byref(g), ctypes.c_void_p(16), 3.0, 1.0, 1e-9, 0.3,
                          ctypes.byref(mask_bc), None) == -1
     assert lib.gmg_solve(None, None, None, 1e-6, 10, None) == -1
+    assert lib.gmg_autotune(None, 3, None) == -1
     assert lib.gmg_num_levels(None) == 0
     lib.gmg_destroy(None)
 

@@ -635,3 +635,29 @@ def test_batch_matches_single_solves():
     r = loads[-1] - fem.matfree_apply(fem.Grid(nx, ny, nz), fem.moduli(rho, 3.0), fem.element_stiffness(0.3), u)
     free = fem.free_dofs(inputs.clamp_xmin_mask(nx, ny, nz))
     assert np.linalg.norm(r[free]) / np.linalg.norm(loads[-1][free]) < 1e-6
+
+
+@pytest.mark.parametrize("cfg_name", ["c1", "c2"])
+def test_autotune_keeps_operator_results(cfg_name):
+    """gmg_autotune picks launch shapes only: the fine operator's output is
+    bitwise the same under the tuned plan, solves still converge to the same
+    solution, and the kept choice is the fastest measured."""
+    cfg = inputs.CONFIGS[cfg_name]
+    opts = config_opts(cfg)
+    S = gpu_solver(cfg.rho(), cfg.p, **opts)
+    u = _t(inputs.random_free_vector(cfg.fixed(), seed=31))
+    y0 = S.apply(u).cpu().numpy()
+    f = _t(cfg.load(), torch.float64)
+    ub, ib = S.solve(f, None, tol=cfg.tol, maxit=cfg.maxit)
+    try:
+        t = S.autotune(reps=3)
+        assert t["fine_candidates"] >= 2 and t["fine_us"] <= t["model_us"]
+        assert all(b["us"] <= b["other_us"] for b in t["bsr"])
+        y1 = S.apply(u).cpu().numpy()
+        assert np.array_equal(y0, y1)
+        ua, ia = S.solve(f, None, tol=cfg.tol, maxit=cfg.maxit)
+        assert ia["status"] == 0 and ia["rel_residual"] <= cfg.tol
+        assert abs(ia["iterations"] - ib["iterations"]) <= 1
+        assert rel_l2(ua.cpu().numpy(), ub.cpu().numpy()) < 1e-5
+    finally:
+        S.autotune(reps=0)
