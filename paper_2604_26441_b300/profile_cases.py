@@ -4,6 +4,7 @@
     python -m paper_2604_26441_b300.profile_cases solve-c2-hostloop  # the same, PCG driven from the host
     python -m paper_2604_26441_b300.profile_cases smooth-c2   # set-up + 3 fine smoothing passes
     python -m paper_2604_26441_b300.profile_cases apply-c2    # set-up + 5 fine operator applies
+    python -m paper_2604_26441_b300.profile_cases smooth-l1-c2  # set-up + 3 level-1 smoothing passes (BSR)
     python -m paper_2604_26441_b300.profile_cases smooth-c2-bf16x3  # fine smoothing, tensor-core contraction
     python -m paper_2604_26441_b300.profile_cases warmstart-80  # 80^3 set-up, one learned warm start + solve
     python -m paper_2604_26441_b300.profile_cases warmstart-80-tf32  # the same with tensor-core convolutions
@@ -74,6 +75,13 @@ def main(case: str) -> None:
         for _ in range(2):
             u, info = S.solve(f, tol=cfg.tol, maxit=cfg.maxit)
             print(info, flush=True)
+    elif case == "smooth-l1-c2":
+        n1 = S.level_nodes(1)
+        b = torch.ones(3 * n1, device="cuda")
+        x = torch.zeros(3 * n1, device="cuda")
+        for _ in range(3):
+            S.level_smooth(1, b, x)
+        torch.cuda.synchronize()
     elif case in ("smooth-c2", "smooth-c2-bf16x3", "apply-c2"):
         x = torch.from_numpy(inputs.random_free_vector(cfg.fixed(), 1)).cuda()
         y = torch.from_numpy(inputs.random_free_vector(cfg.fixed(), 2)).cuda()
