@@ -571,9 +571,11 @@ def main():
     torch.cuda.synchronize()
     apply_ms = statistics.median(a.elapsed_time(b) for a, b in ap)
 
-    batched = None if args.no_batch else batched_leg(dev, stream)
-    warm = None if args.no_warmstart else warmstart_leg(dev)
-    small = None if args.no_configs else configs_leg(dev, stream, flush_l2)
+    # single-GPU characterisations (not part of the replicated metric): N = 1 only
+    solo = world == 1
+    batched = None if args.no_batch or not solo else batched_leg(dev, stream)
+    warm = None if args.no_warmstart or not solo else warmstart_leg(dev)
+    small = None if args.no_configs or not solo else configs_leg(dev, stream, flush_l2)
 
     if rank != 0:
         return
