@@ -996,6 +996,14 @@ __device__ __forceinline__ uint64_t tc_desc(unsigned addr, unsigned lbo, unsigne
     return d;
 }
 
+__device__ __forceinline__ void mma_tf32(unsigned d, uint64_t da, uint64_t db, unsigned idesc, unsigned acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
                                             uint64_t* bar) {
     asm volatile(
@@ -1092,17 +1100,13 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUte
             consumed = c + 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned ab = base + st * Gm::STAGE, wb = ab + 2 * kTcSlabPitch;
-#pragma unroll 1
+            const uint64_t da0 = tc_desc(ab, kTcSlabPitch, kTcHX * 16), db0 = tc_desc(wb, 16 * NB, 128);
+#pragma unroll
             for (int tap = 0; tap < 27; ++tap) {
                 const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
-                const uint64_t da = tc_desc(ab + ((dz * kTcHY + dy) * kTcHX + dx) * 16, kTcSlabPitch, kTcHX * 16);
-                const uint64_t db = tc_desc(wb + tap * 32 * NB, 16 * NB, 128);
-                const unsigned acc = (c > 0 || tap > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                    "l"(da), "l"(db), "r"(idesc), "r"(acc)
-                    : "memory");
+                const uint64_t da = da0 + (uint64_t)((((dz * kTcHY + dy) * kTcHX + dx) * 16) >> 4);
+                const uint64_t db = db0 + (uint64_t)((tap * 32 * NB) >> 4);
+                mma_tf32(tmem, da, db, idesc, (c > 0 || tap > 0) ? 1u : 0u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&empty[st]))
@@ -1161,6 +1165,205 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUte
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Gm::COLS) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core convolution, stride 1, z-marching: a CTA owns an 8 x 16 tile of
+// output nodes over a range of z-planes.  Its weights (every chunk and tap)
+// stay in shared memory for the whole range; the input arrives one z-plane at
+// a time (all channel slabs of the 10 x 18 halo, one TMA box per 4 channels)
+// into a ring of four plane slots, so each plane is loaded once and serves
+// the three output planes that read it.  Output plane z takes its 27 taps
+// from the slots of planes z-1, z, z+1 through shifted descriptors.  One
+// thread (warp 4) issues the loads and the MMAs into two TMEM accumulators
+// used alternately; warps 0-3 drain the accumulator of plane z (bias,
+// activation, store) while the MMAs of plane z+1 run.
+// ---------------------------------------------------------------------------
+constexpr unsigned kTczSlab = kTcHX * kTcHY * 16;              // one 4-channel slab of one plane: 2,880 bytes
+constexpr unsigned kTczSlabPitch = (kTczSlab + 127u) & ~127u;  // 2,944: 128-byte aligned TMA destinations
+constexpr int kTczRing = 4;
+
+struct TczArgs {
+    float* out;
+    int out_pitch, cout;
+    const float* img;   // weight image of one output block: [nch][27][2][NB/8][8][4]
+    const float* bias;
+    int mode;           // 0 = linear, 1 = leaky ReLU
+    int X, Y, Z;
+    int nch, nslab;     // 8-channel chunks, 4-channel slabs (2 nch)
+    int zr;             // output planes per CTA
+    long long out_bs;
+    int* err;
+};
+
+__device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int NB>
+__global__ void __launch_bounds__(160, 1) k_conv_tcz(const __grid_constant__ CUtensorMap tm, TczArgs a) {
+    extern __shared__ unsigned char dyn_raw[];
+    __shared__ __align__(8) uint64_t wbar, pfull[kTczRing], mdone[2], afree[2], fin;
+    __shared__ unsigned tslot;
+    __shared__ volatile int abort_flag;
+    constexpr unsigned COLS = 2 * NB < 32 ? 32u : 2u * NB;  // two accumulators of NB columns
+    unsigned char* dyn = dyn_raw + ((1024u - (smem_u32(dyn_raw) & 1023u)) & 1023u);
+    const unsigned WB = (unsigned)a.nch * 27u * 32u * NB;
+    const unsigned SLOT = (unsigned)a.nslab * kTczSlabPitch;
+    unsigned char* wsm = dyn;
+    unsigned char* ring = dyn + WB;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = (a.X + 7) >> 3;
+    const int bx = blockIdx.x % ntx, by = blockIdx.x / ntx;
+    const int x0 = bx * 8, y0 = by * 16;
+    const int z0 = blockIdx.y * a.zr, z1 = min(z0 + a.zr, a.Z);
+    const int nz = z1 - z0, np = nz + 2;
+    const int b = blockIdx.z;
+    if (tid == 0) {
+        abort_flag = 0;
+        mbar_init(&wbar, 1);
+        for (int i = 0; i < kTczRing; ++i) mbar_init(&pfull[i], 1);
+        mbar_init(&mdone[0], 1);
+        mbar_init(&mdone[1], 1);
+        mbar_init(&afree[0], 128);
+        mbar_init(&afree[1], 128);
+        mbar_init(&fin, 1);
+        mbar_fence_init();
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                     "r"(COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tslot;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            auto wait = [&](uint64_t* bar, unsigned par) -> bool {
+                for (unsigned it = 0; it < kTcSpinW; ++it) {
+                    if (mbar_try_wait(bar, par)) return true;
+                    if (abort_flag) return false;
+                }
+                return false;
+            };
+            int last_q[kTczRing] = {-1, -1, -1, -1}, seen_q[kTczRing] = {-1, -1, -1, -1};
+            auto load_plane = [&](int q) {
+                const int slot = q & (kTczRing - 1);
+                unsigned char* dst = ring + slot * SLOT;
+                mbar_expect_tx(&pfull[slot], (unsigned)a.nslab * kTczSlab);
+                for (int sl = 0; sl < a.nslab; ++sl)
+                    tma_load_5d(dst + sl * kTczSlabPitch, &tm, 4 * sl, x0 - 1, y0 - 1, z0 - 1 + q, b, &pfull[slot]);
+                last_q[slot] = q;
+            };
+            constexpr unsigned idesc =
+                (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(NB >> 3) << 17) | ((128u >> 4) << 24);
+            const uint64_t da0 = tc_desc(smem_u32(ring), kTczSlabPitch, kTcHX * 16);
+            const uint64_t db0 = tc_desc(smem_u32(wsm), 16 * NB, 128);
+            mbar_expect_tx(&wbar, WB);
+            bulk_load(wsm, a.img, WB, &wbar);
+            for (int q = 0; q < kTczRing && q < np; ++q) load_plane(q);
+            bool ok = wait(&wbar, 0);
+            bool w_seen = ok;
+            for (int zi = 0; zi < nz && ok; ++zi) {
+                for (int q = zi; q < zi + 3 && ok; ++q) {
+                    ok = wait(&pfull[q & (kTczRing - 1)], (q >> 2) & 1);
+                    if (ok) seen_q[q & (kTczRing - 1)] = q;
+                }
+                if (ok && zi >= 2) ok = wait(&afree[zi & 1], ((zi - 2) >> 1) & 1);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned acc = tmem + (unsigned)((zi & 1) * NB);
+                // descriptors differ from the base ones only in the address
+                // field (address / 16), so each tap is a constant offset
+                const uint64_t sa[3] = {da0 + (((unsigned)((zi) & (kTczRing - 1)) * SLOT) >> 4),
+                                        da0 + (((unsigned)((zi + 1) & (kTczRing - 1)) * SLOT) >> 4),
+                                        da0 + (((unsigned)((zi + 2) & (kTczRing - 1)) * SLOT) >> 4)};
+#pragma unroll 1
+                for (int c = 0; c < a.nch; ++c) {
+                    const uint64_t ca = (uint64_t)((2u * c * kTczSlabPitch) >> 4);
+                    const uint64_t cb = db0 + (uint64_t)((c * 27u * 32u * NB) >> 4);
+#pragma unroll
+                    for (int tap = 0; tap < 27; ++tap) {
+                        const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+                        const uint64_t da = sa[dz] + ca + (uint64_t)(((dy * kTcHX + dx) * 16) >> 4);
+                        const uint64_t db = cb + (uint64_t)((tap * 32 * NB) >> 4);
+                        mma_tf32(acc, da, db, idesc, (c > 0 || tap > 0) ? 1u : 0u);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&mdone[zi & 1]))
+                             : "memory");
+                // the slot of plane zi-1 is free once output zi-1's MMAs are done: plane zi+3 goes there
+                if (zi >= 1 && zi + 3 < np) {
+                    ok = wait(&mdone[(zi - 1) & 1], ((zi - 1) >> 1) & 1);
+                    if (ok) load_plane(zi + 3);
+                }
+            }
+            // every MMA issued, then every load issued, must finish before the
+            // shared memory and TMEM are given up
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&fin))
+                         : "memory");
+            const int saved = abort_flag;
+            abort_flag = 0;  // the drain below must not stop early
+            bool drained = wait(&fin, 0);
+            if (!w_seen) drained = wait(&wbar, 0) && drained;
+            for (int sl = 0; sl < kTczRing; ++sl)
+                if (last_q[sl] > seen_q[sl]) drained = wait(&pfull[sl], (last_q[sl] >> 2) & 1) && drained;
+            if (!ok || !drained || saved) {
+                abort_flag = 1;
+                atomicExch(a.err, 1);
+            }
+        }
+    } else {
+        const unsigned row = tmem + ((unsigned)(32 * warp) << 16);
+        const int m = 32 * warp + lane;
+        const int x = x0 + (m & 7), y = y0 + (m >> 3);
+        const bool inside = x < a.X && y < a.Y;
+        float bv[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) bv[j] = (a.bias && j < a.cout) ? a.bias[j] : 0.f;
+        for (int zi = 0; zi < nz; ++zi) {
+            bool ok = false;
+            for (unsigned it = 0; it < kTcSpinW; ++it) {
+                if (mbar_try_wait(&mdone[zi & 1], (zi >> 1) & 1)) {
+                    ok = true;
+                    break;
+                }
+                if (abort_flag) break;
+            }
+            if (!__all_sync(0xffffffffu, ok)) {
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float v[NB];
+#pragma unroll
+            for (int c = 0; c < NB; c += 16) tmem_ld16(row + (unsigned)((zi & 1) * NB + c), v + c);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive1(&afree[zi & 1]);
+            if (inside) {
+                const long long node = (long long)((z0 + zi) * a.Y + y) * a.X + x;
+                float* o = a.out + b * a.out_bs + node * a.out_pitch;
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    if (j >= a.cout) break;
+                    float val = v[j] + bv[j];
+                    if (a.mode == 1) val = val > 0.f ? val : kSlope * val;
+                    o[j] = val;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 4)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
 }
 
 // Weight image of one stride-1 layer for k_conv_tc.  Forward (flip = 0): the
@@ -1255,6 +1458,7 @@ struct gmg_net {
     // tensor-core (TF32) stride-1 convolutions: per layer and direction
     // (0 forward, 1 backward data) the weight image and its GEMM blocking
     int arith = GMG_NET_FP32;
+    bool tcz = true;  // z-marching tensor-core kernel where a layer fits it (else one tile per CTA)
     float* img[kLayers][2] = {};
     int img_nb[kLayers][2] = {}, img_nblk[kLayers][2] = {}, img_nch[kLayers][2] = {};
     int* kerr = nullptr;  // sticky error word of the tensor-core kernels
@@ -1309,6 +1513,12 @@ LayerTable make_table(long long* total) {
 
 // ---- tensor-core convolution (stride 1)
 
+template <int NB>
+int tcz_attr() {
+    CU(cudaFuncSetAttribute(k_conv_tcz<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024 + 1024));
+    return GMG_OK;
+}
+
 int tc_nb(int cout) { return cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16); }
 
 template <int NB>
@@ -1325,6 +1535,9 @@ int alloc_images(gmg_net* net) {
     TRY(tc_attr<16>());
     TRY(tc_attr<32>());
     TRY(tc_attr<64>());
+    TRY(tcz_attr<16>());
+    TRY(tcz_attr<32>());
+    TRY(tcz_attr<64>());
     for (int l = 0; l < kLayers; ++l) {
         if (kDefs[l].stride != 1) continue;
         for (int dir = 0; dir < 1; ++dir) {
@@ -1390,6 +1603,64 @@ int launch_conv_tc(gmg_net* net, int l, int dir, const float* in, int in_pitch, 
         case 16: k_conv_tc<16><<<grid, 128, TcGeom<16>::SMEM, s>>>(tm, a); break;
         case 32: k_conv_tc<32><<<grid, 128, TcGeom<32>::SMEM, s>>>(tm, a); break;
         default: k_conv_tc<64><<<grid, 128, TcGeom<64>::SMEM, s>>>(tm, a); break;
+    }
+    note_launch();
+    return GMG_OK;
+}
+
+// Shared memory of k_conv_tcz for a layer (weights + four plane slots), or 0
+// when fewer than two CTAs would fit an SM: with a single CTA per SM the ring's
+// one plane of prefetch leaves the loads exposed, and the one-tile-per-CTA
+// kernel is faster (measured at 80^3: layer u0 307 us vs 189 us, while the
+// 16-channel layers take 81-86 us vs 94-97 us).
+size_t tcz_smem(int nb, int nch) {
+    const size_t wb = (size_t)nch * 27 * 32 * nb;
+    const size_t slot = (size_t)2 * nch * kTczSlabPitch;
+    const size_t total = wb + kTczRing * slot + 1024;
+    return total <= 113 * 1024 ? total : 0;
+}
+
+// Launches k_conv_tcz for the forward pass of stride-1 layer l; returns 1
+// (nothing launched) when the layer does not suit it.
+int launch_conv_tcz(gmg_net* net, int l, const float* in, int in_pitch, int cin, long long in_bs, int X, int Y, int Z,
+                    int B, float* out, int out_pitch, int cout, long long out_bs, const float* bias, int mode,
+                    cudaStream_t s) {
+    if (net->img_nblk[l][0] != 1) return 1;
+    const int nb = net->img_nb[l][0], nch = net->img_nch[l][0];
+    const size_t smem = tcz_smem(nb, nch);
+    if (!smem) return 1;
+    CUtensorMap tm;
+    const unsigned long long dims[5] = {(unsigned long long)cin, (unsigned long long)X, (unsigned long long)Y,
+                                        (unsigned long long)Z, (unsigned long long)B};
+    const unsigned long long st[4] = {4ULL * in_pitch, 4ULL * in_pitch * X, 4ULL * in_pitch * X * Y,
+                                      4ULL * (unsigned long long)in_bs};
+    const unsigned box[5] = {4, kTcHX, kTcHY, 1, 1};
+    if (!gmg::encode_f32_map_strided(&tm, in, 5, dims, st, box)) return 1;
+    const int tiles = ((X + 7) / 8) * ((Y + 15) / 16);
+    const int per_sm = std::max(1, (int)(228 * 1024 / smem));
+    int nzr = std::max(1, std::min(Z, (2 * 148 * per_sm + tiles * B - 1) / (tiles * B)));
+    const int zr = (Z + nzr - 1) / nzr;
+    nzr = (Z + zr - 1) / zr;
+    TczArgs a{};
+    a.out = out;
+    a.out_pitch = out_pitch;
+    a.cout = cout;
+    a.img = net->img[l][0];
+    a.bias = bias;
+    a.mode = mode;
+    a.X = X;
+    a.Y = Y;
+    a.Z = Z;
+    a.nch = nch;
+    a.nslab = 2 * nch;
+    a.zr = zr;
+    a.out_bs = out_bs;
+    a.err = net->kerr;
+    dim3 grid((unsigned)tiles, (unsigned)nzr, (unsigned)B);
+    switch (nb) {
+        case 16: k_conv_tcz<16><<<grid, 160, smem, s>>>(tm, a); break;
+        case 32: k_conv_tcz<32><<<grid, 160, smem, s>>>(tm, a); break;
+        default: k_conv_tcz<64><<<grid, 160, smem, s>>>(tm, a); break;
     }
     note_launch();
     return GMG_OK;
@@ -1471,8 +1742,12 @@ int conv_fwd(gmg_net* net, int l, const float* in, int in_pitch, long long in_bs
     a.in_bs = in_bs;
     a.out_bs = out_bs;
     if (net->arith == GMG_NET_TF32 && d.stride == 1) {
-        const int rc = launch_conv_tc(net, l, 0, in, in_pitch, d.cin, in_bs, X, Y, Z, B, out, out_pitch, cout, out_bs,
-                                      a.bias, nullptr, 0, 0, a.mode, 0, s);
+        int rc = net->tcz ? launch_conv_tcz(net, l, in, in_pitch, d.cin, in_bs, X, Y, Z, B, out, out_pitch, cout, out_bs,
+                                            a.bias, a.mode, s)
+                          : 1;
+        if (rc == 1)
+            rc = launch_conv_tc(net, l, 0, in, in_pitch, d.cin, in_bs, X, Y, Z, B, out, out_pitch, cout, out_bs, a.bias,
+                                nullptr, 0, 0, a.mode, 0, s);
         if (rc != 1) return rc;
     }
     if (d.stride == 2 && split) {
