@@ -383,3 +383,36 @@ def test_trained_network_gains_over_cold_start():
     assert all(r["cold_status"] == 0 and r["warm_status"] == 0 and r["warm_rel_residual"] <= 1e-6 for r in res)
     for r in res:
         assert r["warm_iterations"] <= r["cold_iterations"] + 1, r
+
+
+def test_network_argument_errors():
+    """Bad shapes and arguments come back as GMG_ERR_ARG before any device work."""
+    from paper_2604_26441_b300 import gmg
+    net = gmg.WarmNet(_t(_theta(11)))
+    x = torch.zeros(13 * 9 * 9, W.N_IN, device="cuda")
+    with pytest.raises(gmg.GMGError) as e:
+        net.forward((12, 8, 8), x)  # 12 is not a multiple of 8
+    assert e.value.code == -1
+    rho, fixed, f = _problem(16, 8, 8, 91)
+    S8 = gpu_solver(rho, 3.0, levels=2, smoother="jacobi", coarse_smoother=None, omega=0.5)
+    xs = [_t(W.node_features(16, 8, 8, rho, f, fixed).reshape(-1, W.N_IN))]
+    ts = [torch.zeros(17 * 9 * 9, 3, device="cuda")]
+    rho_o = inputs.filtered_random_density(16, 16, 8, 93)
+    S_other = gpu_solver(rho_o, 3.0, levels=2, smoother="jacobi", coarse_smoother=None, omega=0.5)
+    with pytest.raises(gmg.GMGError):
+        net.train_step((16, 8, 8), xs, ts, 1e-3, ops=[S_other])  # operator grid differs from the batch grid
+    net.train_step((16, 8, 8), xs, ts, 0.0, ops=[S8])  # the matching operator is accepted
+    with pytest.raises(gmg.GMGError):
+        net.train_step((16, 8, 8), xs, ts, float("nan"))
+    with pytest.raises(ValueError):
+        net.train_step((16, 8, 8), xs, [], 1e-3)
+    with pytest.raises(KeyError):
+        net.set_arith("fp16")
+    rho12 = inputs.filtered_random_density(12, 8, 8, 92)
+    S12 = gpu_solver(rho12, 3.0, levels=2, smoother="jacobi", coarse_smoother=None, omega=0.5)
+    with pytest.raises(gmg.GMGError):
+        net.warm_start(S12, _t(rho12), _t(inputs.tip_edge_load(12, 8, 8), torch.float64))
+    net.status()
+    # the network still works after the refused calls
+    g = net.forward((16, 8, 8), xs[0])
+    assert torch.isfinite(g).all()
