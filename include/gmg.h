@@ -60,7 +60,10 @@ extern "C" {
 #define GMG_SMOOTHER_JACOBI 0
 #define GMG_SMOOTHER_CHEBYSHEV 1
 
-/* Fine-level smoother arithmetic (gmg_options.fine_smoother). */
+/* Fine-level smoother arithmetic (gmg_options.fine_smoother).  Plain BF16
+ * makes the V-cycle an inexact, non-symmetric preconditioner: pair it with
+ * GMG_OUTER_FGMRES (under PCG it can stagnate); split BF16 (BF16X3) is close
+ * enough to FP32 for PCG. */
 #define GMG_FINE_FP32 0
 #define GMG_FINE_BF16X3 1
 #define GMG_FINE_BF16 2
@@ -95,7 +98,9 @@ typedef struct {
     int power_iters_coarse;      /* ... on assembled levels (10) */
     int chol_cutoff;             /* dense-Cholesky size limit for the coarsest level (5000) */
     int fused_coarse_nodes;      /* assembled levels with fewer nodes than this run, together with
-                                    the coarsest solve, as one persistent kernel (4096); 0 = off */
+                                    the coarsest solve, as one persistent cooperative kernel; 0 = off
+                                    (default: the per-level kernels, which inside the device-resident
+                                    PCG graph were faster at every size measured) */
     int bsr_tma_nodes;           /* assembled levels with at least this many nodes load their
                                     operator planes as TMA-staged shared-memory tiles;
                                     <= 0 (default) = never: levels of >= 65536 nodes stream one

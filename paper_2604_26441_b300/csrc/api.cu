@@ -780,7 +780,7 @@ void gmg_default_options(gmg_options* o) {
     o->power_iters_fine = 20;
     o->power_iters_coarse = 10;
     o->chol_cutoff = 5000;
-    o->fused_coarse_nodes = 4096;
+    o->fused_coarse_nodes = 0;
     o->bsr_tma_nodes = 0;
     o->device_loop = 1;
     o->ir_factor = 0.0;

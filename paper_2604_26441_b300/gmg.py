@@ -173,7 +173,7 @@ def _ptr(t, dtype, numel: int, name: str):
 def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coarse_smoother: str | None = "jacobi",
             coarse_degree: int | None = 2, omega: float = 0.5, coarse_omega: float | None = 0.5,
             alpha: float = 1.0 / 30.0, lambda_safety: float = 1.1, power_iters_fine: int = 20,
-            power_iters_coarse: int = 10, chol_cutoff: int = 5000, fused_coarse_nodes: int = 4096,
+            power_iters_coarse: int = 10, chol_cutoff: int = 5000, fused_coarse_nodes: int = 0,
             bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
             fine_smoother: str = "fp32", cycle: str = "V", outer: str = "pcg", restart: int = 32,
             stream: int | None = None) -> _Options:
@@ -203,7 +203,7 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
     return o
 
 
-def config_options(cfg, stream: int | None = None, fused_coarse_nodes: int = 4096,
+def config_options(cfg, stream: int | None = None, fused_coarse_nodes: int = 0,
                    bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
                    fine_smoother: str = "fp32", cycle: str = "V", outer: str = "pcg",
                    restart: int = 32) -> _Options:

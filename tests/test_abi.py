@@ -45,7 +45,7 @@ def test_status_strings_and_defaults(lib):
     lib.gmg_default_options(ctypes.byref(o))
     assert o.levels == 4 and o.degree == 2 and o.power_iters_fine == 20 and o.power_iters_coarse == 10
     assert abs(o.cheb_alpha - 1 / 30) < 1e-15 and o.chol_cutoff == 5000
-    assert o.fused_coarse_nodes == 4096 and o.bsr_tma_nodes == 0 and o.device_loop == 1 and o.ir_factor == 0.0 and o.fine_smoother == 0
+    assert o.fused_coarse_nodes == 0 and o.bsr_tma_nodes == 0 and o.device_loop == 1 and o.ir_factor == 0.0 and o.fine_smoother == 0
     assert o.cycle_index == 1 and o.outer == 0 and o.restart == 32
 
 

@@ -478,16 +478,19 @@ def test_tensor_core_smoother_matches_oracle(mode, tol, name, nx, ny, nz, levels
     assert np.all(xs[fixed == 1] == 0)
 
 
-@pytest.mark.parametrize("mode,extra", [("bf16x3", 1), ("bf16", 6)])
+@pytest.mark.parametrize("mode,extra,outer", [("bf16x3", 1, "pcg"), ("bf16", 6, "fgmres")])
 @pytest.mark.parametrize("cfg_name", ["c0", "c1", "c2"])
-def test_tensor_core_smoother_solves(mode, extra, cfg_name):
-    """PCG with the tensor-core fine smoother converges to the FP64-checked
-    tolerance; split BF16 needs at most one more iteration than the FP32 smoother."""
+def test_tensor_core_smoother_solves(mode, extra, outer, cfg_name):
+    """The tensor-core fine smoother converges to the FP64-checked tolerance:
+    split BF16 under PCG with at most one more iteration than the FP32
+    smoother; plain BF16 under FGMRES, the outer solver the paper pairs it
+    with (its rounding makes the V-cycle too far from a symmetric operator for
+    CG: with PCG it stagnated at 6e-5 on 100^3 with the per-level coarse path)."""
     c = inputs.CONFIGS[cfg_name]
     f = c.load()
     iters = {}
     for sm in ("fp32", mode):
-        S = gpu_solver(c.rho(), c.p, **config_opts(c), fine_smoother=sm)
+        S = gpu_solver(c.rho(), c.p, **config_opts(c), fine_smoother=sm, outer=outer)
         u, info = S.solve(_t(f, torch.float64), tol=1e-6, maxit=200)
         assert info["status"] == 0 and info["rel_residual"] < 1e-6
         iters[sm] = info["iterations"]
