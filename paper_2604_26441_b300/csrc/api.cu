@@ -534,6 +534,11 @@ void loop_free(gmg_handle* h) {
     h->loop_exec = nullptr;
     h->loop_graph = nullptr;
     h->loop_u = nullptr;
+    for (auto& e : h->loop_cache) {
+        cudaGraphExecDestroy(e.ex);
+        cudaGraphDestroy(e.g);
+    }
+    h->loop_cache.clear();
 }
 
 // Captures the device-resident PCG loop for iterate u:
@@ -605,8 +610,8 @@ int ensure_cap_stream(gmg_handle* h) {
     return GMG_OK;
 }
 
-int loop_build(gmg_handle* h, double* u) {
-    loop_free(h);
+// Captures the loop for u into the handle's current slot (which must be empty).
+int loop_capture(gmg_handle* h, double* u) {
     TRY(ensure_cap_stream(h));
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ex = nullptr;
@@ -624,6 +629,41 @@ int loop_build(gmg_handle* h, double* u) {
     h->loop_prefix_kernels = pre;
     h->loop_body_kernels = bod;
     return GMG_OK;
+}
+
+constexpr size_t kLoopCache = 3;  // loops kept besides the current one
+
+// Makes the loop of iterate u the current one: taken from the cache when it
+// was captured before, else captured now; the previous current loop is kept
+// in the cache (the least recently used one is dropped beyond kLoopCache).
+int loop_select(gmg_handle* h, double* u) {
+    if (h->loop_exec && h->loop_u == u) return GMG_OK;
+    auto park = [&] {
+        if (!h->loop_exec) return;
+        h->loop_cache.push_back({h->loop_u, h->loop_graph, h->loop_exec, h->loop_prefix_kernels, h->loop_body_kernels});
+        h->loop_exec = nullptr;
+        h->loop_graph = nullptr;
+        h->loop_u = nullptr;
+        if (h->loop_cache.size() > kLoopCache) {
+            cudaGraphExecDestroy(h->loop_cache.front().ex);
+            cudaGraphDestroy(h->loop_cache.front().g);
+            h->loop_cache.erase(h->loop_cache.begin());
+        }
+    };
+    for (size_t i = 0; i < h->loop_cache.size(); ++i)
+        if (h->loop_cache[i].u == u) {
+            const gmg_handle::LoopGraph e = h->loop_cache[i];
+            h->loop_cache.erase(h->loop_cache.begin() + (long)i);
+            park();
+            h->loop_u = e.u;
+            h->loop_graph = e.g;
+            h->loop_exec = e.ex;
+            h->loop_prefix_kernels = e.pre;
+            h->loop_body_kernels = e.body;
+            return GMG_OK;
+        }
+    park();
+    return loop_capture(h, u);
 }
 
 // ---- diagnostics: extreme eigenvalues of a symmetric tridiagonal matrix by
@@ -954,7 +994,7 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     auto inner_target = [&](double rel_start) { return irf > 0.0 ? std::max(tol, irf * rel_start) : tol; };
     double target = inner_target(rel);
     if (maxit > 0 && h->opt.device_loop && !h->loop_unavailable && h->loop_u != u) {
-        if (loop_build(h, u) != GMG_OK) h->loop_unavailable = true;  // e.g. no graph support: host loop
+        if (loop_select(h, u) != GMG_OK) h->loop_unavailable = true;  // e.g. no graph support: host loop
     }
     if (maxit > 0 && h->opt.device_loop && h->loop_exec && h->loop_u == u) {
         // device-resident loop: one graph launch per convergence candidate
@@ -1204,6 +1244,7 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out) {
     h->loop_graph = nullptr;
     h->loop_exec = nullptr;
     h->loop_u = nullptr;
+    h->loop_cache.clear();  // the source's graphs stay the source's
     h->loop_unavailable = false;
     h->fg_V = h->fg_Z = nullptr;
     h->fg_h = nullptr;

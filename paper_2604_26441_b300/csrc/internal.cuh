@@ -230,6 +230,15 @@ struct gmg_handle {
     const double* loop_u = nullptr;             // iterate the captured graph updates
     unsigned long long loop_prefix_kernels = 0, loop_body_kernels = 0;
     bool loop_unavailable = false;              // capture failed once: use the host loop
+    // loops captured for other iterate buffers (least recently used first), so
+    // that a caller alternating between a few u buffers does not recapture
+    struct LoopGraph {
+        const double* u;
+        cudaGraph_t g;
+        cudaGraphExec_t ex;
+        unsigned long long pre, body;
+    };
+    std::vector<LoopGraph> loop_cache;
     // restarted FGMRES (outer = 1): Arnoldi basis V (restart + 1 vectors),
     // preconditioned directions Z (restart vectors), Hessenberg column (device)
     float* fg_V = nullptr;

@@ -664,3 +664,20 @@ def test_autotune_keeps_operator_results(cfg_name):
         assert rel_l2(ua.cpu().numpy(), ub.cpu().numpy()) < 1e-5
     finally:
         S.autotune(reps=0)
+
+
+def test_alternating_iterate_buffers_reuse_their_loop_graphs():
+    """Solves into several u buffers in turn (more than the handle keeps
+    captured loops for) give bitwise the same iterates and solutions as
+    solves into one buffer."""
+    cfg = inputs.CONFIGS["c1"]
+    S = gpu_solver(cfg.rho(), cfg.p, **config_opts(cfg))
+    f = _t(cfg.load(), torch.float64)
+    ref, iref = S.solve(f, None, tol=cfg.tol, maxit=cfg.maxit)
+    us = [torch.zeros_like(f) for _ in range(5)]
+    for rnd in range(2):
+        for u in us:
+            u.zero_()
+            _, info = S.solve(f, u, tol=cfg.tol, maxit=cfg.maxit)
+            assert info["iterations"] == iref["iterations"] and info["status"] == 0
+            assert torch.equal(u, ref)
