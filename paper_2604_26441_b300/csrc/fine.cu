@@ -127,6 +127,7 @@ constexpr int kRing = 4;
 
 template <int BX, int BY, int MODE, bool DOT>
 __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zchunk) {
+    pdl_entry();
     constexpr int NT = BX * BY;
     constexpr int ROW = (BX + 1) * 3;           // floats per staged plane row
     constexpr int PLANE = (BY + 1) * ROW;       // floats per staged plane
@@ -776,6 +777,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine_tc(FineArgs a, int zchunk) 
 // Copies x with the fixed DOFs of the fine level set to 0 (operands supplied by
 // a caller may hold values there; the operator ignores them).
 __global__ void k_mask_copy(const float* x, const uint8_t* mask, long long nn, float* out) {
+    pdl_entry();
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 3 * nn; q += (long long)gridDim.x * blockDim.x)
         out[q] = fixed_bit(mask[q / 3], (int)(q % 3)) ? 0.f : x[q];
 }
@@ -867,8 +869,8 @@ FinePlan plan_fine(int nx, int ny, int nz) {
 
 template <int MODE, bool DOT>
 void launch_shape(const FinePlan& pl, const FineArgs& a, const GHat& G, cudaStream_t s) {
-    if (pl.tile == 0) k_fine<32, 8, MODE, DOT><<<pl.grid, dim3(32, 8), 0, s>>>(a, G, pl.zc);
-    else k_fine<16, 16, MODE, DOT><<<pl.grid, dim3(16, 16), 0, s>>>(a, G, pl.zc);
+    if (pl.tile == 0) pdl_launch(k_fine<32, 8, MODE, DOT>, dim3(pl.grid), dim3(dim3(32, 8)), 0, s, a, G, pl.zc);
+    else pdl_launch(k_fine<16, 16, MODE, DOT>, dim3(pl.grid), dim3(dim3(16, 16)), 0, s, a, G, pl.zc);
 }
 
 }  // namespace
@@ -917,7 +919,7 @@ void launch_fine(int mode, int dot, int mask_in, const FineArgs& a_in, const GHa
     if (mask_in && a.scratch) {
         const long long nn = (long long)(a.nx + 1) * (a.ny + 1) * (a.nz + 1);
         note_launch();
-        k_mask_copy<<<(int)std::min<long long>((3 * nn + 255) / 256, 148 * 8), 256, 0, s>>>(a.xin, a.mask, nn,
+        pdl_launch(k_mask_copy, dim3((int)std::min<long long>((3 * nn + 255) / 256, 148 * 8)), dim3(256), 0, s, a.xin, a.mask, nn,
                                                                                              a.scratch);
         a.xin = a.scratch;
     }

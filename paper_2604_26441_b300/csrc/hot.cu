@@ -49,6 +49,7 @@ __device__ __forceinline__ bool fixed_bit(uint8_t m, int c) { return (m >> c) & 
 
 // First smoother step from x = 0: x_1 = c_a D^{-1} b (no operator application).
 __global__ void k_fine_smooth0(FineArgs a) {
+    pdl_entry();
     const long long NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
     const long long nn = NX * NY * NZ;
     const float ca = (float)a.coef[1];
@@ -130,6 +131,7 @@ __device__ __forceinline__ void bsr_epilogue(const BsrArgs& a, int n, const floa
 // out-of-grid backward terms are scaled by 0.
 template <int MODE, bool DOT, int NTB>
 __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
+    pdl_entry();
     const int nn = (int)a.nn;
     const int n = blockIdx.x * NTB + threadIdx.x;
     DSAcc dotv;
@@ -405,6 +407,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_bsr_pipe(const __grid_const
 // fixed order.
 template <int MODE, bool DOT, int NS>
 __global__ void __launch_bounds__(256) k_bsr_ks(BsrArgs a) {
+    pdl_entry();
     constexpr int NPB = 256 / NS;
     constexpr int NQ = (27 + NS - 1) / NS;
     __shared__ float part[NS][NPB][3];
@@ -466,6 +469,7 @@ __global__ void __launch_bounds__(256) k_bsr_ks(BsrArgs a) {
 }
 
 __global__ void k_bsr_smooth0(BsrArgs a) {
+    pdl_entry();
     const float ca = (float)a.coef[1];
     const long long n3 = 3 * a.nn;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3;
@@ -500,6 +504,7 @@ __device__ __forceinline__ void coarse_parents2(int f, int nf, int idx[2], float
 
 __global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz, const uint8_t* cmask,
                            const float* fine, float* coarse) {
+    pdl_entry();
     const int CX = cnx + 1, CY = cny + 1, nn = CX * CY * (cnz + 1);
     const int FX = fnx + 1, FY = fny + 1;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -531,6 +536,7 @@ __global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
 
 __global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, const uint8_t* fmask,
                               const float* coarse, float* fine) {
+    pdl_entry();
     const int FX = fnx + 1, FY = fny + 1, nn = FX * FY * (fnz + 1);
     const int CX = cnx + 1, CY = cny + 1;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -566,6 +572,7 @@ __global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, const
 constexpr int kCoarseRowsPerBlock = 8;
 __global__ void __launch_bounds__(256) k_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b,
                                                       float* x) {
+    pdl_entry();
     extern __shared__ double bs[];
     for (int j = threadIdx.x; j < nL; j += blockDim.x) bs[j] = (double)b[free_idx[j]];
     __syncthreads();
@@ -591,6 +598,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int nL, const int* free_id
 // summation order are independent of timing).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVecThreads) k_dot_f32(const float* a, const float* b, long long n, double* partial) {
+    pdl_entry();
     DSAcc acc;
     for (long long q = blockIdx.x * (long long)kVecThreads + threadIdx.x; q < n; q += (long long)gridDim.x * kVecThreads)
         acc.add_prod(a[q], b[q]);
@@ -600,6 +608,7 @@ __global__ void __launch_bounds__(kVecThreads) k_dot_f32(const float* a, const f
 
 __global__ void __launch_bounds__(kVecThreads) k_dot_f64_masked(const double* a, const double* b, const uint8_t* mask,
                                                                 long long nn, double* partial) {
+    pdl_entry();
     double s = 0.0;
     for (long long q = blockIdx.x * (long long)kVecThreads + threadIdx.x; q < 3 * nn; q += (long long)gridDim.x * kVecThreads)
         if (!fixed_bit(mask[q / 3], (int)(q % 3))) s += a[q] * b[q];
@@ -608,6 +617,7 @@ __global__ void __launch_bounds__(kVecThreads) k_dot_f64_masked(const double* a,
 }
 
 __global__ void __launch_bounds__(kVecThreads) k_finalize(const double* partial, int n, double* sc, int slot, int op) {
+    pdl_entry();
     double s = 0.0;
     for (int q = threadIdx.x; q < n; q += kVecThreads) s += partial[q];
     s = block_sum<kVecThreads>(s, threadIdx.x);
@@ -628,6 +638,7 @@ __global__ void __launch_bounds__(kVecThreads) k_finalize(const double* partial,
 // entries per thread and iteration with 16-byte loads when every pointer allows.
 __global__ void __launch_bounds__(kVecThreads) k_pcg_update(double* u, float* r, const float* p, const float* q, long long n,
                                                             const double* sc, double* partial, int vec4) {
+    pdl_entry();
     const double alpha = sc[SC_ALPHA];
     const float af = (float)alpha;
     DSAcc acc;
@@ -669,12 +680,14 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(double* u, float* r,
 }
 
 __global__ void k_p_update(float* p, const float* z, long long n, const double* sc) {
+    pdl_entry();
     const float beta = (float)sc[SC_BETA];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         p[i] = fmaf(beta, p[i], z[i]);
 }
 
 __global__ void __launch_bounds__(kVecThreads) k_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial) {
+    pdl_entry();
     double s = 0.0;
     for (long long q = blockIdx.x * (long long)kVecThreads + threadIdx.x; q < 3 * nn; q += (long long)gridDim.x * kVecThreads) {
         if (fixed_bit(mask[q / 3], (int)(q % 3))) u[q] = 0.0;
@@ -686,6 +699,7 @@ __global__ void __launch_bounds__(kVecThreads) k_mask_u64(double* u, const uint8
 
 // y += sign * (*coef) * x (FP32 vectors, coefficient from device memory).
 __global__ void k_axpy_dev(float* y, const float* x, long long n, const double* coef, float sign) {
+    pdl_entry();
     const float c = sign * (float)coef[0];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = fmaf(c, x[i], y[i]);
@@ -693,11 +707,13 @@ __global__ void k_axpy_dev(float* y, const float* x, long long n, const double* 
 
 // u += a * z, accumulated in FP64.
 __global__ void k_axpy_u64(double* u, const float* z, long long n, double a) {
+    pdl_entry();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         u[i] = fma(a, (double)z[i], u[i]);
 }
 
 __global__ void k_loop_check(double* sc, cudaGraphConditionalHandle cond) {
+    pdl_entry();
     if (threadIdx.x != 0) return;
     const double k = sc[SC_IT] + 1.0;
     sc[SC_IT] = k;
@@ -708,11 +724,13 @@ __global__ void k_loop_check(double* sc, cudaGraphConditionalHandle cond) {
 
 // r = f on free DOFs (as FP32), 0 on fixed ones: the residual of the zero iterate.
 __global__ void __launch_bounds__(kVecThreads) k_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r) {
+    pdl_entry();
     for (long long q = blockIdx.x * (long long)kVecThreads + threadIdx.x; q < 3 * nn; q += (long long)gridDim.x * kVecThreads)
         r[q] = fixed_bit(mask[q / 3], (int)(q % 3)) ? 0.f : (float)f[q];
 }
 
 __global__ void k_scale_inv_sqrt(float* v, long long n, const double* sc, int slot) {
+    pdl_entry();
     const double s = sc[slot];
     if (!(s > 0.0) || !isfinite(s)) return;
     const float f = (float)(1.0 / sqrt(s));
@@ -733,6 +751,7 @@ __device__ __forceinline__ float fine_diag(const float* E, int nx, int ny, int n
 
 __global__ void k_scale_invdiag_fine(const float* y, float* w, const float* E, const uint8_t* mask, int nx, int ny,
                                      int nz, float kd) {
+    pdl_entry();
     const long long NX = nx + 1, NY = ny + 1, nn = NX * NY * (nz + 1);
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
@@ -744,12 +763,14 @@ __global__ void k_scale_invdiag_fine(const float* y, float* w, const float* E, c
 }
 
 __global__ void k_scale_invdiag_bsr(const float* y, float* w, const float* invdiag, long long n) {
+    pdl_entry();
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
         w[q] = invdiag[q] * y[q];
 }
 
 __global__ void __launch_bounds__(kVecThreads) k_diag_dot_fine(const float* v, const float* E, const uint8_t* mask, int nx,
                                                                int ny, int nz, float kd, double* partial) {
+    pdl_entry();
     const long long NX = nx + 1, NY = ny + 1, nn = NX * NY * (nz + 1);
     double s = 0.0;
     for (long long n = blockIdx.x * (long long)kVecThreads + threadIdx.x; n < nn; n += (long long)gridDim.x * kVecThreads) {
@@ -765,6 +786,7 @@ __global__ void __launch_bounds__(kVecThreads) k_diag_dot_fine(const float* v, c
 }
 
 __global__ void __launch_bounds__(kVecThreads) k_diag_dot_bsr(const float* v, const float* invdiag, long long n, double* partial) {
+    pdl_entry();
     double s = 0.0;
     for (long long q = blockIdx.x * (long long)kVecThreads + threadIdx.x; q < n; q += (long long)gridDim.x * kVecThreads)
         if (invdiag[q] != 0.f) s += (double)v[q] * (double)v[q] / (double)invdiag[q];
@@ -775,6 +797,7 @@ __global__ void __launch_bounds__(kVecThreads) k_diag_dot_bsr(const float* v, co
 // Power-iteration start vector: v_i = ((i * 2654435761) mod 2^32) / 2^32 - 0.5 over
 // the level's DOF index i, 0 on fixed DOFs.
 __global__ void k_power_start(float* v, const uint8_t* mask, long long nn) {
+    pdl_entry();
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 3 * nn; q += (long long)gridDim.x * blockDim.x) {
         const unsigned long long h = ((unsigned long long)q * 2654435761ull) & 0xffffffffull;
         const double val = (double)h / 4294967296.0 - 0.5;
@@ -789,7 +812,7 @@ __global__ void k_power_start(float* v, const uint8_t* mask, long long nn) {
 // ---------------------------------------------------------------------------
 void launch_fine_smooth0(const FineArgs& a, cudaStream_t s) {
     note_launch();
-    k_fine_smooth0<<<kVecBlocks * 2, kVecThreads, 0, s>>>(a);
+    pdl_launch(k_fine_smooth0, dim3(kVecBlocks * 2), dim3(kVecThreads), 0, s, a);
 }
 
 // Standalone launches of the assembled-level operator.  Levels with tensor maps
@@ -849,25 +872,25 @@ void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
     const int g = bsr_grid_blocks(a.nn, false, a.kind);
     if (bsr_streams(a.nn, a.kind)) {
         if (mode == FM_APPLY) {
-            if (dot) k_bsr<FM_APPLY, true, 256><<<g, 256, 0, s>>>(a);
-            else k_bsr<FM_APPLY, false, 256><<<g, 256, 0, s>>>(a);
+            if (dot) pdl_launch(k_bsr<FM_APPLY, true, 256>, dim3(g), dim3(256), 0, s, a);
+            else pdl_launch(k_bsr<FM_APPLY, false, 256>, dim3(g), dim3(256), 0, s, a);
         } else if (mode == FM_SMOOTH) {
-            if (dot) k_bsr<FM_SMOOTH, true, 256><<<g, 256, 0, s>>>(a);
-            else k_bsr<FM_SMOOTH, false, 256><<<g, 256, 0, s>>>(a);
+            if (dot) pdl_launch(k_bsr<FM_SMOOTH, true, 256>, dim3(g), dim3(256), 0, s, a);
+            else pdl_launch(k_bsr<FM_SMOOTH, false, 256>, dim3(g), dim3(256), 0, s, a);
         } else {
-            k_bsr<FM_RESID, false, 256><<<g, 256, 0, s>>>(a);
+            pdl_launch(k_bsr<FM_RESID, false, 256>, dim3(g), dim3(256), 0, s, a);
         }
         return;
     }
     constexpr int NS = kKsSlices;
     if (mode == FM_APPLY) {
-        if (dot) k_bsr_ks<FM_APPLY, true, NS><<<g, 256, 0, s>>>(a);
-        else k_bsr_ks<FM_APPLY, false, NS><<<g, 256, 0, s>>>(a);
+        if (dot) pdl_launch(k_bsr_ks<FM_APPLY, true, NS>, dim3(g), dim3(256), 0, s, a);
+        else pdl_launch(k_bsr_ks<FM_APPLY, false, NS>, dim3(g), dim3(256), 0, s, a);
     } else if (mode == FM_SMOOTH) {
-        if (dot) k_bsr_ks<FM_SMOOTH, true, NS><<<g, 256, 0, s>>>(a);
-        else k_bsr_ks<FM_SMOOTH, false, NS><<<g, 256, 0, s>>>(a);
+        if (dot) pdl_launch(k_bsr_ks<FM_SMOOTH, true, NS>, dim3(g), dim3(256), 0, s, a);
+        else pdl_launch(k_bsr_ks<FM_SMOOTH, false, NS>, dim3(g), dim3(256), 0, s, a);
     } else {
-        k_bsr_ks<FM_RESID, false, NS><<<g, 256, 0, s>>>(a);
+        pdl_launch(k_bsr_ks<FM_RESID, false, NS>, dim3(g), dim3(256), 0, s, a);
     }
 }
 
@@ -945,7 +968,7 @@ void launch_bsr_smooth0(const BsrArgs& a, cudaStream_t s) {
     const long long n3 = 3 * a.nn;
     const int g = (int)std::min<long long>((n3 + kVecThreads - 1) / kVecThreads, kVecBlocks * 2);
     note_launch();
-    k_bsr_smooth0<<<g, kVecThreads, 0, s>>>(a);
+    pdl_launch(k_bsr_smooth0, dim3(g), dim3(kVecThreads), 0, s, a);
 }
 
 static int grid_for(long long n) {
@@ -954,12 +977,12 @@ static int grid_for(long long n) {
 
 void launch_restrict(const Level& f, const Level& c, const float* fine, float* coarse, cudaStream_t s) {
     note_launch();
-    k_restrict<<<(int)((c.nn + 127) / 128), 128, 0, s>>>(f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, c.mask, fine, coarse);
+    pdl_launch(k_restrict, dim3((int)((c.nn + 127) / 128)), dim3(128), 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, c.mask, fine, coarse);
 }
 
 void launch_prolong_add(const Level& f, const Level& c, const float* coarse, float* fine, cudaStream_t s) {
     note_launch();
-    k_prolong_add<<<(int)((f.nn + 255) / 256), 256, 0, s>>>(f.nx, f.ny, f.nz, c.nx, c.ny, f.mask, coarse, fine);
+    pdl_launch(k_prolong_add, dim3((int)((f.nn + 255) / 256)), dim3(256), 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, f.mask, coarse, fine);
 }
 
 void launch_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b, float* x,
@@ -967,8 +990,7 @@ void launch_coarse_solve(int nL, const int* free_idx, const double* Ainv, const 
     cudaMemsetAsync(x, 0, sizeof(float) * n_dof, s);
     if (nL > 0) {
         note_launch();
-        k_coarse_solve<<<(nL + kCoarseRowsPerBlock - 1) / kCoarseRowsPerBlock, 32 * kCoarseRowsPerBlock,
-                         sizeof(double) * nL, s>>>(nL, free_idx, Ainv, b, x);
+        pdl_launch(k_coarse_solve, dim3((nL + kCoarseRowsPerBlock - 1) / kCoarseRowsPerBlock), dim3(32 * kCoarseRowsPerBlock), sizeof(double) * nL, s, nL, free_idx, Ainv, b, x);
     }
 }
 
@@ -976,18 +998,18 @@ int vec_grid_blocks() { return kVecBlocks; }
 
 void launch_dot_f32(const float* a, const float* b, long long n, double* partial, cudaStream_t s) {
     note_launch();
-    k_dot_f32<<<kVecBlocks, kVecThreads, 0, s>>>(a, b, n, partial);
+    pdl_launch(k_dot_f32, dim3(kVecBlocks), dim3(kVecThreads), 0, s, a, b, n, partial);
 }
 
 void launch_dot_f64_masked(const double* a, const double* b, const uint8_t* mask, long long nn, double* partial,
                            cudaStream_t s) {
     note_launch();
-    k_dot_f64_masked<<<kVecBlocks, kVecThreads, 0, s>>>(a, b, mask, nn, partial);
+    pdl_launch(k_dot_f64_masked, dim3(kVecBlocks), dim3(kVecThreads), 0, s, a, b, mask, nn, partial);
 }
 
 void launch_finalize(const double* partial, int n, double* sc, int slot, int op, cudaStream_t s) {
     note_launch();
-    k_finalize<<<1, kVecThreads, 0, s>>>(partial, n, sc, slot, op);
+    pdl_launch(k_finalize, dim3(1), dim3(kVecThreads), 0, s, partial, n, sc, slot, op);
 }
 
 void launch_pcg_update(double* u, float* r, const float* p, const float* q, long long n, const double* sc,
@@ -995,42 +1017,42 @@ void launch_pcg_update(double* u, float* r, const float* p, const float* q, long
     note_launch();
     const bool vec4 = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(p) |
                         reinterpret_cast<uintptr_t>(q)) & 15) == 0;
-    k_pcg_update<<<kVecBlocks, kVecThreads, 0, s>>>(u, r, p, q, n, sc, partial, vec4 ? 1 : 0);
+    pdl_launch(k_pcg_update, dim3(kVecBlocks), dim3(kVecThreads), 0, s, u, r, p, q, n, sc, partial, vec4 ? 1 : 0);
 }
 
 void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s) {
     note_launch();
-    k_p_update<<<grid_for(n), 256, 0, s>>>(p, z, n, sc);
+    pdl_launch(k_p_update, dim3(grid_for(n)), dim3(256), 0, s, p, z, n, sc);
 }
 
 void launch_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial, cudaStream_t s) {
     note_launch();
-    k_mask_u64<<<kVecBlocks, kVecThreads, 0, s>>>(u, mask, nn, partial);
+    pdl_launch(k_mask_u64, dim3(kVecBlocks), dim3(kVecThreads), 0, s, u, mask, nn, partial);
 }
 
 void launch_axpy_dev(float* y, const float* x, long long n, const double* coef, float sign, cudaStream_t s) {
     note_launch();
-    k_axpy_dev<<<grid_for(n), 256, 0, s>>>(y, x, n, coef, sign);
+    pdl_launch(k_axpy_dev, dim3(grid_for(n)), dim3(256), 0, s, y, x, n, coef, sign);
 }
 
 void launch_axpy_u64(double* u, const float* z, long long n, double a, cudaStream_t s) {
     note_launch();
-    k_axpy_u64<<<grid_for(n), 256, 0, s>>>(u, z, n, a);
+    pdl_launch(k_axpy_u64, dim3(grid_for(n)), dim3(256), 0, s, u, z, n, a);
 }
 
 void launch_loop_check(double* sc, cudaGraphConditionalHandle cond, cudaStream_t s) {
     note_launch();
-    k_loop_check<<<1, 32, 0, s>>>(sc, cond);
+    pdl_launch(k_loop_check, dim3(1), dim3(32), 0, s, sc, cond);
 }
 
 void launch_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r, cudaStream_t s) {
     note_launch();
-    k_cast_masked<<<kVecBlocks, kVecThreads, 0, s>>>(f, mask, nn, r);
+    pdl_launch(k_cast_masked, dim3(kVecBlocks), dim3(kVecThreads), 0, s, f, mask, nn, r);
 }
 
 void launch_scale_by_inv_sqrt(float* v, long long n, const double* sc, int slot, cudaStream_t s) {
     note_launch();
-    k_scale_inv_sqrt<<<grid_for(n), 256, 0, s>>>(v, n, sc, slot);
+    pdl_launch(k_scale_inv_sqrt, dim3(grid_for(n)), dim3(256), 0, s, v, n, sc, slot);
 }
 
 void launch_scale_invdiag_fine(const float* y, float* w, const float* E, const uint8_t* mask, int nx, int ny,

@@ -140,6 +140,31 @@ struct DSAcc {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// ---- programmatic dependent launch: kernels of the solve path start with
+// pdl_entry() -- wait until the grids they depend on have completed and their
+// writes are visible, then let the next kernel in the stream begin launching --
+// and are launched with pdl_launch, so that consecutive kernels overlap their
+// launch latency instead of serialising it.  A kernel launched without the
+// attribute passes pdl_entry() at once.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ---- TMA and mbarrier primitives (inline PTX, sm_90+ forms; this build targets sm_103a)
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 

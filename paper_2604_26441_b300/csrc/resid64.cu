@@ -38,6 +38,7 @@ __device__ __forceinline__ void face_diffs(double u00, double u10, double u01, d
 __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,
                                                    const double* f, const double* uvec, double* r64, float* r32,
                                                    const double* sc, double* partial, GHat64 G, int zchunk) {
+    pdl_entry();
     __shared__ double sp[2][BY + 1][(BX + 1) * 3];
     __shared__ double sx[2][BY][BX * 3];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
@@ -259,7 +260,7 @@ void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t*
     int zc = 0;
     const dim3 g = resid_grid(nx, ny, nz, &zc);
     note_launch();
-    k_resid64<<<g, dim3(BX, BY), 0, s>>>(nx, ny, nz, E, mask, f, u, r64, r32, sc, partial, G, zc);
+    pdl_launch(k_resid64, dim3(g), dim3(dim3(BX, BY)), 0, s, nx, ny, nz, E, mask, f, u, r64, r32, sc, partial, G, zc);
 }
 
 }  // namespace gmg
