@@ -277,10 +277,11 @@ typedef struct {
     int model_tile, model_zchunk;  /* the cost model's choice (used without tuning) */
     int fine_candidates;         /* plans timed */
     double fine_us, model_us;    /* one fine smoothing step: tuned plan, model plan (median of reps) */
-    int bsr_kind[16];            /* per level: 0 streaming, 1 K-split, -1 not tuned (fine level,
-                                    TMA-staged levels, levels inside the fused lower V-cycle) */
+    int bsr_kind[16];            /* per level: 0 streaming (a thread per node), 1 / 2 / 3 K-split with
+                                    8 / 2 / 4 slices per node, -1 not tuned (fine level, TMA-staged
+                                    levels, levels inside the fused lower V-cycle) */
     double bsr_us[16];           /* chosen kernel, one smoothing step */
-    double bsr_alt_us[16];       /* the other kernel */
+    double bsr_alt_us[16];       /* the fastest other kernel */
 } gmg_tuning;
 
 /* Measures the launch shapes of the handle's hot kernels on its own operands
@@ -288,8 +289,8 @@ typedef struct {
  * (candidates of both tile shapes and z-chunks from the whole depth down to 4
  * planes, timed as fused Chebyshev/Jacobi smoothing steps; the choice holds
  * for every handle of that fine grid in this process), and per assembled
- * level outside the TMA-staged and fused paths the streaming or the K-split
- * SpMV kernel (kept in this handle).  The operator's results do not depend on
+ * level outside the TMA-staged and fused paths the streaming SpMV kernel or
+ * the K-split one with 8, 2 or 4 slices per node (kept in this handle).  The operator's results do not depend on
  * these shapes (each node's arithmetic is the same); reduction partial sums
  * are grouped differently.  reps: timed launches per candidate (>= 1); 0
  * returns to the cost model's plan and the size rule.  Drops the handle's

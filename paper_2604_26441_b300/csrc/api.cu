@@ -340,7 +340,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     // (the kernel of a level is chosen later or by gmg_autotune: size for
     // every kernel, and leave room for the fine kernel's tuning candidates)
     for (int li = 1; li < L; ++li)
-        for (int kind = 0; kind < 2; ++kind)
+        for (int kind = 0; kind < 4; ++kind)
             maxp = std::max({maxp, bsr_grid_blocks(h->lev[li].nn, true), bsr_grid_blocks(h->lev[li].nn, false, kind)});
     maxp = std::max(maxp, 4096);
     h->max_partials = maxp;
@@ -1148,8 +1148,8 @@ int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
     for (int li = 1; li < h->L - 1 && li < 16 && rc == GMG_OK; ++li) {
         Level& l = h->lev[li];
         if (l.tma || li >= fused_start) continue;
-        double us[2] = {0.0, 0.0};
-        for (int kind = 0; kind < 2 && rc == GMG_OK; ++kind) {
+        double us[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int kind = 0; kind < 4 && rc == GMG_OK; ++kind) {
             l.bsr_kind = kind;
             BsrArgs a = bsr_args(h, li);
             a.xin = l.x;
@@ -1160,10 +1160,16 @@ int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
             a.step = 0;
             rc = timed([&] { launch_bsr(FM_SMOOTH, 0, a, s); }, us[kind]);
         }
-        l.bsr_kind = us[1] < us[0] ? 1 : 0;
-        t.bsr_kind[li] = l.bsr_kind;
-        t.bsr_us[li] = us[l.bsr_kind];
-        t.bsr_alt_us[li] = us[1 - l.bsr_kind];
+        int best = 0;
+        for (int kind = 1; kind < 4; ++kind)
+            if (us[kind] < us[best]) best = kind;
+        int second = best == 0 ? 1 : 0;
+        for (int kind = 0; kind < 4; ++kind)
+            if (kind != best && us[kind] < us[second]) second = kind;
+        l.bsr_kind = best;
+        t.bsr_kind[li] = best;
+        t.bsr_us[li] = us[best];
+        t.bsr_alt_us[li] = us[second];
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -836,12 +836,33 @@ int pipe_blocks(long long nn) {
     return (int)std::min<long long>(tiles, sms);
 }
 
-bool bsr_streams(long long nn, int kind) { return kind < 0 ? nn >= kBsrStreamLevel : kind == 0; }
+// Slices per node of the level's kernel: 0 = the streaming kernel (one
+// thread per node), else the K-split kernel with that many slices.  kind: -1
+// by size (streaming from 65,536 nodes, 8 slices below), 0 streaming,
+// 1 / 2 / 3 K-split with 8 / 2 / 4 slices.
+int bsr_slices(long long nn, int kind) {
+    if (kind < 0) return nn >= kBsrStreamLevel ? 0 : kKsSlices;
+    return kind == 0 ? 0 : (kind == 1 ? 8 : (kind == 2 ? 2 : 4));
+}
 
 int bsr_grid_blocks(long long nn, bool tma, int kind) {
     if (tma) return pipe_blocks(nn);
-    constexpr int npb = 256 / kKsSlices;
-    return bsr_streams(nn, kind) ? (int)((nn + 255) / 256) : (int)((nn + npb - 1) / npb);
+    const int ns = bsr_slices(nn, kind);
+    const int npb = ns ? 256 / ns : 256;
+    return (int)((nn + npb - 1) / npb);
+}
+
+template <int NS>
+void launch_bsr_ks(int mode, int dot, int g, const BsrArgs& a, cudaStream_t s) {
+    if (mode == FM_APPLY) {
+        if (dot) pdl_launch(k_bsr_ks<FM_APPLY, true, NS>, dim3(g), dim3(256), 0, s, a);
+        else pdl_launch(k_bsr_ks<FM_APPLY, false, NS>, dim3(g), dim3(256), 0, s, a);
+    } else if (mode == FM_SMOOTH) {
+        if (dot) pdl_launch(k_bsr_ks<FM_SMOOTH, true, NS>, dim3(g), dim3(256), 0, s, a);
+        else pdl_launch(k_bsr_ks<FM_SMOOTH, false, NS>, dim3(g), dim3(256), 0, s, a);
+    } else {
+        pdl_launch(k_bsr_ks<FM_RESID, false, NS>, dim3(g), dim3(256), 0, s, a);
+    }
 }
 
 template <int MODE, bool DOT>
@@ -870,7 +891,8 @@ void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
         return;
     }
     const int g = bsr_grid_blocks(a.nn, false, a.kind);
-    if (bsr_streams(a.nn, a.kind)) {
+    const int ns = bsr_slices(a.nn, a.kind);
+    if (ns == 0) {
         if (mode == FM_APPLY) {
             if (dot) pdl_launch(k_bsr<FM_APPLY, true, 256>, dim3(g), dim3(256), 0, s, a);
             else pdl_launch(k_bsr<FM_APPLY, false, 256>, dim3(g), dim3(256), 0, s, a);
@@ -882,16 +904,9 @@ void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
         }
         return;
     }
-    constexpr int NS = kKsSlices;
-    if (mode == FM_APPLY) {
-        if (dot) pdl_launch(k_bsr_ks<FM_APPLY, true, NS>, dim3(g), dim3(256), 0, s, a);
-        else pdl_launch(k_bsr_ks<FM_APPLY, false, NS>, dim3(g), dim3(256), 0, s, a);
-    } else if (mode == FM_SMOOTH) {
-        if (dot) pdl_launch(k_bsr_ks<FM_SMOOTH, true, NS>, dim3(g), dim3(256), 0, s, a);
-        else pdl_launch(k_bsr_ks<FM_SMOOTH, false, NS>, dim3(g), dim3(256), 0, s, a);
-    } else {
-        pdl_launch(k_bsr_ks<FM_RESID, false, NS>, dim3(g), dim3(256), 0, s, a);
-    }
+    if (ns == 8) launch_bsr_ks<8>(mode, dot, g, a, s);
+    else if (ns == 2) launch_bsr_ks<2>(mode, dot, g, a, s);
+    else launch_bsr_ks<4>(mode, dot, g, a, s);
 }
 
 bool encode_f32_map(CUtensorMap* map, const float* base, int rank, const unsigned long long* dims,
