@@ -247,14 +247,21 @@ struct S2tArgs {
     long long go_bs, out_bs, ref_bs;
 };
 
+// A block covers TY x TZ fine rows (y, z) of 8 nodes in x, for all CIG groups of
+// 4 input channels.  Threads are ordered parity class (fy & 1) + 2 (fz & 1)
+// first, then channel group, then row within the class: TY and TZ are even, so
+// every warp holds rows of one class only and never splits over the 1 / 2 / 4
+// (y, z) tap combinations of different parities.
 template <int CIG>
 __global__ void __launch_bounds__(256) k_conv_s2t(S2tArgs a) {
     constexpr int ROWS = 256 / CIG;
     constexpr int TY = ROWS >= 32 ? 8 : 4;
     constexpr int TZ = ROWS / TY;
+    constexpr int RPC = ROWS / 4;  // rows per parity class (16, 8, 4: divides 32)
+    static_assert(TY % 2 == 0 && TZ % 2 == 0 && 32 % RPC == 0, "parity-major thread order");
     const int tid = threadIdx.x;
-    const int row = tid % ROWS, cg = tid / ROWS;
-    const int ty = row % TY, tz = row / TY;
+    const int cls = tid / (RPC * CIG), cg = (tid / RPC) % CIG, q = tid % RPC;
+    const int ty = 2 * (q % (TY / 2)) + (cls & 1), tz = 2 * (q / (TY / 2)) + (cls >> 1);
     const int ntx = (a.X + 7) / 8, nty = (a.Y + TY - 1) / TY;
     int t = blockIdx.x;
     const int bx = t % ntx;
@@ -344,25 +351,30 @@ struct WgArgs {
     long long part_stride;
 };
 
+// One thread per (4 output channels, 4 input channels, tap row (dy, dz)); it
+// holds the three taps dx = 0, 1, 2 of the row, so each node costs one load of
+// the output gradient and three of the input (neighbours in x) for 48 FMAs.
 template <int S>
 __global__ void __launch_bounds__(256) k_wgrad(WgArgs a) {
     const int cin4 = a.cin / 4;
     const int pairs = (a.coutp / 4) * cin4;
     const int task = blockIdx.y * 256 + threadIdx.x;
-    if (task >= pairs * 27) return;
-    const int tap = task / pairs, pr = task % pairs;
+    if (task >= pairs * 9) return;
+    const int trow = task / pairs, pr = task % pairs;
     const int ci4 = pr % cin4, co4 = pr / cin4;
-    const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;
+    const int dy = trow % 3, dz = trow / 3;
     const long long No = (long long)a.Xo * a.Yo * a.Zo;
     const long long o_begin = blockIdx.x * a.nodes_per_split;
     const long long o_end = min(o_begin + a.nodes_per_split, No * a.B);
-    float acc[4][4];
+    float acc[3][4][4];
     float bacc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[j][k] = 0.f;
-    const bool do_bias = (tap == 13) && (ci4 == 0);
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[d][j][k] = 0.f;
+    const bool do_bias = (trow == 4) && (ci4 == 0);  // the row holding the centre tap 13
     if (o_begin < o_end) {
         long long r = o_begin;
         int b = (int)(r / No);
@@ -372,16 +384,22 @@ __global__ void __launch_bounds__(256) k_wgrad(WgArgs a) {
         int oz = (int)(on / ((long long)a.Xo * a.Yo));
         for (long long o = o_begin; o < o_end; ++o) {
             const float4 g = __ldg(reinterpret_cast<const float4*>(a.go + b * a.go_bs + on * a.go_pitch + 4 * co4));
-            const int ix = S * ox + dx - 1, iy = S * oy + dy - 1, iz = S * oz + dz - 1;
-            if (ix >= 0 && ix < a.X && iy >= 0 && iy < a.Y && iz >= 0 && iz < a.Z) {
-                const float4 x = __ldg(reinterpret_cast<const float4*>(
-                    a.in + b * a.in_bs + ((long long)(iz * a.Y + iy) * a.X + ix) * a.in_pitch + 4 * ci4));
+            const int iy = S * oy + dy - 1, iz = S * oz + dz - 1;
+            if (iy >= 0 && iy < a.Y && iz >= 0 && iz < a.Z) {
+                const float* xrow = a.in + b * a.in_bs + ((long long)(iz * a.Y + iy) * a.X) * a.in_pitch + 4 * ci4;
                 const float gv[4] = {g.x, g.y, g.z, g.w};
-                const float xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int dx = 0; dx < 3; ++dx) {
+                    const int ix = S * ox + dx - 1;
+                    if (ix >= 0 && ix < a.X) {
+                        const float4 x = __ldg(reinterpret_cast<const float4*>(xrow + (long long)ix * a.in_pitch));
+                        const float xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) acc[j][k] = fmaf(gv[j], xv[k], acc[j][k]);
+                        for (int j = 0; j < 4; ++j)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) acc[dx][j][k] = fmaf(gv[j], xv[k], acc[dx][j][k]);
+                    }
+                }
             }
             if (do_bias) {
                 bacc[0] += g.x;
@@ -405,9 +423,13 @@ __global__ void __launch_bounds__(256) k_wgrad(WgArgs a) {
     }
     float* p = a.part + blockIdx.x * a.part_stride;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int dx = 0; dx < 3; ++dx) {
+        const int tap = dx + 3 * trow;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) p[((long long)(4 * co4 + j) * 27 + tap) * a.cin + 4 * ci4 + k] = acc[j][k];
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) p[((long long)(4 * co4 + j) * 27 + tap) * a.cin + 4 * ci4 + k] = acc[dx][j][k];
+    }
     if (do_bias)
 #pragma unroll
         for (int j = 0; j < 4; ++j) p[(long long)a.coutp * 27 * a.cin + 4 * co4 + j] = bacc[j];
@@ -1850,8 +1872,25 @@ int conv_bwd_s2(gmg_net* net, int l, const float* gout, int go_pitch, long long 
 }
 
 // Splits of the output nodes for the weight gradient of a layer.
+// Blocks of k_wgrad resident on the whole GPU (the occupancy of the heavier
+// instantiation times the SM count), so that the split grid fills whole waves.
+long long wgrad_wave() {
+    static long long n = 0;
+    if (n == 0) {
+        int dev = 0, sms = 0, r1 = 0, r2 = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 148;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r1, k_wgrad<1>, 256, 0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r2, k_wgrad<2>, 256, 0) != cudaSuccess)
+            r1 = r2 = 2, (void)cudaGetLastError();
+        n = (long long)sms * std::max(1, std::min(r1, r2));
+    }
+    return n;
+}
+
 int wgrad_splits(long long out_nodes, int task_blocks) {
-    const long long target_blocks = 4 * 148;
+    const long long target_blocks = wgrad_wave();
     long long sp = std::max<long long>(1, target_blocks / std::max(1, task_blocks));
     sp = std::min<long long>(sp, std::max<long long>(1, out_nodes / 128));
     return (int)std::min<long long>(sp, 4096);
@@ -1859,7 +1898,7 @@ int wgrad_splits(long long out_nodes, int task_blocks) {
 
 long long wgrad_part_size(int l, long long out_nodes) {
     const int coutp = cpad4(kDefs[l].cout), cin = kDefs[l].cin;
-    const int tasks = (coutp / 4) * (cin / 4) * 27;
+    const int tasks = (coutp / 4) * (cin / 4) * 9;
     const int tb = (tasks + 255) / 256;
     const long long per = (long long)coutp * 27 * cin + coutp;
     return (long long)wgrad_splits(out_nodes, tb) * per;
@@ -1886,7 +1925,7 @@ int wgrad(gmg_net* net, Work* w, int l, const float* in, int in_pitch, long long
     a.in_bs = in_bs;
     a.go_bs = go_bs;
     const long long out_nodes = (long long)a.Xo * a.Yo * a.Zo * w->B;
-    const int tasks = (a.coutp / 4) * (a.cin / 4) * 27;
+    const int tasks = (a.coutp / 4) * (a.cin / 4) * 9;
     const int tb = (tasks + 255) / 256;
     const int splits = wgrad_splits(out_nodes, tb);
     a.nodes_per_split = (out_nodes + splits - 1) / splits;
