@@ -129,6 +129,12 @@ typedef struct {
                                     (MGS Arnoldi, Givens rotations, happy breakdown at 1e-14);
                                     gmg_info.iterations counts Arnoldi steps, .replacements restarts */
     int restart;                 /* FGMRES restart length (32) */
+    int bsr_kernel;              /* kernel of the assembled levels outside the TMA-staged and fused
+                                    paths: -1 (default) = by size (streaming from 65,536 nodes,
+                                    K-split with 8 slices below); 0 = streaming, one thread per
+                                    node; 1 / 2 / 3 = K-split with 8 / 2 / 4 slices per node.
+                                    Results do not depend on the choice (each node's arithmetic is
+                                    the same); gmg_autotune overrides it per level. */
     void* stream;                /* cudaStream_t for all device work; NULL = default stream */
 } gmg_options;
 
@@ -293,7 +299,7 @@ typedef struct {
  * the K-split one with 8, 2 or 4 slices per node (kept in this handle).  The operator's results do not depend on
  * these shapes (each node's arithmetic is the same); reduction partial sums
  * are grouped differently.  reps: timed launches per candidate (>= 1); 0
- * returns to the cost model's plan and the size rule.  Drops the handle's
+ * returns to the cost model's plan and to the options' bsr_kernel choice.  Drops the handle's
  * captured solve graphs.  Synchronous.  out may be NULL. */
 int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out);
 

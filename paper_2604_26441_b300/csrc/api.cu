@@ -465,6 +465,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     // ---- TMA-staged operator for the large assembled levels
     for (int li = 1; li < L; ++li) {
         Level& l = h->lev[li];
+        l.bsr_kind = o.bsr_kernel;
         if (o.bsr_tma_nodes > 0 && l.nn >= o.bsr_tma_nodes) {
             const int rc = encode_bsr_maps(l);
             if (rc != GMG_OK) return fail(rc, "could not encode the tensor maps of an assembled level");
@@ -828,6 +829,7 @@ void gmg_default_options(gmg_options* o) {
     o->cycle_index = 1;
     o->outer = GMG_OUTER_PCG;
     o->restart = 32;
+    o->bsr_kernel = -1;
     o->stream = nullptr;
 }
 
@@ -889,6 +891,7 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
     if (o.fine_smoother != GMG_FINE_FP32 && o.fine_smoother != GMG_FINE_BF16 && o.fine_smoother != GMG_FINE_BF16X3)
         return fail(GMG_ERR_ARG, "unknown fine_smoother");
     if (o.cycle_index < 1 || o.cycle_index > 2) return fail(GMG_ERR_ARG, "cycle_index must be 1 (V) or 2 (W)");
+    if (o.bsr_kernel < -1 || o.bsr_kernel > 3) return fail(GMG_ERR_ARG, "bsr_kernel outside [-1, 3]");
     if (o.outer != GMG_OUTER_PCG && o.outer != GMG_OUTER_FGMRES) return fail(GMG_ERR_ARG, "unknown outer solver");
     if (o.restart < 1 || o.restart > 256) return fail(GMG_ERR_ARG, "restart must be in [1, 256]");
     if (o.power_iters_fine < 1 || o.power_iters_coarse < 1 || o.chol_cutoff < 1)
@@ -1075,14 +1078,14 @@ int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
     CU(cudaStreamSynchronize(s));
     if (reps == 0) {  // back to the cost model and the size rule
         fine_set_plan(h->lev[0].nx, h->lev[0].ny, h->lev[0].nz, -1, 0);
-        for (int li = 1; li < h->L; ++li) h->lev[li].bsr_kind = -1;
+        for (int li = 1; li < h->L; ++li) h->lev[li].bsr_kind = h->opt.bsr_kernel;
         loop_free(h);
         if (out) {
             *out = gmg_tuning{};
             fine_model_plan(h->lev[0].nx, h->lev[0].ny, h->lev[0].nz, &out->fine_tile, &out->fine_zchunk);
             out->model_tile = out->fine_tile;
             out->model_zchunk = out->fine_zchunk;
-            for (int li = 0; li < 16; ++li) out->bsr_kind[li] = -1;
+            for (int li = 0; li < 16; ++li) out->bsr_kind[li] = li >= 1 && li < h->L ? h->opt.bsr_kernel : -1;
         }
         return GMG_OK;
     }

@@ -51,7 +51,7 @@ class _Options(ctypes.Structure):
                 ("ir_factor", ctypes.c_double),
                 ("fine_smoother", ctypes.c_int),
                 ("cycle_index", ctypes.c_int), ("outer", ctypes.c_int), ("restart", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("bsr_kernel", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class _Info(ctypes.Structure):
@@ -176,7 +176,7 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
             power_iters_coarse: int = 10, chol_cutoff: int = 5000, fused_coarse_nodes: int = 0,
             bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
             fine_smoother: str = "fp32", cycle: str = "V", outer: str = "pcg", restart: int = 32,
-            stream: int | None = None) -> _Options:
+            bsr_kernel: int = -1, stream: int | None = None) -> _Options:
     o = _Options()
     load_library().gmg_default_options(ctypes.byref(o))
     o.levels = levels
@@ -199,6 +199,7 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
     o.cycle_index = {"V": 1, "W": 2}[cycle]
     o.outer = {"pcg": 0, "fgmres": 1}[outer]
     o.restart = restart
+    o.bsr_kernel = bsr_kernel
     o.stream = stream
     return o
 
@@ -206,12 +207,13 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
 def config_options(cfg, stream: int | None = None, fused_coarse_nodes: int = 0,
                    bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
                    fine_smoother: str = "fp32", cycle: str = "V", outer: str = "pcg",
-                   restart: int = 32) -> _Options:
+                   restart: int = 32, bsr_kernel: int = -1) -> _Options:
     """Options for one of the synthetic configurations in ``inputs.CONFIGS``."""
     return options(levels=cfg.levels, smoother=cfg.smoother, degree=cfg.degree, coarse_smoother=None,
                    coarse_degree=None, omega=cfg.omega, coarse_omega=None, fused_coarse_nodes=fused_coarse_nodes,
                    bsr_tma_nodes=bsr_tma_nodes, device_loop=device_loop, ir_factor=ir_factor,
-                   fine_smoother=fine_smoother, cycle=cycle, outer=outer, restart=restart, stream=stream)
+                   fine_smoother=fine_smoother, cycle=cycle, outer=outer, restart=restart, bsr_kernel=bsr_kernel,
+                   stream=stream)
 
 
 def residual64_noalloc(dims, E, mask, f, u, r=None, nu: float = 0.3, stream: int | None = None) -> float:

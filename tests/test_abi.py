@@ -46,7 +46,7 @@ def test_status_strings_and_defaults(lib):
     assert o.levels == 4 and o.degree == 2 and o.power_iters_fine == 20 and o.power_iters_coarse == 10
     assert abs(o.cheb_alpha - 1 / 30) < 1e-15 and o.chol_cutoff == 5000
     assert o.fused_coarse_nodes == 0 and o.bsr_tma_nodes == 0 and o.device_loop == 1 and o.ir_factor == 0.0 and o.fine_smoother == 0
-    assert o.cycle_index == 1 and o.outer == 0 and o.restart == 32
+    assert o.cycle_index == 1 and o.outer == 0 and o.restart == 32 and o.bsr_kernel == -1
 
 
 def test_struct_layouts_match_header(tmp_path):

@@ -142,29 +142,30 @@ def test_masks_and_galerkin_operators(name, nx, ny, nz, levels, mask):
         assert np.max(np.abs(A - R)) <= 1e-12 * np.max(np.abs(R))
 
 
-# bsr_tma_nodes=1 forces the TMA-staged operator kernel onto every assembled
-# level (by default no level uses it); 0 keeps the default kernels, which at
-# these sizes are all the K-split form.
-TMA_MODES = [pytest.param(0, id="ksplit"), pytest.param(1, id="tma")]
+# Kernels of the assembled levels: the default at these sizes (all K-split),
+# bsr_tma_nodes=1 forces the TMA-staged kernel onto every assembled level, and
+# bsr_kernel=0 the streaming one-thread-per-node kernel.
+KERNEL_MODES = [pytest.param({}, id="ksplit"), pytest.param({"bsr_tma_nodes": 1}, id="tma"),
+                pytest.param({"bsr_kernel": 0}, id="stream")]
 
 
-@pytest.mark.parametrize("tma", TMA_MODES)
+@pytest.mark.parametrize("kmode", KERNEL_MODES)
 @pytest.mark.parametrize("name,nx,ny,nz,levels,mask", HIER_CASES[:3])
-def test_lambda_estimates(name, nx, ny, nz, levels, mask, tma):
+def test_lambda_estimates(name, nx, ny, nz, levels, mask, kmode):
     rho, fixed, fixed_arg = _case_inputs(nx, ny, nz, mask)
     S = gpu_solver(rho, 3.0, fixed=fixed_arg, levels=levels, smoother="jacobi", coarse_smoother=None, omega=0.4,
-                   bsr_tma_nodes=tma)
+                   **kmode)
     H, _ = oracle_hierarchy(rho, 3.0, fixed, levels)
     for li, lev in enumerate(H):
         assert abs(S.get_lambda(li) - lev.lam) < 1e-4 * lev.lam
 
 
-@pytest.mark.parametrize("tma", TMA_MODES)
+@pytest.mark.parametrize("kmode", KERNEL_MODES)
 @pytest.mark.parametrize("name,nx,ny,nz,levels,mask", HIER_CASES)
-def test_level_ops_restrict_prolong_coarse(name, nx, ny, nz, levels, mask, tma):
+def test_level_ops_restrict_prolong_coarse(name, nx, ny, nz, levels, mask, kmode):
     rho, fixed, fixed_arg = _case_inputs(nx, ny, nz, mask)
     S = gpu_solver(rho, 3.0, fixed=fixed_arg, levels=levels, smoother="jacobi", coarse_smoother=None, omega=0.4,
-                   bsr_tma_nodes=tma)
+                   **kmode)
     H, _ = oracle_hierarchy(rho, 3.0, fixed, levels)
     rng = np.random.default_rng(5)
     for li, lev in enumerate(H):
@@ -213,13 +214,13 @@ SMOOTH_OPTS = [
 ]
 
 
-@pytest.mark.parametrize("tma", TMA_MODES)
+@pytest.mark.parametrize("kmode", KERNEL_MODES)
 @pytest.mark.parametrize("opts", SMOOTH_OPTS, ids=["jacobi", "cheb3", "cheb2+jacobi"])
-def test_smoothers_and_vcycle(opts, tma):
+def test_smoothers_and_vcycle(opts, kmode):
     c = inputs.CONFIGS["c0"]
     rho = inputs.filtered_random_density(c.nx, c.ny, c.nz, 2)
     fixed = c.fixed()
-    S = gpu_solver(rho, 3.0, **opts, bsr_tma_nodes=tma)
+    S = gpu_solver(rho, 3.0, **opts, **kmode)
     H, _ = oracle_hierarchy(rho, 3.0, fixed, opts["levels"])
     for li, lev in enumerate(H):
         S.set_lambda(li, lev.lam)
@@ -286,23 +287,25 @@ def test_solve_config1(p):
     assert info["status"] == 0
 
 
-@pytest.mark.parametrize("tma", TMA_MODES)
-def test_solve_ragged_chebyshev(tma):
+@pytest.mark.parametrize("kmode", KERNEL_MODES)
+def test_solve_ragged_chebyshev(kmode):
     nx, ny, nz = 23, 11, 9
     rho = inputs.filtered_random_density(nx, ny, nz, 4)
     opts = dict(levels=3, smoother="chebyshev", degree=3, coarse_smoother=None, coarse_degree=None, omega=0.5,
-                coarse_omega=None, bsr_tma_nodes=tma)
+                coarse_omega=None, **kmode)
     info, res = _solve_and_compare(rho, 3.0, inputs.clamp_xmin_mask(nx, ny, nz), inputs.tip_edge_load(nx, ny, nz), opts)
     assert info["status"] == 0
 
 
-@pytest.mark.parametrize("tma", [pytest.param(0, id="stream"), pytest.param(65536, id="tma")])
-def test_solve_full_size_config2(tma):
+@pytest.mark.parametrize("kmode", [pytest.param({}, id="stream"), pytest.param({"bsr_tma_nodes": 65536}, id="tma"),
+                                   pytest.param({"bsr_kernel": 1}, id="ksplit")])
+def test_solve_full_size_config2(kmode):
     """100^3, 5 levels, Chebyshev degree 3: the oracle judges the GPU solution by
     its own FP64 residual and the energy identity.  The tma variant runs level 1
-    (132,651 nodes) through the TMA-staged operator kernel."""
+    (132,651 nodes) through the TMA-staged operator kernel, the ksplit one every
+    assembled level (level 1 included) through the K-split kernel."""
     c = inputs.CONFIGS["c2"]
-    S = gpu_solver(c.rho(), c.p, **config_opts(c), bsr_tma_nodes=tma)
+    S = gpu_solver(c.rho(), c.p, **config_opts(c), **kmode)
     f = c.load()
     u, info = S.solve(_t(f, torch.float64), tol=1e-6, maxit=200)
     assert info["status"] == 0
