@@ -567,30 +567,46 @@ __global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, const
 }
 
 // x[free_idx[i]] = sum_j Ainv[i][j] b[free_idx[j]]  (FP64 accumulation): the
-// gathered right-hand side is staged in shared memory once per block, then each
-// warp reduces a few rows of the inverse.
-constexpr int kCoarseRowsPerBlock = 8;
+// gathered right-hand side is staged in shared memory once per block, then 128
+// threads share each row (four independent accumulators per thread, so a
+// thread's loads of the row are all in flight together) and the row's partial
+// sums are combined in a fixed order (warp tree, then the row's four warps).
+constexpr int kCoarseRowsPerBlock = 2;
+constexpr int kCoarseRowThreads = 128;
 __global__ void __launch_bounds__(256) k_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b,
                                                       float* x) {
     pdl_entry();
-    extern __shared__ double bs[];
+    extern __shared__ double bs[];  // nL right-hand-side values, then one partial per warp
+    double* wpart = bs + nL;
     for (int j = threadIdx.x; j < nL; j += blockDim.x) bs[j] = (double)b[free_idx[j]];
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * kCoarseRowsPerBlock + warp;
-    if (row >= nL) return;
-    const double* rp = Ainv + (long long)row * nL;
-    double s0 = 0.0, s1 = 0.0;
-    int jx = lane;
-    for (; jx + 32 < nL; jx += 64) {
-        s0 = fma(rp[jx], bs[jx], s0);
-        s1 = fma(rp[jx + 32], bs[jx + 32], s1);
+    const int half = threadIdx.x / kCoarseRowThreads, t = threadIdx.x % kCoarseRowThreads;
+    const int row = blockIdx.x * kCoarseRowsPerBlock + half;
+    double s = 0.0;
+    if (row < nL) {
+        const double* rp = Ainv + (long long)row * nL;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int j = t;
+        for (; j + 3 * kCoarseRowThreads < nL; j += 4 * kCoarseRowThreads) {
+            a0 = fma(rp[j], bs[j], a0);
+            a1 = fma(rp[j + kCoarseRowThreads], bs[j + kCoarseRowThreads], a1);
+            a2 = fma(rp[j + 2 * kCoarseRowThreads], bs[j + 2 * kCoarseRowThreads], a2);
+            a3 = fma(rp[j + 3 * kCoarseRowThreads], bs[j + 3 * kCoarseRowThreads], a3);
+        }
+        for (; j < nL; j += kCoarseRowThreads) a0 = fma(rp[j], bs[j], a0);
+        s = (a0 + a1) + (a2 + a3);
     }
-    if (jx < nL) s0 = fma(rp[jx], bs[jx], s0);
-    double s = s0 + s1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) x[free_idx[row]] = (float)s;
+    if ((threadIdx.x & 31) == 0) wpart[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (t == 0 && row < nL) {
+        constexpr int W = kCoarseRowThreads / 32;
+        double r = 0.0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) r += wpart[half * W + w];
+        x[free_idx[row]] = (float)r;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1004,8 +1020,19 @@ void launch_coarse_solve(int nL, const int* free_idx, const double* Ainv, const 
                          long long n_dof, cudaStream_t s) {
     cudaMemsetAsync(x, 0, sizeof(float) * n_dof, s);
     if (nL > 0) {
+        const size_t smem = sizeof(double) * (nL + 8);
+        if (smem > 48 * 1024) {  // coarsest levels above ~6,000 free DOFs (a raised chol_cutoff)
+            static std::mutex mu;
+            static size_t granted = 48 * 1024;
+            std::lock_guard<std::mutex> lk(mu);
+            if (smem > granted &&
+                cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                    cudaSuccess)
+                granted = smem;
+        }
         note_launch();
-        pdl_launch(k_coarse_solve, dim3((nL + kCoarseRowsPerBlock - 1) / kCoarseRowsPerBlock), dim3(32 * kCoarseRowsPerBlock), sizeof(double) * nL, s, nL, free_idx, Ainv, b, x);
+        pdl_launch(k_coarse_solve, dim3((nL + kCoarseRowsPerBlock - 1) / kCoarseRowsPerBlock),
+                   dim3(kCoarseRowThreads * kCoarseRowsPerBlock), smem, s, nL, free_idx, Ainv, b, x);
     }
 }
 
