@@ -241,9 +241,34 @@ int check_level(const gmg_handle* h, int li) {
     return GMG_OK;
 }
 
+// Device scalars -> sc_host (and the sticky error words -> err_host): the device
+// writes the pinned host-mapped block itself, so the read-back uses no copy
+// engine and cannot wait behind a caller's large copies on other streams.
 int sync_scalars(gmg_handle* h) {
-    CU(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, h->stream));
+    launch_publish(h->sc, SC_COUNT, h->sc_map, h->kerr, h->use_fused ? h->cf.err : nullptr, h->err_map, h->stream);
+    CU(cudaGetLastError());
     CU(cudaStreamSynchronize(h->stream));
+    return GMG_OK;
+}
+
+// The pinned host-mapped block of sc_host and err_host.
+int alloc_mirror(gmg_handle* h) {
+    const size_t bytes = sizeof(double) * SC_COUNT + 4 * sizeof(int);
+    if (cudaHostAlloc(&h->pinned, bytes, cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        h->pinned = nullptr;
+        return fail(GMG_ERR_NOMEM, "pinned host-mapped scalar block");
+    }
+    void* dev = nullptr;
+    if (cudaHostGetDevicePointer(&dev, h->pinned, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GMG_ERR_CUDA, "no device address for the host-mapped scalar block");
+    }
+    memset(h->pinned, 0, bytes);
+    h->sc_host = static_cast<double*>(h->pinned);
+    h->err_host = reinterpret_cast<int*>(h->sc_host + SC_COUNT);
+    h->sc_map = static_cast<double*>(dev);
+    h->err_map = reinterpret_cast<int*>(h->sc_map + SC_COUNT);
     return GMG_OK;
 }
 
@@ -345,8 +370,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     maxp = std::max(maxp, 4096);
     h->max_partials = maxp;
     TRY(dalloc(h, &h->partials, maxp));
-    CU(cudaMallocHost(&h->pinned, sizeof(double) * SC_COUNT));
-    h->sc_host = static_cast<double*>(h->pinned);
+    TRY(alloc_mirror(h));
 
     // ---- moduli (Eq. simp_filter) and K_e
     launch_moduli(rho, ne, p, E0, Emin, h->E64, h->E32, s);
@@ -513,7 +537,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
 void pcg_restart(gmg_handle* h) {
     const long long n = 3 * h->lev[0].nn;
     vcycle_level(h, 0, h->r, h->z, h->x2_0, SC_RZ, FIN_NONE);
-    cudaMemcpyAsync(h->p, h->z, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->stream);
+    launch_copy_f32(h->p, h->z, n, h->stream);
 }
 // q = K p, alpha = rz / p.q, u += alpha p, r -= alpha q, ||r||^2
 void pcg_step(gmg_handle* h, double* u) {
@@ -792,10 +816,8 @@ int fgmres_solve(gmg_handle* h, const double* f, double* u, double tol, int maxi
 // Reports a timed-out wait of the TMA-staged operator or of the fused lower
 // V-cycle (both error words are sticky).
 int check_fused(gmg_handle* h) {
-    int err[2] = {0, 0};
-    CU(cudaMemcpyAsync(&err[0], h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    if (h->use_fused) CU(cudaMemcpyAsync(&err[1], h->cf.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaStreamSynchronize(h->stream));
+    TRY(sync_scalars(h));
+    const int err[2] = {h->err_host[0], h->err_host[1]};
     if (err[0]) return fail(GMG_ERR_CUDA, "an assembled-level operator gave up waiting for its TMA tiles");
     if (err[1]) return fail(GMG_ERR_CUDA, "the fused coarse-level V-cycle gave up waiting at a grid barrier");
     return GMG_OK;
@@ -979,7 +1001,7 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     if (!std::isfinite(rel)) return finish(GMG_NONFINITE);
     if (rel < tol) return finish(GMG_OK);
     sch[SC_UNZ] = 1.0;
-    CU(cudaMemcpyAsync(h->sc + SC_UNZ, sch + SC_UNZ, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_set_scalars(h->sc + SC_UNZ, 1, 1.0, 0.0, 0.0, 0.0, s);
 
     const double nf = std::sqrt(sch[SC_FF]);
     // Stopping target of an inner PCG phase.  Plain solve: tol.  Outer FP64
@@ -1005,12 +1027,12 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
         sch[SC_TOL] = target;
         sch[SC_MAXIT] = (double)maxit;
         sch[SC_NF] = nf;
-        CU(cudaMemcpyAsync(h->sc + SC_IT, sch + SC_IT, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+        launch_set_scalars(h->sc + SC_IT, 4, sch[SC_IT], sch[SC_TOL], sch[SC_MAXIT], sch[SC_NF], s);
         int k = 0;
         while (true) {
             if (sch[SC_TOL] != target) {
                 sch[SC_TOL] = target;
-                CU(cudaMemcpyAsync(h->sc + SC_TOL, sch + SC_TOL, sizeof(double), cudaMemcpyHostToDevice, s));
+                launch_set_scalars(h->sc + SC_TOL, 1, target, 0.0, 0.0, 0.0, s);
             }
             CU(cudaGraphLaunch(h->loop_exec, s));
             TRY(sync_scalars(h));
@@ -1249,6 +1271,9 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out) {
     h->allocs.clear();
     h->pinned = nullptr;
     h->sc_host = nullptr;
+    h->sc_map = nullptr;
+    h->err_host = nullptr;
+    h->err_map = nullptr;
     h->cap_stream = nullptr;
     h->loop_graph = nullptr;
     h->loop_exec = nullptr;
@@ -1289,12 +1314,11 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out) {
     if (rc == GMG_OK) rc = dalloc(h, &h->partials, h->max_partials);
     if (rc != GMG_OK) return bad(rc);
     if (cudaMemsetAsync(h->sc, 0, sizeof(double) * SC_COUNT, s) != cudaSuccess ||
-        cudaMemsetAsync(h->kerr, 0, sizeof(int), s) != cudaSuccess ||
-        cudaMallocHost(&h->pinned, sizeof(double) * SC_COUNT) != cudaSuccess) {
+        cudaMemsetAsync(h->kerr, 0, sizeof(int), s) != cudaSuccess) {
         cudaGetLastError();
         return bad(fail(GMG_ERR_CUDA, "clone workspace"));
     }
-    h->sc_host = static_cast<double*>(h->pinned);
+    if (int rc2 = alloc_mirror(h); rc2 != GMG_OK) return bad(rc2);
     if (h->use_fused) {
         CoarseFused& cf = h->cf;
         for (int li = 1; li < h->L; ++li) {
@@ -1352,8 +1376,21 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
     const auto t0 = std::chrono::steady_clock::now();
     auto elapsed = [&]() { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); };
     auto sync_all = [&]() -> int {
-        for (int i = 0; i < count; ++i)
-            CU(cudaMemcpyAsync(hs[i]->sc_host, hs[i]->sc, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, s));
+        PublishBatch pb{};
+        pb.n = SC_COUNT;
+        for (int i = 0; i < count; ++i) {
+            const int k = pb.count++;
+            pb.sc[k] = hs[i]->sc;
+            pb.out[k] = hs[i]->sc_map;
+            pb.e0[k] = hs[i]->kerr;
+            pb.e1[k] = hs[i]->use_fused ? hs[i]->cf.err : nullptr;
+            pb.eout[k] = hs[i]->err_map;
+            if (pb.count == kPublishItems || i + 1 == count) {
+                launch_publish_batch(pb, s);
+                pb.count = 0;
+            }
+        }
+        CU(cudaGetLastError());
         CU(cudaStreamSynchronize(s));
         return GMG_OK;
     };
@@ -1451,7 +1488,7 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
             sch[SC_TOL] = tol;
             sch[SC_MAXIT] = (double)maxit;
             sch[SC_NF] = nf[i];
-            CU(cudaMemcpyAsync(hs[i]->sc + SC_IT, sch + SC_IT, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+            launch_set_scalars(hs[i]->sc + SC_IT, 4, sch[SC_IT], sch[SC_TOL], sch[SC_MAXIT], sch[SC_NF], s);
         }
         CU(cudaGraphLaunch(h0->batch_exec, s));
         if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
@@ -1623,7 +1660,7 @@ int gmg_residual64(gmg_handle* h, const double* f, const double* u, double* r, d
     Level& l0 = h->lev[0];
     cudaStream_t s = h->stream;
     h->sc_host[SC_UNZ] = 1.0;
-    CU(cudaMemcpyAsync(h->sc + SC_UNZ, h->sc_host + SC_UNZ, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_set_scalars(h->sc + SC_UNZ, 1, 1.0, 0.0, 0.0, 0.0, s);
     launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, r, nullptr, h->sc, h->partials, h->gh64, s);
     launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
     launch_dot_f64_masked(f, f, l0.mask, l0.nn, h->partials, s);

@@ -238,7 +238,10 @@ struct gmg_handle {
     double* partials = nullptr;
     int max_partials = 0;
     double* sc = nullptr;                       // [SC_COUNT] device scalars
-    double* sc_host = nullptr;                  // pinned mirror
+    double* sc_host = nullptr;                  // pinned, host-mapped mirror (written by k_publish)
+    double* sc_map = nullptr;                   // device address of sc_host
+    int* err_host = nullptr;                    // [2] sticky error words, same pinned block
+    int* err_map = nullptr;                     // device address of err_host
     // coarsest dense solve
     int nL = 0;
     int* free_idx = nullptr;                    // [nL] DOF indices of the coarsest free DOFs
@@ -279,7 +282,7 @@ struct gmg_handle {
     std::vector<std::pair<unsigned long long, unsigned long long>> batch_counts;
     int fused_blocks = 0;
     std::vector<void*> allocs;                  // every device allocation, freed by gmg_destroy
-    void* pinned = nullptr;                     // pinned host block (sc_host)
+    void* pinned = nullptr;                     // pinned host-mapped block (sc_host, err_host)
 };
 
 namespace gmg {
@@ -359,6 +362,28 @@ void launch_bsr_smooth0(const BsrArgs& a, cudaStream_t s);
 
 void launch_restrict(const Level& f, const Level& c, const float* fine, float* coarse, cudaStream_t s);
 void launch_prolong_add(const Level& f, const Level& c, const float* coarse, float* fine, cudaStream_t s);
+// Scalars between host and device without a copy engine (so they never queue
+// behind a caller's large copies on other streams): k_publish writes the device
+// scalars and the two sticky error words (e1 may be null) into the pinned
+// host-mapped block; k_set_scalars writes up to four values passed as kernel
+// arguments.
+void launch_publish(const double* sc, int n, double* out_map, const int* e0, const int* e1, int* err_map,
+                    cudaStream_t s);
+void launch_set_scalars(double* sc, int n, double v0, double v1, double v2, double v3, cudaStream_t s);
+// k_publish for the items of a batch, up to kPublishItems per launch.
+constexpr int kPublishItems = 128;
+struct PublishBatch {
+    const double* sc[kPublishItems];
+    double* out[kPublishItems];
+    const int* e0[kPublishItems];
+    const int* e1[kPublishItems];
+    int* eout[kPublishItems];
+    int count, n;
+};
+void launch_publish_batch(const PublishBatch& b, cudaStream_t s);
+// y[0..n) = x[0..n) by a kernel (a device-to-device cudaMemcpyAsync may take a
+// copy engine that a caller's host copies keep busy)
+void launch_copy_f32(float* y, const float* x, long long n, cudaStream_t s);
 void launch_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b, float* x,
                          long long n_dof, cudaStream_t s);
 
