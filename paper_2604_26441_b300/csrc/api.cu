@@ -183,7 +183,7 @@ void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int
         return;
     }
     if (li == h->L - 1) {
-        launch_coarse_solve(h->nL, h->free_idx, h->Ainv, b, X, 3 * l.nn, s);
+        launch_coarse_solve(h->nL, h->free_idx, h->Ainv, b, X, l.mask, l.nn, s);
         return;
     }
     int writes = 0;
@@ -1642,7 +1642,7 @@ int gmg_prolong_add(gmg_handle* h, int level, const float* coarse, float* fine) 
 int gmg_coarse_solve(gmg_handle* h, const float* b, float* x) {
     if (!h || !b || !x) return fail(GMG_ERR_ARG, "null argument");
     const Level& l = h->lev[h->L - 1];
-    launch_coarse_solve(h->nL, h->free_idx, h->Ainv, b, x, 3 * l.nn, h->stream);
+    launch_coarse_solve(h->nL, h->free_idx, h->Ainv, b, x, l.mask, l.nn, h->stream);
     CU(cudaGetLastError());
     return GMG_OK;
 }

@@ -566,15 +566,18 @@ __global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, const
     if (!fixed_bit(msk, 2)) fine[3 * n + 2] += s2;
 }
 
-// x[free_idx[i]] = sum_j Ainv[i][j] b[free_idx[j]]  (FP64 accumulation): the
-// gathered right-hand side is staged in shared memory once per block, then each
-// warp reduces a few rows of the inverse.  (Giving each row 128 threads measured
+// x[free_idx[i]] = sum_j Ainv[i][j] b[free_idx[j]]  (FP64 accumulation), and
+// x = 0 on the fixed DOFs (mask; no separate memset): the gathered right-hand
+// side is staged in shared memory once per block, then each warp reduces a few
+// rows of the inverse.  (Giving each row 128 threads measured
 // the same for one 100^3 solve and 5 % slower for a batch of 128 small solves
 // running concurrently, whose blocks then repeat the staging four times as often.)
 constexpr int kCoarseRowsPerBlock = 8;
 __global__ void __launch_bounds__(256) k_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b,
-                                                      float* x) {
+                                                      float* x, const uint8_t* mask, int n_nodes) {
     pdl_entry();
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < 3 * n_nodes; j += gridDim.x * blockDim.x)
+        if (fixed_bit(mask[j / 3], j % 3)) x[j] = 0.f;
     extern __shared__ double bs[];
     for (int j = threadIdx.x; j < nL; j += blockDim.x) bs[j] = (double)b[free_idx[j]];
     __syncthreads();
@@ -1057,9 +1060,8 @@ void launch_set_scalars(double* sc, int n, double v0, double v1, double v2, doub
 }
 
 void launch_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b, float* x,
-                         long long n_dof, cudaStream_t s) {
-    cudaMemsetAsync(x, 0, sizeof(float) * n_dof, s);
-    if (nL > 0) {
+                         const uint8_t* mask, long long n_nodes, cudaStream_t s) {
+    {
         const size_t smem = sizeof(double) * nL;
         if (smem > 48 * 1024) {  // coarsest levels above ~6,000 free DOFs (a raised chol_cutoff)
             static std::mutex mu;
@@ -1071,8 +1073,9 @@ void launch_coarse_solve(int nL, const int* free_idx, const double* Ainv, const 
                 granted = smem;
         }
         note_launch();
-        pdl_launch(k_coarse_solve, dim3((nL + kCoarseRowsPerBlock - 1) / kCoarseRowsPerBlock),
-                   dim3(32 * kCoarseRowsPerBlock), smem, s, nL, free_idx, Ainv, b, x);
+        const int g = std::max(1, (nL + kCoarseRowsPerBlock - 1) / kCoarseRowsPerBlock);  // nL = 0: zeroes only
+        pdl_launch(k_coarse_solve, dim3(g), dim3(32 * kCoarseRowsPerBlock), smem, s, nL, free_idx, Ainv, b, x, mask,
+                   (int)n_nodes);
     }
 }
 

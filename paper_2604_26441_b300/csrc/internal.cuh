@@ -384,8 +384,9 @@ void launch_publish_batch(const PublishBatch& b, cudaStream_t s);
 // y[0..n) = x[0..n) by a kernel (a device-to-device cudaMemcpyAsync may take a
 // copy engine that a caller's host copies keep busy)
 void launch_copy_f32(float* y, const float* x, long long n, cudaStream_t s);
+// x = Ainv b on the coarsest level's free DOFs, 0 on its fixed DOFs (mask).
 void launch_coarse_solve(int nL, const int* free_idx, const double* Ainv, const float* b, float* x,
-                         long long n_dof, cudaStream_t s);
+                         const uint8_t* mask, long long n_nodes, cudaStream_t s);
 
 int vec_grid_blocks();
 void launch_dot_f32(const float* a, const float* b, long long n, double* partial, cudaStream_t s);
