@@ -253,7 +253,7 @@ int sync_scalars(gmg_handle* h) {
 
 // The pinned host-mapped block of sc_host and err_host.
 int alloc_mirror(gmg_handle* h) {
-    const size_t bytes = sizeof(double) * SC_COUNT + 4 * sizeof(int);
+    const size_t bytes = sizeof(double) * SC_COUNT + 4 * sizeof(int) + sizeof(double) * (kMaxRestart + 2);
     if (cudaHostAlloc(&h->pinned, bytes, cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
         h->pinned = nullptr;
@@ -269,6 +269,8 @@ int alloc_mirror(gmg_handle* h) {
     h->err_host = reinterpret_cast<int*>(h->sc_host + SC_COUNT);
     h->sc_map = static_cast<double*>(dev);
     h->err_map = reinterpret_cast<int*>(h->sc_map + SC_COUNT);
+    h->hcol_host = reinterpret_cast<double*>(h->err_host + 4);
+    h->hcol_map = reinterpret_cast<double*>(h->err_map + 4);
     return GMG_OK;
 }
 
@@ -781,8 +783,10 @@ int fgmres_solve(gmg_handle* h, const double* f, double* u, double tol, int maxi
             launch_dot_f32(W, W, n, h->partials, s);
             launch_finalize(h->partials, vec_grid_blocks(), h->fg_h, j + 1, FIN_NONE, s);
             launch_scale_by_inv_sqrt(W, n, h->fg_h, j + 1, s);    // v_{j+1} = w / ||w||
-            CU(cudaMemcpyAsync(hcol.data(), h->fg_h, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+            launch_publish(h->fg_h, j + 2, h->hcol_map, nullptr, nullptr, nullptr, s);
+            CU(cudaGetLastError());
             CU(cudaStreamSynchronize(s));
+            std::copy(h->hcol_host, h->hcol_host + j + 2, hcol.begin());
             for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
             double hn = std::sqrt(std::max(hcol[j + 1], 0.0));
             if (!std::isfinite(hn)) return GMG_NONFINITE;
@@ -915,7 +919,7 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
     if (o.cycle_index < 1 || o.cycle_index > 2) return fail(GMG_ERR_ARG, "cycle_index must be 1 (V) or 2 (W)");
     if (o.bsr_kernel < -1 || o.bsr_kernel > 3) return fail(GMG_ERR_ARG, "bsr_kernel outside [-1, 3]");
     if (o.outer != GMG_OUTER_PCG && o.outer != GMG_OUTER_FGMRES) return fail(GMG_ERR_ARG, "unknown outer solver");
-    if (o.restart < 1 || o.restart > 256) return fail(GMG_ERR_ARG, "restart must be in [1, 256]");
+    if (o.restart < 1 || o.restart > kMaxRestart) return fail(GMG_ERR_ARG, "restart must be in [1, 256]");
     if (o.power_iters_fine < 1 || o.power_iters_coarse < 1 || o.chol_cutoff < 1)
         return fail(GMG_ERR_ARG, "bad iteration counts or cutoff");
 
@@ -1274,6 +1278,8 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out) {
     h->sc_map = nullptr;
     h->err_host = nullptr;
     h->err_map = nullptr;
+    h->hcol_host = nullptr;
+    h->hcol_map = nullptr;
     h->cap_stream = nullptr;
     h->loop_graph = nullptr;
     h->loop_exec = nullptr;

@@ -1008,7 +1008,7 @@ void launch_prolong_add(const Level& f, const Level& c, const float* coarse, flo
 namespace {
 __global__ void k_publish(const double* sc, int n, double* out, const int* e0, const int* e1, int* eout) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = sc[i];
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && eout) {
         eout[0] = e0 ? *e0 : 0;
         eout[1] = e1 ? *e1 : 0;
     }

@@ -242,6 +242,8 @@ struct gmg_handle {
     double* sc_map = nullptr;                   // device address of sc_host
     int* err_host = nullptr;                    // [2] sticky error words, same pinned block
     int* err_map = nullptr;                     // device address of err_host
+    double* hcol_host = nullptr;                // [kMaxRestart + 2] FGMRES Hessenberg column, same block
+    double* hcol_map = nullptr;                 // device address of hcol_host
     // coarsest dense solve
     int nL = 0;
     int* free_idx = nullptr;                    // [nL] DOF indices of the coarsest free DOFs
@@ -362,11 +364,12 @@ void launch_bsr_smooth0(const BsrArgs& a, cudaStream_t s);
 
 void launch_restrict(const Level& f, const Level& c, const float* fine, float* coarse, cudaStream_t s);
 void launch_prolong_add(const Level& f, const Level& c, const float* coarse, float* fine, cudaStream_t s);
+constexpr int kMaxRestart = 256;  // FGMRES restart length limit (gmg_options.restart)
 // Scalars between host and device without a copy engine (so they never queue
 // behind a caller's large copies on other streams): k_publish writes the device
 // scalars and the two sticky error words (e1 may be null) into the pinned
-// host-mapped block; k_set_scalars writes up to four values passed as kernel
-// arguments.
+// host-mapped block (err_map null: values only); k_set_scalars writes up to four
+// values passed as kernel arguments.
 void launch_publish(const double* sc, int n, double* out_map, const int* e0, const int* e1, int* err_map,
                     cudaStream_t s);
 void launch_set_scalars(double* sc, int n, double v0, double v1, double v2, double v3, cudaStream_t s);
