@@ -202,6 +202,29 @@ def test_level_ops_restrict_prolong_coarse(name, nx, ny, nz, levels, mask, kmode
     assert rel_l2(x, ref) < 1e-5
 
 
+@pytest.mark.parametrize("name,nx,ny,nz,levels,mask", HIER_CASES[:3])
+def test_coarse_solve_overwrites_every_dof(name, nx, ny, nz, levels, mask):
+    """The coarsest dense solve writes every entry of its output: the fixed DOFs
+    of the coarsest level exactly 0 and the free ones the oracle's solve, also
+    when the output buffer starts out holding NaN (twice in a row, so nothing is
+    left over from the first call)."""
+    rho, fixed, fixed_arg = _case_inputs(nx, ny, nz, mask)
+    S = gpu_solver(rho, 3.0, fixed=fixed_arg, levels=levels, smoother="jacobi", coarse_smoother=None, omega=0.4)
+    H, _ = oracle_hierarchy(rho, 3.0, fixed, levels)
+    last = H[-1]
+    nL = 3 * fem.Grid(*last.dims).n_nodes
+    rng = np.random.default_rng(17)
+    for _ in range(2):
+        b = np.zeros(nL, dtype=np.float32)
+        b[last.free] = rng.uniform(-1, 1, last.n_free)
+        x = torch.full((nL,), float("nan"), dtype=torch.float32, device="cuda")
+        out = S.coarse_solve(_t(b), x).cpu().numpy()
+        fixed_dofs = np.setdiff1d(np.arange(nL), last.free)
+        assert fixed_dofs.size > 0 and np.all(out[fixed_dofs] == 0.0)
+        ref = hy.coarse_solve(last.L, b[last.free].astype(np.float64))
+        assert np.all(np.isfinite(out)) and rel_l2(out[last.free], ref) < 1e-5
+
+
 # ---------------------------------------------------------------------------
 # smoothers and the V-cycle (oracle lambda injected so both use one band)
 # ---------------------------------------------------------------------------
