@@ -355,6 +355,7 @@ def warmstart_leg(dev) -> dict:
     return {"workload": f"train {data.size} solves on {'/'.join(str(n) for n in ws.TRAIN_GRIDS)}^3, "
                         f"evaluate {WARM_EVAL} held-out 80^3 cantilevers (512,000 elements), tol 1e-6, cap 500",
             "train": {"solves": data.size, "generate_s": data.seconds, "skipped_fields": data.skipped_fields,
+                      "skipped_solves": data.skipped_solves,
                       "steps": WARM_STEPS, "batch": WARM_BATCH, "train_s": train_s,
                       "loss_first100": float(losses[:100].mean()), "loss_last100": float(losses[-100:].mean()),
                       "loss": "scale-free energy-norm error^2"},

@@ -130,9 +130,11 @@ typedef struct {
                                     gmg_info.iterations counts Arnoldi steps, .replacements restarts */
     int restart;                 /* FGMRES restart length (32) */
     int bsr_kernel;              /* kernel of the assembled levels outside the TMA-staged and fused
-                                    paths: -1 (default) = by size (streaming from 65,536 nodes,
-                                    K-split with 8 slices below); 0 = streaming, one thread per
-                                    node; 1 / 2 / 3 = K-split with 8 / 2 / 4 slices per node.
+                                    paths: -1 (default) = by size (streaming from 65,536 nodes;
+                                    below, K-split with the most of 32 / 16 / 8 slices that
+                                    keeps the grid within ~4 blocks per SM); 0 = streaming, one thread per
+                                    node; 1 / 2 / 3 / 4 / 5 = K-split with 8 / 2 / 4 / 16 / 32
+                                    slices per node.
                                     Results do not depend on the choice (each node's arithmetic is
                                     the same); gmg_autotune overrides it per level. */
     void* stream;                /* cudaStream_t for all device work; NULL = default stream */
@@ -296,7 +298,7 @@ typedef struct {
  * planes, timed as fused Chebyshev/Jacobi smoothing steps; the choice holds
  * for every handle of that fine grid in this process), and per assembled
  * level outside the TMA-staged and fused paths the streaming SpMV kernel or
- * the K-split one with 8, 2 or 4 slices per node (kept in this handle).  The operator's results do not depend on
+ * the K-split one with 8, 2, 4, 16 or 32 slices per node (kept in this handle).  The operator's results do not depend on
  * these shapes (each node's arithmetic is the same); reduction partial sums
  * are grouped differently.  reps: timed launches per candidate (>= 1); 0
  * returns to the cost model's plan and to the options' bsr_kernel choice.  Drops the handle's

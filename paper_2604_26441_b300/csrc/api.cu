@@ -367,7 +367,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     // (the kernel of a level is chosen later or by gmg_autotune: size for
     // every kernel, and leave room for the fine kernel's tuning candidates)
     for (int li = 1; li < L; ++li)
-        for (int kind = 0; kind < 4; ++kind)
+        for (int kind = 0; kind < kBsrKinds; ++kind)
             maxp = std::max({maxp, bsr_grid_blocks(h->lev[li].nn, true), bsr_grid_blocks(h->lev[li].nn, false, kind)});
     maxp = std::max(maxp, 4096);
     h->max_partials = maxp;
@@ -917,7 +917,7 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
     if (o.fine_smoother != GMG_FINE_FP32 && o.fine_smoother != GMG_FINE_BF16 && o.fine_smoother != GMG_FINE_BF16X3)
         return fail(GMG_ERR_ARG, "unknown fine_smoother");
     if (o.cycle_index < 1 || o.cycle_index > 2) return fail(GMG_ERR_ARG, "cycle_index must be 1 (V) or 2 (W)");
-    if (o.bsr_kernel < -1 || o.bsr_kernel > 3) return fail(GMG_ERR_ARG, "bsr_kernel outside [-1, 3]");
+    if (o.bsr_kernel < -1 || o.bsr_kernel >= kBsrKinds) return fail(GMG_ERR_ARG, "bsr_kernel outside [-1, 5]");
     if (o.outer != GMG_OUTER_PCG && o.outer != GMG_OUTER_FGMRES) return fail(GMG_ERR_ARG, "unknown outer solver");
     if (o.restart < 1 || o.restart > kMaxRestart) return fail(GMG_ERR_ARG, "restart must be in [1, 256]");
     if (o.power_iters_fine < 1 || o.power_iters_coarse < 1 || o.chol_cutoff < 1)
@@ -1177,8 +1177,8 @@ int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
     for (int li = 1; li < h->L - 1 && li < 16 && rc == GMG_OK; ++li) {
         Level& l = h->lev[li];
         if (l.tma || li >= fused_start) continue;
-        double us[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int kind = 0; kind < 4 && rc == GMG_OK; ++kind) {
+        double us[kBsrKinds] = {};
+        for (int kind = 0; kind < kBsrKinds && rc == GMG_OK; ++kind) {
             l.bsr_kind = kind;
             BsrArgs a = bsr_args(h, li);
             a.xin = l.x;
@@ -1190,10 +1190,10 @@ int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
             rc = timed([&] { launch_bsr(FM_SMOOTH, 0, a, s); }, us[kind]);
         }
         int best = 0;
-        for (int kind = 1; kind < 4; ++kind)
+        for (int kind = 1; kind < kBsrKinds; ++kind)
             if (us[kind] < us[best]) best = kind;
         int second = best == 0 ? 1 : 0;
-        for (int kind = 0; kind < 4; ++kind)
+        for (int kind = 0; kind < kBsrKinds; ++kind)
             if (kind != best && us[kind] < us[second]) second = kind;
         l.bsr_kind = best;
         t.bsr_kind[li] = best;

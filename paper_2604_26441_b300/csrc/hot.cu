@@ -829,6 +829,19 @@ void launch_fine_smooth0(const FineArgs& a, cudaStream_t s) {
 constexpr long long kBsrStreamLevel = 65536;
 constexpr int kKsSlices = 8;
 
+// Slices of the K-split kernel by level size: the most of 32 / 16 / 8 that keep
+// the grid within kKsBlockBudget blocks of 256 threads (about four per SM).
+// These levels are latency-bound, and spreading each node's 27 blocks over more
+// threads puts more independent loads in flight; past the budget the extra
+// blocks only queue.  Measured per level (autotuner, all five slice counts):
+// 17,576 nodes -> 8 slices, 9,261 -> 16, 2,197 / 1,331 / 225 -> 32.
+constexpr long long kKsBlockBudget = 4 * 148;
+int ks_slices_for(long long nn) {
+    for (int ns : {32, 16})
+        if ((nn * ns + 255) / 256 <= kKsBlockBudget) return ns;
+    return kKsSlices;
+}
+
 int pipe_blocks(long long nn) {
     static int sms = 0;
     if (sms == 0) {
@@ -843,11 +856,12 @@ int pipe_blocks(long long nn) {
 
 // Slices per node of the level's kernel: 0 = the streaming kernel (one
 // thread per node), else the K-split kernel with that many slices.  kind: -1
-// by size (streaming from 65,536 nodes, 8 slices below), 0 streaming,
-// 1 / 2 / 3 K-split with 8 / 2 / 4 slices.
+// by size (streaming from 65,536 nodes, below that ks_slices_for), 0 streaming,
+// 1 / 2 / 3 / 4 / 5 K-split with 8 / 2 / 4 / 16 / 32 slices.
 int bsr_slices(long long nn, int kind) {
-    if (kind < 0) return nn >= kBsrStreamLevel ? 0 : kKsSlices;
-    return kind == 0 ? 0 : (kind == 1 ? 8 : (kind == 2 ? 2 : 4));
+    if (kind < 0) return nn >= kBsrStreamLevel ? 0 : ks_slices_for(nn);
+    static const int kSlicesOfKind[kBsrKinds] = {0, 8, 2, 4, 16, 32};
+    return (kind >= 0 && kind < kBsrKinds) ? kSlicesOfKind[kind] : kKsSlices;
 }
 
 int bsr_grid_blocks(long long nn, bool tma, int kind) {
@@ -911,6 +925,8 @@ void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
     }
     if (ns == 8) launch_bsr_ks<8>(mode, dot, g, a, s);
     else if (ns == 2) launch_bsr_ks<2>(mode, dot, g, a, s);
+    else if (ns == 16) launch_bsr_ks<16>(mode, dot, g, a, s);
+    else if (ns == 32) launch_bsr_ks<32>(mode, dot, g, a, s);
     else launch_bsr_ks<4>(mode, dot, g, a, s);
 }
 

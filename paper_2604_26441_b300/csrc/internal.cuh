@@ -354,8 +354,9 @@ struct BsrArgs {
 // Blocks (= dot partials) of the operator launch for a level of nn nodes: 64
 // nodes per block for the TMA-staged and K-split kernels, 256 for streaming.
 // kind: -1 = by size (streaming kernel from 65,536 nodes, K-split below),
-// 0 = streaming k_bsr, 1 / 2 / 3 = K-split k_bsr_ks with 8 / 2 / 4 slices
-// (ignored when tma)
+// 0 = streaming k_bsr, 1 / 2 / 3 / 4 / 5 = K-split k_bsr_ks with 8 / 2 / 4 /
+// 16 / 32 slices (ignored when tma)
+constexpr int kBsrKinds = 6;
 int bsr_grid_blocks(long long nn, bool tma, int kind = -1);
 // Encodes the two tensor maps of a level's FP32 planes; GMG_OK or an error code.
 int encode_bsr_maps(Level& l);

@@ -343,7 +343,7 @@ class Solver:
         return {"fine_tile": ["32x8", "16x16"][t.fine_tile], "fine_zchunk": t.fine_zchunk,
                 "model_tile": ["32x8", "16x16"][t.model_tile], "model_zchunk": t.model_zchunk,
                 "fine_candidates": t.fine_candidates, "fine_us": t.fine_us, "model_us": t.model_us,
-                "bsr": [{"level": l, "kind": ["streaming", "k-split-8", "k-split-2", "k-split-4"][t.bsr_kind[l]],
+                "bsr": [{"level": l, "kind": ["streaming", "k-split-8", "k-split-2", "k-split-4", "k-split-16", "k-split-32"][t.bsr_kind[l]],
                          "us": t.bsr_us[l],
                          "other_us": t.bsr_alt_us[l]} for l in range(1, min(L, 16)) if t.bsr_kind[l] >= 0]}
 
