@@ -128,8 +128,10 @@ void level_resid(gmg_handle* h, int li, const float* b, const float* x, float* t
 }
 
 // One smoother step k on level li: reads x_cur (ignored when zero_init), writes x_next.
+// rfrom (levels >= 1, zero_init only): the finer level's residual; the step then
+// first restricts it into the level's own b (l.b, which b must be).
 void smooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, const float* xcur, float* xnext,
-                 bool write_d, bool dot) {
+                 bool write_d, bool dot, const float* rfrom = nullptr) {
     Level& l = h->lev[li];
     float* d = li == 0 ? h->d0 : l.d;
     cudaStream_t s = h->stream;
@@ -146,7 +148,8 @@ void smooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, c
         BsrArgs a = bsr_args(h, li);
         a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
         a.partial = dot ? h->partials : nullptr;
-        if (zero_init) launch_bsr_smooth0(a, s);
+        if (zero_init && rfrom) launch_restrict_smooth0(h->lev[li - 1], rfrom, a, l.b, s);
+        else if (zero_init) launch_bsr_smooth0(a, s);
         else { a.xin = xcur; launch_bsr(FM_SMOOTH, dot, a, s); }
     }
 }
@@ -154,14 +157,14 @@ void smooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, c
 // A smoothing pass of `degree` steps.  Writes alternate S, X, S, ...; returns the
 // buffer holding the result.  With dot_slot >= 0 the last step also forms b . x.
 float* smooth_pass(gmg_handle* h, int li, const float* b, float* cur, float* X, float* S, bool zero_init,
-                   int& writes, int dot_slot = -1, int op = FIN_NONE) {
+                   int& writes, int dot_slot = -1, int op = FIN_NONE, const float* rfrom = nullptr) {
     Level& l = h->lev[li];
     const bool cheb = l.kind == GMG_SMOOTHER_CHEBYSHEV;
     for (int k = 0; k < l.degree; ++k) {
         float* next = (writes % 2 == 0) ? S : X;
         const bool last = k == l.degree - 1;
         const bool dot = last && dot_slot >= 0;
-        smooth_step(h, li, k, zero_init && k == 0, b, cur, next, cheb && !last, dot);
+        smooth_step(h, li, k, zero_init && k == 0, b, cur, next, cheb && !last, dot, k == 0 ? rfrom : nullptr);
         if (dot) launch_finalize(h->partials, partial_count(h, li, 0), h->sc, dot_slot, op, h->stream);
         cur = next;
         ++writes;
@@ -172,8 +175,11 @@ float* smooth_pass(gmg_handle* h, int li, const float* b, float* cur, float* X, 
 // Eq. vcycle on level li: X = V(b), using S as the ping-pong partner.  With
 // cycle index 2 (W-cycle) the coarse level is visited twice, the second visit
 // starting from the first one's result (warm: pre-smoothing from the current X).
+// rfrom: b is this level's own b, still to be restricted from the finer level's
+// residual rfrom; the first pre-smoothing step does that (one launch instead of
+// a restriction and a first step).
 void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int dot_slot, int op,
-                  bool warm = false) {
+                  bool warm = false, const float* rfrom = nullptr) {
     Level& l = h->lev[li];
     cudaStream_t s = h->stream;
     if (h->use_fused && li == h->cf.start && !warm) {
@@ -187,13 +193,17 @@ void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int
         return;
     }
     int writes = 0;
-    float* cur = smooth_pass(h, li, b, warm ? X : nullptr, X, S, !warm, writes);
+    float* cur = smooth_pass(h, li, b, warm ? X : nullptr, X, S, !warm, writes, -1, FIN_NONE, warm ? nullptr : rfrom);
     float* t = li == 0 ? h->t0 : l.t;
     level_resid(h, li, b, cur, t);
     Level& c = h->lev[li + 1];
-    launch_restrict(l, c, t, c.b, s);
+    // the restriction rides on the coarse level's first smoothing step, except
+    // into the coarsest level (dense solve) or the fused lower V-cycle
+    const bool fuse = li + 1 < h->L - 1 && !(h->use_fused && li + 1 == h->cf.start);
+    if (!fuse) launch_restrict(l, c, t, c.b, s);
     const int gamma = li + 1 == h->L - 1 ? 1 : std::max(1, h->opt.cycle_index);  // exact coarsest: one visit
-    for (int g = 0; g < gamma; ++g) vcycle_level(h, li + 1, c.b, c.x, c.x2, -1, FIN_NONE, g > 0);
+    for (int g = 0; g < gamma; ++g)
+        vcycle_level(h, li + 1, c.b, c.x, c.x2, -1, FIN_NONE, g > 0, fuse && g == 0 ? t : nullptr);
     launch_prolong_add(l, c, c.x, cur, s);
     smooth_pass(h, li, b, cur, X, S, false, writes, dot_slot, op);
 }

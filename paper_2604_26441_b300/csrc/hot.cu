@@ -502,13 +502,11 @@ __device__ __forceinline__ void coarse_parents2(int f, int nf, int idx[2], float
     else { idx[0] = idx[1] = nc; w[0] = 1.f; w[1] = 0.f; }
 }
 
-__global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz, const uint8_t* cmask,
-                           const float* fine, float* coarse) {
-    pdl_entry();
-    const int CX = cnx + 1, CY = cny + 1, nn = CX * CY * (cnz + 1);
+// b_c = P^T t at coarse node n (masked), the restriction of Eq. vcycle.
+__device__ __forceinline__ void restrict_node(int n, int fnx, int fny, int fnz, int cnx, int cny, const uint8_t* cmask,
+                                              const float* fine, float out[3]) {
+    const int CX = cnx + 1, CY = cny + 1;
     const int FX = fnx + 1, FY = fny + 1;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= nn) return;
     const int I = n % CX, J = (n / CX) % CY, K = n / (CX * CY);
     int ix[3], iy[3], iz[3];
     float wx[3], wy[3], wz[3];
@@ -529,9 +527,43 @@ __global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
                 s2 = fmaf(w, fine[3 * f + 2], s2);
             }
     const uint8_t m = cmask[n];
-    coarse[3 * n] = fixed_bit(m, 0) ? 0.f : s0;
-    coarse[3 * n + 1] = fixed_bit(m, 1) ? 0.f : s1;
-    coarse[3 * n + 2] = fixed_bit(m, 2) ? 0.f : s2;
+    out[0] = fixed_bit(m, 0) ? 0.f : s0;
+    out[1] = fixed_bit(m, 1) ? 0.f : s1;
+    out[2] = fixed_bit(m, 2) ? 0.f : s2;
+}
+
+// The restriction fused with the first smoothing step of the coarse level from
+// a zero iterate: b_c = P^T t (stored, later steps and the residual read it),
+// then x = c_a D^-1 b_c (and the Chebyshev increment d = x), with the same
+// arithmetic as k_restrict followed by k_bsr_smooth0.
+__global__ void k_restrict_smooth0(int fnx, int fny, int fnz, const float* fine, BsrArgs a, float* bout) {
+    pdl_entry();
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (int)a.nn) return;
+    float bc[3];
+    restrict_node(n, fnx, fny, fnz, a.nx, a.ny, a.mask, fine, bc);
+    const float ca = (float)a.coef[1];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long q = 3LL * n + c;
+        bout[q] = bc[c];
+        const float v = ca * a.invdiag[q] * bc[c];  // invdiag is 0 on fixed DOFs
+        a.out[q] = v;
+        if (a.dnew) a.dnew[q] = v;
+    }
+}
+
+__global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz, const uint8_t* cmask,
+                           const float* fine, float* coarse) {
+    pdl_entry();
+    const int nn = (cnx + 1) * (cny + 1) * (cnz + 1);
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    float bc[3];
+    restrict_node(n, fnx, fny, fnz, cnx, cny, cmask, fine, bc);
+    coarse[3 * n] = bc[0];
+    coarse[3 * n + 1] = bc[1];
+    coarse[3 * n + 2] = bc[2];
 }
 
 __global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, const uint8_t* fmask,
@@ -998,6 +1030,11 @@ int encode_bsr_maps(Level& l) {
     if (!encode_f32_map(&l.tm_back, l.A32, 2, dims, box_back)) return GMG_ERR_CUDA;
     l.tma = true;
     return GMG_OK;
+}
+
+void launch_restrict_smooth0(const Level& f, const float* t, const BsrArgs& a, float* bout, cudaStream_t s) {
+    note_launch();
+    pdl_launch(k_restrict_smooth0, dim3((int)((a.nn + 127) / 128)), dim3(128), 0, s, f.nx, f.ny, f.nz, t, a, bout);
 }
 
 void launch_bsr_smooth0(const BsrArgs& a, cudaStream_t s) {

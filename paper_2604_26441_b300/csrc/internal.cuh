@@ -361,6 +361,9 @@ int bsr_grid_blocks(long long nn, bool tma, int kind = -1);
 // Encodes the two tensor maps of a level's FP32 planes; GMG_OK or an error code.
 int encode_bsr_maps(Level& l);
 void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s);
+// b = P^T t (restriction from fine level f) fused with the first smoothing
+// step from zero on the coarse level of a (a.b unused; b is written to bout).
+void launch_restrict_smooth0(const Level& f, const float* t, const BsrArgs& a, float* bout, cudaStream_t s);
 void launch_bsr_smooth0(const BsrArgs& a, cudaStream_t s);
 
 void launch_restrict(const Level& f, const Level& c, const float* fine, float* coarse, cudaStream_t s);
