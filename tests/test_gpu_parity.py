@@ -142,11 +142,13 @@ def test_masks_and_galerkin_operators(name, nx, ny, nz, levels, mask):
         assert np.max(np.abs(A - R)) <= 1e-12 * np.max(np.abs(R))
 
 
-# Kernels of the assembled levels: the default at these sizes (all K-split),
-# bsr_tma_nodes=1 forces the TMA-staged kernel onto every assembled level, and
-# bsr_kernel=0 the streaming one-thread-per-node kernel.
+# Kernels of the assembled levels: the default at these sizes (K-split with 32 or
+# 16 slices by the size rule), bsr_tma_nodes=1 forces the TMA-staged kernel onto
+# every assembled level, bsr_kernel=0 the streaming one-thread-per-node kernel,
+# and bsr_kernel=1 / 2 the K-split kernel with 8 / 2 slices.
 KERNEL_MODES = [pytest.param({}, id="ksplit"), pytest.param({"bsr_tma_nodes": 1}, id="tma"),
-                pytest.param({"bsr_kernel": 0}, id="stream")]
+                pytest.param({"bsr_kernel": 0}, id="stream"), pytest.param({"bsr_kernel": 1}, id="ks8"),
+                pytest.param({"bsr_kernel": 2}, id="ks2")]
 
 
 @pytest.mark.parametrize("kmode", KERNEL_MODES)
