@@ -551,12 +551,15 @@ void pcg_restart(gmg_handle* h) {
     vcycle_level(h, 0, h->r, h->z, h->x2_0, SC_RZ, FIN_NONE);
     launch_copy_f32(h->p, h->z, n, h->stream);
 }
-// q = K p, alpha = rz / p.q, u += alpha p, r -= alpha q, ||r||^2
-void pcg_step(gmg_handle* h, double* u) {
+// q = K p, alpha = rz / p.q, u += alpha p, r -= alpha q, ||r||^2; with cond
+// (inside the captured loop) the ||r||^2 reduction also takes the loop's
+// convergence test.
+void pcg_step(gmg_handle* h, double* u, const cudaGraphConditionalHandle* cond = nullptr) {
     const long long n = 3 * h->lev[0].nn;
     level_apply(h, 0, h->p, h->q, SC_PQ, FIN_ALPHA);
     launch_pcg_update(u, h->r, h->p, h->q, n, h->sc, h->partials, h->stream);
-    launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_RR, FIN_NONE, h->stream);
+    if (cond) launch_finalize_check(h->partials, vec_grid_blocks(), h->sc, *cond, h->stream);
+    else launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_RR, FIN_NONE, h->stream);
 }
 // z = V(r), beta = r.z / rz, p = z + beta p
 void pcg_direction(gmg_handle* h) {
@@ -600,8 +603,7 @@ bool capture_loop(gmg_handle* h, double* u, cudaGraph_t g, cudaStream_t cap, uns
     if (ok) ok = cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
     if (ok) {
         pcg_restart(h);
-        pcg_step(h, u);
-        launch_loop_check(h->sc, cond, cap);
+        pcg_step(h, u, &cond);
         l1 = g_kernel_launches.load();
         cudaStreamCaptureStatus st{};
         cudaGraph_t cg = nullptr;
@@ -625,8 +627,7 @@ bool capture_loop(gmg_handle* h, double* u, cudaGraph_t g, cudaStream_t cap, uns
         ok = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
         if (ok) {
             pcg_direction(h);
-            pcg_step(h, u);
-            launch_loop_check(h->sc, cond, cap);
+            pcg_step(h, u, &cond);
             l2 = g_kernel_launches.load();
             ok = cudaStreamEndCapture(cap, &body) == cudaSuccess;
         }

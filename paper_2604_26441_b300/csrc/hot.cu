@@ -749,12 +749,19 @@ __global__ void k_axpy_u64(double* u, const float* z, long long n, double a) {
         u[i] = fma(a, (double)z[i], u[i]);
 }
 
-__global__ void k_loop_check(double* sc, cudaGraphConditionalHandle cond) {
+// ||r||^2 from the partial sums (the same sum as k_finalize into SC_RR), then
+// the convergence test of the device-resident loop in the same launch.
+__global__ void __launch_bounds__(kVecThreads) k_finalize_check(const double* partial, int n, double* sc,
+                                                                cudaGraphConditionalHandle cond) {
     pdl_entry();
+    double s = 0.0;
+    for (int q = threadIdx.x; q < n; q += kVecThreads) s += partial[q];
+    s = block_sum<kVecThreads>(s, threadIdx.x);
     if (threadIdx.x != 0) return;
+    sc[SC_RR] = s;
     const double k = sc[SC_IT] + 1.0;
     sc[SC_IT] = k;
-    const double relr = sqrt(sc[SC_RR]) / sc[SC_NF];
+    const double relr = sqrt(s) / sc[SC_NF];
     const bool go = isfinite(relr) && isfinite(sc[SC_ALPHA]) && !(relr < sc[SC_TOL]) && k < sc[SC_MAXIT];
     cudaGraphSetConditional(cond, go ? 1u : 0u);
 }
@@ -1178,9 +1185,10 @@ void launch_axpy_u64(double* u, const float* z, long long n, double a, cudaStrea
     pdl_launch(k_axpy_u64, dim3(grid_for(n)), dim3(256), 0, s, u, z, n, a);
 }
 
-void launch_loop_check(double* sc, cudaGraphConditionalHandle cond, cudaStream_t s) {
+void launch_finalize_check(const double* partial, int n, double* sc, cudaGraphConditionalHandle cond,
+                           cudaStream_t s) {
     note_launch();
-    pdl_launch(k_loop_check, dim3(1), dim3(32), 0, s, sc, cond);
+    pdl_launch(k_finalize_check, dim3(1), dim3(kVecThreads), 0, s, partial, n, sc, cond);
 }
 
 void launch_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r, cudaStream_t s) {

@@ -405,10 +405,12 @@ void launch_pcg_update(double* u, float* r, const float* p, const float* q, long
 void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s);
 void launch_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial, cudaStream_t s);
 void launch_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r, cudaStream_t s);
-// Convergence test of the device-resident loop: counts the iteration and sets
-// the while-node condition to 1 while ||r|| / ||f|| >= tol, the scalars are
-// finite and the cap is not reached.
-void launch_loop_check(double* sc, cudaGraphConditionalHandle cond, cudaStream_t s);
+// ||r||^2 into SC_RR (as launch_finalize) and the convergence test of the
+// device-resident loop: counts the iteration and sets the while-node condition
+// to 1 while ||r|| / ||f|| >= tol, the scalars are finite and the cap is not
+// reached.
+void launch_finalize_check(const double* partial, int n, double* sc, cudaGraphConditionalHandle cond,
+                           cudaStream_t s);
 void launch_axpy_dev(float* y, const float* x, long long n, const double* coef, float sign, cudaStream_t s);
 void launch_axpy_u64(double* u, const float* z, long long n, double a, cudaStream_t s);
 void launch_scale_by_inv_sqrt(float* v, long long n, const double* sc, int slot, cudaStream_t s);
