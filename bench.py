@@ -497,6 +497,14 @@ def main():
     ev_s = [torch.cuda.Event() for _ in range(2)]
     ev_d = [torch.cuda.Event() for _ in range(2)]
     e2e_infos = []
+    # untimed warm-up on the same buffers: the handle captures its PCG loop graph
+    # once per iterate buffer (loop_select), a one-time cost that is not a step's
+    for _ in range(max(1, args.warmup // 2)):
+        for i in range(2):
+            f_devs[i].copy_(f_hosts[i], non_blocking=True)
+            u_devs[i].zero_()
+            S.solve(f_devs[i], u_devs[i], tol=cfg.tol, maxit=cfg.maxit)
+            u_hosts[i].copy_(u_devs[i], non_blocking=True)
     flush_l2(0)
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
