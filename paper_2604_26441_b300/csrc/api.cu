@@ -73,7 +73,7 @@ FineArgs fine_args(gmg_handle* h) {
     const Level& l = h->lev[0];
     FineArgs a{};
     a.nx = l.nx; a.ny = l.ny; a.nz = l.nz;
-    a.E = h->E32; a.mask = l.mask; a.kd = h->kd; a.coef = l.coef;
+    a.E = h->E32; a.mask = l.mask; a.kd = h->kd; a.inv0 = h->inv0; a.coef = l.coef;
     a.tcB = h->tcB; a.err = h->kerr;
     return a;
 }
@@ -393,6 +393,8 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     CU(cudaStreamSynchronize(s));
     for (int i = 0; i < 576; ++i) h->keF.v[i] = (float)h->keD.v[i];
     h->kd = h->keF.v[0];
+    TRY(dalloc(h, &h->inv0, l0.nn));
+    launch_fine_inv0(l0.nx, l0.ny, l0.nz, h->E32, h->kd, h->inv0, s);
     {
         double* g72 = nullptr;
         double gh[72];

@@ -47,12 +47,11 @@ __device__ __forceinline__ double block_sum(double v, int tid) {
 
 __device__ __forceinline__ bool fixed_bit(uint8_t m, int c) { return (m >> c) & 1; }
 
-// First smoother step from x = 0: x_1 = c_a D^{-1} b (no operator application).
-__global__ void k_fine_smooth0(FineArgs a) {
-    pdl_entry();
-    const long long NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
+// The fine level's Jacobi scale per node, 1 / (kd * sum of the moduli of the
+// elements around it) (the diagonal of K is kd E_e summed over those elements).
+__global__ void k_fine_inv0(int nx, int ny, int nz, const float* E, float kd, float* inv0) {
+    const long long NX = nx + 1, NY = ny + 1, NZ = nz + 1;
     const long long nn = NX * NY * NZ;
-    const float ca = (float)a.coef[1];
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
          n += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
@@ -60,10 +59,22 @@ __global__ void k_fine_smooth0(FineArgs a) {
 #pragma unroll
         for (int ea = 0; ea < 8; ++ea) {
             const int ex = i - ldx(ea), ey = j - ldy(ea), ez = k - ldz(ea);
-            if (ex >= 0 && ex < a.nx && ey >= 0 && ey < a.ny && ez >= 0 && ez < a.nz)
-                esum += a.E[ex + (long long)a.nx * (ey + (long long)a.ny * ez)];
+            if (ex >= 0 && ex < nx && ey >= 0 && ey < ny && ez >= 0 && ez < nz)
+                esum += E[ex + (long long)nx * (ey + (long long)ny * ez)];
         }
-        const float inv = 1.f / (a.kd * esum);
+        inv0[n] = 1.f / (kd * esum);
+    }
+}
+
+// First smoother step from x = 0: x_1 = c_a D^{-1} b (no operator application),
+// with the Jacobi scale from set-up.
+__global__ void k_fine_smooth0(FineArgs a) {
+    pdl_entry();
+    const long long nn = (long long)(a.nx + 1) * (a.ny + 1) * (a.nz + 1);
+    const float ca = (float)a.coef[1];
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
+         n += (long long)gridDim.x * blockDim.x) {
+        const float inv = a.inv0[n];
         const uint8_t m = a.mask[n];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -872,6 +883,11 @@ __global__ void k_power_start(float* v, const uint8_t* mask, long long nn) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+void launch_fine_inv0(int nx, int ny, int nz, const float* E, float kd, float* inv0, cudaStream_t s) {
+    note_launch();
+    k_fine_inv0<<<kVecBlocks * 2, kVecThreads, 0, s>>>(nx, ny, nz, E, kd, inv0);
+}
+
 void launch_fine_smooth0(const FineArgs& a, cudaStream_t s) {
     note_launch();
     pdl_launch(k_fine_smooth0, dim3(kVecBlocks * 2), dim3(kVecThreads), 0, s, a);

@@ -231,6 +231,7 @@ struct gmg_handle {
     gmg::GHat gh{};
     gmg::GHat64 gh64{};
     float kd = 0.f;                             // diagonal entry of K_e (all equal)
+    float* inv0 = nullptr;                      // [n_nodes] fine Jacobi scale 1 / (kd * sum of adjacent E_e)
     double* lam = nullptr;                      // [kMaxLevels] lambda estimates (device)
     // fine-level PCG vectors
     float *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x2_0 = nullptr, *t0 = nullptr, *d0 = nullptr;
@@ -305,6 +306,7 @@ struct FineArgs {
     int step;
     double* partial;       // per-block partial dots (nullptr = none)
     float kd;
+    const float* inv0;     // [n_nodes] 1 / (kd * sum of the adjacent moduli), from set-up
     float* scratch;        // fine-level vector used to mask a caller's operand (apply only)
     const void* tcB;       // tensor-core smoother: BF16 mode-to-corner operand (hi, lo), 4 KB
     int* err;              // sticky error word (a tensor-core wait that gave up)
@@ -327,6 +329,8 @@ void launch_fine_tc(int passes, int dot, const FineArgs& a, cudaStream_t s);
 void build_tc_operand(const double g[72], uint16_t out[2048]);
 int resid64_grid_blocks(int nx, int ny, int nz);
 void launch_fine_smooth0(const FineArgs& a, cudaStream_t s);
+// inv0[n] = 1 / (kd * sum of the moduli of the elements around node n), once at set-up.
+void launch_fine_inv0(int nx, int ny, int nz, const float* E, float kd, float* inv0, cudaStream_t s);
 void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,
                          const double* f, const double* u, double* r64, float* r32,
                          const double* sc, double* partial, const GHat64& G, cudaStream_t s);
