@@ -162,20 +162,22 @@ __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
             const int off = dx + NX * (dy + NY * dz);
             const bool okf = i + dx >= 0 && i + dx < NX && j + dy >= 0 && j + dy < NY && k + dz < NZ;
             const int mf = okf ? n + off : n;
+            // operator and iterate through the read-only data path
             const float* A = a.A + (long long)(u * 9) * N + n;
-            const float v0 = a.xin[3 * mf], v1 = a.xin[3 * mf + 1], v2 = a.xin[3 * mf + 2];
-            y0 = fmaf(A[0 * N], v0, fmaf(A[1 * N], v1, fmaf(A[2 * N], v2, y0)));
-            y1 = fmaf(A[3 * N], v0, fmaf(A[4 * N], v1, fmaf(A[5 * N], v2, y1)));
-            y2 = fmaf(A[6 * N], v0, fmaf(A[7 * N], v1, fmaf(A[8 * N], v2, y2)));
+            const float v0 = __ldg(a.xin + 3 * mf), v1 = __ldg(a.xin + 3 * mf + 1), v2 = __ldg(a.xin + 3 * mf + 2);
+            y0 = fmaf(__ldg(A + 0 * N), v0, fmaf(__ldg(A + 1 * N), v1, fmaf(__ldg(A + 2 * N), v2, y0)));
+            y1 = fmaf(__ldg(A + 3 * N), v0, fmaf(__ldg(A + 4 * N), v1, fmaf(__ldg(A + 5 * N), v2, y1)));
+            y2 = fmaf(__ldg(A + 6 * N), v0, fmaf(__ldg(A + 7 * N), v1, fmaf(__ldg(A + 8 * N), v2, y2)));
             if (u > 0) {
                 const bool okb = i - dx >= 0 && i - dx < NX && j - dy >= 0 && j - dy < NY && k - dz >= 0;
                 const int mb = okb ? n - off : n;
                 const float wgt = okb ? 1.f : 0.f;
                 const float* B = a.A + (long long)(u * 9) * N + mb;
-                const float w0 = wgt * a.xin[3 * mb], w1 = wgt * a.xin[3 * mb + 1], w2 = wgt * a.xin[3 * mb + 2];
-                y0 = fmaf(B[0 * N], w0, fmaf(B[3 * N], w1, fmaf(B[6 * N], w2, y0)));
-                y1 = fmaf(B[1 * N], w0, fmaf(B[4 * N], w1, fmaf(B[7 * N], w2, y1)));
-                y2 = fmaf(B[2 * N], w0, fmaf(B[5 * N], w1, fmaf(B[8 * N], w2, y2)));
+                const float w0 = wgt * __ldg(a.xin + 3 * mb), w1 = wgt * __ldg(a.xin + 3 * mb + 1),
+                            w2 = wgt * __ldg(a.xin + 3 * mb + 2);
+                y0 = fmaf(__ldg(B + 0 * N), w0, fmaf(__ldg(B + 3 * N), w1, fmaf(__ldg(B + 6 * N), w2, y0)));
+                y1 = fmaf(__ldg(B + 1 * N), w0, fmaf(__ldg(B + 4 * N), w1, fmaf(__ldg(B + 7 * N), w2, y1)));
+                y2 = fmaf(__ldg(B + 2 * N), w0, fmaf(__ldg(B + 5 * N), w1, fmaf(__ldg(B + 8 * N), w2, y2)));
             }
         }
         const float y[3] = {y0, y1, y2};
@@ -444,16 +446,18 @@ __global__ void __launch_bounds__(256) k_bsr_ks(BsrArgs a) {
             const bool ok = live && i + sx >= 0 && i + sx < NX && j + sy >= 0 && j + sy < NY && k + sz >= 0 && k + sz < NZ;
             const int m = ok ? (fwd ? nsafe + off : nsafe - off) : nsafe;
             const float wgt = ok ? 1.f : 0.f;
-            const float v0 = wgt * a.xin[3 * m], v1 = wgt * a.xin[3 * m + 1], v2 = wgt * a.xin[3 * m + 2];
+            // operator and iterate through the read-only data path
+            const float v0 = wgt * __ldg(a.xin + 3 * m), v1 = wgt * __ldg(a.xin + 3 * m + 1),
+                        v2 = wgt * __ldg(a.xin + 3 * m + 2);
             const float* A = a.A + (long long)(u * 9) * N + (fwd ? nsafe : m);
             if (fwd) {
-                y0 = fmaf(A[0 * N], v0, fmaf(A[1 * N], v1, fmaf(A[2 * N], v2, y0)));
-                y1 = fmaf(A[3 * N], v0, fmaf(A[4 * N], v1, fmaf(A[5 * N], v2, y1)));
-                y2 = fmaf(A[6 * N], v0, fmaf(A[7 * N], v1, fmaf(A[8 * N], v2, y2)));
+                y0 = fmaf(__ldg(A + 0 * N), v0, fmaf(__ldg(A + 1 * N), v1, fmaf(__ldg(A + 2 * N), v2, y0)));
+                y1 = fmaf(__ldg(A + 3 * N), v0, fmaf(__ldg(A + 4 * N), v1, fmaf(__ldg(A + 5 * N), v2, y1)));
+                y2 = fmaf(__ldg(A + 6 * N), v0, fmaf(__ldg(A + 7 * N), v1, fmaf(__ldg(A + 8 * N), v2, y2)));
             } else {
-                y0 = fmaf(A[0 * N], v0, fmaf(A[3 * N], v1, fmaf(A[6 * N], v2, y0)));
-                y1 = fmaf(A[1 * N], v0, fmaf(A[4 * N], v1, fmaf(A[7 * N], v2, y1)));
-                y2 = fmaf(A[2 * N], v0, fmaf(A[5 * N], v1, fmaf(A[8 * N], v2, y2)));
+                y0 = fmaf(__ldg(A + 0 * N), v0, fmaf(__ldg(A + 3 * N), v1, fmaf(__ldg(A + 6 * N), v2, y0)));
+                y1 = fmaf(__ldg(A + 1 * N), v0, fmaf(__ldg(A + 4 * N), v1, fmaf(__ldg(A + 7 * N), v2, y1)));
+                y2 = fmaf(__ldg(A + 2 * N), v0, fmaf(__ldg(A + 5 * N), v1, fmaf(__ldg(A + 8 * N), v2, y2)));
             }
         }
     }
