@@ -102,7 +102,7 @@ def _child_weights_1d(e: np.ndarray, nf: int) -> tuple[np.ndarray, np.ndarray]:
 
 
 def level1_elementwise(dims_f, E: np.ndarray, Ke: np.ndarray, fixed_f: np.ndarray,
-                       fixed_c: np.ndarray, batch: int = 8192) -> sp.csr_matrix:
+                       fixed_c: np.ndarray, batch: int = 65536) -> sp.csr_matrix:
     """Eq. galerkin_level1: K^1 = sum_e E_e (P_e)^T K_e P_e, where P_e is the 24x24
     restriction of the prolongation to fine element e (its coarse parent's eight
     nodes -> its own eight nodes, rows of fixed fine DOFs removed).  Returned on
@@ -121,7 +121,9 @@ def level1_elementwise(dims_f, E: np.ndarray, Ke: np.ndarray, fixed_f: np.ndarra
         cen[:, b] = gc.node(cx + bx, cy + by, cz + bz)
     cdofs = (3 * cen[:, :, None] + np.arange(3)).reshape(-1, 24)
     free_f = (np.asarray(fixed_f) == 0).astype(np.float64)
-    rows_all, cols_all, vals_all = [], [], []
+    # Contributions are summed batch by batch into one sparse matrix, so memory
+    # stays near the size of K^1 itself rather than of all 576 n_elem terms.
+    K1 = sp.csr_matrix((gc.n_dof, gc.n_dof))
     for s in range(0, ex.size, batch):
         sl = slice(s, min(s + batch, ex.size))
         n = sl.stop - sl.start
@@ -134,12 +136,9 @@ def level1_elementwise(dims_f, E: np.ndarray, Ke: np.ndarray, fixed_f: np.ndarra
         Pe *= free_f[fdofs[sl]][:, :, None]
         T = np.einsum("nai,ab,nbj->nij", Pe, Ke, Pe, optimize=True) * E[sl, None, None]
         d = cdofs[sl]
-        rows_all.append(np.repeat(d, 24, axis=1).reshape(-1))
-        cols_all.append(np.tile(d, (1, 24)).reshape(-1))
-        vals_all.append(T.reshape(-1))
-    K1 = sp.coo_matrix((np.concatenate(vals_all),
-                        (np.concatenate(rows_all), np.concatenate(cols_all))),
-                       shape=(gc.n_dof, gc.n_dof)).tocsr()
+        K1 = K1 + sp.coo_matrix((T.reshape(-1), (np.repeat(d, 24, axis=1).reshape(-1),
+                                                 np.tile(d, (1, 24)).reshape(-1))),
+                                shape=(gc.n_dof, gc.n_dof)).tocsr()
     fc = free_dofs(fixed_c)
     return K1[fc][:, fc].tocsr()
 
