@@ -23,7 +23,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -36,7 +35,6 @@ METRIC = "solves/s at rel. residual 1e-6 (1M hex8) vs plain FP32-GMG; fine-op % 
 UNIT = "solves/s"
 WORKLOAD = ("cantilever 100x100x100 hex8 (1,000,000 elements, 3,060,300 free DOF), uniform rho=0.5, p=3, "
             "5-level Galerkin GMG, Chebyshev degree 3, PCG tol 1e-6 (FP64 true residual), cap 200")
-SAMPLE_N = 50          # edge of the cube solved by the CPU oracle as the bounded sample
 FLUSH_BYTES = 256 << 20  # > 2x the 126 MB L2 (written, then a second buffer is read so no dirty lines remain)
 
 
@@ -50,54 +48,153 @@ def _args():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-warmstart", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle leg (a separate, freshly spawned interpreter with one thread)
+# CPU oracle leg (a separate, freshly spawned interpreter)
 # ---------------------------------------------------------------------------
+# The oracle (FP64, numpy/scipy) builds the same 100^3 hierarchy (matrix-free
+# fine level, element-wise level 1) and runs its own GMG-PCG on the same load.
+# A full oracle solve takes about a minute, so the bounded sample is a number
+# of its PCG iterations: the oracle runs as it stands, and a wrapper around the
+# preconditioner it is given only records a timestamp per call (one call per
+# iteration).  A solve that converges is restarted from zero until enough
+# iterations are recorded.  solves/s = 1 / (mean iteration time x iterations
+# of one complete oracle solve).
 _ORACLE_SNIPPET = r"""
-import json, sys, time
+import json, os, sys, time
 sys.path.insert(0, {root!r})
+import contextlib, ctypes
 from oracle import fem, hierarchy as hy, solver as so
+
+
+def _blas_setter():
+    # numpy's bundled OpenBLAS: its thread-count setter, looked up by name in the
+    # loaded libraries (used when threadpoolctl is not installed)
+    import numpy
+    numpy.ones((2, 2)) @ numpy.ones((2, 2))
+    for line in open("/proc/self/maps"):
+        path = line.split()[-1]
+        if "openblas" not in path or not path.endswith(".so") and ".so" not in path:
+            continue
+        try:
+            lib = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for name in ("scipy_openblas_set_num_threads64_", "scipy_openblas_set_num_threads",
+                     "openblas_set_num_threads64_", "openblas_set_num_threads"):
+            fn = getattr(lib, name, None)
+            if fn is not None:
+                return fn
+    return None
+
+
+LIMITS_OK = True
+try:
+    from threadpoolctl import threadpool_limits
+except ImportError:
+    _set = _blas_setter()
+    LIMITS_OK = _set is not None
+
+    @contextlib.contextmanager
+    def threadpool_limits(limits=None):
+        if limits is None or _set is None:
+            yield
+            return
+        _set(int(limits))
+        try:
+            yield
+        finally:
+            _set(os.cpu_count())
 from paper_2604_26441_b300 import inputs
-n, reps = {n}, {reps}
-rho = inputs.uniform_density(n, n, n, 0.5)
+c = inputs.CONFIGS["c2"]
 t0 = time.perf_counter()
-H = hy.build_hierarchy((n, n, n), fem.moduli(rho, 3.0), inputs.clamp_xmin_mask(n, n, n), levels=4)
-t1 = time.perf_counter()
-spec = so.SmootherSpec("chebyshev", 3)
-times, its, rel = [], [], []
-for _ in range(reps):
-    s = time.perf_counter()
-    u, res = so.gmg_pcg(H, inputs.tip_edge_load(n, n, n), spec, tol=1e-6, maxit=200)
-    times.append(time.perf_counter() - s)
-    its.append(res.iterations); rel.append(res.rel_residual)
-print(json.dumps({{"setup_s": t1 - t0, "solve_s": times, "iterations": its, "rel": rel}}))
+H = hy.build_hierarchy((c.nx, c.ny, c.nz), fem.moduli(c.rho(), c.p), c.fixed(), levels=c.levels,
+                       matrix_free_fine=True)
+setup_s = time.perf_counter() - t0
+spec = so.SmootherSpec("chebyshev", c.degree, c.omega, 1.0 / 30.0, 1.1)
+f = c.load()
+
+
+class Enough(Exception):
+    pass
+
+
+def sample(n_iter, threads):
+    its, solves, last = [], [], [None]
+
+    def precond(r):
+        t = time.perf_counter()
+        if last[0] is not None:
+            its.append(t - last[0])
+            if len(its) >= n_iter:
+                raise Enough()
+        last[0] = t
+        return so.vcycle(H, r, spec)
+
+    with threadpool_limits(limits=threads):
+        try:
+            while True:
+                last[0] = None
+                res = so.pcg(H[0].apply, precond, f[H[0].free], None, c.tol, c.maxit)
+                solves.append(res.iterations)
+        except Enough:
+            pass
+    return its, solves
+
+
+plan = json.loads({plan!r})
+out = dict(setup_s=setup_s, nproc=os.cpu_count(), runs=[])
+for threads, n_iter in plan:
+    if threads is not None and not LIMITS_OK:
+        continue  # no way to limit the BLAS threads here: the run is left out, not mislabelled
+    its, solves = sample(n_iter, threads)
+    out["runs"].append(dict(threads=threads, iter_s=its, solve_iterations=solves))
+print(json.dumps(out))
 """
 
 
-def run_oracle_sample(reps: int) -> dict:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _ORACLE_SNIPPET.format(root=ROOT, n=SAMPLE_N, reps=reps)
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+def run_oracle_sample(plan: list) -> dict:
+    """plan: [(threads or None for all cores, PCG iterations to record), ...]."""
+    code = _ORACLE_SNIPPET.format(root=ROOT, plan=json.dumps(plan))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def oracle_rate(rec: dict) -> float:
-    """Sample solves/s scaled to the 1M-element workload by the element count."""
-    scale = (SAMPLE_N ** 3) / 1_000_000
-    return scale / statistics.mean(rec["solve_s"])
+def oracle_run_rate(run: dict, per_solve: int, skip: int = 0) -> tuple[float, float]:
+    """(solves/s, ms per iteration) of one sampled run, ignoring its first `skip`
+    iterations (warm-up); per_solve = iterations of one complete oracle solve."""
+    ms = 1000.0 * statistics.mean(run["iter_s"][skip:])
+    return 1000.0 / (ms * per_solve), ms
 
 
-def cpu_baseline_obj(rec: dict) -> dict:
-    return {"value": oracle_rate(rec), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 CPU oracle (numpy/scipy, 1 thread): GMG-PCG solve of the {SAMPLE_N}^3 cantilever of "
-                       f"the same recipe (4 levels, Chebyshev 3), {len(rec['solve_s'])} solves, mean "
-                       f"{statistics.mean(rec['solve_s']):.2f} s, {rec['iterations'][0]} iterations, setup "
-                       f"{rec['setup_s']:.1f} s excluded; rate scaled by element count x{SAMPLE_N ** 3 / 1e6:.3f}")}
+# all cores for a complete oracle solve (14 PCG iterations at 100^3; the 14th
+# recorded interval belongs to the restarted solve, so the first one completes),
+# then two iterations on one thread
+CPU_BASELINE_PLAN = [(None, 14), (1, 2)]
+
+
+def cpu_baseline_obj(rec: dict, skip: int = 1) -> dict:
+    runs = rec["runs"]
+    per_solve = runs[0]["solve_iterations"][0]
+    rate, ms = oracle_run_rate(runs[0], per_solve, skip)
+    threads = runs[0]["threads"] or rec["nproc"]
+    desc = [f"FP64 CPU oracle (numpy/scipy) on the same 100^3 workload: hierarchy set-up {rec['setup_s']:.1f} s "
+            f"(excluded), then its GMG-PCG; sample = {len(runs[0]['iter_s']) - skip} PCG iterations after {skip} "
+            f"warm-up, {ms:.0f} ms each on {threads} threads (nproc {rec['nproc']}); a complete oracle solve "
+            f"takes {per_solve} iterations, solves/s = 1 / (iteration time x {per_solve})"]
+    obj = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "nproc": rec["nproc"],
+           "oracle_iterations": per_solve, "oracle_setup_s": rec["setup_s"]}
+    for run in runs[1:]:
+        r1, ms1 = oracle_run_rate(run, per_solve, 0)
+        desc.append(f"{run['threads']} thread(s): {ms1:.0f} ms per iteration = {r1:.4f} solves/s")
+        obj[f"value_{run['threads']}_thread"] = r1
+    obj["sample"] = "; ".join(desc)
+    return obj
 
 
 # ---------------------------------------------------------------------------
@@ -158,19 +255,16 @@ def _peaks() -> tuple[float, str]:
 
 
 def _profile_traffic(kernel_src: str) -> float | None:
-    """DRAM bytes per launch of the fine operator from the committed ncu summary,
-    if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "fine_smooth_c2_ncu.md")
+    """DRAM bytes per launch of the fine operator from the committed ncu figure
+    (profiles/fine_smooth_c2_traffic.json), if it was taken on the current
+    kernel source; None otherwise."""
     try:
-        text = open(path).read()
-    except OSError:
+        with open(os.path.join(ROOT, "profiles", "fine_smooth_c2_traffic.json")) as fh:
+            rec = json.load(fh)
+        cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    except (OSError, ValueError):
         return None
-    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    m_h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
-    if not m_b or not m_h:
-        return None
-    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return float(m_b.group(1)) if m_h.group(1) == cur else None
+    return float(rec["dram_bytes_per_launch"]) if rec.get("kernel_source_sha256") == cur else None
 
 
 def max_over_ranks(ms: float, world: int, device) -> float:
@@ -323,6 +417,110 @@ def configs_leg(dev, stream, flush_l2) -> list:
     return out
 
 
+# The FP64 oracle's reference solution of the 40^3 configuration (p = 3): its
+# own GMG-PCG on the assembled hierarchy, run to a 1e-12 true residual.
+_ORACLE_C1_SNIPPET = r"""
+import sys
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import fem, hierarchy as hy, solver as so
+from paper_2604_26441_b300 import inputs
+c = inputs.CONFIGS["c1"]
+H = hy.build_hierarchy((c.nx, c.ny, c.nz), fem.moduli(c.rho(), 3.0), c.fixed(), levels=c.levels)
+u = so.exact_solve(H, c.load(), so.SmootherSpec(c.smoother, c.degree, c.omega))
+np.save({out!r}, u)
+"""
+
+
+def oracle_c1_solution() -> "np.ndarray":
+    import tempfile
+
+    import numpy as np
+    with tempfile.TemporaryDirectory() as d:
+        out = os.path.join(d, "u.npy")
+        res = subprocess.run([sys.executable, "-c", _ORACLE_C1_SNIPPET.format(root=ROOT, out=out)],
+                             capture_output=True, text=True, timeout=1200)
+        if res.returncode != 0:
+            raise RuntimeError("oracle 40^3 solve failed: " + res.stderr[-2000:])
+        return np.load(out)
+
+
+PRECISION_VARIANTS = (
+    ("fp32-pcg", dict()),
+    ("bf16x3-pcg", dict(fine_smoother="bf16x3")),
+    ("bf16-fgmres32", dict(fine_smoother="bf16", outer="fgmres", restart=32)),
+)
+
+
+def precision_leg(dev, stream, flush_l2, u_c1_oracle) -> dict:
+    """The precision line (Sec. "Mixed precision", Eq. prec_schedule) on the
+    40^3 (p = 3) and 100^3 configurations: the FP32 solver, the split-BF16
+    tensor-core fine smoother under PCG, the plain BF16 one under FGMRES(32)
+    (the paper's BF16 pairing), each to the FP64 true residual 1e-6, and PCG
+    inside outer FP64 iterative refinement (ir_factor 1e-3) to 1e-10.  Error:
+    relative L2 against the oracle's 1e-12 solution (40^3) or against the
+    GPU's own FP64-refined 1e-10 solution (100^3; the headline parity test ties
+    the GPU's 100^3 solution to the oracle's).  Also the 100^3 Chebyshev band's
+    safety factor at 1.0 (the literal reading) next to the default 1.1."""
+    import numpy as np
+    import torch
+
+    from paper_2604_26441_b300 import gmg, inputs
+
+    def run(cfg, p, tol, reps=5, **kw):
+        rho = torch.from_numpy(cfg.rho()).to(dev)
+        opt = gmg.config_options(cfg, stream=stream.cuda_stream,
+                                 **{k: v for k, v in kw.items() if k != "lambda_safety"})
+        if "lambda_safety" in kw:
+            opt.lambda_safety = kw["lambda_safety"]
+        S = gmg.Solver(rho, p=p, opts=opt)
+        f = torch.from_numpy(cfg.load()).to(dev)
+        u = torch.zeros_like(f)
+        for _ in range(2):
+            u.zero_()
+            S.solve(f, u, tol=tol, maxit=cfg.maxit)
+        ms, info = [], None
+        for k in range(reps):
+            flush_l2(k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            u.zero_()
+            _, info = S.solve(f, u, tol=tol, maxit=cfg.maxit)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        out = u.cpu().numpy()
+        S.close()
+        med = statistics.median(ms)
+        return out, {"solves_per_s": 1000.0 / med, "solve_ms": med, "iterations": info["iterations"],
+                     "restarts_or_replacements": info["replacements"], "status": info["status"],
+                     "rel_residual_fp64": info["rel_residual"]}
+
+    def err(u, ref):
+        return float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+
+    legs = {}
+    for name, cfg, p, ref in (("c1_p3", inputs.CONFIGS["c1"], 3.0, u_c1_oracle), ("c2", inputs.CONFIGS["c2"], 3.0, None)):
+        u_ir, rec_ir = run(cfg, p, 1e-10, ir_factor=1e-3)
+        if ref is None:
+            ref, ref_kind = u_ir, "GPU FP64-refined solution at 1e-10"
+        else:
+            ref_kind = "oracle GMG-PCG to 1e-12"
+        rows = {}
+        for vname, kw in PRECISION_VARIANTS:
+            u, rec = run(cfg, p, cfg.tol, **kw)
+            rec["error_vs_reference"] = err(u, ref)
+            rows[vname] = rec
+        rec_ir["error_vs_reference"] = err(u_ir, ref)
+        rows["fp32-pcg-ir-1e-10"] = rec_ir
+        if name == "c2":
+            u, rec = run(cfg, p, cfg.tol, lambda_safety=1.0)
+            rec["error_vs_reference"] = err(u, ref)
+            rows["fp32-pcg-lambda_safety-1.0"] = rec
+        legs[name] = {"reference": ref_kind, "variants": rows}
+    return legs
+
+
 WARM_SOLVES, WARM_STEPS, WARM_BATCH, WARM_EVAL = 2000, 4000, 4, 4
 
 
@@ -385,16 +583,22 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        reps = args.warmup + args.steps
-        rec = run_oracle_sample(reps)
-        times = rec["solve_s"][args.warmup:]
-        value = (SAMPLE_N ** 3 / 1e6) / statistics.mean(times)
+        # one step = one PCG iteration of the oracle's 100^3 solve (all host cores)
+        # (at least 14 recorded iterations, so that one oracle solve completes and
+        # gives its iteration count; the timed steps are iterations W .. W+K-1)
+        rec = run_oracle_sample([(None, max(args.warmup + args.steps, 14))])
+        run = rec["runs"][0]
+        run["iter_s"] = run["iter_s"][:args.warmup + args.steps]
+        per_solve = run["solve_iterations"][0]
+        value, ms = oracle_run_rate(run, per_solve, args.warmup)
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1000.0 * statistics.mean(times) / (SAMPLE_N ** 3 / 1e6),
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-                "cpu_baseline": cpu_baseline_obj({**rec, "solve_s": times}),
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "l2": "n/a (CPU)",
+                           "step": f"one PCG iteration of the FP64 CPU oracle's solve of this workload (a complete "
+                                   f"solve takes {per_solve}); solves/s = 1 / (ms_per_step x {per_solve})"},
+                "cpu_baseline": cpu_baseline_obj(rec, skip=args.warmup),
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -585,6 +789,17 @@ def main():
     batched = None if args.no_batch or not solo else batched_leg(dev, stream)
     warm = None if args.no_warmstart or not solo else warmstart_leg(dev)
     small = None if args.no_configs or not solo else configs_leg(dev, stream, flush_l2)
+    prec = None
+    if solo and not args.no_precision:
+        try:
+            u_c1 = oracle_c1_solution()
+        except Exception as exc:  # reported; the 40^3 leg then measures against the GPU's 1e-10 solution
+            u_c1, prec_note = None, f"oracle 40^3 solution failed: {exc}"[:300]
+        else:
+            prec_note = None
+        prec = precision_leg(dev, stream, flush_l2, u_c1)
+        if prec_note:
+            prec["note"] = prec_note
 
     if rank != 0:
         return
@@ -613,9 +828,11 @@ def main():
         line["warmstart"] = warm
     if small is not None:
         line["configs"] = small
+    if prec is not None:
+        line["precision"] = prec
     if world == 1 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = cpu_baseline_obj(run_oracle_sample(3))
+            line["cpu_baseline"] = cpu_baseline_obj(run_oracle_sample(CPU_BASELINE_PLAN))
         except Exception as exc:  # reported, not fatal
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {exc}"[:300]}

@@ -51,6 +51,12 @@ extern "C" {
 #define GMG_ERR_SMOOTHER (-4)    /* damped Jacobi with omega * lambda_max >= 2 */
 #define GMG_ERR_NOMEM (-5)       /* device allocation failed */
 #define GMG_ERR_NO_DEVICE (-6)   /* no CUDA device usable by this build (sm_103a) */
+#define GMG_TIMEOUT (-7)         /* a bounded device-side wait gave up (the grid barrier of the
+                                    fused lower V-cycle after gmg_options.spin_limit polls, or an
+                                    mbarrier wait of a TMA-staged / tensor-core kernel); the
+                                    failure is recorded, never accepted (Sec. "Outer Krylov Solver
+                                    and Convergence Statement"), u is not a solution, and the
+                                    handle's wait state is reset so the next call can run */
 
 /* ---- boundary conditions ----------------------------------------------- */
 #define GMG_BC_CLAMP_XMIN 0      /* every DOF of the face i = 0 fixed */
@@ -138,6 +144,9 @@ typedef struct {
                                     Results do not depend on the choice (each node's arithmetic is
                                     the same); gmg_autotune overrides it per level. */
     void* stream;                /* cudaStream_t for all device work; NULL = default stream */
+    long long spin_limit;        /* polls (each followed by a ~64 ns sleep) that a block of the fused
+                                    lower V-cycle makes at a grid barrier before it gives up and the
+                                    call returns GMG_TIMEOUT; default 2^24 (about a second); >= 0 */
 } gmg_options;
 
 typedef struct {
@@ -147,11 +156,14 @@ typedef struct {
     double rel_residual;         /* FP64 true ||f - K u|| / ||f|| over free DOFs at return */
     double rel_residual_recursive; /* last recursive (FP32-updated) residual ratio */
     double solve_ms;             /* wall time of the call on the host clock */
+    double setup_ms;             /* wall time of the gmg_setup call that built this handle's
+                                    hierarchy (host clock, synchronous; a clone reports its source's) */
 } gmg_info;
 
 /* Fills *opt with the paper's defaults: 4 levels, Chebyshev degree 2 on the
  * fine level, 2 Jacobi steps with omega 0.5 on the coarse levels, alpha = 1/30,
- * lambda_safety 1.1, 20/10 power iterations, Cholesky cutoff 5000, NULL stream. */
+ * lambda_safety 1.1, 20/10 power iterations, Cholesky cutoff 5000, NULL stream,
+ * spin_limit 2^24. */
 void gmg_default_options(gmg_options* opt);
 
 /* Builds the hierarchy for one frozen density field (Eq. simp_filter, Eq.
@@ -184,6 +196,13 @@ int gmg_apply(gmg_handle* h, const float* u_dev, float* y_dev);
 
 /* Frees every device resource of the handle.  NULL is accepted. */
 void gmg_destroy(gmg_handle* h);
+
+/* Replaces the handle's spin_limit (see gmg_options): later calls use the new
+ * bound.  Drops the handle's captured solve graphs (they hold the old value).
+ * polls >= 0, else GMG_ERR_ARG.  A test sets it to 0 to make the fused lower
+ * V-cycle's barrier give up and checks that the solve reports GMG_TIMEOUT and
+ * that the next solve with the default bound succeeds. */
+int gmg_set_spin_limit(gmg_handle* h, long long polls);
 
 /* Static text for a status code. */
 const char* gmg_status_str(int status);
@@ -329,9 +348,14 @@ int gmg_residual64(gmg_handle* h, const double* f_dev, const double* u_dev, doub
  *   nu      : Poisson ratio of the unit element stiffness;
  *   f_dev, u_dev : device double[3*n_nodes]; r_dev : device double[3*n_nodes] or NULL;
  *   rel_out : HOST double; stream : cudaStream_t or NULL (the call synchronises it).
- * Its scratch (the element stiffness and the per-block partial sums, 526 KB) is
- * a static device array that every GPU loading this library holds until the
- * process exits.  The first call on a device looks up that array's device
+ *             When f has no nonzero free entry, *rel_out is 0 if r_free is zero
+ *             too and +inf otherwise.
+ * Grids whose 3 x node count reaches 2^31 are rejected like oversized ones.
+ * A failed copy or synchronisation (where faults of the kernels surface)
+ * returns GMG_ERR_CUDA with the CUDA error text in gmg_last_error().
+ * Its scratch (the element stiffness, two sums and the per-block partial sums:
+ * (576 + 2 + 65,536) doubles = 528,912 bytes, 516.5 KiB) is a static device
+ * array that every GPU loading this library holds until the process exits.  The first call on a device looks up that array's device
  * address (cudaGetSymbolAddress) with the device current; make that first call
  * before any stream capture.  All calls share the array: calls whose kernels
  * overlap on the GPU (for example on two streams) race and must be serialised

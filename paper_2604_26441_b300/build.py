@@ -38,22 +38,44 @@ def needs_build() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build_library(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and not needs_build():
-        return LIB
-    cmd = [nvcc_path(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-cudart", "shared", "-I", os.path.join(ROOT, "include"), "-o", LIB + ".tmp", *sources()]
-    if extra:
-        cmd[1:1] = extra
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    res = subprocess.run(cmd, capture_output=True, text=True)
+def _run(cmd: list[str]) -> subprocess.CompletedProcess:
+    return subprocess.run(cmd, capture_output=True, text=True)
+
+
+def build_library(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+                  out: str | None = None) -> str:
+    """Compiles every csrc/*.cu to an object in parallel (one nvcc per file; no
+    relocatable device code crosses files), then links the shared library.
+    `extra` flags go to every compile (e.g. -DGMG_CHECKED); `out` names another
+    library file (default: libgmg_b300.so, rebuilt only when a source is newer)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    lib = out or LIB
+    if not force and out is None and not needs_build():
+        return lib
+    objdir = os.path.join(HERE, "_build", os.path.splitext(os.path.basename(lib))[0])
+    os.makedirs(objdir, exist_ok=True)
+    base = [nvcc_path(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I",
+            os.path.join(ROOT, "include"), *(extra or [])]
+    jobs = []
+    for src in sources():
+        obj = os.path.join(objdir, os.path.splitext(os.path.basename(src))[0] + ".o")
+        jobs.append((src, obj, base + ["-c", src, "-o", obj]))
+    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(lambda j: _run(j[2]), jobs))
+    for (src, _, cmd), res in zip(jobs, results):
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        if res.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n" + res.stdout + res.stderr)
+        if verbose and res.stderr:
+            print(res.stderr, file=sys.stderr)
+    link = [nvcc_path(), *ARCH, "-shared", "-cudart", "shared", "-o", lib + ".tmp", *[j[1] for j in jobs]]
+    res = _run(link)
     if res.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
-    if verbose and res.stderr:
-        print(res.stderr, file=sys.stderr)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+        raise RuntimeError("nvcc link failed:\n" + res.stdout + res.stderr)
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -534,7 +534,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
             cf.bar_count = words;
             cf.bar_gen = words + 1;
             cf.err = reinterpret_cast<int*>(words + 2);
-            cf.spin_limit = 1LL << 24;
+            cf.spin_limit = o.spin_limit;
             if (coarse_fused_blocks(&h->fused_blocks, sizeof(double) * (size_t)std::max(h->nL, 1)) == GMG_OK &&
                 h->fused_blocks > 0)
                 h->use_fused = true;
@@ -830,14 +830,24 @@ int fgmres_solve(gmg_handle* h, const double* f, double* u, double tol, int maxi
     }
 }
 
-// Reports a timed-out wait of the TMA-staged operator or of the fused lower
-// V-cycle (both error words are sticky).
+// Reports a timed-out wait of a TMA-staged / tensor-core kernel or of the fused
+// lower V-cycle.  Both error words are sticky on the device; once reported they
+// are cleared, together with the grid barrier's arrival counter (blocks that
+// gave up may have left it non-zero), so the handle's next call starts clean.
 int check_fused(gmg_handle* h) {
     TRY(sync_scalars(h));
     const int err[2] = {h->err_host[0], h->err_host[1]};
-    if (err[0]) return fail(GMG_ERR_CUDA, "an assembled-level operator gave up waiting for its TMA tiles");
-    if (err[1]) return fail(GMG_ERR_CUDA, "the fused coarse-level V-cycle gave up waiting at a grid barrier");
-    return GMG_OK;
+    if (!err[0] && !err[1]) return GMG_OK;
+    CU(cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream));
+    if (h->use_fused) {
+        CU(cudaMemsetAsync(h->cf.bar_count, 0, sizeof(unsigned), h->stream));
+        CU(cudaMemsetAsync(h->cf.err, 0, sizeof(int), h->stream));
+    }
+    CU(cudaStreamSynchronize(h->stream));
+    h->err_host[0] = h->err_host[1] = 0;
+    if (err[0]) return fail(GMG_TIMEOUT, "a TMA-staged or tensor-core kernel gave up waiting for its shared-memory tiles");
+    return fail(GMG_TIMEOUT, "the fused coarse-level V-cycle gave up waiting at a grid barrier after " +
+                                 std::to_string(h->cf.spin_limit) + " polls");
 }
 
 }  // namespace
@@ -870,6 +880,7 @@ void gmg_default_options(gmg_options* o) {
     o->restart = 32;
     o->bsr_kernel = -1;
     o->stream = nullptr;
+    o->spin_limit = 1LL << 24;
 }
 
 const char* gmg_status_str(int st) {
@@ -883,6 +894,7 @@ const char* gmg_status_str(int st) {
         case GMG_ERR_SMOOTHER: return "unstable Jacobi damping";
         case GMG_ERR_NOMEM: return "device out of memory";
         case GMG_ERR_NO_DEVICE: return "no usable CUDA device";
+        case GMG_TIMEOUT: return "a bounded device-side wait gave up";
         default: return "unknown status";
     }
 }
@@ -935,6 +947,7 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
     if (o.restart < 1 || o.restart > kMaxRestart) return fail(GMG_ERR_ARG, "restart must be in [1, 256]");
     if (o.power_iters_fine < 1 || o.power_iters_coarse < 1 || o.chol_cutoff < 1)
         return fail(GMG_ERR_ARG, "bad iteration counts or cutoff");
+    if (o.spin_limit < 0) return fail(GMG_ERR_ARG, "spin_limit must be >= 0");
 
     int dev = 0;
     cudaDeviceProp prop;
@@ -949,7 +962,9 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
     h->opt = o;
     h->device = dev;
     h->stream = static_cast<cudaStream_t>(o.stream);
+    const auto t0 = std::chrono::steady_clock::now();
     const int rc = build(h, g, rho_dev, p, E0, Emin, nu, bc);
+    h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc != GMG_OK) {
         std::string keep = g_err;
         gmg_destroy(h);
@@ -981,6 +996,7 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
         if (fe != GMG_OK) return fe;
         inf.status = st;
         inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        inf.setup_ms = h->setup_ms;
         if (info) *info = inf;
         return st;
     };
@@ -1567,11 +1583,28 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
     for (int i = 0; i < count; ++i) {
         if (int fe = check_fused(hs[i]); fe != GMG_OK) { restore(); return fe; }
         infos[i].solve_ms = elapsed();
+        infos[i].setup_ms = hs[i]->setup_ms;
         if (infos[i].status != GMG_OK) worst = infos[i].status;
     }
     restore();
     CU(cudaGetLastError());
     return worst;
+}
+
+int gmg_set_spin_limit(gmg_handle* h, long long polls) {
+    if (!h) return fail(GMG_ERR_ARG, "null handle");
+    if (polls < 0) return fail(GMG_ERR_ARG, "spin_limit must be >= 0");
+    CU(cudaStreamSynchronize(h->stream));
+    h->opt.spin_limit = polls;
+    h->cf.spin_limit = polls;
+    // captured graphs hold the former bound in their kernel arguments
+    loop_free(h);
+    if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
+    if (h->batch_graph) cudaGraphDestroy(h->batch_graph);
+    h->batch_exec = nullptr;
+    h->batch_graph = nullptr;
+    h->batch_key.clear();
+    return GMG_OK;
 }
 
 int gmg_num_levels(const gmg_handle* h) { return h ? h->L : 0; }

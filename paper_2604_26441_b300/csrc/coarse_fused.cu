@@ -17,7 +17,8 @@
 // The barrier is this file's own: an arrival counter and a generation word in
 // global memory.  Waiting is bounded: after `spin_limit` polls a block records
 // an error flag and leaves, so a fault can never turn into a hang (the host
-// reports GMG_ERR_CUDA when the flag is set).  The kernel is launched with
+// reports GMG_TIMEOUT when the flag is set, then clears the flag and the
+// arrival counter).  The kernel is launched with
 // cudaLaunchCooperativeKernel, which guarantees that all blocks are resident.
 #include <algorithm>
 

@@ -231,6 +231,7 @@ struct gmg_handle {
     gmg::GHat gh{};
     gmg::GHat64 gh64{};
     float kd = 0.f;                             // diagonal entry of K_e (all equal)
+    double setup_ms = 0.0;                      // host wall time of gmg_setup (clones: the source's)
     float* inv0 = nullptr;                      // [n_nodes] fine Jacobi scale 1 / (kd * sum of adjacent E_e)
     double* lam = nullptr;                      // [kMaxLevels] lambda estimates (device)
     // fine-level PCG vectors

@@ -14,6 +14,7 @@
 // exits.  All calls share it: two calls whose kernels overlap on the GPU (for
 // example on two streams) race on it.  Each call rewrites every word it reads,
 // so nothing has to be cleared between calls.
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -194,8 +195,18 @@ extern "C" int gmg_residual64_noalloc(const gmg_grid* g, const double* E_dev, co
         set_error_text("gmg_residual64_noalloc: element counts must be >= 1 and nu in (-1, 0.5)");
         return GMG_ERR_ARG;
     }
-    const long long gx = (g->nx + 1 + TX - 1) / TX, gy = (g->ny + 1 + TY - 1) / TY, gz = (g->nz + 1 + TZ - 1) / TZ;
-    if (gx * gy * gz > kNoallocMaxBlocks || gy > 65535 || gz > 65535) {
+    // Sizes in 64-bit before anything is launched: the node count must keep
+    // every DOF index below 2^31 (the limit gmg_setup applies too), and the
+    // block grid must fit the static array of partial sums.
+    const long long NX = (long long)g->nx + 1, NY = (long long)g->ny + 1, NZ = (long long)g->nz + 1;
+    const long long nn = NX * NY * NZ;
+    if (nn > (1LL << 31) / 3) {
+        set_error_text("gmg_residual64_noalloc: grid too large (" + std::to_string(nn) +
+                       " nodes; 3 x nodes must stay below 2^31)");
+        return GMG_ERR_ARG;
+    }
+    const long long gx = (NX + TX - 1) / TX, gy = (NY + TY - 1) / TY, gz = (NZ + TZ - 1) / TZ;
+    if (gx < 1 || gy < 1 || gz < 1 || gx * gy * gz > kNoallocMaxBlocks || gy > 65535 || gz > 65535) {
         set_error_text("gmg_residual64_noalloc: the grid needs " + std::to_string(gx * gy * gz) +
                        " partial sums; the static scratch holds at most " + std::to_string(kNoallocMaxBlocks) +
                        " (nodes per block 32x4x2)");
@@ -212,7 +223,6 @@ extern "C" int gmg_residual64_noalloc(const gmg_grid* g, const double* E_dev, co
     double* Ke = scratch;
     double* res = scratch + 576;
     double* partial = scratch + 578;
-    const long long nn = (long long)(g->nx + 1) * (g->ny + 1) * (g->nz + 1);
     note_launch(5);
     k_na_ke<<<1, 576, 0, s>>>(nu, Ke);
     k_na_resid64<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(TX, TY, TZ), 0, s>>>(
@@ -226,8 +236,20 @@ extern "C" int gmg_residual64_noalloc(const gmg_grid* g, const double* E_dev, co
         return GMG_ERR_CUDA;
     }
     double host[2] = {0.0, 0.0};
-    if (cudaMemcpyAsync(host, res, sizeof host, cudaMemcpyDeviceToHost, s) != cudaSuccess) return GMG_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return GMG_ERR_CUDA;
+    cudaError_t ce = cudaMemcpyAsync(host, res, sizeof host, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+        // Faults of the kernels above, and a call made inside a stream capture,
+        // surface here.
+        set_error_text(std::string("gmg_residual64_noalloc: ") + cudaGetErrorString(ce));
+        return GMG_ERR_CUDA;
+    }
+    // A load with no nonzero free entry has no relative scale: the result is 0
+    // when the residual is zero too (u = 0 solves K u = 0) and +inf otherwise.
+    if (host[1] == 0.0) {
+        *rel_out = host[0] == 0.0 ? 0.0 : HUGE_VAL;
+        return GMG_OK;
+    }
     *rel_out = sqrt(host[0]) / sqrt(host[1]);
     return GMG_OK;
 }

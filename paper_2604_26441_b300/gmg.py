@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgmg_b300.so")
 
 GMG_OK, GMG_NOT_CONVERGED, GMG_NONFINITE = 0, 1, 2
+GMG_TIMEOUT = -7
 BC_CLAMP_XMIN, BC_MASK = 0, 1
 JACOBI, CHEBYSHEV = 0, 1
 _KINDS = {"jacobi": JACOBI, "chebyshev": CHEBYSHEV}
@@ -51,13 +52,13 @@ class _Options(ctypes.Structure):
                 ("ir_factor", ctypes.c_double),
                 ("fine_smoother", ctypes.c_int),
                 ("cycle_index", ctypes.c_int), ("outer", ctypes.c_int), ("restart", ctypes.c_int),
-                ("bsr_kernel", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("bsr_kernel", ctypes.c_int), ("stream", ctypes.c_void_p), ("spin_limit", ctypes.c_longlong)]
 
 
 class _Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("replacements", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("rel_residual_recursive", ctypes.c_double),
-                ("solve_ms", ctypes.c_double)]
+                ("solve_ms", ctypes.c_double), ("setup_ms", ctypes.c_double)]
 
 
 class _Tuning(ctypes.Structure):
@@ -81,6 +82,7 @@ _SIGS = {
     "gmg_apply": (ctypes.c_int, [_P, _P, _P]),
     "gmg_destroy": (None, [_P]),
     "gmg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "gmg_set_spin_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
     "gmg_last_error": (ctypes.c_char_p, []),
     "gmg_kernel_launches": (ctypes.c_ulonglong, []),
     "gmg_num_levels": (ctypes.c_int, [_P]),
@@ -176,7 +178,7 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
             power_iters_coarse: int = 10, chol_cutoff: int = 5000, fused_coarse_nodes: int = 0,
             bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
             fine_smoother: str = "fp32", cycle: str = "V", outer: str = "pcg", restart: int = 32,
-            bsr_kernel: int = -1, stream: int | None = None) -> _Options:
+            bsr_kernel: int = -1, stream: int | None = None, spin_limit: int = 1 << 24) -> _Options:
     o = _Options()
     load_library().gmg_default_options(ctypes.byref(o))
     o.levels = levels
@@ -201,6 +203,7 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
     o.restart = restart
     o.bsr_kernel = bsr_kernel
     o.stream = stream
+    o.spin_limit = spin_limit
     return o
 
 
@@ -331,7 +334,12 @@ class Solver:
         _check(rc, allow=(GMG_OK, GMG_NOT_CONVERGED, GMG_NONFINITE))
         return u, {"status": info.status, "iterations": info.iterations, "replacements": info.replacements,
                    "rel_residual": info.rel_residual, "rel_residual_recursive": info.rel_residual_recursive,
-                   "solve_ms": info.solve_ms}
+                   "solve_ms": info.solve_ms, "setup_ms": info.setup_ms}
+
+    def set_spin_limit(self, polls: int) -> None:
+        """Polls a block of the fused lower V-cycle makes at a grid barrier
+        before it gives up (gmg_set_spin_limit); drops captured solve graphs."""
+        _check(self._lib.gmg_set_spin_limit(self._h, int(polls)))
 
     def autotune(self, reps: int = 5) -> dict:
         """Times the fine kernel's launch shapes and each assembled level's
@@ -460,7 +468,7 @@ def solve_batch(solvers, fs, us=None, tol: float = 1e-6, maxit: int = 200):
     _check(rc, allow=(GMG_OK, GMG_NOT_CONVERGED, GMG_NONFINITE))
     return us, [{"status": i.status, "iterations": i.iterations, "replacements": i.replacements,
                  "rel_residual": i.rel_residual, "rel_residual_recursive": i.rel_residual_recursive,
-                 "solve_ms": i.solve_ms} for i in infos]
+                 "solve_ms": i.solve_ms, "setup_ms": i.setup_ms} for i in infos]
 
 
 # ---------------------------------------------------------------- learned warm start

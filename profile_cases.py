@@ -1,14 +1,14 @@
 """Fixed workloads for profiling the CUDA path under ncu.
 
-    python -m paper_2604_26441_b300.profile_cases solve-c2    # set-up + 2 solves, 100^3
-    python -m paper_2604_26441_b300.profile_cases solve-c2-hostloop  # the same, PCG driven from the host
-    python -m paper_2604_26441_b300.profile_cases smooth-c2   # set-up + 3 fine smoothing passes
-    python -m paper_2604_26441_b300.profile_cases apply-c2    # set-up + 5 fine operator applies
-    python -m paper_2604_26441_b300.profile_cases smooth-l1-c2  # set-up + 3 level-1 smoothing passes (BSR)
-    python -m paper_2604_26441_b300.profile_cases smooth-c2-bf16x3  # fine smoothing, tensor-core contraction
-    python -m paper_2604_26441_b300.profile_cases warmstart-80  # 80^3 set-up, one learned warm start + solve
-    python -m paper_2604_26441_b300.profile_cases warmstart-80-tf32  # the same with tensor-core convolutions
-    python -m paper_2604_26441_b300.profile_cases train-48      # 48^3 set-up, 3 energy-loss train steps (batch 4)
+    python profile_cases.py solve-c2    # set-up + 2 solves, 100^3
+    python profile_cases.py solve-c2-hostloop  # the same, PCG driven from the host
+    python profile_cases.py smooth-c2   # set-up + 3 fine smoothing passes
+    python profile_cases.py apply-c2    # set-up + 5 fine operator applies
+    python profile_cases.py smooth-l1-c2  # set-up + 3 level-1 smoothing passes (BSR)
+    python profile_cases.py smooth-c2-bf16x3  # fine smoothing, tensor-core contraction
+    python profile_cases.py warmstart-80  # 80^3 set-up, one learned warm start + solve
+    python profile_cases.py warmstart-80-tf32  # the same with tensor-core convolutions
+    python profile_cases.py train-48      # 48^3 set-up, 3 energy-loss train steps (batch 4)
 
 Each case prints the library's kernel-launch counter after set-up, so that
 ``ncu -s`` can skip the set-up kernels.  The solve normally runs its PCG
@@ -16,7 +16,7 @@ iterations as one CUDA graph with a conditional while node, whose kernels a
 per-launch ncu list does not show; the host-loop case launches the same kernels
 in the same order one by one.
 
-    python -m paper_2604_26441_b300.profile_cases summarize LAUNCHES.csv [FIRST_ID]
+    python profile_cases.py summarize LAUNCHES.csv [FIRST_ID]
 
 reads the CSV that ``ncu --metrics gpu__time_duration.sum --csv --log-file``
 writes and prints, per kernel, its launches, total time and share of the time of

@@ -376,6 +376,33 @@ def test_edge_cases():
         gpu_solver(c.rho(), c.p, levels=6, smoother="jacobi", coarse_smoother=None, omega=0.5)
 
 
+def test_grid_barrier_timeout_is_reported_and_recovered():
+    """The fused lower V-cycle's grid barrier is a bounded poll of a generation
+    word.  With a bound of 0 polls every block that is not the last to arrive
+    gives up at once (the wait runs out; nothing faults or hangs), so the solve
+    must report GMG_TIMEOUT, not a solution.  After the default bound is
+    restored, the same handle solves normally and matches the per-level path."""
+    from paper_2604_26441_b300 import gmg
+    c = inputs.CONFIGS["c0"]
+    S = gpu_solver(c.rho(), c.p, **config_opts(c), fused_coarse_nodes=65536, spin_limit=0)
+    f = _t(c.load(), torch.float64)
+    with pytest.raises(gmg.GMGError) as ei:
+        S.solve(f)
+    assert ei.value.code == gmg.GMG_TIMEOUT
+    assert b"grid barrier" in gmg.load_library().gmg_last_error()
+    with pytest.raises(gmg.GMGError) as ei:  # still bounded at 0: reported again, not accepted
+        S.solve(f)
+    assert ei.value.code == gmg.GMG_TIMEOUT
+    S.set_spin_limit(1 << 24)
+    u, info = S.solve(f)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-6
+    S_ref = gpu_solver(c.rho(), c.p, **config_opts(c), fused_coarse_nodes=0)
+    u_ref, info_ref = S_ref.solve(f)
+    assert abs(info["iterations"] - info_ref["iterations"]) <= 1
+    assert rel_l2(u.cpu().numpy(), u_ref.cpu().numpy()) < 1e-5
+    assert info["setup_ms"] > 0.0
+
+
 def test_smallest_grid():
     rho = inputs.uniform_density(2, 2, 2)
     opts = dict(levels=2, smoother="jacobi", degree=2, coarse_smoother=None, coarse_degree=None, omega=0.5,

@@ -74,3 +74,37 @@ def test_noalloc_rejects_oversized_grid():
     assert rc == -1
     assert b"65536" in lib.gmg_last_error()
     assert rel.value == -1.0
+
+
+def test_noalloc_rejects_node_count_beyond_int32_dofs():
+    """Sizes are checked in 64-bit before any launch: an element count at the
+    32-bit limit (whose node count nx + 1 overflows int) and a grid whose
+    3 x node count passes 2^31 (the limit of gmg_setup) are both refused."""
+    from paper_2604_26441_b300 import gmg
+    lib = gmg.load_library()
+    dummy = torch.zeros(8, dtype=torch.float64, device="cuda")
+    p = ctypes.c_void_p(dummy.data_ptr())
+    for dims in [(2147483647, 1, 1), (1000, 1000, 1000)]:
+        g = gmg._Grid(*dims)
+        rel = ctypes.c_double(-1.0)
+        rc = lib.gmg_residual64_noalloc(ctypes.byref(g), p, p, 0.3, p, p, None, ctypes.byref(rel), None)
+        assert rc == -1, dims
+        assert rel.value == -1.0
+
+
+def test_noalloc_zero_load_has_a_defined_result():
+    """f = 0 on every free DOF: the relative residual is 0 for u = 0 and +inf
+    for a nonzero u (no NaN)."""
+    from paper_2604_26441_b300 import gmg
+    nx, ny, nz = 16, 8, 8
+    E = _moduli(inputs.uniform_density(nx, ny, nz), 3.0)
+    mask = _clamp_mask(nx, ny, nz)
+    n = 3 * (nx + 1) * (ny + 1) * (nz + 1)
+    f = torch.zeros(n, dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(f)
+    r = torch.full_like(f, float("nan"))
+    assert gmg.residual64_noalloc((nx, ny, nz), E, mask, f, u, r) == 0.0
+    assert float(r.abs().max()) == 0.0
+    fixed = torch.from_numpy(inputs.clamp_xmin_mask(nx, ny, nz)).cuda()
+    u = torch.where(fixed == 0, 1e-3, 0.0).double()
+    assert gmg.residual64_noalloc((nx, ny, nz), E, mask, f, u, r) == float("inf")
