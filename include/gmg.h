@@ -218,7 +218,10 @@ unsigned long long gmg_kernel_launches(void);
  * These expose the individual steps of the hot path so that each can be checked
  * on its own.  Vectors are device float[3*n_nodes(level)] unless stated; all
  * are asynchronous on the handle's stream except the host-output getters, which
- * synchronise that stream before returning. */
+ * synchronise that stream before returning.  Internally the fine level's
+ * vectors pad every node row to a multiple of 4 nodes (16-byte aligned rows for
+ * the TMA-fed operator); the level-0 calls copy the caller's dense vectors in
+ * and out of that layout, using the handle's own work vectors. */
 
 int gmg_num_levels(const gmg_handle* h);
 
@@ -250,6 +253,15 @@ int gmg_level_apply(gmg_handle* h, int level, const float* x_dev, float* y_dev);
  * damped Jacobi) on K^level x = b; x_is_zero != 0 means x enters as 0 (and is
  * not read). */
 int gmg_level_smooth(gmg_handle* h, int level, const float* b_dev, float* x_dev, int x_is_zero);
+
+/* The fine-level operator on the handle's own level-0 vectors, whatever values
+ * they hold, for timing the fused fine-level kernel in isolation (without the
+ * repacking of caller vectors that the level-0 calls above perform):
+ * what = 0: one application y = K x (Eq. mf_matvec); what = 1: one smoothing
+ * pass, degree fused operator + smoother steps from a nonzero iterate
+ * (Algorithm cheb / damped Jacobi; GMG_ERR_ARG on a single-level hierarchy).
+ * Asynchronous on the handle's stream. */
+int gmg_fine_pass(gmg_handle* h, int what);
 
 /* coarse = R^level fine (R = P^T, Eq. vector_prolongation; coarse fixed DOFs 0):
  * fine on `level`, coarse on level+1. */

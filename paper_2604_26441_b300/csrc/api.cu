@@ -73,7 +73,8 @@ FineArgs fine_args(gmg_handle* h) {
     const Level& l = h->lev[0];
     FineArgs a{};
     a.nx = l.nx; a.ny = l.ny; a.nz = l.nz;
-    a.E = h->E32; a.mask = l.mask; a.kd = h->kd; a.inv0 = h->inv0; a.coef = l.coef;
+    a.pitch = l.px; a.epitch = h->ex; a.Ep = h->E32p;
+    a.E = h->E32; a.mask = l.maskp; a.kd = h->kd; a.inv0 = h->inv0; a.coef = l.coef;
     a.tcB = h->tcB; a.err = h->kerr;
     return a;
 }
@@ -97,16 +98,15 @@ int partial_count(gmg_handle* h, int li, int kind) {
 }
 
 // y = K^l x (masked); with dot: partial += x . y and finalised into `slot`.
-// mask_in: x may hold values on fixed DOFs (caller input) that must be ignored.
-void level_apply(gmg_handle* h, int li, const float* x, float* y, int dot_slot = -1, int op = FIN_NONE,
-                 bool mask_in = false) {
+// Level-0 operands are level-0 vectors (padded rows, 0 on fixed DOFs); entry
+// points that take a caller's dense vector pack it first (launch_pack0).
+void level_apply(gmg_handle* h, int li, const float* x, float* y, int dot_slot = -1, int op = FIN_NONE) {
     cudaStream_t s = h->stream;
     const bool dot = dot_slot >= 0;
     if (li == 0) {
         FineArgs a = fine_args(h);
         a.xin = x; a.out = y; a.partial = dot ? h->partials : nullptr;
-        a.scratch = h->t0;
-        launch_fine(FM_APPLY, dot, mask_in && !dot, a, h->gh, s);
+        launch_fine(FM_APPLY, dot, 0, a, h->gh, s);
     } else {
         BsrArgs a = bsr_args(h, li);
         a.xin = x; a.out = y; a.partial = dot ? h->partials : nullptr;
@@ -189,7 +189,7 @@ void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int
         return;
     }
     if (li == h->L - 1) {
-        launch_coarse_solve(h->nL, h->free_idx, h->Ainv, b, X, l.mask, l.nn, s);
+        launch_coarse_solve(h->nL, h->free_idx_p, h->Ainv, b, X, l.maskp, l.nnp, s);
         return;
     }
     int writes = 0;
@@ -212,18 +212,18 @@ void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int
 void power_iteration(gmg_handle* h, int li, int iters) {
     Level& l = h->lev[li];
     cudaStream_t s = h->stream;
-    const long long n = 3 * l.nn;
+    const long long n = 3 * l.nnp;
     float* v = li == 0 ? h->t0 : l.t;
     float* w = li == 0 ? h->x2_0 : l.x2;
     float* y = li == 0 ? h->d0 : l.d;
     cudaMemsetAsync(h->sc + SC_TMP, 0, sizeof(double), s);
-    launch_power_start(v, l.mask, l.nn, s);
+    launch_power_start(v, l, s);
     launch_dot_f32(v, v, n, h->partials, s);
     launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_NRM, FIN_NRMCHK, s);
     launch_scale_by_inv_sqrt(v, n, h->sc, SC_NRM, s);
     for (int it = 0; it < iters; ++it) {
         level_apply(h, li, v, y);
-        if (li == 0) launch_scale_invdiag_fine(y, w, h->E32, l.mask, l.nx, l.ny, l.nz, h->kd, s);
+        if (li == 0) launch_scale_invdiag_fine(y, w, h->E32, l, h->kd, s);
         else launch_scale_invdiag_bsr(y, w, l.invdiag, n, s);
         launch_dot_f32(w, w, n, h->partials, s);
         launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_NRM, FIN_NRMCHK, s);
@@ -233,7 +233,7 @@ void power_iteration(gmg_handle* h, int li, int iters) {
     level_apply(h, li, v, y);
     launch_dot_f32(v, y, n, h->partials, s);
     launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_VKV, FIN_NONE, s);
-    if (li == 0) launch_diag_dot_fine(v, h->E32, l.mask, l.nx, l.ny, l.nz, h->kd, h->partials, s);
+    if (li == 0) launch_diag_dot_fine(v, h->E32, l, h->kd, h->partials, s);
     else launch_diag_dot_bsr(v, l.invdiag, n, h->partials, s);
     launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_VDV, FIN_NONE, s);
     launch_lambda_finish(h->sc, h->lam + li, s);
@@ -292,6 +292,8 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     Level& l0 = h->lev[0];
     l0.nx = g->nx; l0.ny = g->ny; l0.nz = g->nz;
     l0.nn = nodes_of(g->nx, g->ny, g->nz);
+    l0.px = (g->nx + 1 + 3) / 4 * 4;
+    l0.nnp = (long long)l0.px * (g->ny + 1) * (g->nz + 1);
     TRY(dalloc(h, &l0.mask, l0.nn));
     if (bc->kind == GMG_BC_CLAMP_XMIN) {
         launch_mask_clamp(l0.mask, l0.nx, l0.ny, l0.nz, s);
@@ -312,6 +314,8 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         return GMG_OK;
     };
     TRY(count_free(l0, &l0.n_free));
+    TRY(dalloc(h, &l0.maskp, l0.nnp));
+    launch_mask_pad(l0, s);
     int L = 1;
     const int want = o.levels;
     while (true) {
@@ -326,7 +330,10 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         Level& c = h->lev[L];
         c.nx = f.nx / 2; c.ny = f.ny / 2; c.nz = f.nz / 2;
         c.nn = nodes_of(c.nx, c.ny, c.nz);
+        c.px = c.nx + 1;
+        c.nnp = c.nn;
         TRY(dalloc(h, &c.mask, c.nn));
+        c.maskp = c.mask;
         launch_mask_inject(f, c, s);
         TRY(count_free(c, &c.n_free));
         ++L;
@@ -355,16 +362,16 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
             TRY(dalloc(h, &l.d, 3 * l.nn));
         }
     }
-    const long long n0 = 3 * l0.nn;
-    TRY(dalloc(h, &h->r, n0));
-    TRY(dalloc(h, &h->z, n0));
-    TRY(dalloc(h, &h->p, n0));
-    TRY(dalloc(h, &h->q, n0));
-    TRY(dalloc(h, &h->x2_0, n0));
-    TRY(dalloc(h, &h->t0, n0));
-    TRY(dalloc(h, &h->d0, n0));
+    const long long n0 = 3 * l0.nnp;
+    for (float** v : {&h->r, &h->z, &h->p, &h->q, &h->x2_0, &h->t0, &h->d0}) {
+        TRY(dalloc(h, v, n0));
+        CU(cudaMemsetAsync(*v, 0, sizeof(float) * n0, s));  // the pads stay 0
+    }
     const long long ne = (long long)l0.nx * l0.ny * l0.nz;
     TRY(dalloc(h, &h->E32, ne));
+    h->ex = (l0.nx + 3) / 4 * 4;
+    TRY(dalloc(h, &h->E32p, (long long)h->ex * l0.ny * l0.nz));
+    CU(cudaMemsetAsync(h->E32p, 0, sizeof(float) * h->ex * l0.ny * l0.nz, s));
     TRY(dalloc(h, &h->E64, ne));
     TRY(dalloc(h, &h->lam, kMaxLevels));
     TRY(dalloc(h, &h->sc, SC_COUNT));
@@ -386,6 +393,8 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
 
     // ---- moduli (Eq. simp_filter) and K_e
     launch_moduli(rho, ne, p, E0, Emin, h->E64, h->E32, s);
+    CU(cudaMemcpy2DAsync(h->E32p, sizeof(float) * h->ex, h->E32, sizeof(float) * l0.nx, sizeof(float) * l0.nx,
+                         (size_t)l0.ny * l0.nz, cudaMemcpyDeviceToDevice, s));
     double* Ke = nullptr;
     TRY(dalloc(h, &Ke, 576));
     launch_element_stiffness(nu, Ke, s);
@@ -393,8 +402,9 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     CU(cudaStreamSynchronize(s));
     for (int i = 0; i < 576; ++i) h->keF.v[i] = (float)h->keD.v[i];
     h->kd = h->keF.v[0];
-    TRY(dalloc(h, &h->inv0, l0.nn));
-    launch_fine_inv0(l0.nx, l0.ny, l0.nz, h->E32, h->kd, h->inv0, s);
+    TRY(dalloc(h, &h->inv0, l0.nnp));
+    CU(cudaMemsetAsync(h->inv0, 0, sizeof(float) * l0.nnp, s));
+    launch_fine_inv0(l0.nx, l0.ny, l0.nz, l0.px, h->E32, h->kd, h->inv0, s);
     {
         double* g72 = nullptr;
         double gh[72];
@@ -491,6 +501,10 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
             dfree(h, Kc);
         }
         launch_dense_gather(cl, h->free_idx, n, dense, s);
+        if (L == 1) {  // the coarsest level is level 0: its vectors have padded rows
+            TRY(dalloc(h, &h->free_idx_p, n));
+            launch_pad_index(h->free_idx, n, l0, h->free_idx_p, s);
+        }
         launch_regularise(dense, n, eps_dev, s);
         CU(cudaMemcpyAsync(&h->eps, eps_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
         const int rc = cholesky_and_inverse(dense, n, work, info, h->Ainv, s);
@@ -500,6 +514,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         dfree(h, dense);
         dfree(h, work);
     }
+    if (!h->free_idx_p) h->free_idx_p = h->free_idx;
     // ---- TMA-staged operator for the large assembled levels
     for (int li = 1; li < L; ++li) {
         Level& l = h->lev[li];
@@ -549,7 +564,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
 // by the host-driven loop and the captured graph ---------------------------------
 // z = V(r), rz = r . z, p = z
 void pcg_restart(gmg_handle* h) {
-    const long long n = 3 * h->lev[0].nn;
+    const long long n = 3 * h->lev[0].nnp;
     vcycle_level(h, 0, h->r, h->z, h->x2_0, SC_RZ, FIN_NONE);
     launch_copy_f32(h->p, h->z, n, h->stream);
 }
@@ -557,17 +572,30 @@ void pcg_restart(gmg_handle* h) {
 // (inside the captured loop) the ||r||^2 reduction also takes the loop's
 // convergence test.
 void pcg_step(gmg_handle* h, double* u, const cudaGraphConditionalHandle* cond = nullptr) {
-    const long long n = 3 * h->lev[0].nn;
     level_apply(h, 0, h->p, h->q, SC_PQ, FIN_ALPHA);
-    launch_pcg_update(u, h->r, h->p, h->q, n, h->sc, h->partials, h->stream);
+    launch_pcg_update(u, h->r, h->p, h->q, h->lev[0], h->sc, h->partials, h->stream);
     if (cond) launch_finalize_check(h->partials, vec_grid_blocks(), h->sc, *cond, h->stream);
     else launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_RR, FIN_NONE, h->stream);
 }
 // z = V(r), beta = r.z / rz, p = z + beta p
 void pcg_direction(gmg_handle* h) {
-    const long long n = 3 * h->lev[0].nn;
+    const long long n = 3 * h->lev[0].nnp;
     vcycle_level(h, 0, h->r, h->z, h->x2_0, SC_RZNEW, FIN_BETA);
     launch_p_update(h->p, h->z, n, h->sc, h->stream);
+}
+
+// After a solve that ended non-finite, a non-finite step length may have been
+// spread over the pad entries of the level-0 vectors by the full-length vector
+// kernels; the next call on the handle starts from zeroed vectors.
+int clear_pads(gmg_handle* h) {
+    if (!h->pads_dirty) return GMG_OK;
+    const long long n = 3 * h->lev[0].nnp;
+    for (float* v : {h->r, h->z, h->p, h->q, h->x2_0, h->t0, h->d0})
+        CU(cudaMemsetAsync(v, 0, sizeof(float) * n, h->stream));
+    if (h->fg_V) CU(cudaMemsetAsync(h->fg_V, 0, sizeof(float) * (size_t)(h->fg_m + 1) * n, h->stream));
+    if (h->fg_Z) CU(cudaMemsetAsync(h->fg_Z, 0, sizeof(float) * (size_t)h->fg_m * n, h->stream));
+    h->pads_dirty = false;
+    return GMG_OK;
 }
 
 void loop_free(gmg_handle* h) {
@@ -745,7 +773,7 @@ double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e, i
 int fgmres_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, double nf, gmg_info& inf) {
     cudaStream_t s = h->stream;
     Level& l0 = h->lev[0];
-    const long long n = 3 * l0.nn;
+    const long long n = 3 * l0.nnp;
     const int m = h->opt.restart;
     if (h->fg_m != m) {
         dfree(h, h->fg_V);
@@ -755,6 +783,8 @@ int fgmres_solve(gmg_handle* h, const double* f, double* u, double tol, int maxi
         h->fg_h = nullptr;
         TRY(dalloc(h, &h->fg_V, (size_t)(m + 1) * n));
         TRY(dalloc(h, &h->fg_Z, (size_t)m * n));
+        CU(cudaMemsetAsync(h->fg_V, 0, sizeof(float) * (size_t)(m + 1) * n, s));  // the pads stay 0
+        CU(cudaMemsetAsync(h->fg_Z, 0, sizeof(float) * (size_t)m * n, s));
         TRY(dalloc(h, &h->fg_h, (size_t)m + 2));
         h->fg_m = m;
     }
@@ -763,7 +793,8 @@ int fgmres_solve(gmg_handle* h, const double* f, double* u, double tol, int maxi
     int k = 0;
     while (true) {
         double rel = 0.0;
-        launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, h->sc, h->partials, h->gh64, s);
+        launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, l0.px, h->sc, h->partials,
+                            h->gh64, s);
         launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
         TRY(sync_scalars(h));
         const double beta = std::sqrt(sch[SC_TRR]);
@@ -826,7 +857,7 @@ int fgmres_solve(gmg_handle* h, const double* f, double* u, double tol, int maxi
             for (int q = i + 1; q < j; ++q) acc -= H[(size_t)i * m + q] * y[q];
             y[i] = acc / H[(size_t)i * m + i];
         }
-        for (int i = 0; i < j; ++i) launch_axpy_u64(u, h->fg_Z + (size_t)i * n, n, y[i], s);
+        for (int i = 0; i < j; ++i) launch_axpy_u64(u, h->fg_Z + (size_t)i * n, l0, y[i], s);
     }
 }
 
@@ -975,9 +1006,16 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
     return GMG_OK;
 }
 
+// The per-step entry points take level-0 vectors in the dense numbering of the
+// ABI; they pack them into the handle's own (padded) level-0 vectors and unpack
+// the results.  They run between solves, so those vectors are free.
 int gmg_apply(gmg_handle* h, const float* u, float* y) {
     if (!h || !u || !y) return fail(GMG_ERR_ARG, "null argument");
-    level_apply(h, 0, u, y, -1, FIN_NONE, true);
+    TRY(clear_pads(h));
+    const Level& l0 = h->lev[0];
+    launch_pack0(u, l0, h->p, h->stream);
+    level_apply(h, 0, h->p, h->q);
+    launch_unpack0(h->q, l0, y, h->stream);
     CU(cudaGetLastError());
     return GMG_OK;
 }
@@ -991,9 +1029,11 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     const long long n = 3 * l0.nn;
     double* sch = h->sc_host;
     gmg_info inf{};
+    TRY(clear_pads(h));
     auto finish = [&](int st) -> int {
+        if (st == GMG_NONFINITE) h->pads_dirty = true;
         const int fe = check_fused(h);
-        if (fe != GMG_OK) return fe;
+        if (fe != GMG_OK) { h->pads_dirty = true; return fe; }
         inf.status = st;
         inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         inf.setup_ms = h->setup_ms;
@@ -1001,7 +1041,8 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
         return st;
     };
     auto true_residual = [&](double& rel) -> int {
-        launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, h->sc, h->partials, h->gh64, s);
+        launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, l0.px, h->sc, h->partials,
+                            h->gh64, s);
         launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
         TRY(sync_scalars(h));
         rel = std::sqrt(sch[SC_TRR]) / std::sqrt(sch[SC_FF]);
@@ -1023,7 +1064,7 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     double rel = 0.0;
     if (sch[SC_UNZ] == 0.0) {
         // zero iterate (a cold start): K u = 0 exactly, so r = f and ||r|| / ||f|| = 1
-        launch_cast_masked(f, l0.mask, l0.nn, h->r, s);
+        launch_cast_masked(f, l0, h->r, s);
         rel = 1.0;
     } else {
         TRY(true_residual(rel));  // r (FP32) = f - K u, FP64 norm
@@ -1249,12 +1290,14 @@ int gmg_kappa_eff(gmg_handle* h, const double* b, int steps, double out[3]) {
     if (!h || !b || !out) return fail(GMG_ERR_ARG, "null argument");
     if (steps < 1 || steps > 1000) return fail(GMG_ERR_ARG, "steps must be in [1, 1000]");
     if (h->L == 1) return fail(GMG_ERR_ARG, "single-level hierarchy");
+    TRY(clear_pads(h));
+    h->pads_dirty = true;  // the probe may stop at a breakdown with non-finite scalars
     cudaStream_t s = h->stream;
     Level& l0 = h->lev[0];
     const long long n = 3 * l0.nn;
     if (!h->kap_u) TRY(dalloc(h, &h->kap_u, (size_t)n));
     CU(cudaMemsetAsync(h->kap_u, 0, sizeof(double) * n, s));
-    launch_cast_masked(b, l0.mask, l0.nn, h->r, s);
+    launch_cast_masked(b, l0, h->r, s);
     pcg_restart(h);
     std::vector<double> al, be;
     for (int k = 0; k < steps; ++k) {
@@ -1282,13 +1325,17 @@ int gmg_kappa_eff(gmg_handle* h, const double* b, int steps, double out[3]) {
 int gmg_vcycle_symmetry(gmg_handle* h, const float* x, const float* y, double* defect) {
     if (!h || !x || !y || !defect) return fail(GMG_ERR_ARG, "null argument");
     if (h->L == 1) return fail(GMG_ERR_ARG, "single-level hierarchy");
+    TRY(clear_pads(h));
     cudaStream_t s = h->stream;
-    const long long n = 3 * h->lev[0].nn;
-    vcycle_level(h, 0, y, h->z, h->x2_0, -1, FIN_NONE);   // M y
-    vcycle_level(h, 0, x, h->p, h->x2_0, -1, FIN_NONE);   // M x
-    launch_dot_f32(x, h->z, n, h->partials, s);
+    const Level& l0 = h->lev[0];
+    const long long n = 3 * l0.nnp;
+    launch_pack0(x, l0, h->r, s);
+    launch_pack0(y, l0, h->q, s);
+    vcycle_level(h, 0, h->q, h->z, h->x2_0, -1, FIN_NONE);   // M y
+    vcycle_level(h, 0, h->r, h->p, h->x2_0, -1, FIN_NONE);   // M x
+    launch_dot_f32(h->r, h->z, n, h->partials, s);
     launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_TMP, FIN_NONE, s);
-    launch_dot_f32(y, h->p, n, h->partials, s);
+    launch_dot_f32(h->q, h->p, n, h->partials, s);
     launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_TMP + 1, FIN_NONE, s);
     TRY(sync_scalars(h));
     const double a = h->sc_host[SC_TMP], b = h->sc_host[SC_TMP + 1];
@@ -1331,7 +1378,7 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out) {
         return rc;
     };
     cudaStream_t s = h->stream;
-    const long long n0 = 3 * h->lev[0].nn;
+    const long long n0 = 3 * h->lev[0].nnp;
     int rc = GMG_OK;
     for (int li = 1; li < h->L && rc == GMG_OK; ++li) {
         Level& l = h->lev[li];
@@ -1342,8 +1389,11 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out) {
         if (rc == GMG_OK) rc = dalloc(h, &l.d, 3 * l.nn);
     }
     float** fv[] = {&h->r, &h->z, &h->p, &h->q, &h->x2_0, &h->t0, &h->d0};
-    for (float** v : fv)
+    for (float** v : fv) {
         if (rc == GMG_OK) rc = dalloc(h, v, n0);
+        if (rc == GMG_OK && cudaMemsetAsync(*v, 0, sizeof(float) * n0, s) != cudaSuccess) rc = GMG_ERR_CUDA;
+    }
+    h->pads_dirty = false;
     if (rc == GMG_OK) rc = dalloc(h, &h->sc, SC_COUNT);
     if (rc == GMG_OK) rc = dalloc(h, &h->kerr, 1);
     if (rc == GMG_OK) rc = dalloc(h, &h->partials, h->max_partials);
@@ -1432,6 +1482,8 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
     std::vector<int> state(count, 0);  // 0: active, 1: done
     std::vector<double> nf(count, 0.0);
     for (int i = 0; i < count; ++i) infos[i] = gmg_info{};
+    for (int i = 0; i < count; ++i)
+        if (int rc = clear_pads(hs[i]); rc != GMG_OK) { restore(); return rc; }
     // ---- norms, nonzero count of u, fixed DOFs of u to 0
     for (int i = 0; i < count; ++i) {
         gmg_handle* h = hs[i];
@@ -1455,10 +1507,10 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
         }
         nf[i] = std::sqrt(ff);
         if (h->sc_host[SC_UNZ] == 0.0) {
-            launch_cast_masked(f[i], l0.mask, l0.nn, h->r, s);
+            launch_cast_masked(f[i], l0, h->r, s);
             infos[i].rel_residual = 1.0;
         } else {
-            launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, h->sc, h->partials,
+            launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, l0.px, h->sc, h->partials,
                                 h->gh64, s);
             launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
             need_rel = true;
@@ -1544,7 +1596,7 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
                 state[i] = 1;
                 continue;
             }
-            launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, h->sc, h->partials,
+            launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, l0.px, h->sc, h->partials,
                                 h->gh64, s);
             launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
         }
@@ -1580,8 +1632,10 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
         }
     }
     int worst = GMG_OK;
+    for (int i = 0; i < count; ++i)
+        if (infos[i].status == GMG_NONFINITE) hs[i]->pads_dirty = true;
     for (int i = 0; i < count; ++i) {
-        if (int fe = check_fused(hs[i]); fe != GMG_OK) { restore(); return fe; }
+        if (int fe = check_fused(hs[i]); fe != GMG_OK) { hs[i]->pads_dirty = true; restore(); return fe; }
         infos[i].solve_ms = elapsed();
         infos[i].setup_ms = hs[i]->setup_ms;
         if (infos[i].status != GMG_OK) worst = infos[i].status;
@@ -1655,7 +1709,8 @@ int gmg_set_lambda(gmg_handle* h, int level, double lam) {
 int gmg_level_apply(gmg_handle* h, int level, const float* x, float* y) {
     TRY(check_level(h, level));
     if (!x || !y) return fail(GMG_ERR_ARG, "null vector");
-    level_apply(h, level, x, y, -1, FIN_NONE, true);
+    if (level == 0) return gmg_apply(h, x, y);
+    level_apply(h, level, x, y);
     CU(cudaGetLastError());
     return GMG_OK;
 }
@@ -1665,10 +1720,33 @@ int gmg_level_smooth(gmg_handle* h, int level, const float* b, float* x, int x_i
     if (level == h->L - 1) return fail(GMG_ERR_ARG, "the coarsest level has no smoother");
     if (!b || !x) return fail(GMG_ERR_ARG, "null vector");
     Level& l = h->lev[level];
-    float* S = level == 0 ? h->x2_0 : l.x2;
     int writes = 0;
-    float* res = smooth_pass(h, level, b, x, x, S, x_is_zero != 0, writes);
+    if (level == 0) {
+        TRY(clear_pads(h));
+        launch_pack0(b, l, h->r, h->stream);
+        if (!x_is_zero) launch_pack0(x, l, h->z, h->stream);
+        float* res = smooth_pass(h, 0, h->r, h->z, h->z, h->x2_0, x_is_zero != 0, writes);
+        launch_unpack0(res, l, x, h->stream);
+        CU(cudaGetLastError());
+        return GMG_OK;
+    }
+    float* res = smooth_pass(h, level, b, x, x, l.x2, x_is_zero != 0, writes);
     if (res != x) CU(cudaMemcpyAsync(x, res, sizeof(float) * 3 * l.nn, cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaGetLastError());
+    return GMG_OK;
+}
+
+int gmg_fine_pass(gmg_handle* h, int what) {
+    if (!h) return fail(GMG_ERR_ARG, "null handle");
+    if (what != 0 && what != 1) return fail(GMG_ERR_ARG, "what must be 0 (apply) or 1 (smoothing pass)");
+    if (what == 1 && h->L == 1) return fail(GMG_ERR_ARG, "single-level hierarchy");
+    TRY(clear_pads(h));
+    if (what == 0) {
+        level_apply(h, 0, h->p, h->q);
+    } else {
+        int writes = 0;
+        smooth_pass(h, 0, h->r, h->z, h->z, h->x2_0, false, writes);
+    }
     CU(cudaGetLastError());
     return GMG_OK;
 }
@@ -1677,6 +1755,11 @@ int gmg_restrict(gmg_handle* h, int level, const float* fine, float* coarse) {
     TRY(check_level(h, level));
     if (level + 1 >= h->L) return fail(GMG_ERR_ARG, "no coarser level");
     if (!fine || !coarse) return fail(GMG_ERR_ARG, "null vector");
+    if (level == 0) {
+        TRY(clear_pads(h));
+        launch_pack0(fine, h->lev[0], h->t0, h->stream);
+        fine = h->t0;
+    }
     launch_restrict(h->lev[level], h->lev[level + 1], fine, coarse, h->stream);
     CU(cudaGetLastError());
     return GMG_OK;
@@ -1686,6 +1769,15 @@ int gmg_prolong_add(gmg_handle* h, int level, const float* coarse, float* fine) 
     TRY(check_level(h, level));
     if (level + 1 >= h->L) return fail(GMG_ERR_ARG, "no coarser level");
     if (!fine || !coarse) return fail(GMG_ERR_ARG, "null vector");
+    if (level == 0) {
+        TRY(clear_pads(h));
+        const Level& l0 = h->lev[0];
+        launch_pack0(fine, l0, h->z, h->stream);
+        launch_prolong_add(l0, h->lev[1], coarse, h->z, h->stream);
+        launch_unpack0(h->z, l0, fine, h->stream);
+        CU(cudaGetLastError());
+        return GMG_OK;
+    }
     launch_prolong_add(h->lev[level], h->lev[level + 1], coarse, fine, h->stream);
     CU(cudaGetLastError());
     return GMG_OK;
@@ -1694,6 +1786,14 @@ int gmg_prolong_add(gmg_handle* h, int level, const float* coarse, float* fine) 
 int gmg_coarse_solve(gmg_handle* h, const float* b, float* x) {
     if (!h || !b || !x) return fail(GMG_ERR_ARG, "null argument");
     const Level& l = h->lev[h->L - 1];
+    if (h->L == 1) {  // the coarsest level is level 0
+        TRY(clear_pads(h));
+        launch_pack0(b, l, h->r, h->stream);
+        launch_coarse_solve(h->nL, h->free_idx_p, h->Ainv, h->r, h->z, l.maskp, l.nnp, h->stream);
+        launch_unpack0(h->z, l, x, h->stream);
+        CU(cudaGetLastError());
+        return GMG_OK;
+    }
     launch_coarse_solve(h->nL, h->free_idx, h->Ainv, b, x, l.mask, l.nn, h->stream);
     CU(cudaGetLastError());
     return GMG_OK;
@@ -1702,7 +1802,11 @@ int gmg_coarse_solve(gmg_handle* h, const float* b, float* x) {
 int gmg_vcycle(gmg_handle* h, const float* r, float* z) {
     if (!h || !r || !z) return fail(GMG_ERR_ARG, "null argument");
     if (h->L == 1) return fail(GMG_ERR_ARG, "single-level hierarchy");
-    vcycle_level(h, 0, r, z, h->x2_0, -1, FIN_NONE);
+    TRY(clear_pads(h));
+    const Level& l0 = h->lev[0];
+    launch_pack0(r, l0, h->r, h->stream);
+    vcycle_level(h, 0, h->r, h->z, h->x2_0, -1, FIN_NONE);
+    launch_unpack0(h->z, l0, z, h->stream);
     CU(cudaGetLastError());
     return GMG_OK;
 }
@@ -1713,7 +1817,8 @@ int gmg_residual64(gmg_handle* h, const double* f, const double* u, double* r, d
     cudaStream_t s = h->stream;
     h->sc_host[SC_UNZ] = 1.0;
     launch_set_scalars(h->sc + SC_UNZ, 1, 1.0, 0.0, 0.0, 0.0, s);
-    launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, r, nullptr, h->sc, h->partials, h->gh64, s);
+    launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, r, nullptr, l0.px, h->sc, h->partials, h->gh64,
+                        s);
     launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
     launch_dot_f64_masked(f, f, l0.mask, l0.nn, h->partials, s);
     launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_FF, FIN_NONE, s);

@@ -41,6 +41,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -143,7 +144,8 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
     const int nx = a.nx;
-    const int NX = nx + 1, NY = a.ny + 1, NZ = a.nz + 1, NXY = NX * NY, NEXY = nx * a.ny;
+    const int NX = nx + 1, NY = a.ny + 1, NZ = a.nz + 1, NEXY = nx * a.ny;
+    const int PX = a.pitch ? a.pitch : NX, NXY = PX * NY;  // vectors and mask: PX nodes per row
     const int x0 = blockIdx.x * (BX - 1), y0 = blockIdx.y * (BY - 1);
     const int k0 = blockIdx.z * zchunk, k1 = min(k0 + zchunk, NZ);
     const int kb = k0 - 1;                         // slot of plane / layer p is (p - kb) mod kRing
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
     const int ox = cx + 1, oy = cy + 1;
     const bool owner = tx < BX - 1 && ty < BY - 1 && ox < NX && oy < NY;
     const bool cell_in = cx >= 0 && cx < nx && cy >= 0 && cy < a.ny;
-    const int onode_base = oy * NX + ox, e_base = cy * nx + cx;
+    const int onode_base = oy * PX + ox, e_base = cy * nx + cx;
     const int own3 = 3 * (ty * (BX - 1) + tx);  // owned-node slot inside the block (owners only)
 
     // per-thread plane copy slots: offset inside a global plane and validity
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
         const int row = idx / ROW, c3 = idx % ROW;
         const int px = x0 - 1 + c3 / 3, py = y0 - 1 + row;
         cp_ok[q] = idx < PLANE && px >= 0 && px < NX && py >= 0 && py < NY;
-        cp_goff[q] = cp_ok[q] ? 3 * (py * NX + px) + c3 % 3 : 0;
+        cp_goff[q] = cp_ok[q] ? 3 * (py * PX + px) + c3 % 3 : 0;
     }
     const unsigned sp_dst = smem_u32(&sp[0][tid]), sE_dst = smem_u32(&sE[0][tid]);
     const unsigned sB_dst = smem_u32(&sB[0][EPI_B ? own3 : 0]), sD_dst = smem_u32(&sD[0][EPI_D ? own3 : 0]);
@@ -445,14 +447,15 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine_tc(FineArgs a, int zchunk) 
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty, warp = tid >> 5;
     const int nx = a.nx;
-    const int NX = nx + 1, NY = a.ny + 1, NZ = a.nz + 1, NXY = NX * NY, NEXY = nx * a.ny;
+    const int NX = nx + 1, NY = a.ny + 1, NZ = a.nz + 1, NEXY = nx * a.ny;
+    const int PX = a.pitch ? a.pitch : NX, NXY = PX * NY;  // vectors and mask: PX nodes per row
     const int x0 = blockIdx.x * (BX - 1), y0 = blockIdx.y * (BY - 1);
     const int k0 = blockIdx.z * zchunk, k1 = min(k0 + zchunk, NZ);
     const int kb = k0 - 1;
     const int cx = x0 - 1 + tx, cy = y0 - 1 + ty, ox = cx + 1, oy = cy + 1;
     const bool owner = tx < BX - 1 && ty < BY - 1 && ox < NX && oy < NY;
     const bool cell_in = cx >= 0 && cx < nx && cy >= 0 && cy < a.ny;
-    const int onode_base = oy * NX + ox, e_base = cy * nx + cx;
+    const int onode_base = oy * PX + ox, e_base = cy * nx + cx;
     const int own3 = 3 * (ty * (BX - 1) + tx);
     const int trow = tid & 127, ttile = tid >> 7;  // this element's row and tile in the MMA
 
@@ -489,7 +492,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine_tc(FineArgs a, int zchunk) 
         const int row = idx / ROW, c3 = idx % ROW;
         const int px = x0 - 1 + c3 / 3, py = y0 - 1 + row;
         cp_ok[q] = idx < PLANE && px >= 0 && px < NX && py >= 0 && py < NY;
-        cp_goff[q] = cp_ok[q] ? 3 * (py * NX + px) + c3 % 3 : 0;
+        cp_goff[q] = cp_ok[q] ? 3 * (py * PX + px) + c3 % 3 : 0;
     }
     const unsigned sp_dst = smem_u32(&sp[0][tid]), sE_dst = smem_u32(&sE[0][tid]);
     const unsigned sB_dst = smem_u32(&sB[0][own3]), sD_dst = smem_u32(&sD[0][own3]);
@@ -774,6 +777,321 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine_tc(FineArgs a, int zchunk) 
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-fed fine operator (the default for the solver's own level-0 vectors).
+// Same element arithmetic and z-march as k_fine, but every operand tile of a
+// step arrives by tiled TMA (cp.async.bulk.tensor) issued by one thread on one
+// mbarrier per ring slot, instead of per-thread 4-byte copies with their
+// address and predicate work.  This needs the level-0 vectors in the padded
+// layout [NZ][NY][px][3] with px (nodes per row) a multiple of 4, so every node
+// row starts on a 16-byte boundary, and the moduli in [nz][ny][ex] with ex a
+// multiple of 4.  A box's innermost coordinate is rounded down to a multiple of
+// 4 floats; the block reads its tile at a constant offset (0..3 floats) inside
+// the box.  Boxes reaching outside the grid read zeros (TMA fill), so there are
+// no edge predicates on the staged data.
+//
+// Stage s (ring slot (s - kb) mod 4) holds: node plane s+1 (the top face of
+// layer s), moduli layer s, and the epilogue operands (b, previous increment)
+// of node plane s-1, which is finished at step s.  Stage s is issued at step
+// s-3, right after the block barrier that ends the reads of the slot's previous
+// stage.  The loop takes four steps per trip, so ring slots are compile-time
+// offsets and the mbarrier phase is one bit per trip.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+          "r"(smem_u32(bar))
+        : "memory");
+}
+
+__host__ __device__ constexpr int round4(int v) { return (v + 3) / 4 * 4; }
+__host__ __device__ constexpr int round128(int v) { return (v + 127) / 128 * 128; }
+__device__ __forceinline__ int floor4(int v) { return v & ~3; }  // two's complement: rounds toward -inf
+
+template <int BX, int BY>
+struct TmaTile {
+    static constexpr int XW = round4(3 * (BX + 1) + 3);  // floats per staged node row (+ up to 3 of offset)
+    static constexpr int XR = BY + 1;                    // node rows
+    static constexpr int EW = round4(BX + 3);            // moduli per staged row
+    static constexpr int ER = BY;
+    static constexpr int OW = round4(3 * (BX - 1) + 3);  // floats per row of owned nodes
+    static constexpr int OR = BY - 1;
+    static constexpr int XB = XW * XR * 4, EB = EW * ER * 4, OB = OW * OR * 4;
+    static constexpr int XOFF = 0;
+    static constexpr int EOFF = round128(XB);
+    static constexpr int BOFF = EOFF + round128(EB);
+    static constexpr int DOFF = BOFF + round128(OB);
+    static constexpr int STAGE = DOFF + round128(OB);
+    static constexpr int SXOFF = 4 * STAGE;              // y-exchange [2][BY][BX] float4
+    static constexpr int BAROFF = SXOFF + 2 * BY * BX * 16;
+    static constexpr int SMEM = BAROFF + 4 * 8;
+};
+
+constexpr unsigned kTmaSpin = 1u << 22;
+
+template <int BX, int BY, int MODE, bool DOT>
+__global__ void __launch_bounds__(BX * BY, 2)
+k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tme,
+           const __grid_constant__ CUtensorMap tmb, const __grid_constant__ CUtensorMap tmd, FineArgs a, GHat G,
+           int zchunk) {
+    using T = TmaTile<BX, BY>;
+    constexpr int NT = BX * BY;
+    constexpr bool EPI_B = MODE != FM_APPLY;
+    constexpr bool EPI_D = MODE == FM_SMOOTH;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4(*sx)[BY][BX] = reinterpret_cast<float4(*)[BY][BX]>(smem + T::SXOFF);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + T::BAROFF);
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
+    const int px = a.pitch, NXYp = px * NY;
+    const int x0 = blockIdx.x * (BX - 1), y0 = blockIdx.y * (BY - 1);
+    const int k0 = blockIdx.z * zchunk, k1 = min(k0 + zchunk, NZ);
+    const int kb = k0 - 1;
+    // box origins (innermost coordinate rounded down to 4 floats) and offsets
+    const int xs = floor4(3 * (x0 - 1)), es = floor4(x0 - 1), bs = floor4(3 * x0);
+    const int rx = ty * T::XW + 3 * tx + (3 * (x0 - 1) - xs);  // this column's low corner in a node plane
+    const int re = ty * T::EW + tx + (x0 - 1 - es);            // this column's modulus in a layer
+    const int rb = ty * T::OW + 3 * tx + (3 * x0 - bs);        // this owner's node in an epilogue plane
+    const int ox = x0 + tx, oy = y0 + ty;
+    const bool owner = tx < BX - 1 && ty < BY - 1 && ox < NX && oy < NY;
+    const int onode = oy * px + ox;
+    const float cd = EPI_D ? (float)a.coef[2 * a.step] : 0.f;
+    const float ca = EPI_D ? (float)a.coef[2 * a.step + 1] : 0.f;
+    const bool need_d = EPI_D && cd != 0.f;
+    const unsigned epi_bytes = EPI_B ? (unsigned)T::OB * (need_d ? 2u : 1u) : 0u;
+
+    if ((smem_u32(smem) & 127) != 0) {  // TMA destinations are laid out on 128-byte boundaries
+        if (tid == 0) atomicExch(a.err, 1);
+        return;
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mbar_init(&full[q], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    // Everything above ran before the previous kernel finished (programmatic
+    // dependent launch); the operands may only be read from here on.
+    pdl_entry();
+
+    // stage s into its ring slot (thread 0 only); stages past the chunk's last
+    // read are skipped, and so are their waits.  issued[q] counts the phases
+    // started on slot q (thread 0's copy only), for the failure path.
+    int issued[4] = {0, 0, 0, 0};
+    auto issue = [&](int s) {
+        const int q = (s - kb) & 3;
+        unsigned char* st = smem + q * T::STAGE;
+        const bool xe = s < k1;
+        const bool ep = EPI_B && s > k0;
+        const unsigned bytes = (xe ? (unsigned)(T::XB + T::EB) : 0u) + (ep ? epi_bytes : 0u);
+        if (bytes == 0) return;
+        ++issued[q];
+        mbar_expect_tx(&full[q], bytes);
+        if (xe) {
+            tma_load_3d(st + T::XOFF, &tmx, xs, y0 - 1, s + 1, &full[q]);
+            tma_load_3d(st + T::EOFF, &tme, es, y0 - 1, s, &full[q]);
+        }
+        if (ep) {
+            tma_load_3d(st + T::BOFF, &tmb, bs, y0, s - 1, &full[q]);
+            if (need_d) tma_load_3d(st + T::DOFF, &tmd, bs, y0, s - 1, &full[q]);
+        }
+    };
+    auto wait_full = [&](int q, unsigned parity) -> bool {
+        for (unsigned it = 0; it < kTmaSpin; ++it)
+            if (mbar_try_wait(&full[q], parity)) return true;
+        return false;
+    };
+    auto load_mask = [&](int kp) -> uint8_t {
+        return (owner && kp >= k0 && kp < k1) ? a.mask[onode + kp * NXYp] : (uint8_t)7;
+    };
+
+    // ---- prologue: bottom plane kb into slot 3's plane region (its first phase),
+    // stages kb .. kb+2 into slots 0..2
+    if (tid == 0) {
+        issued[3] = 1;
+        mbar_expect_tx(&full[3], (unsigned)T::XB);
+        tma_load_3d(smem + 3 * T::STAGE + T::XOFF, &tmx, xs, y0 - 1, kb, &full[3]);
+        issue(kb);
+        if (kb + 1 <= k1) issue(kb + 1);
+        if (kb + 2 <= k1) issue(kb + 2);
+    }
+    bool failed = !wait_full(3, 0);
+    Layer s0, s1;
+    {
+        const float* pl = reinterpret_cast<const float*>(smem + 3 * T::STAGE + T::XOFF) + rx;
+        s0.C[0] = vld(pl);
+        s0.C[1] = vld(pl + 3);
+        s0.C[2] = vld(pl + T::XW);
+        s0.C[3] = vld(pl + T::XW + 3);
+        face_diffs(s0.C, s0.Q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s0.T[q] = V3{make_float2(0.f, 0.f), 0.f};
+        s0.E = 0.f;
+    }
+    uint8_t mk0 = 7, mk1 = load_mask(k0);
+    bool pending = false;
+    V3 R1{make_float2(0.f, 0.f), 0.f}, un_pend{make_float2(0.f, 0.f), 0.f};
+    float eR1 = 0.f;
+    uint8_t m_pend = 7;
+    DSAcc dotv;
+
+    // epilogue of the owned node of plane kp from the stage in slot q
+    auto finish = [&](int kp, int q) {
+        const float4 up = sx[kp & 1][ty + 1][tx];
+        const float y[3] = {R1.xy.x + up.x, R1.xy.y + up.y, R1.z + up.z};
+        float* out = a.out + 3 * (onode + kp * NXYp);
+        if (MODE == FM_APPLY) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float v = fixed_bit(m_pend, c) ? 0.f : y[c];
+                out[c] = v;
+                if (DOT) dotv.add_prod(comp(un_pend, c), v);
+            }
+        } else {
+            const float* bb = reinterpret_cast<const float*>(smem + q * T::STAGE + T::BOFF) + rb;
+            if (MODE == FM_RESID) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[c] = fixed_bit(m_pend, c) ? 0.f : bb[c] - y[c];
+            } else {
+                const float* dd = reinterpret_cast<const float*>(smem + q * T::STAGE + T::DOFF) + rb;
+                const float inv = __frcp_rn(a.kd * (eR1 + up.w));
+                float* dn_out = a.dnew ? a.dnew + 3 * (onode + kp * NXYp) : nullptr;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float xn = 0.f, dn = 0.f;
+                    if (!fixed_bit(m_pend, c)) {
+                        dn = ca * inv * (bb[c] - y[c]);
+                        if (need_d) dn = fmaf(cd, dd[c], dn);
+                        xn = comp(un_pend, c) + dn;
+                        if (DOT) dotv.add_prod(bb[c], xn);
+                    }
+                    out[c] = xn;
+                    if (dn_out) dn_out[c] = dn;
+                }
+            }
+        }
+    };
+
+    // one step s = one element layer (bottom face in `in`, top face into `out`)
+    // with the stage in slot Q; `par` is the trip's phase bit
+    auto step = [&](auto Qc, const int s, const unsigned par, const Layer& in, Layer& out) -> bool {
+        constexpr int Q = decltype(Qc)::value;
+        if (!wait_full(Q, par ^ (Q == 3 ? 1u : 0u))) failed = true;
+        if (__syncthreads_or(failed)) return false;
+        if (tid == 0 && s + 3 <= k1) issue(s + 3);
+        if (pending && owner) finish(s - 1, Q);
+        pending = false;
+        const uint8_t mcur = mk0;
+        mk0 = mk1;
+        mk1 = load_mask(s + 2);
+        {
+            const float* pl = reinterpret_cast<const float*>(smem + Q * T::STAGE + T::XOFF) + rx;
+            out.C[0] = vld(pl);
+            out.C[1] = vld(pl + 3);
+            out.C[2] = vld(pl + T::XW);
+            out.C[3] = vld(pl + T::XW + 3);
+            face_diffs(out.C, out.Q);
+        }
+        out.E = reinterpret_cast<const float*>(smem + Q * T::STAGE + T::EOFF)[re];
+        V3 v[8];
+        {
+            const V3 z00 = vsub(out.C[0], in.C[0]), z10 = vsub(out.C[1], in.C[1]);
+            const V3 z01 = vsub(out.C[2], in.C[2]), z11 = vsub(out.C[3], in.C[3]);
+            v[4] = vadd(vadd(z00, z10), vadd(z01, z11));
+#pragma unroll
+            for (int q = 1; q < 4; ++q) {
+                v[q] = vadd(out.Q[q], in.Q[q]);
+                v[q + 4] = vsub(out.Q[q], in.Q[q]);
+            }
+        }
+        V3 w[8];
+        w[0] = V3{make_float2(0.f, 0.f), 0.f};
+#pragma unroll
+        for (int sg = 0; sg < 8; ++sg) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const int mi = mono(sg, i);
+                if (mi == 0) continue;
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int mj = mono(sg, j);
+                    if (mj == 0) continue;
+                    acc = fmaf(G.g[sg * 9 + i * 3 + j], comp(v[mj], j), acc);
+                }
+                set_comp(w[mi], i, acc);
+            }
+        }
+        const float2 E2 = make_float2(out.E, out.E);
+#pragma unroll
+        for (int m = 1; m < 8; ++m) w[m] = V3{__fmul2_rn(E2, w[m].xy), out.E * w[m].z};
+        V3 Bf[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            out.T[q] = vadd(w[q], w[q + 4]);
+            Bf[q] = vsub(w[q], w[q + 4]);
+        }
+        if (s >= k0) {
+            const V3 S0 = vadd(in.T[0], Bf[0]), S1 = vadd(in.T[1], Bf[1]);
+            const V3 S2 = vadd(in.T[2], Bf[2]), S3 = vadd(in.T[3], Bf[3]);
+            const V3 p = vsub(S0, S2), qd = vsub(S1, S3), r = vadd(S0, S2), sd = vadd(S1, S3);
+            const V3 c00 = vsub(p, qd), c10 = vadd(p, qd), c01 = vsub(r, sd), c11 = vadd(r, sd);
+            V3 n01, n00;
+            n01.xy.x = __shfl_down_sync(0xffffffffu, c01.xy.x, 1, BX);
+            n01.xy.y = __shfl_down_sync(0xffffffffu, c01.xy.y, 1, BX);
+            n01.z = __shfl_down_sync(0xffffffffu, c01.z, 1, BX);
+            n00.xy.x = __shfl_down_sync(0xffffffffu, c00.xy.x, 1, BX);
+            n00.xy.y = __shfl_down_sync(0xffffffffu, c00.xy.y, 1, BX);
+            n00.z = __shfl_down_sync(0xffffffffu, c00.z, 1, BX);
+            R1 = vadd(c11, n01);
+            const V3 r0 = vadd(c10, n00);
+            const float esum = in.E + out.E;
+            const float er = esum + __shfl_down_sync(0xffffffffu, esum, 1, BX);
+            sx[s & 1][ty][tx] = make_float4(r0.xy.x, r0.xy.y, r0.z, er);
+            pending = true;
+            eR1 = er;
+            un_pend = in.C[3];
+            m_pend = mcur;
+        }
+        return true;
+    };
+
+    // layers kb .. k1-1, four per trip (slots 0..3 in order), the layer state
+    // alternating between s0 and s1
+    unsigned par = 0;
+    bool ok = !failed;
+    for (int s = kb; ok && s < k1; s += 4, par ^= 1u) {
+        ok = step(std::integral_constant<int, 0>{}, s, par, s0, s1);
+        if (ok && s + 1 < k1) ok = step(std::integral_constant<int, 1>{}, s + 1, par, s1, s0);
+        if (ok && s + 2 < k1) ok = step(std::integral_constant<int, 2>{}, s + 2, par, s0, s1);
+        if (ok && s + 3 < k1) ok = step(std::integral_constant<int, 3>{}, s + 3, par, s1, s0);
+    }
+    if (ok) {
+        // the last plane: its epilogue operands are stage k1's
+        const int q = (k1 - kb) & 3;
+        const unsigned pq = (unsigned)(((k1 - kb) >> 2) & 1) ^ (q == 3 ? 1u : 0u);
+        if (EPI_B && !wait_full(q, pq)) failed = true;
+        ok = !__syncthreads_or(failed);
+        if (ok && pending && owner) finish(k1 - 1, q);
+    }
+    if (!ok) {
+        // a wait gave up: let the copies already issued land (bounded) before
+        // the block's shared memory is released, and record the failure
+        if (tid == 0) {
+            for (int q = 0; q < 4; ++q)
+                if (issued[q] > 0) wait_full(q, (unsigned)(issued[q] - 1) & 1u);  // phases complete in order
+            atomicExch(a.err, 1);
+        }
+        return;
+    }
+    if (DOT) {
+        const double sum = block_sum<NT>(dotv.value(), tid);
+        if (tid == 0) a.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = sum;
+    }
+}
+
 // Copies x with the fixed DOFs of the fine level set to 0 (operands supplied by
 // a caller may hold values there; the operator ignores them).
 __global__ void k_mask_copy(const float* x, const uint8_t* mask, long long nn, float* out) {
@@ -914,6 +1232,10 @@ void fine_set_plan(int nx, int ny, int nz, int tile, int zc) {
 }
 
 void launch_fine(int mode, int dot, int mask_in, const FineArgs& a_in, const GHat& G, cudaStream_t s) {
+    // the solver's own level-0 vectors (padded rows, padded moduli): TMA-fed kernel
+    if (!mask_in && a_in.Ep && a_in.pitch % 4 == 0 && a_in.pitch > 0 &&
+        launch_fine_tma(mode, dot, a_in, G, s) == GMG_OK)
+        return;
     const FinePlan pl = plan_fine(a_in.nx, a_in.ny, a_in.nz);
     FineArgs a = a_in;
     if (mask_in && a.scratch) {
@@ -933,6 +1255,52 @@ void launch_fine(int mode, int dot, int mask_in, const FineArgs& a_in, const GHa
     } else {
         launch_shape<FM_RESID, false>(pl, a, G, s);
     }
+}
+
+namespace {
+template <int BX, int BY, int MODE, bool DOT>
+int launch_tma_tile(const FinePlan& pl, const FineArgs& a, const GHat& G, cudaStream_t s) {
+    using T = TmaTile<BX, BY>;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_fine_tma<BX, BY, MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 T::SMEM) != cudaSuccess)
+            return GMG_ERR_CUDA;
+        attr = true;
+    }
+    const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
+    // node vectors: [NZ][NY][pitch][3] FP32, of which 3 NX floats per row are the grid
+    const unsigned long long vd[3] = {3ull * NX, (unsigned long long)NY, (unsigned long long)NZ};
+    const unsigned long long vs[2] = {12ull * a.pitch, 12ull * a.pitch * NY};
+    const unsigned long long ed[3] = {(unsigned long long)a.nx, (unsigned long long)a.ny, (unsigned long long)a.nz};
+    const unsigned long long es[2] = {4ull * a.epitch, 4ull * a.epitch * a.ny};
+    const unsigned bx_x[3] = {(unsigned)T::XW, (unsigned)T::XR, 1u};
+    const unsigned bx_o[3] = {(unsigned)T::OW, (unsigned)T::OR, 1u};
+    const unsigned bx_e[3] = {(unsigned)T::EW, (unsigned)T::ER, 1u};
+    CUtensorMap mx, me, mb, md;
+    const float* b = a.b ? a.b : a.xin;
+    const float* d = a.dold ? a.dold : b;
+    if (!encode_f32_map_strided(&mx, a.xin, 3, vd, vs, bx_x) || !encode_f32_map_strided(&me, a.Ep, 3, ed, es, bx_e) ||
+        !encode_f32_map_strided(&mb, b, 3, vd, vs, bx_o) || !encode_f32_map_strided(&md, d, 3, vd, vs, bx_o))
+        return GMG_ERR_CUDA;
+    note_launch();
+    pdl_launch(k_fine_tma<BX, BY, MODE, DOT>, dim3(pl.grid), dim3(BX, BY), (size_t)T::SMEM, s, mx, me, mb, md, a, G,
+               pl.zc);
+    return GMG_OK;
+}
+template <int MODE, bool DOT>
+int launch_tma_shape(const FinePlan& pl, const FineArgs& a, const GHat& G, cudaStream_t s) {
+    return pl.tile == 0 ? launch_tma_tile<32, 8, MODE, DOT>(pl, a, G, s) : launch_tma_tile<16, 16, MODE, DOT>(pl, a, G, s);
+}
+}  // namespace
+
+int launch_fine_tma(int mode, int dot, const FineArgs& a, const GHat& G, cudaStream_t s) {
+    if (a.pitch % 4 != 0 || a.epitch % 4 != 0 || !a.Ep) return GMG_ERR_ARG;
+    const FinePlan pl = plan_fine(a.nx, a.ny, a.nz);
+    if (mode == FM_APPLY) return dot ? launch_tma_shape<FM_APPLY, true>(pl, a, G, s) : launch_tma_shape<FM_APPLY, false>(pl, a, G, s);
+    if (mode == FM_SMOOTH)
+        return dot ? launch_tma_shape<FM_SMOOTH, true>(pl, a, G, s) : launch_tma_shape<FM_SMOOTH, false>(pl, a, G, s);
+    return launch_tma_shape<FM_RESID, false>(pl, a, G, s);
 }
 
 // Operand B of the tensor-core smoother: row o = the 24 corner forces of an

@@ -49,7 +49,7 @@ __device__ __forceinline__ bool fixed_bit(uint8_t m, int c) { return (m >> c) & 
 
 // The fine level's Jacobi scale per node, 1 / (kd * sum of the moduli of the
 // elements around it) (the diagonal of K is kd E_e summed over those elements).
-__global__ void k_fine_inv0(int nx, int ny, int nz, const float* E, float kd, float* inv0) {
+__global__ void k_fine_inv0(int nx, int ny, int nz, int px, const float* E, float kd, float* inv0) {
     const long long NX = nx + 1, NY = ny + 1, NZ = nz + 1;
     const long long nn = NX * NY * NZ;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
@@ -62,7 +62,7 @@ __global__ void k_fine_inv0(int nx, int ny, int nz, const float* E, float kd, fl
             if (ex >= 0 && ex < nx && ey >= 0 && ey < ny && ez >= 0 && ez < nz)
                 esum += E[ex + (long long)nx * (ey + (long long)ny * ez)];
         }
-        inv0[n] = 1.f / (kd * esum);
+        inv0[i + (long long)px * (j + NY * k)] = 1.f / (kd * esum);
     }
 }
 
@@ -70,7 +70,7 @@ __global__ void k_fine_inv0(int nx, int ny, int nz, const float* E, float kd, fl
 // with the Jacobi scale from set-up.
 __global__ void k_fine_smooth0(FineArgs a) {
     pdl_entry();
-    const long long nn = (long long)(a.nx + 1) * (a.ny + 1) * (a.nz + 1);
+    const long long nn = (long long)a.pitch * (a.ny + 1) * (a.nz + 1);  // pads: mask 7, output 0
     const float ca = (float)a.coef[1];
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
          n += (long long)gridDim.x * blockDim.x) {
@@ -518,10 +518,10 @@ __device__ __forceinline__ void coarse_parents2(int f, int nf, int idx[2], float
 }
 
 // b_c = P^T t at coarse node n (masked), the restriction of Eq. vcycle.
-__device__ __forceinline__ void restrict_node(int n, int fnx, int fny, int fnz, int cnx, int cny, const uint8_t* cmask,
-                                              const float* fine, float out[3]) {
+__device__ __forceinline__ void restrict_node(int n, int fnx, int fny, int fnz, int fpx, int cnx, int cny,
+                                              const uint8_t* cmask, const float* fine, float out[3]) {
     const int CX = cnx + 1, CY = cny + 1;
-    const int FX = fnx + 1, FY = fny + 1;
+    const int FX = fpx, FY = fny + 1;  // fine vectors: fpx nodes per row
     const int I = n % CX, J = (n / CX) % CY, K = n / (CX * CY);
     int ix[3], iy[3], iz[3];
     float wx[3], wy[3], wz[3];
@@ -551,12 +551,12 @@ __device__ __forceinline__ void restrict_node(int n, int fnx, int fny, int fnz, 
 // a zero iterate: b_c = P^T t (stored, later steps and the residual read it),
 // then x = c_a D^-1 b_c (and the Chebyshev increment d = x), with the same
 // arithmetic as k_restrict followed by k_bsr_smooth0.
-__global__ void k_restrict_smooth0(int fnx, int fny, int fnz, const float* fine, BsrArgs a, float* bout) {
+__global__ void k_restrict_smooth0(int fnx, int fny, int fnz, int fpx, const float* fine, BsrArgs a, float* bout) {
     pdl_entry();
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (int)a.nn) return;
     float bc[3];
-    restrict_node(n, fnx, fny, fnz, a.nx, a.ny, a.mask, fine, bc);
+    restrict_node(n, fnx, fny, fnz, fpx, a.nx, a.ny, a.mask, fine, bc);
     const float ca = (float)a.coef[1];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -568,20 +568,20 @@ __global__ void k_restrict_smooth0(int fnx, int fny, int fnz, const float* fine,
     }
 }
 
-__global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz, const uint8_t* cmask,
+__global__ void k_restrict(int fnx, int fny, int fnz, int fpx, int cnx, int cny, int cnz, const uint8_t* cmask,
                            const float* fine, float* coarse) {
     pdl_entry();
     const int nn = (cnx + 1) * (cny + 1) * (cnz + 1);
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
     float bc[3];
-    restrict_node(n, fnx, fny, fnz, cnx, cny, cmask, fine, bc);
+    restrict_node(n, fnx, fny, fnz, fpx, cnx, cny, cmask, fine, bc);
     coarse[3 * n] = bc[0];
     coarse[3 * n + 1] = bc[1];
     coarse[3 * n + 2] = bc[2];
 }
 
-__global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, const uint8_t* fmask,
+__global__ void k_prolong_add(int fnx, int fny, int fnz, int fpx, int cnx, int cny, const uint8_t* fmask,
                               const float* coarse, float* fine) {
     pdl_entry();
     const int FX = fnx + 1, FY = fny + 1, nn = FX * FY * (fnz + 1);
@@ -608,9 +608,10 @@ __global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, const
                 s2 = fmaf(w, coarse[3 * m + 2], s2);
             }
     const uint8_t msk = fmask[n];
-    if (!fixed_bit(msk, 0)) fine[3 * n] += s0;
-    if (!fixed_bit(msk, 1)) fine[3 * n + 1] += s1;
-    if (!fixed_bit(msk, 2)) fine[3 * n + 2] += s2;
+    const int np = i + fpx * (j + FY * k);  // the node in the fine vectors' numbering
+    if (!fixed_bit(msk, 0)) fine[3 * np] += s0;
+    if (!fixed_bit(msk, 1)) fine[3 * np + 1] += s1;
+    if (!fixed_bit(msk, 2)) fine[3 * np + 2] += s2;
 }
 
 // x[free_idx[i]] = sum_j Ainv[i][j] b[free_idx[j]]  (FP64 accumulation), and
@@ -686,46 +687,37 @@ __global__ void __launch_bounds__(kVecThreads) k_finalize(const double* partial,
     }
 }
 
-// u += alpha p (FP64), r -= alpha q (FP32), partial ||r||^2.  Four consecutive
-// entries per thread and iteration with 16-byte loads when every pointer allows.
-__global__ void __launch_bounds__(kVecThreads) k_pcg_update(double* u, float* r, const float* p, const float* q, long long n,
-                                                            const double* sc, double* partial, int vec4) {
+// u += alpha p (FP64, dense numbering), r -= alpha q (FP32 level-0 vectors of
+// pitch px), partial ||r||^2.  A thread takes four consecutive vector entries
+// (16-byte loads; a row of 3 px floats is a multiple of 4) and skips the pads,
+// whose values stay 0.
+__global__ void __launch_bounds__(kVecThreads) k_pcg_update(double* u, float* r, const float* p, const float* q, int NX,
+                                                            int px, long long n4, const double* sc, double* partial) {
     pdl_entry();
     const double alpha = sc[SC_ALPHA];
     const float af = (float)alpha;
+    const int rowp = 3 * px, rowd = 3 * NX;
     DSAcc acc;
     const long long stride = (long long)gridDim.x * kVecThreads;
-    long long done = 0;
-    if (vec4) {
-        const long long n4 = n / 4;
-        for (long long i = blockIdx.x * (long long)kVecThreads + threadIdx.x; i < n4; i += stride) {
-            const float4 pv = reinterpret_cast<const float4*>(p)[i];
-            const float4 qv = reinterpret_cast<const float4*>(q)[i];
-            float4 rv = reinterpret_cast<float4*>(r)[i];
-            double2 u0 = reinterpret_cast<double2*>(u)[2 * i], u1 = reinterpret_cast<double2*>(u)[2 * i + 1];
-            u0.x = fma(alpha, (double)pv.x, u0.x);
-            u0.y = fma(alpha, (double)pv.y, u0.y);
-            u1.x = fma(alpha, (double)pv.z, u1.x);
-            u1.y = fma(alpha, (double)pv.w, u1.y);
-            rv.x = fmaf(-af, qv.x, rv.x);
-            rv.y = fmaf(-af, qv.y, rv.y);
-            rv.z = fmaf(-af, qv.z, rv.z);
-            rv.w = fmaf(-af, qv.w, rv.w);
-            reinterpret_cast<double2*>(u)[2 * i] = u0;
-            reinterpret_cast<double2*>(u)[2 * i + 1] = u1;
-            reinterpret_cast<float4*>(r)[i] = rv;
-            acc.add_prod(rv.x, rv.x);
-            acc.add_prod(rv.y, rv.y);
-            acc.add_prod(rv.z, rv.z);
-            acc.add_prod(rv.w, rv.w);
+    for (long long i = blockIdx.x * (long long)kVecThreads + threadIdx.x; i < n4; i += stride) {
+        const long long e = 4 * i;
+        const long long row = e / rowp;
+        const int c0 = (int)(e - row * rowp);
+        if (c0 >= rowd) continue;  // four pad entries
+        const float4 pv = reinterpret_cast<const float4*>(p)[i];
+        const float4 qv = reinterpret_cast<const float4*>(q)[i];
+        float4 rv = reinterpret_cast<float4*>(r)[i];
+        const float pa[4] = {pv.x, pv.y, pv.z, pv.w}, qa[4] = {qv.x, qv.y, qv.z, qv.w};
+        float ra[4] = {rv.x, rv.y, rv.z, rv.w};
+        double* ud = u + row * rowd + c0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (c0 + t >= rowd) break;
+            ud[t] = fma(alpha, (double)pa[t], ud[t]);
+            ra[t] = fmaf(-af, qa[t], ra[t]);
+            acc.add_prod(ra[t], ra[t]);
         }
-        done = 4 * n4;
-    }
-    for (long long i = done + blockIdx.x * (long long)kVecThreads + threadIdx.x; i < n; i += stride) {
-        u[i] = fma(alpha, (double)p[i], u[i]);
-        const float rn = fmaf(-af, q[i], r[i]);
-        r[i] = rn;
-        acc.add_prod(rn, rn);
+        reinterpret_cast<float4*>(r)[i] = make_float4(ra[0], ra[1], ra[2], ra[3]);
     }
     const double s = block_sum<kVecThreads>(acc.value(), threadIdx.x);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -775,11 +767,14 @@ __global__ void k_axpy_dev(float* y, const float* x, long long n, const double* 
         y[i] = fmaf(c, x[i], y[i]);
 }
 
-// u += a * z, accumulated in FP64.
-__global__ void k_axpy_u64(double* u, const float* z, long long n, double a) {
+// u (dense numbering) += a * z (a level-0 vector of pitch px), accumulated in FP64.
+__global__ void k_axpy_u64(double* u, const float* z, int NX, int px, long long n, double a) {
     pdl_entry();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        u[i] = fma(a, (double)z[i], u[i]);
+    const int rowd = 3 * NX, rowp = 3 * px;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long row = i / rowd;
+        u[i] = fma(a, (double)z[i + row * (rowp - rowd)], u[i]);
+    }
 }
 
 // ||r||^2 from the partial sums (the same sum as k_finalize into SC_RR), then
@@ -799,11 +794,38 @@ __global__ void __launch_bounds__(kVecThreads) k_finalize_check(const double* pa
     cudaGraphSetConditional(cond, go ? 1u : 0u);
 }
 
-// r = f on free DOFs (as FP32), 0 on fixed ones: the residual of the zero iterate.
-__global__ void __launch_bounds__(kVecThreads) k_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r) {
+// r = f on free DOFs (as FP32), 0 on fixed ones and on the pads: the residual of
+// the zero iterate.  f dense; r and maskp in the level-0 vector numbering.
+__global__ void __launch_bounds__(kVecThreads) k_cast_masked(const double* f, const uint8_t* maskp, int NX, int px,
+                                                             long long nnp, float* r) {
     pdl_entry();
-    for (long long q = blockIdx.x * (long long)kVecThreads + threadIdx.x; q < 3 * nn; q += (long long)gridDim.x * kVecThreads)
-        r[q] = fixed_bit(mask[q / 3], (int)(q % 3)) ? 0.f : (float)f[q];
+    const int rowd = 3 * NX, rowp = 3 * px;
+    for (long long q = blockIdx.x * (long long)kVecThreads + threadIdx.x; q < 3 * nnp; q += (long long)gridDim.x * kVecThreads) {
+        const long long row = q / rowp;
+        const int c = (int)(q - row * rowp);
+        r[q] = (c >= rowd || fixed_bit(maskp[q / 3], c % 3)) ? 0.f : (float)f[row * rowd + c];
+    }
+}
+
+// out = in with fixed DOFs and pads 0: in dense, out a level-0 vector.
+__global__ void k_pack0(const float* in, const uint8_t* maskp, int NX, int px, long long nnp, float* out) {
+    pdl_entry();
+    const int rowd = 3 * NX, rowp = 3 * px;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 3 * nnp; q += (long long)gridDim.x * blockDim.x) {
+        const long long row = q / rowp;
+        const int c = (int)(q - row * rowp);
+        out[q] = (c >= rowd || fixed_bit(maskp[q / 3], c % 3)) ? 0.f : in[row * rowd + c];
+    }
+}
+
+// out (dense) = in (a level-0 vector).
+__global__ void k_unpack0(const float* in, int NX, int px, long long n, float* out) {
+    pdl_entry();
+    const int rowd = 3 * NX, rowp = 3 * px;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const long long row = q / rowd;
+        out[q] = in[q + row * (rowp - rowd)];
+    }
 }
 
 __global__ void k_scale_inv_sqrt(float* v, long long n, const double* sc, int slot) {
@@ -827,15 +849,16 @@ __device__ __forceinline__ float fine_diag(const float* E, int nx, int ny, int n
 }
 
 __global__ void k_scale_invdiag_fine(const float* y, float* w, const float* E, const uint8_t* mask, int nx, int ny,
-                                     int nz, float kd) {
+                                     int nz, int px, float kd) {
     pdl_entry();
     const long long NX = nx + 1, NY = ny + 1, nn = NX * NY * (nz + 1);
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
         const float inv = 1.f / fine_diag(E, nx, ny, nz, i, j, k, kd);
         const uint8_t m = mask[n];
+        const long long v = 3 * (i + px * (j + NY * k));
 #pragma unroll
-        for (int c = 0; c < 3; ++c) w[3 * n + c] = fixed_bit(m, c) ? 0.f : inv * y[3 * n + c];
+        for (int c = 0; c < 3; ++c) w[v + c] = fixed_bit(m, c) ? 0.f : inv * y[v + c];
     }
 }
 
@@ -846,7 +869,7 @@ __global__ void k_scale_invdiag_bsr(const float* y, float* w, const float* invdi
 }
 
 __global__ void __launch_bounds__(kVecThreads) k_diag_dot_fine(const float* v, const float* E, const uint8_t* mask, int nx,
-                                                               int ny, int nz, float kd, double* partial) {
+                                                               int ny, int nz, int px, float kd, double* partial) {
     pdl_entry();
     const long long NX = nx + 1, NY = ny + 1, nn = NX * NY * (nz + 1);
     double s = 0.0;
@@ -854,9 +877,10 @@ __global__ void __launch_bounds__(kVecThreads) k_diag_dot_fine(const float* v, c
         const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
         const double dg = fine_diag(E, nx, ny, nz, i, j, k, kd);
         const uint8_t m = mask[n];
+        const long long q = 3 * (i + px * (j + NY * k));
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            if (!fixed_bit(m, c)) s += dg * (double)v[3 * n + c] * (double)v[3 * n + c];
+            if (!fixed_bit(m, c)) s += dg * (double)v[q + c] * (double)v[q + c];
     }
     s = block_sum<kVecThreads>(s, threadIdx.x);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -873,12 +897,13 @@ __global__ void __launch_bounds__(kVecThreads) k_diag_dot_bsr(const float* v, co
 
 // Power-iteration start vector: v_i = ((i * 2654435761) mod 2^32) / 2^32 - 0.5 over
 // the level's DOF index i, 0 on fixed DOFs.
-__global__ void k_power_start(float* v, const uint8_t* mask, long long nn) {
+__global__ void k_power_start(float* v, const uint8_t* mask, long long nn, int NX, int px) {
     pdl_entry();
+    const int rowd = 3 * NX, rowp = 3 * px;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 3 * nn; q += (long long)gridDim.x * blockDim.x) {
         const unsigned long long h = ((unsigned long long)q * 2654435761ull) & 0xffffffffull;
         const double val = (double)h / 4294967296.0 - 0.5;
-        v[q] = fixed_bit(mask[q / 3], (int)(q % 3)) ? 0.f : (float)val;
+        v[q + (q / rowd) * (rowp - rowd)] = fixed_bit(mask[q / 3], (int)(q % 3)) ? 0.f : (float)val;
     }
 }
 
@@ -887,9 +912,9 @@ __global__ void k_power_start(float* v, const uint8_t* mask, long long nn) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-void launch_fine_inv0(int nx, int ny, int nz, const float* E, float kd, float* inv0, cudaStream_t s) {
+void launch_fine_inv0(int nx, int ny, int nz, int px, const float* E, float kd, float* inv0, cudaStream_t s) {
     note_launch();
-    k_fine_inv0<<<kVecBlocks * 2, kVecThreads, 0, s>>>(nx, ny, nz, E, kd, inv0);
+    k_fine_inv0<<<kVecBlocks * 2, kVecThreads, 0, s>>>(nx, ny, nz, px, E, kd, inv0);
 }
 
 void launch_fine_smooth0(const FineArgs& a, cudaStream_t s) {
@@ -1079,7 +1104,7 @@ int encode_bsr_maps(Level& l) {
 
 void launch_restrict_smooth0(const Level& f, const float* t, const BsrArgs& a, float* bout, cudaStream_t s) {
     note_launch();
-    pdl_launch(k_restrict_smooth0, dim3((int)((a.nn + 127) / 128)), dim3(128), 0, s, f.nx, f.ny, f.nz, t, a, bout);
+    pdl_launch(k_restrict_smooth0, dim3((int)((a.nn + 127) / 128)), dim3(128), 0, s, f.nx, f.ny, f.nz, f.px, t, a, bout);
 }
 
 void launch_bsr_smooth0(const BsrArgs& a, cudaStream_t s) {
@@ -1095,12 +1120,14 @@ static int grid_for(long long n) {
 
 void launch_restrict(const Level& f, const Level& c, const float* fine, float* coarse, cudaStream_t s) {
     note_launch();
-    pdl_launch(k_restrict, dim3((int)((c.nn + 127) / 128)), dim3(128), 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, c.mask, fine, coarse);
+    pdl_launch(k_restrict, dim3((int)((c.nn + 127) / 128)), dim3(128), 0, s, f.nx, f.ny, f.nz, f.px, c.nx, c.ny, c.nz, c.mask, fine,
+               coarse);
 }
 
 void launch_prolong_add(const Level& f, const Level& c, const float* coarse, float* fine, cudaStream_t s) {
     note_launch();
-    pdl_launch(k_prolong_add, dim3((int)((f.nn + 255) / 256)), dim3(256), 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, f.mask, coarse, fine);
+    pdl_launch(k_prolong_add, dim3((int)((f.nn + 255) / 256)), dim3(256), 0, s, f.nx, f.ny, f.nz, f.px, c.nx, c.ny, f.mask, coarse,
+               fine);
 }
 
 namespace {
@@ -1195,12 +1222,11 @@ void launch_finalize(const double* partial, int n, double* sc, int slot, int op,
     pdl_launch(k_finalize, dim3(1), dim3(kVecThreads), 0, s, partial, n, sc, slot, op);
 }
 
-void launch_pcg_update(double* u, float* r, const float* p, const float* q, long long n, const double* sc,
+void launch_pcg_update(double* u, float* r, const float* p, const float* q, const Level& l0, const double* sc,
                        double* partial, cudaStream_t s) {
     note_launch();
-    const bool vec4 = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(p) |
-                        reinterpret_cast<uintptr_t>(q)) & 15) == 0;
-    pdl_launch(k_pcg_update, dim3(kVecBlocks), dim3(kVecThreads), 0, s, u, r, p, q, n, sc, partial, vec4 ? 1 : 0);
+    pdl_launch(k_pcg_update, dim3(kVecBlocks), dim3(kVecThreads), 0, s, u, r, p, q, l0.nx + 1, l0.px, 3 * l0.nnp / 4, sc,
+               partial);
 }
 
 void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s) {
@@ -1219,9 +1245,10 @@ void launch_axpy_dev(float* y, const float* x, long long n, const double* coef, 
     pdl_launch(k_axpy_dev, dim3(grid_for(n)), dim3(256), 0, s, y, x, n, coef, sign);
 }
 
-void launch_axpy_u64(double* u, const float* z, long long n, double a, cudaStream_t s) {
+void launch_axpy_u64(double* u, const float* z, const Level& l0, double a, cudaStream_t s) {
     note_launch();
-    pdl_launch(k_axpy_u64, dim3(grid_for(n)), dim3(256), 0, s, u, z, n, a);
+    const long long n = 3 * l0.nn;
+    pdl_launch(k_axpy_u64, dim3(grid_for(n)), dim3(256), 0, s, u, z, l0.nx + 1, l0.px, n, a);
 }
 
 void launch_finalize_check(const double* partial, int n, double* sc, cudaGraphConditionalHandle cond,
@@ -1230,9 +1257,19 @@ void launch_finalize_check(const double* partial, int n, double* sc, cudaGraphCo
     pdl_launch(k_finalize_check, dim3(1), dim3(kVecThreads), 0, s, partial, n, sc, cond);
 }
 
-void launch_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r, cudaStream_t s) {
+void launch_cast_masked(const double* f, const Level& l0, float* r, cudaStream_t s) {
     note_launch();
-    pdl_launch(k_cast_masked, dim3(kVecBlocks), dim3(kVecThreads), 0, s, f, mask, nn, r);
+    pdl_launch(k_cast_masked, dim3(kVecBlocks), dim3(kVecThreads), 0, s, f, l0.maskp, l0.nx + 1, l0.px, l0.nnp, r);
+}
+
+void launch_pack0(const float* in, const Level& l0, float* out, cudaStream_t s) {
+    note_launch();
+    pdl_launch(k_pack0, dim3(grid_for(3 * l0.nnp)), dim3(256), 0, s, in, l0.maskp, l0.nx + 1, l0.px, l0.nnp, out);
+}
+
+void launch_unpack0(const float* in, const Level& l0, float* out, cudaStream_t s) {
+    note_launch();
+    pdl_launch(k_unpack0, dim3(grid_for(3 * l0.nn)), dim3(256), 0, s, in, l0.nx + 1, l0.px, 3 * l0.nn, out);
 }
 
 void launch_scale_by_inv_sqrt(float* v, long long n, const double* sc, int slot, cudaStream_t s) {
@@ -1240,11 +1277,9 @@ void launch_scale_by_inv_sqrt(float* v, long long n, const double* sc, int slot,
     pdl_launch(k_scale_inv_sqrt, dim3(grid_for(n)), dim3(256), 0, s, v, n, sc, slot);
 }
 
-void launch_scale_invdiag_fine(const float* y, float* w, const float* E, const uint8_t* mask, int nx, int ny,
-                               int nz, float kd, cudaStream_t s) {
-    const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+void launch_scale_invdiag_fine(const float* y, float* w, const float* E, const Level& l0, float kd, cudaStream_t s) {
     note_launch();
-    k_scale_invdiag_fine<<<grid_for(nn), 256, 0, s>>>(y, w, E, mask, nx, ny, nz, kd);
+    k_scale_invdiag_fine<<<grid_for(l0.nn), 256, 0, s>>>(y, w, E, l0.mask, l0.nx, l0.ny, l0.nz, l0.px, kd);
 }
 
 void launch_scale_invdiag_bsr(const float* y, float* w, const float* invdiag, long long n, cudaStream_t s) {
@@ -1252,10 +1287,9 @@ void launch_scale_invdiag_bsr(const float* y, float* w, const float* invdiag, lo
     k_scale_invdiag_bsr<<<grid_for(n), 256, 0, s>>>(y, w, invdiag, n);
 }
 
-void launch_diag_dot_fine(const float* v, const float* E, const uint8_t* mask, int nx, int ny, int nz, float kd,
-                          double* partial, cudaStream_t s) {
+void launch_diag_dot_fine(const float* v, const float* E, const Level& l0, float kd, double* partial, cudaStream_t s) {
     note_launch();
-    k_diag_dot_fine<<<kVecBlocks, kVecThreads, 0, s>>>(v, E, mask, nx, ny, nz, kd, partial);
+    k_diag_dot_fine<<<kVecBlocks, kVecThreads, 0, s>>>(v, E, l0.mask, l0.nx, l0.ny, l0.nz, l0.px, kd, partial);
 }
 
 void launch_diag_dot_bsr(const float* v, const float* invdiag, long long n, double* partial, cudaStream_t s) {
@@ -1263,9 +1297,9 @@ void launch_diag_dot_bsr(const float* v, const float* invdiag, long long n, doub
     k_diag_dot_bsr<<<kVecBlocks, kVecThreads, 0, s>>>(v, invdiag, n, partial);
 }
 
-void launch_power_start(float* v, const uint8_t* mask, long long nn, cudaStream_t s) {
+void launch_power_start(float* v, const Level& l, cudaStream_t s) {
     note_launch();
-    k_power_start<<<grid_for(3 * nn), 256, 0, s>>>(v, mask, nn);
+    k_power_start<<<grid_for(3 * l.nn), 256, 0, s>>>(v, l.mask, l.nn, l.nx + 1, l.px);
 }
 
 }  // namespace gmg

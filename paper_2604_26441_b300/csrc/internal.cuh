@@ -75,7 +75,14 @@ enum FinOp { FIN_NONE = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_NRMCHK = 3 };
 struct Level {
     int nx = 0, ny = 0, nz = 0;     // element counts
     long long nn = 0;               // node count (nx+1)(ny+1)(nz+1)
-    uint8_t* mask = nullptr;        // [nn] fixed-component bits
+    // Vectors of a level are node-major, 3 floats per node, node (i, j, k) at
+    // i + px (j + (ny+1) k).  Levels >= 1: px = nx + 1 (dense).  Level 0 pads
+    // every node row to px = nx + 1 rounded up to a multiple of 4, so that each
+    // row starts on a 16-byte boundary (TMA-fed fine operator); pad nodes hold 0.
+    int px = 0;                     // nodes per row of the level's vectors
+    long long nnp = 0;              // nodes allocated per vector: px (ny+1)(nz+1)
+    uint8_t* mask = nullptr;        // [nn] fixed-component bits (dense numbering)
+    uint8_t* maskp = nullptr;       // [nnp] the same bits in the vectors' numbering (pads: 7)
     float* invdiag = nullptr;       // [3nn] D^{-1} (levels >= 1), 0 on fixed DOFs
     double* A64 = nullptr;          // [243 nn] Galerkin operator planes, FP64 (levels >= 1)
     float* A32 = nullptr;           // [126 ps] FP32 diagonal + forward blocks (levels >= 1)
@@ -224,7 +231,11 @@ struct gmg_handle {
     cudaStream_t stream = nullptr;
     gmg_options opt{};
     int device = 0;
-    float* E32 = nullptr;                       // fine moduli, FP32
+    float* E32 = nullptr;                       // fine moduli, FP32, [nz][ny][nx]
+    float* E32p = nullptr;                      // the same, rows padded: [nz][ny][ex]
+    int ex = 0;                                 // nx rounded up to a multiple of 4
+    int* free_idx_p = nullptr;                  // coarsest free DOFs in the vectors' numbering
+    bool pads_dirty = false;                    // a solve ended non-finite: re-zero level-0 vectors
     double* E64 = nullptr;                      // fine moduli, FP64
     gmg::KeF keF{};
     gmg::KeD keD{};
@@ -296,6 +307,10 @@ enum FineMode { FM_APPLY = 0, FM_SMOOTH = 1, FM_RESID = 2 };
 
 struct FineArgs {
     int nx, ny, nz;
+    int pitch;             // nodes per row of the vectors and the mask (nx + 1, or the padded
+                           // level-0 pitch, a multiple of 4)
+    int epitch;            // moduli per row of Ep (a multiple of 4)
+    const float* Ep;       // moduli in the padded layout [nz][ny][epitch] (TMA-fed kernel)
     const float* E;
     const uint8_t* mask;
     const float* xin;      // operand of K
@@ -323,6 +338,10 @@ void fine_set_plan(int nx, int ny, int nz, int tile, int zc);
 // mask_in: treat fixed DOFs of the operand as 0 (for operands that may hold
 // values there, e.g. user input); internal vectors are already 0 on them.
 void launch_fine(int mode, int dot, int mask_in, const FineArgs& a, const GHat& G, cudaStream_t s);
+// The TMA-fed fine operator on padded level-0 vectors (a.pitch and a.epitch
+// multiples of 4, a.Ep the padded moduli); GMG_OK, or an error when a tensor map
+// cannot be encoded (nothing is launched then).
+int launch_fine_tma(int mode, int dot, const FineArgs& a, const GHat& G, cudaStream_t s);
 void launch_hadamard_blocks(const double* Ke, double* g72, cudaStream_t s);
 // Tensor-core fine smoother step (SMOOTH mode): passes = 1 (BF16) or 3 (split BF16).
 void launch_fine_tc(int passes, int dot, const FineArgs& a, cudaStream_t s);
@@ -331,9 +350,11 @@ void build_tc_operand(const double g[72], uint16_t out[2048]);
 int resid64_grid_blocks(int nx, int ny, int nz);
 void launch_fine_smooth0(const FineArgs& a, cudaStream_t s);
 // inv0[n] = 1 / (kd * sum of the moduli of the elements around node n), once at set-up.
-void launch_fine_inv0(int nx, int ny, int nz, const float* E, float kd, float* inv0, cudaStream_t s);
+void launch_fine_inv0(int nx, int ny, int nz, int px, const float* E, float kd, float* inv0, cudaStream_t s);
+// r64 (optional) in the dense numbering; r32 (optional) in the level-0 vector
+// numbering of pitch px.
 void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,
-                         const double* f, const double* u, double* r64, float* r32,
+                         const double* f, const double* u, double* r64, float* r32, int px,
                          const double* sc, double* partial, const GHat64& G, cudaStream_t s);
 
 struct BsrArgs {
@@ -405,11 +426,17 @@ void launch_dot_f32(const float* a, const float* b, long long n, double* partial
 void launch_dot_f64_masked(const double* a, const double* b, const uint8_t* mask, long long nn,
                            double* partial, cudaStream_t s);
 void launch_finalize(const double* partial, int n, double* sc, int slot, int op, cudaStream_t s);
-void launch_pcg_update(double* u, float* r, const float* p, const float* q, long long n,
+// u (dense numbering, FP64) += alpha p; r -= alpha q (level-0 vectors of pitch px)
+void launch_pcg_update(double* u, float* r, const float* p, const float* q, const Level& l0,
                        const double* sc, double* partial, cudaStream_t s);
 void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s);
 void launch_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial, cudaStream_t s);
-void launch_cast_masked(const double* f, const uint8_t* mask, long long nn, float* r, cudaStream_t s);
+// r = f on free DOFs, 0 elsewhere (pads included): f dense, r a level-0 vector
+void launch_cast_masked(const double* f, const Level& l0, float* r, cudaStream_t s);
+// Level-0 vectors to and from the dense numbering a caller uses: pack writes
+// every entry of out (fixed DOFs and pads 0); unpack writes every dense entry.
+void launch_pack0(const float* in, const Level& l0, float* out, cudaStream_t s);
+void launch_unpack0(const float* in, const Level& l0, float* out, cudaStream_t s);
 // ||r||^2 into SC_RR (as launch_finalize) and the convergence test of the
 // device-resident loop: counts the iteration and sets the while-node condition
 // to 1 while ||r|| / ||f|| >= tol, the scalars are finite and the cap is not
@@ -417,15 +444,15 @@ void launch_cast_masked(const double* f, const uint8_t* mask, long long nn, floa
 void launch_finalize_check(const double* partial, int n, double* sc, cudaGraphConditionalHandle cond,
                            cudaStream_t s);
 void launch_axpy_dev(float* y, const float* x, long long n, const double* coef, float sign, cudaStream_t s);
-void launch_axpy_u64(double* u, const float* z, long long n, double a, cudaStream_t s);
+// u (dense, FP64) += a z (a level-0 vector)
+void launch_axpy_u64(double* u, const float* z, const Level& l0, double a, cudaStream_t s);
 void launch_scale_by_inv_sqrt(float* v, long long n, const double* sc, int slot, cudaStream_t s);
-void launch_scale_invdiag_fine(const float* y, float* w, const float* E, const uint8_t* mask,
-                               int nx, int ny, int nz, float kd, cudaStream_t s);
+void launch_scale_invdiag_fine(const float* y, float* w, const float* E, const Level& l0, float kd, cudaStream_t s);
 void launch_scale_invdiag_bsr(const float* y, float* w, const float* invdiag, long long n, cudaStream_t s);
-void launch_diag_dot_fine(const float* v, const float* E, const uint8_t* mask, int nx, int ny, int nz,
-                          float kd, double* partial, cudaStream_t s);
+void launch_diag_dot_fine(const float* v, const float* E, const Level& l0, float kd, double* partial, cudaStream_t s);
 void launch_diag_dot_bsr(const float* v, const float* invdiag, long long n, double* partial, cudaStream_t s);
-void launch_power_start(float* v, const uint8_t* mask, long long nn, cudaStream_t s);
+// start vector over the level's dense DOF index, written in its vector numbering
+void launch_power_start(float* v, const Level& l, cudaStream_t s);
 
 // ---- launchers implemented in setup.cu ----------------------------------------
 void launch_moduli(const float* rho, long long ne, double p, double E0, double Emin, double* E64,
@@ -435,6 +462,9 @@ void launch_mask_clamp(uint8_t* mask, int nx, int ny, int nz, cudaStream_t s);
 void launch_mask_from_dofs(const uint8_t* fixed_dofs, uint8_t* mask, long long nn, cudaStream_t s);
 void launch_mask_inject(const Level& f, Level& c, cudaStream_t s);
 void launch_count_free(const uint8_t* mask, long long nn, int* out, cudaStream_t s);
+// l0.maskp from l0.mask (pad nodes fixed); dense DOF indices -> level-0 vector numbering
+void launch_mask_pad(const Level& l0, cudaStream_t s);
+void launch_pad_index(const int* idx, int n, const Level& l0, int* out, cudaStream_t s);
 void launch_child_patterns(const double* Ke, double* Mpat, cudaStream_t s);
 void launch_coarse_element_matrices(int nx, int ny, int nz, const double* E, const uint8_t* fine_mask,
                                     const double* Ke, const double* Mpat, double* Kc, cudaStream_t s);

@@ -37,7 +37,7 @@ __device__ __forceinline__ void face_diffs(double u00, double u10, double u01, d
 
 __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,
                                                    const double* f, const double* uvec, double* r64, float* r32,
-                                                   const double* sc, double* partial, GHat64 G, int zchunk) {
+                                                   int px, const double* sc, double* partial, GHat64 G, int zchunk) {
     pdl_entry();
     __shared__ double sp[2][BY + 1][(BX + 1) * 3];
     __shared__ double sx[2][BY][BX * 3];
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const
         for (int c = 0; c < 3; ++c) {
             const double v = fixed_bit(m, c) ? 0.0 : f[3 * n + c] - (R1[c] + r0[c]);
             if (r64) r64[3 * n + c] = v;
-            if (r32) r32[3 * n + c] = (float)v;
+            if (r32) r32[3 * (ox + px * (oy + NY * pend_k)) + c] = (float)v;
             rr += v * v;
         }
     };
@@ -256,11 +256,13 @@ int resid64_grid_blocks(int nx, int ny, int nz) {
 }
 
 void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask, const double* f, const double* u,
-                         double* r64, float* r32, const double* sc, double* partial, const GHat64& G, cudaStream_t s) {
+                         double* r64, float* r32, int px, const double* sc, double* partial, const GHat64& G,
+                         cudaStream_t s) {
     int zc = 0;
     const dim3 g = resid_grid(nx, ny, nz, &zc);
     note_launch();
-    pdl_launch(k_resid64, dim3(g), dim3(dim3(BX, BY)), 0, s, nx, ny, nz, E, mask, f, u, r64, r32, sc, partial, G, zc);
+    pdl_launch(k_resid64, dim3(g), dim3(dim3(BX, BY)), 0, s, nx, ny, nz, E, mask, f, u, r64, r32, px, sc, partial, G,
+               zc);
 }
 
 }  // namespace gmg

@@ -487,6 +487,23 @@ __global__ void k_xtx(const double* X, int n, double* Ainv) {
     if (i < n && j < n) Ainv[(long long)i * n + j] = s;
 }
 
+// The level-0 mask in the vectors' numbering (rows of px nodes; pad nodes fixed).
+__global__ void k_mask_pad(const uint8_t* mask, int NX, int px, long long nnp, uint8_t* maskp) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnp; q += (long long)gridDim.x * blockDim.x) {
+        const long long row = q / px;
+        const int i = (int)(q - row * px);
+        maskp[q] = i < NX ? mask[row * NX + i] : (uint8_t)7;
+    }
+}
+
+// DOF indices in the dense numbering -> the same DOFs in the level-0 vectors' numbering.
+__global__ void k_pad_index(const int* idx, int n, int NX, int px, int* out) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const int dof = idx[q], node = dof / 3;
+        out[q] = 3 * (node + (node / NX) * (px - NX)) + dof % 3;
+    }
+}
+
 }  // namespace
 
 static int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 148 * 8)); }
@@ -516,6 +533,16 @@ void launch_mask_from_dofs(const uint8_t* fixed_dofs, uint8_t* mask, long long n
 void launch_mask_inject(const Level& f, Level& c, cudaStream_t s) {
     note_launch();
     k_mask_inject<<<grid_for(c.nn), 256, 0, s>>>(f.mask, f.nx, f.ny, c.mask, c.nx, c.ny, c.nz);
+}
+
+void launch_mask_pad(const Level& l0, cudaStream_t s) {
+    note_launch();
+    k_mask_pad<<<grid_for(l0.nnp), 256, 0, s>>>(l0.mask, l0.nx + 1, l0.px, l0.nnp, l0.maskp);
+}
+
+void launch_pad_index(const int* idx, int n, const Level& l0, int* out, cudaStream_t s) {
+    note_launch();
+    k_pad_index<<<grid_for(n), 256, 0, s>>>(idx, n, l0.nx + 1, l0.px, out);
 }
 
 void launch_count_free(const uint8_t* mask, long long nn, int* out, cudaStream_t s) {

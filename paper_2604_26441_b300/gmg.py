@@ -94,6 +94,7 @@ _SIGS = {
     "gmg_level_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "gmg_level_smooth": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
     "gmg_restrict": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "gmg_fine_pass": (ctypes.c_int, [_P, ctypes.c_int]),
     "gmg_prolong_add": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "gmg_coarse_solve": (ctypes.c_int, [_P, _P, _P]),
     "gmg_vcycle": (ctypes.c_int, [_P, _P, _P]),
@@ -392,6 +393,12 @@ class Solver:
         _check(self._lib.gmg_level_smooth(self._h, level, _ptr(b, torch.float32, n, "b"),
                                           _ptr(x, torch.float32, n, "x"), int(zero)))
         return x
+
+    def fine_pass(self, what: str = "smooth") -> None:
+        """The fine-level operator on the handle's own vectors ("apply": one
+        y = K x; "smooth": one smoothing pass), for timing the fused fine kernel
+        without repacking caller vectors (gmg_fine_pass)."""
+        _check(self._lib.gmg_fine_pass(self._h, {"apply": 0, "smooth": 1}[what]))
 
     def restrict(self, level: int, fine, coarse=None):
         import torch
