@@ -204,6 +204,18 @@ void gmg_destroy(gmg_handle* h);
  * that the next solve with the default bound succeeds. */
 int gmg_set_spin_limit(gmg_handle* h, long long polls);
 
+/* Bounds-checked build.  Compiled with -DGMG_CHECKED, the hot-path kernels
+ * check the index of each global access they compute against the size of the
+ * buffer it addresses; an index out of range records the number of its check
+ * site in a sticky device word and the access is redirected to element 0 (no
+ * trap, nothing read or written outside the buffer), and every solve then
+ * returns GMG_ERR_CUDA naming the site.  gmg_bounds_checked() is 1 in that
+ * build and 0 otherwise; gmg_bounds_site() synchronises the device and returns
+ * the first recorded site (0 = none), clearing the words (always 0 in the
+ * normal build).  This is the device-side stand-in for a memory checker. */
+int gmg_bounds_checked(void);
+unsigned gmg_bounds_site(void);
+
 /* Static text for a status code. */
 const char* gmg_status_str(int status);
 

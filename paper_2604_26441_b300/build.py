@@ -78,6 +78,22 @@ def build_library(force: bool = False, verbose: bool = False, extra: list[str] |
     return lib
 
 
+CHECKED_LIB = os.path.join(HERE, "libgmg_b300_checked.so")
+
+
+def build_checked_library(force: bool = False) -> str:
+    """The bounds-checked build (-DGMG_CHECKED): every checked global access of
+    the hot-path kernels records an out-of-range index in a sticky device word
+    instead of touching memory outside its buffer.  Rebuilt when a source is
+    newer than it."""
+    if not force and os.path.exists(CHECKED_LIB):
+        t = os.path.getmtime(CHECKED_LIB)
+        deps = sources() + glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+        if all(os.path.getmtime(d) <= t for d in deps):
+            return CHECKED_LIB
+    return build_library(force=True, extra=["-DGMG_CHECKED"], out=CHECKED_LIB)
+
+
 if __name__ == "__main__":
     print(build_library(force="--force" in sys.argv, verbose=True,
                         extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))

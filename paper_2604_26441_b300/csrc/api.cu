@@ -24,6 +24,26 @@ thread_local std::string g_err;
 namespace gmg {
 std::atomic<unsigned long long> g_kernel_launches{0};
 void set_error_text(const std::string& msg) { g_err = msg; }
+
+namespace {
+std::vector<BoundsReader>& bounds_readers() {
+    static std::vector<BoundsReader> v;  // filled during static initialisation
+    return v;
+}
+}  // namespace
+void register_bounds_reader(BoundsReader r) { bounds_readers().push_back(r); }
+// The first recorded out-of-range site of any translation unit (0: none); all
+// words are cleared.  Synchronises the device first.
+unsigned bounds_site_collect() {
+    if (bounds_readers().empty()) return 0;
+    cudaDeviceSynchronize();
+    unsigned first = 0;
+    for (BoundsReader r : bounds_readers()) {
+        const unsigned v = r();
+        if (!first) first = v;
+    }
+    return first;
+}
 }  // namespace gmg
 
 namespace {
@@ -867,6 +887,10 @@ int fgmres_solve(gmg_handle* h, const double* f, double* u, double tol, int maxi
 // gave up may have left it non-zero), so the handle's next call starts clean.
 int check_fused(gmg_handle* h) {
     TRY(sync_scalars(h));
+#ifdef GMG_CHECKED
+    if (const unsigned site = bounds_site_collect(); site != 0)
+        return fail(GMG_ERR_CUDA, "bounds-checked build: out-of-range index at check site " + std::to_string(site));
+#endif
     const int err[2] = {h->err_host[0], h->err_host[1]};
     if (!err[0] && !err[1]) return GMG_OK;
     CU(cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream));
@@ -1644,6 +1668,16 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
     CU(cudaGetLastError());
     return worst;
 }
+
+int gmg_bounds_checked(void) {
+#ifdef GMG_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+unsigned gmg_bounds_site(void) { return bounds_site_collect(); }
 
 int gmg_set_spin_limit(gmg_handle* h, long long polls) {
     if (!h) return fail(GMG_ERR_ARG, "null handle");

@@ -80,7 +80,7 @@ __device__ __forceinline__ void warp_row(const CoarseLevel& L, int n, const floa
         const int off = dx + NX * (dy + NY * dz);
         const int sx = fwd ? dx : -dx, sy = fwd ? dy : -dy, sz = fwd ? dz : -dz;
         const bool ok = i + sx >= 0 && i + sx < NX && j + sy >= 0 && j + sy < NY && k + sz >= 0 && k + sz < NZ;
-        const int m = ok ? (fwd ? n + off : n - off) : n;
+        const int m = (int)GMG_B(ok ? (fwd ? n + off : n - off) : n, L.nn, 401);
         const float wgt = ok ? 1.f : 0.f;
         const float v0 = wgt * __ldcg(x + 3 * m), v1 = wgt * __ldcg(x + 3 * m + 1), v2 = wgt * __ldcg(x + 3 * m + 2);
         const float* A = L.A + (long long)(u * 9) * N + (fwd ? n : m);

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
     };
     // output masks of owned nodes, two planes ahead in registers
     auto load_mask = [&](int kp) -> uint8_t {
-        return (owner && kp >= k0 && kp < k1) ? a.mask[onode_base + kp * NXY] : (uint8_t)7;
+        return (owner && kp >= k0 && kp < k1) ? a.mask[GMG_B(onode_base + kp * NXY, (long long)NXY * NZ, 111)] : (uint8_t)7;
     };
 
     // ---- prologue: bottom plane k0-1 (own group), then the groups of steps k0-4 .. k0-2
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
     auto finish = [&](int kp) {
         const float4 up = sx[kp & 1][ty + 1][tx];
         const float y[3] = {R1.xy.x + up.x, R1.xy.y + up.y, R1.z + up.z};
-        const int n = onode_base + kp * NXY;
+        const long long n = GMG_B(onode_base + kp * NXY, (long long)NXY * NZ, 112);
         float* out = a.out + 3 * n;
         if (MODE == FM_APPLY) {
 #pragma unroll
@@ -823,8 +823,8 @@ struct TmaTile {
     static constexpr int BOFF = EOFF + round128(EB);
     static constexpr int DOFF = BOFF + round128(OB);
     static constexpr int STAGE = DOFF + round128(OB);
-    static constexpr int SXOFF = 4 * STAGE;              // y-exchange [2][BY][BX] float4
-    static constexpr int BAROFF = SXOFF + 2 * BY * BX * 16;
+    static constexpr int SXOFF = 4 * STAGE;              // y-exchange [2][BY + 1][BX] float4 (row BY unused)
+    static constexpr int BAROFF = SXOFF + 2 * (BY + 1) * BX * 16;
     static constexpr int SMEM = BAROFF + 4 * 8;
 };
 
@@ -840,7 +840,7 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
     constexpr bool EPI_B = MODE != FM_APPLY;
     constexpr bool EPI_D = MODE == FM_SMOOTH;
     extern __shared__ __align__(128) unsigned char smem[];
-    float4(*sx)[BY][BX] = reinterpret_cast<float4(*)[BY][BX]>(smem + T::SXOFF);
+    float4(*sx)[BY + 1][BX] = reinterpret_cast<float4(*)[BY + 1][BX]>(smem + T::SXOFF);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + T::BAROFF);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
@@ -903,8 +903,9 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
             if (mbar_try_wait(&full[q], parity)) return true;
         return false;
     };
-    auto load_mask = [&](int kp) -> uint8_t {
-        return (owner && kp >= k0 && kp < k1) ? a.mask[onode + kp * NXYp] : (uint8_t)7;
+    // masks held as int (no byte packing); non-owners see every DOF fixed
+    auto load_mask = [&](int kp) -> int {
+        return (owner && kp >= k0 && kp < k1) ? (int)a.mask[GMG_B(onode + kp * NXYp, (long long)NXYp * NZ, 101)] : 7;
     };
 
     // ---- prologue: bottom plane kb into slot 3's plane region (its first phase),
@@ -930,45 +931,52 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
         for (int q = 0; q < 4; ++q) s0.T[q] = V3{make_float2(0.f, 0.f), 0.f};
         s0.E = 0.f;
     }
-    uint8_t mk0 = 7, mk1 = load_mask(k0);
+    int mk0 = 7, mk1 = load_mask(k0);
     bool pending = false;
     V3 R1{make_float2(0.f, 0.f), 0.f}, un_pend{make_float2(0.f, 0.f), 0.f};
     float eR1 = 0.f;
-    uint8_t m_pend = 7;
+    int m_pend = 7;
     DSAcc dotv;
 
-    // epilogue of the owned node of plane kp from the stage in slot q
+    // Epilogue of the owned node of plane kp from the stage in slot q.  Every
+    // thread runs it without branches (non-owners hold an all-fixed mask, so
+    // their values are zeros or discarded); only the stores are predicated.
     auto finish = [&](int kp, int q) {
         const float4 up = sx[kp & 1][ty + 1][tx];
         const float y[3] = {R1.xy.x + up.x, R1.xy.y + up.y, R1.z + up.z};
-        float* out = a.out + 3 * (onode + kp * NXYp);
+        const long long on = owner ? GMG_B(onode + kp * NXYp, (long long)NXYp * NZ, 102) : 0;
+        float* out = a.out + 3 * on;
         if (MODE == FM_APPLY) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float v = fixed_bit(m_pend, c) ? 0.f : y[c];
-                out[c] = v;
-                if (DOT) dotv.add_prod(comp(un_pend, c), v);
+                const bool fr = !fixed_bit(m_pend, c);
+                const float v = fr ? y[c] : 0.f;
+                if (owner) out[c] = v;
+                if (DOT) dotv.add_prod(fr ? comp(un_pend, c) : 0.f, v);
             }
         } else {
             const float* bb = reinterpret_cast<const float*>(smem + q * T::STAGE + T::BOFF) + rb;
             if (MODE == FM_RESID) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) out[c] = fixed_bit(m_pend, c) ? 0.f : bb[c] - y[c];
+                for (int c = 0; c < 3; ++c) {
+                    const float v = fixed_bit(m_pend, c) ? 0.f : bb[c] - y[c];
+                    if (owner) out[c] = v;
+                }
             } else {
                 const float* dd = reinterpret_cast<const float*>(smem + q * T::STAGE + T::DOFF) + rb;
                 const float inv = __frcp_rn(a.kd * (eR1 + up.w));
-                float* dn_out = a.dnew ? a.dnew + 3 * (onode + kp * NXYp) : nullptr;
+                float* dn_out = a.dnew + 3 * on;
+                const bool wd = owner && a.dnew != nullptr;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    float xn = 0.f, dn = 0.f;
-                    if (!fixed_bit(m_pend, c)) {
-                        dn = ca * inv * (bb[c] - y[c]);
-                        if (need_d) dn = fmaf(cd, dd[c], dn);
-                        xn = comp(un_pend, c) + dn;
-                        if (DOT) dotv.add_prod(bb[c], xn);
-                    }
-                    out[c] = xn;
-                    if (dn_out) dn_out[c] = dn;
+                    const bool fr = !fixed_bit(m_pend, c);
+                    float dn = ca * inv * (bb[c] - y[c]);
+                    if (need_d) dn = fmaf(cd, dd[c], dn);
+                    dn = fr ? dn : 0.f;
+                    const float xn = fr ? comp(un_pend, c) + dn : 0.f;
+                    if (DOT) dotv.add_prod(fr ? bb[c] : 0.f, xn);
+                    if (owner) out[c] = xn;
+                    if (wd) dn_out[c] = dn;
                 }
             }
         }
@@ -981,9 +989,9 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
         if (!wait_full(Q, par ^ (Q == 3 ? 1u : 0u))) failed = true;
         if (__syncthreads_or(failed)) return false;
         if (tid == 0 && s + 3 <= k1) issue(s + 3);
-        if (pending && owner) finish(s - 1, Q);
+        if (pending) finish(s - 1, Q);
         pending = false;
-        const uint8_t mcur = mk0;
+        const int mcur = mk0;
         mk0 = mk1;
         mk1 = load_mask(s + 2);
         {
@@ -1074,7 +1082,7 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
         const unsigned pq = (unsigned)(((k1 - kb) >> 2) & 1) ^ (q == 3 ? 1u : 0u);
         if (EPI_B && !wait_full(q, pq)) failed = true;
         ok = !__syncthreads_or(failed);
-        if (ok && pending && owner) finish(k1 - 1, q);
+        if (ok && pending) finish(k1 - 1, q);
     }
     if (!ok) {
         // a wait gave up: let the copies already issued land (bounded) before

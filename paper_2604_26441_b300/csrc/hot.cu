@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
             const int dx = sl % 3 - 1, dy = (sl / 3) % 3 - 1, dz = sl / 9 - 1;
             const int off = dx + NX * (dy + NY * dz);
             const bool okf = i + dx >= 0 && i + dx < NX && j + dy >= 0 && j + dy < NY && k + dz < NZ;
-            const int mf = okf ? n + off : n;
+            const int mf = (int)GMG_B(okf ? n + off : n, nn, 201);
             // operator and iterate through the read-only data path
             const float* A = a.A + (long long)(u * 9) * N + n;
             const float v0 = __ldg(a.xin + 3 * mf), v1 = __ldg(a.xin + 3 * mf + 1), v2 = __ldg(a.xin + 3 * mf + 2);
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(NTB) k_bsr(BsrArgs a) {
             y2 = fmaf(__ldg(A + 6 * N), v0, fmaf(__ldg(A + 7 * N), v1, fmaf(__ldg(A + 8 * N), v2, y2)));
             if (u > 0) {
                 const bool okb = i - dx >= 0 && i - dx < NX && j - dy >= 0 && j - dy < NY && k - dz >= 0;
-                const int mb = okb ? n - off : n;
+                const int mb = (int)GMG_B(okb ? n - off : n, nn, 202);
                 const float wgt = okb ? 1.f : 0.f;
                 const float* B = a.A + (long long)(u * 9) * N + mb;
                 const float w0 = wgt * __ldg(a.xin + 3 * mb), w1 = wgt * __ldg(a.xin + 3 * mb + 1),
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(256) k_bsr_ks(BsrArgs a) {
             const int off = dx + NX * (dy + NY * dz);
             const int sx = fwd ? dx : -dx, sy = fwd ? dy : -dy, sz = fwd ? dz : -dz;
             const bool ok = live && i + sx >= 0 && i + sx < NX && j + sy >= 0 && j + sy < NY && k + sz >= 0 && k + sz < NZ;
-            const int m = ok ? (fwd ? nsafe + off : nsafe - off) : nsafe;
+            const int m = (int)GMG_B(ok ? (fwd ? nsafe + off : nsafe - off) : nsafe, nn, 203);
             const float wgt = ok ? 1.f : 0.f;
             // operator and iterate through the read-only data path
             const float v0 = wgt * __ldg(a.xin + 3 * m), v1 = wgt * __ldg(a.xin + 3 * m + 1),
@@ -536,7 +536,7 @@ __device__ __forceinline__ void restrict_node(int n, int fnx, int fny, int fnz, 
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const float w = wx[a] * wy[b] * wz[c];
-                const int f = ix[a] + FX * (iy[b] + FY * iz[c]);
+                const int f = (int)GMG_B(ix[a] + FX * (iy[b] + FY * iz[c]), (long long)FX * FY * (fnz + 1), 211);
                 s0 = fmaf(w, fine[3 * f], s0);
                 s1 = fmaf(w, fine[3 * f + 1], s1);
                 s2 = fmaf(w, fine[3 * f + 2], s2);
@@ -602,13 +602,13 @@ __global__ void k_prolong_add(int fnx, int fny, int fnz, int fpx, int cnx, int c
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
                 const float w = wx[a] * wy[b] * wz[c];
-                const int m = ix[a] + CX * (iy[b] + CY * iz[c]);
+                const int m = (int)GMG_B(ix[a] + CX * (iy[b] + CY * iz[c]), (long long)CX * CY * (fnz / 2 + 1), 212);
                 s0 = fmaf(w, coarse[3 * m], s0);
                 s1 = fmaf(w, coarse[3 * m + 1], s1);
                 s2 = fmaf(w, coarse[3 * m + 2], s2);
             }
     const uint8_t msk = fmask[n];
-    const int np = i + fpx * (j + FY * k);  // the node in the fine vectors' numbering
+    const int np = (int)GMG_B(i + fpx * (j + FY * k), (long long)fpx * FY * (fnz + 1), 213);  // fine vector numbering
     if (!fixed_bit(msk, 0)) fine[3 * np] += s0;
     if (!fixed_bit(msk, 1)) fine[3 * np + 1] += s1;
     if (!fixed_bit(msk, 2)) fine[3 * np + 2] += s2;
@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int nL, const int* free_id
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < 3 * n_nodes; j += gridDim.x * blockDim.x)
         if (fixed_bit(mask[j / 3], j % 3)) x[j] = 0.f;
     extern __shared__ double bs[];
-    for (int j = threadIdx.x; j < nL; j += blockDim.x) bs[j] = (double)b[free_idx[j]];
+    for (int j = threadIdx.x; j < nL; j += blockDim.x) bs[j] = (double)b[GMG_B(free_idx[j], 3LL * n_nodes, 231)];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * kCoarseRowsPerBlock + warp;
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int nL, const int* free_id
     double s = s0 + s1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) x[free_idx[row]] = (float)s;
+    if (lane == 0) x[GMG_B(free_idx[row], 3LL * n_nodes, 232)] = (float)s;
 }
 
 // ---------------------------------------------------------------------------
@@ -699,17 +699,18 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(double* u, float* r,
     const int rowp = 3 * px, rowd = 3 * NX;
     DSAcc acc;
     const long long stride = (long long)gridDim.x * kVecThreads;
+    const unsigned rowq = (unsigned)rowp / 4u;  // float4 groups per padded row (3 px is a multiple of 4)
     for (long long i = blockIdx.x * (long long)kVecThreads + threadIdx.x; i < n4; i += stride) {
-        const long long e = 4 * i;
-        const long long row = e / rowp;
-        const int c0 = (int)(e - row * rowp);
+        const unsigned row32 = (unsigned)i / rowq;  // 32-bit division: 3 nnp < 2^31
+        const long long row = row32;
+        const int c0 = 4 * (int)((unsigned)i - row32 * rowq);
         if (c0 >= rowd) continue;  // four pad entries
         const float4 pv = reinterpret_cast<const float4*>(p)[i];
         const float4 qv = reinterpret_cast<const float4*>(q)[i];
         float4 rv = reinterpret_cast<float4*>(r)[i];
         const float pa[4] = {pv.x, pv.y, pv.z, pv.w}, qa[4] = {qv.x, qv.y, qv.z, qv.w};
         float ra[4] = {rv.x, rv.y, rv.z, rv.w};
-        double* ud = u + row * rowd + c0;
+        double* ud = u + GMG_B(row * rowd + c0, n4 * 4 / rowp * rowd, 221);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             if (c0 + t >= rowd) break;
@@ -773,7 +774,7 @@ __global__ void k_axpy_u64(double* u, const float* z, int NX, int px, long long 
     const int rowd = 3 * NX, rowp = 3 * px;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const long long row = i / rowd;
-        u[i] = fma(a, (double)z[i + row * (rowp - rowd)], u[i]);
+        u[i] = fma(a, (double)z[GMG_B(i + row * (rowp - rowd), n / rowd * rowp, 225)], u[i]);
     }
 }
 
@@ -803,7 +804,8 @@ __global__ void __launch_bounds__(kVecThreads) k_cast_masked(const double* f, co
     for (long long q = blockIdx.x * (long long)kVecThreads + threadIdx.x; q < 3 * nnp; q += (long long)gridDim.x * kVecThreads) {
         const long long row = q / rowp;
         const int c = (int)(q - row * rowp);
-        r[q] = (c >= rowd || fixed_bit(maskp[q / 3], c % 3)) ? 0.f : (float)f[row * rowd + c];
+        r[q] = (c >= rowd || fixed_bit(maskp[q / 3], c % 3)) ? 0.f
+                                                             : (float)f[GMG_B(row * rowd + c, nnp / px * rowd, 222)];
     }
 }
 
@@ -814,7 +816,7 @@ __global__ void k_pack0(const float* in, const uint8_t* maskp, int NX, int px, l
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 3 * nnp; q += (long long)gridDim.x * blockDim.x) {
         const long long row = q / rowp;
         const int c = (int)(q - row * rowp);
-        out[q] = (c >= rowd || fixed_bit(maskp[q / 3], c % 3)) ? 0.f : in[row * rowd + c];
+        out[q] = (c >= rowd || fixed_bit(maskp[q / 3], c % 3)) ? 0.f : in[GMG_B(row * rowd + c, nnp / px * rowd, 223)];
     }
 }
 
@@ -824,7 +826,7 @@ __global__ void k_unpack0(const float* in, int NX, int px, long long n, float* o
     const int rowd = 3 * NX, rowp = 3 * px;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const long long row = q / rowd;
-        out[q] = in[q + row * (rowp - rowd)];
+        out[q] = in[GMG_B(q + row * (rowp - rowd), n / rowd * rowp, 224)];
     }
 }
 

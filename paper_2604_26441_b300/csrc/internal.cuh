@@ -24,6 +24,43 @@ inline void note_launch(unsigned long long n = 1) { g_kernel_launches.fetch_add(
 // Records the text gmg_last_error() returns on the calling thread.
 void set_error_text(const std::string& msg);
 
+// ---- bounds-checked build (compiled with -DGMG_CHECKED) ----------------------
+// GMG_B(i, n, site) is the index i of a global access into a buffer of n
+// elements.  In the checked build an index outside [0, n) records `site` in
+// the translation unit's sticky word (the first site wins) and is replaced by
+// 0, so the access stays inside the buffer: nothing traps and nothing is read
+// or written out of range.  The host collects the words with
+// bounds_site_collect() (gmg_bounds_site, and every solve's final check).  In
+// the normal build GMG_B(i, n, site) is just i.
+using BoundsReader = unsigned (*)();
+void register_bounds_reader(BoundsReader r);
+unsigned bounds_site_collect();
+#ifdef GMG_CHECKED
+static __device__ unsigned g_bounds_site = 0u;
+__device__ __forceinline__ long long bounds_index(long long i, long long n, unsigned site) {
+    if (i < 0 || i >= n) {
+        atomicCAS(&g_bounds_site, 0u, site);
+        return 0;
+    }
+    return i;
+}
+#define GMG_B(i, n, site) ::gmg::bounds_index((long long)(i), (long long)(n), (site))
+namespace {
+struct BoundsReg {
+    static unsigned read_and_clear() {
+        unsigned v = 0, z = 0;
+        if (cudaMemcpyFromSymbol(&v, g_bounds_site, sizeof v) != cudaSuccess) { cudaGetLastError(); return 0; }
+        if (v) cudaMemcpyToSymbol(g_bounds_site, &z, sizeof z);
+        return v;
+    }
+    BoundsReg() { register_bounds_reader(&read_and_clear); }
+};
+static BoundsReg g_bounds_reg;
+}  // namespace
+#else
+#define GMG_B(i, n, site) (i)
+#endif
+
 constexpr int kMaxLevels = 16;
 constexpr int kMaxDegree = 16;
 constexpr int kSlots = 27;     // 27-point neighbourhood of a node

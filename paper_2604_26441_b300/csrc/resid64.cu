@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const
         for (int c = 0; c < 3; ++c) {
             const double v = fixed_bit(m, c) ? 0.0 : f[3 * n + c] - (R1[c] + r0[c]);
             if (r64) r64[3 * n + c] = v;
-            if (r32) r32[3 * (ox + px * (oy + NY * pend_k)) + c] = (float)v;
+            if (r32) r32[GMG_B(3 * (ox + px * (oy + NY * pend_k)) + c, 3LL * px * NY * NZ, 301)] = (float)v;
             rr += v * v;
         }
     };

@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgmg_b300.so")
+# GMG_LIBRARY may name another build of the same library (e.g. the
+# bounds-checked libgmg_b300_checked.so built with -DGMG_CHECKED)
+LIB_PATH = os.environ.get("GMG_LIBRARY") or os.path.join(HERE, "libgmg_b300.so")
 
 GMG_OK, GMG_NOT_CONVERGED, GMG_NONFINITE = 0, 1, 2
 GMG_TIMEOUT = -7
@@ -83,6 +85,8 @@ _SIGS = {
     "gmg_destroy": (None, [_P]),
     "gmg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "gmg_set_spin_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
+    "gmg_bounds_checked": (ctypes.c_int, []),
+    "gmg_bounds_site": (ctypes.c_uint, []),
     "gmg_last_error": (ctypes.c_char_p, []),
     "gmg_kernel_launches": (ctypes.c_ulonglong, []),
     "gmg_num_levels": (ctypes.c_int, [_P]),
