@@ -14,7 +14,9 @@ Paper passages followed:
   diag(K^l), power iteration on D^{-1} K^l (20 fine / 10 coarse iterations,
   floor 1e-6);
 * Sec. "Matrix-Free V-Cycle" and the reported safeguards -- coarsest level by
-  dense Cholesky of K^L + eps I, eps = max(mean_diag * 1e-8, 1e-14).
+  dense Cholesky of K^L + eps I, eps = max(mean_diag * 1e-8, 1e-14), when it
+  has at most the dense-Cholesky cutoff (5000) free DOFs; above the cutoff a
+  fixed-count PCG (80 steps, the reproducibility defaults table) instead.
 
 Readings where the paper is silent:
 
@@ -24,7 +26,10 @@ Readings where the paper is silent:
   over the level's full DOF index i, restricted to free DOFs, is normalised in
   the 2-norm every step, and returns the D-Rayleigh quotient v^T K v / v^T D v;
 * automatic depth coarsens while the coarsest free-DOF count exceeds the
-  Cholesky cutoff and every element count is at least 2.
+  Cholesky cutoff and every element count is at least 2;
+* the fixed-count coarsest PCG is preconditioned by the level's diagonal
+  (Jacobi), starts from 0, takes exactly the configured number of steps, and
+  stops early only when r.z becomes exactly 0 (the solution is then exact).
 """
 
 from __future__ import annotations
@@ -187,6 +192,37 @@ def coarse_solve(L: np.ndarray, r: np.ndarray) -> np.ndarray:
     return sla.solve_triangular(L.T, y, lower=False, check_finite=False)
 
 
+def coarse_pcg(apply_K: Callable, diag: np.ndarray, b: np.ndarray, steps: int) -> np.ndarray:
+    """Fixed-count Jacobi-preconditioned CG from x = 0 (the coarsest solve above
+    the dense-Cholesky cutoff): `steps` updates x += alpha p, r -= alpha q, each
+    followed by z = D^{-1} r, beta = r.z / r_old.z_old, p = z + beta p."""
+    x = np.zeros_like(b)
+    r = np.array(b, dtype=np.float64)
+    z = r / diag
+    p = z.copy()
+    rz = float(r @ z)
+    for _ in range(steps):
+        if rz == 0.0:
+            break
+        q = apply_K(p)
+        alpha = rz / float(p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        z = r / diag
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x
+
+
+def coarsest_solve(lev, r: np.ndarray) -> np.ndarray:
+    """The coarsest-level solve of Eq. vcycle: Cholesky when the level has a
+    factor, else the fixed-count PCG."""
+    if lev.L is not None:
+        return coarse_solve(lev.L, r)
+    return coarse_pcg(lev.apply, lev.diag, r, lev.coarse_steps)
+
+
 @dataclasses.dataclass
 class Level:
     dims: tuple
@@ -197,8 +233,9 @@ class Level:
     diag: np.ndarray            # diag(K_ff)
     lam: float = 0.0            # lambda_max(D^{-1} K)
     P: sp.csr_matrix | None = None   # free_f x free_c transfer to the next level
-    L: np.ndarray | None = None      # Cholesky factor (coarsest only)
+    L: np.ndarray | None = None      # Cholesky factor (coarsest only, at most chol_cutoff free DOFs)
     eps: float = 0.0
+    coarse_steps: int = 0            # fixed-count PCG steps (coarsest only, above the cutoff)
 
     @property
     def n_free(self) -> int:
@@ -219,9 +256,10 @@ def auto_levels(dims, fixed0: np.ndarray, chol_cutoff: int = 5000) -> int:
 def build_hierarchy(dims, E: np.ndarray, fixed0: np.ndarray, nu: float = 0.3,
                     levels: int = 0, chol_cutoff: int = 5000, power_fine: int = 20,
                     power_coarse: int = 10, matrix_free_fine: bool = False,
-                    Ke: np.ndarray | None = None) -> list[Level]:
+                    Ke: np.ndarray | None = None, coarse_pcg_steps: int = 80) -> list[Level]:
     """All levels: fine K (assembled, or matrix-free), Galerkin coarse operators,
-    diagonals, lambda_max estimates and the coarsest Cholesky factor."""
+    diagonals, lambda_max estimates and the coarsest solve: the Cholesky factor
+    up to chol_cutoff free DOFs, else coarse_pcg_steps of Jacobi-PCG."""
     from .fem import element_stiffness
 
     if Ke is None:
@@ -265,6 +303,9 @@ def build_hierarchy(dims, E: np.ndarray, fixed0: np.ndarray, nu: float = 0.3,
         v0 = power_start_vector(3 * Grid(*lev.dims).n_nodes, lev.free)
         lev.lam = lambda_max(lev.apply, lev.diag, v0, power_fine if li == 0 else power_coarse)
     last = H[-1]
+    if last.n_free > chol_cutoff:
+        last.coarse_steps = int(coarse_pcg_steps)
+        return H
     dense = last.K.toarray() if last.K is not None else np.column_stack(
         [last.apply(e) for e in np.eye(last.n_free)])
     last.L, last.eps = coarse_factor(dense)

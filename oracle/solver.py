@@ -12,7 +12,8 @@ Paper passages followed:
   fine smoother degree 2, two coarse-level smoothing steps, omega capped at 0.5
   on coarse levels;
 * Sec. "Matrix-Free V-Cycle", Eq. vcycle -- pre-smooth from zero, residual,
-  restrict, recurse, prolong-add, post-smooth; coarsest level solved exactly;
+  restrict, recurse, prolong-add, post-smooth; coarsest level solved by dense
+  Cholesky, or by a fixed-count PCG above the dense-Cholesky cutoff;
 * Sec. "Outer Krylov Solver and Convergence Statement" -- left-preconditioned
   CG with the frozen V-cycle, ||r_k|| / ||b|| < tol accepted only by the true
   residual; iteration caps and non-finite iterates are failures; restarted
@@ -45,7 +46,7 @@ import dataclasses
 
 import numpy as np
 
-from .hierarchy import Level, coarse_solve
+from .hierarchy import Level, coarsest_solve
 
 OK, NOT_CONVERGED, NONFINITE = 0, 1, 2
 
@@ -114,7 +115,7 @@ def vcycle(H: list[Level], r: np.ndarray, spec: SmootherSpec, l: int = 0) -> np.
     """Eq. vcycle on the free-DOF vector r of level l."""
     lev = H[l]
     if l == len(H) - 1:
-        return coarse_solve(lev.L, r)
+        return coarsest_solve(lev, r)
     x = smooth(lev, r, np.zeros_like(r), spec, l)
     t = r - lev.apply(x)
     e = vcycle(H, lev.P.T @ t, spec, l + 1)
@@ -130,7 +131,7 @@ def mgcycle(H: list[Level], b: np.ndarray, spec: SmootherSpec, l: int = 0, gamma
     post-smooth; the coarsest level is solved exactly."""
     lev = H[l]
     if l == len(H) - 1:
-        return coarse_solve(lev.L, b)
+        return coarsest_solve(lev, b)
     x = smooth(lev, b, np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64), spec, l)
     t = b - lev.apply(x)
     bc = lev.P.T @ t

@@ -209,3 +209,72 @@ def test_auto_levels():
         d = hy.coarse_dims(d)
         counts.append(int((f == 0).sum()))
     assert counts[-1] <= 5000 and counts[-2] > 5000
+
+
+# ---------------------------------------------------------------------------
+# coarsest solve above the dense-Cholesky cutoff: fixed-count Jacobi-PCG
+# (Sec. "Matrix-Free V-Cycle"; the reproducibility defaults: 80 PCG steps)
+# ---------------------------------------------------------------------------
+def _small_level_operator():
+    dims = (6, 3, 3)
+    fixed = inputs.clamp_xmin_mask(*dims)
+    rho = inputs.filtered_random_density(*dims, 5)
+    g = fem.Grid(*dims)
+    K = fem.assemble(g, fem.moduli(rho, 3.0), fem.element_stiffness(0.3))
+    free = fem.free_dofs(fixed)
+    return K[free][:, free].tocsr()
+
+
+def test_coarse_pcg_matches_scipy_cg_iterates():
+    """k steps of the oracle's fixed-count PCG equal scipy's preconditioned CG
+    after k iterations (an independent implementation of the same Krylov
+    iterate), for k below the system size; a wrong preconditioner (D instead of
+    D^-1) or a wrong beta would break this."""
+    import scipy.sparse.linalg as spla
+    A = _small_level_operator()
+    d = A.diagonal()
+    b = np.random.default_rng(3).standard_normal(A.shape[0])
+    M = spla.LinearOperator(A.shape, matvec=lambda v: v / d)
+    for k in (1, 3, 10, 25):
+        x = hy.coarse_pcg(A.dot, d, b, k)
+        xs, _ = spla.cg(A, b, x0=np.zeros_like(b), rtol=0.0, atol=0.0, maxiter=k, M=M)
+        assert np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs), k
+
+
+def test_coarse_pcg_with_enough_steps_is_the_exact_solve():
+    """CG terminates in at most n steps: with steps >= n the fixed-count PCG
+    reproduces the dense solution (rounding aside); its residual also falls
+    monotonically in the energy norm as steps grow."""
+    A = _small_level_operator()
+    n = A.shape[0]
+    d = A.diagonal()
+    b = np.random.default_rng(4).standard_normal(n)
+    x_exact = np.linalg.solve(A.toarray(), b)
+    x = hy.coarse_pcg(A.dot, d, b, 3 * n)
+    assert np.linalg.norm(x - x_exact) <= 1e-8 * np.linalg.norm(x_exact)
+    errs = [float((xe := hy.coarse_pcg(A.dot, d, b, k) - x_exact) @ (A @ xe)) for k in (2, 8, 32)]
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_hierarchy_above_cutoff_uses_fixed_count_pcg():
+    """A coarsest level with more free DOFs than the cutoff gets no Cholesky
+    factor but the fixed-count PCG (80 steps by default); with a step count at
+    least its size, the V-cycle equals the one with an exact coarsest solve (a
+    Cholesky factor of K^L without the eps regularisation)."""
+    from oracle import solver as so
+    dims = (8, 4, 4)
+    fixed = inputs.clamp_xmin_mask(*dims)
+    E = fem.moduli(inputs.uniform_density(*dims), 3.0)
+    H_chol = hy.build_hierarchy(dims, E, fixed, levels=2)
+    H_chol[-1].L = np.linalg.cholesky(H_chol[-1].K.toarray())
+    n_c = H_chol[-1].n_free
+    H_pcg = hy.build_hierarchy(dims, E, fixed, levels=2, chol_cutoff=n_c - 1)
+    assert H_pcg[-1].L is None and H_pcg[-1].coarse_steps == 80
+    H_big = hy.build_hierarchy(dims, E, fixed, levels=2, chol_cutoff=n_c - 1, coarse_pcg_steps=3 * n_c)
+    spec = so.SmootherSpec("jacobi", 2, 0.5)
+    r = inputs.random_free_vector(fixed, seed=9)[H_chol[0].free]
+    z_chol = so.vcycle(H_chol, r, spec)
+    z_big = so.vcycle(H_big, r, spec)
+    assert np.linalg.norm(z_big - z_chol) <= 1e-9 * np.linalg.norm(z_chol)
+    z_80 = so.vcycle(H_pcg, r, spec)
+    assert np.all(np.isfinite(z_80)) and np.linalg.norm(z_80 - z_chol) > 0.0
