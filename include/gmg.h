@@ -147,6 +147,13 @@ typedef struct {
     long long spin_limit;        /* polls (each followed by a ~64 ns sleep) that a block of the fused
                                     lower V-cycle makes at a grid barrier before it gives up and the
                                     call returns GMG_TIMEOUT; default 2^24 (about a second); >= 0 */
+    int coarse_pcg_steps;        /* when the coarsest level has more free DOFs than chol_cutoff (the
+                                    hierarchy was not coarsened enough, e.g. a fixed `levels`), it is
+                                    solved by this many Jacobi-preconditioned CG steps from 0 instead
+                                    of dense Cholesky (Sec. "Matrix-Free V-Cycle"; 80 in the paper's
+                                    defaults).  The V-cycle is then a fixed nonlinear operator: pair
+                                    it with GMG_OUTER_FGMRES when PCG stalls.  A single-level
+                                    hierarchy above the cutoff is refused (GMG_ERR_ARG). */
 } gmg_options;
 
 typedef struct {
@@ -163,7 +170,7 @@ typedef struct {
 /* Fills *opt with the paper's defaults: 4 levels, Chebyshev degree 2 on the
  * fine level, 2 Jacobi steps with omega 0.5 on the coarse levels, alpha = 1/30,
  * lambda_safety 1.1, 20/10 power iterations, Cholesky cutoff 5000, NULL stream,
- * spin_limit 2^24. */
+ * spin_limit 2^24, 80 coarsest PCG steps. */
 void gmg_default_options(gmg_options* opt);
 
 /* Builds the hierarchy for one frozen density field (Eq. simp_filter, Eq.
@@ -204,9 +211,10 @@ void gmg_destroy(gmg_handle* h);
  * that the next solve with the default bound succeeds. */
 int gmg_set_spin_limit(gmg_handle* h, long long polls);
 
-/* Bounds-checked build.  Compiled with -DGMG_CHECKED, the hot-path kernels
- * check the index of each global access they compute against the size of the
- * buffer it addresses; an index out of range records the number of its check
+/* Bounds-checked build.  Compiled with -DGMG_CHECKED, the kernels of the solve
+ * path check the indices they compute (neighbour, transfer, mask,
+ * coarsest-solve and layout-conversion accesses) against the size of the
+ * buffer addressed; an index out of range records the number of its check
  * site in a sticky device word and the access is redirected to element 0 (no
  * trap, nothing read or written outside the buffer), and every solve then
  * returns GMG_ERR_CUDA naming the site.  gmg_bounds_checked() is 1 in that
@@ -282,7 +290,8 @@ int gmg_restrict(gmg_handle* h, int level, const float* fine_dev, float* coarse_
 /* fine += P^level coarse (fine fixed DOFs untouched). */
 int gmg_prolong_add(gmg_handle* h, int level, const float* coarse_dev, float* fine_dev);
 
-/* x = (K^L_ff + eps I)^-1 b on the coarsest level (FP64 Cholesky factor). */
+/* x = (K^L_ff + eps I)^-1 b on the coarsest level (FP64 Cholesky factor), or,
+ * above the dense-Cholesky cutoff, coarse_pcg_steps Jacobi-PCG steps from 0. */
 int gmg_coarse_solve(gmg_handle* h, const float* b_dev, float* x_dev);
 
 /* Lanczos probe of the effective condition number of the preconditioned

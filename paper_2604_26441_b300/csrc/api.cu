@@ -110,6 +110,18 @@ BsrArgs bsr_args(gmg_handle* h, int li) {
     return a;
 }
 
+// The device view of assembled level li used by the cooperative and
+// single-block kernels (coarse_fused.cu).
+CoarseLevel coarse_view(const gmg_handle* h, int li) {
+    const Level& l = h->lev[li];
+    CoarseLevel c{};
+    c.nx = l.nx; c.ny = l.ny; c.nz = l.nz; c.nn = (int)l.nn;
+    c.mask = l.mask; c.A = l.A32; c.ps = (int)l.ps; c.invdiag = l.invdiag;
+    c.x = l.x; c.x2 = l.x2; c.b = l.b; c.t = l.t; c.d = l.d;
+    c.coef = l.coef; c.kind = l.kind; c.degree = l.degree;
+    return c;
+}
+
 int partial_count(gmg_handle* h, int li, int kind) {
     // kind 0: operator-kernel partials, 1: vector-kernel partials
     if (kind == 1) return vec_grid_blocks();
@@ -209,7 +221,8 @@ void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int
         return;
     }
     if (li == h->L - 1) {
-        launch_coarse_solve(h->nL, h->free_idx_p, h->Ainv, b, X, l.maskp, l.nnp, s);
+        if (h->coarse_pcg) launch_coarse_pcg(coarse_view(h, li), b, X, l.t, l.d, l.x2, h->opt.coarse_pcg_steps, s);
+        else launch_coarse_solve(h->nL, h->free_idx_p, h->Ainv, b, X, l.maskp, l.nnp, s);
         return;
     }
     int writes = 0;
@@ -490,10 +503,15 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     launch_free_index(cl.mask, cl.nn, h->free_idx, cnt, s);
     CU(cudaMemcpyAsync(&h->nL, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    if (h->nL > 0) {
-        if (h->nL > o.chol_cutoff)
-            return fail(GMG_ERR_ARG, "coarsest level has " + std::to_string(h->nL) +
-                                         " free DOFs, more than the dense-Cholesky cutoff");
+    if (h->nL > o.chol_cutoff) {
+        // above the cutoff the coarsest level is solved by a fixed-count PCG on
+        // its assembled operator (the fine level has none: one level is refused)
+        if (L == 1)
+            return fail(GMG_ERR_ARG, "a single-level hierarchy with " + std::to_string(h->nL) +
+                                         " free DOFs exceeds the dense-Cholesky cutoff; use more levels");
+        h->coarse_pcg = true;
+    }
+    if (h->nL > 0 && !h->coarse_pcg) {
         const int n = h->nL;
         double *dense = nullptr, *work = nullptr, *eps_dev = nullptr;
         int* info = nullptr;
@@ -545,7 +563,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         }
     }
     // ---- fused lower V-cycle: every assembled level below the node threshold
-    if (o.fused_coarse_nodes > 0 && L >= 2 && o.cycle_index <= 1) {
+    if (o.fused_coarse_nodes > 0 && L >= 2 && o.cycle_index <= 1 && !h->coarse_pcg) {
         int start = L - 1;
         while (start - 1 >= 1 && h->lev[start - 1].nn < o.fused_coarse_nodes) --start;
         if (h->lev[start].nn < o.fused_coarse_nodes || start == L - 1) {
@@ -936,6 +954,7 @@ void gmg_default_options(gmg_options* o) {
     o->bsr_kernel = -1;
     o->stream = nullptr;
     o->spin_limit = 1LL << 24;
+    o->coarse_pcg_steps = 80;
 }
 
 const char* gmg_status_str(int st) {
@@ -1003,6 +1022,8 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
     if (o.power_iters_fine < 1 || o.power_iters_coarse < 1 || o.chol_cutoff < 1)
         return fail(GMG_ERR_ARG, "bad iteration counts or cutoff");
     if (o.spin_limit < 0) return fail(GMG_ERR_ARG, "spin_limit must be >= 0");
+    if (o.coarse_pcg_steps < 1 || o.coarse_pcg_steps > 100000)
+        return fail(GMG_ERR_ARG, "coarse_pcg_steps must be in [1, 100000]");
 
     int dev = 0;
     cudaDeviceProp prop;
@@ -1828,7 +1849,9 @@ int gmg_coarse_solve(gmg_handle* h, const float* b, float* x) {
         CU(cudaGetLastError());
         return GMG_OK;
     }
-    launch_coarse_solve(h->nL, h->free_idx, h->Ainv, b, x, l.mask, l.nn, h->stream);
+    if (h->coarse_pcg) launch_coarse_pcg(coarse_view(h, h->L - 1), b, x, l.t, l.d, l.x2, h->opt.coarse_pcg_steps,
+                                         h->stream);
+    else launch_coarse_solve(h->nL, h->free_idx, h->Ainv, b, x, l.mask, l.nn, h->stream);
     CU(cudaGetLastError());
     return GMG_OK;
 }

@@ -284,6 +284,83 @@ __global__ void __launch_bounds__(kThreads) k_coarse_vcycle(CoarseFused a) {
 #undef BARRIER
 }
 
+// ---------------------------------------------------------------------------
+// Coarsest level above the dense-Cholesky cutoff: a fixed-count PCG
+// (Sec. "Matrix-Free V-Cycle": Cholesky if n_L <= cutoff, else PCG; 80 steps in
+// the reproducibility defaults) preconditioned by the level's diagonal, from
+// x = 0.  Each step: q = K p (one warp per node, warp_row), alpha = rz / p.q,
+// x += alpha p, r -= alpha q, z = D^-1 r, beta = r.z / rz, p = z + beta p; it
+// stops early only when r.z is exactly 0.  One block of 1024 threads does all
+// steps, so the phases are separated by __syncthreads alone (no grid-wide
+// wait); vectors FP32, dot products accumulated in FP64.
+// ---------------------------------------------------------------------------
+constexpr int kCpThreads = 1024;
+
+// Sum over the block of one FP64 value per thread; every thread gets the sum.
+__device__ double cp_block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();  // sh may still be read from the previous sum
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double t = lane < kCpThreads / 32 ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[32] = t;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+__global__ void __launch_bounds__(kCpThreads, 1) k_coarse_pcg(CoarseLevel L, const float* b, float* x, float* r,
+                                                               float* p, float* q, int steps) {
+    __shared__ double sh[33];
+    pdl_entry();
+    const long long n3 = 3LL * L.nn;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double rz_part = 0.0;
+    for (long long i = threadIdx.x; i < n3; i += kCpThreads) {
+        const float ri = b[i];
+        const float zi = L.invdiag[i] * ri;  // 0 on fixed DOFs
+        x[i] = 0.f;
+        r[i] = ri;
+        p[i] = zi;
+        rz_part += (double)ri * (double)zi;
+    }
+    double rz = cp_block_sum(rz_part, sh);
+    for (int k = 0; k < steps && rz != 0.0; ++k) {
+        // q = K p and p.q
+        double pq_part = 0.0;
+        for (int n = warp; n < L.nn; n += kCpThreads / 32) {
+            float y[3];
+            warp_row(L, n, p, lane, y);
+            if (lane == 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    q[3 * n + c] = y[c];
+                    pq_part += (double)__ldcg(p + 3 * n + c) * (double)y[c];
+                }
+            }
+        }
+        const double pq = cp_block_sum(pq_part, sh);
+        const float alpha = (float)(rz / pq);
+        double rzn_part = 0.0;
+        for (long long i = threadIdx.x; i < n3; i += kCpThreads) {
+            x[i] = fmaf(alpha, p[i], x[i]);
+            const float ri = fmaf(-alpha, q[i], r[i]);
+            r[i] = ri;
+            rzn_part += (double)ri * (double)(L.invdiag[i] * ri);
+        }
+        const double rzn = cp_block_sum(rzn_part, sh);
+        const float beta = (float)(rzn / rz);
+        rz = rzn;
+        for (long long i = threadIdx.x; i < n3; i += kCpThreads) p[i] = fmaf(beta, p[i], L.invdiag[i] * r[i]);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 int coarse_fused_blocks(int* blocks_out, size_t shm) {
@@ -296,6 +373,12 @@ int coarse_fused_blocks(int* blocks_out, size_t shm) {
         return GMG_ERR_CUDA;
     *blocks_out = sms * std::max(1, std::min(per_sm, 2));
     return GMG_OK;
+}
+
+void launch_coarse_pcg(const CoarseLevel& l, const float* b, float* x, float* r, float* p, float* q, int steps,
+                       cudaStream_t s) {
+    note_launch();
+    pdl_launch(k_coarse_pcg, dim3(1), dim3(kCpThreads), 0, s, l, b, x, r, p, q, steps);
 }
 
 int launch_coarse_fused(const CoarseFused& a, int blocks, cudaStream_t s) {

@@ -273,6 +273,7 @@ struct gmg_handle {
     int ex = 0;                                 // nx rounded up to a multiple of 4
     int* free_idx_p = nullptr;                  // coarsest free DOFs in the vectors' numbering
     bool pads_dirty = false;                    // a solve ended non-finite: re-zero level-0 vectors
+    bool coarse_pcg = false;                    // coarsest above the Cholesky cutoff: fixed-count PCG
     double* E64 = nullptr;                      // fine moduli, FP64
     gmg::KeF keF{};
     gmg::KeD keD{};
@@ -519,6 +520,10 @@ int cholesky_and_inverse(double* A, int n, double* work, int* info_dev, double* 
 // ---- coarse_fused.cu ------------------------------------------------------------
 int coarse_fused_blocks(int* blocks_out, size_t shm);
 int launch_coarse_fused(const CoarseFused& a, int blocks, cudaStream_t s);
+// x = `steps` Jacobi-PCG steps on K^L x = b from 0 (the coarsest solve above the
+// dense-Cholesky cutoff); r, p, q: level-sized scratch vectors.
+void launch_coarse_pcg(const CoarseLevel& l, const float* b, float* x, float* r, float* p, float* q, int steps,
+                       cudaStream_t s);
 void launch_lambda_finish(double* sc, double* lam_slot, cudaStream_t s);
 
 }  // namespace gmg

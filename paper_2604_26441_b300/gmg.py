@@ -54,7 +54,8 @@ class _Options(ctypes.Structure):
                 ("ir_factor", ctypes.c_double),
                 ("fine_smoother", ctypes.c_int),
                 ("cycle_index", ctypes.c_int), ("outer", ctypes.c_int), ("restart", ctypes.c_int),
-                ("bsr_kernel", ctypes.c_int), ("stream", ctypes.c_void_p), ("spin_limit", ctypes.c_longlong)]
+                ("bsr_kernel", ctypes.c_int), ("stream", ctypes.c_void_p), ("spin_limit", ctypes.c_longlong),
+                ("coarse_pcg_steps", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -183,7 +184,8 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
             power_iters_coarse: int = 10, chol_cutoff: int = 5000, fused_coarse_nodes: int = 0,
             bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
             fine_smoother: str = "fp32", cycle: str = "V", outer: str = "pcg", restart: int = 32,
-            bsr_kernel: int = -1, stream: int | None = None, spin_limit: int = 1 << 24) -> _Options:
+            bsr_kernel: int = -1, stream: int | None = None, spin_limit: int = 1 << 24,
+            coarse_pcg_steps: int = 80) -> _Options:
     o = _Options()
     load_library().gmg_default_options(ctypes.byref(o))
     o.levels = levels
@@ -209,6 +211,7 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
     o.bsr_kernel = bsr_kernel
     o.stream = stream
     o.spin_limit = spin_limit
+    o.coarse_pcg_steps = coarse_pcg_steps
     return o
 
 

@@ -403,6 +403,54 @@ def test_grid_barrier_timeout_is_reported_and_recovered():
     assert info["setup_ms"] > 0.0
 
 
+COARSE_PCG_OPTS = dict(levels=2, smoother="jacobi", degree=2, coarse_smoother=None, coarse_degree=None, omega=0.6,
+                       coarse_omega=None, chol_cutoff=500)
+
+
+@pytest.mark.parametrize("steps,tol", [(5, 1e-4), (20, 1e-3)])
+def test_coarsest_pcg_fallback_matches_oracle(steps, tol):
+    """The coarsest level above the dense-Cholesky cutoff (16x8x8 in two levels
+    with cutoff 500: level 1 has 600 free DOFs) is solved by a fixed count of
+    Jacobi-PCG steps from 0 (Sec. "Matrix-Free V-Cycle"); FP32 against the
+    oracle's FP64 iterate after the same steps."""
+    c = inputs.CONFIGS["c0"]
+    rho, fixed = c.rho(), c.fixed()
+    S = gpu_solver(rho, c.p, **COARSE_PCG_OPTS, coarse_pcg_steps=steps)
+    H = hy.build_hierarchy((c.nx, c.ny, c.nz), fem.moduli(rho, c.p), fixed, levels=2, chol_cutoff=500,
+                           coarse_pcg_steps=steps)
+    last = H[-1]
+    assert last.L is None and last.n_free > 500
+    b = inputs.random_free_vector(last.fixed, seed=21)
+    x = S.coarse_solve(_t(b)).cpu().numpy()
+    ref = np.zeros_like(b, dtype=np.float64)
+    ref[last.free] = hy.coarse_pcg(last.apply, last.diag, b[last.free].astype(np.float64), steps)
+    assert np.all(x[last.fixed == 1] == 0)
+    assert rel_l2(x, ref) < tol, rel_l2(x, ref)
+
+
+def test_coarsest_pcg_fallback_solve():
+    """A full GMG-PCG solve with the 80-step coarsest PCG: the same outcome as
+    the oracle's, the oracle's own FP64 residual of the GPU solution below 1e-6,
+    and the displacement within 1e-5 of the oracle's exact solution."""
+    c = inputs.CONFIGS["c0"]
+    rho, fixed, f = c.rho(), c.fixed(), c.load()
+    S = gpu_solver(rho, c.p, **COARSE_PCG_OPTS)
+    H = hy.build_hierarchy((c.nx, c.ny, c.nz), fem.moduli(rho, c.p), fixed, levels=2, chol_cutoff=500)
+    spec = so.SmootherSpec("jacobi", 2, 0.6)
+    u_or, res = so.gmg_pcg(H, f, spec, tol=1e-6, maxit=200)
+    u, info = S.solve(_t(f, torch.float64), tol=1e-6, maxit=200)
+    assert (info["status"] == 0) == (res.status == so.OK)
+    assert info["status"] == 0
+    assert abs(info["iterations"] - res.iterations) <= max(2, 0.1 * res.iterations), (info, res.iterations)
+    u = u.cpu().numpy()
+    g = fem.Grid(c.nx, c.ny, c.nz)
+    r = f - fem.matfree_apply(g, fem.moduli(rho, c.p), fem.element_stiffness(0.3), u)
+    free = fem.free_dofs(fixed)
+    assert np.linalg.norm(r[free]) / np.linalg.norm(f[free]) <= 1e-6
+    H_exact = hy.build_hierarchy((c.nx, c.ny, c.nz), fem.moduli(rho, c.p), fixed, levels=c.levels)
+    assert rel_l2(u, so.exact_solve(H_exact, f)) < 1e-5
+
+
 def test_smallest_grid():
     rho = inputs.uniform_density(2, 2, 2)
     opts = dict(levels=2, smoother="jacobi", degree=2, coarse_smoother=None, coarse_degree=None, omega=0.5,
