@@ -6,11 +6,20 @@
 // Same factorisation and schedule as the FP32 fine operator (fine.cu): K_e =
 // H^T G H with G in eight 3x3 parity-class blocks, one thread per element column
 // marching along z, face difference sums shared between layers, and the node
-// sums formed by warp shuffles and a shared-memory exchange.  FP64 arithmetic
-// runs at a small fraction of FP32 throughput on this part, so the ~200 FP64
-// operations per element of this form (instead of ~600 for the dense element
-// matrix) set the cost; a one-plane register prefetch is enough to cover memory
-// latency behind that arithmetic.
+// sums formed by warp shuffles and a shared-memory exchange.
+//
+// Arithmetic.  FP64 runs at about 1/64 of the FP32 rate on this part, and the
+// ~200 FP64 operations per element of the factored form kept the FP64 pipe 82 %
+// busy for 0.56 ms at 100^3.  The element arithmetic therefore runs in
+// double-float form instead: a value is an unevaluated sum hi + lo of two FP32
+// numbers (~44 significant bits), added with Knuth's error-free TwoSum and
+// multiplied with an FMA-based exact product (Dekker's scheme), followed by a
+// renormalisation.  Each double-float operation costs ~6-10 FP32 instructions
+// and its error stays within a few units of 2^-44 of its operands' magnitude,
+// far below what a 1e-6 acceptance test needs (the result agrees with a plain
+// FP64 evaluation to ~1e-13).  FP64 remains for what is read and written: u,
+// f and E are FP64 and split once per value; f - K u, r and ||r||^2 are
+// formed in FP64.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -28,8 +37,46 @@ __host__ __device__ constexpr int mono(int sigma, int c) {
 
 __device__ __forceinline__ bool fixed_bit(uint8_t m, int c) { return (m >> c) & 1; }
 
-__device__ __forceinline__ void face_diffs(double u00, double u10, double u01, double u11, double q[4]) {
-    const double dx0 = u10 - u00, dx1 = u11 - u01;
+// ---- double-float numbers: value = hi + lo, |lo| <= ulp(hi) / 2 ----------------
+// The intrinsics (__fadd_rn, __fmul_rn) are never contracted into FMAs, which
+// the error-free transformations rely on.
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df df_of(double d) {
+    const float h = __double2float_rn(d);
+    return {h, __double2float_rn(d - (double)h)};
+}
+__device__ __forceinline__ double df_val(df a) { return (double)a.hi + (double)a.lo; }
+// TwoSum of the high parts, the low parts added to its error, renormalised.
+__device__ __forceinline__ df operator+(df a, df b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+    const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, t);
+    return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+// Exact product of the high parts by an FMA, cross terms added, renormalised.
+__device__ __forceinline__ df operator*(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)));
+    const float h = __fadd_rn(p, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+__device__ __forceinline__ df shfl_down(df a, int d, int w) {
+    return {__shfl_down_sync(0xffffffffu, a.hi, d, w), __shfl_down_sync(0xffffffffu, a.lo, d, w)};
+}
+
+// G of the element operator as double-float pairs (split on the host).
+struct GHatDF {
+    float hi[72], lo[72];
+};
+
+__device__ __forceinline__ void face_diffs(df u00, df u10, df u01, df u11, df q[4]) {
+    const df dx0 = u10 - u00, dx1 = u11 - u01;
     q[1] = dx0 + dx1;
     q[2] = (u01 - u00) + (u11 - u10);
     q[3] = dx1 - dx0;
@@ -37,10 +84,10 @@ __device__ __forceinline__ void face_diffs(double u00, double u10, double u01, d
 
 __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,
                                                    const double* f, const double* uvec, double* r64, float* r32,
-                                                   int px, const double* sc, double* partial, GHat64 G, int zchunk) {
+                                                   int px, const double* sc, double* partial, GHatDF G, int zchunk) {
     pdl_entry();
-    __shared__ double sp[2][BY + 1][(BX + 1) * 3];
-    __shared__ double sx[2][BY][BX * 3];
+    __shared__ df sp[2][BY + 1][(BX + 1) * 3];
+    __shared__ df sx[2][BY][BX * 3];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
     const int NX = nx + 1, NY = ny + 1, NZ = nz + 1, NXY = NX * NY, NEXY = nx * ny;
     const int x0 = blockIdx.x * (BX - 1), y0 = blockIdx.y * (BY - 1);
@@ -78,15 +125,15 @@ __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const
         }
     };
     auto store_plane = [&](int buf) {
-        double* d = &sp[buf][ty][3 * tx];
-        d[0] = (pm & 1) ? 0.0 : pv[0];
-        d[1] = (pm & 2) ? 0.0 : pv[1];
-        d[2] = (pm & 4) ? 0.0 : pv[2];
+        df* d = &sp[buf][ty][3 * tx];
+        d[0] = df_of((pm & 1) ? 0.0 : pv[0]);
+        d[1] = df_of((pm & 2) ? 0.0 : pv[1]);
+        d[2] = df_of((pm & 4) ? 0.0 : pv[2]);
         if (halo) {
-            double* e = &sp[buf][hy][3 * hx];
-            e[0] = (phm & 1) ? 0.0 : ph[0];
-            e[1] = (phm & 2) ? 0.0 : ph[1];
-            e[2] = (phm & 4) ? 0.0 : ph[2];
+            df* e = &sp[buf][hy][3 * hx];
+            e[0] = df_of((phm & 1) ? 0.0 : ph[0]);
+            e[1] = df_of((phm & 2) ? 0.0 : ph[1]);
+            e[2] = df_of((phm & 4) ? 0.0 : ph[2]);
         }
     };
 
@@ -94,7 +141,10 @@ __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const
     store_plane((k0 - 1) & 1);
     prefetch(k0);
     __syncthreads();
-    double Qb[4][3] = {}, Cb[4][3] = {}, Tprev[4][3] = {};
+    const df zero{0.f, 0.f};
+    df Qb[4][3], Cb[4][3], Tprev[4][3];
+    for (int q = 0; q < 4; ++q)
+        for (int c = 0; c < 3; ++c) Qb[q][c] = Cb[q][c] = Tprev[q][c] = zero;
     {
         const int b = (k0 - 1) & 1;
         for (int c = 0; c < 3; ++c) {
@@ -102,7 +152,7 @@ __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const
             Cb[1][c] = sp[b][ty][3 * (tx + 1) + c];
             Cb[2][c] = sp[b][ty + 1][3 * tx + c];
             Cb[3][c] = sp[b][ty + 1][3 * (tx + 1) + c];
-            double q[4];
+            df q[4];
             face_diffs(Cb[0][c], Cb[1][c], Cb[2][c], Cb[3][c], q);
             for (int i = 1; i < 4; ++i) Qb[i][c] = q[i];
         }
@@ -110,15 +160,15 @@ __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const
     double Enext = (!uzero && cell_in && k0 - 1 >= 0 && k0 - 1 < nz) ? E[e_base + (k0 - 1) * NEXY] : 0.0;
     bool pending = false;
     int pend_k = 0;
-    double R1[3] = {0.0, 0.0, 0.0};
+    df R1[3] = {zero, zero, zero};
     double rr = 0.0;
 
     auto finish = [&]() {
-        const double* r0 = &sx[pend_k & 1][ty + 1][3 * tx];
+        const df* r0 = &sx[pend_k & 1][ty + 1][3 * tx];
         const int n = onode_base + pend_k * NXY;
         const uint8_t m = mask[n];
         for (int c = 0; c < 3; ++c) {
-            const double v = fixed_bit(m, c) ? 0.0 : f[3 * n + c] - (R1[c] + r0[c]);
+            const double v = fixed_bit(m, c) ? 0.0 : f[3 * n + c] - df_val(R1[c] + r0[c]);
             if (r64) r64[3 * n + c] = v;
             if (r32) r32[GMG_B(3 * (ox + px * (oy + NY * pend_k)) + c, 3LL * px * NY * NZ, 301)] = (float)v;
             rr += v * v;
@@ -131,64 +181,65 @@ __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const
         __syncthreads();
         if (pending && owner) finish();
         pending = false;
-        const double Ee = Enext;
+        const df Ee = df_of(Enext);
         if (pt + 1 <= k1) prefetch(pt + 1);
         Enext = (!uzero && cell_in && kl + 1 < nz && kl + 1 < k1) ? E[e_base + (kl + 1) * NEXY] : 0.0;
         const int b = pt & 1;
-        double Qt[4][3], Ct[4][3];
+        df Qt[4][3], Ct[4][3];
         for (int c = 0; c < 3; ++c) {
             Ct[0][c] = sp[b][ty][3 * tx + c];
             Ct[1][c] = sp[b][ty][3 * (tx + 1) + c];
             Ct[2][c] = sp[b][ty + 1][3 * tx + c];
             Ct[3][c] = sp[b][ty + 1][3 * (tx + 1) + c];
-            double q[4];
+            df q[4];
             face_diffs(Ct[0][c], Ct[1][c], Ct[2][c], Ct[3][c], q);
-            Qt[0][c] = 0.0;
+            Qt[0][c] = zero;
             for (int i = 1; i < 4; ++i) Qt[i][c] = q[i];
         }
-        double v[8][3];
+        df v[8][3];
         for (int c = 0; c < 3; ++c) {
-            v[0][c] = 0.0;
+            v[0][c] = zero;
             v[4][c] = ((Ct[0][c] - Cb[0][c]) + (Ct[1][c] - Cb[1][c])) + ((Ct[2][c] - Cb[2][c]) + (Ct[3][c] - Cb[3][c]));
             for (int q = 1; q < 4; ++q) {
                 v[q][c] = Qt[q][c] + Qb[q][c];
                 v[q + 4][c] = Qt[q][c] - Qb[q][c];
             }
         }
-        double w[8][3];
-        for (int c = 0; c < 3; ++c) w[0][c] = 0.0;
+        df w[8][3];
+        for (int c = 0; c < 3; ++c) w[0][c] = zero;
 #pragma unroll
         for (int s = 0; s < 8; ++s)
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const int mi = mono(s, i);
                 if (mi == 0) continue;
-                double acc = 0.0;
+                df acc = zero;
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     const int mj = mono(s, j);
                     if (mj == 0) continue;
-                    acc = fma(G.g[s * 9 + i * 3 + j], v[mj][j], acc);
+                    const int gi = s * 9 + i * 3 + j;
+                    acc = acc + df{G.hi[gi], G.lo[gi]} * v[mj][j];
                 }
                 w[mi][i] = Ee * acc;
             }
-        double T[4][3], B[4][3];
+        df T[4][3], B[4][3];
         for (int q = 0; q < 4; ++q)
             for (int c = 0; c < 3; ++c) {
                 T[q][c] = w[q][c] + w[q + 4][c];
                 B[q][c] = w[q][c] - w[q + 4][c];
             }
         if (kl >= k0) {
-            double r0[3];
+            df r0[3];
             for (int c = 0; c < 3; ++c) {
-                const double S0 = Tprev[0][c] + B[0][c], S1 = Tprev[1][c] + B[1][c];
-                const double S2 = Tprev[2][c] + B[2][c], S3 = Tprev[3][c] + B[3][c];
-                const double p = S0 - S2, qd = S1 - S3, r = S0 + S2, sd = S1 + S3;
-                const double c00 = p - qd, c10 = p + qd, c01 = r - sd, c11 = r + sd;
-                R1[c] = c11 + __shfl_down_sync(0xffffffffu, c01, 1, BX);
-                r0[c] = c10 + __shfl_down_sync(0xffffffffu, c00, 1, BX);
+                const df S0 = Tprev[0][c] + B[0][c], S1 = Tprev[1][c] + B[1][c];
+                const df S2 = Tprev[2][c] + B[2][c], S3 = Tprev[3][c] + B[3][c];
+                const df p = S0 - S2, qd = S1 - S3, r = S0 + S2, sd = S1 + S3;
+                const df c00 = p - qd, c10 = p + qd, c01 = r - sd, c11 = r + sd;
+                R1[c] = c11 + shfl_down(c01, 1, BX);
+                r0[c] = c10 + shfl_down(c00, 1, BX);
             }
-            double* dst = &sx[kl & 1][ty][3 * tx];
+            df* dst = &sx[kl & 1][ty][3 * tx];
             dst[0] = r0[0]; dst[1] = r0[1]; dst[2] = r0[2];
             pending = true;
             pend_k = kl;
@@ -260,8 +311,13 @@ void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t*
                          cudaStream_t s) {
     int zc = 0;
     const dim3 g = resid_grid(nx, ny, nz, &zc);
+    GHatDF gd;
+    for (int i = 0; i < 72; ++i) {
+        gd.hi[i] = (float)G.g[i];
+        gd.lo[i] = (float)(G.g[i] - (double)gd.hi[i]);
+    }
     note_launch();
-    pdl_launch(k_resid64, dim3(g), dim3(dim3(BX, BY)), 0, s, nx, ny, nz, E, mask, f, u, r64, r32, px, sc, partial, G,
+    pdl_launch(k_resid64, dim3(g), dim3(dim3(BX, BY)), 0, s, nx, ny, nz, E, mask, f, u, r64, r32, px, sc, partial, gd,
                zc);
 }
 
