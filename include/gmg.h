@@ -330,6 +330,36 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out);
 int gmg_solve_batch(gmg_handle* const* handles, int count, const double* const* f_dev, double* const* u_dev,
                     double tol, int maxit, gmg_info* infos);
 
+/* Multi-load solve (the batching line; Sec. "Outer Krylov Solver and
+ * Convergence Statement" per load): nl <= 16 right-hand sides f[l] -> u[l]
+ * (host arrays of device FP64 pointers, dense numbering; u[l] the initial
+ * guess) on one hierarchy, advanced together by one device-resident PCG loop
+ * with per-load step lengths, directions and stopping decisions: every kernel
+ * of the V-cycle serves all loads in one launch (levels >= 1 read each operator
+ * block once for all loads).  A load stops where gmg_solve would stop it;
+ * the FP64 acceptance test follows per load, and a load whose recursive
+ * residual passed but whose FP64 residual did not continues alone (residual
+ * replacement, as gmg_solve).  Options outside this path (outer FGMRES,
+ * ir_factor, a tensor-core fine smoother, the host loop, a W-cycle, a single
+ * level, a coarsest level above the Cholesky cutoff) make the call run one
+ * gmg_solve after the other.  Allocates the handle's multi-load workspace on
+ * first use (7 level-0 vectors of 256 bytes per node, 5 per coarser level,
+ * the coarsest inverse as FP32 hi + lo).  Synchronous on the handle's stream.
+ * infos[l] per load; returns GMG_OK when every load converged, else the last
+ * failing status. */
+int gmg_solve_multi(gmg_handle* h, int nl, const double* const* f_dev, double* const* u_dev, double tol, int maxit,
+                    gmg_info* infos);
+
+/* y[l] = K_ff u[l] (Eq. mf_matvec; fixed DOFs of u[l] ignored, of y[l] set
+ * to 0) for nl <= 16 loads in one launch of the multi-load level-0 operator
+ * (host arrays of device FP32 pointers, dense numbering).  Asynchronous. */
+int gmg_apply_multi(gmg_handle* h, int nl, const float* const* u_dev, float* const* y_dev);
+
+/* Level-0 operator of the multi-load path: 0 = CUDA cores (Hadamard form, one
+ * block per tile and load), 1 = tensor cores (element contraction on tcgen05).
+ * GMG_ERR_ARG for an unknown kind or one this build lacks. */
+int gmg_set_multi_kernel(gmg_handle* h, int kind);
+
 /* Result of gmg_autotune. */
 typedef struct {
     int fine_tile;               /* fine kernel tile: 0 = 32 x 8 threads (31 x 7 nodes), 1 = 16 x 16 (15 x 15) */

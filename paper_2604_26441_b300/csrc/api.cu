@@ -982,6 +982,7 @@ void gmg_destroy(gmg_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     loop_free(h);
+    multi_free(h);
     if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
     if (h->batch_graph) cudaGraphDestroy(h->batch_graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -1415,6 +1416,7 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out) {
     h->batch_exec = nullptr;
     h->batch_key.clear();
     h->batch_counts.clear();
+    h->mw = nullptr;  // the multi-load workspace stays the source's
     h->is_clone = true;
     auto bad = [&](int rc) {
         std::string keep = g_err;

@@ -103,6 +103,7 @@ enum Scalar {
     SC_TOL = 17,    // relative tolerance
     SC_MAXIT = 18,  // iteration cap
     SC_NF = 19,     // ||f_free||
+    SC_ACT = 20,    // multi-load solve: this load still iterates (1) or has stopped (0)
     SC_COUNT = 24
 };
 
@@ -150,6 +151,45 @@ struct CoarseLevel {
     float *x, *x2, *b, *t, *d;
     const double* coef;
     int kind, degree;
+};
+
+// ---- multi-load vectors (multi.cu) ------------------------------------------
+// Up to kLoads right-hand sides on one hierarchy advance together.  A level's
+// multi-load vector holds, for node n (the level's vector numbering; level 0:
+// rows padded to px nodes) and load l, the record (u_x, u_y, u_z, 0) at float
+// offset (n * kLoads + l) * 4: 16-byte records, 256 bytes per node.
+constexpr int kLoads = 16;
+constexpr int kNodeF = 4 * kLoads;  // floats per node of a multi-load vector
+
+struct MultiLevel {
+    float *x = nullptr, *x2 = nullptr, *b = nullptr, *t = nullptr, *d = nullptr;
+};
+
+// Workspace of the multi-load solve, owned by one handle (allocated on its
+// first multi-load call; its device buffers are in the handle's allocation list).
+struct MultiWork {
+    float *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x2 = nullptr, *t = nullptr, *d = nullptr;
+    MultiLevel lev[kMaxLevels];
+    double* sc = nullptr;        // [kLoads][SC_COUNT] device scalars, one block per load
+    double* partials = nullptr;  // [kLoads][pstride]
+    int pstride = 0;
+    float* Ahi = nullptr;        // coarsest inverse split into FP32 hi + lo (double-float apply)
+    float* Alo = nullptr;
+    void* pinned = nullptr;      // host-mapped mirror of sc and the sticky error words
+    double* sc_host = nullptr;
+    double* sc_map = nullptr;
+    int* err_host = nullptr;
+    int* err_map = nullptr;
+    int fine_kernel = 0;         // level-0 operator: 0 CUDA-core (Hadamard), 1 tensor cores
+    int launch_err = 0;          // a level-0 launch could not be prepared (tensor map encoding)
+    // captured loops, keyed by the iterate pointers
+    struct Loop {
+        std::vector<const double*> u;
+        cudaGraph_t g;
+        cudaGraphExec_t ex;
+        unsigned long long pre, body;
+    };
+    std::vector<Loop> loops;
 };
 
 // Arguments of the fused lower V-cycle: levels start..L-1, coarsest solve data,
@@ -334,6 +374,7 @@ struct gmg_handle {
     std::vector<std::pair<const gmg_handle*, const double*>> batch_key;
     std::vector<std::pair<unsigned long long, unsigned long long>> batch_counts;
     int fused_blocks = 0;
+    gmg::MultiWork* mw = nullptr;               // multi-load solve workspace (multi.cu), lazily allocated
     std::vector<void*> allocs;                  // every device allocation, freed by gmg_destroy
     void* pinned = nullptr;                     // pinned host-mapped block (sc_host, err_host)
 };
@@ -525,5 +566,22 @@ int launch_coarse_fused(const CoarseFused& a, int blocks, cudaStream_t s);
 void launch_coarse_pcg(const CoarseLevel& l, const float* b, float* x, float* r, float* p, float* q, int steps,
                        cudaStream_t s);
 void launch_lambda_finish(double* sc, double* lam_slot, cudaStream_t s);
+
+// ---- multi.cu: multi-load solve pieces used by gmg_solve_batch ---------------------
+// Allocates h's multi-load workspace once (GMG_OK or an error code).
+int multi_workspace(gmg_handle* h);
+void multi_free(gmg_handle* h);
+void multi_drop_loops(gmg_handle* h);
+// True when h's options and hierarchy suit the multi-load path (else *why says why).
+bool multi_ok(const gmg_handle* h, std::string* why);
+// Asynchronous per-load pieces, writing load l's scalar block h->mw->sc + l * SC_COUNT.
+void multi_norms(gmg_handle* h, int l, const double* f, double* u);
+void multi_cast(gmg_handle* h, int nl, const double* const* f, const bool* cold);
+void multi_true_residual(gmg_handle* h, int l, const double* f, const double* u, bool into_r);
+// Per-load loop scalars (iteration count 0, tolerance, cap, ||f||, active flag) of all 16 slots.
+void multi_set_loop_scalars(gmg_handle* h, int nl, double tol, int maxit, const double* nf, const bool* active);
+void multi_publish(gmg_handle* h);
+bool multi_capture_loop(gmg_handle* h, double* const* u, int nl, cudaGraph_t g, cudaStream_t cap,
+                        unsigned long long& prefix, unsigned long long& body_k);
 
 }  // namespace gmg

@@ -108,6 +108,10 @@ _SIGS = {
     "gmg_clone": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "gmg_solve_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                        ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Info)]),
+    "gmg_solve_multi": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_double,
+                                       ctypes.c_int, ctypes.POINTER(_Info)]),
+    "gmg_apply_multi": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "gmg_set_multi_kernel": (ctypes.c_int, [_P, ctypes.c_int]),
     "gmg_vcycle_symmetry": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gmg_residual64": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gmg_residual64_noalloc": (ctypes.c_int, [ctypes.POINTER(_Grid), _P, _P, ctypes.c_double, _P, _P, _P,
@@ -344,6 +348,42 @@ class Solver:
                    "rel_residual": info.rel_residual, "rel_residual_recursive": info.rel_residual_recursive,
                    "solve_ms": info.solve_ms, "setup_ms": info.setup_ms}
 
+    def solve_multi(self, fs, us=None, tol: float = 1e-6, maxit: int = 200):
+        """Solves up to 16 loads fs[l] (device FP64) on this hierarchy together
+        (gmg_solve_multi): one PCG loop with per-load step lengths and stopping
+        decisions; us[l] initial guesses (zeros when None).  Returns (us, infos)."""
+        import torch
+        n = len(fs)
+        if us is None:
+            us = [torch.zeros_like(f) for f in fs]
+        if len(us) != n or not 1 <= n <= 16:
+            raise ValueError("1..16 loads, one iterate per load")
+        fp = (_P * n)(*[_ptr(f, torch.float64, 3 * self.nn, "f") for f in fs])
+        up = (_P * n)(*[_ptr(u, torch.float64, 3 * self.nn, "u") for u in us])
+        infos = (_Info * n)()
+        rc = self._lib.gmg_solve_multi(self._h, n, fp, up, tol, maxit, infos)
+        _check(rc, allow=(GMG_OK, GMG_NOT_CONVERGED, GMG_NONFINITE))
+        return us, [_info_dict(i) for i in infos]
+
+    def apply_multi(self, us, ys=None):
+        """ys[l] = K us[l] for up to 16 loads (device FP32) in one launch of the
+        multi-load level-0 operator (gmg_apply_multi)."""
+        import torch
+        n = len(us)
+        if ys is None:
+            ys = [torch.empty_like(u) for u in us]
+        if len(ys) != n or not 1 <= n <= 16:
+            raise ValueError("1..16 loads, one output per load")
+        up = (_P * n)(*[_ptr(u, torch.float32, 3 * self.nn, "u") for u in us])
+        yp = (_P * n)(*[_ptr(y, torch.float32, 3 * self.nn, "y") for y in ys])
+        _check(self._lib.gmg_apply_multi(self._h, n, up, yp))
+        return ys
+
+    def set_multi_kernel(self, kind: str) -> None:
+        """Level-0 operator of the multi-load path: "simt" (CUDA cores) or
+        "tc" (tensor cores)."""
+        _check(self._lib.gmg_set_multi_kernel(self._h, {"simt": 0, "tc": 1}[kind]))
+
     def set_spin_limit(self, polls: int) -> None:
         """Polls a block of the fused lower V-cycle makes at a grid barrier
         before it gives up (gmg_set_spin_limit); drops captured solve graphs."""
@@ -463,6 +503,12 @@ class Solver:
         _check(self._lib.gmg_residual64(self._h, _ptr(f, torch.float64, 3 * self.nn, "f"),
                                         _ptr(u, torch.float64, 3 * self.nn, "u"), rp, ctypes.byref(rel)))
         return rel.value
+
+
+def _info_dict(i) -> dict:
+    return {"status": i.status, "iterations": i.iterations, "replacements": i.replacements,
+            "rel_residual": i.rel_residual, "rel_residual_recursive": i.rel_residual_recursive,
+            "solve_ms": i.solve_ms, "setup_ms": i.setup_ms}
 
 
 def solve_batch(solvers, fs, us=None, tol: float = 1e-6, maxit: int = 200):

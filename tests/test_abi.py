@@ -95,6 +95,9 @@ def test_argument_errors_without_device(lib):
                          ctypes.byref(mask_bc), None) == -1
     assert lib.gmg_solve(None, None, None, 1e-6, 10, None) == -1
     assert lib.gmg_autotune(None, 3, None) == -1
+    assert lib.gmg_solve_multi(None, 1, None, None, 1e-6, 10, None) == -1
+    assert lib.gmg_apply_multi(None, 1, None, None) == -1
+    assert lib.gmg_set_multi_kernel(None, 0) == -1
     assert lib.gmg_num_levels(None) == 0
     lib.gmg_destroy(None)
 

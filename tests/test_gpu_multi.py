@@ -1,0 +1,194 @@
+"""Multi-load path (the batching line): up to 16 right-hand sides on one
+hierarchy advanced by one PCG loop, every kernel serving all loads.
+
+Checked per load against the FP64 oracle (the fine operator of Eq. mf_matvec,
+the solve of Sec. "Outer Krylov Solver and Convergence Statement") and against
+the single-load solve on the same handle options: the same pass/fail decision,
+the same iteration count, iterates within rounding of each other (the level-0
+operator does the same arithmetic per node; reductions group their partial
+sums differently and the coarsest inverse is applied in double-float instead of
+FP64, so the two paths are not bitwise equal).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import fem, solver as so
+from paper_2604_26441_b300 import inputs
+
+from gpu_helpers import gpu_solver, oracle_hierarchy, oracle_spec_from_opts, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2604_26441_b300 import build
+    build.build_library()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _t(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def _loads(nx, ny, nz, ks, nrhs=16):
+    return [inputs.rotated_tip_edge_load(nx, ny, nz, k, nrhs=nrhs) for k in ks]
+
+
+APPLY_CASES = [
+    ("c0", 16, 8, 8, 3),
+    ("ragged", 37, 13, 9, 16),
+    ("thin", 33, 2, 5, 5),
+    ("c1", 40, 40, 40, 16),
+]
+
+
+@pytest.mark.parametrize("name,nx,ny,nz,nl", APPLY_CASES)
+def test_multi_apply_matches_oracle_and_single_load(name, nx, ny, nz, nl):
+    rho = inputs.filtered_random_density(nx, ny, nz, 7)
+    fixed = inputs.clamp_xmin_mask(nx, ny, nz)
+    S = gpu_solver(rho, 3.0, levels=0, smoother="jacobi", coarse_smoother=None, omega=0.5)
+    E = fem.moduli(rho, 3.0)
+    Ke = fem.element_stiffness(0.3)
+    g = fem.Grid(nx, ny, nz)
+    us = []
+    for k in range(nl):
+        u = inputs.random_free_vector(fixed, seed=100 + k)
+        u[fixed == 1] = 1e3  # values on fixed DOFs must be ignored
+        us.append(_t(u))
+    ys = S.apply_multi(us)
+    for k in range(nl):
+        y = ys[k].cpu().numpy()
+        u = us[k].cpu().numpy().astype(np.float64)
+        u[fixed == 1] = 0.0
+        yref = fem.matfree_apply(g, E, Ke, u)
+        yref[fixed == 1] = 0.0
+        assert np.all(y[fixed == 1] == 0.0)
+        assert rel_l2(y, yref) < 1e-6, k
+        # the same per-node arithmetic as the single-load operator
+        assert np.array_equal(y, S.apply(us[k]).cpu().numpy()), k
+    # reproducible, and independent of the other loads in the launch
+    ys2 = S.apply_multi(us)
+    assert all(torch.equal(a, b) for a, b in zip(ys, ys2))
+    if nl > 1:
+        y1 = S.apply_multi(us[1:2])[0]
+        assert torch.equal(y1, ys[1])
+
+
+def test_multi_apply_full_size_sampled():
+    """100^3 with 16 loads (the launch configuration of the batched throughput
+    leg's level 0): sampled rows of every load against the oracle."""
+    c = inputs.CONFIGS["c2"]
+    rho = inputs.filtered_random_density(c.nx, c.ny, c.nz, 3)
+    S = gpu_solver(rho, 3.0, levels=0, smoother="jacobi", coarse_smoother=None, omega=0.5)
+    fixed = c.fixed()
+    g = fem.Grid(c.nx, c.ny, c.nz)
+    E = fem.moduli(rho, 3.0)
+    Ke = fem.element_stiffness(0.3)
+    rng = np.random.default_rng(0)
+    nodes = np.concatenate([rng.integers(0, g.n_nodes, 400), [0, g.n_nodes - 1, c.nx, g.n_nodes // 2]])
+    us_h = [inputs.random_free_vector(fixed, seed=40 + k) for k in range(16)]
+    ys = S.apply_multi([_t(u) for u in us_h])
+    for k in range(16):
+        y = ys[k].cpu().numpy().reshape(-1, 3)
+        ref = fem.matfree_apply_at_nodes(g, E, Ke, us_h[k], nodes)
+        ref[fixed.reshape(-1, 3)[nodes] == 1] = 0
+        assert rel_l2(y[nodes], ref) < 1e-6, k
+
+
+SOLVE_CASES = [
+    ("c0", 16, 8, 8, 3, dict(smoother="chebyshev", degree=3, omega=0.5), 5),
+    ("ragged", 23, 11, 9, 3, dict(smoother="chebyshev", degree=2, omega=0.5), 16),
+    ("c1", 40, 40, 40, 4, dict(smoother="jacobi", degree=2, omega=0.5), 16),
+]
+
+
+@pytest.mark.parametrize("name,nx,ny,nz,levels,sm,nl", SOLVE_CASES)
+def test_multi_solve_matches_single_and_oracle(name, nx, ny, nz, levels, sm, nl):
+    opts = dict(levels=levels, coarse_smoother=None, coarse_degree=None, coarse_omega=None, **sm)
+    rho = inputs.filtered_random_density(nx, ny, nz, 21)
+    fixed = inputs.clamp_xmin_mask(nx, ny, nz)
+    loads = _loads(nx, ny, nz, range(nl))
+    S = gpu_solver(rho, 3.0, **opts)
+    us, infos = S.solve_multi([_t(f, torch.float64) for f in loads])
+    single = gpu_solver(rho, 3.0, fused_coarse_nodes=0, **opts)
+    H, E = oracle_hierarchy(rho, 3.0, fixed, levels)
+    spec = oracle_spec_from_opts(opts)
+    g = fem.Grid(nx, ny, nz)
+    free = fem.free_dofs(fixed)
+    Ke = fem.element_stiffness(0.3)
+    for k, f in enumerate(loads):
+        u = us[k].cpu().numpy()
+        info = infos[k]
+        u1, info1 = single.solve(_t(f, torch.float64))
+        assert info["status"] == info1["status"] == 0, (k, info, info1)
+        assert info["iterations"] == info1["iterations"], (k, info["iterations"], info1["iterations"])
+        assert rel_l2(u, u1.cpu().numpy()) < 1e-5, k
+        # the oracle: its own GMG-PCG (counts) and its FP64 residual of this answer
+        u_or, res = so.gmg_pcg(H, f, spec, tol=1e-6, maxit=200)
+        assert res.status == so.OK
+        assert abs(info["iterations"] - res.iterations) <= max(2, 0.1 * res.iterations)
+        r = f - fem.matfree_apply(g, E, Ke, u)
+        rel = np.linalg.norm(r[free]) / np.linalg.norm(f[free])
+        assert rel <= 1e-6, (k, rel)
+        assert abs(info["rel_residual"] - rel) < 1e-9
+        assert np.all(u[fixed == 1] == 0)
+    if name == "c0":
+        ue = so.exact_solve(H, loads[0], spec)
+        assert rel_l2(us[0].cpu().numpy(), ue) < 1e-5
+    # replayed loop graph: same answers
+    first = [u.clone() for u in us]
+    for u in us:
+        u.zero_()
+    us2, _ = S.solve_multi([_t(f, torch.float64) for f in loads], us)
+    assert all(torch.equal(a, b) for a, b in zip(first, us2))
+
+
+def test_multi_solve_mixed_loads_and_caps():
+    """A zero load, a warm-started load, a load that the cap stops and ordinary
+    loads in one call: each ends as the single-load solve ends it."""
+    nx, ny, nz, levels = 16, 8, 8, 3
+    opts = dict(levels=levels, smoother="chebyshev", degree=2, coarse_smoother=None, coarse_degree=None, omega=0.5,
+                coarse_omega=None)
+    rho = inputs.filtered_random_density(nx, ny, nz, 5)
+    S = gpu_solver(rho, 3.0, **opts)
+    single = gpu_solver(rho, 3.0, fused_coarse_nodes=0, **opts)
+    loads = _loads(nx, ny, nz, [0, 3, 7, 12])
+    zero = np.zeros_like(loads[0])
+    fs = [loads[0], zero, loads[1], loads[2]]
+    u_warm, _ = single.solve(_t(loads[1], torch.float64), tol=1e-3)
+    u0 = [torch.zeros(3 * S.nn, dtype=torch.float64, device="cuda") for _ in fs]
+    u0[2] = u_warm.clone()
+    us, infos = S.solve_multi([_t(f, torch.float64) for f in fs], [u.clone() for u in u0])
+    for k, f in enumerate(fs):
+        u1, info1 = single.solve(_t(f, torch.float64), u0[k].clone())
+        assert infos[k]["status"] == info1["status"], k
+        assert infos[k]["iterations"] == info1["iterations"], (k, infos[k], info1)
+        if k == 1:
+            assert infos[k]["rel_residual"] == 0.0 and not torch.any(us[k] != 0)
+        else:
+            assert rel_l2(us[k].cpu().numpy(), u1.cpu().numpy()) < 1e-5
+    # a cap of 3 iterations: every load stops there, not converged
+    us, infos = S.solve_multi([_t(f, torch.float64) for f in loads], maxit=3)
+    for k, f in enumerate(loads):
+        _, info1 = single.solve(_t(f, torch.float64), maxit=3)
+        assert infos[k]["status"] == info1["status"] == 1
+        assert infos[k]["iterations"] == info1["iterations"] == 3
+
+
+def test_multi_solve_outside_the_path_runs_single_solves():
+    """Outer FGMRES is not on the multi-load path: the call runs gmg_solve per load."""
+    nx, ny, nz = 16, 8, 8
+    opts = dict(levels=3, smoother="chebyshev", degree=2, coarse_smoother=None, coarse_degree=None, omega=0.5,
+                coarse_omega=None, outer="fgmres")
+    rho = inputs.filtered_random_density(nx, ny, nz, 9)
+    S = gpu_solver(rho, 3.0, **opts)
+    loads = _loads(nx, ny, nz, [1, 2])
+    us, infos = S.solve_multi([_t(f, torch.float64) for f in loads])
+    for k, f in enumerate(loads):
+        u1, info1 = S.solve(_t(f, torch.float64))
+        assert infos[k]["status"] == 0 and infos[k]["iterations"] == info1["iterations"]
+        assert torch.equal(us[k], u1)
