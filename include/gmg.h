@@ -317,16 +317,21 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out);
 
 /* Solves count independent problems -- handles of different grids, clones for
  * further loads -- f[i] -> u[i] (device FP64, u[i] the initial guess), sharing
- * tol and maxit.  The device-resident PCG loops of all items run as independent
- * branches of one CUDA graph (captured on the first call for a given list of
- * handles and iterates, then replayed), so small instances run concurrently;
- * the FP64 acceptance test is taken for all items after one synchronisation.
- * Each item's iterates equal those of gmg_solve on a handle with
- * fused_coarse_nodes = 0 (the batch uses the per-level lower V-cycle).  Items
- * whose options need the host loop (outer FGMRES, ir_factor, device_loop = 0)
- * make the batch run one gmg_solve after the other.  Each handle appears at
- * most once.  Runs on the first handle's stream.  Returns GMG_OK when every
- * item converged, else the last failing status; infos[i] per item. */
+ * tol and maxit.  Items whose handles share one hierarchy (a handle and its
+ * clones, on the multi-load path's options) are solved together as multi-load
+ * chunks of up to 16 loads (the loop of gmg_solve_multi, owned by the chunk's
+ * first handle, whose multi-load workspace it allocates on first use); every
+ * other item runs its own device-resident PCG loop.  The loops run as
+ * independent branches of one CUDA graph (captured on the first call for a
+ * given list of handles and iterates, then replayed), so small instances run
+ * concurrently; the FP64 acceptance test is taken for all items after one
+ * synchronisation.  A single item's iterates equal those of gmg_solve on a
+ * handle with fused_coarse_nodes = 0 (the per-level lower V-cycle); a chunk's
+ * equal those of gmg_solve_multi on the same loads.  Items whose options need
+ * the host loop (outer FGMRES, ir_factor, device_loop = 0) make the batch run
+ * one gmg_solve after the other.  Each handle appears at most once.  Runs on
+ * the first handle's stream.  Returns GMG_OK when every item converged, else
+ * the last failing status; infos[i] per item. */
 int gmg_solve_batch(gmg_handle* const* handles, int count, const double* const* f_dev, double* const* u_dev,
                     double tol, int maxit, gmg_info* infos);
 

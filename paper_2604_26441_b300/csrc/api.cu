@@ -1495,6 +1495,46 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
         }
         return worst;
     }
+    // ---- items that share a hierarchy (a handle and its clones) are solved
+    // together as multi-load chunks of up to 16 loads, owned by the chunk's
+    // first handle; the other items keep their own single-load loops
+    struct Chunk {
+        gmg_handle* owner;
+        std::vector<int> items;
+    };
+    std::vector<Chunk> chunks;
+    std::vector<int> chunk_of(count, -1), slot_of(count, -1);
+    {
+        std::vector<bool> seen(count, false);
+        for (int i = 0; i < count; ++i) {
+            if (seen[i]) continue;
+            std::vector<int> grp;
+            for (int j = i; j < count; ++j)
+                if (!seen[j] && hs[j]->E32 == hs[i]->E32 && hs[j]->L == hs[i]->L &&
+                    hs[j]->lev[0].maskp == hs[i]->lev[0].maskp) {
+                    grp.push_back(j);
+                    seen[j] = true;
+                }
+            bool ok = grp.size() >= 2;
+            for (int j : grp) ok = ok && multi_ok(hs[j], nullptr);
+            if (!ok) continue;
+            for (size_t a = 0; a < grp.size(); a += kLoads) {
+                Chunk c{hs[grp[a]], {}};
+                for (size_t b = a; b < std::min(grp.size(), a + kLoads); ++b) {
+                    chunk_of[grp[b]] = (int)chunks.size();
+                    slot_of[grp[b]] = (int)c.items.size();
+                    c.items.push_back(grp[b]);
+                }
+                if (c.items.size() < 2) {  // a lone remainder stays a single-load item
+                    chunk_of[c.items[0]] = slot_of[c.items[0]] = -1;
+                    continue;
+                }
+                chunks.push_back(c);
+            }
+        }
+    }
+    for (Chunk& c : chunks)
+        if (int rc = multi_workspace(c.owner); rc != GMG_OK) return rc;
     gmg_handle* h0 = hs[0];
     cudaStream_t s = h0->stream;
     std::vector<cudaStream_t> saved(count);
@@ -1507,45 +1547,63 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
     };
     const auto t0 = std::chrono::steady_clock::now();
     auto elapsed = [&]() { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); };
+    // each item's FP64 scalars: its own block, or its load slot in the chunk owner's
+    auto scd = [&](int i) -> double* {
+        return chunk_of[i] < 0 ? hs[i]->sc : chunks[chunk_of[i]].owner->mw->sc + slot_of[i] * SC_COUNT;
+    };
+    auto sch = [&](int i) -> double* {
+        return chunk_of[i] < 0 ? hs[i]->sc_host : chunks[chunk_of[i]].owner->mw->sc_host + slot_of[i] * SC_COUNT;
+    };
+    // the handle whose scratch an item's kernels use (partials, FP32 residual)
+    auto work = [&](int i) -> gmg_handle* { return chunk_of[i] < 0 ? hs[i] : chunks[chunk_of[i]].owner; };
     auto sync_all = [&]() -> int {
         PublishBatch pb{};
         pb.n = SC_COUNT;
         for (int i = 0; i < count; ++i) {
+            if (chunk_of[i] >= 0) continue;
             const int k = pb.count++;
             pb.sc[k] = hs[i]->sc;
             pb.out[k] = hs[i]->sc_map;
             pb.e0[k] = hs[i]->kerr;
             pb.e1[k] = hs[i]->use_fused ? hs[i]->cf.err : nullptr;
             pb.eout[k] = hs[i]->err_map;
-            if (pb.count == kPublishItems || i + 1 == count) {
+            if (pb.count == kPublishItems) {
                 launch_publish_batch(pb, s);
                 pb.count = 0;
             }
         }
+        launch_publish_batch(pb, s);
+        for (Chunk& c : chunks) multi_publish(c.owner);
         CU(cudaGetLastError());
         CU(cudaStreamSynchronize(s));
+        for (Chunk& c : chunks)
+            if (c.owner->mw->err_host[0] != 0) {
+                cudaMemsetAsync(c.owner->kerr, 0, sizeof(int), s);
+                cudaStreamSynchronize(s);
+                return fail(GMG_TIMEOUT, "batch: a TMA wait of the multi-load level-0 operator gave up");
+            }
         return GMG_OK;
     };
     std::vector<int> state(count, 0);  // 0: active, 1: done
     std::vector<double> nf(count, 0.0);
+    std::vector<bool> cold(count, false);
     for (int i = 0; i < count; ++i) infos[i] = gmg_info{};
     for (int i = 0; i < count; ++i)
         if (int rc = clear_pads(hs[i]); rc != GMG_OK) { restore(); return rc; }
     // ---- norms, nonzero count of u, fixed DOFs of u to 0
     for (int i = 0; i < count; ++i) {
-        gmg_handle* h = hs[i];
+        gmg_handle* h = work(i);
         const Level& l0 = h->lev[0];
         launch_mask_u64(u[i], l0.mask, l0.nn, h->partials, s);
-        launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_UNZ, FIN_NONE, s);
+        launch_finalize(h->partials, vec_grid_blocks(), scd(i), SC_UNZ, FIN_NONE, s);
         launch_dot_f64_masked(f[i], f[i], l0.mask, l0.nn, h->partials, s);
-        launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_FF, FIN_NONE, s);
+        launch_finalize(h->partials, vec_grid_blocks(), scd(i), SC_FF, FIN_NONE, s);
     }
     if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
     bool need_rel = false;
     for (int i = 0; i < count; ++i) {
-        gmg_handle* h = hs[i];
-        const Level& l0 = h->lev[0];
-        const double ff = h->sc_host[SC_FF];
+        const Level& l0 = hs[i]->lev[0];
+        const double ff = sch(i)[SC_FF];
         if (!(ff > 0.0)) {
             state[i] = 1;
             if (!std::isfinite(ff)) { infos[i].status = GMG_NONFINITE; infos[i].rel_residual = NAN; }
@@ -1553,21 +1611,41 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
             continue;
         }
         nf[i] = std::sqrt(ff);
-        if (h->sc_host[SC_UNZ] == 0.0) {
+        cold[i] = sch(i)[SC_UNZ] == 0.0;
+        if (cold[i]) infos[i].rel_residual = 1.0;
+        else need_rel = true;
+    }
+    // initial residuals: single items into their own r, chunks into their load slots
+    for (int i = 0; i < count; ++i) {
+        if (chunk_of[i] >= 0 || state[i] != 0) continue;
+        gmg_handle* h = hs[i];
+        const Level& l0 = h->lev[0];
+        if (cold[i]) {
             launch_cast_masked(f[i], l0, h->r, s);
-            infos[i].rel_residual = 1.0;
         } else {
-            launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, l0.px, h->sc, h->partials,
-                                h->gh64, s);
+            launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, l0.px, h->sc,
+                                h->partials, h->gh64, s);
             launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
-            need_rel = true;
+        }
+    }
+    for (Chunk& c : chunks) {
+        const int nl = (int)c.items.size();
+        const double* fc[kLoads] = {};
+        bool cc[kLoads] = {};
+        for (int l = 0; l < nl; ++l) {
+            fc[l] = f[c.items[l]];
+            cc[l] = state[c.items[l]] == 0 && cold[c.items[l]];
+        }
+        multi_cast(c.owner, nl, fc, cc);
+        for (int l = 0; l < nl; ++l) {
+            const int i = c.items[l];
+            if (state[i] == 0 && !cold[i]) multi_true_residual(c.owner, l, f[i], u[i], true);
         }
     }
     if (need_rel) {
         if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
         for (int i = 0; i < count; ++i)
-            if (state[i] == 0 && hs[i]->sc_host[SC_UNZ] != 0.0)
-                infos[i].rel_residual = std::sqrt(hs[i]->sc_host[SC_TRR]) / nf[i];
+            if (state[i] == 0 && !cold[i]) infos[i].rel_residual = std::sqrt(sch(i)[SC_TRR]) / nf[i];
     }
     for (int i = 0; i < count; ++i)
         if (state[i] == 0) {
@@ -1576,12 +1654,16 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
             if (!std::isfinite(rel)) { infos[i].status = GMG_NONFINITE; state[i] = 1; }
             else if (rel < tol) { infos[i].status = GMG_OK; state[i] = 1; }
         }
-    // ---- one graph for every active item: independent branches, each the
-    // device-resident PCG loop of its handle and iterate (the per-level lower
-    // V-cycle: concurrent cooperative kernels could not all be co-resident)
+    // ---- one graph: independent branches, each the device-resident PCG loop of
+    // a single item or of a chunk (the per-level lower V-cycle: concurrent
+    // cooperative kernels could not all be co-resident)
+    std::vector<bool> chunk_live(chunks.size(), false);
+    for (size_t c = 0; c < chunks.size(); ++c)
+        for (int i : chunks[c].items) chunk_live[c] = chunk_live[c] || state[i] == 0;
     std::vector<std::pair<const gmg_handle*, const double*>> key;
     for (int i = 0; i < count; ++i)
-        if (state[i] == 0) key.emplace_back(hs[i], u[i]);
+        if ((chunk_of[i] < 0 && state[i] == 0) || (chunk_of[i] >= 0 && chunk_live[chunk_of[i]]))
+            key.emplace_back(hs[i], u[i]);
     if (!key.empty()) {
         if (key != h0->batch_key || !h0->batch_exec) {
             if (h0->batch_exec) cudaGraphExecDestroy(h0->batch_exec);
@@ -1594,12 +1676,21 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
             cudaGraph_t g = nullptr;
             bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
             for (int i = 0; i < count && ok; ++i) {
-                if (state[i] != 0) continue;
+                if (chunk_of[i] >= 0 || state[i] != 0) continue;
                 unsigned long long pre = 0, bod = 0;
                 const bool fused = hs[i]->use_fused;
                 hs[i]->use_fused = false;
                 ok = capture_loop(hs[i], u[i], g, h0->cap_stream, pre, bod);
                 hs[i]->use_fused = fused;
+                h0->batch_counts.emplace_back(pre, bod);
+            }
+            for (size_t c = 0; c < chunks.size() && ok; ++c) {
+                if (!chunk_live[c]) continue;
+                double* uc[kLoads] = {};
+                const int nl = (int)chunks[c].items.size();
+                for (int l = 0; l < nl; ++l) uc[l] = u[chunks[c].items[l]];
+                unsigned long long pre = 0, bod = 0;
+                ok = multi_capture_loop(chunks[c].owner, uc, nl, g, h0->cap_stream, pre, bod);
                 h0->batch_counts.emplace_back(pre, bod);
             }
             cudaGraphExec_t ex = nullptr;
@@ -1616,42 +1707,70 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
             h0->batch_key = key;
         }
         for (int i = 0; i < count; ++i) {
-            if (state[i] != 0) continue;
-            double* sch = hs[i]->sc_host;
-            sch[SC_IT] = 0.0;
-            sch[SC_TOL] = tol;
-            sch[SC_MAXIT] = (double)maxit;
-            sch[SC_NF] = nf[i];
-            launch_set_scalars(hs[i]->sc + SC_IT, 4, sch[SC_IT], sch[SC_TOL], sch[SC_MAXIT], sch[SC_NF], s);
+            if (chunk_of[i] >= 0 || state[i] != 0) continue;
+            double* sh = hs[i]->sc_host;
+            sh[SC_IT] = 0.0;
+            sh[SC_TOL] = tol;
+            sh[SC_MAXIT] = (double)maxit;
+            sh[SC_NF] = nf[i];
+            launch_set_scalars(hs[i]->sc + SC_IT, 4, sh[SC_IT], sh[SC_TOL], sh[SC_MAXIT], sh[SC_NF], s);
+        }
+        for (size_t c = 0; c < chunks.size(); ++c) {
+            const int nl = (int)chunks[c].items.size();
+            double nfc[kLoads] = {};
+            bool act[kLoads] = {};
+            for (int l = 0; l < nl; ++l) {
+                nfc[l] = nf[chunks[c].items[l]];
+                act[l] = state[chunks[c].items[l]] == 0;
+            }
+            multi_set_loop_scalars(chunks[c].owner, nl, tol, maxit, nfc, act);
         }
         CU(cudaGraphLaunch(h0->batch_exec, s));
         if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
+        // launches: per single item and per chunk (its longest-running load)
+        {
+            size_t q = 0;
+            for (int i = 0; i < count; ++i) {
+                if (chunk_of[i] >= 0 || state[i] != 0) continue;
+                const int k = (int)hs[i]->sc_host[SC_IT];
+                note_launch(h0->batch_counts[q].first + h0->batch_counts[q].second * (unsigned long long)std::max(0, k - 1));
+                ++q;
+            }
+            for (size_t c = 0; c < chunks.size(); ++c) {
+                if (!chunk_live[c]) continue;
+                int k = 0;
+                for (int i : chunks[c].items) k = std::max(k, (int)sch(i)[SC_IT]);
+                note_launch(h0->batch_counts[q].first + h0->batch_counts[q].second * (unsigned long long)std::max(0, k - 1));
+                ++q;
+            }
+        }
         // FP64 true residual of every item that left its loop
-        size_t q = 0;
         for (int i = 0; i < count; ++i) {
             if (state[i] != 0) continue;
-            gmg_handle* h = hs[i];
-            const Level& l0 = h->lev[0];
-            const int k = (int)h->sc_host[SC_IT];
-            note_launch(h0->batch_counts[q].first + h0->batch_counts[q].second * (unsigned long long)std::max(0, k - 1));
-            ++q;
-            infos[i].iterations = k;
-            infos[i].rel_residual_recursive = std::sqrt(h->sc_host[SC_RR]) / nf[i];
-            if (!std::isfinite(infos[i].rel_residual_recursive) || !std::isfinite(h->sc_host[SC_ALPHA])) {
+            const double* sh = sch(i);
+            infos[i].iterations = (int)sh[SC_IT];
+            infos[i].rel_residual_recursive = std::sqrt(sh[SC_RR]) / nf[i];
+            if (!std::isfinite(infos[i].rel_residual_recursive) || !std::isfinite(sh[SC_ALPHA])) {
                 infos[i].status = GMG_NONFINITE;
                 infos[i].rel_residual = infos[i].rel_residual_recursive;
                 state[i] = 1;
                 continue;
             }
-            launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, l0.px, h->sc, h->partials,
-                                h->gh64, s);
-            launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
+            if (chunk_of[i] >= 0) {
+                multi_true_residual(chunks[chunk_of[i]].owner, slot_of[i], f[i], u[i], false);
+            } else {
+                gmg_handle* h = hs[i];
+                const Level& l0 = h->lev[0];
+                launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, l0.px, h->sc,
+                                    h->partials, h->gh64, s);
+                launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
+            }
         }
         if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
         for (int i = 0; i < count; ++i) {
             if (state[i] != 0) continue;
             gmg_handle* h = hs[i];
-            const double rel = std::sqrt(h->sc_host[SC_TRR]) / nf[i];
+            const double rel = std::sqrt(sch(i)[SC_TRR]) / nf[i];
             infos[i].rel_residual = rel;
             state[i] = 1;
             if (!std::isfinite(rel)) infos[i].status = GMG_NONFINITE;

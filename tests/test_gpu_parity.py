@@ -710,10 +710,13 @@ def _batch_problems():
 
 
 def test_batch_matches_single_solves():
+    """Clones of one hierarchy run as one multi-load chunk: per item the same
+    status and iteration count as a single solve, iterates within rounding of
+    it, and bitwise the answers of gmg_solve_multi on the same loads."""
     from paper_2604_26441_b300 import gmg
     opts = dict(smoother="chebyshev", degree=3, coarse_smoother=None, coarse_degree=None, omega=0.5,
                 coarse_omega=None)
-    solvers, fs, ref = [], [], []
+    solvers, fs, ref, multi = [], [], [], []
     for rho, levels, loads in _batch_problems():
         base = gpu_solver(rho, 3.0, levels=levels, **opts)
         for k, load in enumerate(loads):
@@ -723,11 +726,14 @@ def test_batch_matches_single_solves():
         for load in loads:
             u, info = single.solve(_t(load, torch.float64))
             ref.append((u.cpu().numpy(), info))
+        um, im = single.solve_multi([_t(load, torch.float64) for load in loads])
+        multi += [(u.cpu().numpy(), i) for u, i in zip(um, im)]
     us, infos = gmg.solve_batch(solvers, fs)
-    for (u_ref, info_ref), u, info in zip(ref, us, infos):
+    for (u_ref, info_ref), (u_m, info_m), u, info in zip(ref, multi, us, infos):
         assert info["status"] == 0 and info["rel_residual"] < 1e-6
-        assert info["iterations"] == info_ref["iterations"]
-        assert np.array_equal(u.cpu().numpy(), u_ref)
+        assert info["iterations"] == info_ref["iterations"] == info_m["iterations"]
+        assert rel_l2(u.cpu().numpy(), u_ref) < 1e-5
+        assert np.array_equal(u.cpu().numpy(), u_m)
     # the captured graph is replayed for the same handles and iterates
     first = [u.clone() for u in us]
     for u in us:
@@ -741,6 +747,25 @@ def test_batch_matches_single_solves():
     r = loads[-1] - fem.matfree_apply(fem.Grid(nx, ny, nz), fem.moduli(rho, 3.0), fem.element_stiffness(0.3), u)
     free = fem.free_dofs(inputs.clamp_xmin_mask(nx, ny, nz))
     assert np.linalg.norm(r[free]) / np.linalg.norm(loads[-1][free]) < 1e-6
+
+
+def test_batch_of_distinct_grids_equals_single_solves():
+    """Handles that share no hierarchy keep their own single-load loops as
+    graph branches: bitwise the iterates of gmg_solve."""
+    from paper_2604_26441_b300 import gmg
+    opts = dict(smoother="chebyshev", degree=3, coarse_smoother=None, coarse_degree=None, omega=0.5,
+                coarse_omega=None)
+    solvers, fs, ref = [], [], []
+    for rho, levels, loads in _batch_problems():
+        solvers.append(gpu_solver(rho, 3.0, levels=levels, **opts))
+        fs.append(_t(loads[1], torch.float64))
+        single = gpu_solver(rho, 3.0, levels=levels, **opts, fused_coarse_nodes=0)
+        u, info = single.solve(_t(loads[1], torch.float64))
+        ref.append((u.cpu().numpy(), info))
+    us, infos = gmg.solve_batch(solvers, fs)
+    for (u_ref, info_ref), u, info in zip(ref, us, infos):
+        assert info["status"] == 0 and info["iterations"] == info_ref["iterations"]
+        assert np.array_equal(u.cpu().numpy(), u_ref)
 
 
 @pytest.mark.parametrize("cfg_name", ["c1", "c2"])
