@@ -1554,8 +1554,6 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
     auto sch = [&](int i) -> double* {
         return chunk_of[i] < 0 ? hs[i]->sc_host : chunks[chunk_of[i]].owner->mw->sc_host + slot_of[i] * SC_COUNT;
     };
-    // the handle whose scratch an item's kernels use (partials, FP32 residual)
-    auto work = [&](int i) -> gmg_handle* { return chunk_of[i] < 0 ? hs[i] : chunks[chunk_of[i]].owner; };
     auto sync_all = [&]() -> int {
         PublishBatch pb{};
         pb.n = SC_COUNT;
@@ -1590,14 +1588,28 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
     for (int i = 0; i < count; ++i) infos[i] = gmg_info{};
     for (int i = 0; i < count; ++i)
         if (int rc = clear_pads(hs[i]); rc != GMG_OK) { restore(); return rc; }
+    // the loads and iterates of a chunk, in slot order
+    auto chunk_vecs = [&](const Chunk& c, const double** fc, double** uc) {
+        for (size_t l = 0; l < c.items.size(); ++l) {
+            fc[l] = f[c.items[l]];
+            uc[l] = u[c.items[l]];
+        }
+    };
     // ---- norms, nonzero count of u, fixed DOFs of u to 0
     for (int i = 0; i < count; ++i) {
-        gmg_handle* h = work(i);
+        if (chunk_of[i] >= 0) continue;
+        gmg_handle* h = hs[i];
         const Level& l0 = h->lev[0];
         launch_mask_u64(u[i], l0.mask, l0.nn, h->partials, s);
-        launch_finalize(h->partials, vec_grid_blocks(), scd(i), SC_UNZ, FIN_NONE, s);
+        launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_UNZ, FIN_NONE, s);
         launch_dot_f64_masked(f[i], f[i], l0.mask, l0.nn, h->partials, s);
-        launch_finalize(h->partials, vec_grid_blocks(), scd(i), SC_FF, FIN_NONE, s);
+        launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_FF, FIN_NONE, s);
+    }
+    for (Chunk& c : chunks) {
+        const double* fc[kLoads] = {};
+        double* uc[kLoads] = {};
+        chunk_vecs(c, fc, uc);
+        multi_norms(c.owner, (int)c.items.size(), fc, uc);
     }
     if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
     bool need_rel = false;
@@ -1757,7 +1769,7 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
                 continue;
             }
             if (chunk_of[i] >= 0) {
-                multi_true_residual(chunks[chunk_of[i]].owner, slot_of[i], f[i], u[i], false);
+                continue;  // one launch per chunk below
             } else {
                 gmg_handle* h = hs[i];
                 const Level& l0 = h->lev[0];
@@ -1765,6 +1777,13 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
                                     h->partials, h->gh64, s);
                 launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
             }
+        }
+        for (size_t c = 0; c < chunks.size(); ++c) {
+            if (!chunk_live[c]) continue;
+            const double* fc[kLoads] = {};
+            double* uc[kLoads] = {};
+            chunk_vecs(chunks[c], fc, uc);
+            multi_true_residuals(chunks[c].owner, (int)chunks[c].items.size(), fc, uc);
         }
         if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
         for (int i = 0; i < count; ++i) {

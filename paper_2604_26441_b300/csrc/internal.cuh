@@ -175,6 +175,7 @@ struct MultiWork {
     int pstride = 0;
     float* Ahi = nullptr;        // coarsest inverse split into FP32 hi + lo (double-float apply)
     float* Alo = nullptr;
+    float* bc = nullptr;         // [nL][kLoads] gathered coarsest right-hand sides
     void* pinned = nullptr;      // host-mapped mirror of sc and the sticky error words
     double* sc_host = nullptr;
     double* sc_map = nullptr;
@@ -427,6 +428,14 @@ void launch_fine_tc(int passes, int dot, const FineArgs& a, cudaStream_t s);
 // Host: the BF16 hi/lo mode-to-corner operand of the tensor-core smoother from G.
 void build_tc_operand(const double g[72], uint16_t out[2048]);
 int resid64_grid_blocks(int nx, int ny, int nz);
+// The FP64 residual of nl <= kLoads loads in one launch (no vector output):
+// ||f_l - K u_l||^2 partials of load l at partial[l * pstride ...], its grid
+// (blocks per load) from resid64_grid_blocks_multi; sc: the loads' scalar
+// blocks (SC_COUNT apart, SC_UNZ read).
+int resid64_grid_blocks_multi(int nx, int ny, int nz, int nl);
+void launch_fine_resid64_multi(int nx, int ny, int nz, const double* E, const uint8_t* mask, int nl,
+                               const double* const* f, const double* const* u, const double* sc, double* partial,
+                               int pstride, const GHat64& G, cudaStream_t s);
 void launch_fine_smooth0(const FineArgs& a, cudaStream_t s);
 // inv0[n] = 1 / (kd * sum of the moduli of the elements around node n), once at set-up.
 void launch_fine_inv0(int nx, int ny, int nz, int px, const float* E, float kd, float* inv0, cudaStream_t s);
@@ -575,7 +584,8 @@ void multi_drop_loops(gmg_handle* h);
 // True when h's options and hierarchy suit the multi-load path (else *why says why).
 bool multi_ok(const gmg_handle* h, std::string* why);
 // Asynchronous per-load pieces, writing load l's scalar block h->mw->sc + l * SC_COUNT.
-void multi_norms(gmg_handle* h, int l, const double* f, double* u);
+void multi_norms(gmg_handle* h, int nl, const double* const* f, double* const* u);
+void multi_true_residuals(gmg_handle* h, int nl, const double* const* f, const double* const* u);
 void multi_cast(gmg_handle* h, int nl, const double* const* f, const bool* cold);
 void multi_true_residual(gmg_handle* h, int l, const double* f, const double* u, bool into_r);
 // Per-load loop scalars (iteration count 0, tolerance, cap, ||f||, active flag) of all 16 slots.

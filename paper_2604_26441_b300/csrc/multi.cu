@@ -99,6 +99,43 @@ __global__ void __launch_bounds__(kMT) k_mcast(const __grid_constant__ F64In f, 
     }
 }
 
+// Per load: fixed DOFs of u_l to 0, the nonzero count of u_l (partial) and
+// ||f_l||^2 over the free DOFs (partial2), in the dense numbering.  A block of
+// 16 warps takes 32 consecutive nodes, warp l load l.
+__global__ void __launch_bounds__(32 * kLoads) k_mnorms(const __grid_constant__ F64Out u,
+                                                       const __grid_constant__ F64In f, int nl, const uint8_t* mask,
+                                                       long long nn, double* partial, double* partial2, int pstride) {
+    pdl_entry();
+    const int l = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double cnt = 0.0, ff = 0.0;
+    if (l < nl) {
+        double* ul = u.p[l];
+        const double* fl = f.p[l];
+        for (long long n = blockIdx.x * 32LL + lane; n < nn; n += (long long)gridDim.x * 32) {
+            const uint8_t m = mask[n];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (fixed_bit(m, c)) {
+                    ul[3 * n + c] = 0.0;
+                } else {
+                    if (ul[3 * n + c] != 0.0) cnt += 1.0;
+                    const double fv = fl[3 * n + c];
+                    ff += fv * fv;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        ff += __shfl_down_sync(0xffffffffu, ff, o);
+    }
+    if (lane == 0) {
+        partial[(long long)l * pstride + blockIdx.x] = cnt;
+        partial2[(long long)l * pstride + blockIdx.x] = ff;
+    }
+}
+
 // Slot l of a multi-load vector from a single-load level-0 vector (padded rows).
 __global__ void k_mpack_slot(const float* v, long long nnp, int l, float* mv) {
     pdl_entry();
@@ -167,10 +204,11 @@ __global__ void __launch_bounds__(kMT) k_mfinalize(const double* partial, int n,
 }
 
 // ||r_l||^2 and the per-load convergence test of the device-resident loop
-// (k_finalize_check for each load still iterating); the while condition is
-// set while any load iterates.  One block, warp l takes load l.
+// (k_finalize_check for each load still iterating); the while condition
+// (set_cond; the host-driven loop reads the active flags instead) is set while
+// any load iterates.  One block, warp l takes load l.
 __global__ void __launch_bounds__(32 * kLoads) k_mfinalize_check(const double* partial, int n, int pstride, double* sc,
-                                                                 cudaGraphConditionalHandle cond) {
+                                                                 cudaGraphConditionalHandle cond, int set_cond) {
     pdl_entry();
     __shared__ int go_any[kLoads];
     const int l = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -197,30 +235,34 @@ __global__ void __launch_bounds__(32 * kLoads) k_mfinalize_check(const double* p
         int any = 0;
 #pragma unroll
         for (int q = 0; q < kLoads; ++q) any |= go_any[q];
-        cudaGraphSetConditional(cond, any ? 1u : 0u);
+        if (set_cond) cudaGraphSetConditional(cond, any ? 1u : 0u);
     }
 }
 
 // u_l (dense, FP64) += alpha_l p, r -= alpha_l q, partial ||r_l||^2, for the
-// loads still iterating (the others keep their values).
-__global__ void __launch_bounds__(kMT) k_mpcg_update(const __grid_constant__ F64Out u, int nl, float* r, const float* p, const float* q, int NX,
-                                                     int px, long long nnp, const double* sc, double* partial,
-                                                     int pstride) {
+// loads still iterating (the others keep their values).  A block of 16 warps
+// takes 32 consecutive nodes, warp l load l: the FP64 iterate of a load is
+// read and written in 768-byte runs, and the records of a node's 16 loads are
+// read by the 16 warps of the same block.
+constexpr int kPcgThreads = 32 * kLoads;
+__global__ void __launch_bounds__(kPcgThreads) k_mpcg_update(const __grid_constant__ F64Out u, int nl, float* r,
+                                                             const float* p, const float* q, int NX, int px,
+                                                             long long nnp, const double* sc, double* partial,
+                                                             int pstride) {
     pdl_entry();
-    const int l = threadIdx.x & 15;
+    const int l = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double* c = sc + l * SC_COUNT;
     const bool act = l < nl && c[SC_ACT] != 0.0;
-    const double alpha = act ? c[SC_ALPHA] : 0.0;
-    const float af = (float)alpha;
     DSAcc acc;
     if (act) {
+        const double alpha = c[SC_ALPHA];
+        const float af = (float)alpha;
         double* ul = u.p[l];
-        const long long nrec = nnp * kLoads;
-        for (long long qi = blockIdx.x * (long long)kMT + threadIdx.x; qi < nrec; qi += (long long)gridDim.x * kMT) {
-            const long long n = qi >> 4;
+        for (long long n = blockIdx.x * 32LL + lane; n < nnp; n += (long long)gridDim.x * 32) {
             const long long row = n / px;
             const int i = (int)(n - row * px);
             if (i >= NX) continue;  // pad node: stays 0
+            const long long qi = n * kLoads + l;
             const float4 pv = reinterpret_cast<const float4*>(p)[qi];
             const float4 qv = reinterpret_cast<const float4*>(q)[qi];
             float4 rv = reinterpret_cast<float4*>(r)[qi];
@@ -237,8 +279,10 @@ __global__ void __launch_bounds__(kMT) k_mpcg_update(const __grid_constant__ F64
             reinterpret_cast<float4*>(r)[qi] = rv;
         }
     }
-    const double s = block_sum_load<kMT>(acc.value(), threadIdx.x);
-    if (threadIdx.x < kLoads) partial[(long long)threadIdx.x * pstride + blockIdx.x] = s;
+    double v = acc.value();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) partial[(long long)l * pstride + blockIdx.x] = v;
 }
 
 // p = z + beta_l p for the loads still iterating.
@@ -274,6 +318,8 @@ __global__ void k_mset_loop(double* sc, LoopScalars v) {
     c[SC_MAXIT] = v.maxit;
     c[SC_NF] = v.nf[l];
     c[SC_ACT] = v.act[l];
+    // every later residual of an iterating load sees u != 0 (the PCG updates)
+    if (v.act[l] != 0.0) c[SC_UNZ] = 1.0;
 }
 
 // ---- level 0: first smoother step from zero: x = c_a D^-1 b (d = x) -----------
@@ -311,23 +357,28 @@ struct MBsrArgs {
     int step;
 };
 
-// y = K^l x for all 16 loads of a node: each operator block is loaded once and
-// applied to the 16 records of the neighbour (same branch-free neighbour
-// handling as k_bsr: clamped indices, zero-stored forward blocks outside the
-// grid, backward terms scaled by 0 outside it).
-template <int MODE>
+// y = K^l x on multi-load vectors.  16 / LQ threads share a node, each taking
+// LQ of its loads: the node's operator blocks are read once per thread (the
+// reads of a node's threads hit the same L1 line) and applied to the thread's
+// LQ records of each neighbour (same branch-free neighbour handling as k_bsr:
+// clamped indices, zero-stored forward blocks outside the grid, backward terms
+// scaled by 0 outside it).  LQ = 4 on large levels; LQ = 1 on small ones,
+// where a thread per record gives the latency-bound kernel more warps.
+template <int MODE, int kBsrLq>
 __global__ void __launch_bounds__(128) k_mbsr(MBsrArgs a) {
     pdl_entry();
-    const int n = blockIdx.x * 128 + threadIdx.x;
+    constexpr int TPN = kLoads / kBsrLq;  // threads per node
+    const long long t = blockIdx.x * 128LL + threadIdx.x;
+    const int n = (int)(t / TPN), g = (int)(t % TPN);
     if (n >= a.nn) return;
     const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
     const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
     const long long N = a.ps;
-    const float4* X = reinterpret_cast<const float4*>(a.xin);
-    float y[kLoads][3];
+    const float4* X = reinterpret_cast<const float4*>(a.xin) + kBsrLq * g;
+    float y[kBsrLq][3];
 #pragma unroll
-    for (int l = 0; l < kLoads; ++l) y[l][0] = y[l][1] = y[l][2] = 0.f;
-#pragma unroll 1
+    for (int l = 0; l < kBsrLq; ++l) y[l][0] = y[l][1] = y[l][2] = 0.f;
+#pragma unroll
     for (int u = 0; u < 14; ++u) {
         const int sl = 13 + u;
         const int dx = sl % 3 - 1, dy = (sl / 3) % 3 - 1, dz = sl / 9 - 1;
@@ -340,7 +391,7 @@ __global__ void __launch_bounds__(128) k_mbsr(MBsrArgs a) {
         for (int e = 0; e < 9; ++e) A[e] = __ldg(Ap + e * N);
         const float4* xf = X + (long long)mf * kLoads;
 #pragma unroll
-        for (int l = 0; l < kLoads; ++l) {
+        for (int l = 0; l < kBsrLq; ++l) {
             const float4 v = __ldg(xf + l);
             y[l][0] = fmaf(A[0], v.x, fmaf(A[1], v.y, fmaf(A[2], v.z, y[l][0])));
             y[l][1] = fmaf(A[3], v.x, fmaf(A[4], v.y, fmaf(A[5], v.z, y[l][1])));
@@ -356,7 +407,7 @@ __global__ void __launch_bounds__(128) k_mbsr(MBsrArgs a) {
             for (int e = 0; e < 9; ++e) B[e] = wgt * __ldg(Bp + e * N);
             const float4* xb = X + (long long)mb * kLoads;
 #pragma unroll
-            for (int l = 0; l < kLoads; ++l) {
+            for (int l = 0; l < kBsrLq; ++l) {
                 const float4 w = __ldg(xb + l);
                 y[l][0] = fmaf(B[0], w.x, fmaf(B[3], w.y, fmaf(B[6], w.z, y[l][0])));
                 y[l][1] = fmaf(B[1], w.x, fmaf(B[4], w.y, fmaf(B[7], w.z, y[l][1])));
@@ -366,15 +417,15 @@ __global__ void __launch_bounds__(128) k_mbsr(MBsrArgs a) {
     }
     const uint8_t msk = a.mask[n];
     const bool f0 = !fixed_bit(msk, 0), f1 = !fixed_bit(msk, 1), f2 = !fixed_bit(msk, 2);
-    const long long base = (long long)n * kLoads;
+    const long long base = (long long)n * kLoads + kBsrLq * g;
     if (MODE == FM_APPLY) {
 #pragma unroll
-        for (int l = 0; l < kLoads; ++l)
+        for (int l = 0; l < kBsrLq; ++l)
             reinterpret_cast<float4*>(a.out)[base + l] =
                 make_float4(f0 ? y[l][0] : 0.f, f1 ? y[l][1] : 0.f, f2 ? y[l][2] : 0.f, 0.f);
     } else if (MODE == FM_RESID) {
 #pragma unroll
-        for (int l = 0; l < kLoads; ++l) {
+        for (int l = 0; l < kBsrLq; ++l) {
             const float4 bv = reinterpret_cast<const float4*>(a.b)[base + l];
             reinterpret_cast<float4*>(a.out)[base + l] = make_float4(
                 f0 ? bv.x - y[l][0] : 0.f, f1 ? bv.y - y[l][1] : 0.f, f2 ? bv.z - y[l][2] : 0.f, 0.f);
@@ -383,7 +434,7 @@ __global__ void __launch_bounds__(128) k_mbsr(MBsrArgs a) {
         const float cd = (float)a.coef[2 * a.step], ca = (float)a.coef[2 * a.step + 1];
         const float i0 = a.invdiag[3 * n], i1 = a.invdiag[3 * n + 1], i2 = a.invdiag[3 * n + 2];
 #pragma unroll
-        for (int l = 0; l < kLoads; ++l) {
+        for (int l = 0; l < kBsrLq; ++l) {
             const float4 bv = reinterpret_cast<const float4*>(a.b)[base + l];
             const float4 xv = reinterpret_cast<const float4*>(a.xin)[base + l];
             float d0 = ca * i0 * (bv.x - y[l][0]), d1 = ca * i1 * (bv.y - y[l][1]), d2 = ca * i2 * (bv.z - y[l][2]);
@@ -511,54 +562,58 @@ __global__ void __launch_bounds__(kMT) k_mprolong_add(int fnx, int fny, int fnz,
 }
 
 // ---- coarsest level: x(l) = Ainv b(l) on the free DOFs, 0 on fixed ones ---------
-// Ainv = Ahi + Alo (FP32 parts of the FP64 inverse); each product is split
-// exactly with an FMA and summed in double-float, so a row's sum carries ~44
-// significant bits.  A block takes 16 rows x 16 loads; the gathered right-hand
-// sides are staged in shared memory in chunks of kCoarseChunk free DOFs.
-constexpr int kCoarseChunk = 256;
-__global__ void __launch_bounds__(256) k_mcoarse(int nL, const int* free_idx, const float* Ahi, const float* Alo,
-                                                 const float* b, float* x, const uint8_t* mask, int n_nodes) {
+// k_mcoarse_gather packs the free entries of b as bc[j][l] (and zeroes the
+// fixed DOFs of x); k_mcoarse then forms x = Ainv bc with Ainv = Ahi + Alo
+// (FP32 parts of the FP64 inverse): each product is split exactly with an FMA
+// and summed in double-float, so a row's sum carries ~44 significant bits.  A
+// block takes 4 rows x 16 loads, each row's sum split over 4 interleaved
+// column slices that are added in a fixed order at the end.
+__global__ void __launch_bounds__(256) k_mcoarse_gather(int nL, const int* free_idx, const float* b, float* bc,
+                                                        float* x, const uint8_t* mask, int n_nodes) {
     pdl_entry();
-    __shared__ float bs[kCoarseChunk][kLoads];
-    const int tid = threadIdx.x, l = tid & 15;
-    // fixed DOFs of every load to 0 (the records' pads stay 0)
-    for (long long q = blockIdx.x * 256LL + tid; q < 3LL * n_nodes * kLoads; q += (long long)gridDim.x * 256) {
+    const long long stride = (long long)gridDim.x * 256;
+    for (long long q = blockIdx.x * 256LL + threadIdx.x; q < 3LL * n_nodes * kLoads; q += stride) {
         const long long rec = q / 3;
         const int c = (int)(q - rec * 3);
         if (fixed_bit(mask[rec >> 4], c)) x[rec * 4 + c] = 0.f;
     }
-    const int row = blockIdx.x * 16 + (tid >> 4);
-    const bool has_row = row < nL;
-    const float* ah = Ahi + (long long)(has_row ? row : 0) * nL;
-    const float* al = Alo + (long long)(has_row ? row : 0) * nL;
+    for (long long q = blockIdx.x * 256LL + threadIdx.x; q < (long long)nL * kLoads; q += stride) {
+        const int jj = (int)(q >> 4), ll = (int)(q & 15);
+        const int dof = free_idx[jj];
+        const int node = dof / 3, c = dof - 3 * (dof / 3);
+        bc[q] = b[GMG_B(((long long)node * kLoads + ll) * 4 + c, (long long)n_nodes * kNodeF, 531)];
+    }
+}
+
+constexpr int kCoarseRows = 4, kCoarseSlices = 4;
+__global__ void __launch_bounds__(256) k_mcoarse(int nL, const int* free_idx, const float* Ahi, const float* Alo,
+                                                 const float* bc, float* x, int n_nodes) {
+    pdl_entry();
+    __shared__ double part[kCoarseRows][kCoarseSlices][kLoads];
+    const int tid = threadIdx.x, l = tid & 15, sl = (tid >> 4) & 3, rr = tid >> 6;
+    const int row = blockIdx.x * kCoarseRows + rr;
     float hi = 0.f, lo = 0.f;
-    for (int j0 = 0; j0 < nL; j0 += kCoarseChunk) {
-        const int nj = min(kCoarseChunk, nL - j0);
-        __syncthreads();
-        for (int e = tid; e < nj * kLoads; e += 256) {
-            const int jj = e >> 4, ll = e & 15;
-            const int dof = free_idx[j0 + jj];
-            const int node = dof / 3, c = dof - 3 * (dof / 3);
-            bs[jj][ll] = b[GMG_B(((long long)node * kLoads + ll) * 4 + c, (long long)n_nodes * kNodeF, 531)];
-        }
-        __syncthreads();
-        if (has_row) {
-            for (int jj = 0; jj < nj; ++jj) {
-                const float a = __ldg(ah + j0 + jj), a2 = __ldg(al + j0 + jj), bv = bs[jj][l];
-                const float p = a * bv;
-                const float e = fmaf(a, bv, -p);
-                const float s = hi + p;
-                const float bb = s - hi;
-                const float t = (hi - (s - bb)) + (p - bb);
-                hi = s;
-                lo += t + fmaf(a2, bv, e);
-            }
+    if (row < nL) {
+        const float* ah = Ahi + (long long)row * nL;
+        const float* al = Alo + (long long)row * nL;
+        for (int j = sl; j < nL; j += kCoarseSlices) {
+            const float a = __ldg(ah + j), a2 = __ldg(al + j), bv = __ldg(bc + (long long)j * kLoads + l);
+            const float p = a * bv;
+            const float e = fmaf(a, bv, -p);
+            const float s = hi + p;
+            const float bb = s - hi;
+            const float t = (hi - (s - bb)) + (p - bb);
+            hi = s;
+            lo += t + fmaf(a2, bv, e);
         }
     }
-    if (has_row) {
+    part[rr][sl][l] = (double)hi + (double)lo;
+    __syncthreads();
+    if (sl == 0 && row < nL) {
+        const double v = ((part[rr][0][l] + part[rr][1][l]) + part[rr][2][l]) + part[rr][3][l];
         const int dof = free_idx[row];
         const int node = dof / 3, c = dof - 3 * (dof / 3);
-        x[GMG_B(((long long)node * kLoads + l) * 4 + c, (long long)n_nodes * kNodeF, 532)] = hi + lo;
+        x[GMG_B(((long long)node * kLoads + l) * 4 + c, (long long)n_nodes * kNodeF, 532)] = (float)v;
     }
 }
 
@@ -1046,12 +1101,20 @@ MBsrArgs mbsr_args(const Level& l, const MultiLevel& m) {
     return a;
 }
 
+constexpr int kBsrSmallLevel = 32768;  // nodes below which a thread takes one record
+
+template <int LQ>
+void launch_mbsr_lq(int mode, const MBsrArgs& a, cudaStream_t s) {
+    const dim3 g((unsigned)(((long long)a.nn * (kLoads / LQ) + 127) / 128));
+    if (mode == FM_APPLY) pdl_launch(k_mbsr<FM_APPLY, LQ>, g, dim3(128), 0, s, a);
+    else if (mode == FM_RESID) pdl_launch(k_mbsr<FM_RESID, LQ>, g, dim3(128), 0, s, a);
+    else pdl_launch(k_mbsr<FM_SMOOTH, LQ>, g, dim3(128), 0, s, a);
+}
+
 void launch_mbsr(int mode, const MBsrArgs& a, cudaStream_t s) {
     note_launch();
-    const dim3 g((unsigned)((a.nn + 127) / 128));
-    if (mode == FM_APPLY) pdl_launch(k_mbsr<FM_APPLY>, g, dim3(128), 0, s, a);
-    else if (mode == FM_RESID) pdl_launch(k_mbsr<FM_RESID>, g, dim3(128), 0, s, a);
-    else pdl_launch(k_mbsr<FM_SMOOTH>, g, dim3(128), 0, s, a);
+    if (a.nn < kBsrSmallLevel) launch_mbsr_lq<1>(mode, a, s);
+    else launch_mbsr_lq<4>(mode, a, s);
 }
 
 // ---- host side ----------------------------------------------------------------------
@@ -1088,7 +1151,6 @@ bool multi_eligible(const gmg_handle* h, std::string* why) {
     else if (o.outer != GMG_OUTER_PCG) r = "outer FGMRES";
     else if (o.ir_factor != 0.0) r = "iterative refinement";
     else if (o.fine_smoother != GMG_FINE_FP32) r = "a tensor-core fine smoother";
-    else if (!o.device_loop) r = "the host-driven loop";
     else if (o.cycle_index != 1) r = "a W-cycle";
     if (r && why) *why = r;
     return r == nullptr;
@@ -1125,7 +1187,10 @@ int multi_workspace(gmg_handle* h) {
     }
     w->pstride = kMBlocks;
     for (int nl = 1; nl <= kLoads; ++nl) w->pstride = std::max(w->pstride, mfine_blocks(l0.nx, l0.ny, l0.nz, nl));
-    if (int rc = malloc_dev(h, &w->partials, (size_t)kLoads * w->pstride); rc != GMG_OK) return bad(rc);
+    for (int nl = 1; nl <= kLoads; ++nl)
+        w->pstride = std::max(w->pstride, resid64_grid_blocks_multi(l0.nx, l0.ny, l0.nz, nl));
+    // two partial arrays of kLoads rows (the norms kernel fills both)
+    if (int rc = malloc_dev(h, &w->partials, (size_t)2 * kLoads * w->pstride); rc != GMG_OK) return bad(rc);
     if (int rc = malloc_dev(h, &w->sc, (size_t)kLoads * SC_COUNT); rc != GMG_OK) return bad(rc);
     if (cudaMemsetAsync(w->sc, 0, sizeof(double) * kLoads * SC_COUNT, s) != cudaSuccess)
         return bad(mfail(GMG_ERR_CUDA, "multi memset"));
@@ -1133,6 +1198,7 @@ int multi_workspace(gmg_handle* h) {
         const size_t nn2 = (size_t)h->nL * h->nL;
         if (int rc = malloc_dev(h, &w->Ahi, nn2); rc != GMG_OK) return bad(rc);
         if (int rc = malloc_dev(h, &w->Alo, nn2); rc != GMG_OK) return bad(rc);
+        if (int rc = malloc_dev(h, &w->bc, (size_t)h->nL * kLoads); rc != GMG_OK) return bad(rc);
         note_launch();
         k_split_inverse<<<kMBlocks, kMT, 0, s>>>(h->Ainv, (long long)nn2, w->Ahi, w->Alo);
     }
@@ -1277,10 +1343,12 @@ float* msmooth_pass(gmg_handle* h, int li, const float* b, float* cur, float* X,
 
 void launch_mcoarse(gmg_handle* h, const float* b, float* x) {
     const Level& l = h->lev[h->L - 1];
-    note_launch();
-    const int g = std::max(1, (h->nL + 15) / 16);
+    note_launch(2);
+    pdl_launch(k_mcoarse_gather, dim3(kMBlocks), dim3(256), 0, h->stream, h->nL, (const int*)h->free_idx, b,
+               h->mw->bc, x, (const uint8_t*)l.mask, (int)l.nn);
+    const int g = std::max(1, (h->nL + kCoarseRows - 1) / kCoarseRows);
     pdl_launch(k_mcoarse, dim3(g), dim3(256), 0, h->stream, h->nL, (const int*)h->free_idx, (const float*)h->mw->Ahi,
-               (const float*)h->mw->Alo, b, x, (const uint8_t*)l.mask, (int)l.nn);
+               (const float*)h->mw->Alo, (const float*)h->mw->bc, x, (int)l.nn);
 }
 
 void launch_mrestrict(const Level& f, const Level& c, const float* fine, float* coarse, cudaStream_t s) {
@@ -1324,18 +1392,20 @@ void mpcg_restart(gmg_handle* h, int nl) {
     launch_copy_f32(w.p, w.z, h->lev[0].nnp * kNodeF, h->stream);
 }
 
-void mpcg_step(gmg_handle* h, const F64Out& u, int nl, const cudaGraphConditionalHandle* cond) {
+// cond: inside the captured loop (sets the while condition); host_check: the
+// host-driven loop (the same per-load test, read back by the host).
+void mpcg_step(gmg_handle* h, const F64Out& u, int nl, const cudaGraphConditionalHandle* cond, bool host_check = false) {
     MultiWork& w = *h->mw;
     const Level& l0 = h->lev[0];
     cudaStream_t s = h->stream;
     mlevel_apply(h, 0, w.p, w.q, SC_PQ, FIN_ALPHA, nl);
     note_launch();
-    pdl_launch(k_mpcg_update, dim3(kMBlocks), dim3(kMT), 0, s, u, nl, w.r, (const float*)w.p, (const float*)w.q,
-               l0.nx + 1, l0.px, l0.nnp, (const double*)w.sc, w.partials, w.pstride);
+    pdl_launch(k_mpcg_update, dim3(kMBlocks), dim3(kPcgThreads), 0, s, u, nl, w.r, (const float*)w.p,
+               (const float*)w.q, l0.nx + 1, l0.px, l0.nnp, (const double*)w.sc, w.partials, w.pstride);
     note_launch();
-    if (cond)
+    if (cond || host_check)
         pdl_launch(k_mfinalize_check, dim3(1), dim3(32 * kLoads), 0, s, (const double*)w.partials, kMBlocks, w.pstride,
-                   w.sc, *cond);
+                   w.sc, cond ? *cond : cudaGraphConditionalHandle{}, cond ? 1 : 0);
     else
         pdl_launch(k_mfinalize, dim3(kLoads), dim3(kMT), 0, s, (const double*)w.partials, kMBlocks, w.pstride, w.sc,
                    (int)SC_RR, (int)FIN_NONE);
@@ -1408,14 +1478,36 @@ bool multi_capture_loop(gmg_handle* h, double* const* u, int nl, cudaGraph_t g, 
 }
 
 // ---- the pieces of a multi-load solve shared with gmg_solve_batch --------------------
-// Norms and nonzero counts of load l into its scalar block (asynchronous).
-void multi_norms(gmg_handle* h, int l, const double* f, double* u) {
+// Fixed DOFs of u_l to 0, nonzero counts of u_l and ||f_l||^2 of nl loads
+// into their scalar blocks (SC_UNZ, SC_FF), three launches (asynchronous).
+void multi_norms(gmg_handle* h, int nl, const double* const* f, double* const* u) {
+    MultiWork& w = *h->mw;
     const Level& l0 = h->lev[0];
-    double* sc = h->mw->sc + l * SC_COUNT;
-    launch_mask_u64(u, l0.mask, l0.nn, h->partials, h->stream);
-    launch_finalize(h->partials, vec_grid_blocks(), sc, SC_UNZ, FIN_NONE, h->stream);
-    launch_dot_f64_masked(f, f, l0.mask, l0.nn, h->partials, h->stream);
-    launch_finalize(h->partials, vec_grid_blocks(), sc, SC_FF, FIN_NONE, h->stream);
+    F64Out uo{};
+    F64In fi{};
+    for (int l = 0; l < nl; ++l) {
+        uo.p[l] = u[l];
+        fi.p[l] = f[l];
+    }
+    double* p2 = w.partials + (size_t)kLoads * w.pstride;
+    note_launch(3);
+    pdl_launch(k_mnorms, dim3(kMBlocks), dim3(32 * kLoads), 0, h->stream, uo, fi, nl, (const uint8_t*)l0.mask, l0.nn,
+               w.partials, p2, w.pstride);
+    pdl_launch(k_mfinalize, dim3(kLoads), dim3(kMT), 0, h->stream, (const double*)w.partials, kMBlocks, w.pstride,
+               w.sc, (int)SC_UNZ, (int)FIN_NONE);
+    pdl_launch(k_mfinalize, dim3(kLoads), dim3(kMT), 0, h->stream, (const double*)p2, kMBlocks, w.pstride, w.sc,
+               (int)SC_FF, (int)FIN_NONE);
+}
+
+// The FP64 true residual of loads 0..nl-1 into their SC_TRR, one launch.
+void multi_true_residuals(gmg_handle* h, int nl, const double* const* f, const double* const* u) {
+    MultiWork& w = *h->mw;
+    const Level& l0 = h->lev[0];
+    launch_fine_resid64_multi(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, nl, f, u, w.sc, w.partials, w.pstride, h->gh64,
+                              h->stream);
+    note_launch();
+    pdl_launch(k_mfinalize, dim3(kLoads), dim3(kMT), 0, h->stream, (const double*)w.partials,
+               resid64_grid_blocks_multi(l0.nx, l0.ny, l0.nz, nl), w.pstride, w.sc, (int)SC_TRR, (int)FIN_NONE);
 }
 
 // r(l) = f_l for the loads with cold[l] (0 for the others and loads >= nl).
@@ -1552,7 +1644,7 @@ int gmg_solve_multi(gmg_handle* h, int nl, const double* const* f, double* const
     };
     double* sch = w.sc_host;
     auto S = [&](int l, int slot) -> double& { return sch[l * SC_COUNT + slot]; };
-    for (int l = 0; l < nl; ++l) multi_norms(h, l, f[l], u[l]);
+    multi_norms(h, nl, f, u);
     MTRY(sync());
     std::vector<int> state(nl, 0);  // 0 active, 1 done
     std::vector<double> nf(nl, 0.0);
@@ -1592,7 +1684,22 @@ int gmg_solve_multi(gmg_handle* h, int nl, const double* const* f, double* const
         for (int l = 0; l < nl; ++l) act[l] = state[l] == 0;
         multi_set_loop_scalars(h, nl, tol, maxit, nf.data(), act);
     }
-    if (any) {
+    if (any && !h->opt.device_loop) {
+        // host-driven loop: the kernels of the captured loop, launched one by
+        // one, with the per-load test read back after every step
+        F64Out up{};
+        for (int l = 0; l < nl; ++l) up.p[l] = u[l];
+        mpcg_restart(h, nl);
+        mpcg_step(h, up, nl, nullptr, true);
+        while (true) {
+            MTRY(sync());
+            bool go = false;
+            for (int l = 0; l < nl; ++l) go = go || (state[l] == 0 && S(l, SC_ACT) != 0.0);
+            if (!go) break;
+            mpcg_direction(h, nl);
+            mpcg_step(h, up, nl, nullptr, true);
+        }
+    } else if (any) {
         // the captured loop for these iterates (cached per iterate list)
         std::vector<const double*> key(u, u + nl);
         MultiWork::Loop* lp = nullptr;
@@ -1629,6 +1736,8 @@ int gmg_solve_multi(gmg_handle* h, int nl, const double* const* f, double* const
         unsigned long long kmax = 0;
         for (int l = 0; l < nl; ++l) kmax = std::max<unsigned long long>(kmax, (unsigned long long)S(l, SC_IT));
         note_launch(lp->pre + lp->body * (kmax > 0 ? kmax - 1 : 0));
+    }
+    if (any) {
         for (int l = 0; l < nl; ++l) {
             if (state[l] != 0) continue;
             infos[l].iterations = (int)S(l, SC_IT);
@@ -1637,10 +1746,9 @@ int gmg_solve_multi(gmg_handle* h, int nl, const double* const* f, double* const
                 infos[l].status = GMG_NONFINITE;
                 infos[l].rel_residual = infos[l].rel_residual_recursive;
                 state[l] = 1;
-                continue;
             }
-            multi_true_residual(h, l, f[l], u[l], false);
         }
+        multi_true_residuals(h, nl, f, u);
         MTRY(sync());
         for (int l = 0; l < nl; ++l) {
             if (state[l] != 0) continue;

@@ -82,16 +82,32 @@ __device__ __forceinline__ void face_diffs(df u00, df u10, df u01, df u11, df q[
     q[3] = dx1 - dx0;
 }
 
+// Operands of one launch: one load (single-load calls), or up to kLoads loads
+// whose blocks share the grid's z dimension (gz chunks per load).
+struct ResidLoads {
+    const double* f[kLoads];
+    const double* u[kLoads];
+    int gz;
+    int pstride;  // partial sums of load l at partial[l * pstride ...]
+};
+
 __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,
-                                                   const double* f, const double* uvec, double* r64, float* r32,
+                                                   const __grid_constant__ ResidLoads L, double* r64, float* r32,
                                                    int px, const double* sc, double* partial, GHatDF G, int zchunk) {
     pdl_entry();
+    // load l of a multi-load launch: grid.z = L.gz chunks x loads, its own
+    // f, u, scalar block and partial range
+    const int l = (int)(blockIdx.z / (unsigned)L.gz), bz = (int)(blockIdx.z % (unsigned)L.gz);
+    const double* f = L.f[l];
+    const double* uvec = L.u[l];
+    sc += l * SC_COUNT;
+    partial += (long long)l * L.pstride;
     __shared__ df sp[2][BY + 1][(BX + 1) * 3];
     __shared__ df sx[2][BY][BX * 3];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
     const int NX = nx + 1, NY = ny + 1, NZ = nz + 1, NXY = NX * NY, NEXY = nx * ny;
     const int x0 = blockIdx.x * (BX - 1), y0 = blockIdx.y * (BY - 1);
-    const int k0 = blockIdx.z * zchunk, k1 = min(k0 + zchunk, NZ);
+    const int k0 = bz * zchunk, k1 = min(k0 + zchunk, NZ);
     const int cx = x0 - 1 + tx, cy = y0 - 1 + ty, ox = cx + 1, oy = cy + 1;
     const bool owner = tx < BX - 1 && ty < BY - 1 && ox < NX && oy < NY;
     const bool cell_in = cx >= 0 && cx < nx && cy >= 0 && cy < ny;
@@ -261,7 +277,7 @@ __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const
     if (tid == 0) {
         double s = 0.0;
         for (int w2 = 0; w2 < NT / 32; ++w2) s += wsum[w2];
-        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * bz)] = s;
     }
 }
 
@@ -269,7 +285,7 @@ __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const
 // registers per thread one 256-thread block fits per SM, so a partial last wave
 // costs a whole chunk of steps: at 100^3 (7 x 7 columns of blocks) chunks of 34
 // planes give one wave of 147 blocks, where chunks of 15 gave 3 waves of 343.
-dim3 resid_grid(int nx, int ny, int nz, int* zc_out) {
+dim3 resid_grid(int nx, int ny, int nz, int* zc_out, int nl = 1) {
     const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
     const int gx = (NX + BX - 2) / (BX - 1), gy = (NY + BY - 2) / (BY - 1);
     static int slots = 0;
@@ -287,7 +303,7 @@ dim3 resid_grid(int nx, int ny, int nz, int* zc_out) {
     for (int gz = 1; gz <= NZ; ++gz) {
         const int zc = (NZ + gz - 1) / gz;
         if (zc < 4 && gz > 1) break;
-        const long long blocks = (long long)gx * gy * ((NZ + zc - 1) / zc);
+        const long long blocks = (long long)gx * gy * ((NZ + zc - 1) / zc) * nl;
         const long long cost = ((blocks + slots - 1) / slots) * (zc + 1);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
@@ -316,9 +332,41 @@ void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t*
         gd.hi[i] = (float)G.g[i];
         gd.lo[i] = (float)(G.g[i] - (double)gd.hi[i]);
     }
+    ResidLoads L{};
+    L.f[0] = f;
+    L.u[0] = u;
+    L.gz = (int)g.z;
     note_launch();
-    pdl_launch(k_resid64, dim3(g), dim3(dim3(BX, BY)), 0, s, nx, ny, nz, E, mask, f, u, r64, r32, px, sc, partial, gd,
+    pdl_launch(k_resid64, dim3(g), dim3(dim3(BX, BY)), 0, s, nx, ny, nz, E, mask, L, r64, r32, px, sc, partial, gd,
                zc);
+}
+
+int resid64_grid_blocks_multi(int nx, int ny, int nz, int nl) {
+    int zc = 0;
+    const dim3 g = resid_grid(nx, ny, nz, &zc, nl);
+    return (int)(g.x * g.y * g.z);
+}
+
+void launch_fine_resid64_multi(int nx, int ny, int nz, const double* E, const uint8_t* mask, int nl,
+                               const double* const* f, const double* const* u, const double* sc, double* partial,
+                               int pstride, const GHat64& G, cudaStream_t s) {
+    int zc = 0;
+    const dim3 g = resid_grid(nx, ny, nz, &zc, nl);
+    GHatDF gd;
+    for (int i = 0; i < 72; ++i) {
+        gd.hi[i] = (float)G.g[i];
+        gd.lo[i] = (float)(G.g[i] - (double)gd.hi[i]);
+    }
+    ResidLoads L{};
+    for (int l = 0; l < nl; ++l) {
+        L.f[l] = f[l];
+        L.u[l] = u[l];
+    }
+    L.gz = (int)g.z;
+    L.pstride = pstride;
+    note_launch();
+    pdl_launch(k_resid64, dim3(g.x, g.y, g.z * nl), dim3(dim3(BX, BY)), 0, s, nx, ny, nz, E, mask, L,
+               (double*)nullptr, (float*)nullptr, 0, sc, partial, gd, zc);
 }
 
 }  // namespace gmg

@@ -9,6 +9,8 @@
     python profile_cases.py warmstart-80  # 80^3 set-up, one learned warm start + solve
     python profile_cases.py warmstart-80-tf32  # the same with tensor-core convolutions
     python profile_cases.py train-48      # 48^3 set-up, 3 energy-loss train steps (batch 4)
+    python profile_cases.py multi-64      # 64^3 (a batch grid), one 16-load solve, host-driven loop
+    python profile_cases.py multi-apply-c2  # 100^3, 16 loads: packing, then 5 multi-load operator applies
 
 Each case prints the library's kernel-launch counter after set-up, so that
 ``ncu -s`` can skip the set-up kernels.  The solve normally runs its PCG
@@ -64,6 +66,8 @@ def main(case: str) -> None:
 
     if case in ("warmstart-80", "warmstart-80-tf32", "train-48"):
         return net_case(case)
+    if case.startswith("multi-"):
+        return multi_case(case)
     cfg = inputs.CONFIGS["c2"]
     fine = "bf16x3" if case.endswith("-bf16x3") else "fp32"
     S = gmg.Solver(torch.from_numpy(cfg.rho()).cuda(), p=cfg.p,
@@ -96,6 +100,38 @@ def main(case: str) -> None:
         torch.cuda.synchronize()
     else:
         raise SystemExit(f"unknown case {case}")
+    print("total launches", gmg.kernel_launches(), flush=True)
+
+
+def multi_case(case: str) -> None:
+    """The multi-load path: a batch grid's 16-load solve (the loop launched
+    from the host, so that every kernel is its own launch), or the 100^3
+    multi-load level-0 operator alone."""
+    import torch
+
+    from paper_2604_26441_b300 import gmg, inputs
+
+    n = 64 if case == "multi-64" else 100
+    rho = torch.from_numpy(inputs.filtered_random_density(n, n, n, 305)).cuda()
+    if case == "multi-64":
+        opts = gmg.options(levels=0, smoother="jacobi", degree=2, coarse_smoother=None, coarse_degree=None,
+                           omega=0.5, coarse_omega=None, device_loop=False)
+    else:
+        opts = gmg.options(levels=2, smoother="jacobi", coarse_smoother=None, omega=0.5)
+    S = gmg.Solver(rho, p=3.0, opts=opts)
+    fs = [torch.from_numpy(inputs.rotated_tip_edge_load(n, n, n, k, 16)).cuda() for k in range(16)]
+    fixed = inputs.clamp_xmin_mask(n, n, n)
+    xs = [torch.from_numpy(inputs.random_free_vector(fixed, 50 + k)).cuda() for k in range(16)]
+    S.apply_multi(xs)  # allocates the workspace and packs the operands
+    torch.cuda.synchronize()
+    print("setup launches", gmg.kernel_launches(), flush=True)
+    if case == "multi-64":
+        _, infos = S.solve_multi(fs)
+        print([i["iterations"] for i in infos], flush=True)
+    else:
+        for _ in range(5):
+            S.apply_multi(xs)
+    torch.cuda.synchronize()
     print("total launches", gmg.kernel_launches(), flush=True)
 
 

@@ -126,6 +126,7 @@ def test_multi_solve_matches_single_and_oracle(name, nx, ny, nz, levels, sm, nl)
         u1, info1 = single.solve(_t(f, torch.float64))
         assert info["status"] == info1["status"] == 0, (k, info, info1)
         assert info["iterations"] == info1["iterations"], (k, info["iterations"], info1["iterations"])
+        assert info["replacements"] == info1["replacements"], (k, info, info1)
         assert rel_l2(u, u1.cpu().numpy()) < 1e-5, k
         # the oracle: its own GMG-PCG (counts) and its FP64 residual of this answer
         u_or, res = so.gmg_pcg(H, f, spec, tol=1e-6, maxit=200)
@@ -167,6 +168,7 @@ def test_multi_solve_mixed_loads_and_caps():
         u1, info1 = single.solve(_t(f, torch.float64), u0[k].clone())
         assert infos[k]["status"] == info1["status"], k
         assert infos[k]["iterations"] == info1["iterations"], (k, infos[k], info1)
+        assert infos[k]["replacements"] == info1["replacements"], (k, infos[k], info1)
         if k == 1:
             assert infos[k]["rel_residual"] == 0.0 and not torch.any(us[k] != 0)
         else:
@@ -192,3 +194,20 @@ def test_multi_solve_outside_the_path_runs_single_solves():
         u1, info1 = S.solve(_t(f, torch.float64))
         assert infos[k]["status"] == 0 and infos[k]["iterations"] == info1["iterations"]
         assert torch.equal(us[k], u1)
+
+
+def test_multi_host_loop_equals_device_loop():
+    """The host-driven multi-load loop launches the captured loop's kernels in
+    the same order: bitwise the same iterates and counts."""
+    nx, ny, nz = 23, 11, 9
+    rho = inputs.filtered_random_density(nx, ny, nz, 13)
+    loads = [_t(f, torch.float64) for f in _loads(nx, ny, nz, range(0, 16, 3))]
+    base = dict(levels=3, smoother="chebyshev", degree=2, coarse_smoother=None, coarse_degree=None, omega=0.5,
+                coarse_omega=None)
+    dev = gpu_solver(rho, 3.0, **base)
+    host = gpu_solver(rho, 3.0, device_loop=False, **base)
+    ud, idev = dev.solve_multi(loads)
+    uh, ihost = host.solve_multi(loads)
+    for a, b, ia, ib in zip(ud, uh, idev, ihost):
+        assert ia["status"] == ib["status"] == 0 and ia["iterations"] == ib["iterations"]
+        assert torch.equal(a, b)
