@@ -360,6 +360,13 @@ int gmg_solve_multi(gmg_handle* h, int nl, const double* const* f_dev, double* c
  * (host arrays of device FP32 pointers, dense numbering).  Asynchronous. */
 int gmg_apply_multi(gmg_handle* h, int nl, const float* const* u_dev, float* const* y_dev);
 
+/* One pass of the multi-load level-0 operator on the handle's own multi-load
+ * vectors, for timing: what = 0: q = K p; what = 1: a smoothing pass (degree
+ * fused operator + smoother steps from the iterate z, right-hand side r).
+ * nl loads (1..16).  Allocates the multi-load workspace on first use.
+ * Asynchronous. */
+int gmg_multi_fine_pass(gmg_handle* h, int nl, int what);
+
 /* Level-0 operator of the multi-load path: 0 = CUDA cores (Hadamard form, one
  * block per tile and load), 1 = tensor cores (element contraction on tcgen05).
  * GMG_ERR_ARG for an unknown kind or one this build lacks. */

@@ -182,6 +182,9 @@ struct MultiWork {
     int* err_host = nullptr;
     int* err_map = nullptr;
     int fine_kernel = 0;         // level-0 operator: 0 CUDA-core (Hadamard), 1 tensor cores
+    float* tcB = nullptr;        // tensor-core operator: K_e operand, [hi, lo][4 corner pairs][2][32][4] FP32
+    float tc_scale = 1.f;        // K_e = tc_scale * (hi + lo)
+    int tc_passes = 0;           // MMA passes per corner pair: 3 (K_e exact in TF32) or 5 (K_e split)
     int launch_err = 0;          // a level-0 launch could not be prepared (tensor map encoding)
     // captured loops, keyed by the iterate pointers
     struct Loop {
@@ -575,6 +578,39 @@ int launch_coarse_fused(const CoarseFused& a, int blocks, cudaStream_t s);
 void launch_coarse_pcg(const CoarseLevel& l, const float* b, float* x, float* r, float* p, float* q, int steps,
                        cudaStream_t s);
 void launch_lambda_finish(double* sc, double* lam_slot, cudaStream_t s);
+
+// ---- the level-0 operator of the multi-load path (multi.cu, multi_tc.cu) ------------
+struct MFineArgs {
+    int nx, ny, nz;
+    int px;                // nodes per row of the level-0 vectors (multiple of 4)
+    int epitch;            // moduli per row of Ep
+    int nl;                // loads processed
+    const float* Ep;       // moduli [nz][ny][epitch]
+    const uint8_t* maskp;  // level-0 mask, vector numbering
+    const float* inv0;     // [nnp] fine Jacobi scale (tensor-core smoother)
+    const float* xin;
+    const float* b;
+    const float* dold;
+    float* dnew;
+    float* out;
+    const double* coef;
+    int step;
+    double* partial;       // [kLoads][pstride] (nullptr = no dot)
+    int pstride;
+    float kd;
+    int* err;
+};
+// CUDA-core operator: one block per (tile, load); GMG_OK or an error (tensor maps).
+int launch_mfine(int mode, int dot, const MFineArgs& a, const GHat& G, cudaStream_t s);
+int mfine_blocks(int nx, int ny, int nz, int nl);
+// Tensor-core operator (multi_tc.cu): blocks per load group, and the launch.
+int mfine_tc_blocks(int nx, int ny, int nz);
+int launch_mfine_tc(int mode, int dot, const MFineArgs& a, const float* Bop, float scale, int passes,
+                    cudaStream_t s);
+// Host: the K_e operand of the tensor-core operator from K_e (FP64, 24 x 24):
+// returns the MMA passes (3 when K_e is a multiple of an integer matrix exact in
+// TF32, else 5) and the scale; out receives 2 x 1024 floats.
+int build_mfine_tc_operand(const double* Ke, float* out, float* scale);
 
 // ---- multi.cu: multi-load solve pieces used by gmg_solve_batch ---------------------
 // Allocates h's multi-load workspace once (GMG_OK or an error code).

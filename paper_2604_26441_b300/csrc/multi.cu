@@ -712,26 +712,6 @@ struct MLayer {
 
 }  // namespace
 
-struct MFineArgs {
-    int nx, ny, nz;
-    int px;                // nodes per row of the level-0 vectors (multiple of 4)
-    int epitch;            // moduli per row of Ep
-    int nl;                // loads processed (blocks per tile)
-    const float* Ep;       // moduli [nz][ny][epitch]
-    const uint8_t* maskp;  // level-0 mask, vector numbering
-    const float* xin;
-    const float* b;
-    const float* dold;
-    float* dnew;
-    float* out;
-    const double* coef;
-    int step;
-    double* partial;       // [kLoads][pstride] (nullptr = no dot)
-    int pstride;
-    float kd;
-    int* err;
-};
-
 namespace {
 
 template <int BX, int BY, int MODE, bool DOT>
@@ -1189,12 +1169,20 @@ int multi_workspace(gmg_handle* h) {
     for (int nl = 1; nl <= kLoads; ++nl) w->pstride = std::max(w->pstride, mfine_blocks(l0.nx, l0.ny, l0.nz, nl));
     for (int nl = 1; nl <= kLoads; ++nl)
         w->pstride = std::max(w->pstride, resid64_grid_blocks_multi(l0.nx, l0.ny, l0.nz, nl));
+    w->pstride = std::max(w->pstride, mfine_tc_blocks(l0.nx, l0.ny, l0.nz));
+    {
+        std::vector<float> op(2048);
+        w->tc_passes = build_mfine_tc_operand(h->keD.v, op.data(), &w->tc_scale);
+        if (int rc = malloc_dev(h, &w->tcB, op.size()); rc != GMG_OK) return bad(rc);
+        if (cudaMemcpy(w->tcB, op.data(), sizeof(float) * op.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bad(mfail(GMG_ERR_CUDA, "multi-load tensor-core operand"));
+    }
     // two partial arrays of kLoads rows (the norms kernel fills both)
     if (int rc = malloc_dev(h, &w->partials, (size_t)2 * kLoads * w->pstride); rc != GMG_OK) return bad(rc);
     if (int rc = malloc_dev(h, &w->sc, (size_t)kLoads * SC_COUNT); rc != GMG_OK) return bad(rc);
     if (cudaMemsetAsync(w->sc, 0, sizeof(double) * kLoads * SC_COUNT, s) != cudaSuccess)
         return bad(mfail(GMG_ERR_CUDA, "multi memset"));
-    if (h->nL > 0) {
+    if (h->nL > 0 && h->Ainv && !h->coarse_pcg) {
         const size_t nn2 = (size_t)h->nL * h->nL;
         if (int rc = malloc_dev(h, &w->Ahi, nn2); rc != GMG_OK) return bad(rc);
         if (int rc = malloc_dev(h, &w->Alo, nn2); rc != GMG_OK) return bad(rc);
@@ -1251,9 +1239,20 @@ MFineArgs mfine_args(gmg_handle* h, int nl) {
     const Level& l = h->lev[0];
     MFineArgs a{};
     a.nx = l.nx; a.ny = l.ny; a.nz = l.nz; a.px = l.px; a.epitch = h->ex; a.nl = nl;
-    a.Ep = h->E32p; a.maskp = l.maskp; a.coef = l.coef; a.kd = h->kd; a.err = h->kerr;
+    a.Ep = h->E32p; a.maskp = l.maskp; a.inv0 = h->inv0; a.coef = l.coef; a.kd = h->kd; a.err = h->kerr;
     a.pstride = h->mw->pstride;
     return a;
+}
+
+// The level-0 operator of the multi-load path on the handle's chosen unit.
+int mfine_launch(gmg_handle* h, int mode, int dot, const MFineArgs& a) {
+    MultiWork& w = *h->mw;
+    if (w.fine_kernel == 1) return launch_mfine_tc(mode, dot, a, w.tcB, w.tc_scale, w.tc_passes, h->stream);
+    return launch_mfine(mode, dot, a, h->gh, h->stream);
+}
+int mfine_partials(gmg_handle* h, int nl) {
+    const Level& l0 = h->lev[0];
+    return h->mw->fine_kernel == 1 ? mfine_tc_blocks(l0.nx, l0.ny, l0.nz) : mfine_blocks(l0.nx, l0.ny, l0.nz, nl);
 }
 
 // y = K^l x on multi-load vectors (dot: partial x . y per load, finalised into slot).
@@ -1263,11 +1262,11 @@ void mlevel_apply(gmg_handle* h, int li, const float* x, float* y, int dot_slot,
     if (li == 0) {
         MFineArgs a = mfine_args(h, nl);
         a.xin = x; a.out = y; a.partial = dot_slot >= 0 ? w.partials : nullptr;
-        if (launch_mfine(FM_APPLY, dot_slot >= 0, a, h->gh, s) != GMG_OK) w.launch_err = 1;
+        if (mfine_launch(h, FM_APPLY, dot_slot >= 0, a) != GMG_OK) w.launch_err = 1;
         if (dot_slot >= 0) {
             note_launch();
-            pdl_launch(k_mfinalize, dim3(kLoads), dim3(kMT), 0, s, (const double*)w.partials,
-                       mfine_blocks(a.nx, a.ny, a.nz, nl), w.pstride, w.sc, dot_slot, op);
+            pdl_launch(k_mfinalize, dim3(kLoads), dim3(kMT), 0, s, (const double*)w.partials, mfine_partials(h, nl),
+                       w.pstride, w.sc, dot_slot, op);
         }
     } else {
         MBsrArgs a = mbsr_args(h->lev[li], w.lev[li]);
@@ -1281,7 +1280,7 @@ void mlevel_resid(gmg_handle* h, int li, const float* b, const float* x, float* 
     if (li == 0) {
         MFineArgs a = mfine_args(h, nl);
         a.xin = x; a.b = b; a.out = t;
-        if (launch_mfine(FM_RESID, 0, a, h->gh, s) != GMG_OK) h->mw->launch_err = 1;
+        if (mfine_launch(h, FM_RESID, 0, a) != GMG_OK) h->mw->launch_err = 1;
     } else {
         MBsrArgs a = mbsr_args(h->lev[li], h->mw->lev[li]);
         a.xin = x; a.b = b; a.out = t;
@@ -1304,7 +1303,7 @@ void msmooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, 
             MFineArgs a = mfine_args(h, nl);
             a.xin = xcur; a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
             a.partial = dot ? w.partials : nullptr;
-            if (launch_mfine(FM_SMOOTH, dot, a, h->gh, s) != GMG_OK) w.launch_err = 1;
+            if (mfine_launch(h, FM_SMOOTH, dot, a) != GMG_OK) w.launch_err = 1;
         }
     } else {
         MBsrArgs a = mbsr_args(l, w.lev[li]);
@@ -1330,10 +1329,9 @@ float* msmooth_pass(gmg_handle* h, int li, const float* b, float* cur, float* X,
         const bool dot = last && dot_slot >= 0;
         msmooth_step(h, li, k, zero_init && k == 0, b, cur, next, cheb && !last, dot, nl);
         if (dot) {
-            const Level& l0 = h->lev[0];
             note_launch();
             pdl_launch(k_mfinalize, dim3(kLoads), dim3(kMT), 0, h->stream, (const double*)w.partials,
-                       mfine_blocks(l0.nx, l0.ny, l0.nz, nl), w.pstride, w.sc, dot_slot, op);
+                       mfine_partials(h, nl), w.pstride, w.sc, dot_slot, op);
         }
         cur = next;
         ++writes;
@@ -1591,10 +1589,29 @@ int gmg_apply_multi(gmg_handle* h, int nl, const float* const* u, float* const* 
     return GMG_OK;
 }
 
+int gmg_multi_fine_pass(gmg_handle* h, int nl, int what) {
+    if (!h || nl < 1 || nl > kLoads || what < 0 || what > 1) return mfail(GMG_ERR_ARG, "bad handle, load count or pass");
+    if (what == 1 && h->L < 2) return mfail(GMG_ERR_ARG, "smoothing pass needs an assembled level below");
+    MTRY(multi_workspace(h));
+    MultiWork& w = *h->mw;
+    w.launch_err = 0;
+    if (what == 0) {
+        mlevel_apply(h, 0, w.p, w.q, -1, FIN_NONE, nl);
+    } else {
+        int writes = 0;  // steps alternate x2, z, ... starting from the iterate in z
+        msmooth_pass(h, 0, w.r, w.z, w.z, w.x2, false, writes, nl);
+    }
+    if (w.launch_err) {
+        w.launch_err = 0;
+        return mfail(GMG_ERR_CUDA, "multi-load pass: tensor map encoding failed");
+    }
+    if (cudaGetLastError() != cudaSuccess) return mfail(GMG_ERR_CUDA, "multi-load pass launch");
+    return GMG_OK;
+}
+
 int gmg_set_multi_kernel(gmg_handle* h, int kind) {
     if (!h || kind < 0 || kind > 1) return mfail(GMG_ERR_ARG, "kind must be 0 (CUDA cores) or 1 (tensor cores)");
     MTRY(multi_workspace(h));
-    if (kind == 1) return mfail(GMG_ERR_ARG, "tensor-core multi-load operator not available in this build");
     if (h->mw->fine_kernel != kind) multi_drop_loops(h);
     h->mw->fine_kernel = kind;
     return GMG_OK;

@@ -112,6 +112,7 @@ _SIGS = {
                                        ctypes.c_int, ctypes.POINTER(_Info)]),
     "gmg_apply_multi": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "gmg_set_multi_kernel": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gmg_multi_fine_pass": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "gmg_vcycle_symmetry": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gmg_residual64": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "gmg_residual64_noalloc": (ctypes.c_int, [ctypes.POINTER(_Grid), _P, _P, ctypes.c_double, _P, _P, _P,
@@ -378,6 +379,11 @@ class Solver:
         yp = (_P * n)(*[_ptr(y, torch.float32, 3 * self.nn, "y") for y in ys])
         _check(self._lib.gmg_apply_multi(self._h, n, up, yp))
         return ys
+
+    def multi_fine_pass(self, what: str = "apply", nl: int = 16) -> None:
+        """One multi-load level-0 operator pass on this handle's own multi-load
+        vectors ("apply" or "smooth"), for timing (gmg_multi_fine_pass)."""
+        _check(self._lib.gmg_multi_fine_pass(self._h, nl, {"apply": 0, "smooth": 1}[what]))
 
     def set_multi_kernel(self, kind: str) -> None:
         """Level-0 operator of the multi-load path: "simt" (CUDA cores) or

@@ -11,6 +11,7 @@
     python profile_cases.py train-48      # 48^3 set-up, 3 energy-loss train steps (batch 4)
     python profile_cases.py multi-64      # 64^3 (a batch grid), one 16-load solve, host-driven loop
     python profile_cases.py multi-apply-c2  # 100^3, 16 loads: packing, then 5 multi-load operator applies
+    python profile_cases.py multi-apply-c2-tc  # the same with the tensor-core level-0 operator
 
 Each case prints the library's kernel-launch counter after set-up, so that
 ``ncu -s`` can skip the set-up kernels.  The solve normally runs its PCG
@@ -119,6 +120,8 @@ def multi_case(case: str) -> None:
     else:
         opts = gmg.options(levels=2, smoother="jacobi", coarse_smoother=None, omega=0.5)
     S = gmg.Solver(rho, p=3.0, opts=opts)
+    if case.endswith("-tc"):
+        S.set_multi_kernel("tc")
     fs = [torch.from_numpy(inputs.rotated_tip_edge_load(n, n, n, k, 16)).cuda() for k in range(16)]
     fixed = inputs.clamp_xmin_mask(n, n, n)
     xs = [torch.from_numpy(inputs.random_free_vector(fixed, 50 + k)).cuda() for k in range(16)]

@@ -211,3 +211,114 @@ def test_multi_host_loop_equals_device_loop():
     for a, b, ia, ib in zip(ud, uh, idev, ihost):
         assert ia["status"] == ib["status"] == 0 and ia["iterations"] == ib["iterations"]
         assert torch.equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# tensor-core level-0 operator (tcgen05, TF32 limbs of u, K_e exact in TF32)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,nx,ny,nz,nl", APPLY_CASES + [("c2", 100, 100, 100, 16)])
+def test_multi_tc_apply_matches_oracle(name, nx, ny, nz, nl):
+    rho = inputs.filtered_random_density(nx, ny, nz, 7)
+    fixed = inputs.clamp_xmin_mask(nx, ny, nz)
+    S = gpu_solver(rho, 3.0, levels=0, smoother="jacobi", coarse_smoother=None, omega=0.5)
+    S.set_multi_kernel("tc")
+    E = fem.moduli(rho, 3.0)
+    Ke = fem.element_stiffness(0.3)
+    g = fem.Grid(nx, ny, nz)
+    us_h = []
+    for k in range(nl):
+        u = inputs.random_free_vector(fixed, seed=100 + k)
+        u[fixed == 1] = 1e3
+        us_h.append(u)
+    us = [_t(u) for u in us_h]
+    ys = S.apply_multi(us)
+    if name == "c2":
+        rng = np.random.default_rng(1)
+        nodes = np.concatenate([rng.integers(0, g.n_nodes, 300), [0, g.n_nodes - 1, nx, g.n_nodes // 2]])
+    worst = 0.0
+    for k in range(nl):
+        y = ys[k].cpu().numpy()
+        u = us_h[k].astype(np.float64)
+        u[fixed == 1] = 0.0
+        assert np.all(y[fixed == 1] == 0.0)
+        if name == "c2":
+            ref = fem.matfree_apply_at_nodes(g, E, Ke, u, nodes)
+            ref[fixed.reshape(-1, 3)[nodes] == 1] = 0
+            err = rel_l2(y.reshape(-1, 3)[nodes], ref)
+        else:
+            yref = fem.matfree_apply(g, E, Ke, u)
+            yref[fixed == 1] = 0.0
+            err = rel_l2(y, yref)
+        worst = max(worst, err)
+        assert err < 1e-6, (k, err)
+    print(f"{name}: worst relative L2 error of the tensor-core apply {worst:.2e}")
+    ys2 = S.apply_multi(us)
+    assert all(torch.equal(a, b) for a, b in zip(ys, ys2))
+
+
+@pytest.mark.parametrize("name,nx,ny,nz,levels,sm,nl", SOLVE_CASES)
+def test_multi_tc_solve_matches_single_and_oracle(name, nx, ny, nz, levels, sm, nl):
+    opts = dict(levels=levels, coarse_smoother=None, coarse_degree=None, coarse_omega=None, **sm)
+    rho = inputs.filtered_random_density(nx, ny, nz, 21)
+    fixed = inputs.clamp_xmin_mask(nx, ny, nz)
+    loads = _loads(nx, ny, nz, range(nl))
+    S = gpu_solver(rho, 3.0, **opts)
+    S.set_multi_kernel("tc")
+    us, infos = S.solve_multi([_t(f, torch.float64) for f in loads])
+    single = gpu_solver(rho, 3.0, fused_coarse_nodes=0, **opts)
+    H, E = oracle_hierarchy(rho, 3.0, fixed, levels)
+    spec = oracle_spec_from_opts(opts)
+    g = fem.Grid(nx, ny, nz)
+    free = fem.free_dofs(fixed)
+    Ke = fem.element_stiffness(0.3)
+    for k, f in enumerate(loads):
+        u = us[k].cpu().numpy()
+        info = infos[k]
+        u1, info1 = single.solve(_t(f, torch.float64))
+        assert info["status"] == info1["status"] == 0, (k, info, info1)
+        # the tensor-core forces round differently from the FP32 Hadamard form
+        # (both ~1e-7 of K u): a load that meets the tolerance at the margin may
+        # take one iteration more or less
+        assert abs(info["iterations"] - info1["iterations"]) <= 1, (k, info["iterations"], info1["iterations"])
+        assert rel_l2(u, u1.cpu().numpy()) < 1e-5, k
+        u_or, res = so.gmg_pcg(H, f, spec, tol=1e-6, maxit=200)
+        assert abs(info["iterations"] - res.iterations) <= max(2, 0.1 * res.iterations)
+        r = f - fem.matfree_apply(g, E, Ke, u)
+        rel = np.linalg.norm(r[free]) / np.linalg.norm(f[free])
+        assert rel <= 1e-6, (k, rel)
+        assert abs(info["rel_residual"] - rel) < 1e-9
+
+
+@pytest.mark.parametrize("kind", ["simt", "tc"])
+def test_multi_apply_smooth_fields(kind):
+    """K u for smooth u (converged displacement fields and a low-frequency
+    mode): K u is then far smaller than |K| |u|, the case where rounding of u
+    itself, not of the differences, would show.  Both level-0 operators stay
+    within 1e-5 of the FP64 oracle."""
+    nx, ny, nz = 40, 20, 20
+    rho = inputs.filtered_random_density(nx, ny, nz, 31)
+    fixed = inputs.clamp_xmin_mask(nx, ny, nz)
+    S = gpu_solver(rho, 3.0, levels=3, smoother="chebyshev", degree=2, coarse_smoother=None, omega=0.5)
+    S.set_multi_kernel(kind)
+    E = fem.moduli(rho, 3.0)
+    Ke = fem.element_stiffness(0.3)
+    g = fem.Grid(nx, ny, nz)
+    us = []
+    for k in (0, 4, 9):
+        u, info = S.solve(_t(inputs.rotated_tip_edge_load(nx, ny, nz, k, nrhs=16), torch.float64))
+        assert info["status"] == 0
+        us.append(u.cpu().numpy())
+    X, Y, Z = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    mode = np.stack([np.sin(np.pi * X / nx) * np.cos(np.pi * Y / ny), np.sin(np.pi * Z / nz),
+                     1e3 + 0.0 * X], axis=-1).transpose(2, 1, 0, 3).reshape(-1)  # a large constant z part
+    mode[fixed == 1] = 0.0
+    us.append(mode)
+    ys = S.apply_multi([_t(u) for u in us])
+    errs = []
+    for u, y in zip(us, ys):
+        u32 = u.astype(np.float32).astype(np.float64)
+        yref = fem.matfree_apply(g, E, Ke, u32)
+        yref[fixed == 1] = 0.0
+        errs.append(rel_l2(y.cpu().numpy(), yref))
+    print(kind, "smooth-field relative errors", " ".join(f"{e:.1e}" for e in errs))
+    assert max(errs) < 1e-5, errs
