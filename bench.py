@@ -333,6 +333,25 @@ def batched_leg(dev, stream) -> dict:
     batch_ms = statistics.median(times)
     ok = all(i["status"] == 0 and i["rel_residual"] <= 1e-6 for i in infos)
     its = [i["iterations"] for i in infos]
+    # the same batch with the tensor-core level-0 operator in every chunk
+    for base in solvers[::BATCH_RHS]:
+        base.set_multi_kernel("tc")
+    zero_all()
+    _, infos_tc = gmg.solve_batch(solvers, fs, us)  # recaptures the batch graph
+    tc_times = []
+    for _ in range(reps):
+        zero_all()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, infos_tc = gmg.solve_batch(solvers, fs, us)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tc_times.append(a.elapsed_time(b))
+    tc_ms = statistics.median(tc_times)
+    its_tc = [i["iterations"] for i in infos_tc]
+    ok_tc = all(i["status"] == 0 and i["rel_residual"] <= 1e-6 for i in infos_tc)
+    for base in solvers[::BATCH_RHS]:
+        base.set_multi_kernel("simt")
     # the same solves one after another (each handle's own loop graph, captured in the warm-up)
     for s_, f, u in zip(solvers, fs, us):
         u.zero_()
@@ -350,6 +369,10 @@ def batched_leg(dev, stream) -> dict:
         s_.close()
     return {"workload": f"8 cantilevers {'/'.join(str(n) for n in BATCH_GRIDS)}^3 ({elements:,} elements) x "
                         f"{BATCH_RHS} rotated tip loads = {nsol} solves, Jacobi 2/2, auto levels, tol 1e-6",
+            "path": "one multi-load PCG loop per grid (16 loads: per-load step lengths and stopping), the 8 loops "
+                    "as branches of one CUDA graph; level 0 on CUDA cores (Hadamard form)",
+            "tensor_core_level0": {"value": nsol / (tc_ms / 1000.0), "ms_per_batch": tc_ms, "all_converged": ok_tc,
+                                   "iterations_min_max": [min(its_tc), max(its_tc)]},
             "value": nsol / (batch_ms / 1000.0), "unit": "solves/s", "ms_per_batch": batch_ms,
             "sequential_solves_per_s": nsol / (seq_ms / 1000.0), "speedup_vs_sequential": seq_ms / batch_ms,
             "all_converged": ok, "iterations_min_max": [min(its), max(its)],
@@ -357,6 +380,42 @@ def batched_leg(dev, stream) -> dict:
                           "model": f"{t['model_tile']}/z{t['model_zchunk']}",
                           "fine_us": round(t["fine_us"], 2), "model_us": round(t["model_us"], 2)}
                          for n, t in zip(BATCH_GRIDS, tuned)]}
+
+
+def multi_fine_leg(S, nn: int, ne: int, single_apply_ms: float, single_pass_ms: float, deg: int) -> dict:
+    """The level-0 operator of the multi-load path at 100^3, 16 loads in one
+    launch (the 16-load vectors, 264 MB each, exceed L2): per-load time of one
+    application and of one fused smoothing pass against the single-load kernel
+    timed above, for the CUDA-core and the tensor-core operator."""
+    import torch
+
+    def timed(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        ev = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+    peak, _ = _peaks()
+    out = {"loads": 16, "single_apply_us": 1000.0 * single_apply_ms, "single_pass_us": 1000.0 * single_pass_ms}
+    for kind in ("simt", "tc"):
+        S.set_multi_kernel(kind)
+        ap = timed(lambda: S.multi_fine_pass("apply"))
+        sp = timed(lambda: S.multi_fine_pass("smooth"))
+        alg = 16 * 32 * nn + 4 * ne  # 16-byte records read and written per load, moduli once
+        out[kind] = {"apply_us": 1000.0 * ap, "apply_us_per_load": 1000.0 * ap / 16,
+                     "apply_per_load_vs_single": ap / 16 / single_apply_ms,
+                     "pass_us": 1000.0 * sp, "pass_us_per_load": 1000.0 * sp / 16,
+                     "pass_per_load_vs_single": sp / 16 / single_pass_ms,
+                     "apply_hbm_frac": alg / (ap * 1e-3) / 1e9 / peak}
+    S.set_multi_kernel("simt")
+    return out
 
 
 def configs_leg(dev, stream, flush_l2) -> list:
@@ -786,6 +845,7 @@ def main():
 
     # single-GPU characterisations (not part of the replicated metric): N = 1 only
     solo = world == 1
+    mfine = None if args.no_batch or not solo else multi_fine_leg(S, nn, ne, apply_ms, pass_ms, deg)
     batched = None if args.no_batch or not solo else batched_leg(dev, stream)
     warm = None if args.no_warmstart or not solo else warmstart_leg(dev)
     small = None if args.no_configs or not solo else configs_leg(dev, stream, flush_l2)
@@ -824,6 +884,8 @@ def main():
     }
     if batched is not None:
         line["batched"] = batched
+    if mfine is not None:
+        line["multi_fine"] = mfine
     if warm is not None:
         line["warmstart"] = warm
     if small is not None:

@@ -1677,7 +1677,7 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
         if ((chunk_of[i] < 0 && state[i] == 0) || (chunk_of[i] >= 0 && chunk_live[chunk_of[i]]))
             key.emplace_back(hs[i], u[i]);
     if (!key.empty()) {
-        if (key != h0->batch_key || !h0->batch_exec) {
+        if (key != h0->batch_key || !h0->batch_exec || h0->batch_gen != multi_generation()) {
             if (h0->batch_exec) cudaGraphExecDestroy(h0->batch_exec);
             if (h0->batch_graph) cudaGraphDestroy(h0->batch_graph);
             h0->batch_exec = nullptr;
@@ -1717,6 +1717,7 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
             h0->batch_graph = g;
             h0->batch_exec = ex;
             h0->batch_key = key;
+            h0->batch_gen = multi_generation();
         }
         for (int i = 0; i < count; ++i) {
             if (chunk_of[i] >= 0 || state[i] != 0) continue;

@@ -377,6 +377,7 @@ struct gmg_handle {
     cudaGraphExec_t batch_exec = nullptr;
     std::vector<std::pair<const gmg_handle*, const double*>> batch_key;
     std::vector<std::pair<unsigned long long, unsigned long long>> batch_counts;
+    unsigned batch_gen = 0;                     // multi_generation() when batch_graph was captured
     int fused_blocks = 0;
     gmg::MultiWork* mw = nullptr;               // multi-load solve workspace (multi.cu), lazily allocated
     std::vector<void*> allocs;                  // every device allocation, freed by gmg_destroy
@@ -627,6 +628,9 @@ void multi_true_residual(gmg_handle* h, int l, const double* f, const double* u,
 // Per-load loop scalars (iteration count 0, tolerance, cap, ||f||, active flag) of all 16 slots.
 void multi_set_loop_scalars(gmg_handle* h, int nl, double tol, int maxit, const double* nf, const bool* active);
 void multi_publish(gmg_handle* h);
+// Changes whenever some handle's multi-load level-0 operator is switched (a
+// captured batch graph records the value it was built under).
+unsigned multi_generation();
 bool multi_capture_loop(gmg_handle* h, double* const* u, int nl, cudaGraph_t g, cudaStream_t cap,
                         unsigned long long& prefix, unsigned long long& body_k);
 

@@ -1234,6 +1234,12 @@ void multi_drop_loops(gmg_handle* h) {
 }
 
 namespace {
+std::atomic<unsigned> g_multi_gen{0};  // bumped whenever a handle's level-0 multi-load operator changes
+}  // namespace
+
+unsigned multi_generation() { return g_multi_gen.load(std::memory_order_relaxed); }
+
+namespace {
 
 MFineArgs mfine_args(gmg_handle* h, int nl) {
     const Level& l = h->lev[0];
@@ -1612,7 +1618,10 @@ int gmg_multi_fine_pass(gmg_handle* h, int nl, int what) {
 int gmg_set_multi_kernel(gmg_handle* h, int kind) {
     if (!h || kind < 0 || kind > 1) return mfail(GMG_ERR_ARG, "kind must be 0 (CUDA cores) or 1 (tensor cores)");
     MTRY(multi_workspace(h));
-    if (h->mw->fine_kernel != kind) multi_drop_loops(h);
+    if (h->mw->fine_kernel != kind) {
+        multi_drop_loops(h);
+        g_multi_gen.fetch_add(1);  // captured batch graphs that contain this handle's loop are stale
+    }
     h->mw->fine_kernel = kind;
     return GMG_OK;
 }
