@@ -362,8 +362,7 @@ struct MBsrArgs {
 // reads of a node's threads hit the same L1 line) and applied to the thread's
 // LQ records of each neighbour (same branch-free neighbour handling as k_bsr:
 // clamped indices, zero-stored forward blocks outside the grid, backward terms
-// scaled by 0 outside it).  LQ = 4 on large levels; LQ = 1 on small ones,
-// where a thread per record gives the latency-bound kernel more warps.
+// scaled by 0 outside it).
 template <int MODE, int kBsrLq>
 __global__ void __launch_bounds__(128) k_mbsr(MBsrArgs a) {
     pdl_entry();
@@ -586,11 +585,12 @@ __global__ void __launch_bounds__(256) k_mcoarse_gather(int nL, const int* free_
 }
 
 constexpr int kCoarseRows = 4, kCoarseSlices = 4;
+static_assert(kCoarseRows * kCoarseSlices * kLoads == 256, "one block of 256 threads");
 __global__ void __launch_bounds__(256) k_mcoarse(int nL, const int* free_idx, const float* Ahi, const float* Alo,
                                                  const float* bc, float* x, int n_nodes) {
     pdl_entry();
     __shared__ double part[kCoarseRows][kCoarseSlices][kLoads];
-    const int tid = threadIdx.x, l = tid & 15, sl = (tid >> 4) & 3, rr = tid >> 6;
+    const int tid = threadIdx.x, l = tid & 15, sl = (tid >> 4) % kCoarseSlices, rr = (tid >> 4) / kCoarseSlices;
     const int row = blockIdx.x * kCoarseRows + rr;
     float hi = 0.f, lo = 0.f;
     if (row < nL) {
@@ -610,7 +610,9 @@ __global__ void __launch_bounds__(256) k_mcoarse(int nL, const int* free_idx, co
     part[rr][sl][l] = (double)hi + (double)lo;
     __syncthreads();
     if (sl == 0 && row < nL) {
-        const double v = ((part[rr][0][l] + part[rr][1][l]) + part[rr][2][l]) + part[rr][3][l];
+        double v = part[rr][0][l];
+#pragma unroll
+        for (int k = 1; k < kCoarseSlices; ++k) v += part[rr][k][l];
         const int dof = free_idx[row];
         const int node = dof / 3, c = dof - 3 * (dof / 3);
         x[GMG_B(((long long)node * kLoads + l) * 4 + c, (long long)n_nodes * kNodeF, 532)] = (float)v;
@@ -1081,8 +1083,6 @@ MBsrArgs mbsr_args(const Level& l, const MultiLevel& m) {
     return a;
 }
 
-constexpr int kBsrSmallLevel = 32768;  // nodes below which a thread takes one record
-
 template <int LQ>
 void launch_mbsr_lq(int mode, const MBsrArgs& a, cudaStream_t s) {
     const dim3 g((unsigned)(((long long)a.nn * (kLoads / LQ) + 127) / 128));
@@ -1091,10 +1091,14 @@ void launch_mbsr_lq(int mode, const MBsrArgs& a, cudaStream_t s) {
     else pdl_launch(k_mbsr<FM_SMOOTH, LQ>, g, dim3(128), 0, s, a);
 }
 
+// Four loads per thread on every level: inside a batch the chunks' kernels run
+// concurrently and the GPU is full, so instructions count more than warps in
+// flight (8 x 16 loads on 32^3-80^3, one bench run each: 1,560 solves/s with
+// four loads per thread everywhere, 1,483 with one per thread below 32,768
+// nodes, 1,400 with one everywhere, 1,418 with eight).
 void launch_mbsr(int mode, const MBsrArgs& a, cudaStream_t s) {
     note_launch();
-    if (a.nn < kBsrSmallLevel) launch_mbsr_lq<1>(mode, a, s);
-    else launch_mbsr_lq<4>(mode, a, s);
+    launch_mbsr_lq<4>(mode, a, s);
 }
 
 // ---- host side ----------------------------------------------------------------------
