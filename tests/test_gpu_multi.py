@@ -322,3 +322,39 @@ def test_multi_apply_smooth_fields(kind):
         errs.append(rel_l2(y.cpu().numpy(), yref))
     print(kind, "smooth-field relative errors", " ".join(f"{e:.1e}" for e in errs))
     assert max(errs) < 1e-5, errs
+
+
+def test_multi_loads_are_independent_and_interleave_with_single_solves():
+    """Per-load independence: 16 loads where two are zero and one is scaled by
+    1e6 give each load the answer it gets alone (nl = 1); single-load solves on
+    the same handle before and after the multi-load call are unchanged; a
+    W-cycle handle (outside the multi-load path) solves load by load."""
+    nx, ny, nz = 23, 11, 9
+    opts = dict(levels=3, smoother="chebyshev", degree=2, coarse_smoother=None, coarse_degree=None, omega=0.5,
+                coarse_omega=None)
+    rho = inputs.filtered_random_density(nx, ny, nz, 17)
+    S = gpu_solver(rho, 3.0, **opts)
+    loads = _loads(nx, ny, nz, range(16))
+    loads[3] = np.zeros_like(loads[3])
+    loads[9] = np.zeros_like(loads[9])
+    loads[5] = loads[5] * 1e6
+    u_before, i_before = S.solve(_t(loads[0], torch.float64))
+    us, infos = S.solve_multi([_t(f, torch.float64) for f in loads])
+    u_after, i_after = S.solve(_t(loads[0], torch.float64))
+    assert torch.equal(u_before, u_after) and i_before["iterations"] == i_after["iterations"]
+    for k, f in enumerate(loads):
+        u1, i1 = S.solve_multi([_t(f, torch.float64)])
+        assert infos[k]["status"] == i1[0]["status"] == 0, k
+        assert infos[k]["iterations"] == i1[0]["iterations"], (k, infos[k], i1[0])
+        if k in (3, 9):
+            assert not torch.any(us[k] != 0)
+        else:
+            assert rel_l2(us[k].cpu().numpy(), u1[0].cpu().numpy()) < 1e-6, k
+    # the scaled load: the same iterations as its unscaled twin, the answer scaled
+    assert infos[5]["iterations"] == S.solve_multi([_t(loads[5] / 1e6, torch.float64)])[1][0]["iterations"]
+    W = gpu_solver(rho, 3.0, cycle="W", **opts)
+    uw, iw = W.solve_multi([_t(f, torch.float64) for f in loads[:3]])
+    for k in range(3):
+        u1, i1 = W.solve(_t(loads[k], torch.float64))
+        assert iw[k]["status"] == 0 and iw[k]["iterations"] == i1["iterations"]
+        assert torch.equal(uw[k], u1)
