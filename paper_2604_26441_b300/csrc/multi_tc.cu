@@ -133,10 +133,10 @@ __device__ __forceinline__ void tmem_ld24(unsigned addr, float* v) {
 // u rounded to TF32 (11 significant bits, ties away from zero).
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
 
-template <int MODE, bool DOT>
+template <int MODE, bool DOT, int PASSES>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_mfine_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tme, MFineArgs a,
-           const float* __restrict__ Bop, float scale, int passes, int zchunk, int gx, int gy, int ngroups) {
+           const float* __restrict__ Bop, float scale, int zchunk, int gx, int gy, int ngroups) {
     extern __shared__ unsigned char sm_raw[];
     unsigned char* sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
     uint64_t* tbar = reinterpret_cast<uint64_t*>(sm + kBarOff);  // [3] plane slots
@@ -182,8 +182,10 @@ k_mfine_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tslot;
 
-    // thread 0's accounting of issued copies and MMA commits, for the drain
-    int tiss[3] = {0, 0, 0}, tcon[3] = {0, 0, 0}, miss[2] = {0, 0}, mcon[2] = {0, 0};
+    // for the drain (thread 0's view): the last plane issued and the last one
+    // waited for, the last layer whose MMAs were committed and the last one
+    // waited for; copies and commits complete in order on each barrier
+    int p_iss = kb - 1, p_con = kb - 1, z_iss = kb - 1, z_con = kb - 1;
     auto slot_of = [&](int p) { return (p - kb) % 3; };
     auto issue_plane = [&](int p) {  // node plane p and moduli layer p - 1
         const int s = slot_of(p);
@@ -191,7 +193,7 @@ k_mfine_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
         mbar_expect_tx(&tbar[s], (unsigned)(kPlaneB + kEB));
         tma4(st, &tmx, 32 * lg, x0e, y0e, p, &tbar[s]);
         tma3(st + kLimbs * kPlaneB, &tme, es, y0e, p - 1, &tbar[s]);
-        ++tiss[s];
+        p_iss = p;
     };
     auto wait_bar = [&](uint64_t* bar, unsigned parity) -> bool {
         for (unsigned it = 0; it < kTcSpinM; ++it)
@@ -203,13 +205,13 @@ k_mfine_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
     auto wait_plane = [&](int p) -> bool {
         const int s = slot_of(p);
         const bool ok = wait_bar(&tbar[s], (unsigned)(((p - kb) / 3) & 1));
-        if (ok) ++tcon[s];
+        if (ok) p_con = p;
         return ok;
     };
     auto wait_mma = [&](int z) -> bool {
         const int b = (z - kb) & 1;
         const bool ok = wait_bar(&mbar[b], (unsigned)(((z - kb) >> 1) & 1));
-        if (ok) ++mcon[b];
+        if (ok) z_con = z;
         return ok;
     };
     // The record (in the hi limb) -> hi, mid, lo on a grid shared by the whole
@@ -219,7 +221,7 @@ k_mfine_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
     // a TF32 number; all hi products of an element are multiples of one or two
     // neighbouring quanta, so their sum is exact even where u changes sign or
     // magnitude inside the element, and mid and lo follow at 2^-11 and 2^-22.
-    double* const qred = red;  // [16 warps][8 loads] maxima, as doubles (scratch shared with the dot sums)
+    float* const qred = reinterpret_cast<float*>(red);  // [16 warps][8 loads] maxima (scratch shared with the dot sums)
     auto split = [&](int p) {
         unsigned char* st = sm + slot_of(p) * kSlotB;
         float4* hi = reinterpret_cast<float4*>(st);
@@ -233,11 +235,11 @@ k_mfine_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
         __syncthreads();  // the previous split's reads of qred are done
-        if (lane < kLG) qred[warp * kLG + lane] = (double)mx;
+        if (lane < kLG) qred[warp * kLG + lane] = mx;
         __syncthreads();
         float m = 0.f;
 #pragma unroll
-        for (int w = 0; w < 16; ++w) m = fmaxf(m, (float)qred[w * kLG + (tid & 7)]);
+        for (int w = 0; w < 16; ++w) m = fmaxf(m, qred[w * kLG + (tid & 7)]);
         int ex = 0;
         (void)frexpf(m, &ex);                  // m < 2^ex (m = 0: ex = 0)
         const float Q = ldexpf(1.f, ex - 11), iQ = ldexpf(1.f, 11 - ex);
@@ -259,25 +261,30 @@ k_mfine_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
         const unsigned p0 = smem_u32(sm + slot_of(z) * kSlotB), p1 = smem_u32(sm + slot_of(z + 1) * kSlotB);
         const unsigned bb = smem_u32(sm + kBOff);
         // limb-major: all hi products of the element first (their running sum
-        // is exact: one quantum, far from 2^24 quanta), then mid, then lo
+        // is exact: one quantum, far from 2^24 quanta), then mid, then lo.
+        // Descriptors: the plane and operand bases once, then compile-time
+        // offsets (the address field holds byte address / 16 in its low bits).
+        const uint64_t dA0 = mdesc(p0, kNodeB, kNodeB), dA1 = mdesc(p1, kNodeB, kNodeB), dB = mdesc(bb, 512, 128);
+#pragma unroll
         for (int t = 0; t < kTEY; ++t) {
             const unsigned d = tmem + (unsigned)(b * 256 + t * 32);
-            for (int pass = 0; pass < passes; ++pass) {
+#pragma unroll
+            for (int pass = 0; pass < PASSES; ++pass) {
                 const int limb = pass < 3 ? pass : pass - 3;  // u limb: hi, mid, lo (then hi, mid with K_e lo)
                 const unsigned boff = pass < 3 ? 0u : 4096u;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int dy = j & 1, dz = j >> 1;
-                    const unsigned aa = (dz ? p1 : p0) + (unsigned)((t + dy) * kRowB + limb * kPlaneB);
-                    mma_tf32_m(d, mdesc(aa, kNodeB, kNodeB), mdesc(bb + boff + (unsigned)(j * 1024), 512, 128),
-                               (pass > 0 || j > 0) ? 1u : 0u);
+                    const uint64_t da = (dz ? dA1 : dA0) + (uint64_t)(((t + dy) * kRowB + limb * kPlaneB) >> 4);
+                    const uint64_t db = dB + (uint64_t)((boff + (unsigned)(j * 1024)) >> 4);
+                    mma_tf32_m(d, da, db, (pass > 0 || j > 0) ? 1u : 0u);
                 }
             }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&mbar[b]))
                      : "memory");
-        ++miss[b];
+        z_iss = z;
     };
 
     float top[2][12];
@@ -413,10 +420,8 @@ k_mfine_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
         // drain: every copy and MMA commit issued must complete before the
         // shared memory and TMEM are released
         if (tid == 0) {
-            for (int s = 0; s < 3; ++s)
-                for (int k = tcon[s]; k < tiss[s]; ++k) wait_bar(&tbar[s], (unsigned)(k & 1));
-            for (int b = 0; b < 2; ++b)
-                for (int k = mcon[b]; k < miss[b]; ++k) wait_bar(&mbar[b], (unsigned)(k & 1));
+            for (int p = p_con + 1; p <= p_iss; ++p) wait_bar(&tbar[slot_of(p)], (unsigned)(((p - kb) / 3) & 1));
+            for (int z = z_con + 1; z <= z_iss; ++z) wait_bar(&mbar[(z - kb) & 1], (unsigned)(((z - kb) >> 1) & 1));
             atomicExch(a.err, 1);
         }
         __syncthreads();
@@ -478,12 +483,11 @@ TcPlan tc_plan(int nx, int ny, int nz, int ngroups) {
     return best;
 }
 
-template <int MODE, bool DOT>
-int tc_launch(const TcPlan& pl, int ngroups, const MFineArgs& a, const float* Bop, float scale, int passes,
-              cudaStream_t s) {
+template <int MODE, bool DOT, int PASSES>
+int tc_launch(const TcPlan& pl, int ngroups, const MFineArgs& a, const float* Bop, float scale, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_mfine_tc<MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem) !=
+        if (cudaFuncSetAttribute(k_mfine_tc<MODE, DOT, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem) !=
             cudaSuccess)
             return GMG_ERR_CUDA;
         attr = true;
@@ -500,9 +504,16 @@ int tc_launch(const TcPlan& pl, int ngroups, const MFineArgs& a, const float* Bo
     if (!encode_f32_map_strided(&mx, a.xin, 4, vd, vs, bx) || !encode_f32_map_strided(&me, a.Ep, 3, ed, es, be))
         return GMG_ERR_CUDA;
     note_launch();
-    pdl_launch(k_mfine_tc<MODE, DOT>, dim3((unsigned)(pl.gx * pl.gy * pl.gz * ngroups)), dim3(kTcThreads),
-               (size_t)kSmem, s, mx, me, a, Bop, scale, passes, pl.zc, pl.gx, pl.gy, ngroups);
+    pdl_launch(k_mfine_tc<MODE, DOT, PASSES>, dim3((unsigned)(pl.gx * pl.gy * pl.gz * ngroups)), dim3(kTcThreads),
+               (size_t)kSmem, s, mx, me, a, Bop, scale, pl.zc, pl.gx, pl.gy, ngroups);
     return GMG_OK;
+}
+
+template <int MODE, bool DOT>
+int tc_launch_p(const TcPlan& pl, int ngroups, const MFineArgs& a, const float* Bop, float scale, int passes,
+                cudaStream_t s) {
+    return passes > 3 ? tc_launch<MODE, DOT, 5>(pl, ngroups, a, Bop, scale, s)
+                      : tc_launch<MODE, DOT, 3>(pl, ngroups, a, Bop, scale, s);
 }
 
 // standard local index of the corner at offset (dx, dy, dz)
@@ -529,12 +540,12 @@ int launch_mfine_tc(int mode, int dot, const MFineArgs& a, const float* Bop, flo
     const int ngroups = a.nl > kLG ? 2 : 1;
     const TcPlan pl = tc_plan(a.nx, a.ny, a.nz, 2);  // the same tiles for any load count (partial layout)
     if (mode == FM_APPLY)
-        return dot ? tc_launch<FM_APPLY, true>(pl, ngroups, a, Bop, scale, passes, s)
-                   : tc_launch<FM_APPLY, false>(pl, ngroups, a, Bop, scale, passes, s);
+        return dot ? tc_launch_p<FM_APPLY, true>(pl, ngroups, a, Bop, scale, passes, s)
+                   : tc_launch_p<FM_APPLY, false>(pl, ngroups, a, Bop, scale, passes, s);
     if (mode == FM_SMOOTH)
-        return dot ? tc_launch<FM_SMOOTH, true>(pl, ngroups, a, Bop, scale, passes, s)
-                   : tc_launch<FM_SMOOTH, false>(pl, ngroups, a, Bop, scale, passes, s);
-    return tc_launch<FM_RESID, false>(pl, ngroups, a, Bop, scale, passes, s);
+        return dot ? tc_launch_p<FM_SMOOTH, true>(pl, ngroups, a, Bop, scale, passes, s)
+                   : tc_launch_p<FM_SMOOTH, false>(pl, ngroups, a, Bop, scale, passes, s);
+    return tc_launch_p<FM_RESID, false>(pl, ngroups, a, Bop, scale, passes, s);
 }
 
 int build_mfine_tc_operand(const double* Ke, float* out, float* scale_out) {
