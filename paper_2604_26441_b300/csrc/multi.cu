@@ -1075,11 +1075,10 @@ int rec_grid(long long nrec) {
     return (int)std::max<long long>(1, std::min<long long>((nrec + kMT - 1) / kMT, kMBlocks));
 }
 
-MBsrArgs mbsr_args(const Level& l, const MultiLevel& m) {
+MBsrArgs mbsr_args(const Level& l) {
     MBsrArgs a{};
     a.nx = l.nx; a.ny = l.ny; a.nz = l.nz; a.nn = (int)l.nn;
     a.ps = l.ps; a.A = l.A32; a.invdiag = l.invdiag; a.mask = l.mask; a.coef = l.coef;
-    (void)m;
     return a;
 }
 
@@ -1279,7 +1278,7 @@ void mlevel_apply(gmg_handle* h, int li, const float* x, float* y, int dot_slot,
                        w.pstride, w.sc, dot_slot, op);
         }
     } else {
-        MBsrArgs a = mbsr_args(h->lev[li], w.lev[li]);
+        MBsrArgs a = mbsr_args(h->lev[li]);
         a.xin = x; a.out = y;
         launch_mbsr(FM_APPLY, a, s);
     }
@@ -1292,7 +1291,7 @@ void mlevel_resid(gmg_handle* h, int li, const float* b, const float* x, float* 
         a.xin = x; a.b = b; a.out = t;
         if (mfine_launch(h, FM_RESID, 0, a) != GMG_OK) h->mw->launch_err = 1;
     } else {
-        MBsrArgs a = mbsr_args(h->lev[li], h->mw->lev[li]);
+        MBsrArgs a = mbsr_args(h->lev[li]);
         a.xin = x; a.b = b; a.out = t;
         launch_mbsr(FM_RESID, a, s);
     }
@@ -1316,7 +1315,7 @@ void msmooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, 
             if (mfine_launch(h, FM_SMOOTH, dot, a) != GMG_OK) w.launch_err = 1;
         }
     } else {
-        MBsrArgs a = mbsr_args(l, w.lev[li]);
+        MBsrArgs a = mbsr_args(l);
         a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
         if (zero_init) {
             note_launch();

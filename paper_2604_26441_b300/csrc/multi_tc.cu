@@ -130,9 +130,6 @@ __device__ __forceinline__ void tmem_ld24(unsigned addr, float* v) {
     for (int i = 0; i < 24; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// u rounded to TF32 (11 significant bits, ties away from zero).
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
-
 template <int MODE, bool DOT, int PASSES>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_mfine_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tme, MFineArgs a,
