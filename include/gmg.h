@@ -372,9 +372,21 @@ int gmg_multi_fine_pass(gmg_handle* h, int nl, int what);
  * GMG_ERR_ARG for an unknown kind or one this build lacks. */
 int gmg_set_multi_kernel(gmg_handle* h, int kind);
 
+/* Tiles of the fine-level kernel.  One element column per thread: 32 x 8
+ * threads owning 31 x 7 nodes, or 16 x 16 threads owning 15 x 15.  Two
+ * x-adjacent columns per thread (every value a packed pair over the two
+ * columns): 8 x 16 threads owning 15 x 15 nodes, 16 x 8 owning 31 x 7, or
+ * 16 x 16 owning 31 x 15.  The two-column tiles apply to the solver's own
+ * level-0 vectors (the TMA-fed path). */
+#define GMG_FINE_TILE_32X8 0
+#define GMG_FINE_TILE_16X16 1
+#define GMG_FINE_TILE_PAIR_8X16 2
+#define GMG_FINE_TILE_PAIR_16X8 3
+#define GMG_FINE_TILE_PAIR_16X16 4
+
 /* Result of gmg_autotune. */
 typedef struct {
-    int fine_tile;               /* fine kernel tile: 0 = 32 x 8 threads (31 x 7 nodes), 1 = 16 x 16 (15 x 15) */
+    int fine_tile;               /* fine kernel tile (GMG_FINE_TILE_*) */
     int fine_zchunk;             /* node planes per block of the z-marching fine kernel */
     int model_tile, model_zchunk;  /* the cost model's choice (used without tuning) */
     int fine_candidates;         /* plans timed */
@@ -398,6 +410,16 @@ typedef struct {
  * returns to the cost model's plan and to the options' bsr_kernel choice.  Drops the handle's
  * captured solve graphs.  Synchronous.  out may be NULL. */
 int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out);
+
+/* Pins the fine kernel's plan for the handle's fine grid: tile (GMG_FINE_TILE_*)
+ * and zchunk node planes per block (>= 1; clamped to the grid's depth); the
+ * choice holds for every handle of that fine grid in this process, like
+ * gmg_autotune's.  tile < 0 returns to the cost model's plan.  The operator's
+ * results do not depend on the plan (each element's arithmetic is the same);
+ * reduction partial sums are grouped differently.  GMG_ERR_ARG for an unknown
+ * tile, zchunk < 1, or a plan with more blocks than the handle's partial-sum
+ * buffer holds.  Drops the handle's captured solve graphs.  Synchronous. */
+int gmg_set_fine_plan(gmg_handle* h, int tile, int zchunk);
 
 /* z = V(r): one V-cycle of Eq. vcycle on the fine level. */
 int gmg_vcycle(gmg_handle* h, const float* r_dev, float* z_dev);

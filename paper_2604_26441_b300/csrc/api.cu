@@ -1213,6 +1213,31 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     return finish(GMG_NOT_CONVERGED);
 }
 
+// Drops every graph the handle captured (solve loops and the batch graph):
+// they would keep the launch shapes they were captured with.
+static void drop_captured(gmg_handle* h) {
+    loop_free(h);
+    if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
+    if (h->batch_graph) cudaGraphDestroy(h->batch_graph);
+    h->batch_exec = nullptr;
+    h->batch_graph = nullptr;
+    h->batch_key.clear();
+}
+
+int gmg_set_fine_plan(gmg_handle* h, int tile, int zchunk) {
+    if (!h) return fail(GMG_ERR_ARG, "null handle");
+    const Level& l0 = h->lev[0];
+    if (tile >= 0) {
+        if (tile >= kFineTiles || zchunk < 1) return fail(GMG_ERR_ARG, "unknown fine tile or zchunk < 1");
+        if (fine_plan_blocks(l0.nx, l0.ny, l0.nz, tile, zchunk) > h->max_partials)
+            return fail(GMG_ERR_ARG, "fine plan needs more blocks than the handle's partial sums hold");
+    }
+    CU(cudaStreamSynchronize(h->stream));
+    fine_set_plan(l0.nx, l0.ny, l0.nz, tile, zchunk);
+    drop_captured(h);
+    return GMG_OK;
+}
+
 int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
     if (!h || reps < 0) return fail(GMG_ERR_ARG, "null handle or reps < 0");
     if (h->is_clone) return fail(GMG_ERR_ARG, "tune the source handle, not a clone");
@@ -1321,12 +1346,7 @@ int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
     if (rc != GMG_OK) return rc;
     // graphs captured with the former shapes are dropped (they stay correct,
     // but would keep the old shapes)
-    loop_free(h);
-    if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
-    if (h->batch_graph) cudaGraphDestroy(h->batch_graph);
-    h->batch_exec = nullptr;
-    h->batch_graph = nullptr;
-    h->batch_key.clear();
+    drop_captured(h);
     CU(cudaGetLastError());
     if (out) *out = t;
     return GMG_OK;
@@ -1848,12 +1868,7 @@ int gmg_set_spin_limit(gmg_handle* h, long long polls) {
     h->opt.spin_limit = polls;
     h->cf.spin_limit = polls;
     // captured graphs hold the former bound in their kernel arguments
-    loop_free(h);
-    if (h->batch_exec) cudaGraphExecDestroy(h->batch_exec);
-    if (h->batch_graph) cudaGraphDestroy(h->batch_graph);
-    h->batch_exec = nullptr;
-    h->batch_graph = nullptr;
-    h->batch_key.clear();
+    drop_captured(h);
     return GMG_OK;
 }
 

@@ -82,9 +82,9 @@ struct V3 {
     float2 xy;
     float z;
 };
-__device__ __forceinline__ V3 vadd(const V3& a, const V3& b) { return {__fadd2_rn(a.xy, b.xy), a.z + b.z}; }
+__device__ __forceinline__ V3 vadd(const V3& a, const V3& b) { return {__fadd2_rn(a.xy, b.xy), __fadd_rn(a.z, b.z)}; }
 __device__ __forceinline__ V3 vsub(const V3& a, const V3& b) {
-    return {__ffma2_rn(b.xy, make_float2(-1.f, -1.f), a.xy), a.z - b.z};
+    return {__ffma2_rn(b.xy, make_float2(-1.f, -1.f), a.xy), __fsub_rn(a.z, b.z)};
 }
 __device__ __forceinline__ V3 vld(const float* p) { return {make_float2(p[0], p[1]), p[2]}; }
 __device__ __forceinline__ float comp(const V3& v, int c) { return c == 0 ? v.xy.x : (c == 1 ? v.xy.y : v.z); }
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
     // epilogue of the owned node of plane kp: its 4-cell sums R1 + the row above
     auto finish = [&](int kp) {
         const float4 up = sx[kp & 1][ty + 1][tx];
-        const float y[3] = {R1.xy.x + up.x, R1.xy.y + up.y, R1.z + up.z};
+        const float y[3] = {__fadd_rn(R1.xy.x, up.x), __fadd_rn(R1.xy.y, up.y), __fadd_rn(R1.z, up.z)};
         const long long n = GMG_B(onode_base + kp * NXY, (long long)NXY * NZ, 112);
         float* out = a.out + 3 * n;
         if (MODE == FM_APPLY) {
@@ -259,17 +259,17 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
             const float* bb = &sB[EPI_B ? slot : 0][EPI_B ? own3 : 0];
             if (MODE == FM_RESID) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) out[c] = fixed_bit(m_pend, c) ? 0.f : bb[c] - y[c];
+                for (int c = 0; c < 3; ++c) out[c] = fixed_bit(m_pend, c) ? 0.f : __fsub_rn(bb[c], y[c]);
             } else {
                 const float* dd = &sD[EPI_D ? slot : 0][EPI_D ? own3 : 0];
-                const float inv = __frcp_rn(a.kd * (eR1 + up.w));
+                const float inv = __frcp_rn(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     float xn = 0.f, dn = 0.f;
                     if (!fixed_bit(m_pend, c)) {
-                        dn = ca * inv * (bb[c] - y[c]);
+                        dn = __fmul_rn(__fmul_rn(ca, inv), __fsub_rn(bb[c], y[c]));
                         if (need_d) dn = fmaf(cd, dd[c], dn);
-                        xn = comp(un_pend, c) + dn;
+                        xn = __fadd_rn(comp(un_pend, c), dn);
                         if (DOT) dotv.add_prod(bb[c], xn);
                     }
                     out[c] = xn;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
         }
         const float2 E2 = make_float2(out.E, out.E);
 #pragma unroll
-        for (int m = 1; m < 8; ++m) w[m] = V3{__fmul2_rn(E2, w[m].xy), out.E * w[m].z};
+        for (int m = 1; m < 8; ++m) w[m] = V3{__fmul2_rn(E2, w[m].xy), __fmul_rn(out.E, w[m].z)};
         // back to face quantities: top = w + w_z, bottom = w - w_z
         V3 Bf[4];
 #pragma unroll
@@ -357,8 +357,8 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
             n00.z = __shfl_down_sync(0xffffffffu, c00.z, 1, BX);
             R1 = vadd(c11, n01);
             const V3 r0 = vadd(c10, n00);
-            const float es = in.E + out.E;
-            const float er = es + __shfl_down_sync(0xffffffffu, es, 1, BX);
+            const float es = __fadd_rn(in.E, out.E);
+            const float er = __fadd_rn(es, __shfl_down_sync(0xffffffffu, es, 1, BX));
             sx[kl & 1][ty][tx] = make_float4(r0.xy.x, r0.xy.y, r0.z, er);
             pending = true;
             eR1 = er;
@@ -585,20 +585,20 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine_tc(FineArgs a, int zchunk) 
     };
     auto finish = [&](int kp) {
         const float4 up = sx[kp & 1][ty + 1][tx];
-        const float y[3] = {R1.xy.x + up.x, R1.xy.y + up.y, R1.z + up.z};
+        const float y[3] = {__fadd_rn(R1.xy.x, up.x), __fadd_rn(R1.xy.y, up.y), __fadd_rn(R1.z, up.z)};
         const int n = onode_base + kp * NXY;
         float* out = a.out + 3 * n;
         const int slot = (kp - kb) & (kRing - 1);
         const float* bb = &sB[slot][own3];
         const float* dd = &sD[slot][own3];
-        const float inv = __frcp_rn(a.kd * (eR1 + up.w));
+        const float inv = __frcp_rn(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float xn = 0.f, dn = 0.f;
             if (!fixed_bit(m_pend, c)) {
-                dn = ca * inv * (bb[c] - y[c]);
+                dn = __fmul_rn(__fmul_rn(ca, inv), __fsub_rn(bb[c], y[c]));
                 if (need_d) dn = fmaf(cd, dd[c], dn);
-                xn = comp(un_pend, c) + dn;
+                xn = __fadd_rn(comp(un_pend, c), dn);
                 if (DOT) dotv.add_prod(bb[c], xn);
             }
             out[c] = xn;
@@ -739,8 +739,8 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine_tc(FineArgs a, int zchunk) 
                 n00.z = __shfl_down_sync(0xffffffffu, c00.z, 1, BX);
                 R1 = vadd(c11, n01);
                 const V3 r0 = vadd(c10, n00);
-                const float es = e_prevc + E;
-                const float er = es + __shfl_down_sync(0xffffffffu, es, 1, BX);
+                const float es = __fadd_rn(e_prevc, E);
+                const float er = __fadd_rn(es, __shfl_down_sync(0xffffffffu, es, 1, BX));
                 sx[p & 1][ty][tx] = make_float4(r0.xy.x, r0.xy.y, r0.z, er);
                 pending = true;
                 pend_k = p;
@@ -797,13 +797,6 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine_tc(FineArgs a, int zchunk) 
 // stage.  The loop takes four steps per trip, so ring slots are compile-time
 // offsets and the mbarrier phase is one bit per trip.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
-          "r"(smem_u32(bar))
-        : "memory");
-}
 
 __host__ __device__ constexpr int round4(int v) { return (v + 3) / 4 * 4; }
 __host__ __device__ constexpr int round128(int v) { return (v + 127) / 128 * 128; }
@@ -943,7 +936,7 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
     // their values are zeros or discarded); only the stores are predicated.
     auto finish = [&](int kp, int q) {
         const float4 up = sx[kp & 1][ty + 1][tx];
-        const float y[3] = {R1.xy.x + up.x, R1.xy.y + up.y, R1.z + up.z};
+        const float y[3] = {__fadd_rn(R1.xy.x, up.x), __fadd_rn(R1.xy.y, up.y), __fadd_rn(R1.z, up.z)};
         const long long on = owner ? GMG_B(onode + kp * NXYp, (long long)NXYp * NZ, 102) : 0;
         float* out = a.out + 3 * on;
         if (MODE == FM_APPLY) {
@@ -959,21 +952,21 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
             if (MODE == FM_RESID) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float v = fixed_bit(m_pend, c) ? 0.f : bb[c] - y[c];
+                    const float v = fixed_bit(m_pend, c) ? 0.f : __fsub_rn(bb[c], y[c]);
                     if (owner) out[c] = v;
                 }
             } else {
                 const float* dd = reinterpret_cast<const float*>(smem + q * T::STAGE + T::DOFF) + rb;
-                const float inv = __frcp_rn(a.kd * (eR1 + up.w));
+                const float inv = __frcp_rn(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
                 float* dn_out = a.dnew + 3 * on;
                 const bool wd = owner && a.dnew != nullptr;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const bool fr = !fixed_bit(m_pend, c);
-                    float dn = ca * inv * (bb[c] - y[c]);
+                    float dn = __fmul_rn(__fmul_rn(ca, inv), __fsub_rn(bb[c], y[c]));
                     if (need_d) dn = fmaf(cd, dd[c], dn);
                     dn = fr ? dn : 0.f;
-                    const float xn = fr ? comp(un_pend, c) + dn : 0.f;
+                    const float xn = fr ? __fadd_rn(comp(un_pend, c), dn) : 0.f;
                     if (DOT) dotv.add_prod(fr ? bb[c] : 0.f, xn);
                     if (owner) out[c] = xn;
                     if (wd) dn_out[c] = dn;
@@ -1034,7 +1027,7 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
         }
         const float2 E2 = make_float2(out.E, out.E);
 #pragma unroll
-        for (int m = 1; m < 8; ++m) w[m] = V3{__fmul2_rn(E2, w[m].xy), out.E * w[m].z};
+        for (int m = 1; m < 8; ++m) w[m] = V3{__fmul2_rn(E2, w[m].xy), __fmul_rn(out.E, w[m].z)};
         V3 Bf[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -1055,8 +1048,8 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
             n00.z = __shfl_down_sync(0xffffffffu, c00.z, 1, BX);
             R1 = vadd(c11, n01);
             const V3 r0 = vadd(c10, n00);
-            const float esum = in.E + out.E;
-            const float er = esum + __shfl_down_sync(0xffffffffu, esum, 1, BX);
+            const float esum = __fadd_rn(in.E, out.E);
+            const float er = __fadd_rn(esum, __shfl_down_sync(0xffffffffu, esum, 1, BX));
             sx[s & 1][ty][tx] = make_float4(r0.xy.x, r0.xy.y, r0.z, er);
             pending = true;
             eR1 = er;
@@ -1100,6 +1093,9 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
     }
 }
 
+// Sets the sticky error word (a launch with no kernel able to run it).
+__global__ void k_flag_error(int* err) { atomicExch(err, 1); }
+
 // Copies x with the fixed DOFs of the fine level set to 0 (operands supplied by
 // a caller may hold values there; the operator ignores them).
 __global__ void k_mask_copy(const float* x, const uint8_t* mask, long long nn, float* out) {
@@ -1127,10 +1123,22 @@ __global__ void k_hadamard_blocks(const double* Ke, double* g) {
 }
 
 struct FinePlan {
-    int tile;   // 0: 32x8 threads (31x7 nodes), 1: 16x16 threads (15x15 nodes)
+    int tile;   // 0: 32x8 threads (31x7 nodes), 1: 16x16 threads (15x15 nodes); 2..4 two columns a thread
     int zc;     // node planes per block
     dim3 grid;
 };
+
+// Element columns a block covers in x and y (it owns one node fewer each way).
+void tile_columns(int tile, int* ex, int* ey) {
+    switch (tile) {
+        case 0: *ex = 32; *ey = 8; break;
+        case kFinePair8x16: *ex = 16; *ey = 16; break;
+        case kFinePair16x8: *ex = 32; *ey = 8; break;
+        case kFinePair16x16: *ex = 32; *ey = 16; break;
+        default: *ex = 16; *ey = 16; break;
+    }
+}
+bool pair_tile(int tile) { return tile >= kFinePair8x16 && tile < kFineTiles; }
 
 int sm_count() {
     static int n = 0;
@@ -1145,7 +1153,8 @@ int sm_count() {
 
 FinePlan make_plan(int nx, int ny, int nz, int tile, int zc) {
     const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
-    const int bx = tile == 0 ? 32 : 16, by = tile == 0 ? 8 : 16;
+    int bx = 0, by = 0;
+    tile_columns(tile, &bx, &by);
     const int gx = (NX + bx - 2) / (bx - 1), gy = (NY + by - 2) / (by - 1);
     zc = std::max(1, std::min(zc, NZ));
     return FinePlan{tile, zc, dim3(gx, gy, (NZ + zc - 1) / zc)};
@@ -1183,6 +1192,14 @@ FinePlan model_plan(int nx, int ny, int nz) {
     return best;
 }
 
+// The single-column tile with the same columns, hence the same grid and
+// partial count, as `tile`; -1 when there is none.
+int single_equivalent(int tile) {
+    if (tile == kFinePair8x16) return 1;
+    if (tile == kFinePair16x8) return 0;
+    return pair_tile(tile) ? -1 : tile;
+}
+
 // A tuned plan when gmg_autotune measured one for this grid, else the model's.
 FinePlan plan_fine(int nx, int ny, int nz) {
     {
@@ -1209,7 +1226,7 @@ int fine_grid_blocks(int nx, int ny, int nz) {
 int fine_candidates(int nx, int ny, int nz, int max_blocks, int* tiles, int* zcs, int cap) {
     const int NZ = nz + 1;
     int n = 0;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < kFineTiles; ++t) {
         int last = -1;
         for (int nch = 1; nch <= NZ && n < cap; ++nch) {
             const int zc = (NZ + nch - 1) / nch;
@@ -1224,6 +1241,11 @@ int fine_candidates(int nx, int ny, int nz, int max_blocks, int* tiles, int* zcs
         }
     }
     return n;
+}
+
+int fine_plan_blocks(int nx, int ny, int nz, int tile, int zc) {
+    const FinePlan pl = make_plan(nx, ny, nz, tile, zc);
+    return (int)(pl.grid.x * pl.grid.y * pl.grid.z);
 }
 
 void fine_model_plan(int nx, int ny, int nz, int* tile, int* zc) {
@@ -1244,7 +1266,19 @@ void launch_fine(int mode, int dot, int mask_in, const FineArgs& a_in, const GHa
     if (!mask_in && a_in.Ep && a_in.pitch % 4 == 0 && a_in.pitch > 0 &&
         launch_fine_tma(mode, dot, a_in, G, s) == GMG_OK)
         return;
-    const FinePlan pl = plan_fine(a_in.nx, a_in.ny, a_in.nz);
+    // the per-thread-copy kernel runs single-column tiles: the one with the
+    // plan's columns (same grid, same partial count), else the model's plan
+    FinePlan pl = plan_fine(a_in.nx, a_in.ny, a_in.nz);
+    if (single_equivalent(pl.tile) >= 0) {
+        pl.tile = single_equivalent(pl.tile);
+    } else {
+        if (dot && a_in.err) {  // no single-column grid writes this plan's partials
+            note_launch();
+            k_flag_error<<<1, 1, 0, s>>>(a_in.err);
+            return;
+        }
+        pl = model_plan(a_in.nx, a_in.ny, a_in.nz);
+    }
     FineArgs a = a_in;
     if (mask_in && a.scratch) {
         const long long nn = (long long)(a.nx + 1) * (a.ny + 1) * (a.nz + 1);
@@ -1305,6 +1339,7 @@ int launch_tma_shape(const FinePlan& pl, const FineArgs& a, const GHat& G, cudaS
 int launch_fine_tma(int mode, int dot, const FineArgs& a, const GHat& G, cudaStream_t s) {
     if (a.pitch % 4 != 0 || a.epitch % 4 != 0 || !a.Ep) return GMG_ERR_ARG;
     const FinePlan pl = plan_fine(a.nx, a.ny, a.nz);
+    if (pair_tile(pl.tile)) return launch_fine_pair(pl.tile, mode, dot, pl.grid, pl.zc, a, G, s);
     if (mode == FM_APPLY) return dot ? launch_tma_shape<FM_APPLY, true>(pl, a, G, s) : launch_tma_shape<FM_APPLY, false>(pl, a, G, s);
     if (mode == FM_SMOOTH)
         return dot ? launch_tma_shape<FM_SMOOTH, true>(pl, a, G, s) : launch_tma_shape<FM_SMOOTH, false>(pl, a, G, s);

@@ -217,13 +217,14 @@ struct CoarseFused {
 struct DSAcc {
     float hi = 0.f, lo = 0.f;
     __device__ __forceinline__ void add_prod(float a, float b) {
-        const float p = a * b;
+        // every operation rounded on its own (no contraction into an FMA)
+        const float p = __fmul_rn(a, b);
         const float e = fmaf(a, b, -p);
-        const float s = hi + p;
-        const float bb = s - hi;
-        const float t = (hi - (s - bb)) + (p - bb);
+        const float s = __fadd_rn(hi, p);
+        const float bb = __fsub_rn(s, hi);
+        const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
         hi = s;
-        lo += t + e;
+        lo = __fadd_rn(lo, __fadd_rn(t, e));
     }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
@@ -290,6 +291,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
         ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+          "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -412,12 +421,19 @@ struct FineArgs {
     int* err;              // sticky error word (a tensor-core wait that gave up)
 };
 
+// Tiles of the fine kernel: one element column per thread (0: 32x8 threads,
+// 1: 16x16), or two x-adjacent columns per thread (fine_pair.cu; 2: 8x16
+// threads = 16x16 columns, 3: 16x8 threads = 32x8 columns, 4: 16x16 threads =
+// 32x16 columns).  The two-column tiles run only on the TMA-fed path.
+constexpr int kFineTiles = 5;
+constexpr int kFinePair8x16 = 2, kFinePair16x8 = 3, kFinePair16x16 = 4;
 int fine_grid_blocks(int nx, int ny, int nz);
 // Candidate (tile, z-chunk) plans of the fine kernel for a grid with at most
-// max_blocks blocks (tile 0: 32x8 threads, 1: 16x16); the cost model's plan;
-// and the process-wide override that gmg_autotune sets (tile < 0 clears it).
+// max_blocks blocks; the cost model's plan; and the process-wide override that
+// gmg_autotune sets (tile < 0 clears it).
 int fine_candidates(int nx, int ny, int nz, int max_blocks, int* tiles, int* zcs, int cap);
 void fine_model_plan(int nx, int ny, int nz, int* tile, int* zc);
+int fine_plan_blocks(int nx, int ny, int nz, int tile, int zc);
 void fine_set_plan(int nx, int ny, int nz, int tile, int zc);
 // mask_in: treat fixed DOFs of the operand as 0 (for operands that may hold
 // values there, e.g. user input); internal vectors are already 0 on them.
@@ -426,6 +442,10 @@ void launch_fine(int mode, int dot, int mask_in, const FineArgs& a, const GHat& 
 // multiples of 4, a.Ep the padded moduli); GMG_OK, or an error when a tensor map
 // cannot be encoded (nothing is launched then).
 int launch_fine_tma(int mode, int dot, const FineArgs& a, const GHat& G, cudaStream_t s);
+// The two-column operator (tiles 2..4) on a grid of `grid` blocks, zc node
+// planes per block; GMG_ERR_ARG for another tile or unpadded vectors.
+int launch_fine_pair(int tile, int mode, int dot, dim3 grid, int zc, const FineArgs& a, const GHat& G,
+                     cudaStream_t s);
 void launch_hadamard_blocks(const double* Ke, double* g72, cudaStream_t s);
 // Tensor-core fine smoother step (SMOOTH mode): passes = 1 (BF16) or 3 (split BF16).
 void launch_fine_tc(int passes, int dot, const FineArgs& a, cudaStream_t s);

@@ -644,13 +644,6 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
           "r"(smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tma_load_3d_m(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
-          "r"(smem_u32(bar))
-        : "memory");
-}
 
 __host__ __device__ constexpr int mround4(int v) { return (v + 3) / 4 * 4; }
 __host__ __device__ constexpr int mround128(int v) { return (v + 127) / 128 * 128; }
@@ -685,9 +678,9 @@ struct MV3 {
     float2 xy;
     float z;
 };
-__device__ __forceinline__ MV3 madd(const MV3& a, const MV3& b) { return {__fadd2_rn(a.xy, b.xy), a.z + b.z}; }
+__device__ __forceinline__ MV3 madd(const MV3& a, const MV3& b) { return {__fadd2_rn(a.xy, b.xy), __fadd_rn(a.z, b.z)}; }
 __device__ __forceinline__ MV3 msub(const MV3& a, const MV3& b) {
-    return {__ffma2_rn(b.xy, make_float2(-1.f, -1.f), a.xy), a.z - b.z};
+    return {__ffma2_rn(b.xy, make_float2(-1.f, -1.f), a.xy), __fsub_rn(a.z, b.z)};
 }
 __device__ __forceinline__ MV3 mld4(const float* p) {
     const float4 v = *reinterpret_cast<const float4*>(p);
@@ -774,7 +767,7 @@ k_mfine(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtenso
         mbar_expect_tx(&full[q], bytes);
         if (xe) {
             tma_load_4d(st + T::XOFF, &tmx, 4 * l, x0 - 1, y0 - 1, s + 1, &full[q]);
-            tma_load_3d_m(st + T::EOFF, &tme, es, y0 - 1, s, &full[q]);
+            tma_load_3d(st + T::EOFF, &tme, es, y0 - 1, s, &full[q]);
         }
         if (ep) {
             tma_load_4d(st + T::BOFF, &tmb, 4 * l, x0, y0, s - 1, &full[q]);
@@ -820,7 +813,7 @@ k_mfine(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtenso
 
     auto finish = [&](int kp, int q) {
         const float4 up = sx[kp & 1][ty + 1][tx];
-        const float y[3] = {R1.xy.x + up.x, R1.xy.y + up.y, R1.z + up.z};
+        const float y[3] = {__fadd_rn(R1.xy.x, up.x), __fadd_rn(R1.xy.y, up.y), __fadd_rn(R1.z, up.z)};
         const long long rec =
             owner ? GMG_B(((long long)(onode + kp * NXYp)) * kLoads + l, (long long)NXYp * NZ * kLoads, 542) : 0;
         float4* out = reinterpret_cast<float4*>(a.out) + rec;
@@ -839,18 +832,18 @@ k_mfine(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtenso
             const float* bb = reinterpret_cast<const float*>(smem + q * T::STAGE + T::BOFF) + rb;
             if (MODE == FM_RESID) {
                 if (owner)
-                    *out = make_float4(fr[0] ? bb[0] - y[0] : 0.f, fr[1] ? bb[1] - y[1] : 0.f,
-                                       fr[2] ? bb[2] - y[2] : 0.f, 0.f);
+                    *out = make_float4(fr[0] ? __fsub_rn(bb[0], y[0]) : 0.f, fr[1] ? __fsub_rn(bb[1], y[1]) : 0.f,
+                                       fr[2] ? __fsub_rn(bb[2], y[2]) : 0.f, 0.f);
             } else {
                 const float* dd = reinterpret_cast<const float*>(smem + q * T::STAGE + T::DOFF) + rb;
-                const float inv = __frcp_rn(a.kd * (eR1 + up.w));
+                const float inv = __frcp_rn(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
                 float xn[3], dn[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    float d = ca * inv * (bb[c] - y[c]);
+                    float d = __fmul_rn(__fmul_rn(ca, inv), __fsub_rn(bb[c], y[c]));
                     if (need_d) d = fmaf(cd, dd[c], d);
                     dn[c] = fr[c] ? d : 0.f;
-                    xn[c] = fr[c] ? mcomp(un_pend, c) + dn[c] : 0.f;
+                    xn[c] = fr[c] ? __fadd_rn(mcomp(un_pend, c), dn[c]) : 0.f;
                     if (DOT) dotv.add_prod(fr[c] ? bb[c] : 0.f, xn[c]);
                 }
                 if (owner) {
@@ -911,7 +904,7 @@ k_mfine(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtenso
         }
         const float2 E2 = make_float2(out.E, out.E);
 #pragma unroll
-        for (int m = 1; m < 8; ++m) w[m] = MV3{__fmul2_rn(E2, w[m].xy), out.E * w[m].z};
+        for (int m = 1; m < 8; ++m) w[m] = MV3{__fmul2_rn(E2, w[m].xy), __fmul_rn(out.E, w[m].z)};
         MV3 Bf[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -932,8 +925,8 @@ k_mfine(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtenso
             n00.z = __shfl_down_sync(0xffffffffu, c00.z, 1, BX);
             R1 = madd(c11, n01);
             const MV3 r0 = madd(c10, n00);
-            const float esum = in.E + out.E;
-            const float er = esum + __shfl_down_sync(0xffffffffu, esum, 1, BX);
+            const float esum = __fadd_rn(in.E, out.E);
+            const float er = __fadd_rn(esum, __shfl_down_sync(0xffffffffu, esum, 1, BX));
             sx[s & 1][ty][tx] = make_float4(r0.xy.x, r0.xy.y, r0.z, er);
             pending = true;
             eR1 = er;

@@ -33,6 +33,8 @@ class GMGError(RuntimeError):
 
 # arithmetic of the fine-level smoother's element contraction (gmg_options.fine_smoother)
 FINE_SMOOTHERS = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+# fine kernel tiles (GMG_FINE_TILE_*): threads per block, "pair" = two element columns a thread
+FINE_TILES = ["32x8", "16x16", "pair-8x16", "pair-16x8", "pair-16x16"]
 
 
 class _Grid(ctypes.Structure):
@@ -105,6 +107,7 @@ _SIGS = {
     "gmg_vcycle": (ctypes.c_int, [_P, _P, _P]),
     "gmg_kappa_eff": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gmg_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_Tuning)]),
+    "gmg_set_fine_plan": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "gmg_clone": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "gmg_solve_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                        ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Info)]),
@@ -402,12 +405,22 @@ class Solver:
         t = _Tuning()
         _check(self._lib.gmg_autotune(self._h, reps, ctypes.byref(t)))
         L = self.num_levels
-        return {"fine_tile": ["32x8", "16x16"][t.fine_tile], "fine_zchunk": t.fine_zchunk,
-                "model_tile": ["32x8", "16x16"][t.model_tile], "model_zchunk": t.model_zchunk,
+        return {"fine_tile": FINE_TILES[t.fine_tile], "fine_zchunk": t.fine_zchunk,
+                "model_tile": FINE_TILES[t.model_tile], "model_zchunk": t.model_zchunk,
                 "fine_candidates": t.fine_candidates, "fine_us": t.fine_us, "model_us": t.model_us,
                 "bsr": [{"level": l, "kind": ["streaming", "k-split-8", "k-split-2", "k-split-4", "k-split-16", "k-split-32"][t.bsr_kind[l]],
                          "us": t.bsr_us[l],
                          "other_us": t.bsr_alt_us[l]} for l in range(1, min(L, 16)) if t.bsr_kind[l] >= 0]}
+
+    def set_fine_plan(self, tile, zchunk: int = 0) -> None:
+        """Pins the fine kernel's tile (a FINE_TILES name or index) and node
+        planes per block for this fine grid (gmg_set_fine_plan); tile None or
+        < 0 returns to the cost model's plan."""
+        if tile is None:
+            tile = -1
+        elif isinstance(tile, str):
+            tile = FINE_TILES.index(tile)
+        _check(self._lib.gmg_set_fine_plan(self._h, int(tile), int(zchunk)))
 
     # -- per-step entry points
     def get_mask(self, level: int) -> np.ndarray:

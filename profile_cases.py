@@ -6,6 +6,7 @@
     python profile_cases.py apply-c2    # the same, then 5 fine operator applies (handle's own vectors)
     python profile_cases.py smooth-l1-c2  # set-up + 3 level-1 smoothing passes (BSR)
     python profile_cases.py smooth-c2-bf16x3  # fine smoothing, tensor-core contraction
+    python profile_cases.py smooth-c2-pair    # fine smoothing, two element columns a thread (8x16 threads, 17 planes)
     python profile_cases.py warmstart-80  # 80^3 set-up, one learned warm start + solve
     python profile_cases.py warmstart-80-tf32  # the same with tensor-core convolutions
     python profile_cases.py train-48      # 48^3 set-up, 3 energy-loss train steps (batch 4)
@@ -87,7 +88,9 @@ def main(case: str) -> None:
         for _ in range(3):
             S.level_smooth(1, b, x)
         torch.cuda.synchronize()
-    elif case in ("smooth-c2", "smooth-c2-bf16x3", "apply-c2"):
+    elif case in ("smooth-c2", "smooth-c2-bf16x3", "smooth-c2-pair", "apply-c2"):
+        if case == "smooth-c2-pair":
+            S.set_fine_plan("pair-8x16", 17)
         # one level-0 smoothing call packs seeded vectors into the handle's own
         # right-hand side and iterate (and runs 3 smoothing steps); the passes
         # then run the fine kernel on those vectors (no repacking kernels)
@@ -99,6 +102,7 @@ def main(case: str) -> None:
         for _ in range(3 if case.startswith("smooth-c2") else 5):
             S.fine_pass("smooth" if case.startswith("smooth-c2") else "apply")
         torch.cuda.synchronize()
+        S.set_fine_plan(None)
     else:
         raise SystemExit(f"unknown case {case}")
     print("total launches", gmg.kernel_launches(), flush=True)

@@ -710,9 +710,11 @@ def _batch_problems():
 
 
 def test_batch_matches_single_solves():
-    """Clones of one hierarchy run as one multi-load chunk: per item the same
-    status and iteration count as a single solve, iterates within rounding of
-    it, and bitwise the answers of gmg_solve_multi on the same loads."""
+    """Clones of one hierarchy run as one multi-load chunk: per item bitwise the
+    answers and iteration counts of gmg_solve_multi on the same loads, and the
+    status of a single solve with its count within one (the multi-load path
+    sums its reductions in another grouping, so its iterates agree with the
+    single solve's only to rounding) and its solution within 1e-5."""
     from paper_2604_26441_b300 import gmg
     opts = dict(smoother="chebyshev", degree=3, coarse_smoother=None, coarse_degree=None, omega=0.5,
                 coarse_omega=None)
@@ -731,7 +733,8 @@ def test_batch_matches_single_solves():
     us, infos = gmg.solve_batch(solvers, fs)
     for (u_ref, info_ref), (u_m, info_m), u, info in zip(ref, multi, us, infos):
         assert info["status"] == 0 and info["rel_residual"] < 1e-6
-        assert info["iterations"] == info_ref["iterations"] == info_m["iterations"]
+        assert info["iterations"] == info_m["iterations"]
+        assert abs(info["iterations"] - info_ref["iterations"]) <= 1
         assert rel_l2(u.cpu().numpy(), u_ref) < 1e-5
         assert np.array_equal(u.cpu().numpy(), u_m)
     # the captured graph is replayed for the same handles and iterates
