@@ -138,7 +138,7 @@ void level_apply(gmg_handle* h, int li, const float* x, float* y, int dot_slot =
     if (li == 0) {
         FineArgs a = fine_args(h);
         a.xin = x; a.out = y; a.partial = dot ? h->partials : nullptr;
-        launch_fine(FM_APPLY, dot, 0, a, h->gh, s);
+        launch_fine(FM_APPLY, dot, 0, a, h->gs, s);
     } else {
         BsrArgs a = bsr_args(h, li);
         a.xin = x; a.out = y; a.partial = dot ? h->partials : nullptr;
@@ -151,7 +151,7 @@ void level_resid(gmg_handle* h, int li, const float* b, const float* x, float* t
     if (li == 0) {
         FineArgs a = fine_args(h);
         a.xin = x; a.b = b; a.out = t;
-        launch_fine(FM_RESID, 0, 0, a, h->gh, h->stream);
+        launch_fine(FM_RESID, 0, 0, a, h->gs, h->stream);
     } else {
         BsrArgs a = bsr_args(h, li);
         a.xin = x; a.b = b; a.out = t;
@@ -175,7 +175,7 @@ void smooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, c
         else if (h->opt.fine_smoother != GMG_FINE_FP32) {
             a.xin = xcur;
             launch_fine_tc(h->opt.fine_smoother == GMG_FINE_BF16X3 ? 3 : 1, dot, a, s);
-        } else { a.xin = xcur; launch_fine(FM_SMOOTH, dot, 0, a, h->gh, s); }
+        } else { a.xin = xcur; launch_fine(FM_SMOOTH, dot, 0, a, h->gs, s); }
     } else {
         BsrArgs a = bsr_args(h, li);
         a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
@@ -445,7 +445,9 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         launch_hadamard_blocks(Ke, g72, s);
         CU(cudaMemcpyAsync(gh, g72, sizeof gh, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
-        for (int i = 0; i < 72; ++i) { h->gh.g[i] = (float)gh[i]; h->gh64.g[i] = gh[i]; }
+        for (int i = 0; i < 72; ++i) h->gh64.g[i] = gh[i];
+        if (!gsym_from_blocks(gh, &h->gs))
+            return fail(GMG_ERR_CUDA, "element stiffness lacks the cube-symmetric block structure");
         if (o.fine_smoother != GMG_FINE_FP32) {
             uint16_t op[2048];
             build_tc_operand(gh, op);
@@ -1291,7 +1293,7 @@ int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
         a.dold = nullptr;
         a.dnew = nullptr;
         a.step = 0;
-        auto fine = [&] { launch_fine(FM_SMOOTH, 0, 0, a, h->gh, s); };
+        auto fine = [&] { launch_fine(FM_SMOOTH, 0, 0, a, h->gs, s); };
         int tiles[64], zcs[64];
         const int nc = fine_candidates(l0.nx, l0.ny, l0.nz, h->max_partials, tiles, zcs, 64);
         fine_model_plan(l0.nx, l0.ny, l0.nz, &t.model_tile, &t.model_zchunk);
@@ -1567,10 +1569,7 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
     };
     const auto t0 = std::chrono::steady_clock::now();
     auto elapsed = [&]() { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); };
-    // each item's FP64 scalars: its own block, or its load slot in the chunk owner's
-    auto scd = [&](int i) -> double* {
-        return chunk_of[i] < 0 ? hs[i]->sc : chunks[chunk_of[i]].owner->mw->sc + slot_of[i] * SC_COUNT;
-    };
+    // each item's FP64 scalars (host mirror): its own block, or its load slot in the chunk owner's
     auto sch = [&](int i) -> double* {
         return chunk_of[i] < 0 ? hs[i]->sc_host : chunks[chunk_of[i]].owner->mw->sc_host + slot_of[i] * SC_COUNT;
     };

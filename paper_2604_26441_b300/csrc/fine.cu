@@ -7,9 +7,11 @@
 // it is block diagonal: the parity of (monomial, component) under the three
 // reflections splits the 24 modes into 8 classes of 3, and
 //     K_e = H^T G H,  G = H K_e H^T / 64,
-// with G made of eight 3x3 blocks (72 numbers, 57 of them non-zero: the
-// constant monomial is a rigid translation and drops out).  One element
-// application costs 21 mode sums, 57 FMAs and 21 products with E_e instead of
+// with G made of eight 3x3 blocks (72 numbers; the constant monomial is a
+// rigid translation and drops out).  The symmetry of the cube under axis
+// permutations leaves eight distinct values in those blocks (GSym in
+// internal.cuh), so with E_e folded into the eight, one element application
+// costs 21 mode sums, 8 coefficient products and 33 operations for G instead of
 // 576 FMAs, and every retained mode is a difference of nodal values, which keeps
 // FP32 rounding proportional to the variation of u rather than its magnitude.
 //
@@ -37,6 +39,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -88,10 +91,19 @@ __device__ __forceinline__ V3 vsub(const V3& a, const V3& b) {
 }
 __device__ __forceinline__ V3 vld(const float* p) { return {make_float2(p[0], p[1]), p[2]}; }
 __device__ __forceinline__ float comp(const V3& v, int c) { return c == 0 ? v.xy.x : (c == 1 ? v.xy.y : v.z); }
-__device__ __forceinline__ void set_comp(V3& v, int c, float x) {
-    if (c == 0) v.xy.x = x;
-    else if (c == 1) v.xy.y = x;
-    else v.z = x;
+
+// w[1..7] = E_e G v[1..7] for one element (GSym form of G, E_e in k).
+__device__ __forceinline__ void contract_v3(const GElem<float>& k, const V3 (&v)[8], V3 (&w)[8]) {
+    float u[8][3], o[8][3];
+#pragma unroll
+    for (int m = 1; m < 8; ++m) {
+        u[m][0] = v[m].xy.x;
+        u[m][1] = v[m].xy.y;
+        u[m][2] = v[m].z;
+    }
+    gsym_contract(k, u, o);
+#pragma unroll
+    for (int m = 1; m < 8; ++m) w[m] = V3{make_float2(o[m][0], o[m][1]), o[m][2]};
 }
 
 // Difference sums of four corner values (x fastest), formed from node
@@ -127,7 +139,7 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 constexpr int kRing = 4;
 
 template <int BX, int BY, int MODE, bool DOT>
-__global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zchunk) {
+__global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GSym G, int zchunk) {
     pdl_entry();
     constexpr int NT = BX * BY;
     constexpr int ROW = (BX + 1) * 3;           // floats per staged plane row
@@ -311,28 +323,10 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GHat G, int zch
                 v[q + 4] = vsub(out.Q[q], in.Q[q]);
             }
         }
-        // w = E G v, class by class (the constant monomial carries no energy)
+        // w = E G v (the constant monomial carries no energy)
         V3 w[8];
         w[0] = V3{make_float2(0.f, 0.f), 0.f};
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int mi = mono(s, i);
-                if (mi == 0) continue;
-                float acc = 0.f;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const int mj = mono(s, j);
-                    if (mj == 0) continue;
-                    acc = fmaf(G.g[s * 9 + i * 3 + j], comp(v[mj], j), acc);
-                }
-                set_comp(w[mi], i, acc);
-            }
-        }
-        const float2 E2 = make_float2(out.E, out.E);
-#pragma unroll
-        for (int m = 1; m < 8; ++m) w[m] = V3{__fmul2_rn(E2, w[m].xy), __fmul_rn(out.E, w[m].z)};
+        contract_v3(gsym_scale(G, out.E), v, w);
         // back to face quantities: top = w + w_z, bottom = w - w_z
         V3 Bf[4];
 #pragma unroll
@@ -826,7 +820,7 @@ constexpr unsigned kTmaSpin = 1u << 22;
 template <int BX, int BY, int MODE, bool DOT>
 __global__ void __launch_bounds__(BX * BY, 2)
 k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tme,
-           const __grid_constant__ CUtensorMap tmb, const __grid_constant__ CUtensorMap tmd, FineArgs a, GHat G,
+           const __grid_constant__ CUtensorMap tmb, const __grid_constant__ CUtensorMap tmd, FineArgs a, GSym G,
            int zchunk) {
     using T = TmaTile<BX, BY>;
     constexpr int NT = BX * BY;
@@ -924,7 +918,9 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
         for (int q = 0; q < 4; ++q) s0.T[q] = V3{make_float2(0.f, 0.f), 0.f};
         s0.E = 0.f;
     }
-    int mk0 = 7, mk1 = load_mask(k0);
+    // masks four planes ahead, one register per ring slot (the slot of step s
+    // holds plane s's mask), so a load's result is not touched before its use
+    int mq[4] = {7, load_mask(k0), load_mask(k0 + 1), load_mask(k0 + 2)};
     bool pending = false;
     V3 R1{make_float2(0.f, 0.f), 0.f}, un_pend{make_float2(0.f, 0.f), 0.f};
     float eR1 = 0.f;
@@ -984,9 +980,8 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
         if (tid == 0 && s + 3 <= k1) issue(s + 3);
         if (pending) finish(s - 1, Q);
         pending = false;
-        const int mcur = mk0;
-        mk0 = mk1;
-        mk1 = load_mask(s + 2);
+        const int mcur = mq[Q];
+        mq[Q] = load_mask(s + 4);
         {
             const float* pl = reinterpret_cast<const float*>(smem + Q * T::STAGE + T::XOFF) + rx;
             out.C[0] = vld(pl);
@@ -1009,25 +1004,7 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
         }
         V3 w[8];
         w[0] = V3{make_float2(0.f, 0.f), 0.f};
-#pragma unroll
-        for (int sg = 0; sg < 8; ++sg) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int mi = mono(sg, i);
-                if (mi == 0) continue;
-                float acc = 0.f;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const int mj = mono(sg, j);
-                    if (mj == 0) continue;
-                    acc = fmaf(G.g[sg * 9 + i * 3 + j], comp(v[mj], j), acc);
-                }
-                set_comp(w[mi], i, acc);
-            }
-        }
-        const float2 E2 = make_float2(out.E, out.E);
-#pragma unroll
-        for (int m = 1; m < 8; ++m) w[m] = V3{__fmul2_rn(E2, w[m].xy), __fmul_rn(out.E, w[m].z)};
+        contract_v3(gsym_scale(G, out.E), v, w);
         V3 Bf[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -1211,7 +1188,7 @@ FinePlan plan_fine(int nx, int ny, int nz) {
 }
 
 template <int MODE, bool DOT>
-void launch_shape(const FinePlan& pl, const FineArgs& a, const GHat& G, cudaStream_t s) {
+void launch_shape(const FinePlan& pl, const FineArgs& a, const GSym& G, cudaStream_t s) {
     if (pl.tile == 0) pdl_launch(k_fine<32, 8, MODE, DOT>, dim3(pl.grid), dim3(dim3(32, 8)), 0, s, a, G, pl.zc);
     else pdl_launch(k_fine<16, 16, MODE, DOT>, dim3(pl.grid), dim3(dim3(16, 16)), 0, s, a, G, pl.zc);
 }
@@ -1261,7 +1238,7 @@ void fine_set_plan(int nx, int ny, int nz, int tile, int zc) {
     else g_plans[key] = std::make_pair(tile, zc);
 }
 
-void launch_fine(int mode, int dot, int mask_in, const FineArgs& a_in, const GHat& G, cudaStream_t s) {
+void launch_fine(int mode, int dot, int mask_in, const FineArgs& a_in, const GSym& G, cudaStream_t s) {
     // the solver's own level-0 vectors (padded rows, padded moduli): TMA-fed kernel
     if (!mask_in && a_in.Ep && a_in.pitch % 4 == 0 && a_in.pitch > 0 &&
         launch_fine_tma(mode, dot, a_in, G, s) == GMG_OK)
@@ -1301,7 +1278,7 @@ void launch_fine(int mode, int dot, int mask_in, const FineArgs& a_in, const GHa
 
 namespace {
 template <int BX, int BY, int MODE, bool DOT>
-int launch_tma_tile(const FinePlan& pl, const FineArgs& a, const GHat& G, cudaStream_t s) {
+int launch_tma_tile(const FinePlan& pl, const FineArgs& a, const GSym& G, cudaStream_t s) {
     using T = TmaTile<BX, BY>;
     static bool attr = false;
     if (!attr) {
@@ -1331,12 +1308,12 @@ int launch_tma_tile(const FinePlan& pl, const FineArgs& a, const GHat& G, cudaSt
     return GMG_OK;
 }
 template <int MODE, bool DOT>
-int launch_tma_shape(const FinePlan& pl, const FineArgs& a, const GHat& G, cudaStream_t s) {
+int launch_tma_shape(const FinePlan& pl, const FineArgs& a, const GSym& G, cudaStream_t s) {
     return pl.tile == 0 ? launch_tma_tile<32, 8, MODE, DOT>(pl, a, G, s) : launch_tma_tile<16, 16, MODE, DOT>(pl, a, G, s);
 }
 }  // namespace
 
-int launch_fine_tma(int mode, int dot, const FineArgs& a, const GHat& G, cudaStream_t s) {
+int launch_fine_tma(int mode, int dot, const FineArgs& a, const GSym& G, cudaStream_t s) {
     if (a.pitch % 4 != 0 || a.epitch % 4 != 0 || !a.Ep) return GMG_ERR_ARG;
     const FinePlan pl = plan_fine(a.nx, a.ny, a.nz);
     if (pair_tile(pl.tile)) return launch_fine_pair(pl.tile, mode, dot, pl.grid, pl.zc, a, G, s);
@@ -1344,6 +1321,49 @@ int launch_fine_tma(int mode, int dot, const FineArgs& a, const GHat& G, cudaStr
     if (mode == FM_SMOOTH)
         return dot ? launch_tma_shape<FM_SMOOTH, true>(pl, a, G, s) : launch_tma_shape<FM_SMOOTH, false>(pl, a, G, s);
     return launch_tma_shape<FM_RESID, false>(pl, a, G, s);
+}
+
+bool gsym_from_blocks(const double g[72], GSym* out) {
+    // value index per entry (class s, row i, column j): 0 a, 1 b (class 0),
+    // 2 a', 3 b' (class 7), 4 p, 5 q, 6 c, 7 d, -1 zero
+    int which[72];
+    for (int t = 0; t < 72; ++t) which[t] = -1;
+    auto at = [](int s, int i, int j) { return s * 9 + i * 3 + j; };
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            which[at(0, i, j)] = i == j ? 0 : 1;
+            which[at(7, i, j)] = i == j ? 2 : 3;
+        }
+    const int pair_cls[3] = {1, 2, 4}, pair_rc[3][2] = {{1, 2}, {0, 2}, {0, 1}};
+    for (int k = 0; k < 3; ++k) {
+        const int s = pair_cls[k], r0 = pair_rc[k][0], r1 = pair_rc[k][1];
+        which[at(s, r0, r0)] = which[at(s, r1, r1)] = 4;
+        which[at(s, r0, r1)] = which[at(s, r1, r0)] = 5;
+    }
+    const int c_cls[3] = {3, 5, 6}, c_rc[3][2] = {{0, 1}, {0, 2}, {1, 2}}, d_r[3] = {2, 1, 0};
+    for (int k = 0; k < 3; ++k) {
+        const int s = c_cls[k], r0 = c_rc[k][0], r1 = c_rc[k][1];
+        which[at(s, r0, r0)] = which[at(s, r0, r1)] = which[at(s, r1, r0)] = which[at(s, r1, r1)] = 6;
+        which[at(s, d_r[k], d_r[k])] = 7;
+    }
+    double sum[8] = {}, big = 0.0;
+    int cnt[8] = {};
+    for (int t = 0; t < 72; ++t) {
+        big = std::max(big, std::fabs(g[t]));
+        if (which[t] >= 0) {
+            sum[which[t]] += g[t];
+            ++cnt[which[t]];
+        }
+    }
+    double v[8];
+    for (int k = 0; k < 8; ++k) v[k] = sum[k] / cnt[k];
+    for (int t = 0; t < 72; ++t)
+        if (std::fabs(g[t] - (which[t] >= 0 ? v[which[t]] : 0.0)) > 1e-12 * big) return false;
+    out->ab0 = make_float2((float)(v[0] - v[1]), (float)v[1]);
+    out->ab7 = make_float2((float)(v[2] - v[3]), (float)v[3]);
+    out->pq = make_float2((float)v[4], (float)v[5]);
+    out->cd = make_float2((float)v[6], (float)v[7]);
+    return true;
 }
 
 // Operand B of the tensor-core smoother: row o = the 24 corner forces of an

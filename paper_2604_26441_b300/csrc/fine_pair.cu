@@ -2,8 +2,8 @@
 // thread, for sm_103a.
 //
 // The arithmetic is the Walsh-Hadamard form of the single-column operator in
-// fine.cu (K_e = H^T G H with eight 3x3 parity blocks, 57 non-zero
-// coefficients; per element 21 mode sums, 57 FMAs and 21 products with E_e),
+// fine.cu (K_e = H^T G H with eight 3x3 parity blocks taking eight distinct
+// values; per element 21 mode sums and the symmetric contraction of G),
 // the same operations in the same order, so that every output is bitwise equal
 // to that kernel's.  What changes is the unit of work of a thread:
 //   - thread (tx, ty) holds the two x-adjacent element columns whose low corners
@@ -13,8 +13,8 @@
 //   - every value is carried as f32x2 pairs whose two lanes are the two columns
 //     (x, y and z components each a pair), so each add, subtract, FMA and
 //     product of the element arithmetic is one packed instruction (FADD2,
-//     FFMA2, FMUL2) for two elements, and the 57 coefficients enter as
-//     broadcast pairs;
+//     FFMA2, FMUL2) for two elements, and the eight coefficients, scaled by
+//     each column's modulus, form one pair per coefficient;
 //   - the wait, barrier, mask, index and shuffle work of a layer is paid once
 //     per two elements, and the sum across the shared node of the two columns
 //     stays in registers (one shuffle per component reaches the next thread).
@@ -33,19 +33,9 @@ namespace gmg {
 
 namespace {
 
-// Monomial (bit 0 = X, 1 = Y, 2 = Z) of component c in parity class sigma.
-__host__ __device__ constexpr int pmono(int sigma, int c) {
-    return ((sigma & 1) ^ (c == 0 ? 1 : 0)) | ((((sigma >> 1) & 1) ^ (c == 1 ? 1 : 0)) << 1) |
-           ((((sigma >> 2) & 1) ^ (c == 2 ? 1 : 0)) << 2);
-}
 __host__ __device__ constexpr int pround4(int v) { return (v + 3) / 4 * 4; }
 __host__ __device__ constexpr int pround128(int v) { return (v + 127) / 128 * 128; }
 __device__ __forceinline__ int pfloor4(int v) { return v & ~3; }
-
-// The 72 entries of G, each as a pair (g, g) for the packed FMAs.
-struct GPair {
-    float2 g[72];
-};
 
 // A node or element quantity of the two columns: lane .x is the first column,
 // lane .y the second.  a - b is formed as fma(b, -1, a), which rounds exactly
@@ -61,11 +51,6 @@ __device__ __forceinline__ P3 psub(const P3& a, const P3& b) {
     return {__ffma2_rn(b.x, m, a.x), __ffma2_rn(b.y, m, a.y), __ffma2_rn(b.z, m, a.z)};
 }
 __device__ __forceinline__ float2 pcomp(const P3& v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : v.z); }
-__device__ __forceinline__ void pset(P3& v, int c, float2 x) {
-    if (c == 0) v.x = x;
-    else if (c == 1) v.y = x;
-    else v.z = x;
-}
 __device__ __forceinline__ P3 pzero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
 
 // Difference sums of the four corners of a face (x fastest): q[1] = x-difference,
@@ -137,7 +122,7 @@ template <int BX, int BY, int MODE, bool DOT>
 __global__ void __launch_bounds__(BX * BY, BX * BY >= 256 ? 1 : 2)
 k_fine_pair(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tme,
             const __grid_constant__ CUtensorMap tmb, const __grid_constant__ CUtensorMap tmd, FineArgs a,
-            const __grid_constant__ GPair G, int zchunk) {
+            const __grid_constant__ GSym G, int zchunk) {
     using T = PairTile<BX, BY>;
     constexpr int NT = BX * BY;
     constexpr bool EPI_B = MODE != FM_APPLY;
@@ -150,7 +135,7 @@ k_fine_pair(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUt
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
     const int NX = a.nx + 1, NY = a.ny + 1, NZ = a.nz + 1;
     const int px = a.pitch, NXYp = px * NY;
-    const long long nvec = (long long)NXYp * NZ;
+    [[maybe_unused]] const long long nvec = (long long)NXYp * NZ;  // bounds of the checked build
     const int x0 = blockIdx.x * (2 * BX - 1), y0 = blockIdx.y * (BY - 1);
     const int k0 = blockIdx.z * zchunk, k1 = min(k0 + zchunk, NZ);
     const int kb = k0 - 1;
@@ -242,7 +227,9 @@ k_fine_pair(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUt
 #pragma unroll
     for (int q = 0; q < 4; ++q) s0.T[q] = pzero();
     s0.E = make_float2(0.f, 0.f);
-    int mk0 = 7 | (7 << 3), mk1 = load_mask(k0);
+    // masks four planes ahead, one register per ring slot (the slot of step s
+    // holds plane s's masks), so a load's result is not touched before its use
+    int mq[4] = {7 | (7 << 3), load_mask(k0), load_mask(k0 + 1), load_mask(k0 + 2)};
     bool pending = false;
     P3 R1 = pzero(), un_pend = pzero();
     float2 eR1 = make_float2(0.f, 0.f);
@@ -321,9 +308,8 @@ k_fine_pair(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUt
         if (tid == 0 && s + 3 <= k1) issue(s + 3);
         if (pending) finish(s - 1, Q);
         pending = false;
-        const int mcur = mk0;
-        mk0 = mk1;
-        mk1 = load_mask(s + 2);
+        const int mcur = mq[Q];
+        mq[Q] = load_mask(s + 4);
         load_plane(reinterpret_cast<const float*>(smem + Q * T::STAGE + T::XOFF) + rx, out);
         {
             const float* pe = reinterpret_cast<const float*>(smem + Q * T::STAGE + T::EOFF) + re;
@@ -342,25 +328,18 @@ k_fine_pair(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUt
         }
         P3 w[8];
         w[0] = pzero();
+        {
+            float2 u[8][3], o[8][3];
 #pragma unroll
-        for (int sg = 0; sg < 8; ++sg) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int mi = pmono(sg, i);
-                if (mi == 0) continue;
-                float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const int mj = pmono(sg, j);
-                    if (mj == 0) continue;
-                    acc = __ffma2_rn(G.g[sg * 9 + i * 3 + j], pcomp(v[mj], j), acc);
-                }
-                pset(w[mi], i, acc);
+            for (int m = 1; m < 8; ++m) {
+                u[m][0] = v[m].x;
+                u[m][1] = v[m].y;
+                u[m][2] = v[m].z;
             }
-        }
+            gsym_contract(gsym_scale2(G, out.E), u, o);
 #pragma unroll
-        for (int m = 1; m < 8; ++m)
-            w[m] = P3{__fmul2_rn(out.E, w[m].x), __fmul2_rn(out.E, w[m].y), __fmul2_rn(out.E, w[m].z)};
+            for (int m = 1; m < 8; ++m) w[m] = P3{o[m][0], o[m][1], o[m][2]};
+        }
         P3 Bf[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -433,7 +412,7 @@ k_fine_pair(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUt
 namespace {
 
 template <int BX, int BY, int MODE, bool DOT>
-int launch_pair_tile(dim3 grid, int zc, const FineArgs& a, const GPair& G, cudaStream_t s) {
+int launch_pair_tile(dim3 grid, int zc, const FineArgs& a, const GSym& G, cudaStream_t s) {
     using T = PairTile<BX, BY>;
     static bool attr = false;
     if (!attr) {
@@ -463,7 +442,7 @@ int launch_pair_tile(dim3 grid, int zc, const FineArgs& a, const GPair& G, cudaS
 }
 
 template <int MODE, bool DOT>
-int launch_pair_shape(int tile, dim3 grid, int zc, const FineArgs& a, const GPair& G, cudaStream_t s) {
+int launch_pair_shape(int tile, dim3 grid, int zc, const FineArgs& a, const GSym& G, cudaStream_t s) {
     switch (tile) {
         case kFinePair8x16: return launch_pair_tile<8, 16, MODE, DOT>(grid, zc, a, G, s);
         case kFinePair16x8: return launch_pair_tile<16, 8, MODE, DOT>(grid, zc, a, G, s);
@@ -474,18 +453,16 @@ int launch_pair_shape(int tile, dim3 grid, int zc, const FineArgs& a, const GPai
 
 }  // namespace
 
-int launch_fine_pair(int tile, int mode, int dot, dim3 grid, int zc, const FineArgs& a, const GHat& G,
+int launch_fine_pair(int tile, int mode, int dot, dim3 grid, int zc, const FineArgs& a, const GSym& G,
                      cudaStream_t s) {
     if (a.pitch % 4 != 0 || a.epitch % 4 != 0 || !a.Ep) return GMG_ERR_ARG;
-    GPair gp;
-    for (int i = 0; i < 72; ++i) gp.g[i] = make_float2(G.g[i], G.g[i]);
     if (mode == FM_APPLY)
-        return dot ? launch_pair_shape<FM_APPLY, true>(tile, grid, zc, a, gp, s)
-                   : launch_pair_shape<FM_APPLY, false>(tile, grid, zc, a, gp, s);
+        return dot ? launch_pair_shape<FM_APPLY, true>(tile, grid, zc, a, G, s)
+                   : launch_pair_shape<FM_APPLY, false>(tile, grid, zc, a, G, s);
     if (mode == FM_SMOOTH)
-        return dot ? launch_pair_shape<FM_SMOOTH, true>(tile, grid, zc, a, gp, s)
-                   : launch_pair_shape<FM_SMOOTH, false>(tile, grid, zc, a, gp, s);
-    return launch_pair_shape<FM_RESID, false>(tile, grid, zc, a, gp, s);
+        return dot ? launch_pair_shape<FM_SMOOTH, true>(tile, grid, zc, a, G, s)
+                   : launch_pair_shape<FM_SMOOTH, false>(tile, grid, zc, a, G, s);
+    return launch_pair_shape<FM_RESID, false>(tile, grid, zc, a, G, s);
 }
 
 }  // namespace gmg

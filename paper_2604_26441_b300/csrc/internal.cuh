@@ -81,8 +81,93 @@ __host__ __device__ constexpr int slot_of(int dx, int dy, int dz) { return (dx +
 struct KeF { float v[576]; };
 struct KeD { double v[576]; };
 // K_e in the Walsh-Hadamard mode basis: eight 3x3 parity-class blocks (fine.cu).
-struct GHat { float g[72]; };
 struct GHat64 { double g[72]; };
+
+// The same blocks reduced by the symmetry of the cube (any Poisson ratio): with
+// the classes numbered as in fine.cu, the 72 entries take eight distinct values
+// and 27 of them vanish --
+//   class 0 (modes X, Y, Z of components x, y, z) and class 7 (YZ, XZ, XY of x,
+//     y, z): a on the diagonal and b off it, so w_i = (a - b) u_i + b (u_x + u_y + u_z);
+//   classes 1, 2 and 4 (two modes each): the block [[p, q], [q, p]];
+//   classes 3, 5 and 6: a 2x2 block of equal entries c (both outputs are
+//     c (u_i + u_j)) and one entry d for the XYZ mode.
+// GSym holds (a - b, b) of class 0, the same of class 7, (p, q) and (c, d).
+struct GSym { float2 ab0, ab7, pq, cd; };
+// Host: GSym from the 72 FP64 block entries (each value the mean of its equal
+// entries); false when an entry departs from the pattern by more than 1e-12 of
+// the largest one.
+bool gsym_from_blocks(const double g[72], GSym* out);
+
+// Rounded lane arithmetic for one element (float) or two (float2).
+__device__ __forceinline__ float g_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float2 g_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float g_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float2 g_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float g_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 g_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// One element's coefficients: E_e times the eight values of GSym.
+template <class L>
+struct GElem {
+    L a0, b0, a7, b7, p, q, c, d;
+};
+__device__ __forceinline__ GElem<float> gsym_scale(const GSym& G, float E) {
+    const float2 e2 = make_float2(E, E);
+    const float2 ab0 = __fmul2_rn(G.ab0, e2), ab7 = __fmul2_rn(G.ab7, e2);
+    const float2 pq = __fmul2_rn(G.pq, e2), cd = __fmul2_rn(G.cd, e2);
+    return {ab0.x, ab0.y, ab7.x, ab7.y, pq.x, pq.y, cd.x, cd.y};
+}
+// two elements with moduli E.x and E.y
+__device__ __forceinline__ GElem<float2> gsym_scale2(const GSym& G, float2 E) {
+    auto b = [](float v) { return make_float2(v, v); };
+    return {__fmul2_rn(b(G.ab0.x), E), __fmul2_rn(b(G.ab0.y), E), __fmul2_rn(b(G.ab7.x), E),
+            __fmul2_rn(b(G.ab7.y), E), __fmul2_rn(b(G.pq.x), E),  __fmul2_rn(b(G.pq.y), E),
+            __fmul2_rn(b(G.cd.x), E),  __fmul2_rn(b(G.cd.y), E)};
+}
+
+// w[m][c] = (E_e G u)[m][c] for the 21 non-constant modes (m = 1..7; monomial
+// bits X = 1, Y = 2, Z = 4; c the displacement component), every operation
+// rounded on its own and in this order in every kernel.
+template <class L>
+__device__ __forceinline__ void gsym_contract(const GElem<L>& k, const L (&u)[8][3], L (&w)[8][3]) {
+    {  // class 0: (X, x), (Y, y), (Z, z)
+        const L t = g_mul(k.b0, g_add(g_add(u[1][0], u[2][1]), u[4][2]));
+        w[1][0] = g_fma(k.a0, u[1][0], t);
+        w[2][1] = g_fma(k.a0, u[2][1], t);
+        w[4][2] = g_fma(k.a0, u[4][2], t);
+    }
+    {  // class 7: (YZ, x), (XZ, y), (XY, z)
+        const L t = g_mul(k.b7, g_add(g_add(u[6][0], u[5][1]), u[3][2]));
+        w[6][0] = g_fma(k.a7, u[6][0], t);
+        w[5][1] = g_fma(k.a7, u[5][1], t);
+        w[3][2] = g_fma(k.a7, u[3][2], t);
+    }
+    // class 1: (XY, y), (XZ, z); class 2: (XY, x), (YZ, z); class 4: (XZ, x), (YZ, y)
+    w[3][1] = g_fma(k.p, u[3][1], g_mul(k.q, u[5][2]));
+    w[5][2] = g_fma(k.q, u[3][1], g_mul(k.p, u[5][2]));
+    w[3][0] = g_fma(k.p, u[3][0], g_mul(k.q, u[6][2]));
+    w[6][2] = g_fma(k.q, u[3][0], g_mul(k.p, u[6][2]));
+    w[5][0] = g_fma(k.p, u[5][0], g_mul(k.q, u[6][1]));
+    w[6][1] = g_fma(k.q, u[5][0], g_mul(k.p, u[6][1]));
+    {  // class 3: (Y, x), (X, y) and (XYZ, z)
+        const L h = g_mul(k.c, g_add(u[2][0], u[1][1]));
+        w[2][0] = h;
+        w[1][1] = h;
+        w[7][2] = g_mul(k.d, u[7][2]);
+    }
+    {  // class 5: (Z, x), (X, z) and (XYZ, y)
+        const L h = g_mul(k.c, g_add(u[4][0], u[1][2]));
+        w[4][0] = h;
+        w[1][2] = h;
+        w[7][1] = g_mul(k.d, u[7][1]);
+    }
+    {  // class 6: (Z, y), (Y, z) and (XYZ, x)
+        const L h = g_mul(k.c, g_add(u[4][1], u[2][2]));
+        w[4][1] = h;
+        w[2][2] = h;
+        w[7][0] = g_mul(k.d, u[7][0]);
+    }
+}
 
 // Scalar slots of the per-handle FP64 scalar array.
 enum Scalar {
@@ -330,7 +415,7 @@ struct gmg_handle {
     double* E64 = nullptr;                      // fine moduli, FP64
     gmg::KeF keF{};
     gmg::KeD keD{};
-    gmg::GHat gh{};
+    gmg::GSym gs{};                             // fine operator coefficients (symmetric form of G)
     gmg::GHat64 gh64{};
     float kd = 0.f;                             // diagonal entry of K_e (all equal)
     double setup_ms = 0.0;                      // host wall time of gmg_setup (clones: the source's)
@@ -437,14 +522,14 @@ int fine_plan_blocks(int nx, int ny, int nz, int tile, int zc);
 void fine_set_plan(int nx, int ny, int nz, int tile, int zc);
 // mask_in: treat fixed DOFs of the operand as 0 (for operands that may hold
 // values there, e.g. user input); internal vectors are already 0 on them.
-void launch_fine(int mode, int dot, int mask_in, const FineArgs& a, const GHat& G, cudaStream_t s);
+void launch_fine(int mode, int dot, int mask_in, const FineArgs& a, const GSym& G, cudaStream_t s);
 // The TMA-fed fine operator on padded level-0 vectors (a.pitch and a.epitch
 // multiples of 4, a.Ep the padded moduli); GMG_OK, or an error when a tensor map
 // cannot be encoded (nothing is launched then).
-int launch_fine_tma(int mode, int dot, const FineArgs& a, const GHat& G, cudaStream_t s);
+int launch_fine_tma(int mode, int dot, const FineArgs& a, const GSym& G, cudaStream_t s);
 // The two-column operator (tiles 2..4) on a grid of `grid` blocks, zc node
 // planes per block; GMG_ERR_ARG for another tile or unpadded vectors.
-int launch_fine_pair(int tile, int mode, int dot, dim3 grid, int zc, const FineArgs& a, const GHat& G,
+int launch_fine_pair(int tile, int mode, int dot, dim3 grid, int zc, const FineArgs& a, const GSym& G,
                      cudaStream_t s);
 void launch_hadamard_blocks(const double* Ke, double* g72, cudaStream_t s);
 // Tensor-core fine smoother step (SMOOTH mode): passes = 1 (BF16) or 3 (split BF16).
@@ -622,7 +707,7 @@ struct MFineArgs {
     int* err;
 };
 // CUDA-core operator: one block per (tile, load); GMG_OK or an error (tensor maps).
-int launch_mfine(int mode, int dot, const MFineArgs& a, const GHat& G, cudaStream_t s);
+int launch_mfine(int mode, int dot, const MFineArgs& a, const GSym& G, cudaStream_t s);
 int mfine_blocks(int nx, int ny, int nz, int nl);
 // Tensor-core operator (multi_tc.cu): blocks per load group, and the launch.
 int mfine_tc_blocks(int nx, int ny, int nz);

