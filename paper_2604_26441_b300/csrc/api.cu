@@ -445,8 +445,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         launch_hadamard_blocks(Ke, g72, s);
         CU(cudaMemcpyAsync(gh, g72, sizeof gh, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
-        for (int i = 0; i < 72; ++i) h->gh64.g[i] = gh[i];
-        if (!gsym_from_blocks(gh, &h->gs))
+        if (!gsym_from_blocks(gh, &h->gs, h->gs64))
             return fail(GMG_ERR_CUDA, "element stiffness lacks the cube-symmetric block structure");
         if (o.fine_smoother != GMG_FINE_FP32) {
             uint16_t op[2048];
@@ -834,7 +833,7 @@ int fgmres_solve(gmg_handle* h, const double* f, double* u, double tol, int maxi
     while (true) {
         double rel = 0.0;
         launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, l0.px, h->sc, h->partials,
-                            h->gh64, s);
+                            h->gs64, s);
         launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
         TRY(sync_scalars(h));
         const double beta = std::sqrt(sch[SC_TRR]);
@@ -1090,7 +1089,7 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     };
     auto true_residual = [&](double& rel) -> int {
         launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, l0.px, h->sc, h->partials,
-                            h->gh64, s);
+                            h->gs64, s);
         launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
         TRY(sync_scalars(h));
         rel = std::sqrt(sch[SC_TRR]) / std::sqrt(sch[SC_FF]);
@@ -1655,7 +1654,7 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
             launch_cast_masked(f[i], l0, h->r, s);
         } else {
             launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, l0.px, h->sc,
-                                h->partials, h->gh64, s);
+                                h->partials, h->gs64, s);
             launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
         }
     }
@@ -1794,7 +1793,7 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
                 gmg_handle* h = hs[i];
                 const Level& l0 = h->lev[0];
                 launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, l0.px, h->sc,
-                                    h->partials, h->gh64, s);
+                                    h->partials, h->gs64, s);
                 launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
             }
         }
@@ -2029,7 +2028,7 @@ int gmg_residual64(gmg_handle* h, const double* f, const double* u, double* r, d
     cudaStream_t s = h->stream;
     h->sc_host[SC_UNZ] = 1.0;
     launch_set_scalars(h->sc + SC_UNZ, 1, 1.0, 0.0, 0.0, 0.0, s);
-    launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, r, nullptr, l0.px, h->sc, h->partials, h->gh64,
+    launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, r, nullptr, l0.px, h->sc, h->partials, h->gs64,
                         s);
     launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
     launch_dot_f64_masked(f, f, l0.mask, l0.nn, h->partials, s);

@@ -1323,7 +1323,7 @@ int launch_fine_tma(int mode, int dot, const FineArgs& a, const GSym& G, cudaStr
     return launch_tma_shape<FM_RESID, false>(pl, a, G, s);
 }
 
-bool gsym_from_blocks(const double g[72], GSym* out) {
+bool gsym_from_blocks(const double g[72], GSym* out, double* v64) {
     // value index per entry (class s, row i, column j): 0 a, 1 b (class 0),
     // 2 a', 3 b' (class 7), 4 p, 5 q, 6 c, 7 d, -1 zero
     int which[72];
@@ -1363,6 +1363,10 @@ bool gsym_from_blocks(const double g[72], GSym* out) {
     out->ab7 = make_float2((float)(v[2] - v[3]), (float)v[3]);
     out->pq = make_float2((float)v[4], (float)v[5]);
     out->cd = make_float2((float)v[6], (float)v[7]);
+    if (v64) {
+        const double w[8] = {v[0] - v[1], v[1], v[2] - v[3], v[3], v[4], v[5], v[6], v[7]};
+        for (int k = 0; k < 8; ++k) v64[k] = w[k];
+    }
     return true;
 }
 

@@ -80,8 +80,6 @@ __host__ __device__ constexpr int slot_of(int dx, int dy, int dz) { return (dx +
 // private to each launch, so handles with different nu never collide).
 struct KeF { float v[576]; };
 struct KeD { double v[576]; };
-// K_e in the Walsh-Hadamard mode basis: eight 3x3 parity-class blocks (fine.cu).
-struct GHat64 { double g[72]; };
 
 // The same blocks reduced by the symmetry of the cube (any Poisson ratio): with
 // the classes numbered as in fine.cu, the 72 entries take eight distinct values
@@ -95,8 +93,9 @@ struct GHat64 { double g[72]; };
 struct GSym { float2 ab0, ab7, pq, cd; };
 // Host: GSym from the 72 FP64 block entries (each value the mean of its equal
 // entries); false when an entry departs from the pattern by more than 1e-12 of
-// the largest one.
-bool gsym_from_blocks(const double g[72], GSym* out);
+// the largest one.  v64, when given, receives the eight values in FP64 in the
+// order of GSym (a - b, b, a' - b', b', p, q, c, d).
+bool gsym_from_blocks(const double g[72], GSym* out, double* v64 = nullptr);
 
 // Rounded lane arithmetic for one element (float) or two (float2).
 __device__ __forceinline__ float g_add(float a, float b) { return __fadd_rn(a, b); }
@@ -416,7 +415,7 @@ struct gmg_handle {
     gmg::KeF keF{};
     gmg::KeD keD{};
     gmg::GSym gs{};                             // fine operator coefficients (symmetric form of G)
-    gmg::GHat64 gh64{};
+    double gs64[8] = {};                        // the same eight values in FP64 (FP64 true residual)
     float kd = 0.f;                             // diagonal entry of K_e (all equal)
     double setup_ms = 0.0;                      // host wall time of gmg_setup (clones: the source's)
     float* inv0 = nullptr;                      // [n_nodes] fine Jacobi scale 1 / (kd * sum of adjacent E_e)
@@ -544,7 +543,7 @@ int resid64_grid_blocks(int nx, int ny, int nz);
 int resid64_grid_blocks_multi(int nx, int ny, int nz, int nl);
 void launch_fine_resid64_multi(int nx, int ny, int nz, const double* E, const uint8_t* mask, int nl,
                                const double* const* f, const double* const* u, const double* sc, double* partial,
-                               int pstride, const GHat64& G, cudaStream_t s);
+                               int pstride, const double* g8, cudaStream_t s);
 void launch_fine_smooth0(const FineArgs& a, cudaStream_t s);
 // inv0[n] = 1 / (kd * sum of the moduli of the elements around node n), once at set-up.
 void launch_fine_inv0(int nx, int ny, int nz, int px, const float* E, float kd, float* inv0, cudaStream_t s);
@@ -552,7 +551,7 @@ void launch_fine_inv0(int nx, int ny, int nz, int px, const float* E, float kd, 
 // numbering of pitch px.
 void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,
                          const double* f, const double* u, double* r64, float* r32, int px,
-                         const double* sc, double* partial, const GHat64& G, cudaStream_t s);
+                         const double* sc, double* partial, const double* g8, cudaStream_t s);
 
 struct BsrArgs {
     int nx, ny, nz;

@@ -1486,7 +1486,7 @@ void multi_norms(gmg_handle* h, int nl, const double* const* f, double* const* u
 void multi_true_residuals(gmg_handle* h, int nl, const double* const* f, const double* const* u) {
     MultiWork& w = *h->mw;
     const Level& l0 = h->lev[0];
-    launch_fine_resid64_multi(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, nl, f, u, w.sc, w.partials, w.pstride, h->gh64,
+    launch_fine_resid64_multi(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, nl, f, u, w.sc, w.partials, w.pstride, h->gs64,
                               h->stream);
     note_launch();
     pdl_launch(k_mfinalize, dim3(kLoads), dim3(kMT), 0, h->stream, (const double*)w.partials,
@@ -1508,7 +1508,7 @@ void multi_cast(gmg_handle* h, int nl, const double* const* f, const bool* cold)
 void multi_true_residual(gmg_handle* h, int l, const double* f, const double* u, bool into_r) {
     const Level& l0 = h->lev[0];
     double* sc = h->mw->sc + l * SC_COUNT;
-    launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, l0.px, sc, h->partials, h->gh64,
+    launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, l0.px, sc, h->partials, h->gs64,
                         h->stream);
     launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), sc, SC_TRR, FIN_NONE, h->stream);
     if (into_r) {

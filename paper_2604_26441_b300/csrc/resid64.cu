@@ -30,11 +30,6 @@ namespace {
 
 constexpr int BX = 16, BY = 16, NT = BX * BY;
 
-__host__ __device__ constexpr int mono(int sigma, int c) {
-    return ((sigma & 1) ^ (c == 0 ? 1 : 0)) | ((((sigma >> 1) & 1) ^ (c == 1 ? 1 : 0)) << 1) |
-           ((((sigma >> 2) & 1) ^ (c == 2 ? 1 : 0)) << 2);
-}
-
 __device__ __forceinline__ bool fixed_bit(uint8_t m, int c) { return (m >> c) & 1; }
 
 // ---- double-float numbers: value = hi + lo, |lo| <= ulp(hi) / 2 ----------------
@@ -66,14 +61,27 @@ __device__ __forceinline__ df operator*(df a, df b) {
     const float h = __fadd_rn(p, e);
     return {h, __fsub_rn(e, __fsub_rn(h, p))};
 }
+// lane arithmetic of the symmetric contraction (gsym_contract) in double-float
+__device__ __forceinline__ df g_add(df a, df b) { return a + b; }
+__device__ __forceinline__ df g_mul(df a, df b) { return a * b; }
+__device__ __forceinline__ df g_fma(df a, df b, df c) { return a * b + c; }
 __device__ __forceinline__ df shfl_down(df a, int d, int w) {
     return {__shfl_down_sync(0xffffffffu, a.hi, d, w), __shfl_down_sync(0xffffffffu, a.lo, d, w)};
 }
 
-// G of the element operator as double-float pairs (split on the host).
-struct GHatDF {
-    float hi[72], lo[72];
+// The eight values of G's symmetric form (GSym order) as double-float pairs
+// (split on the host from FP64).
+struct GSymDF {
+    float hi[8], lo[8];
 };
+GSymDF gsym_df(const double* g8) {
+    GSymDF d;
+    for (int k = 0; k < 8; ++k) {
+        d.hi[k] = (float)g8[k];
+        d.lo[k] = (float)(g8[k] - (double)d.hi[k]);
+    }
+    return d;
+}
 
 __device__ __forceinline__ void face_diffs(df u00, df u10, df u01, df u11, df q[4]) {
     const df dx0 = u10 - u00, dx1 = u11 - u01;
@@ -93,7 +101,7 @@ struct ResidLoads {
 
 __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask,
                                                    const __grid_constant__ ResidLoads L, double* r64, float* r32,
-                                                   int px, const double* sc, double* partial, GHatDF G, int zchunk) {
+                                                   int px, const double* sc, double* partial, GSymDF G, int zchunk) {
     pdl_entry();
     // load l of a multi-load launch: grid.z = L.gz chunks x loads, its own
     // f, u, scalar block and partial range
@@ -223,22 +231,12 @@ __global__ void __launch_bounds__(NT, 1) k_resid64(int nx, int ny, int nz, const
         }
         df w[8][3];
         for (int c = 0; c < 3; ++c) w[0][c] = zero;
+        {
+            df g[8];
 #pragma unroll
-        for (int s = 0; s < 8; ++s)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int mi = mono(s, i);
-                if (mi == 0) continue;
-                df acc = zero;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const int mj = mono(s, j);
-                    if (mj == 0) continue;
-                    const int gi = s * 9 + i * 3 + j;
-                    acc = acc + df{G.hi[gi], G.lo[gi]} * v[mj][j];
-                }
-                w[mi][i] = Ee * acc;
-            }
+            for (int k = 0; k < 8; ++k) g[k] = Ee * df{G.hi[k], G.lo[k]};
+            gsym_contract(GElem<df>{g[0], g[1], g[2], g[3], g[4], g[5], g[6], g[7]}, v, w);
+        }
         df T[4][3], B[4][3];
         for (int q = 0; q < 4; ++q)
             for (int c = 0; c < 3; ++c) {
@@ -323,15 +321,11 @@ int resid64_grid_blocks(int nx, int ny, int nz) {
 }
 
 void launch_fine_resid64(int nx, int ny, int nz, const double* E, const uint8_t* mask, const double* f, const double* u,
-                         double* r64, float* r32, int px, const double* sc, double* partial, const GHat64& G,
+                         double* r64, float* r32, int px, const double* sc, double* partial, const double* g8,
                          cudaStream_t s) {
     int zc = 0;
     const dim3 g = resid_grid(nx, ny, nz, &zc);
-    GHatDF gd;
-    for (int i = 0; i < 72; ++i) {
-        gd.hi[i] = (float)G.g[i];
-        gd.lo[i] = (float)(G.g[i] - (double)gd.hi[i]);
-    }
+    const GSymDF gd = gsym_df(g8);
     ResidLoads L{};
     L.f[0] = f;
     L.u[0] = u;
@@ -349,14 +343,10 @@ int resid64_grid_blocks_multi(int nx, int ny, int nz, int nl) {
 
 void launch_fine_resid64_multi(int nx, int ny, int nz, const double* E, const uint8_t* mask, int nl,
                                const double* const* f, const double* const* u, const double* sc, double* partial,
-                               int pstride, const GHat64& G, cudaStream_t s) {
+                               int pstride, const double* g8, cudaStream_t s) {
     int zc = 0;
     const dim3 g = resid_grid(nx, ny, nz, &zc, nl);
-    GHatDF gd;
-    for (int i = 0; i < 72; ++i) {
-        gd.hi[i] = (float)G.g[i];
-        gd.lo[i] = (float)(G.g[i] - (double)gd.hi[i]);
-    }
+    const GSymDF gd = gsym_df(g8);
     ResidLoads L{};
     for (int l = 0; l < nl; ++l) {
         L.f[l] = f[l];
