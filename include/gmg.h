@@ -138,11 +138,16 @@ typedef struct {
     int bsr_kernel;              /* kernel of the assembled levels outside the TMA-staged and fused
                                     paths: -1 (default) = by size (streaming from 65,536 nodes;
                                     below, K-split with the most of 32 / 16 / 8 slices that
-                                    keeps the grid within ~4 blocks per SM); 0 = streaming, one thread per
+                                    keeps the grid within ~4 blocks per SM), and level 1 applied
+                                    matrix-free from the fine moduli where that equals the
+                                    assembled operator (even fine sizes, every fixed fine DOF with
+                                    fixed prolongation parents; Eq. galerkin_level1 summed per
+                                    coarse element); 0 = streaming, one thread per
                                     node; 1 / 2 / 3 / 4 / 5 = K-split with 8 / 2 / 4 / 16 / 32
-                                    slices per node.
-                                    Results do not depend on the choice (each node's arithmetic is
-                                    the same); gmg_autotune overrides it per level. */
+                                    slices per node (these pin the assembled operator).
+                                    The assembled kernels give the same results (each node's
+                                    arithmetic is the same); the matrix-free level 1 agrees with
+                                    them to FP32 rounding.  gmg_autotune overrides it per level. */
     void* stream;                /* cudaStream_t for all device work; NULL = default stream */
     long long spin_limit;        /* polls (each followed by a ~64 ns sleep) that a block of the fused
                                     lower V-cycle makes at a grid barrier before it gives up and the
@@ -391,8 +396,11 @@ typedef struct {
     int model_tile, model_zchunk;  /* the cost model's choice (used without tuning) */
     int fine_candidates;         /* plans timed */
     double fine_us, model_us;    /* one fine smoothing step: tuned plan, model plan (median of reps) */
-    int bsr_kind[16];            /* per level: 0 streaming (a thread per node), 1 / 2 / 3 K-split with
-                                    8 / 2 / 4 slices per node, -1 not tuned (fine level, TMA-staged
+    int bsr_kind[16];            /* per level: 0 streaming (a thread per node), 1 / 2 / 3 / 4 / 5 K-split
+                                    with 8 / 2 / 4 / 16 / 32 slices per node, 6 level 1 applied
+                                    matrix-free from the fine moduli (only where that equals the
+                                    assembled operator: even fine sizes, every fixed fine DOF with
+                                    fixed prolongation parents), -1 not tuned (fine level, TMA-staged
                                     levels, levels inside the fused lower V-cycle) */
     double bsr_us[16];           /* chosen kernel, one smoothing step */
     double bsr_alt_us[16];       /* the fastest other kernel */

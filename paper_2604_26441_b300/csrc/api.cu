@@ -107,7 +107,16 @@ BsrArgs bsr_args(gmg_handle* h, int li) {
     a.err = h->kerr;
     a.kind = l.bsr_kind;
     if (l.tma) { a.tm_own = &l.tm_own; a.tm_back = &l.tm_back; }
+    if (l.eh) { a.eh = l.eh; a.l1g = &h->l1g; a.cf = l.cf; }
     return a;
+}
+
+// The level kernel a level uses without tuning: the options' choice, or for
+// level 1 under the size rule the matrix-free form where it is exact.
+int default_bsr_kind(const gmg_handle* h, int li) {
+    const Level& l = h->lev[li];
+    if (li == 1 && l.eh && h->opt.bsr_kernel < 0 && !l.tma) return kBsrMatrixFree;
+    return h->opt.bsr_kernel;
 }
 
 // The device view of assembled level li used by the cooperative and
@@ -126,7 +135,9 @@ int partial_count(gmg_handle* h, int li, int kind) {
     // kind 0: operator-kernel partials, 1: vector-kernel partials
     if (kind == 1) return vec_grid_blocks();
     if (li == 0) return fine_grid_blocks(h->lev[0].nx, h->lev[0].ny, h->lev[0].nz);
-    return bsr_grid_blocks(h->lev[li].nn, h->lev[li].tma, h->lev[li].bsr_kind);
+    const Level& l = h->lev[li];
+    if (l.bsr_kind == kBsrMatrixFree && l.eh && !l.tma) return l1mf_grid_blocks(l.nx, l.ny, l.nz);
+    return bsr_grid_blocks(l.nn, l.tma, l.bsr_kind);
 }
 
 // y = K^l x (masked); with dot: partial += x . y and finalised into `slot`.
@@ -419,6 +430,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     for (int li = 1; li < L; ++li)
         for (int kind = 0; kind < kBsrKinds; ++kind)
             maxp = std::max({maxp, bsr_grid_blocks(h->lev[li].nn, true), bsr_grid_blocks(h->lev[li].nn, false, kind)});
+    if (L >= 2) maxp = std::max(maxp, l1mf_grid_blocks(h->lev[1].nx, h->lev[1].ny, h->lev[1].nz));
     maxp = std::max(maxp, 4096);
     h->max_partials = maxp;
     TRY(dalloc(h, &h->partials, maxp));
@@ -445,7 +457,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         launch_hadamard_blocks(Ke, g72, s);
         CU(cudaMemcpyAsync(gh, g72, sizeof gh, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
-        if (!gsym_from_blocks(gh, &h->gs, h->gs64))
+        if (!gsym_from_blocks(gh, &h->gs, h->gs64) || !l1_coef_from_blocks(gh, &h->l1g))
             return fail(GMG_ERR_CUDA, "element stiffness lacks the cube-symmetric block structure");
         if (o.fine_smoother != GMG_FINE_FP32) {
             uint16_t op[2048];
@@ -478,6 +490,20 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
             launch_finish_bsr(h->lev[li], s);
         }
     }
+    // ---- level 1 matrix-free where that equals the assembled operator (a
+    // smoothed level, even fine sizes, fixed fine DOFs with fixed parents)
+    if (L >= 3 && !(o.bsr_tma_nodes > 0 && h->lev[1].nn >= o.bsr_tma_nodes)) {
+        std::vector<uint8_t> m0((size_t)l0.nn);
+        CU(cudaMemcpyAsync(m0.data(), l0.mask, m0.size(), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (l1mf_eligible(l0.nx, l0.ny, l0.nz, m0.data())) {
+            Level& c = h->lev[1];
+            TRY(dalloc(h, &c.eh, 8 * (size_t)c.nx * c.ny * c.nz));
+            TRY(dalloc(h, &c.cf, 32 * (size_t)c.nx * c.ny * c.nz));
+            launch_l1_ehat(h->E64, l0.nx, l0.ny, l0.nz, c.eh, s);
+        }
+    }
+    for (int li = 1; li < L; ++li) h->lev[li].bsr_kind = default_bsr_kind(h, li);
     CU(cudaGetLastError());
 
     // ---- spectral estimates and smoother coefficients
@@ -557,7 +583,6 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
     // ---- TMA-staged operator for the large assembled levels
     for (int li = 1; li < L; ++li) {
         Level& l = h->lev[li];
-        l.bsr_kind = o.bsr_kernel;
         if (o.bsr_tma_nodes > 0 && l.nn >= o.bsr_tma_nodes) {
             const int rc = encode_bsr_maps(l);
             if (rc != GMG_OK) return fail(rc, "could not encode the tensor maps of an assembled level");
@@ -1246,14 +1271,14 @@ int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
     CU(cudaStreamSynchronize(s));
     if (reps == 0) {  // back to the cost model and the size rule
         fine_set_plan(h->lev[0].nx, h->lev[0].ny, h->lev[0].nz, -1, 0);
-        for (int li = 1; li < h->L; ++li) h->lev[li].bsr_kind = h->opt.bsr_kernel;
+        for (int li = 1; li < h->L; ++li) h->lev[li].bsr_kind = default_bsr_kind(h, li);
         loop_free(h);
         if (out) {
             *out = gmg_tuning{};
             fine_model_plan(h->lev[0].nx, h->lev[0].ny, h->lev[0].nz, &out->fine_tile, &out->fine_zchunk);
             out->model_tile = out->fine_tile;
             out->model_zchunk = out->fine_zchunk;
-            for (int li = 0; li < 16; ++li) out->bsr_kind[li] = li >= 1 && li < h->L ? h->opt.bsr_kernel : -1;
+            for (int li = 0; li < 16; ++li) out->bsr_kind[li] = li >= 1 && li < h->L ? default_bsr_kind(h, li) : -1;
         }
         return GMG_OK;
     }
@@ -1319,8 +1344,10 @@ int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
     for (int li = 1; li < h->L - 1 && li < 16 && rc == GMG_OK; ++li) {
         Level& l = h->lev[li];
         if (l.tma || li >= fused_start) continue;
-        double us[kBsrKinds] = {};
-        for (int kind = 0; kind < kBsrKinds && rc == GMG_OK; ++kind) {
+        // the assembled kernels, and on level 1 the matrix-free form where exact
+        const int nkinds = l.eh ? kBsrMatrixFree + 1 : kBsrKinds;
+        double us[kBsrMatrixFree + 1] = {};
+        for (int kind = 0; kind < nkinds && rc == GMG_OK; ++kind) {
             l.bsr_kind = kind;
             BsrArgs a = bsr_args(h, li);
             a.xin = l.x;
@@ -1332,10 +1359,10 @@ int gmg_autotune(gmg_handle* h, int reps, gmg_tuning* out) {
             rc = timed([&] { launch_bsr(FM_SMOOTH, 0, a, s); }, us[kind]);
         }
         int best = 0;
-        for (int kind = 1; kind < kBsrKinds; ++kind)
+        for (int kind = 1; kind < nkinds; ++kind)
             if (us[kind] < us[best]) best = kind;
         int second = best == 0 ? 1 : 0;
-        for (int kind = 0; kind < kBsrKinds; ++kind)
+        for (int kind = 0; kind < nkinds; ++kind)
             if (kind != best && us[kind] < us[second]) second = kind;
         l.bsr_kind = best;
         t.bsr_kind[li] = best;
@@ -1455,6 +1482,8 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out) {
         if (rc == GMG_OK) rc = dalloc(h, &l.b, 3 * l.nn);
         if (rc == GMG_OK) rc = dalloc(h, &l.t, 3 * l.nn);
         if (rc == GMG_OK) rc = dalloc(h, &l.d, 3 * l.nn);
+        // the matrix-free level 1's corner forces are workspace of each handle
+        if (rc == GMG_OK && l.cf) rc = dalloc(h, &l.cf, 32 * (size_t)l.nx * l.ny * l.nz);
     }
     float** fv[] = {&h->r, &h->z, &h->p, &h->q, &h->x2_0, &h->t0, &h->d0};
     for (float** v : fv) {

@@ -999,6 +999,10 @@ void launch_bsr_tma(int g, const BsrArgs& a, cudaStream_t s) {
 }
 
 void launch_bsr(int mode, int dot, const BsrArgs& a, cudaStream_t s) {
+    if (a.kind == kBsrMatrixFree && a.eh && a.l1g && a.cf && !a.tm_own) {
+        launch_l1mf(mode, dot, a, *a.l1g, a.cf, s);
+        return;
+    }
     note_launch();
     if (a.tm_own) {
         const int g = bsr_grid_blocks(a.nn, true);

@@ -91,6 +91,10 @@ struct KeD { double v[576]; };
 //     c (u_i + u_j)) and one entry d for the XYZ mode.
 // GSym holds (a - b, b) of class 0, the same of class 7, (p, q) and (c, d).
 struct GSym { float2 ab0, ab7, pq, cd; };
+// The level-1 operator in the coarse element's mode basis: G0 = T0^T G T0 on
+// the structural pattern of level1_mf.cu (279 entries).
+constexpr int kL1Coefs = 279;
+struct L1Coef { float g[kL1Coefs]; };
 // Host: GSym from the 72 FP64 block entries (each value the mean of its equal
 // entries); false when an entry departs from the pattern by more than 1e-12 of
 // the largest one.  v64, when given, receives the eight values in FP64 in the
@@ -211,6 +215,8 @@ struct Level {
     long long ps = 0;               // plane stride of A32: nn rounded up to 4 (16-byte aligned planes)
     bool tma = false;               // operator streamed by the TMA-staged kernel (tm_own / tm_back valid)
     int bsr_kind = -1;              // kernel of the non-TMA operator (bsr_grid_blocks), set by gmg_autotune
+    float* eh = nullptr;            // level 1: Ehat per coarse element when the matrix-free form is exact
+    float* cf = nullptr;            // level 1: corner forces of the matrix-free form [8][ne] float4 (per handle)
     CUtensorMap tm_own{};           // A32 as a [126][ps] FP32 tensor, box 126 planes x 64 nodes
     CUtensorMap tm_back{};          // same tensor, box 9 planes x 68 nodes
     float* x = nullptr;             // [3nn] smoother iterate / V-cycle output (levels >= 1)
@@ -415,6 +421,7 @@ struct gmg_handle {
     gmg::KeF keF{};
     gmg::KeD keD{};
     gmg::GSym gs{};                             // fine operator coefficients (symmetric form of G)
+    gmg::L1Coef l1g{};                          // level-1 matrix-free coefficients (G0 on its pattern)
     double gs64[8] = {};                        // the same eight values in FP64 (FP64 true residual)
     float kd = 0.f;                             // diagonal entry of K_e (all equal)
     double setup_ms = 0.0;                      // host wall time of gmg_setup (clones: the source's)
@@ -572,6 +579,9 @@ struct BsrArgs {
     int kind;                    // kernel choice, as bsr_grid_blocks
     const CUtensorMap* tm_own;   // non-null: stream through the TMA-staged kernel
     const CUtensorMap* tm_back;
+    const float* eh;             // level 1 applied matrix-free (kind kBsrMatrixFree): Ehat per coarse element
+    const L1Coef* l1g;           // and its coefficients (host copy, passed by value to the kernel)
+    float* cf;                   // and its corner-force workspace [8][ne] float4
 };
 // Blocks (= dot partials) of the operator launch for a level of nn nodes: 64
 // nodes per block for the TMA-staged and K-split kernels, 256 for streaming.
@@ -579,6 +589,19 @@ struct BsrArgs {
 // 0 = streaming k_bsr, 1 / 2 / 3 / 4 / 5 = K-split k_bsr_ks with 8 / 2 / 4 /
 // 16 / 32 slices (ignored when tma)
 constexpr int kBsrKinds = 6;
+// Level 1 applied matrix-free from the fine moduli (level1_mf.cu), where exact.
+constexpr int kBsrMatrixFree = 6;
+int l1mf_grid_blocks(int nx, int ny, int nz);
+void launch_l1mf(int mode, int dot, const BsrArgs& a, const L1Coef& G, float* cf, cudaStream_t s);
+// Ehat (8 floats per coarse element, [ne1][8]) from the FP64 fine moduli; fine sizes even.
+void launch_l1_ehat(const double* E_fine, int nx, int ny, int nz, float* eh, cudaStream_t s);
+// Host: the 279 values from the FP64 blocks of G; false if G0 has entries off the pattern.
+bool l1_coef_from_blocks(const double g[72], L1Coef* out);
+// Host: whether the matrix-free form equals the assembled level-1 operator for a
+// fine grid of nx x ny x nz elements with fixed-component bits fine_mask_host
+// (dense numbering): even sizes, and every fixed fine DOF with only fixed
+// prolongation parents.
+bool l1mf_eligible(int nx, int ny, int nz, const uint8_t* fine_mask_host);
 int bsr_grid_blocks(long long nn, bool tma, int kind = -1);
 // Encodes the two tensor maps of a level's FP32 planes; GMG_OK or an error code.
 int encode_bsr_maps(Level& l);

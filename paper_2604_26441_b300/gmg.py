@@ -33,6 +33,9 @@ class GMGError(RuntimeError):
 
 # arithmetic of the fine-level smoother's element contraction (gmg_options.fine_smoother)
 FINE_SMOOTHERS = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+# assembled-level kernels (gmg_options.bsr_kernel, gmg_tuning.bsr_kind); kind 6 is level 1
+# applied matrix-free from the fine moduli (chosen where it equals the assembled operator)
+BSR_KINDS = ["streaming", "k-split-8", "k-split-2", "k-split-4", "k-split-16", "k-split-32", "matrix-free"]
 # fine kernel tiles (GMG_FINE_TILE_*): threads per block, "pair" = two element columns a thread
 FINE_TILES = ["32x8", "16x16", "pair-8x16", "pair-16x8", "pair-16x16"]
 
@@ -408,7 +411,7 @@ class Solver:
         return {"fine_tile": FINE_TILES[t.fine_tile], "fine_zchunk": t.fine_zchunk,
                 "model_tile": FINE_TILES[t.model_tile], "model_zchunk": t.model_zchunk,
                 "fine_candidates": t.fine_candidates, "fine_us": t.fine_us, "model_us": t.model_us,
-                "bsr": [{"level": l, "kind": ["streaming", "k-split-8", "k-split-2", "k-split-4", "k-split-16", "k-split-32"][t.bsr_kind[l]],
+                "bsr": [{"level": l, "kind": BSR_KINDS[t.bsr_kind[l]],
                          "us": t.bsr_us[l],
                          "other_us": t.bsr_alt_us[l]} for l in range(1, min(L, 16)) if t.bsr_kind[l] >= 0]}
 
