@@ -222,20 +222,22 @@ __global__ void __launch_bounds__(kL1Threads) k_l1mf_elem(BsrArgs a, const __gri
                                                            int stage) {
     extern __shared__ float4 sn[];  // [stage]: 2 ranges of at most stage / 2 nodes
     pdl_entry();
+    // 32-bit indices throughout (set-up admits level 1 only with 8 ne < 2^31)
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long ne = (long long)nx * ny * nz;
-    const long long NX = nx + 1, NXY = NX * (ny + 1);
-    const long long e_first = blockIdx.x * (long long)kL1Threads;
-    const long long e_last = (e_first + kL1Threads < ne ? e_first + kL1Threads : ne) - 1;
-    auto low_node = [&](long long e) {
-        return (e % nx) + NX * ((e / nx) % ny) + NXY * (e / ((long long)nx * ny));
+    const int ne = nx * ny * nz, nxy = nx * ny;
+    const int NX = nx + 1, NXY = NX * (ny + 1), nn = (int)a.nn;
+    const int e_first = blockIdx.x * kL1Threads;
+    const int e_last = (e_first + kL1Threads < ne ? e_first + kL1Threads : ne) - 1;
+    auto low_node = [&](int e) {
+        const int k = e / nxy, r = e - k * nxy, j = r / nx;
+        return (r - j * nx) + NX * j + NXY * k;
     };
-    const long long lo = low_node(e_first);
-    const int span = (int)(low_node(e_last) + NX + 2 - lo);  // nodes per range
+    const int lo = low_node(e_first);
+    const int span = low_node(e_last) + NX + 2 - lo;  // nodes per range
     for (int t = threadIdx.x; t < 2 * span; t += kL1Threads) {
-        const long long n = lo + (t < span ? t : t - span + NXY);
+        const int n = lo + (t < span ? t : t - span + NXY);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (n < a.nn) {
+        if (n < nn) {
             const int m = __ldg(a.mask + n);
             const float x = __ldg(a.xin + 3 * n), y = __ldg(a.xin + 3 * n + 1), z = __ldg(a.xin + 3 * n + 2);
             v = make_float4((m & 1) ? 0.f : x, (m & 2) ? 0.f : y, (m & 4) ? 0.f : z, 0.f);
@@ -243,13 +245,13 @@ __global__ void __launch_bounds__(kL1Threads) k_l1mf_elem(BsrArgs a, const __gri
         sn[GMG_B(t, stage, 617)] = v;
     }
     __syncthreads();
-    const long long e = e_first + threadIdx.x;
+    const int e = e_first + threadIdx.x;
     if (e >= ne) return;
-    const int r0 = (int)(low_node(e) - lo);
+    const int r0 = low_node(e) - lo;
     float u[3][8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const int r = r0 + (q & 1) + (int)NX * ((q >> 1) & 1) + ((q >> 2) & 1) * span;
+        const int r = r0 + (q & 1) + NX * ((q >> 1) & 1) + ((q >> 2) & 1) * span;
         const float4 v = sn[GMG_B(r, stage, 618)];
         u[0][q] = v.x;
         u[1][q] = v.y;
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(kL1Threads) k_l1mf_elem(BsrArgs a, const __gri
     }
     float eh[8];
     {
-        const float4* p = reinterpret_cast<const float4*>(a.eh) + GMG_B(2 * e, 2 * ne, 613);
+        const float4* p = reinterpret_cast<const float4*>(a.eh) + GMG_B(2 * e, 2LL * ne, 613);
         const float4 e0 = __ldg(p), e1 = __ldg(p + 1);
         eh[0] = e0.x; eh[1] = e0.y; eh[2] = e0.z; eh[3] = e0.w;
         eh[4] = e1.x; eh[5] = e1.y; eh[6] = e1.z; eh[7] = e1.w;
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(kL1Threads) k_l1mf_elem(BsrArgs a, const __gri
         l1_wht_t(f[c]);
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) cf[GMG_B(q * ne + e, 8 * ne, 615)] = make_float4(f[0][q], f[1][q], f[2][q], 0.f);
+    for (int q = 0; q < 8; ++q) cf[GMG_B(q * ne + e, 8LL * ne, 615)] = make_float4(f[0][q], f[1][q], f[2][q], 0.f);
 }
 
 // Phase 2, one thread per node: the corner forces of its (up to 8) cells added
@@ -290,19 +292,19 @@ template <int MODE, bool DOT>
 __global__ void __launch_bounds__(kL1Threads) k_l1mf_node(BsrArgs a, const float4* cf) {
     pdl_entry();
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long nn = a.nn, ne = (long long)nx * ny * nz;
-    const long long n = blockIdx.x * (long long)kL1Threads + threadIdx.x;
+    const int nn = (int)a.nn, ne = nx * ny * nz;
+    const int n = blockIdx.x * kL1Threads + threadIdx.x;
     DSAcc dotv;
     if (n < nn) {
-        const int NX = nx + 1, NY = ny + 1;
-        const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / ((long long)NX * NY));
+        const int NX = nx + 1, NXY = NX * (ny + 1);
+        const int k = n / NXY, r = n - k * NXY, j = r / NX, i = r - j * NX;
         float y[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 8; ++q) {  // this node is corner q of element (i - qx, j - qy, k - qz)
             const int I = i - (q & 1), J = j - ((q >> 1) & 1), K = k - ((q >> 2) & 1);
             const bool ok = I >= 0 && I < nx && J >= 0 && J < ny && K >= 0 && K < nz;
-            const long long e = ok ? I + (long long)nx * (J + (long long)ny * K) : 0;
-            const float4 f = __ldg(cf + GMG_B(q * ne + e, 8 * ne, 616));
+            const int e = ok ? I + nx * (J + ny * K) : 0;
+            const float4 f = __ldg(cf + GMG_B(q * ne + e, 8LL * ne, 616));
             y[0] = __fadd_rn(y[0], ok ? f.x : 0.f);
             y[1] = __fadd_rn(y[1], ok ? f.y : 0.f);
             y[2] = __fadd_rn(y[2], ok ? f.z : 0.f);
@@ -452,6 +454,7 @@ bool l1_coef_from_blocks(const double g[72], L1Coef* out) {
 
 bool l1mf_eligible(int nx, int ny, int nz, const uint8_t* fine_mask_host) {
     if (nx % 2 || ny % 2 || nz % 2 || nx < 2 || ny < 2 || nz < 2) return false;
+    if (8LL * (nx / 2) * (ny / 2) * (nz / 2) >= (1LL << 31) - 1) return false;  // the kernels' 32-bit indices
     const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
     // every fixed fine DOF: all of its prolongation parents' DOFs fixed (the
     // parents' fixed bits are the fine bits at their injection nodes)
