@@ -92,9 +92,10 @@ struct KeD { double v[576]; };
 // GSym holds (a - b, b) of class 0, the same of class 7, (p, q) and (c, d).
 struct GSym { float2 ab0, ab7, pq, cd; };
 // The level-1 operator in the coarse element's mode basis: G0 = T0^T G T0 on
-// the structural pattern of level1_mf.cu (279 entries).
-constexpr int kL1Coefs = 279;
-struct L1Coef { float g[kL1Coefs]; };
+// the structural pattern of level1_mf.cu (279 entries, which take 21 values up
+// to sign for every Poisson ratio; L1Coef holds those 21).
+constexpr int kL1Coefs = 279, kL1Classes = 21;
+struct L1Coef { float g[kL1Classes]; };
 // Host: GSym from the 72 FP64 block entries (each value the mean of its equal
 // entries); false when an entry departs from the pattern by more than 1e-12 of
 // the largest one.  v64, when given, receives the eight values in FP64 in the
@@ -595,7 +596,8 @@ int l1mf_grid_blocks(int nx, int ny, int nz);
 void launch_l1mf(int mode, int dot, const BsrArgs& a, const L1Coef& G, float* cf, cudaStream_t s);
 // Ehat (8 floats per coarse element, [ne1][8]) from the FP64 fine moduli; fine sizes even.
 void launch_l1_ehat(const double* E_fine, int nx, int ny, int nz, float* eh, cudaStream_t s);
-// Host: the 279 values from the FP64 blocks of G; false if G0 has entries off the pattern.
+// Host: the 21 class values from the FP64 blocks of G; false if G0 has entries off
+// the pattern or a class whose entries differ.
 bool l1_coef_from_blocks(const double g[72], L1Coef* out);
 // Host: whether the matrix-free form equals the assembled level-1 operator for a
 // fine grid of nx x ny x nz elements with fixed-component bits fine_mask_host

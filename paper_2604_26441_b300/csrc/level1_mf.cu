@@ -91,29 +91,88 @@ constexpr bool l1_g_nonzero(int a, int c, int b, int c2) {
 
 constexpr int kL1Modes = 24;  // (m, c) -> 3 m + c
 
+// Which of the eight values of G's symmetric form (0 a, 1 b of class 0; 2 a',
+// 3 b' of class 7; 4 p, 5 q of classes 1, 2, 4; 6 c, 7 d of classes 3, 5, 6)
+// G couples modes (a, c) and (b, c2) with, or -1.
+constexpr int l1_g_value(int a, int c, int b, int c2) {
+    if (!l1_g_nonzero(a, c, b, c2)) return -1;
+    const int sigma = l1_parity(a, c);
+    if (sigma == 0) return c == c2 ? 0 : 1;
+    if (sigma == 7) return c == c2 ? 2 : 3;
+    if (sigma == 1 || sigma == 2 || sigma == 4) return c == c2 ? 4 : 5;
+    const int dr = sigma == 3 ? 2 : (sigma == 5 ? 1 : 0);
+    return c == dr ? 7 : 6;
+}
+// T0: child monomial a from coarse monomial m (per axis 1, -1/2 or 1/2; 0 when
+// a is not inside m).  Products of these are exact in double.
+constexpr double l1_t0(int a, int m) {
+    double w = 1.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        const int ab = (a >> ax) & 1, mb = (m >> ax) & 1;
+        if (ab && !mb) return 0.0;
+        if (mb) w *= ab ? 0.5 : -0.5;
+    }
+    return w;
+}
+
 struct L1Pattern {
-    int count;
+    int count, classes;
     int i[kL1Coefs], j[kL1Coefs], d[kL1Coefs];
+    int cls[kL1Coefs];   // the entry equals (neg ? -1 : 1) * class value cls
+    bool neg[kL1Coefs];
+    double w[kL1Coefs][8];  // the entry as a combination of G's eight values
 };
 // Entries (i, j) of G0 = T0^T G T0 with some a inside m_i and b inside m_j
-// coupled by G, sorted by row, then parity difference, then column.
+// coupled by G, sorted by row, then parity difference, then column; each entry
+// is the combination sum_{a, b} T0[a][m_i] G_ab T0[b][m_j] of G's eight values,
+// and entries with the same combination up to sign share a class (equal for
+// every Poisson ratio).
 constexpr L1Pattern l1_make_pattern() {
     L1Pattern p{};
     p.count = 0;
+    p.classes = 0;
+    int rep[kL1Coefs] = {};  // the first entry of each class
     for (int i = 0; i < kL1Modes; ++i)
         for (int d = 0; d < 8; ++d)
             for (int j = 0; j < kL1Modes; ++j) {
                 const int mi = i / 3, ci = i % 3, mj = j / 3, cj = j % 3;
                 if ((l1_parity(mi, ci) ^ l1_parity(mj, cj)) != d) continue;
+                double w[8] = {};
                 bool nz = false;
                 for (int a = 0; a < 8; ++a)
-                    for (int b = 0; b < 8; ++b)
-                        if ((a & ~mi) == 0 && (b & ~mj) == 0 && l1_g_nonzero(a, ci, b, cj)) nz = true;
+                    for (int b = 0; b < 8; ++b) {
+                        const int g = l1_g_value(a, ci, b, cj);
+                        if ((a & ~mi) == 0 && (b & ~mj) == 0 && g >= 0) {
+                            w[g] += l1_t0(a, mi) * l1_t0(b, mj);
+                            nz = true;
+                        }
+                    }
                 if (!nz) continue;
                 if (p.count < kL1Coefs) {
-                    p.i[p.count] = i;
-                    p.j[p.count] = j;
-                    p.d[p.count] = d;
+                    const int n = p.count;
+                    p.i[n] = i;
+                    p.j[n] = j;
+                    p.d[n] = d;
+                    for (int k = 0; k < 8; ++k) p.w[n][k] = w[k];
+                    int c = -1;
+                    bool ng = false;
+                    for (int q = 0; q < p.classes && c < 0; ++q) {
+                        bool same = true, opp = true;
+                        for (int k = 0; k < 8; ++k) {
+                            same = same && p.w[rep[q]][k] == w[k];
+                            opp = opp && p.w[rep[q]][k] == -w[k];
+                        }
+                        if (same || opp) {
+                            c = q;
+                            ng = !same;
+                        }
+                    }
+                    if (c < 0) {
+                        c = p.classes++;
+                        rep[c] = n;
+                    }
+                    p.cls[n] = c;
+                    p.neg[n] = ng;
                 }
                 ++p.count;
             }
@@ -121,6 +180,7 @@ constexpr L1Pattern l1_make_pattern() {
 }
 constexpr L1Pattern kL1Pat = l1_make_pattern();
 static_assert(kL1Pat.count == kL1Coefs, "G0 has 279 structural non-zeros");
+static_assert(kL1Pat.classes == kL1Classes, "G0's entries take 21 values up to sign");
 
 }  // namespace
 
@@ -139,20 +199,22 @@ __host__ __device__ constexpr int l1_group_start(int n) {
     return n;
 }
 template <int N>
-__device__ __forceinline__ void l1_term(L1Acc& s, const float* G, const float (&v)[kL1Modes], const float (&eh)[8],
-                                        float (&w)[kL1Modes]) {
-    constexpr int I = kL1Pat.i[N], J = kL1Pat.j[N], D = kL1Pat.d[N];
+__device__ __forceinline__ void l1_term(L1Acc& s, const float (&G)[kL1Classes], const float (&v)[kL1Modes],
+                                        const float (&eh)[8], float (&w)[kL1Modes]) {
+    constexpr int I = kL1Pat.i[N], J = kL1Pat.j[N], D = kL1Pat.d[N], C = kL1Pat.cls[N];
+    constexpr bool NEG = kL1Pat.neg[N];
     constexpr int S = l1_group_start(N);
     constexpr bool grp_first = S == N;
     constexpr bool row_first_group = S == 0 || kL1Pat.i[S - 1] != I;  // the row's first group
     constexpr bool row_last = N + 1 == kL1Coefs || kL1Pat.i[N + 1] != I;
     constexpr bool grp_last = row_last || kL1Pat.d[N + 1] != D;
-    s.t = grp_first ? __fmul_rn(G[N], v[J]) : __fmaf_rn(G[N], v[J], s.t);
+    const float g = NEG ? -G[C] : G[C];
+    s.t = grp_first ? __fmul_rn(g, v[J]) : __fmaf_rn(g, v[J], s.t);
     if (grp_last) s.acc = row_first_group ? __fmul_rn(eh[D], s.t) : __fmaf_rn(eh[D], s.t, s.acc);
     if (row_last) w[I] = s.acc;
 }
 template <int... Ns>
-__device__ __forceinline__ void l1_terms(std::integer_sequence<int, Ns...>, const float* G,
+__device__ __forceinline__ void l1_terms(std::integer_sequence<int, Ns...>, const float (&G)[kL1Classes],
                                          const float (&v)[kL1Modes], const float (&eh)[8], float (&w)[kL1Modes]) {
     L1Acc s{0.f, 0.f};
     (l1_term<Ns>(s, G, v, eh, w), ...);
@@ -273,7 +335,10 @@ __global__ void __launch_bounds__(kL1Threads) k_l1mf_elem(BsrArgs a, const __gri
     }
 #pragma unroll
     for (int i = 0; i < kL1Modes; ++i) w[i] = 0.f;
-    l1_terms(std::make_integer_sequence<int, kL1Coefs>{}, G.g, v, eh, w);
+    float gc[kL1Classes];  // the 21 class values, in registers for the whole contraction
+#pragma unroll
+    for (int k = 0; k < kL1Classes; ++k) gc[k] = G.g[k];
+    l1_terms(std::make_integer_sequence<int, kL1Coefs>{}, gc, v, eh, w);
     float f[3][8];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -442,10 +507,19 @@ bool l1_coef_from_blocks(const double g[72], L1Coef* out) {
             big = std::max(big, std::fabs(s));
         }
     bool inpat[kL1Modes][kL1Modes] = {};
+    double cv[kL1Classes] = {};
+    bool have[kL1Classes] = {};
     for (int n = 0; n < kL1Coefs; ++n) {
+        const double v = G0[kL1Pat.i[n]][kL1Pat.j[n]] * (kL1Pat.neg[n] ? -1.0 : 1.0);
         inpat[kL1Pat.i[n]][kL1Pat.j[n]] = true;
-        out->g[n] = (float)G0[kL1Pat.i[n]][kL1Pat.j[n]];
+        if (!have[kL1Pat.cls[n]]) {
+            cv[kL1Pat.cls[n]] = v;
+            have[kL1Pat.cls[n]] = true;
+        } else if (std::fabs(v - cv[kL1Pat.cls[n]]) > 1e-12 * big) {
+            return false;  // a class whose entries differ: G lacks the assumed structure
+        }
     }
+    for (int k = 0; k < kL1Classes; ++k) out->g[k] = (float)cv[k];
     for (int i = 0; i < kL1Modes; ++i)
         for (int j = 0; j < kL1Modes; ++j)
             if (!inpat[i][j] && std::fabs(G0[i][j]) > 1e-12 * big) return false;
