@@ -614,6 +614,91 @@ __global__ void k_prolong_add(int fnx, int fny, int fnz, int fpx, int cnx, int c
     if (!fixed_bit(msk, 2)) fine[3 * np + 2] += s2;
 }
 
+// The same for a fine level whose rows are padded to a multiple of 4 nodes
+// (level 0): a thread takes 4 x-consecutive fine nodes of a row, whose x-parents
+// are among 3 coarse nodes, so that each coarse value is loaded once per group
+// instead of once per fine node and weight; the fine row segment (12 floats,
+// 16-byte aligned) moves as 3 float4.  Per node the weights, parents and the
+// order of the sum are those of k_prolong_add, so the results are bitwise equal.
+__global__ void k_prolong_add4(int fnx, int fny, int fnz, int fpx, int cnx, int cny, const uint8_t* fmask,
+                               const float* coarse, float* fine) {
+    pdl_entry();
+    const int FX = fnx + 1, FY = fny + 1, NZ = fnz + 1;
+    const int CX = cnx + 1, CY = cny + 1;
+    const int G = (FX + 3) / 4;  // groups per row
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= G * FY * NZ) return;
+    const int q = t % G, r = t / G, j = r % FY, k = r / FY;
+    const int i0 = 4 * q, xb = 2 * q;  // x-parents of the group lie in xb .. xb + 2
+    int iy[2], iz[2];
+    float wy[2], wz[2];
+    coarse_parents2(j, fny, iy, wy);
+    coarse_parents2(k, fnz, iz, wz);
+    [[maybe_unused]] const long long cn = (long long)CX * CY * (fnz / 2 + 1);  // bounds of the checked build
+    // coarse values cv[c][b][x - xb][comp] of the group's parents
+    float cv[2][2][3][3];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const bool zdup = c == 1 && iz[1] == iz[0], ydup = b == 1 && iy[1] == iy[0];
+            if (zdup || ydup) {  // the same parent row as one already loaded
+#pragma unroll
+                for (int x = 0; x < 3; ++x)
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) cv[c][b][x][m] = zdup ? cv[0][b][x][m] : cv[c][0][x][m];
+                continue;
+            }
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                const int cx = min(xb + x, CX - 1);
+                const int mi = (int)GMG_B(cx + CX * (iy[b] + CY * iz[c]), cn, 214);
+#pragma unroll
+                for (int m = 0; m < 3; ++m) cv[c][b][x][m] = __ldg(coarse + 3 * mi + m);
+            }
+        }
+    const long long row = (long long)fpx * (j + (long long)FY * k);
+    float4* seg = reinterpret_cast<float4*>(fine + 3 * GMG_B(row + i0, (long long)fpx * FY * NZ, 215));
+    float f[12];
+    {
+        const float4 a = seg[0], b = seg[1], c = seg[2];
+        f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y;
+        f[6] = b.z; f[7] = b.w; f[8] = c.x; f[9] = c.y; f[10] = c.z; f[11] = c.w;
+    }
+    const long long nrow = (long long)FX * (j + (long long)FY * k);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u;
+        if (i >= FX) break;  // pad nodes stay 0
+        int ix[2];
+        float wx[2];
+        coarse_parents2(i, fnx, ix, wx);  // (parents xb + x below; only the weights are used)
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const float w = wx[a] * wy[b] * wz[c];
+                    // the parent's slot among the group's three: u / 2 for an even
+                    // node (both weights on it), u's two neighbours for an odd one
+                    // (at the clamped end of an odd row the second weight is 0)
+                    const int x = (a == 0 || !(u & 1)) ? (u >> 1) : ((u + 1) >> 1);
+                    s0 = fmaf(w, cv[c][b][x][0], s0);
+                    s1 = fmaf(w, cv[c][b][x][1], s1);
+                    s2 = fmaf(w, cv[c][b][x][2], s2);
+                }
+        const uint8_t msk = fmask[GMG_B(nrow + i, (long long)FX * FY * NZ, 216)];
+        if (!fixed_bit(msk, 0)) f[3 * u] += s0;
+        if (!fixed_bit(msk, 1)) f[3 * u + 1] += s1;
+        if (!fixed_bit(msk, 2)) f[3 * u + 2] += s2;
+    }
+    seg[0] = make_float4(f[0], f[1], f[2], f[3]);
+    seg[1] = make_float4(f[4], f[5], f[6], f[7]);
+    seg[2] = make_float4(f[8], f[9], f[10], f[11]);
+}
+
 // x[free_idx[i]] = sum_j Ainv[i][j] b[free_idx[j]]  (FP64 accumulation), and
 // x = 0 on the fixed DOFs (mask; no separate memset): the gathered right-hand
 // side is staged in shared memory once per block, then each warp reduces a few
@@ -1132,6 +1217,12 @@ void launch_restrict(const Level& f, const Level& c, const float* fine, float* c
 
 void launch_prolong_add(const Level& f, const Level& c, const float* coarse, float* fine, cudaStream_t s) {
     note_launch();
+    if (f.px % 4 == 0 && (reinterpret_cast<uintptr_t>(fine) & 15) == 0) {  // padded rows: 4-node groups
+        const long long groups = (long long)((f.nx + 1 + 3) / 4) * (f.ny + 1) * (f.nz + 1);
+        pdl_launch(k_prolong_add4, dim3((int)((groups + 255) / 256)), dim3(256), 0, s, f.nx, f.ny, f.nz, f.px, c.nx,
+                   c.ny, f.mask, coarse, fine);
+        return;
+    }
     pdl_launch(k_prolong_add, dim3((int)((f.nn + 255) / 256)), dim3(256), 0, s, f.nx, f.ny, f.nz, f.px, c.nx, c.ny, f.mask, coarse,
                fine);
 }
