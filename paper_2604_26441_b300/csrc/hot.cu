@@ -68,19 +68,42 @@ __global__ void k_fine_inv0(int nx, int ny, int nz, int px, const float* E, floa
 
 // First smoother step from x = 0: x_1 = c_a D^{-1} b (no operator application),
 // with the Jacobi scale from set-up.
+// Four nodes per thread and iteration: the padded level-0 vectors hold a
+// multiple of 4 nodes, so the Jacobi scales and masks of 4 nodes are one 16-byte
+// and one 4-byte load and their 12 vector entries three float4 (the same
+// arithmetic per entry as one node at a time).
 __global__ void k_fine_smooth0(FineArgs a) {
     pdl_entry();
     const long long nn = (long long)a.pitch * (a.ny + 1) * (a.nz + 1);  // pads: mask 7, output 0
     const float ca = (float)a.coef[1];
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
-         n += (long long)gridDim.x * blockDim.x) {
-        const float inv = a.inv0[n];
-        const uint8_t m = a.mask[n];
+    const long long n4 = nn / 4;
+    const float4* inv4 = reinterpret_cast<const float4*>(a.inv0);
+    const unsigned* m4 = reinterpret_cast<const unsigned*>(a.mask);
+    const float4* b4 = reinterpret_cast<const float4*>(a.b);
+    float4* o4 = reinterpret_cast<float4*>(a.out);
+    float4* d4 = reinterpret_cast<float4*>(a.dnew);
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n4;
+         g += (long long)gridDim.x * blockDim.x) {
+        const float4 iv = inv4[g];
+        const unsigned mw = m4[g];
+        const float inv[4] = {iv.x, iv.y, iv.z, iv.w};
+        float v[12];
+        {
+            const float4 x0 = b4[3 * g], x1 = b4[3 * g + 1], x2 = b4[3 * g + 2];
+            const float bb[12] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x2.x, x2.y, x2.z, x2.w};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float v = fixed_bit(m, c) ? 0.f : ca * inv * a.b[3 * n + c];
-            a.out[3 * n + c] = v;
-            if (a.dnew) a.dnew[3 * n + c] = v;
+            for (int e = 0; e < 12; ++e) {
+                const unsigned m = (mw >> (8 * (e / 3))) & 0xffu;
+                v[e] = fixed_bit((uint8_t)m, e % 3) ? 0.f : __fmul_rn(__fmul_rn(ca, inv[e / 3]), bb[e]);
+            }
+        }
+        o4[3 * g] = make_float4(v[0], v[1], v[2], v[3]);
+        o4[3 * g + 1] = make_float4(v[4], v[5], v[6], v[7]);
+        o4[3 * g + 2] = make_float4(v[8], v[9], v[10], v[11]);
+        if (a.dnew) {
+            d4[3 * g] = make_float4(v[0], v[1], v[2], v[3]);
+            d4[3 * g + 1] = make_float4(v[4], v[5], v[6], v[7]);
+            d4[3 * g + 2] = make_float4(v[8], v[9], v[10], v[11]);
         }
     }
 }
@@ -777,7 +800,8 @@ __global__ void __launch_bounds__(kVecThreads) k_finalize(const double* partial,
 // (16-byte loads; a row of 3 px floats is a multiple of 4) and skips the pads,
 // whose values stay 0.
 __global__ void __launch_bounds__(kVecThreads) k_pcg_update(double* u, float* r, const float* p, const float* q, int NX,
-                                                            int px, long long n4, const double* sc, double* partial) {
+                                                            int px, long long n4, const double* sc, double* partial,
+                                                            int u16) {
     pdl_entry();
     const double alpha = sc[SC_ALPHA];
     const float af = (float)alpha;
@@ -795,13 +819,41 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(double* u, float* r,
         float4 rv = reinterpret_cast<float4*>(r)[i];
         const float pa[4] = {pv.x, pv.y, pv.z, pv.w}, qa[4] = {qv.x, qv.y, qv.z, qv.w};
         float ra[4] = {rv.x, rv.y, rv.z, rv.w};
-        double* ud = u + GMG_B(row * rowd + c0, n4 * 4 / rowp * rowd, 221);
+        const long long ub = row * rowd + c0;
+        double* ud = u + GMG_B(ub, n4 * 4 / rowp * rowd, 221);
+        if (u16 && c0 + 4 <= rowd) {
+            // a full group: the four FP64 entries as two 16-byte accesses, or one
+            // 8 + 16 + 8 when the group starts on an odd entry (rows of 3 NX doubles)
+            double ua[4];
+            if ((ub & 1) == 0) {
+                const double2 a0 = reinterpret_cast<const double2*>(ud)[0], a1 = reinterpret_cast<const double2*>(ud)[1];
+                ua[0] = a0.x; ua[1] = a0.y; ua[2] = a1.x; ua[3] = a1.y;
+            } else {
+                const double2 a1 = *reinterpret_cast<const double2*>(ud + 1);
+                ua[0] = ud[0]; ua[1] = a1.x; ua[2] = a1.y; ua[3] = ud[3];
+            }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if (c0 + t >= rowd) break;
-            ud[t] = fma(alpha, (double)pa[t], ud[t]);
-            ra[t] = fmaf(-af, qa[t], ra[t]);
-            acc.add_prod(ra[t], ra[t]);
+            for (int t = 0; t < 4; ++t) {
+                ua[t] = fma(alpha, (double)pa[t], ua[t]);
+                ra[t] = fmaf(-af, qa[t], ra[t]);
+                acc.add_prod(ra[t], ra[t]);
+            }
+            if ((ub & 1) == 0) {
+                reinterpret_cast<double2*>(ud)[0] = make_double2(ua[0], ua[1]);
+                reinterpret_cast<double2*>(ud)[1] = make_double2(ua[2], ua[3]);
+            } else {
+                ud[0] = ua[0];
+                *reinterpret_cast<double2*>(ud + 1) = make_double2(ua[1], ua[2]);
+                ud[3] = ua[3];
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (c0 + t >= rowd) break;
+                ud[t] = fma(alpha, (double)pa[t], ud[t]);
+                ra[t] = fmaf(-af, qa[t], ra[t]);
+                acc.add_prod(ra[t], ra[t]);
+            }
         }
         reinterpret_cast<float4*>(r)[i] = make_float4(ra[0], ra[1], ra[2], ra[3]);
     }
@@ -1322,8 +1374,9 @@ void launch_finalize(const double* partial, int n, double* sc, int slot, int op,
 void launch_pcg_update(double* u, float* r, const float* p, const float* q, const Level& l0, const double* sc,
                        double* partial, cudaStream_t s) {
     note_launch();
+    const int u16 = (reinterpret_cast<uintptr_t>(u) & 15) == 0;  // 16-byte accesses to u when aligned
     pdl_launch(k_pcg_update, dim3(kVecBlocks), dim3(kVecThreads), 0, s, u, r, p, q, l0.nx + 1, l0.px, 3 * l0.nnp / 4, sc,
-               partial);
+               partial, u16);
 }
 
 void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s) {
