@@ -570,6 +570,54 @@ __device__ __forceinline__ void restrict_node(int n, int fnx, int fny, int fnz, 
     out[2] = fixed_bit(m, 2) ? 0.f : s2;
 }
 
+// The same restriction for small coarse levels, one coarse node per warp: lane
+// a + 3 b + 9 c (< 27) takes the weighted fine node (a, b, c) of the node's
+// 3 x 3 x 3 support, and the warp adds the 27 terms in a fixed butterfly order
+// (every lane ends with the sums).  With a thread per node these levels leave
+// the GPU nearly idle while each thread walks 27 dependent loads.
+__device__ __forceinline__ void fine_support1(int I, int nf, int a, int& idx, float& w) {
+    const int nc = nf >> 1, f = 2 * I + 1;
+    if (a == 0) {
+        idx = I >= 1 ? 2 * I - 1 : 2 * I;
+        w = I >= 1 ? 0.5f : 0.f;
+    } else if (a == 1) {
+        idx = 2 * I;
+        w = 1.f;
+    } else {
+        idx = f <= nf ? f : 2 * I;
+        w = f <= nf ? (f < 2 * nc ? 0.5f : 1.f) : 0.f;
+    }
+}
+__device__ __forceinline__ void restrict_node_warp(int n, int lane, int fnx, int fny, int fnz, int fpx, int cnx,
+                                                   int cny, const uint8_t* cmask, const float* fine, float out[3]) {
+    const int CX = cnx + 1, CY = cny + 1;
+    const int FX = fpx, FY = fny + 1;  // fine vectors: fpx nodes per row
+    const int I = n % CX, J = (n / CX) % CY, K = n / (CX * CY);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    if (lane < 27) {
+        int ix, iy, iz;
+        float wx, wy, wz;
+        fine_support1(I, fnx, lane % 3, ix, wx);
+        fine_support1(J, fny, (lane / 3) % 3, iy, wy);
+        fine_support1(K, fnz, lane / 9, iz, wz);
+        const float w = wx * wy * wz;
+        const int f = (int)GMG_B(ix + FX * (iy + FY * iz), (long long)FX * FY * (fnz + 1), 217);
+        s0 = __fmul_rn(w, __ldg(fine + 3 * f));
+        s1 = __fmul_rn(w, __ldg(fine + 3 * f + 1));
+        s2 = __fmul_rn(w, __ldg(fine + 3 * f + 2));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 = __fadd_rn(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+        s1 = __fadd_rn(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+        s2 = __fadd_rn(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+    }
+    const uint8_t m = cmask[n];
+    out[0] = fixed_bit(m, 0) ? 0.f : s0;
+    out[1] = fixed_bit(m, 1) ? 0.f : s1;
+    out[2] = fixed_bit(m, 2) ? 0.f : s2;
+}
+
 // The restriction fused with the first smoothing step of the coarse level from
 // a zero iterate: b_c = P^T t (stored, later steps and the residual read it),
 // then x = c_a D^-1 b_c (and the Chebyshev increment d = x), with the same
@@ -602,6 +650,40 @@ __global__ void k_restrict(int fnx, int fny, int fnz, int fpx, int cnx, int cny,
     coarse[3 * n] = bc[0];
     coarse[3 * n + 1] = bc[1];
     coarse[3 * n + 2] = bc[2];
+}
+
+constexpr int kRwWarps = 8;  // coarse nodes per block of the warp-per-node restrictions
+
+__global__ void __launch_bounds__(32 * kRwWarps) k_restrict_smooth0_w(int fnx, int fny, int fnz, int fpx,
+                                                                     const float* fine, BsrArgs a, float* bout) {
+    pdl_entry();
+    const int lane = threadIdx.x & 31;
+    const int n = blockIdx.x * kRwWarps + (threadIdx.x >> 5);
+    if (n >= (int)a.nn) return;  // whole warps leave together
+    float bc[3];
+    restrict_node_warp(n, lane, fnx, fny, fnz, fpx, a.nx, a.ny, a.mask, fine, bc);
+    if (lane < 3) {
+        const int c = lane;
+        const long long q = 3LL * n + c;
+        const float v0 = c == 0 ? bc[0] : (c == 1 ? bc[1] : bc[2]);
+        bout[q] = v0;
+        const float v = __fmul_rn(__fmul_rn((float)a.coef[1], a.invdiag[q]), v0);  // invdiag is 0 on fixed DOFs
+        a.out[q] = v;
+        if (a.dnew) a.dnew[q] = v;
+    }
+}
+
+__global__ void __launch_bounds__(32 * kRwWarps) k_restrict_w(int fnx, int fny, int fnz, int fpx, int cnx, int cny,
+                                                              int cnz, const uint8_t* cmask, const float* fine,
+                                                              float* coarse) {
+    pdl_entry();
+    const int nn = (cnx + 1) * (cny + 1) * (cnz + 1);
+    const int lane = threadIdx.x & 31;
+    const int n = blockIdx.x * kRwWarps + (threadIdx.x >> 5);
+    if (n >= nn) return;
+    float bc[3];
+    restrict_node_warp(n, lane, fnx, fny, fnz, fpx, cnx, cny, cmask, fine, bc);
+    if (lane < 3) coarse[3 * n + lane] = lane == 0 ? bc[0] : (lane == 1 ? bc[1] : bc[2]);
 }
 
 __global__ void k_prolong_add(int fnx, int fny, int fnz, int fpx, int cnx, int cny, const uint8_t* fmask,
@@ -1245,8 +1327,16 @@ int encode_bsr_maps(Level& l) {
     return GMG_OK;
 }
 
+// Coarse levels below this many nodes restrict with a warp per coarse node.
+constexpr long long kRestrictWarpNodes = 32768;
+
 void launch_restrict_smooth0(const Level& f, const float* t, const BsrArgs& a, float* bout, cudaStream_t s) {
     note_launch();
+    if (a.nn < kRestrictWarpNodes) {
+        pdl_launch(k_restrict_smooth0_w, dim3((int)((a.nn + kRwWarps - 1) / kRwWarps)), dim3(32 * kRwWarps), 0, s, f.nx,
+                   f.ny, f.nz, f.px, t, a, bout);
+        return;
+    }
     pdl_launch(k_restrict_smooth0, dim3((int)((a.nn + 127) / 128)), dim3(128), 0, s, f.nx, f.ny, f.nz, f.px, t, a, bout);
 }
 
@@ -1263,6 +1353,11 @@ static int grid_for(long long n) {
 
 void launch_restrict(const Level& f, const Level& c, const float* fine, float* coarse, cudaStream_t s) {
     note_launch();
+    if (c.nn < kRestrictWarpNodes) {
+        pdl_launch(k_restrict_w, dim3((int)((c.nn + kRwWarps - 1) / kRwWarps)), dim3(32 * kRwWarps), 0, s, f.nx, f.ny,
+                   f.nz, f.px, c.nx, c.ny, c.nz, c.mask, fine, coarse);
+        return;
+    }
     pdl_launch(k_restrict, dim3((int)((c.nn + 127) / 128)), dim3(128), 0, s, f.nx, f.ny, f.nz, f.px, c.nx, c.ny, c.nz, c.mask, fine,
                coarse);
 }
