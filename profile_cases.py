@@ -4,7 +4,8 @@
     python profile_cases.py solve-c2-hostloop  # the same, PCG driven from the host
     python profile_cases.py smooth-c2   # set-up, one packed smoothing call, 3 fine smoothing passes
     python profile_cases.py apply-c2    # the same, then 5 fine operator applies (handle's own vectors)
-    python profile_cases.py smooth-l1-c2  # set-up + 3 level-1 smoothing passes (BSR)
+    python profile_cases.py smooth-l1-c2  # set-up + 3 level-1 smoothing passes (the level's default kernel)
+    python profile_cases.py apply-l1-c2   # set-up + 3 level-1 operator applies (matrix-free where exact)
     python profile_cases.py smooth-c2-bf16x3  # fine smoothing, tensor-core contraction
     python profile_cases.py smooth-c2-pair    # fine smoothing, two element columns a thread (8x16 threads, 17 planes)
     python profile_cases.py warmstart-80  # 80^3 set-up, one learned warm start + solve
@@ -81,6 +82,13 @@ def main(case: str) -> None:
         for _ in range(2):
             u, info = S.solve(f, tol=cfg.tol, maxit=cfg.maxit)
             print(info, flush=True)
+    elif case == "apply-l1-c2":
+        n1 = S.level_nodes(1)
+        x = torch.ones(3 * n1, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            S.level_apply(1, x, y)
+        torch.cuda.synchronize()
     elif case == "smooth-l1-c2":
         n1 = S.level_nodes(1)
         b = torch.ones(3 * n1, device="cuda")
