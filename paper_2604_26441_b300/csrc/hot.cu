@@ -916,7 +916,7 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(double* u, float* r,
             }
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                ua[t] = fma(alpha, (double)pa[t], ua[t]);
+                ua[t] = fma(alpha, f2d_exact(pa[t]), ua[t]);
                 ra[t] = fmaf(-af, qa[t], ra[t]);
                 acc.add_prod(ra[t], ra[t]);
             }
@@ -932,7 +932,7 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(double* u, float* r,
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 if (c0 + t >= rowd) break;
-                ud[t] = fma(alpha, (double)pa[t], ud[t]);
+                ud[t] = fma(alpha, f2d_exact(pa[t]), ud[t]);
                 ra[t] = fmaf(-af, qa[t], ra[t]);
                 acc.add_prod(ra[t], ra[t]);
             }
@@ -993,7 +993,7 @@ __global__ void k_axpy_u64(double* u, const float* z, int NX, int px, long long 
     const int rowd = 3 * NX, rowp = 3 * px;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const long long row = i / rowd;
-        u[i] = fma(a, (double)z[GMG_B(i + row * (rowp - rowd), n / rowd * rowp, 225)], u[i]);
+        u[i] = fma(a, f2d_exact(z[GMG_B(i + row * (rowp - rowd), n / rowd * rowp, 225)]), u[i]);
     }
 }
 

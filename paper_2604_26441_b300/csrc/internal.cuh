@@ -300,6 +300,19 @@ struct CoarseFused {
     long long spin_limit;
 };
 
+// float -> double, equal to (double)f for every input, with the conversion of
+// zeros and normal values done by integer operations (IEEE 754: the binary64
+// exponent is the binary32 exponent + 896, the 23 mantissa bits move up by 29).
+// The FP64 pipe of this part issues a small fraction of the FP32 rate, and a
+// conversion costs it as much as a DFMA; subnormal, inf and NaN inputs (which do
+// not occur in the solve's vectors) take the hardware conversion.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned b = __float_as_uint(f), a = b & 0x7fffffffu, e = a >> 23;
+    if ((e == 0u && a != 0u) || e == 0xffu) return (double)f;
+    const unsigned hi = (b & 0x80000000u) | (a == 0u ? 0u : (a >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 // Per-thread dot-product accumulator in double-single arithmetic: products are
 // split exactly with an FMA and summed with TwoSum, so a thread's partial is
 // accurate to ~2^-48 of the sum of |terms| while staying on the FP32 pipes (FP64

@@ -267,9 +267,9 @@ __global__ void __launch_bounds__(kPcgThreads) k_mpcg_update(const __grid_consta
             const float4 qv = reinterpret_cast<const float4*>(q)[qi];
             float4 rv = reinterpret_cast<float4*>(r)[qi];
             double* ud = ul + GMG_B(3 * (row * NX + i), 3 * (nnp / px) * NX - 2, 501);
-            ud[0] = fma(alpha, (double)pv.x, ud[0]);
-            ud[1] = fma(alpha, (double)pv.y, ud[1]);
-            ud[2] = fma(alpha, (double)pv.z, ud[2]);
+            ud[0] = fma(alpha, f2d_exact(pv.x), ud[0]);
+            ud[1] = fma(alpha, f2d_exact(pv.y), ud[1]);
+            ud[2] = fma(alpha, f2d_exact(pv.z), ud[2]);
             rv.x = fmaf(-af, qv.x, rv.x);
             rv.y = fmaf(-af, qv.y, rv.y);
             rv.z = fmaf(-af, qv.z, rv.z);
