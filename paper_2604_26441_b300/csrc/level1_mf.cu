@@ -224,7 +224,7 @@ __device__ __forceinline__ void l1_terms(std::integer_sequence<int, Ns...>, cons
 
 namespace {
 
-constexpr int kL1Threads = 256;
+constexpr int kL1Threads = 128;
 
 template <int NTH>
 __device__ __forceinline__ double l1_block_sum(double v, int tid) {
