@@ -407,7 +407,7 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
         }
     }
     const long long n0 = 3 * l0.nnp;
-    for (float** v : {&h->r, &h->z, &h->p, &h->q, &h->x2_0, &h->t0, &h->d0}) {
+    for (float** v : {&h->r, &h->z, &h->p, &h->q, &h->x2_0, &h->t0, &h->d0, &h->wh, &h->wl}) {
         TRY(dalloc(h, v, n0));
         CU(cudaMemsetAsync(*v, 0, sizeof(float) * n0, s));  // the pads stay 0
     }
@@ -632,14 +632,30 @@ void pcg_restart(gmg_handle* h) {
     vcycle_level(h, 0, h->r, h->z, h->x2_0, SC_RZ, FIN_NONE);
     launch_copy_f32(h->p, h->z, n, h->stream);
 }
-// q = K p, alpha = rz / p.q, u += alpha p, r -= alpha q, ||r||^2; with cond
-// (inside the captured loop) the ||r||^2 reduction also takes the loop's
-// convergence test.
-void pcg_step(gmg_handle* h, double* u, const cudaGraphConditionalHandle* cond = nullptr) {
+// q = K p, alpha = rz / p.q, w += alpha p (the iterate's pending change, added
+// to u by flush_w), r -= alpha q, ||r||^2; with cond (inside the captured loop)
+// the ||r||^2 reduction also takes the loop's convergence test.
+void pcg_step(gmg_handle* h, const cudaGraphConditionalHandle* cond = nullptr) {
     level_apply(h, 0, h->p, h->q, SC_PQ, FIN_ALPHA);
-    launch_pcg_update(u, h->r, h->p, h->q, h->lev[0], h->sc, h->partials, h->stream);
+    launch_pcg_update(h->wh, h->wl, h->r, h->p, h->q, h->lev[0], h->sc, h->partials, h->stream);
     if (cond) launch_finalize_check(h->partials, vec_grid_blocks(), h->sc, *cond, h->stream);
     else launch_finalize(h->partials, vec_grid_blocks(), h->sc, SC_RR, FIN_NONE, h->stream);
+    h->w_dirty = true;
+}
+// u += w, w = 0 (before u is read: the FP64 residual, the end of a solve)
+void flush_w(gmg_handle* h, double* u) {
+    if (!h->w_dirty) return;
+    launch_flush_w(u, h->wh, h->wl, h->lev[0], h->stream);
+    h->w_dirty = false;
+}
+// w = 0 without touching an iterate (steps of an abandoned call)
+int reset_w(gmg_handle* h) {
+    if (!h->w_dirty) return GMG_OK;
+    const long long n = 3 * h->lev[0].nnp;
+    CU(cudaMemsetAsync(h->wh, 0, sizeof(float) * n, h->stream));
+    CU(cudaMemsetAsync(h->wl, 0, sizeof(float) * n, h->stream));
+    h->w_dirty = false;
+    return GMG_OK;
 }
 // z = V(r), beta = r.z / rz, p = z + beta p
 void pcg_direction(gmg_handle* h) {
@@ -654,10 +670,11 @@ void pcg_direction(gmg_handle* h) {
 int clear_pads(gmg_handle* h) {
     if (!h->pads_dirty) return GMG_OK;
     const long long n = 3 * h->lev[0].nnp;
-    for (float* v : {h->r, h->z, h->p, h->q, h->x2_0, h->t0, h->d0})
+    for (float* v : {h->r, h->z, h->p, h->q, h->x2_0, h->t0, h->d0, h->wh, h->wl})
         CU(cudaMemsetAsync(v, 0, sizeof(float) * n, h->stream));
     if (h->fg_V) CU(cudaMemsetAsync(h->fg_V, 0, sizeof(float) * (size_t)(h->fg_m + 1) * n, h->stream));
     if (h->fg_Z) CU(cudaMemsetAsync(h->fg_Z, 0, sizeof(float) * (size_t)h->fg_m * n, h->stream));
+    h->w_dirty = false;
     h->pads_dirty = false;
     return GMG_OK;
 }
@@ -697,7 +714,7 @@ bool capture_loop(gmg_handle* h, double* u, cudaGraph_t g, cudaStream_t cap, uns
     if (ok) ok = cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
     if (ok) {
         pcg_restart(h);
-        pcg_step(h, u, &cond);
+        pcg_step(h, &cond);
         l1 = g_kernel_launches.load();
         cudaStreamCaptureStatus st{};
         cudaGraph_t cg = nullptr;
@@ -721,7 +738,7 @@ bool capture_loop(gmg_handle* h, double* u, cudaGraph_t g, cudaStream_t cap, uns
         ok = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
         if (ok) {
             pcg_direction(h);
-            pcg_step(h, u, &cond);
+            pcg_step(h, &cond);
             l2 = g_kernel_launches.load();
             ok = cudaStreamEndCapture(cap, &body) == cudaSuccess;
         }
@@ -1102,7 +1119,9 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     double* sch = h->sc_host;
     gmg_info inf{};
     TRY(clear_pads(h));
+    TRY(reset_w(h));
     auto finish = [&](int st) -> int {
+        flush_w(h, u);  // the steps since the last FP64 residual
         if (st == GMG_NONFINITE) h->pads_dirty = true;
         const int fe = check_fused(h);
         if (fe != GMG_OK) { h->pads_dirty = true; return fe; }
@@ -1113,6 +1132,7 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
         return st;
     };
     auto true_residual = [&](double& rel) -> int {
+        flush_w(h, u);
         launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f, u, nullptr, h->r, l0.px, h->sc, h->partials,
                             h->gs64, s);
         launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
@@ -1181,6 +1201,7 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
                 launch_set_scalars(h->sc + SC_TOL, 1, target, 0.0, 0.0, 0.0, s);
             }
             CU(cudaGraphLaunch(h->loop_exec, s));
+            h->w_dirty = true;
             TRY(sync_scalars(h));
             const int k_new = (int)sch[SC_IT];
             note_launch(h->loop_prefix_kernels + h->loop_body_kernels * (unsigned long long)(k_new - k - 1));
@@ -1211,7 +1232,7 @@ int gmg_solve(gmg_handle* h, const double* f, double* u, double tol, int maxit, 
     pcg_restart(h);
     int k = 0;
     while (k < maxit) {
-        pcg_step(h, u);
+        pcg_step(h);
         ++k;
         TRY(sync_scalars(h));
         const double relr = std::sqrt(sch[SC_RR]) / nf;
@@ -1385,6 +1406,7 @@ int gmg_kappa_eff(gmg_handle* h, const double* b, int steps, double out[3]) {
     if (steps < 1 || steps > 1000) return fail(GMG_ERR_ARG, "steps must be in [1, 1000]");
     if (h->L == 1) return fail(GMG_ERR_ARG, "single-level hierarchy");
     TRY(clear_pads(h));
+    TRY(reset_w(h));
     h->pads_dirty = true;  // the probe may stop at a breakdown with non-finite scalars
     cudaStream_t s = h->stream;
     Level& l0 = h->lev[0];
@@ -1395,7 +1417,7 @@ int gmg_kappa_eff(gmg_handle* h, const double* b, int steps, double out[3]) {
     pcg_restart(h);
     std::vector<double> al, be;
     for (int k = 0; k < steps; ++k) {
-        pcg_step(h, h->kap_u);
+        pcg_step(h);
         pcg_direction(h);
         TRY(sync_scalars(h));
         const double a = h->sc_host[SC_ALPHA], bt = h->sc_host[SC_BETA];
@@ -1404,6 +1426,7 @@ int gmg_kappa_eff(gmg_handle* h, const double* b, int steps, double out[3]) {
         be.push_back(bt);
         if (bt == 0.0) break;
     }
+    TRY(reset_w(h));  // the probe's iterate is not kept
     if (al.empty()) return fail(GMG_NONFINITE, "the Lanczos probe broke down at its first step");
     // Lanczos matrix from the CG coefficients
     const size_t kk = al.size();
@@ -1485,7 +1508,7 @@ int gmg_clone(const gmg_handle* src, gmg_handle** out) {
         // the matrix-free level 1's corner forces are workspace of each handle
         if (rc == GMG_OK && l.cf) rc = dalloc(h, &l.cf, 32 * (size_t)l.nx * l.ny * l.nz);
     }
-    float** fv[] = {&h->r, &h->z, &h->p, &h->q, &h->x2_0, &h->t0, &h->d0};
+    float** fv[] = {&h->r, &h->z, &h->p, &h->q, &h->x2_0, &h->t0, &h->d0, &h->wh, &h->wl};
     for (float** v : fv) {
         if (rc == GMG_OK) rc = dalloc(h, v, n0);
         if (rc == GMG_OK && cudaMemsetAsync(*v, 0, sizeof(float) * n0, s) != cudaSuccess) rc = GMG_ERR_CUDA;
@@ -1633,8 +1656,10 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
     std::vector<double> nf(count, 0.0);
     std::vector<bool> cold(count, false);
     for (int i = 0; i < count; ++i) infos[i] = gmg_info{};
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count; ++i) {
         if (int rc = clear_pads(hs[i]); rc != GMG_OK) { restore(); return rc; }
+        if (int rc = reset_w(hs[i]); rc != GMG_OK) { restore(); return rc; }
+    }
     // the loads and iterates of a chunk, in slot order
     auto chunk_vecs = [&](const Chunk& c, const double** fc, double** uc) {
         for (size_t l = 0; l < c.items.size(); ++l) {
@@ -1786,6 +1811,8 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
             multi_set_loop_scalars(chunks[c].owner, nl, tol, maxit, nfc, act);
         }
         CU(cudaGraphLaunch(h0->batch_exec, s));
+        for (int i = 0; i < count; ++i)
+            if (chunk_of[i] < 0 && state[i] == 0) hs[i]->w_dirty = true;  // their loops took PCG steps
         if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
         // launches: per single item and per chunk (its longest-running load)
         {
@@ -1821,6 +1848,7 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
             } else {
                 gmg_handle* h = hs[i];
                 const Level& l0 = h->lev[0];
+                flush_w(h, u[i]);
                 launch_fine_resid64(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, f[i], u[i], nullptr, h->r, l0.px, h->sc,
                                     h->partials, h->gs64, s);
                 launch_finalize(h->partials, resid64_grid_blocks(l0.nx, l0.ny, l0.nz), h->sc, SC_TRR, FIN_NONE, s);
@@ -1865,6 +1893,8 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
         }
     }
     int worst = GMG_OK;
+    for (int i = 0; i < count; ++i)
+        if (chunk_of[i] < 0) flush_w(hs[i], u[i]);  // items that stopped without an FP64 residual
     for (int i = 0; i < count; ++i)
         if (infos[i].status == GMG_NONFINITE) hs[i]->pads_dirty = true;
     for (int i = 0; i < count; ++i) {

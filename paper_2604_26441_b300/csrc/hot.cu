@@ -877,70 +877,67 @@ __global__ void __launch_bounds__(kVecThreads) k_finalize(const double* partial,
     }
 }
 
-// u += alpha p (FP64, dense numbering), r -= alpha q (FP32 level-0 vectors of
-// pitch px), partial ||r||^2.  A thread takes four consecutive vector entries
-// (16-byte loads; a row of 3 px floats is a multiple of 4) and skips the pads,
-// whose values stay 0.
-__global__ void __launch_bounds__(kVecThreads) k_pcg_update(double* u, float* r, const float* p, const float* q, int NX,
-                                                            int px, long long n4, const double* sc, double* partial,
-                                                            int u16) {
+// alpha = r.z / p.q (already in sc), r -= alpha q with ||r||^2 partials, and
+// the step alpha p added to the double-float correction (wh + wl, level-0
+// layout) that stands for the FP64 iterate's change since its last flush
+// (k_flush_w): the product by the FP64 alpha is formed exactly as
+// ah p + (al p + e) (alpha = ah + al in FP32 parts, e the FMA error of ah p)
+// and added with a TwoSum, so the FP64 pipe, a small fraction of the FP32 rate
+// on this part, takes no work per entry.  16-byte accesses over whole padded
+// rows (pad entries of r, p, q and w are zero, and zero terms leave the ||r||^2
+// accumulator unchanged).
+__global__ void __launch_bounds__(kVecThreads) k_pcg_update(float* __restrict__ wh, float* __restrict__ wl,
+                                                            float* __restrict__ r, const float* __restrict__ p,
+                                                            const float* __restrict__ q, long long n4,
+                                                            const double* sc, double* partial) {
     pdl_entry();
     const double alpha = sc[SC_ALPHA];
     const float af = (float)alpha;
-    const int rowp = 3 * px, rowd = 3 * NX;
+    const float ah = af, al = (float)(alpha - (double)ah);
     DSAcc acc;
     const long long stride = (long long)gridDim.x * kVecThreads;
-    const unsigned rowq = (unsigned)rowp / 4u;  // float4 groups per padded row (3 px is a multiple of 4)
     for (long long i = blockIdx.x * (long long)kVecThreads + threadIdx.x; i < n4; i += stride) {
-        const unsigned row32 = (unsigned)i / rowq;  // 32-bit division: 3 nnp < 2^31
-        const long long row = row32;
-        const int c0 = 4 * (int)((unsigned)i - row32 * rowq);
-        if (c0 >= rowd) continue;  // four pad entries
         const float4 pv = reinterpret_cast<const float4*>(p)[i];
         const float4 qv = reinterpret_cast<const float4*>(q)[i];
-        float4 rv = reinterpret_cast<float4*>(r)[i];
+        const float4 rv = reinterpret_cast<const float4*>(r)[i];
+        const float4 hv = reinterpret_cast<const float4*>(wh)[i];
+        const float4 lv = reinterpret_cast<const float4*>(wl)[i];
         const float pa[4] = {pv.x, pv.y, pv.z, pv.w}, qa[4] = {qv.x, qv.y, qv.z, qv.w};
-        float ra[4] = {rv.x, rv.y, rv.z, rv.w};
-        const long long ub = row * rowd + c0;
-        double* ud = u + GMG_B(ub, n4 * 4 / rowp * rowd, 221);
-        if (u16 && c0 + 4 <= rowd) {
-            // a full group: the four FP64 entries as two 16-byte accesses, or one
-            // 8 + 16 + 8 when the group starts on an odd entry (rows of 3 NX doubles)
-            double ua[4];
-            if ((ub & 1) == 0) {
-                const double2 a0 = reinterpret_cast<const double2*>(ud)[0], a1 = reinterpret_cast<const double2*>(ud)[1];
-                ua[0] = a0.x; ua[1] = a0.y; ua[2] = a1.x; ua[3] = a1.y;
-            } else {
-                const double2 a1 = *reinterpret_cast<const double2*>(ud + 1);
-                ua[0] = ud[0]; ua[1] = a1.x; ua[2] = a1.y; ua[3] = ud[3];
-            }
+        float ra[4] = {rv.x, rv.y, rv.z, rv.w}, ha[4] = {hv.x, hv.y, hv.z, hv.w}, la[4] = {lv.x, lv.y, lv.z, lv.w};
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                ua[t] = fma(alpha, f2d_exact(pa[t]), ua[t]);
-                ra[t] = fmaf(-af, qa[t], ra[t]);
-                acc.add_prod(ra[t], ra[t]);
-            }
-            if ((ub & 1) == 0) {
-                reinterpret_cast<double2*>(ud)[0] = make_double2(ua[0], ua[1]);
-                reinterpret_cast<double2*>(ud)[1] = make_double2(ua[2], ua[3]);
-            } else {
-                ud[0] = ua[0];
-                *reinterpret_cast<double2*>(ud + 1) = make_double2(ua[1], ua[2]);
-                ud[3] = ua[3];
-            }
-        } else {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                if (c0 + t >= rowd) break;
-                ud[t] = fma(alpha, f2d_exact(pa[t]), ud[t]);
-                ra[t] = fmaf(-af, qa[t], ra[t]);
-                acc.add_prod(ra[t], ra[t]);
-            }
+        for (int t = 0; t < 4; ++t) {
+            // w += alpha p in double-float
+            const float ph = __fmul_rn(ah, pa[t]);
+            const float pl = __fmaf_rn(al, pa[t], __fmaf_rn(ah, pa[t], -ph));
+            const float s = __fadd_rn(ha[t], ph);
+            const float bb = __fsub_rn(s, ha[t]);
+            const float e = __fadd_rn(__fsub_rn(ha[t], __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+            const float lo = __fadd_rn(la[t], __fadd_rn(pl, e));
+            ha[t] = __fadd_rn(s, lo);
+            la[t] = __fsub_rn(lo, __fsub_rn(ha[t], s));
+            ra[t] = fmaf(-af, qa[t], ra[t]);
+            acc.add_prod(ra[t], ra[t]);
         }
         reinterpret_cast<float4*>(r)[i] = make_float4(ra[0], ra[1], ra[2], ra[3]);
+        reinterpret_cast<float4*>(wh)[i] = make_float4(ha[0], ha[1], ha[2], ha[3]);
+        reinterpret_cast<float4*>(wl)[i] = make_float4(la[0], la[1], la[2], la[3]);
     }
-    const double s = block_sum<kVecThreads>(acc.value(), threadIdx.x);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    const double sum = block_sum<kVecThreads>(acc.value(), threadIdx.x);
+    if (threadIdx.x == 0) partial[blockIdx.x] = sum;
+}
+
+// u (dense numbering, FP64) += wh + wl (level-0 layout), then w = 0: the PCG
+// steps since the last flush, added to the FP64 iterate once.
+__global__ void k_flush_w(double* u, float* wh, float* wl, int NX, int px, long long n) {
+    pdl_entry();
+    const int rowd = 3 * NX, rowp = 3 * px;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long row = i / rowd;
+        const long long j = GMG_B(i + row * (rowp - rowd), n / rowd * rowp, 226);
+        u[i] = u[i] + (f2d_exact(wh[j]) + f2d_exact(wl[j]));
+        wh[j] = 0.f;
+        wl[j] = 0.f;
+    }
 }
 
 // p = z + beta p; four consecutive entries per thread and iteration with 16-byte
@@ -1466,12 +1463,16 @@ void launch_finalize(const double* partial, int n, double* sc, int slot, int op,
     pdl_launch(k_finalize, dim3(1), dim3(kVecThreads), 0, s, partial, n, sc, slot, op);
 }
 
-void launch_pcg_update(double* u, float* r, const float* p, const float* q, const Level& l0, const double* sc,
-                       double* partial, cudaStream_t s) {
+void launch_pcg_update(float* wh, float* wl, float* r, const float* p, const float* q, const Level& l0,
+                       const double* sc, double* partial, cudaStream_t s) {
     note_launch();
-    const int u16 = (reinterpret_cast<uintptr_t>(u) & 15) == 0;  // 16-byte accesses to u when aligned
-    pdl_launch(k_pcg_update, dim3(kVecBlocks), dim3(kVecThreads), 0, s, u, r, p, q, l0.nx + 1, l0.px, 3 * l0.nnp / 4, sc,
-               partial, u16);
+    pdl_launch(k_pcg_update, dim3(kVecBlocks), dim3(kVecThreads), 0, s, wh, wl, r, p, q, 3 * l0.nnp / 4, sc, partial);
+}
+
+void launch_flush_w(double* u, float* wh, float* wl, const Level& l0, cudaStream_t s) {
+    note_launch();
+    const long long n = 3 * l0.nn;
+    pdl_launch(k_flush_w, dim3(grid_for(n)), dim3(256), 0, s, u, wh, wl, l0.nx + 1, l0.px, n);
 }
 
 void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s) {

@@ -443,6 +443,10 @@ struct gmg_handle {
     double* lam = nullptr;                      // [kMaxLevels] lambda estimates (device)
     // fine-level PCG vectors
     float *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x2_0 = nullptr, *t0 = nullptr, *d0 = nullptr;
+    // the PCG steps since the FP64 iterate was last updated, in double-float
+    // (level-0 layout); added to u by launch_flush_w before u is read
+    float *wh = nullptr, *wl = nullptr;
+    bool w_dirty = false;                       // steps were launched since the last flush
     // reductions
     double* partials = nullptr;
     int max_partials = 0;
@@ -660,9 +664,12 @@ void launch_dot_f32(const float* a, const float* b, long long n, double* partial
 void launch_dot_f64_masked(const double* a, const double* b, const uint8_t* mask, long long nn,
                            double* partial, cudaStream_t s);
 void launch_finalize(const double* partial, int n, double* sc, int slot, int op, cudaStream_t s);
-// u (dense numbering, FP64) += alpha p; r -= alpha q (level-0 vectors of pitch px)
-void launch_pcg_update(double* u, float* r, const float* p, const float* q, const Level& l0,
+// w = wh + wl (double-float) += alpha p; r -= alpha q; ||r||^2 partials
+// (level-0 vectors of pitch px)
+void launch_pcg_update(float* wh, float* wl, float* r, const float* p, const float* q, const Level& l0,
                        const double* sc, double* partial, cudaStream_t s);
+// u (dense numbering, FP64) += wh + wl, then wh = wl = 0
+void launch_flush_w(double* u, float* wh, float* wl, const Level& l0, cudaStream_t s);
 void launch_p_update(float* p, const float* z, long long n, const double* sc, cudaStream_t s);
 void launch_mask_u64(double* u, const uint8_t* mask, long long nn, double* partial, cudaStream_t s);
 // r = f on free DOFs, 0 elsewhere (pads included): f dense, r a level-0 vector
