@@ -159,6 +159,18 @@ typedef struct {
                                     defaults).  The V-cycle is then a fixed nonlinear operator: pair
                                     it with GMG_OUTER_FGMRES when PCG stalls.  A single-level
                                     hierarchy above the cutoff is refused (GMG_ERR_ARG). */
+    int lower_cluster;           /* 0 (default): one launch per step of the V-cycle's bottom.  1: when
+                                    the last assembled level m >= 2 is small enough that its operator
+                                    fits the shared memory of one 16-CTA thread-block cluster (~3,000
+                                    nodes) and the coarsest level is solved densely, level m's
+                                    smoothing passes, residual and transfers and the coarsest solve
+                                    (the inverse applied in double-float, ~44 bits) run as one
+                                    cluster launch whose steps are separated by the cluster barrier;
+                                    results agree with the per-level kernels to FP32 rounding.  At
+                                    100^3 the one launch (59 us) is slower than the ten per-level
+                                    launches it replaces (5.49 against 5.17 ms per solve), so it is
+                                    off by default.  Not used with fused_coarse_nodes > 0 or a
+                                    pinned bsr_kernel. */
 } gmg_options;
 
 typedef struct {

@@ -231,6 +231,19 @@ void vcycle_level(gmg_handle* h, int li, const float* b, float* X, float* S, int
         launch_coarse_fused(h->cf, h->fused_blocks, s);
         return;
     }
+    if (h->use_lc && li == h->L - 2 && !warm && rfrom && b == l.b && X == l.x) {
+        // this level and the coarsest solve in one cluster launch; the result in l.x
+        const Level& f = h->lev[li - 1];
+        const Level& c = h->lev[li + 1];
+        LowerClusterArgs a{};
+        a.fnx = f.nx; a.fny = f.ny; a.fnz = f.nz; a.ft = rfrom;
+        a.m = coarse_view(h, li);
+        a.cnx = c.nx; a.cny = c.ny; a.cnz = c.nz; a.cnn = (int)c.nn;
+        a.cmask = c.mask; a.cb = c.b; a.cx = c.x;
+        a.nL = h->nL; a.free_idx = h->free_idx; a.Ahi = h->Ahi; a.Alo = h->Alo;
+        launch_lower_cluster(a, h->lc_smem, s);
+        return;
+    }
     if (li == h->L - 1) {
         if (h->coarse_pcg) launch_coarse_pcg(coarse_view(h, li), b, X, l.t, l.d, l.x2, h->opt.coarse_pcg_steps, s);
         else launch_coarse_solve(h->nL, h->free_idx_p, h->Ainv, b, X, l.maskp, l.nnp, s);
@@ -619,6 +632,19 @@ int build(gmg_handle* h, const gmg_grid* g, const float* rho, double p, double E
                 h->use_fused = true;
         }
     }
+    // ---- the bottom of the V-cycle (level L-2 >= 2 and the dense coarsest solve)
+    // as one thread-block cluster launch, when its operator fits the cluster
+    if (o.lower_cluster && !h->use_fused && o.bsr_kernel < 0 && !h->coarse_pcg && h->nL > 0 && L >= 4) {
+        const size_t smem = lower_cluster_smem((int)h->lev[L - 2].nn, h->nL);
+        if (lower_cluster_available(smem)) {
+            const size_t n2 = (size_t)h->nL * h->nL;
+            TRY(dalloc(h, &h->Ahi, n2));
+            TRY(dalloc(h, &h->Alo, n2));
+            launch_split_inverse(h->Ainv, (long long)n2, h->Ahi, h->Alo, s);
+            h->use_lc = true;
+            h->lc_smem = smem;
+        }
+    }
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(s));
     return GMG_OK;
@@ -998,6 +1024,7 @@ void gmg_default_options(gmg_options* o) {
     o->stream = nullptr;
     o->spin_limit = 1LL << 24;
     o->coarse_pcg_steps = 80;
+    o->lower_cluster = 0;
 }
 
 const char* gmg_status_str(int st) {
@@ -1068,6 +1095,7 @@ int gmg_setup(gmg_handle** out, const gmg_grid* g, const float* rho_dev, double 
     if (o.spin_limit < 0) return fail(GMG_ERR_ARG, "spin_limit must be >= 0");
     if (o.coarse_pcg_steps < 1 || o.coarse_pcg_steps > 100000)
         return fail(GMG_ERR_ARG, "coarse_pcg_steps must be in [1, 100000]");
+    if (o.lower_cluster != 0 && o.lower_cluster != 1) return fail(GMG_ERR_ARG, "lower_cluster must be 0 or 1");
 
     int dev = 0;
     cudaDeviceProp prop;

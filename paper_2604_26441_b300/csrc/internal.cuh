@@ -244,6 +244,29 @@ struct CoarseLevel {
     int kind, degree;
 };
 
+// ---- the bottom of the V-cycle as one cluster launch (lower_cluster.cu) -------
+struct LowerClusterArgs {
+    // finer level m - 1 (dense vectors): its residual, restricted into level m
+    int fnx, fny, fnz;
+    const float* ft;
+    // level m, the last assembled level (dense vectors); its x holds the result
+    CoarseLevel m;
+    // coarsest level (dense vectors), its free DOFs and the inverse's FP32 parts
+    int cnx, cny, cnz, cnn;
+    const uint8_t* cmask;
+    float *cb, *cx;
+    int nL;
+    const int* free_idx;
+    const float *Ahi, *Alo;
+};
+// shared memory per CTA for a level m of nn nodes and nL coarsest free DOFs
+size_t lower_cluster_smem(int nn, int nL);
+// whether a cluster with that shared memory can run (sets the kernel attributes)
+bool lower_cluster_available(size_t smem);
+void launch_lower_cluster(const LowerClusterArgs& a, size_t smem, cudaStream_t s);
+// hi[i] = (float)A[i], lo[i] = (float)(A[i] - hi[i])
+void launch_split_inverse(const double* A, long long n, float* hi, float* lo, cudaStream_t s);
+
 // ---- multi-load vectors (multi.cu) ------------------------------------------
 // Up to kLoads right-hand sides on one hierarchy advance together.  A level's
 // multi-load vector holds, for node n (the level's vector numbering; level 0:
@@ -461,6 +484,9 @@ struct gmg_handle {
     int nL = 0;
     int* free_idx = nullptr;                    // [nL] DOF indices of the coarsest free DOFs
     double* Ainv = nullptr;                     // [nL nL]
+    float *Ahi = nullptr, *Alo = nullptr;       // [nL nL] FP32 parts of Ainv (cluster path)
+    bool use_lc = false;                        // bottom of the V-cycle as one cluster launch
+    size_t lc_smem = 0;                         // its shared memory per CTA
     double eps = 0.0;
     gmg::CoarseFused cf{};                      // fused lower V-cycle (levels cf.start..L-1)
     bool use_fused = false;

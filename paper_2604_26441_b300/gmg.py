@@ -60,7 +60,7 @@ class _Options(ctypes.Structure):
                 ("fine_smoother", ctypes.c_int),
                 ("cycle_index", ctypes.c_int), ("outer", ctypes.c_int), ("restart", ctypes.c_int),
                 ("bsr_kernel", ctypes.c_int), ("stream", ctypes.c_void_p), ("spin_limit", ctypes.c_longlong),
-                ("coarse_pcg_steps", ctypes.c_int)]
+                ("coarse_pcg_steps", ctypes.c_int), ("lower_cluster", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -196,7 +196,7 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
             bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
             fine_smoother: str = "fp32", cycle: str = "V", outer: str = "pcg", restart: int = 32,
             bsr_kernel: int = -1, stream: int | None = None, spin_limit: int = 1 << 24,
-            coarse_pcg_steps: int = 80) -> _Options:
+            coarse_pcg_steps: int = 80, lower_cluster: bool = False) -> _Options:
     o = _Options()
     load_library().gmg_default_options(ctypes.byref(o))
     o.levels = levels
@@ -223,19 +223,20 @@ def options(levels: int = 4, smoother: str = "chebyshev", degree: int = 2, coars
     o.stream = stream
     o.spin_limit = spin_limit
     o.coarse_pcg_steps = coarse_pcg_steps
+    o.lower_cluster = 1 if lower_cluster else 0
     return o
 
 
 def config_options(cfg, stream: int | None = None, fused_coarse_nodes: int = 0,
                    bsr_tma_nodes: int = 0, device_loop: bool = True, ir_factor: float = 0.0,
                    fine_smoother: str = "fp32", cycle: str = "V", outer: str = "pcg",
-                   restart: int = 32, bsr_kernel: int = -1) -> _Options:
+                   restart: int = 32, bsr_kernel: int = -1, lower_cluster: bool = False) -> _Options:
     """Options for one of the synthetic configurations in ``inputs.CONFIGS``."""
     return options(levels=cfg.levels, smoother=cfg.smoother, degree=cfg.degree, coarse_smoother=None,
                    coarse_degree=None, omega=cfg.omega, coarse_omega=None, fused_coarse_nodes=fused_coarse_nodes,
                    bsr_tma_nodes=bsr_tma_nodes, device_loop=device_loop, ir_factor=ir_factor,
                    fine_smoother=fine_smoother, cycle=cycle, outer=outer, restart=restart, bsr_kernel=bsr_kernel,
-                   stream=stream)
+                   stream=stream, lower_cluster=lower_cluster)
 
 
 def residual64_noalloc(dims, E, mask, f, u, r=None, nu: float = 0.3, stream: int | None = None) -> float:
