@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine(FineArgs a, GSym G, int zch
                 for (int c = 0; c < 3; ++c) out[c] = fixed_bit(m_pend, c) ? 0.f : __fsub_rn(bb[c], y[c]);
             } else {
                 const float* dd = &sD[EPI_D ? slot : 0][EPI_D ? own3 : 0];
-                const float inv = __frcp_rn(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
+                const float inv = jacobi_rcp(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     float xn = 0.f, dn = 0.f;
@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(BX * BY, 2) k_fine_tc(FineArgs a, int zchunk) 
         const int slot = (kp - kb) & (kRing - 1);
         const float* bb = &sB[slot][own3];
         const float* dd = &sD[slot][own3];
-        const float inv = __frcp_rn(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
+        const float inv = jacobi_rcp(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float xn = 0.f, dn = 0.f;
@@ -953,7 +953,7 @@ k_fine_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
                 }
             } else {
                 const float* dd = reinterpret_cast<const float*>(smem + q * T::STAGE + T::DOFF) + rb;
-                const float inv = __frcp_rn(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
+                const float inv = jacobi_rcp(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
                 float* dn_out = a.dnew + 3 * on;
                 const bool wd = owner && a.dnew != nullptr;
 #pragma unroll

@@ -276,7 +276,7 @@ k_fine_pair(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUt
             } else {
                 const float* dd = reinterpret_cast<const float*>(smem + q * T::STAGE + T::DOFF) + rb;
                 const float2 den = __fmul2_rn(make_float2(a.kd, a.kd), __fadd2_rn(eR1, make_float2(u1.z, u1.w)));
-                const float2 cai = __fmul2_rn(make_float2(ca, ca), make_float2(__frcp_rn(den.x), __frcp_rn(den.y)));
+                const float2 cai = __fmul2_rn(make_float2(ca, ca), make_float2(jacobi_rcp(den.x), jacobi_rcp(den.y)));
                 float* dn_out = a.dnew;
                 const bool wa = own_a && dn_out != nullptr, wb = own_b && dn_out != nullptr;
 #pragma unroll

@@ -62,7 +62,7 @@ __global__ void k_fine_inv0(int nx, int ny, int nz, int px, const float* E, floa
             if (ex >= 0 && ex < nx && ey >= 0 && ey < ny && ez >= 0 && ez < nz)
                 esum += E[ex + (long long)nx * (ey + (long long)ny * ez)];
         }
-        inv0[i + (long long)px * (j + NY * k)] = 1.f / (kd * esum);
+        inv0[i + (long long)px * (j + NY * k)] = jacobi_rcp(__fmul_rn(kd, esum));
     }
 }
 
@@ -1072,7 +1072,7 @@ __global__ void k_scale_invdiag_fine(const float* y, float* w, const float* E, c
     const long long NX = nx + 1, NY = ny + 1, nn = NX * NY * (nz + 1);
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
-        const float inv = 1.f / fine_diag(E, nx, ny, nz, i, j, k, kd);
+        const float inv = jacobi_rcp(fine_diag(E, nx, ny, nz, i, j, k, kd));
         const uint8_t m = mask[n];
         const long long v = 3 * (i + px * (j + NY * k));
 #pragma unroll

@@ -336,6 +336,16 @@ __device__ __forceinline__ double f2d_exact(float f) {
     return __hiloint2double((int)hi, (int)(b << 29));
 }
 
+// 1 / (k_d sum E), the fine level's Jacobi scale: the hardware reciprocal
+// approximation (rcp.approx, within about one ulp), one instruction where the
+// IEEE reciprocal takes a refinement sequence.  Every kernel that forms the
+// scale uses it, so the fine kernels stay bitwise equal to each other.
+__device__ __forceinline__ float jacobi_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Per-thread dot-product accumulator in double-single arithmetic: products are
 // split exactly with an FMA and summed with TwoSum, so a thread's partial is
 // accurate to ~2^-48 of the sum of |terms| while staying on the FP32 pipes (FP64

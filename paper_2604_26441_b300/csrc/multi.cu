@@ -827,7 +827,7 @@ k_mfine(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtenso
                                        fr[2] ? __fsub_rn(bb[2], y[2]) : 0.f, 0.f);
             } else {
                 const float* dd = reinterpret_cast<const float*>(smem + q * T::STAGE + T::DOFF) + rb;
-                const float inv = __frcp_rn(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
+                const float inv = jacobi_rcp(__fmul_rn(a.kd, __fadd_rn(eR1, up.w)));
                 float xn[3], dn[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
