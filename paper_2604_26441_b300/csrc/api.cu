@@ -173,14 +173,16 @@ void level_resid(gmg_handle* h, int li, const float* b, const float* x, float* t
 // One smoother step k on level li: reads x_cur (ignored when zero_init), writes x_next.
 // rfrom (levels >= 1, zero_init only): the finer level's residual; the step then
 // first restricts it into the level's own b (l.b, which b must be).
+// dold_from (level 0): read the previous increment from there instead of the
+// level's d vector (after a first step from zero, whose increment is its output).
 void smooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, const float* xcur, float* xnext,
-                 bool write_d, bool dot, const float* rfrom = nullptr) {
+                 bool write_d, bool dot, const float* rfrom = nullptr, const float* dold_from = nullptr) {
     Level& l = h->lev[li];
     float* d = li == 0 ? h->d0 : l.d;
     cudaStream_t s = h->stream;
     if (li == 0) {
         FineArgs a = fine_args(h);
-        a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
+        a.b = b; a.out = xnext; a.step = k; a.dold = dold_from ? dold_from : d; a.dnew = write_d ? d : nullptr;
         a.partial = dot ? h->partials : nullptr;
         if (zero_init) launch_fine_smooth0(a, s);
         else if (h->opt.fine_smoother != GMG_FINE_FP32) {
@@ -203,11 +205,17 @@ float* smooth_pass(gmg_handle* h, int li, const float* b, float* cur, float* X, 
                    int& writes, int dot_slot = -1, int op = FIN_NONE, const float* rfrom = nullptr) {
     Level& l = h->lev[li];
     const bool cheb = l.kind == GMG_SMOOTHER_CHEBYSHEV;
+    // fine level: a first step from zero leaves d = x, so the next step reads its
+    // increment from that step's output and no copy of it is written
+    const float* d_alias = nullptr;
     for (int k = 0; k < l.degree; ++k) {
         float* next = (writes % 2 == 0) ? S : X;
         const bool last = k == l.degree - 1;
         const bool dot = last && dot_slot >= 0;
-        smooth_step(h, li, k, zero_init && k == 0, b, cur, next, cheb && !last, dot, k == 0 ? rfrom : nullptr);
+        const bool alias = li == 0 && zero_init && k == 0;
+        smooth_step(h, li, k, zero_init && k == 0, b, cur, next, cheb && !last && !alias, dot, k == 0 ? rfrom : nullptr,
+                    k == 1 ? d_alias : nullptr);
+        if (alias && cheb && !last) d_alias = next;
         if (dot) launch_finalize(h->partials, partial_count(h, li, 0), h->sc, dot_slot, op, h->stream);
         cur = next;
         ++writes;
