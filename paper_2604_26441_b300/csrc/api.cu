@@ -1849,6 +1849,8 @@ int gmg_solve_batch(gmg_handle* const* hs, int count, const double* const* f, do
         CU(cudaGraphLaunch(h0->batch_exec, s));
         for (int i = 0; i < count; ++i)
             if (chunk_of[i] < 0 && state[i] == 0) hs[i]->w_dirty = true;  // their loops took PCG steps
+        for (size_t c = 0; c < chunks.size(); ++c)
+            if (chunk_live[c]) chunks[c].owner->mw->w_dirty = true;
         if (int rc = sync_all(); rc != GMG_OK) { restore(); return rc; }
         // launches: per single item and per chunk (its longest-running load)
         {

@@ -290,6 +290,9 @@ struct MultiWork {
     float* Ahi = nullptr;        // coarsest inverse split into FP32 hi + lo (double-float apply)
     float* Alo = nullptr;
     float* bc = nullptr;         // [nL][kLoads] gathered coarsest right-hand sides
+    float2* wcor = nullptr;      // [kLoads][3 nn] the PCG steps since the iterates were last updated
+                                 // (double-float hi, lo per DOF); added to them before the FP64 residual
+    bool w_dirty = false;        // steps were launched since the last flush
     void* pinned = nullptr;      // host-mapped mirror of sc and the sticky error words
     double* sc_host = nullptr;
     double* sc_map = nullptr;
@@ -807,7 +810,8 @@ void multi_drop_loops(gmg_handle* h);
 bool multi_ok(const gmg_handle* h, std::string* why);
 // Asynchronous per-load pieces, writing load l's scalar block h->mw->sc + l * SC_COUNT.
 void multi_norms(gmg_handle* h, int nl, const double* const* f, double* const* u);
-void multi_true_residuals(gmg_handle* h, int nl, const double* const* f, const double* const* u);
+// (adds the pending PCG steps to the iterates first)
+void multi_true_residuals(gmg_handle* h, int nl, const double* const* f, double* const* u);
 void multi_cast(gmg_handle* h, int nl, const double* const* f, const bool* cold);
 void multi_true_residual(gmg_handle* h, int l, const double* f, const double* u, bool into_r);
 // Per-load loop scalars (iteration count 0, tolerance, cap, ||f||, active flag) of all 16 slots.

@@ -239,13 +239,26 @@ __global__ void __launch_bounds__(32 * kLoads) k_mfinalize_check(const double* p
     }
 }
 
-// u_l (dense, FP64) += alpha_l p, r -= alpha_l q, partial ||r_l||^2, for the
-// loads still iterating (the others keep their values).  A block of 16 warps
-// takes 32 consecutive nodes, warp l load l: the FP64 iterate of a load is
-// read and written in 768-byte runs, and the records of a node's 16 loads are
-// read by the 16 warps of the same block.
+// w_l += alpha_l p (the double-float correction of load l's FP64 iterate,
+// dense numbering), r -= alpha_l q, partial ||r_l||^2, for the loads still
+// iterating (the others keep their values).  The product by the FP64 alpha is
+// formed exactly as ah p + (al p + e) and added with a TwoSum, on the FP32
+// pipes (the FP64 pipe, a small fraction of the FP32 rate on this part, bound
+// the FP64 update).  A block of 16 warps takes 32 consecutive nodes, warp l
+// load l: a load's correction is read and written in 768-byte runs, and the
+// records of a node's 16 loads are read by the 16 warps of the same block.
 constexpr int kPcgThreads = 32 * kLoads;
-__global__ void __launch_bounds__(kPcgThreads) k_mpcg_update(const __grid_constant__ F64Out u, int nl, float* r,
+__device__ __forceinline__ float2 df_add_prod(float2 w, float ah, float al, float p) {
+    const float ph = __fmul_rn(ah, p);
+    const float pl = __fmaf_rn(al, p, __fmaf_rn(ah, p, -ph));
+    const float s = __fadd_rn(w.x, ph);
+    const float bb = __fsub_rn(s, w.x);
+    const float e = __fadd_rn(__fsub_rn(w.x, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+    const float lo = __fadd_rn(w.y, __fadd_rn(pl, e));
+    const float hi = __fadd_rn(s, lo);
+    return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
+}
+__global__ void __launch_bounds__(kPcgThreads) k_mpcg_update(float2* wcor, long long n3, int nl, float* r,
                                                              const float* p, const float* q, int NX, int px,
                                                              long long nnp, const double* sc, double* partial,
                                                              int pstride) {
@@ -257,7 +270,8 @@ __global__ void __launch_bounds__(kPcgThreads) k_mpcg_update(const __grid_consta
     if (act) {
         const double alpha = c[SC_ALPHA];
         const float af = (float)alpha;
-        double* ul = u.p[l];
+        const float ah = af, al = (float)(alpha - (double)ah);
+        float2* wl = wcor + (long long)l * n3;
         for (long long n = blockIdx.x * 32LL + lane; n < nnp; n += (long long)gridDim.x * 32) {
             const long long row = n / px;
             const int i = (int)(n - row * px);
@@ -266,10 +280,10 @@ __global__ void __launch_bounds__(kPcgThreads) k_mpcg_update(const __grid_consta
             const float4 pv = reinterpret_cast<const float4*>(p)[qi];
             const float4 qv = reinterpret_cast<const float4*>(q)[qi];
             float4 rv = reinterpret_cast<float4*>(r)[qi];
-            double* ud = ul + GMG_B(3 * (row * NX + i), 3 * (nnp / px) * NX - 2, 501);
-            ud[0] = fma(alpha, f2d_exact(pv.x), ud[0]);
-            ud[1] = fma(alpha, f2d_exact(pv.y), ud[1]);
-            ud[2] = fma(alpha, f2d_exact(pv.z), ud[2]);
+            float2* wd = wl + GMG_B(3 * (row * NX + i), n3 - 2, 501);
+            wd[0] = df_add_prod(wd[0], ah, al, pv.x);
+            wd[1] = df_add_prod(wd[1], ah, al, pv.y);
+            wd[2] = df_add_prod(wd[2], ah, al, pv.z);
             rv.x = fmaf(-af, qv.x, rv.x);
             rv.y = fmaf(-af, qv.y, rv.y);
             rv.z = fmaf(-af, qv.z, rv.z);
@@ -283,6 +297,19 @@ __global__ void __launch_bounds__(kPcgThreads) k_mpcg_update(const __grid_consta
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) partial[(long long)l * pstride + blockIdx.x] = v;
+}
+
+// u_l += w_l (FP64), then w_l = 0, for loads 0..nl-1.
+__global__ void k_mflush(const __grid_constant__ F64Out u, int nl, float2* wcor, long long n3) {
+    pdl_entry();
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nl * n3;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(q / n3);
+        const long long i = q - l * n3;
+        const float2 w = wcor[q];
+        u.p[l][i] = u.p[l][i] + (f2d_exact(w.x) + f2d_exact(w.y));
+        wcor[q] = make_float2(0.f, 0.f);
+    }
 }
 
 // p = z + beta_l p for the loads still iterating.
@@ -1159,6 +1186,9 @@ int multi_workspace(gmg_handle* h) {
     // two partial arrays of kLoads rows (the norms kernel fills both)
     if (int rc = malloc_dev(h, &w->partials, (size_t)2 * kLoads * w->pstride); rc != GMG_OK) return bad(rc);
     if (int rc = malloc_dev(h, &w->sc, (size_t)kLoads * SC_COUNT); rc != GMG_OK) return bad(rc);
+    if (int rc = malloc_dev(h, &w->wcor, (size_t)kLoads * 3 * l0.nn); rc != GMG_OK) return bad(rc);
+    if (cudaMemsetAsync(w->wcor, 0, sizeof(float2) * kLoads * 3 * (size_t)l0.nn, s) != cudaSuccess)
+        return bad(mfail(GMG_ERR_CUDA, "multi memset"));
     if (cudaMemsetAsync(w->sc, 0, sizeof(double) * kLoads * SC_COUNT, s) != cudaSuccess)
         return bad(mfail(GMG_ERR_CUDA, "multi memset"));
     if (h->nL > 0 && h->Ainv && !h->coarse_pcg) {
@@ -1377,14 +1407,15 @@ void mpcg_restart(gmg_handle* h, int nl) {
 
 // cond: inside the captured loop (sets the while condition); host_check: the
 // host-driven loop (the same per-load test, read back by the host).
-void mpcg_step(gmg_handle* h, const F64Out& u, int nl, const cudaGraphConditionalHandle* cond, bool host_check = false) {
+void mpcg_step(gmg_handle* h, int nl, const cudaGraphConditionalHandle* cond, bool host_check = false) {
     MultiWork& w = *h->mw;
     const Level& l0 = h->lev[0];
     cudaStream_t s = h->stream;
     mlevel_apply(h, 0, w.p, w.q, SC_PQ, FIN_ALPHA, nl);
     note_launch();
-    pdl_launch(k_mpcg_update, dim3(kMBlocks), dim3(kPcgThreads), 0, s, u, nl, w.r, (const float*)w.p,
+    pdl_launch(k_mpcg_update, dim3(kMBlocks), dim3(kPcgThreads), 0, s, w.wcor, 3 * l0.nn, nl, w.r, (const float*)w.p,
                (const float*)w.q, l0.nx + 1, l0.px, l0.nnp, (const double*)w.sc, w.partials, w.pstride);
+    w.w_dirty = true;
     note_launch();
     if (cond || host_check)
         pdl_launch(k_mfinalize_check, dim3(1), dim3(32 * kLoads), 0, s, (const double*)w.partials, kMBlocks, w.pstride,
@@ -1409,8 +1440,7 @@ void mpcg_direction(gmg_handle* h, int nl) {
 // into graph g as an independent branch, on stream cap.
 bool multi_capture_loop(gmg_handle* h, double* const* u, int nl, cudaGraph_t g, cudaStream_t cap,
                         unsigned long long& prefix, unsigned long long& body_k) {
-    F64Out up{};
-    for (int l = 0; l < nl; ++l) up.p[l] = u[l];
+    (void)u;  // the loop updates the handle's correction; u keys the captured graph
     const unsigned long long l0 = g_kernel_launches.load();
     cudaStream_t user = h->stream;
     h->stream = cap;
@@ -1421,7 +1451,7 @@ bool multi_capture_loop(gmg_handle* h, double* const* u, int nl, cudaGraph_t g, 
     if (ok) ok = cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
     if (ok) {
         mpcg_restart(h, nl);
-        mpcg_step(h, up, nl, &cond);
+        mpcg_step(h, nl, &cond);
         l1 = g_kernel_launches.load();
         cudaStreamCaptureStatus st{};
         cudaGraph_t cg = nullptr;
@@ -1445,7 +1475,7 @@ bool multi_capture_loop(gmg_handle* h, double* const* u, int nl, cudaGraph_t g, 
         ok = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
         if (ok) {
             mpcg_direction(h, nl);
-            mpcg_step(h, up, nl, &cond);
+            mpcg_step(h, nl, &cond);
             l2 = g_kernel_launches.load();
             ok = cudaStreamEndCapture(cap, &body) == cudaSuccess;
         }
@@ -1466,6 +1496,10 @@ bool multi_capture_loop(gmg_handle* h, double* const* u, int nl, cudaGraph_t g, 
 void multi_norms(gmg_handle* h, int nl, const double* const* f, double* const* u) {
     MultiWork& w = *h->mw;
     const Level& l0 = h->lev[0];
+    if (w.w_dirty) {  // steps of an abandoned call: not part of any iterate
+        cudaMemsetAsync(w.wcor, 0, sizeof(float2) * kLoads * 3 * (size_t)l0.nn, h->stream);
+        w.w_dirty = false;
+    }
     F64Out uo{};
     F64In fi{};
     for (int l = 0; l < nl; ++l) {
@@ -1483,9 +1517,17 @@ void multi_norms(gmg_handle* h, int nl, const double* const* f, double* const* u
 }
 
 // The FP64 true residual of loads 0..nl-1 into their SC_TRR, one launch.
-void multi_true_residuals(gmg_handle* h, int nl, const double* const* f, const double* const* u) {
+void multi_true_residuals(gmg_handle* h, int nl, const double* const* f, double* const* u) {
     MultiWork& w = *h->mw;
     const Level& l0 = h->lev[0];
+    if (w.w_dirty) {  // the PCG steps since the last flush into the FP64 iterates
+        F64Out uo{};
+        for (int l = 0; l < nl; ++l) uo.p[l] = u[l];
+        const long long n3 = 3 * l0.nn;
+        note_launch();
+        pdl_launch(k_mflush, dim3(kMBlocks), dim3(256), 0, h->stream, uo, nl, w.wcor, n3);
+        w.w_dirty = false;
+    }
     launch_fine_resid64_multi(l0.nx, l0.ny, l0.nz, h->E64, l0.mask, nl, f, u, w.sc, w.partials, w.pstride, h->gs64,
                               h->stream);
     note_launch();
@@ -1692,17 +1734,15 @@ int gmg_solve_multi(gmg_handle* h, int nl, const double* const* f, double* const
     if (any && !h->opt.device_loop) {
         // host-driven loop: the kernels of the captured loop, launched one by
         // one, with the per-load test read back after every step
-        F64Out up{};
-        for (int l = 0; l < nl; ++l) up.p[l] = u[l];
         mpcg_restart(h, nl);
-        mpcg_step(h, up, nl, nullptr, true);
+        mpcg_step(h, nl, nullptr, true);
         while (true) {
             MTRY(sync());
             bool go = false;
             for (int l = 0; l < nl; ++l) go = go || (state[l] == 0 && S(l, SC_ACT) != 0.0);
             if (!go) break;
             mpcg_direction(h, nl);
-            mpcg_step(h, up, nl, nullptr, true);
+            mpcg_step(h, nl, nullptr, true);
         }
     } else if (any) {
         // the captured loop for these iterates (cached per iterate list)
@@ -1737,6 +1777,7 @@ int gmg_solve_multi(gmg_handle* h, int nl, const double* const* f, double* const
             cudaGetLastError();
             return mfail(GMG_ERR_CUDA, "multi-load loop launch");
         }
+        w.w_dirty = true;  // the loop's steps went to the correction
         MTRY(sync());
         unsigned long long kmax = 0;
         for (int l = 0; l < nl; ++l) kmax = std::max<unsigned long long>(kmax, (unsigned long long)S(l, SC_IT));
