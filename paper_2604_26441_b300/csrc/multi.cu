@@ -1303,8 +1303,10 @@ void mlevel_resid(gmg_handle* h, int li, const float* b, const float* x, float* 
     }
 }
 
+// dold_from (level 0): read the previous increment from there instead of the
+// level's d vector (after a first step from zero, whose increment is its output).
 void msmooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, const float* xcur, float* xnext,
-                  bool write_d, bool dot, int nl) {
+                  bool write_d, bool dot, int nl, const float* dold_from = nullptr) {
     MultiWork& w = *h->mw;
     Level& l = h->lev[li];
     cudaStream_t s = h->stream;
@@ -1316,7 +1318,8 @@ void msmooth_step(gmg_handle* h, int li, int k, bool zero_init, const float* b, 
                        (const uint8_t*)l.maskp, l.nnp, (const double*)l.coef, xnext, write_d ? d : (float*)nullptr);
         } else {
             MFineArgs a = mfine_args(h, nl);
-            a.xin = xcur; a.b = b; a.out = xnext; a.step = k; a.dold = d; a.dnew = write_d ? d : nullptr;
+            a.xin = xcur; a.b = b; a.out = xnext; a.step = k; a.dold = dold_from ? dold_from : d;
+            a.dnew = write_d ? d : nullptr;
             a.partial = dot ? w.partials : nullptr;
             if (mfine_launch(h, FM_SMOOTH, dot, a) != GMG_OK) w.launch_err = 1;
         }
@@ -1338,11 +1341,17 @@ float* msmooth_pass(gmg_handle* h, int li, const float* b, float* cur, float* X,
     MultiWork& w = *h->mw;
     Level& l = h->lev[li];
     const bool cheb = l.kind == GMG_SMOOTHER_CHEBYSHEV;
+    // level 0: a first step from zero leaves d = x, so the next step reads its
+    // increment from that step's output and no copy of it is written
+    const float* d_alias = nullptr;
     for (int k = 0; k < l.degree; ++k) {
         float* next = (writes % 2 == 0) ? S : X;
         const bool last = k == l.degree - 1;
         const bool dot = last && dot_slot >= 0;
-        msmooth_step(h, li, k, zero_init && k == 0, b, cur, next, cheb && !last, dot, nl);
+        const bool alias = li == 0 && zero_init && k == 0;
+        msmooth_step(h, li, k, zero_init && k == 0, b, cur, next, cheb && !last && !alias, dot, nl,
+                     k == 1 ? d_alias : nullptr);
+        if (alias && cheb && !last) d_alias = next;
         if (dot) {
             note_launch();
             pdl_launch(k_mfinalize, dim3(kLoads), dim3(kMT), 0, h->stream, (const double*)w.partials,
